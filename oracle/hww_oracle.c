@@ -1,0 +1,1084 @@
+/*
+ * hww_oracle.c -- plain, slow, FP64 CPU oracle of one time step of the
+ * hybrid weight-window (HWW) Monte Carlo method of Shaw & Anistratov
+ * (arXiv 2512.19925).
+ *
+ * TEST INFRASTRUCTURE ONLY: tests, the smoke check and the CPU-baseline leg
+ * of the benchmark may use it; the library never does.  It shares no code
+ * with the CUDA path.
+ *
+ * What each part follows in the paper:
+ *   transport physics ............ Sec. 3, Eq. (HO_transport), BCs and IC
+ *   weight-window center ......... Sec. 2, Eq. (ww-center); ceiling/floor Eq. (ww-c&f)
+ *   split / roulette ............. Sec. 2 (N_d = ceil(w/ww), survival p = w/ww)
+ *   track-length tally ........... Sec. 3, Eq. (phi-mc)
+ *   time-crossing (census) tally . Sec. 3, Eq. (ct-mc); edge current by linear
+ *                                  interpolation of adjacent cell averages
+ *   LOSM equations ............... Sec. 3, Eqs. (losm), (theta-scheme),
+ *                                  (losm-0), (losm-1), (losm-disc-bc)
+ *   semi-implicit HLOSM .......... Sec. 3, Eqs. (losm-1-semi), (losm-disc-bc-semi)
+ *   moving-average filter ........ Sec. 4, Eq. (moving_average)
+ *   uniform combing .............. Sec. 5.1 (population control)
+ * Readings of passages the paper leaves open are listed next to the code
+ * that takes them.
+ *
+ * Floating point: every operation below is a single IEEE-754 double
+ * operation in the order written (build with -ffp-contract=off, no
+ * -ffast-math); fma() appears only where the numerics contract names it.
+ * Tallies are accumulated as 128-bit fixed-point integers, so their value does
+ * not depend on the order in which particles are processed.
+ */
+#include "hww_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Numerics contract                                                        */
+/* ------------------------------------------------------------------------ */
+
+enum { OR_VACUUM = 0, OR_REFLECT = 1 };
+enum { OR_MODE_HWW = 0, OR_MODE_ANALOG = 1, OR_MODE_LWW = 2 };
+enum { OR_SCALE_MEAN_WEIGHT = 0, OR_SCALE_LITERAL = 1 };
+enum {
+    K_TL_PHI = 0, K_TL_J, K_TL_F, K_CEN_PHI, K_CEN_J, K_CEN_F, K_BATCH_PHI, K_BOUNDARY,
+    K_WW_CENTER, K_CLOSURE_PHI, K_CLOSURE_J, K_CLOSURE_F
+};
+enum { E_ARG = -1, E_STATE = -2, E_OOM = -3, E_NUMERIC = -6 };
+
+#define MAX_EVENTS_PER_TRACK (1u << 30)
+#define MAX_DAUGHTERS (1u << 24)
+#define GRAZE_MU 0.01 /* surface-estimator cutoff: 1/|mu| -> 2/GRAZE_MU below it */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+ * 32x32->64 multiplications with a Weyl-sequence key schedule. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform on the open interval (0,1): the top 52 bits of the 64-bit word
+ * hi:lo, offset by half a unit, scaled by 2^-52.  Exact in double. */
+double or_u01(uint32_t lo, uint32_t hi) {
+    uint64_t x = ((uint64_t)hi << 32) | lo;
+    return ((double)(x >> 12) + 0.5) * 0x1p-52;
+}
+
+/* Natural logarithm of a positive normal double by the textbook reduction
+ * u = m 2^k with m in [sqrt(1/2), sqrt(2)) and log m = 2 atanh(s),
+ * s = (m-1)/(m+1), summed as the odd series 2s(1 + s^2/3 + s^4/5 + ...)
+ * through the s^22/23 term (|s| <= 0.1716), plus k ln 2 with ln 2 split into
+ * a 32-bit head and a tail.  The series is evaluated by Horner's rule with
+ * fused multiply-adds; both implementations follow this exact sequence. */
+static const double LN2_HI = 0x1.62e42fee00000p-1;
+static const double LN2_LO = 0x1.a39ef35793c76p-33;
+
+double or_log(double u) {
+    uint64_t b;
+    memcpy(&b, &u, sizeof b);
+    int k = (int)((b >> 52) & 0x7ff) - 1023;
+    uint64_t mb = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull; /* m in [1,2) */
+    double m;
+    memcpy(&m, &mb, sizeof m);
+    if (m > 0x1.6a09e667f3bcdp+0) { /* sqrt(2) rounded */
+        m = m * 0.5;
+        k = k + 1;
+    }
+    double f = m - 1.0;
+    double s = f / (m + 1.0);
+    double z = s * s;
+    double p = 1.0 / 23.0;
+    p = fma(p, z, 1.0 / 21.0);
+    p = fma(p, z, 1.0 / 19.0);
+    p = fma(p, z, 1.0 / 17.0);
+    p = fma(p, z, 1.0 / 15.0);
+    p = fma(p, z, 1.0 / 13.0);
+    p = fma(p, z, 1.0 / 11.0);
+    p = fma(p, z, 1.0 / 9.0);
+    p = fma(p, z, 1.0 / 7.0);
+    p = fma(p, z, 1.0 / 5.0);
+    p = fma(p, z, 1.0 / 3.0);
+    double s2 = s + s;
+    double tail = s2 * (z * p);          /* 2s(z/3 + z^2/5 + ...) */
+    double kd = (double)k;
+    double lo = fma(kd, LN2_LO, tail);
+    return fma(kd, LN2_HI, s2 + lo);
+}
+
+/* 128-bit two's-complement accumulator and its conversion to double:
+ * values that fit a signed 64-bit integer convert in one rounding,
+ * wider values as hi*2^64 + lo (two roundings). */
+typedef __int128 i128;
+
+static double conv128(i128 a) {
+    if (a >= -(i128)0x7fffffffffffffffLL - 1 && a <= (i128)0x7fffffffffffffffLL)
+        return (double)(int64_t)a;
+    int64_t hi = (int64_t)(a >> 64);
+    uint64_t lo = (uint64_t)a;
+    return (double)hi * 0x1p64 + (double)lo;
+}
+
+/* exponent E of w_bar (w_bar = m 2^E, m in [1,2)); 0 for w_bar == 0 */
+static int wbar_exponent(double wbar) {
+    if (!(wbar > 0.0)) return 0;
+    int e;
+    frexp(wbar, &e);   /* wbar = f 2^e, f in [0.5,1) */
+    return e - 1;
+}
+
+static int bit_length(int64_t n) {
+    int l = 0;
+    while (n > 0) { ++l; n >>= 1; }
+    return l;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem state                                                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double x, mu, tau, w;
+    int32_t cell;
+    uint32_t id;
+    uint64_t lin;
+    uint32_t e;
+} or_particle;
+
+typedef struct {
+    double x, mu, w;
+    int32_t cell;
+    uint32_t id;
+    uint64_t lin;
+} or_census;
+
+struct or_problem {
+    or_desc d;
+    int32_t I;
+    double *edges, *dx, *sigt, *inv_sigt, *c, *siga;
+    int xs_set, ww_set;
+    double rho, eps;
+    int32_t mode, scaling;
+    int64_t N;           /* particles per step = source particles */
+    int64_t n;           /* completed steps */
+    /* combed bank for the next step (x, mu, cell); weight w_bar each */
+    double *bx, *bmu;
+    int32_t* bcell;
+    int64_t nbank;
+    double wbar;
+    /* WW arrays for the current step */
+    double *ww_c, *ww_hi, *ww_lo;
+    double* ww_override;
+    int has_override;
+    /* fixed-point tallies of the last step (scale 2^(40-E)) */
+    i128 *tl_phi, *tl_j, *tl_f, *cen_w, *cen_wmu, *cen_wf, *batch;
+    i128 bnd[6];
+    int tally_shift;
+    /* closure / IC vectors at the end of the last step (paper indexing) */
+    double *clo_phi, *clo_J, *clo_F; /* I+2, I+1, I+2 */
+    double clo_PL, clo_PR;
+    /* LOSM solutions of the last step */
+    double *semi_phi, *semi_J, *full_phi, *full_J;
+    /* previous-step track-length flux (for lagged windows) */
+    double* prev_tl_phi;
+    int has_prev_tl;
+};
+
+static void* xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
+
+int or_create(const or_desc* d, or_problem** out) {
+    if (!d || !out) return E_ARG;
+    *out = NULL;
+    int32_t I = d->n_cells;
+    if (I < 1 || !d->edges || !(d->v > 0) || !(d->dt > 0) || d->particles_per_step < 1 ||
+        d->particles_per_step > 0x7fffffffLL || (d->theta != 0.5 && d->theta != 1.0) ||
+        d->n_var_batches < 1 || d->bc_left < 0 || d->bc_left > 1 || d->bc_right < 0 ||
+        d->bc_right > 1 || d->filter < 0 || d->filter > 1 || (d->filter == 1 && d->filter_k < 1))
+        return E_ARG;
+    for (int32_t i = 0; i < I; ++i)
+        if (!(d->edges[i + 1] > d->edges[i])) return E_ARG;
+    if (!(d->src_x >= d->edges[0] && d->src_x <= d->edges[I])) return E_ARG;
+    or_problem* p = (or_problem*)calloc(1, sizeof *p);
+    if (!p) return E_OOM;
+    p->d = *d;
+    p->I = I;
+    p->N = d->particles_per_step;
+    p->edges = xcalloc(I + 1, sizeof(double));
+    p->dx = xcalloc(I, sizeof(double));
+    p->sigt = xcalloc(I, sizeof(double));
+    p->inv_sigt = xcalloc(I, sizeof(double));
+    p->c = xcalloc(I, sizeof(double));
+    p->siga = xcalloc(I, sizeof(double));
+    p->ww_c = xcalloc(I, sizeof(double));
+    p->ww_hi = xcalloc(I, sizeof(double));
+    p->ww_lo = xcalloc(I, sizeof(double));
+    p->ww_override = xcalloc(I, sizeof(double));
+    p->tl_phi = xcalloc(I, sizeof(i128));
+    p->tl_j = xcalloc(I, sizeof(i128));
+    p->tl_f = xcalloc(I, sizeof(i128));
+    p->cen_w = xcalloc(I, sizeof(i128));
+    p->cen_wmu = xcalloc(I, sizeof(i128));
+    p->cen_wf = xcalloc(I, sizeof(i128));
+    p->batch = xcalloc((size_t)I * d->n_var_batches, sizeof(i128));
+    p->clo_phi = xcalloc(I + 2, sizeof(double));
+    p->clo_J = xcalloc(I + 1, sizeof(double));
+    p->clo_F = xcalloc(I + 2, sizeof(double));
+    p->semi_phi = xcalloc(I + 2, sizeof(double));
+    p->semi_J = xcalloc(I + 1, sizeof(double));
+    p->full_phi = xcalloc(I + 2, sizeof(double));
+    p->full_J = xcalloc(I + 1, sizeof(double));
+    p->prev_tl_phi = xcalloc(I, sizeof(double));
+    if (!p->edges || !p->dx || !p->sigt || !p->inv_sigt || !p->c || !p->siga || !p->ww_c ||
+        !p->ww_hi || !p->ww_lo || !p->ww_override || !p->tl_phi || !p->tl_j || !p->tl_f ||
+        !p->cen_w || !p->cen_wmu || !p->cen_wf || !p->batch || !p->clo_phi || !p->clo_J ||
+        !p->clo_F || !p->semi_phi || !p->semi_J || !p->full_phi || !p->full_J || !p->prev_tl_phi) {
+        or_destroy(p);
+        return E_OOM;
+    }
+    memcpy(p->edges, d->edges, sizeof(double) * (I + 1));
+    p->d.edges = p->edges;
+    for (int32_t i = 0; i < I; ++i) p->dx[i] = p->edges[i + 1] - p->edges[i];
+    p->wbar = 1.0;
+    p->rho = 1.0;
+    p->eps = 1e-3;
+    *out = p;
+    return 0;
+}
+
+void or_destroy(or_problem* p) {
+    if (!p) return;
+    free(p->edges); free(p->dx); free(p->sigt); free(p->inv_sigt); free(p->c); free(p->siga);
+    free(p->bx); free(p->bmu); free(p->bcell);
+    free(p->ww_c); free(p->ww_hi); free(p->ww_lo); free(p->ww_override);
+    free(p->tl_phi); free(p->tl_j); free(p->tl_f); free(p->cen_w); free(p->cen_wmu);
+    free(p->cen_wf); free(p->batch);
+    free(p->clo_phi); free(p->clo_J); free(p->clo_F);
+    free(p->semi_phi); free(p->semi_J); free(p->full_phi); free(p->full_J);
+    free(p->prev_tl_phi);
+    free(p);
+}
+
+int or_set_cross_sections(or_problem* p, const double* sigma_t, const double* c) {
+    if (!p || !sigma_t || !c) return E_ARG;
+    for (int32_t i = 0; i < p->I; ++i)
+        if (!(sigma_t[i] > 0) || !(c[i] >= 0 && c[i] <= 1) || !isfinite(sigma_t[i])) return E_ARG;
+    for (int32_t i = 0; i < p->I; ++i) {
+        p->sigt[i] = sigma_t[i];
+        p->inv_sigt[i] = 1.0 / sigma_t[i];
+        p->c[i] = c[i];
+        p->siga[i] = sigma_t[i] * (1.0 - c[i]); /* Sigma_t - Sigma_s (no fission) */
+    }
+    p->xs_set = 1;
+    return 0;
+}
+
+int or_set_ww_params(or_problem* p, double rho, double eps_min, int32_t mode, int32_t scaling) {
+    if (!p || !(rho >= 1.0) || !(eps_min > 0.0 && eps_min <= 1.0) || mode < 0 || mode > 2 ||
+        scaling < 0 || scaling > 1)
+        return E_ARG;
+    p->rho = rho;
+    p->eps = eps_min;
+    p->mode = mode;
+    p->scaling = scaling;
+    p->ww_set = 1;
+    return 0;
+}
+
+int or_set_ww_centers(or_problem* p, const double* centers) {
+    if (!p || !centers) return E_ARG;
+    for (int32_t i = 0; i < p->I; ++i) {
+        if (!(centers[i] > 0)) return E_ARG;
+        p->ww_override[i] = centers[i];
+    }
+    p->has_override = 1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Moving-average filter, Eq. (moving_average)                              */
+/* Reading: the base shrinks symmetrically near the ends,                   */
+/* k_m = min(k, m-1, M-m) for 1-based m, so the window never leaves the     */
+/* vector and the end values are kept.                                      */
+/* ------------------------------------------------------------------------ */
+int or_ma_filter(const double* in, double* out, int32_t m, int32_t k) {
+    if (!in || !out || m < 0 || k < 0) return E_ARG;
+    for (int32_t j = 1; j <= m; ++j) {
+        int32_t kk = k;
+        if (j - 1 < kk) kk = j - 1;
+        if (m - j < kk) kk = m - j;
+        double s = 0.0;
+        for (int32_t l = -kk; l <= kk; ++l) s = s + in[j - l - 1];
+        out[j - 1] = s / (double)(2 * kk + 1);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* LOSM solve, Eqs. (losm-0), (losm-1), (losm-disc-bc)                       */
+/*                                                                          */
+/* Unknowns in interleaved order u = (phi_0, J_0, phi_1, J_1, ..., phi_I,   */
+/* J_I, phi_{I+1}); rows: 0 left BC, 2i+1 first-moment equation on the     */
+/* half cells around edge x_i (i = 0..I), 2i balance on cell i (i = 1..I), */
+/* 2I+2 right BC.  The matrix is tridiagonal in this order and is solved   */
+/* by Gaussian elimination with partial pivoting (two rows compete per     */
+/* column, one extra super-diagonal of fill).                              */
+/*                                                                          */
+/* Arrays follow the paper's 1-based cell indexing:                         */
+/*   dx, sigma_t, sigma_a, q_*  : length I, entry i-1 is cell i            */
+/*   phi_old, F_old, F_new      : length I+2 (boundary, cells 1..I, boundary)*/
+/*   J_old, J_new               : length I+1 (edges x_0..x_I)              */
+/* Readings:                                                                 */
+/*  - the sign of the old-level gradient term in Eq. (losm-1) is taken as   */
+/*    (phi_{i+1} - phi_i), the one the continuous theta scheme gives;       */
+/*  - Sigma_hat_i averages the two cells that share edge x_i (cells i and   */
+/*    i+1), with the boundary edges using the single interior cell, the    */
+/*    same pairing as Delta x_hat_i;                                       */
+/*  - q_i is the source integrated over cell i (zero for a pulse start);    */
+/*  - a reflecting side replaces its BC row by J = 0;                      */
+/*  - inflow currents J_L, J_R are zero (vacuum).                          */
+/* ------------------------------------------------------------------------ */
+int or_losm_solve(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a,
+                  double v, double dt, double theta, int32_t bc_left, int32_t bc_right,
+                  const double* phi_old, const double* J_old, const double* F_old,
+                  const double* F_new, double PL_new, double PR_new,
+                  const double* q_old, const double* q_new, double* phi_new, double* J_new) {
+    if (I < 1 || !dx || !sigma_t || !sigma_a || !phi_old || !J_old || !F_old || !F_new ||
+        !phi_new || !J_new)
+        return E_ARG;
+    int32_t n = 2 * I + 3;
+    double* a = xcalloc(n, sizeof(double));  /* sub-diagonal  A[r][r-1] */
+    double* b = xcalloc(n, sizeof(double));  /* diagonal      A[r][r]   */
+    double* c = xcalloc(n, sizeof(double));  /* super         A[r][r+1] */
+    double* f = xcalloc(n, sizeof(double));  /* fill          A[r][r+2] */
+    double* r = xcalloc(n, sizeof(double));
+    if (!a || !b || !c || !f || !r) {
+        free(a); free(b); free(c); free(f); free(r);
+        return E_OOM;
+    }
+    const double vdt = v * dt;
+    const double tm1 = theta - 1.0;
+    /* left boundary row */
+    if (bc_left == OR_REFLECT) {
+        b[0] = 0.0; c[0] = 1.0; r[0] = 0.0;           /* J_0 = 0 */
+        /* keep the row well posed for pivoting: J_0 is column 1 */
+    } else {
+        b[0] = 0.5; c[0] = 1.0; r[0] = PL_new;         /* J_0 + phi_0/2 = P_L */
+    }
+    for (int32_t i = 0; i <= I; ++i) {
+        /* first-moment equation at edge x_i, row 2i+1 */
+        double dxl = (i >= 1) ? dx[i - 1] : 0.0;       /* cell i   (Delta x_0 = 0)     */
+        double dxr = (i <= I - 1) ? dx[i] : 0.0;       /* cell i+1 (Delta x_{I+1} = 0) */
+        double stl = (i >= 1) ? sigma_t[i - 1] : 0.0;
+        double str = (i <= I - 1) ? sigma_t[i] : 0.0;
+        double dxh = 0.5 * (dxl + dxr);
+        double sth = (stl * dxl + str * dxr) / (dxl + dxr);
+        int32_t row = 2 * i + 1;
+        a[row] = -theta / 3.0;                         /* phi_i     */
+        b[row] = dxh / vdt + theta * sth * dxh;        /* J_i       */
+        c[row] = theta / 3.0;                          /* phi_{i+1} */
+        double old = (phi_old[i + 1] - phi_old[i]) / 3.0 + sth * dxh * J_old[i] - F_old[i + 1] + F_old[i];
+        r[row] = dxh / vdt * J_old[i] + theta * (F_new[i + 1] - F_new[i]) + tm1 * old;
+    }
+    for (int32_t i = 1; i <= I; ++i) {
+        /* balance on cell i, row 2i */
+        int32_t row = 2 * i;
+        double dxi = dx[i - 1];
+        a[row] = -theta;                               /* J_{i-1} */
+        b[row] = dxi / vdt + theta * sigma_a[i - 1] * dxi;
+        c[row] = theta;                                /* J_i     */
+        double qn = q_new ? q_new[i - 1] : 0.0;
+        double qo = q_old ? q_old[i - 1] : 0.0;
+        double old = J_old[i] - J_old[i - 1] + sigma_a[i - 1] * dxi * phi_old[i] - qo;
+        r[row] = dxi / vdt * phi_old[i] + theta * qn + tm1 * old;
+    }
+    /* right boundary row */
+    if (bc_right == OR_REFLECT) {
+        a[n - 1] = 1.0; b[n - 1] = 0.0; r[n - 1] = 0.0; /* J_I = 0 */
+    } else {
+        a[n - 1] = 1.0; b[n - 1] = -0.5; r[n - 1] = -PR_new; /* J_I - phi_{I+1}/2 = -P_R */
+    }
+    /* Gaussian elimination with partial pivoting on the tridiagonal matrix */
+    for (int32_t k = 0; k < n - 1; ++k) {
+        if (fabs(a[k + 1]) > fabs(b[k])) {
+            /* swap rows k and k+1 (row k+1 has entries a,b,c in columns k..k+2) */
+            double t;
+            t = b[k]; b[k] = a[k + 1]; a[k + 1] = t;
+            t = c[k]; c[k] = b[k + 1]; b[k + 1] = t;
+            t = f[k]; f[k] = c[k + 1]; c[k + 1] = t;
+            t = r[k]; r[k] = r[k + 1]; r[k + 1] = t;
+        }
+        if (b[k] == 0.0) {
+            free(a); free(b); free(c); free(f); free(r);
+            return E_NUMERIC;
+        }
+        double l = a[k + 1] / b[k];
+        a[k + 1] = 0.0;
+        b[k + 1] = b[k + 1] - l * c[k];
+        c[k + 1] = c[k + 1] - l * f[k];
+        r[k + 1] = r[k + 1] - l * r[k];
+    }
+    if (b[n - 1] == 0.0) {
+        free(a); free(b); free(c); free(f); free(r);
+        return E_NUMERIC;
+    }
+    double* u = r; /* back substitution in place */
+    u[n - 1] = r[n - 1] / b[n - 1];
+    u[n - 2] = (r[n - 2] - c[n - 2] * u[n - 1]) / b[n - 2];
+    for (int32_t k = n - 3; k >= 0; --k) u[k] = (r[k] - c[k] * u[k + 1] - f[k] * u[k + 2]) / b[k];
+    for (int32_t i = 0; i <= I + 1; ++i) phi_new[i] = u[2 * i];
+    for (int32_t i = 0; i <= I; ++i) J_new[i] = u[2 * i + 1];
+    free(a); free(b); free(c); free(f); free(r);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Uniform comb (Sec. 5.1)                                                   */
+/* Census particles in canonical order (source id, then lineage key) occupy */
+/* consecutive intervals of their fixed-point weights on [0, W).  Teeth sit */
+/* at (k + u) W / N, k = 0..N-1; tooth k becomes particle k of the next     */
+/* step.  The first tooth at or after a cumulative weight C is              */
+/* ceil(N C / W - u) evaluated in doubles (monotone in C), with C = W       */
+/* mapped to N so the copy counts sum to exactly N.                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint32_t id;
+    uint64_t lin;
+    int64_t idx;
+} or_key;
+
+static int key_cmp(const void* A, const void* B) {
+    const or_key* a = (const or_key*)A;
+    const or_key* b = (const or_key*)B;
+    if (a->id != b->id) return a->id < b->id ? -1 : 1;
+    if (a->lin != b->lin) return a->lin < b->lin ? -1 : 1;
+    return 0;
+}
+
+static int64_t first_tooth(uint64_t C, uint64_t W, int64_t N, double u) {
+    if (C == W) return N;
+    double q = ((double)N * (double)C) / (double)W - u;
+    double k = ceil(q);
+    if (k < 0.0) return 0;
+    if (k > (double)N) return N;
+    return (int64_t)k;
+}
+
+int or_comb(int64_t m, const uint32_t* id, const uint64_t* lin, const uint64_t* wfx, int64_t n,
+            double u, int32_t* src_of_slot) {
+    if (m < 0 || n < 0 || !src_of_slot || (m > 0 && (!id || !lin || !wfx))) return E_ARG;
+    or_key* k = (or_key*)xcalloc(m, sizeof(or_key));
+    if (!k) return E_OOM;
+    uint64_t W = 0;
+    for (int64_t j = 0; j < m; ++j) {
+        k[j].id = id[j];
+        k[j].lin = lin[j];
+        k[j].idx = j;
+        W += wfx[j];
+    }
+    qsort(k, (size_t)m, sizeof(or_key), key_cmp);
+    for (int64_t s = 0; s < n; ++s) src_of_slot[s] = -1;
+    if (W == 0) {
+        free(k);
+        return 0;
+    }
+    uint64_t C = 0;
+    for (int64_t j = 0; j < m; ++j) {
+        int64_t k0 = first_tooth(C, W, n, u);
+        C += wfx[k[j].idx];
+        int64_t k1 = first_tooth(C, W, n, u);
+        for (int64_t s = k0; s < k1; ++s) src_of_slot[s] = (int32_t)k[j].idx;
+    }
+    free(k);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One time step                                                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    or_particle* v;
+    int64_t n, cap;
+} pstack;
+
+static int ps_push(pstack* s, const or_particle* q) {
+    if (s->n == s->cap) {
+        int64_t nc = s->cap ? 2 * s->cap : 1024;
+        or_particle* nv = (or_particle*)realloc(s->v, sizeof(or_particle) * nc);
+        if (!nv) return E_OOM;
+        s->v = nv;
+        s->cap = nc;
+    }
+    s->v[s->n++] = *q;
+    return 0;
+}
+
+typedef struct {
+    or_census* v;
+    int64_t n, cap;
+} cbank;
+
+static int cb_push(cbank* s, const or_census* q) {
+    if (s->n == s->cap) {
+        int64_t nc = s->cap ? 2 * s->cap : 1024;
+        or_census* nv = (or_census*)realloc(s->v, sizeof(or_census) * nc);
+        if (!nv) return E_OOM;
+        s->v = nv;
+        s->cap = nc;
+    }
+    s->v[s->n++] = *q;
+    return 0;
+}
+
+static void philox_event(const or_particle* q, uint32_t word, const uint32_t key[2], uint32_t r[4]) {
+    uint32_t ctr[4] = {q->id, (uint32_t)q->lin, (uint32_t)(q->lin >> 32), word};
+    or_philox4x32_10(ctr, key, r);
+}
+
+/* lineage key of daughter j of a split at event e: Philox of (lin, e, j)
+ * under a fixed key */
+static uint64_t lineage_hash(uint64_t lin, uint32_t e, uint32_t j) {
+    uint32_t ctr[4] = {(uint32_t)lin, (uint32_t)(lin >> 32), e, j};
+    uint32_t key[2] = {0x4C494E45u, 0x41474521u};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    return ((uint64_t)r[1] << 32) | r[0];
+}
+
+/* round-to-nearest-even of x * 2^s to a signed 64-bit integer */
+static int64_t to_fixed(double x, int s) { return llrint(ldexp(x, s)); }
+
+/* Closure and initial-condition vectors from the census (time-crossing)
+ * tallies, Eq. (ct-mc).  Readings: phi_0, phi_{I+1}, F_0, F_{I+1} copy the
+ * adjacent cell; interior edge currents interpolate the two adjacent cell
+ * averages linearly in space; the boundary edge current follows the BC
+ * relation (0 on a reflecting side); the MA filter, when on, acts on the
+ * cell vectors of phi and F and on the edge vector of J. */
+static void build_closures(or_problem* p, const double* cphi, const double* cJ, const double* cF,
+                           double PL, double PR) {
+    int32_t I = p->I;
+    double* tmp = xcalloc(I + 1, sizeof(double));
+    double* tmp2 = xcalloc(I + 1, sizeof(double));
+    for (int32_t i = 1; i <= I; ++i) {
+        p->clo_phi[i] = cphi[i - 1];
+        p->clo_F[i] = cF[i - 1];
+    }
+    for (int32_t i = 1; i <= I - 1; ++i) {
+        double dl = p->dx[i - 1], dr = p->dx[i];
+        p->clo_J[i] = (cJ[i - 1] * dr + cJ[i] * dl) / (dl + dr);
+    }
+    p->clo_phi[0] = p->clo_phi[1];
+    p->clo_phi[I + 1] = p->clo_phi[I];
+    p->clo_F[0] = p->clo_F[1];
+    p->clo_F[I + 1] = p->clo_F[I];
+    p->clo_J[0] = (p->d.bc_left == OR_REFLECT) ? 0.0 : (-0.5 * p->clo_phi[0] + PL);
+    p->clo_J[I] = (p->d.bc_right == OR_REFLECT) ? 0.0 : (0.5 * p->clo_phi[I + 1] - PR);
+    p->clo_PL = (p->d.bc_left == OR_REFLECT) ? 0.0 : PL;
+    p->clo_PR = (p->d.bc_right == OR_REFLECT) ? 0.0 : PR;
+    if (p->d.filter == 1) {
+        or_ma_filter(p->clo_phi + 1, tmp, I, p->d.filter_k);
+        memcpy(p->clo_phi + 1, tmp, sizeof(double) * I);
+        or_ma_filter(p->clo_F + 1, tmp, I, p->d.filter_k);
+        memcpy(p->clo_F + 1, tmp, sizeof(double) * I);
+        or_ma_filter(p->clo_J, tmp2, I + 1, p->d.filter_k);
+        memcpy(p->clo_J, tmp2, sizeof(double) * (I + 1));
+        /* the end values are unchanged by the filter, so the copies above hold */
+    }
+    free(tmp);
+    free(tmp2);
+}
+
+/* Exact moments of the unit isotropic plane pulse at t = 0 (step-1 IC).
+ * Reading: the pulse goes to the cell containing src_x, split evenly when
+ * src_x is an interior edge; on a domain end it belongs to the end cell.
+ * phi = v * density; J = F = P = 0 for an isotropic pulse. */
+static void source_moments(or_problem* p) {
+    int32_t I = p->I;
+    for (int32_t i = 0; i <= I + 1; ++i) p->clo_phi[i] = 0.0;
+    for (int32_t i = 0; i <= I; ++i) p->clo_J[i] = 0.0;
+    for (int32_t i = 0; i <= I + 1; ++i) p->clo_F[i] = 0.0;
+    p->clo_PL = p->clo_PR = 0.0;
+    double xs = p->d.src_x, v = p->d.v;
+    int32_t edge = -1;
+    for (int32_t i = 0; i <= I; ++i)
+        if (p->edges[i] == xs) edge = i;
+    if (edge == 0) {
+        p->clo_phi[1] = v / p->dx[0];
+    } else if (edge == I) {
+        p->clo_phi[I] = v / p->dx[I - 1];
+    } else if (edge > 0) {
+        p->clo_phi[edge] = 0.5 * v / p->dx[edge - 1];
+        p->clo_phi[edge + 1] = 0.5 * v / p->dx[edge];
+    } else {
+        for (int32_t i = 0; i < I; ++i)
+            if (xs > p->edges[i] && xs < p->edges[i + 1]) p->clo_phi[i + 1] = v / p->dx[i];
+    }
+    p->clo_phi[0] = p->clo_phi[1];
+    p->clo_phi[I + 1] = p->clo_phi[I];
+}
+
+/* WW centers, Eq. (ww-center), from a cell vector phi_tilde (length I):
+ * phi_tilde clamped at 0 (a CN solution can undershoot ahead of a front),
+ * normalised by its maximum, floored by eps, scaled by w_bar
+ * (MEAN_WEIGHT) or 1 (LITERAL); ceiling rho*center, floor center/rho,
+ * Eq. (ww-c&f). */
+static void ww_from_flux(or_problem* p, const double* phit) {
+    int32_t I = p->I;
+    double mx = 0.0;
+    for (int32_t i = 0; i < I; ++i) {
+        double f = phit[i] > 0.0 ? phit[i] : 0.0;
+        if (f > mx) mx = f;
+    }
+    double scale = (p->scaling == OR_SCALE_MEAN_WEIGHT) ? p->wbar : 1.0;
+    for (int32_t i = 0; i < I; ++i) {
+        double f = phit[i] > 0.0 ? phit[i] : 0.0;
+        double ratio = (mx > 0.0) ? f / mx : 1.0;
+        double b = ratio * (1.0 - p->eps) + p->eps;
+        double ctr = scale * b;
+        p->ww_c[i] = ctr;
+        p->ww_hi[i] = ctr * p->rho;
+        p->ww_lo[i] = ctr / p->rho;
+    }
+}
+
+/* locate the birth cell of src_x for direction mu.  Reading: x_{k} <= x <
+ * x_{k+1}, except on an interior edge with mu < 0, where the left cell is
+ * taken; on a domain end the end cell. */
+static int32_t birth_cell(const or_problem* p, double x, double mu) {
+    int32_t I = p->I;
+    if (x <= p->edges[0]) return 0;
+    if (x >= p->edges[I]) return I - 1;
+    for (int32_t i = 0; i < I; ++i) {
+        if (x == p->edges[i] && i > 0) return mu < 0.0 ? i - 1 : i;
+        if (x > p->edges[i] && x < p->edges[i + 1]) return i;
+    }
+    return I - 1;
+}
+
+int or_run_step(or_problem* p, or_stats* st) {
+    if (!p) return E_ARG;
+    if (!p->xs_set || !p->ww_set) return E_STATE;
+    const int32_t I = p->I;
+    const int32_t B = p->d.n_var_batches;
+    const int64_t N = p->N;
+    const int64_t n = p->n + 1;
+    const double v = p->d.v;
+    const double tau0 = v * p->d.dt;
+    or_stats s;
+    memset(&s, 0, sizeof s);
+
+    /* 1. ICs and lagged closures: exact pulse moments for n = 1, else the
+     *    closure vectors built at the end of step n-1. */
+    if (n == 1) source_moments(p);
+    double* phi_old = xcalloc(I + 2, sizeof(double));
+    double* J_old = xcalloc(I + 1, sizeof(double));
+    double* F_old = xcalloc(I + 2, sizeof(double));
+    memcpy(phi_old, p->clo_phi, sizeof(double) * (I + 2));
+    memcpy(J_old, p->clo_J, sizeof(double) * (I + 1));
+    memcpy(F_old, p->clo_F, sizeof(double) * (I + 2));
+    double PL_old = p->clo_PL, PR_old = p->clo_PR;
+
+    /* 2. semi-implicit HLOSM, Eqs. (losm-0), (losm-1-semi), (losm-disc-bc-semi):
+     *    the new-level closure is the lagged one. */
+    int rc = or_losm_solve(I, p->dx, p->sigt, p->siga, v, p->d.dt, p->d.theta, p->d.bc_left,
+                           p->d.bc_right, phi_old, J_old, F_old, F_old, PL_old, PR_old, NULL, NULL,
+                           p->semi_phi, p->semi_J);
+    if (rc) goto fail;
+
+    /* 3. weight windows */
+    if (p->has_override) {
+        for (int32_t i = 0; i < I; ++i) {
+            double ctr = p->ww_override[i];
+            p->ww_c[i] = ctr;
+            p->ww_hi[i] = ctr * p->rho;
+            p->ww_lo[i] = ctr / p->rho;
+        }
+        p->has_override = 0;
+    } else if (p->mode == OR_MODE_HWW) {
+        ww_from_flux(p, p->semi_phi + 1);
+    } else if (p->mode == OR_MODE_LWW && p->has_prev_tl) {
+        ww_from_flux(p, p->prev_tl_phi);
+    }
+    const int ww_on = (p->mode == OR_MODE_HWW) || (p->mode == OR_MODE_LWW && p->has_prev_tl);
+
+    /* 4. tracking */
+    const int E = wbar_exponent(p->wbar);
+    const int S = 40 - E;                       /* tally fixed-point shift */
+    p->tally_shift = S;
+    const int Sc = 59 - E - bit_length(N);      /* comb weight shift */
+    const uint32_t key[2] = {(uint32_t)p->d.seed, (uint32_t)(p->d.seed >> 32) ^ (uint32_t)n};
+    for (int32_t i = 0; i < I; ++i) {
+        p->tl_phi[i] = p->tl_j[i] = p->tl_f[i] = 0;
+        p->cen_w[i] = p->cen_wmu[i] = p->cen_wf[i] = 0;
+    }
+    for (int64_t i = 0; i < (int64_t)I * B; ++i) p->batch[i] = 0;
+    for (int j = 0; j < 6; ++j) p->bnd[j] = 0;
+
+    pstack stack = {0};
+    cbank census = {0};
+    int64_t nstart = (n == 1) ? N : p->nbank;
+    s.n_start = nstart;
+    for (int64_t k = nstart - 1; k >= 0; --k) {
+        or_particle q;
+        q.id = (uint32_t)k;
+        q.lin = 0;
+        q.e = 0;
+        q.tau = tau0;
+        q.w = p->wbar;
+        if (n == 1) {
+            uint32_t ctr[4] = {(uint32_t)k, 0u, 0u, 0xFFFFFFFFu}, r[4];
+            or_philox4x32_10(ctr, key, r);
+            q.mu = 2.0 * or_u01(r[0], r[1]) - 1.0;
+            q.x = p->d.src_x;
+            if (q.x <= p->edges[0] && q.mu < 0.0 && p->d.bc_left == OR_REFLECT) q.mu = -q.mu;
+            if (q.x >= p->edges[I] && q.mu > 0.0 && p->d.bc_right == OR_REFLECT) q.mu = -q.mu;
+            q.cell = birth_cell(p, q.x, q.mu);
+        } else {
+            q.x = p->bx[k];
+            q.mu = p->bmu[k];
+            q.cell = p->bcell[k];
+        }
+        if (ps_push(&stack, &q)) { rc = E_OOM; goto fail_track; }
+    }
+
+    while (stack.n > 0) {
+        or_particle q = stack.v[--stack.n];
+        for (;;) {
+            if (q.e >= MAX_EVENTS_PER_TRACK) { s.error = E_NUMERIC; break; }
+            uint32_t r[4];
+            philox_event(&q, 2u * q.e, key, r);
+            const double uf = or_u01(r[0], r[1]);
+            const double uc = or_u01(r[2], r[3]);
+            const int32_t k = q.cell;
+            const double inv_mu = 1.0 / q.mu;
+            const double dcoll = (-or_log(uf)) * p->inv_sigt[k];
+            const double xe = (q.mu > 0.0) ? p->edges[k + 1] : p->edges[k];
+            const double dedge = (xe - q.x) * inv_mu;
+            const double dcens = q.tau;
+            int ev; /* 0 census, 1 crossing, 2 collision */
+            double l;
+            if (dcens <= dedge && dcens <= dcoll) { ev = 0; l = dcens; }
+            else if (dedge <= dcoll) { ev = 1; l = dedge; }
+            else { ev = 2; l = dcoll; }
+            /* track-length tallies, Eq. (phi-mc) */
+            const double wl = q.w * l;
+            const double wlmu = wl * q.mu;
+            const double wlf = wl * (1.0 / 3.0 - q.mu * q.mu);
+            p->tl_phi[k] += to_fixed(wl, S);
+            p->tl_j[k] += to_fixed(wlmu, S);
+            p->tl_f[k] += to_fixed(wlf, S);
+            p->batch[(int64_t)(q.id % (uint32_t)B) * I + k] += to_fixed(wl, S);
+            s.segments++;
+            /* move */
+            if (ev == 1) {
+                q.x = xe;
+            } else {
+                double xn = q.x + q.mu * l;
+                if (xn < p->edges[k]) xn = p->edges[k];
+                if (xn > p->edges[k + 1]) xn = p->edges[k + 1];
+                q.x = xn;
+            }
+            q.tau = (ev == 0) ? 0.0 : q.tau - l;
+            const uint32_t e_ev = q.e;
+            q.e = q.e + 1;
+            if (ev == 0) {
+                /* census: time-crossing tallies, Eq. (ct-mc) */
+                const double wmu = q.w * q.mu;
+                const double wf = q.w * (1.0 / 3.0 - q.mu * q.mu);
+                p->cen_w[k] += to_fixed(q.w, S);
+                p->cen_wmu[k] += to_fixed(wmu, S);
+                p->cen_wf[k] += to_fixed(wf, S);
+                or_census cq = {q.x, q.mu, q.w, q.cell, q.id, q.lin};
+                if (cb_push(&census, &cq)) { rc = E_OOM; goto fail_track; }
+                s.census++;
+                if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
+                break;
+            }
+            int need_ww = 0;
+            int have_r2 = 0;
+            uint32_t r2[4];
+            if (ev == 1) {
+                s.crossings++;
+                const int32_t nk = (q.mu > 0.0) ? k + 1 : k - 1;
+                if (nk < 0 || nk >= I) {
+                    const int side = (nk < 0) ? 0 : 1;
+                    const int32_t bc = side ? p->d.bc_right : p->d.bc_left;
+                    const double amu = fabs(q.mu);
+                    const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
+                    if (bc == OR_VACUUM) {
+                        /* surface estimators for the boundary closures:
+                         * phi_b ~ w/|mu|, F_b ~ w(1/3-mu^2)/|mu|, P_b ~ w(1/2-|mu|)/|mu| */
+                        const double wi = q.w * ia;
+                        p->bnd[3 * side + 0] += to_fixed(wi, S);
+                        p->bnd[3 * side + 1] += to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu), S);
+                        p->bnd[3 * side + 2] += to_fixed(wi * (0.5 - amu), S);
+                        s.leaked++;
+                        if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
+                        break;
+                    }
+                    q.mu = -q.mu; /* specular reflection, stays in cell k */
+                    s.reflections++;
+                } else {
+                    q.cell = nk;
+                }
+                need_ww = 1;
+            } else {
+                s.collisions++;
+                if (uc >= p->c[k]) {
+                    s.absorbed++;
+                    if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
+                    break;
+                }
+                philox_event(&q, 2u * e_ev + 1u, key, r2);
+                have_r2 = 1;
+                q.mu = 2.0 * or_u01(r2[0], r2[1]) - 1.0;
+                s.scatters++;
+                need_ww = 1;
+            }
+            if (need_ww && ww_on) {
+                const int32_t kc = q.cell;
+                if (q.w > p->ww_hi[kc]) {
+                    const double ratio = q.w / p->ww_c[kc];
+                    const double ndd = ceil(ratio);
+                    if (ndd > (double)MAX_DAUGHTERS) { s.error = E_NUMERIC; break; }
+                    const uint32_t nd = (uint32_t)ndd;
+                    const double wd = q.w / (double)nd;
+                    s.split_events++;
+                    s.daughters += nd - 1;
+                    for (uint32_t j = nd - 1; j >= 1; --j) {
+                        or_particle dq = q;
+                        dq.w = wd;
+                        dq.lin = lineage_hash(q.lin, e_ev, j);
+                        dq.e = 0;
+                        if (ps_push(&stack, &dq)) { rc = E_OOM; goto fail_track; }
+                    }
+                    q.w = wd;
+                    q.lin = lineage_hash(q.lin, e_ev, 0);
+                    q.e = 0;
+                } else if (q.w < p->ww_lo[kc]) {
+                    if (!have_r2) philox_event(&q, 2u * e_ev + 1u, key, r2);
+                    const double ur = or_u01(r2[2], r2[3]);
+                    const double ps = q.w / p->ww_c[kc];
+                    if (ur < ps) {
+                        q.w = p->ww_c[kc];
+                        s.roulette_survivals++;
+                    } else {
+                        s.roulette_kills++;
+                        if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    free(stack.v);
+    stack.v = NULL;
+
+    /* 5. normalised census tallies -> closures at t^n -> fully implicit HLOSM */
+    {
+        double* cphi = xcalloc(I, sizeof(double));
+        double* cJ = xcalloc(I, sizeof(double));
+        double* cF = xcalloc(I, sizeof(double));
+        for (int32_t i = 0; i < I; ++i) {
+            const double den = (double)N * p->dx[i];
+            cphi[i] = (v * ldexp(conv128(p->cen_w[i]), -S)) / den;
+            cJ[i] = (v * ldexp(conv128(p->cen_wmu[i]), -S)) / den;
+            cF[i] = (v * ldexp(conv128(p->cen_wf[i]), -S)) / den;
+        }
+        const double PL = ldexp(conv128(p->bnd[2]), -S) / ((double)N * p->d.dt);
+        const double PR = ldexp(conv128(p->bnd[5]), -S) / ((double)N * p->d.dt);
+        build_closures(p, cphi, cJ, cF, PL, PR);
+        free(cphi); free(cJ); free(cF);
+        rc = or_losm_solve(I, p->dx, p->sigt, p->siga, v, p->d.dt, p->d.theta, p->d.bc_left,
+                           p->d.bc_right, phi_old, J_old, F_old, p->clo_F, p->clo_PL, p->clo_PR,
+                           NULL, NULL, p->full_phi, p->full_J);
+        if (rc) goto fail_track;
+        for (int32_t i = 0; i < I; ++i)
+            p->prev_tl_phi[i] = ldexp(conv128(p->tl_phi[i]), -S) / (((double)N * p->dx[i]) * p->d.dt);
+        p->has_prev_tl = 1;
+    }
+
+    /* 6. uniform comb to N */
+    {
+        const int64_t m = census.n;
+        uint32_t* ids = xcalloc(m, sizeof(uint32_t));
+        uint64_t* lins = xcalloc(m, sizeof(uint64_t));
+        uint64_t* wfx = xcalloc(m, sizeof(uint64_t));
+        int32_t* src = xcalloc(N, sizeof(int32_t));
+        uint64_t W = 0;
+        for (int64_t j = 0; j < m; ++j) {
+            ids[j] = census.v[j].id;
+            lins[j] = census.v[j].lin;
+            wfx[j] = (uint64_t)to_fixed(census.v[j].w, Sc);
+            W += wfx[j];
+        }
+        /* lineage collisions: equal (id, lineage) pairs */
+        {
+            or_key* kk = xcalloc(m, sizeof(or_key));
+            for (int64_t j = 0; j < m; ++j) { kk[j].id = ids[j]; kk[j].lin = lins[j]; kk[j].idx = j; }
+            qsort(kk, (size_t)m, sizeof(or_key), key_cmp);
+            for (int64_t j = 1; j < m; ++j)
+                if (kk[j].id == kk[j - 1].id && kk[j].lin == kk[j - 1].lin) s.lineage_collisions++;
+            free(kk);
+        }
+        uint32_t cctr[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xC0B0u}, r[4];
+        or_philox4x32_10(cctr, key, r);
+        const double u = or_u01(r[0], r[1]);
+        or_comb(m, ids, lins, wfx, N, u, src);
+        free(p->bx); free(p->bmu); free(p->bcell);
+        p->bx = xcalloc(N, sizeof(double));
+        p->bmu = xcalloc(N, sizeof(double));
+        p->bcell = xcalloc(N, sizeof(int32_t));
+        if (W == 0) {
+            p->nbank = 0;
+            p->wbar = 0.0;
+        } else {
+            for (int64_t k = 0; k < N; ++k) {
+                const or_census* cq = &census.v[src[k]];
+                p->bx[k] = cq->x;
+                p->bmu[k] = cq->mu;
+                p->bcell[k] = cq->cell;
+            }
+            p->nbank = N;
+            p->wbar = ldexp((double)W, -Sc) / (double)N;
+        }
+        s.n_next = p->nbank;
+        s.w_bar_next = p->wbar;
+        free(ids); free(lins); free(wfx); free(src);
+    }
+    free(census.v);
+    free(phi_old); free(J_old); free(F_old);
+    p->n = n;
+    if (st) *st = s;
+    return s.error;
+
+fail_track:
+    free(stack.v);
+    free(census.v);
+fail:
+    free(phi_old); free(J_old); free(F_old);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Read-out                                                                 */
+/* ------------------------------------------------------------------------ */
+
+int or_get_tallies(const or_problem* p, int32_t kind, double* out, int64_t n) {
+    if (!p || !out) return E_ARG;
+    const int32_t I = p->I, B = p->d.n_var_batches;
+    const int64_t N = p->N;
+    const int S = p->tally_shift;
+    const double v = p->d.v, dt = p->d.dt;
+    switch (kind) {
+    case K_TL_PHI: case K_TL_J: case K_TL_F: {
+        if (n < I) return E_ARG;
+        const i128* a = kind == K_TL_PHI ? p->tl_phi : kind == K_TL_J ? p->tl_j : p->tl_f;
+        for (int32_t i = 0; i < I; ++i) out[i] = ldexp(conv128(a[i]), -S) / (((double)N * p->dx[i]) * dt);
+        return 0;
+    }
+    case K_CEN_PHI: case K_CEN_J: case K_CEN_F: {
+        if (n < I) return E_ARG;
+        const i128* a = kind == K_CEN_PHI ? p->cen_w : kind == K_CEN_J ? p->cen_wmu : p->cen_wf;
+        for (int32_t i = 0; i < I; ++i) out[i] = (v * ldexp(conv128(a[i]), -S)) / ((double)N * p->dx[i]);
+        return 0;
+    }
+    case K_BATCH_PHI: {
+        if (n < (int64_t)I * B) return E_ARG;
+        for (int32_t b = 0; b < B; ++b) {
+            const int64_t nb = (b < N) ? (N - b - 1) / B + 1 : 0; /* ids with id mod B == b */
+            for (int32_t i = 0; i < I; ++i)
+                out[(int64_t)b * I + i] =
+                    nb ? ldexp(conv128(p->batch[(int64_t)b * I + i]), -S) / (((double)nb * p->dx[i]) * dt)
+                       : 0.0;
+        }
+        return 0;
+    }
+    case K_BOUNDARY: {
+        if (n < 6) return E_ARG;
+        for (int j = 0; j < 6; ++j) out[j] = ldexp(conv128(p->bnd[j]), -S) / ((double)N * dt);
+        return 0;
+    }
+    case K_WW_CENTER:
+        if (n < I) return E_ARG;
+        memcpy(out, p->ww_c, sizeof(double) * I);
+        return 0;
+    case K_CLOSURE_PHI:
+        if (n < I + 2) return E_ARG;
+        memcpy(out, p->clo_phi, sizeof(double) * (I + 2));
+        return 0;
+    case K_CLOSURE_J:
+        if (n < I + 1) return E_ARG;
+        memcpy(out, p->clo_J, sizeof(double) * (I + 1));
+        return 0;
+    case K_CLOSURE_F:
+        if (n < I + 2) return E_ARG;
+        memcpy(out, p->clo_F, sizeof(double) * (I + 2));
+        return 0;
+    default:
+        return E_ARG;
+    }
+}
+
+int or_get_tallies_raw(const or_problem* p, int32_t kind, int64_t* out, int64_t n) {
+    if (!p || !out) return E_ARG;
+    const int32_t I = p->I, B = p->d.n_var_batches;
+    const i128* a = NULL;
+    int64_t len = I;
+    switch (kind) {
+    case K_TL_PHI: a = p->tl_phi; break;
+    case K_TL_J: a = p->tl_j; break;
+    case K_TL_F: a = p->tl_f; break;
+    case K_CEN_PHI: a = p->cen_w; break;
+    case K_CEN_J: a = p->cen_wmu; break;
+    case K_CEN_F: a = p->cen_wf; break;
+    case K_BATCH_PHI: a = p->batch; len = (int64_t)I * B; break;
+    case K_BOUNDARY: a = p->bnd; len = 6; break;
+    default: return E_ARG;
+    }
+    if (n < 2 * len) return E_ARG;
+    for (int64_t i = 0; i < len; ++i) {
+        out[2 * i] = (int64_t)(uint64_t)a[i];
+        out[2 * i + 1] = (int64_t)(a[i] >> 64);
+    }
+    return 0;
+}
+
+int or_get_losm_solution(const or_problem* p, int32_t which, double* phi, double* J) {
+    if (!p || !phi || !J || which < 0 || which > 1) return E_ARG;
+    memcpy(phi, which == 0 ? p->semi_phi : p->full_phi, sizeof(double) * (p->I + 2));
+    memcpy(J, which == 0 ? p->semi_J : p->full_J, sizeof(double) * (p->I + 1));
+    return 0;
+}
+
+int or_get_ww(const or_problem* p, double* center, double* ceil_, double* floor_) {
+    if (!p) return E_ARG;
+    if (center) memcpy(center, p->ww_c, sizeof(double) * p->I);
+    if (ceil_) memcpy(ceil_, p->ww_hi, sizeof(double) * p->I);
+    if (floor_) memcpy(floor_, p->ww_lo, sizeof(double) * p->I);
+    return 0;
+}
+
+int or_get_bank(const or_problem* p, double* x, double* mu, int32_t* cell, int64_t cap, int64_t* n) {
+    if (!p || !n) return E_ARG;
+    *n = p->nbank;
+    if (cap < p->nbank) return p->nbank ? E_ARG : 0;
+    for (int64_t k = 0; k < p->nbank; ++k) {
+        if (x) x[k] = p->bx[k];
+        if (mu) mu[k] = p->bmu[k];
+        if (cell) cell[k] = p->bcell[k];
+    }
+    return 0;
+}

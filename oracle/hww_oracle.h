@@ -1,0 +1,77 @@
+/*
+ * hww_oracle.h -- plain FP64 CPU oracle of the hybrid weight-window (HWW)
+ * time-dependent Monte Carlo step (Shaw & Anistratov, arXiv 2512.19925).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists to check the CUDA library.
+ * Only tests, the smoke check and the CPU-baseline leg of the benchmark may
+ * load it.  It shares no code, header, table or constant generator with the
+ * CUDA path; the only thing both sides agree on is the written numerics
+ * contract (Philox4x32-10 keyed as documented, the 52-bit uniform map, the
+ * atanh-series logarithm, the fixed-point tally format and the event rules),
+ * which each side implements on its own.
+ *
+ * Every function returns 0 on success and a negative code on error.
+ */
+#ifndef HWW_ORACLE_H
+#define HWW_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct or_problem or_problem;
+
+typedef struct {
+    int32_t n_cells;
+    const double* edges;          /* n_cells+1, strictly increasing */
+    double v, dt;
+    int32_t bc_left, bc_right;    /* 0 vacuum, 1 reflecting */
+    double src_x;                 /* unit isotropic plane pulse at t = 0 */
+    int64_t particles_per_step;
+    uint64_t seed;
+    double theta;                 /* 0.5 Crank-Nicolson, 1.0 backward Euler */
+    int32_t filter, filter_k;     /* 0 none, 1 moving average of base k */
+    int32_t n_var_batches;        /* B for the batch-mean variance tally */
+} or_desc;
+
+typedef struct {
+    int64_t n_start, segments, collisions, crossings, reflections;
+    int64_t leaked, absorbed, scatters, split_events, daughters;
+    int64_t roulette_kills, roulette_survivals, census, lineage_collisions;
+    int64_t max_events, n_next;
+    double w_bar_next;
+    int32_t error;
+} or_stats;
+
+/* problem life cycle (mirrors the C ABI verbs of the library) */
+int or_create(const or_desc* d, or_problem** out);
+int or_set_cross_sections(or_problem* p, const double* sigma_t, const double* c);
+int or_set_ww_params(or_problem* p, double rho, double eps_min, int32_t mode, int32_t center_scaling);
+int or_set_ww_centers(or_problem* p, const double* centers); /* override for the next step only */
+int or_run_step(or_problem* p, or_stats* st);
+int or_get_tallies(const or_problem* p, int32_t kind, double* out, int64_t n);
+int or_get_tallies_raw(const or_problem* p, int32_t kind, int64_t* out, int64_t n);
+int or_get_losm_solution(const or_problem* p, int32_t which, double* phi, double* J);
+int or_get_ww(const or_problem* p, double* center, double* ceil_, double* floor_);
+int or_get_bank(const or_problem* p, double* x, double* mu, int32_t* cell, int64_t cap, int64_t* n);
+void or_destroy(or_problem* p);
+
+/* building blocks, exported so that each can be pinned on its own */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_u01(uint32_t lo, uint32_t hi);
+double or_log(double u);
+int or_ma_filter(const double* in, double* out, int32_t m, int32_t k);
+int or_losm_solve(int32_t n_cells, const double* dx, const double* sigma_t, const double* sigma_a,
+                  double v, double dt, double theta, int32_t bc_left, int32_t bc_right,
+                  const double* phi_old, const double* J_old, const double* F_old,
+                  const double* F_new, double PL_new, double PR_new,
+                  const double* q_old, const double* q_new,
+                  double* phi_new, double* J_new);
+int or_comb(int64_t m, const uint32_t* id, const uint64_t* lin, const uint64_t* wfx,
+            int64_t n, double u, int32_t* src_of_slot);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
