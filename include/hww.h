@@ -1,0 +1,208 @@
+/*
+ * hww.h -- C ABI of the GB300 (sm_103a) library for one time step of the
+ * hybrid weight-window (HWW) time-dependent Monte Carlo method of
+ * Shaw & Anistratov, "Hybrid weight windows for time-dependent Monte Carlo
+ * transport" (arXiv 2512.19925).
+ *
+ * The method (paper Secs. 2-4): one-speed particles with isotropic
+ * scattering move through a 1D slab (Eq. HO_transport).  Each time step
+ *   1. solves the semi-implicit hybrid low-order second-moment (HLOSM)
+ *      equations (Eqs. losm-0, losm-1-semi, losm-disc-bc-semi) with the
+ *      closures of the previous step to obtain weight-window (WW) centers
+ *      (Eq. ww-center) with ceiling and floor (Eq. ww-c&f);
+ *   2. tracks the particle bank (collision, cell-crossing and census
+ *      events), splitting and rouletting against the windows (Sec. 2),
+ *      accumulating track-length tallies (Eq. phi-mc) and census
+ *      (time-crossing) tallies (Eq. ct-mc);
+ *   3. builds the closures F, P_L, P_R and the initial conditions of the
+ *      next step from the census tallies, optionally filtered by a moving
+ *      average (Sec. 4, Eq. moving_average), and solves the fully implicit
+ *      HLOSM equations (Eqs. losm-0, losm-1, losm-disc-bc);
+ *   4. combs the census bank back to N particles (uniform combing, Sec. 5.1).
+ *
+ * Conventions for every entry point:
+ *   - All functions return an hww_status; nothing throws across the ABI.
+ *   - Input arrays are caller-owned and copied before the call returns.
+ *   - Output arrays are caller-allocated.  When an `on_device` argument is 1
+ *     the pointer is a CUDA device pointer on the problem's device (for
+ *     instance a torch tensor's data_ptr()); when 0 it is host memory.
+ *   - Work is enqueued on the CUDA stream given at creation (0 = the legacy
+ *     default stream).  Calls that return data to host memory, and
+ *     run_step with a non-NULL stats pointer, synchronize that stream.
+ *   - A problem must be used from one host thread at a time.
+ *   - Device memory is allocated by create_problem (stream-ordered
+ *     allocation on the problem's stream) and released by destroy_problem.
+ *   - Array layouts: cells are 0-based (cell k spans [edges[k],
+ *     edges[k+1]]); the LOSM vectors use the paper's layout: phi has I+2
+ *     entries (x_0 boundary value, cells 1..I, x_I boundary value) and J has
+ *     I+1 entries (edges x_0..x_I).
+ */
+#ifndef HWW_H
+#define HWW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hww_problem hww_problem; /* opaque, library-owned */
+typedef struct hww_batch hww_batch;     /* opaque, library-owned */
+
+typedef enum {
+    HWW_OK = 0,
+    HWW_ERR_ARG = 1,           /* an argument is out of range or NULL */
+    HWW_ERR_STATE = 2,         /* a verb was called out of order */
+    HWW_ERR_OOM = 3,           /* device or host allocation failed */
+    HWW_ERR_BANK_OVERFLOW = 4, /* a particle bank or queue filled up; the step is invalid */
+    HWW_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    HWW_ERR_NUMERIC = 6,       /* a numeric guard fired (split count, event count, LOSM pivot) */
+    HWW_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+    HWW_ERR_NO_DEVICE = 8      /* no usable CUDA device */
+} hww_status;
+
+enum { HWW_BC_VACUUM = 0, HWW_BC_REFLECT = 1 };
+enum { HWW_FP64 = 0, HWW_FP32_TRACK = 1 };
+enum { HWW_FILTER_NONE = 0, HWW_FILTER_MA = 1 };
+/* window modes: HLOSM centers (the paper's method), analog (no windows),
+ * lagged (centers from the previous step's track-length flux) */
+enum { HWW_MODE_HWW = 0, HWW_MODE_ANALOG = 1, HWW_MODE_LWW = 2 };
+/* center scaling: multiply Eq. (ww-center) by the mean particle weight after
+ * the previous comb, or use it literally */
+enum { HWW_SCALE_MEAN_WEIGHT = 0, HWW_SCALE_LITERAL = 1 };
+/* get_tallies kinds; all are normalised per source particle */
+enum {
+    HWW_TL_PHI = 0,      /* <phi>_i^n, Eq. (phi-mc)                       [I]   */
+    HWW_TL_J = 1,        /* track-length current, same normalisation      [I]   */
+    HWW_TL_F = 2,        /* track-length (1/3 - mu^2) moment              [I]   */
+    HWW_CENSUS_PHI = 3,  /* [[phi]]_i^n, Eq. (ct-mc)                       [I]   */
+    HWW_CENSUS_J = 4,    /* census current                                [I]   */
+    HWW_CENSUS_F = 5,    /* census closure F_i^n, Eq. (F)                  [I]   */
+    HWW_BATCH_PHI = 6,   /* <phi> per variance batch b = id mod B          [B*I] */
+    HWW_BOUNDARY = 7,    /* phi_L, F_L, P_L, phi_R, F_R, P_R time averages [6]   */
+    HWW_WW_CENTER = 8,   /* window centers used in the step               [I]   */
+    HWW_CLOSURE_PHI = 9, /* IC / closure vectors built at t^n            [I+2] */
+    HWW_CLOSURE_J = 10,  /*                                               [I+1] */
+    HWW_CLOSURE_F = 11   /*                                               [I+2] */
+};
+enum { HWW_LOSM_SEMI = 0, HWW_LOSM_FULL = 1 };
+
+typedef struct {
+    int32_t n_cells;          /* I >= 1 */
+    const double* edges;      /* I+1 strictly increasing positions (host) */
+    double v;                 /* particle speed > 0 */
+    double dt;                /* time step > 0 */
+    int32_t bc_left, bc_right;/* HWW_BC_VACUUM | HWW_BC_REFLECT */
+    double src_x;             /* unit isotropic plane pulse at t = 0, in [edges[0], edges[I]] */
+    int64_t particles_per_step; /* N, 1 <= N < 2^31 */
+    uint64_t seed;            /* Philox key (with the step index) */
+    int32_t precision;        /* HWW_FP64 | HWW_FP32_TRACK */
+    double theta;             /* 0.5 Crank-Nicolson | 1.0 backward Euler */
+    int32_t filter, filter_k; /* HWW_FILTER_NONE | HWW_FILTER_MA with base k >= 1 */
+    int32_t n_var_batches;    /* B >= 1 batches for the batch-mean variance tally */
+    int32_t deriv_regions;    /* 0, or R >= 1 regions for derivative tallies (FP64 only) */
+    int64_t bank_capacity;    /* census slots; each record queue gets half; 0 = 4 N census, 2 N per queue */
+    void* cuda_stream;        /* cudaStream_t; NULL = legacy default stream */
+    int32_t device;           /* CUDA device ordinal */
+} hww_problem_desc;
+
+typedef struct {
+    int64_t n_start, segments, collisions, crossings, reflections;
+    int64_t leaked, absorbed, scatters, split_events, daughters;
+    int64_t roulette_kills, roulette_survivals, census, lineage_collisions;
+    int64_t max_events, n_next;
+    double w_bar_next;  /* weight of each combed particle for the next step */
+    int32_t waves;      /* tracking launches the step needed */
+    int32_t status;     /* hww_status of the step */
+} hww_step_stats;
+
+/* Create a problem from the description (paper Sec. 3 problem statement:
+ * slab [x_0, x_I], cells of Eq. losm-disc, pulse initial condition).
+ * Errors: HWW_ERR_ARG for an invalid field, HWW_ERR_NO_DEVICE, HWW_ERR_OOM,
+ * HWW_ERR_CUDA.  On error *out is NULL. */
+hww_status create_problem(const hww_problem_desc* desc, hww_problem** out);
+
+/* Per-cell total cross section Sigma_t > 0 and scattering ratio 0 <= c <= 1
+ * (Sigma_s = c Sigma_t, no fission), Eq. (HO_transport).  `region` (nullable)
+ * maps each cell to a region 0..R-1 for the derivative tallies.  Host arrays
+ * of length I.  May be called again between steps. */
+hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const double* c,
+                              const int32_t* region);
+
+/* Window width rho >= 1 (ceiling rho*ww, floor ww/rho, Eq. ww-c&f), minimum
+ * center 0 < eps_min <= 1 (Eq. ww-center), mode HWW_MODE_*, center scaling
+ * HWW_SCALE_*. */
+hww_status set_ww_params(hww_problem* p, double rho, double eps_min, int32_t mode,
+                         int32_t center_scaling);
+
+/* Replace the window centers of the next step only (I host values > 0);
+ * ceiling and floor follow from rho.  Used to run both implementations
+ * from identical windows. */
+hww_status set_ww_centers(hww_problem* p, const double* centers);
+
+/* Advance the problem by one time step (steps 1-4 above).  Asynchronous on
+ * the problem's stream unless `stats` is non-NULL, in which case the stream
+ * is synchronized and the counts of the step are returned.  A bank overflow
+ * or numeric guard makes this or the next synchronizing call return the
+ * error; the step's results are then invalid. */
+hww_status run_step(hww_problem* p, hww_step_stats* stats);
+
+/* Copy tally `kind` (HWW_* kinds above) of the last completed step into
+ * `out` (capacity n doubles; host or device per on_device).  Values are
+ * normalised per source particle: track-length kinds by N dx_i dt, census
+ * kinds by N dx_i / v, boundary kinds by N dt. */
+hww_status get_tallies(const hww_problem* p, int32_t kind, double* out, int64_t n,
+                       int32_t on_device);
+
+/* Raw 128-bit fixed-point accumulators of a tally kind 0..7 as (lo, hi)
+ * int64 pairs (2 n values), for bit-exact comparisons.  Host memory. */
+hww_status get_tallies_raw(const hww_problem* p, int32_t kind, int64_t* out, int64_t n);
+
+/* Copy the HLOSM solution of the last step: HWW_LOSM_SEMI (the one that set
+ * the windows, Eq. losm-disc-semi) or HWW_LOSM_FULL (end of step, Eq.
+ * losm-disc).  phi has I+2 entries and J has I+1. */
+hww_status get_losm_solution(const hww_problem* p, int32_t which, double* phi, double* J,
+                             int32_t on_device);
+
+/* Copy the combed bank that will start the next step (positions, directions,
+ * cells; each particle carries weight stats.w_bar_next).  Host arrays of
+ * capacity cap; *n receives the bank size (call with cap = 0 to query). */
+hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, int64_t cap,
+                    int64_t* n);
+
+/* Copy the census bank of the last step (the particles that reached t^n,
+ * before combing): positions, directions, weights, cells, source ids and
+ * lineage keys, in the device's storage order.  Host arrays of capacity
+ * cap (any pointer may be NULL); *n receives the census size (cap = 0
+ * queries it).  Used to check individual histories. */
+hww_status get_census(const hww_problem* p, double* x, double* mu, double* w, int32_t* cell,
+                      uint32_t* id, uint64_t* lin, int64_t cap, int64_t* n);
+
+/* Release the problem and its device memory (NULL is allowed). */
+void destroy_problem(hww_problem* p);
+
+/* Static text for a status code. */
+const char* hww_status_string(hww_status s);
+
+/* Solve one LOSM system (Eqs. losm-0, losm-1, losm-disc-bc) on the device
+ * for given inputs, with the library's solver.  Host arrays in the paper's
+ * layout (dx, sigma_t, sigma_a, q_old, q_new: I cells, q cell-integrated and
+ * nullable; phi_old, F_old, F_new, phi_new: I+2; J_old, J_new: I+1).
+ * Synchronous.  Used to check the device solver on its own. */
+hww_status hww_losm_solve(int32_t n_cells, const double* dx, const double* sigma_t,
+                          const double* sigma_a, double v, double dt, double theta,
+                          int32_t bc_left, int32_t bc_right, const double* phi_old,
+                          const double* J_old, const double* F_old, const double* F_new,
+                          double PL_new, double PR_new, const double* q_old, const double* q_new,
+                          double* phi_new, double* J_new);
+
+/* Philox4x32-10 of n consecutive counters {c0 + i, c1, c2, c3} under key
+ * (k0, k1), computed by the library's device generator; out holds 4 n
+ * words (host).  Synchronous.  Used to check the generator. */
+hww_status hww_philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                            uint32_t k1, int64_t n, uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HWW_H */

@@ -93,6 +93,9 @@ def lib():
             L.or_get_ww.argtypes = [C.c_void_p, dp, dp, dp]
             L.or_get_bank.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int32), C.c_int64,
                                       C.POINTER(C.c_int64)]
+            L.or_set_bank.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.c_double]
+            L.or_get_census.argtypes = [C.c_void_p, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
+                                        C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_int64)]
             L.or_destroy.argtypes = [C.c_void_p]
             L.or_destroy.restype = None
             L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
@@ -271,6 +274,27 @@ class Problem:
         _check(lib().or_get_bank(self._h, _dp(x), _dp(mu), cell.ctypes.data_as(C.POINTER(C.c_int32)),
                                  m, C.byref(n)), "get_bank")
         return x, mu, cell
+
+    def set_bank(self, x, mu, cell, w_bar):
+        x, mu = _f64(x), _f64(mu)
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        _check(lib().or_set_bank(self._h, _dp(x), _dp(mu), cell.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 x.size, float(w_bar)), "set_bank")
+
+    def get_census(self):
+        n = C.c_int64()
+        L = lib()
+        _check(L.or_get_census(self._h, None, None, None, None, None, None, 0, C.byref(n)), "get_census")
+        m = n.value
+        out = dict(x=np.empty(m), mu=np.empty(m), w=np.empty(m), cell=np.empty(m, np.int32),
+                   id=np.empty(m, np.uint32), lin=np.empty(m, np.uint64))
+        if m:
+            _check(L.or_get_census(self._h, _dp(out["x"]), _dp(out["mu"]), _dp(out["w"]),
+                                   out["cell"].ctypes.data_as(C.POINTER(C.c_int32)),
+                                   out["id"].ctypes.data_as(C.POINTER(C.c_uint32)),
+                                   out["lin"].ctypes.data_as(C.POINTER(C.c_uint64)), m, C.byref(n)),
+                   "get_census")
+        return out
 
 
 def problem_from_workload(wl, particles_per_step=None, seed=None):

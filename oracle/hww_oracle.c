@@ -194,6 +194,9 @@ struct or_problem {
     /* previous-step track-length flux (for lagged windows) */
     double* prev_tl_phi;
     int has_prev_tl;
+    /* census bank of the last step */
+    or_census* census;
+    int64_t ncensus;
 };
 
 static void* xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
@@ -267,6 +270,7 @@ void or_destroy(or_problem* p) {
     free(p->clo_phi); free(p->clo_J); free(p->clo_F);
     free(p->semi_phi); free(p->semi_J); free(p->full_phi); free(p->full_J);
     free(p->prev_tl_phi);
+    free(p->census);
     free(p);
 }
 
@@ -958,7 +962,9 @@ int or_run_step(or_problem* p, or_stats* st) {
         s.w_bar_next = p->wbar;
         free(ids); free(lins); free(wfx); free(src);
     }
-    free(census.v);
+    free(p->census);
+    p->census = census.v;
+    p->ncensus = census.n;
     free(phi_old); free(J_old); free(F_old);
     p->n = n;
     if (st) *st = s;
@@ -1068,6 +1074,41 @@ int or_get_ww(const or_problem* p, double* center, double* ceil_, double* floor_
     if (center) memcpy(center, p->ww_c, sizeof(double) * p->I);
     if (ceil_) memcpy(ceil_, p->ww_hi, sizeof(double) * p->I);
     if (floor_) memcpy(floor_, p->ww_lo, sizeof(double) * p->I);
+    return 0;
+}
+
+int or_set_bank(or_problem* p, const double* x, const double* mu, const int32_t* cell, int64_t n, double wbar) {
+    if (!p || n < 0 || n > p->N || (n > 0 && (!x || !mu || !cell)) || !(wbar > 0.0) || p->n < 1) return E_ARG;
+    for (int64_t k = 0; k < n; ++k)
+        if (cell[k] < 0 || cell[k] >= p->I || !(mu[k] != 0.0) || !(mu[k] >= -1.0 && mu[k] <= 1.0)) return E_ARG;
+    free(p->bx); free(p->bmu); free(p->bcell);
+    p->bx = xcalloc(n, sizeof(double));
+    p->bmu = xcalloc(n, sizeof(double));
+    p->bcell = xcalloc(n, sizeof(int32_t));
+    if (!p->bx || !p->bmu || !p->bcell) return E_OOM;
+    memcpy(p->bx, x, sizeof(double) * n);
+    memcpy(p->bmu, mu, sizeof(double) * n);
+    memcpy(p->bcell, cell, sizeof(int32_t) * n);
+    p->nbank = n;
+    p->wbar = wbar;
+    return 0;
+}
+
+int or_get_census(const or_problem* p, double* x, double* mu, double* w, int32_t* cell, uint32_t* id,
+                  uint64_t* lin, int64_t cap, int64_t* n) {
+    if (!p || !n) return E_ARG;
+    *n = p->ncensus;
+    if (cap == 0) return 0;
+    if (cap < p->ncensus) return E_ARG;
+    for (int64_t j = 0; j < p->ncensus; ++j) {
+        const or_census* c = &p->census[j];
+        if (x) x[j] = c->x;
+        if (mu) mu[j] = c->mu;
+        if (w) w[j] = c->w;
+        if (cell) cell[j] = c->cell;
+        if (id) id[j] = c->id;
+        if (lin) lin[j] = c->lin;
+    }
     return 0;
 }
 

@@ -1,0 +1,309 @@
+"""Python binding of the HWW library (include/hww.h).
+
+Argument marshalling only: every stage of a time step runs in the library's
+CUDA kernels.  PyTorch supplies the CUDA stream (and device tensors for
+outputs when asked); it computes nothing here.  There is no CPU fallback:
+if the compiled library is missing or cannot be loaded, every call raises.
+
+Functions keep the C names (``create_problem``, ``set_cross_sections``,
+``set_ww_params``, ``run_step``, ``get_tallies``, ``get_losm_solution``, ...);
+``Problem`` wraps them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+HWW_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of memory",
+          4: "particle bank or queue overflow", 5: "bounded wait gave up", 6: "numeric guard fired",
+          7: "CUDA runtime error", 8: "no CUDA device"}
+BC_VACUUM, BC_REFLECT = 0, 1
+FP64, FP32_TRACK = 0, 1
+FILTER_NONE, FILTER_MA = 0, 1
+MODE_HWW, MODE_ANALOG, MODE_LWW = 0, 1, 2
+SCALE_MEAN_WEIGHT, SCALE_LITERAL = 0, 1
+TL_PHI, TL_J, TL_F, CENSUS_PHI, CENSUS_J, CENSUS_F, BATCH_PHI, BOUNDARY = range(8)
+WW_CENTER, CLOSURE_PHI, CLOSURE_J, CLOSURE_F = 8, 9, 10, 11
+LOSM_SEMI, LOSM_FULL = 0, 1
+
+STAT_FIELDS = [
+    "n_start", "segments", "collisions", "crossings", "reflections", "leaked", "absorbed",
+    "scatters", "split_events", "daughters", "roulette_kills", "roulette_survivals", "census",
+    "lineage_collisions", "max_events", "n_next",
+]
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [
+        ("n_cells", C.c_int32), ("edges", C.POINTER(C.c_double)), ("v", C.c_double),
+        ("dt", C.c_double), ("bc_left", C.c_int32), ("bc_right", C.c_int32), ("src_x", C.c_double),
+        ("particles_per_step", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int32),
+        ("theta", C.c_double), ("filter", C.c_int32), ("filter_k", C.c_int32),
+        ("n_var_batches", C.c_int32), ("deriv_regions", C.c_int32), ("bank_capacity", C.c_int64),
+        ("cuda_stream", C.c_void_p), ("device", C.c_int32),
+    ]
+
+
+class StepStats(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in STAT_FIELDS] + [
+        ("w_bar_next", C.c_double), ("waves", C.c_int32), ("status", C.c_int32)]
+
+
+class HWWError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (status %d)" % (what, STATUS.get(code, "unknown"), code))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+SYMBOLS = ["create_problem", "set_cross_sections", "set_ww_params", "set_ww_centers", "run_step",
+           "get_tallies", "get_tallies_raw", "get_losm_solution", "get_bank", "get_census", "destroy_problem",
+           "hww_status_string", "hww_losm_solve", "hww_philox_block"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the compiled library (building it when the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("HWW CUDA library not built: %s is missing" % _build.LIB)
+        L = C.CDLL(_build.LIB)
+        dp = C.POINTER(C.c_double)
+        vp = C.c_void_p
+        L.create_problem.argtypes = [C.POINTER(ProblemDesc), C.POINTER(vp)]
+        L.set_cross_sections.argtypes = [vp, dp, dp, C.POINTER(C.c_int32)]
+        L.set_ww_params.argtypes = [vp, C.c_double, C.c_double, C.c_int32, C.c_int32]
+        L.set_ww_centers.argtypes = [vp, dp]
+        L.run_step.argtypes = [vp, C.POINTER(StepStats)]
+        L.get_tallies.argtypes = [vp, C.c_int32, vp, C.c_int64, C.c_int32]
+        L.get_tallies_raw.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), C.c_int64]
+        L.get_losm_solution.argtypes = [vp, C.c_int32, vp, vp, C.c_int32]
+        L.get_bank.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.POINTER(C.c_int64)]
+        L.get_census.argtypes = [vp, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
+                                 C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_int64)]
+        L.destroy_problem.argtypes = [vp]
+        L.destroy_problem.restype = None
+        L.hww_status_string.argtypes = [C.c_int32]
+        L.hww_status_string.restype = C.c_char_p
+        L.hww_losm_solve.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                     C.c_int32, C.c_int32, dp, dp, dp, dp, C.c_double, C.c_double,
+                                     dp, dp, dp, dp]
+        L.hww_philox_block.argtypes = [C.c_uint32] * 6 + [C.c_int64, C.POINTER(C.c_uint32)]
+        for name in SYMBOLS:
+            f = getattr(L, name)
+            if name not in ("destroy_problem", "hww_status_string"):
+                f.restype = C.c_int32
+        _lib = L
+        return L
+
+
+def _check(rc, what):
+    if rc != HWW_OK:
+        raise HWWError(rc, what)
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def hww_losm_solve(dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, phi_old, J_old, F_old,
+                   F_new, PL_new=0.0, PR_new=0.0, q_old=None, q_new=None):
+    """One LOSM solve on the device with the library's solver."""
+    dx = _f64(dx)
+    I = dx.size
+    st, sa = _f64(sigma_t, I), _f64(sigma_a, I)
+    po, Jo, Fo, Fn = _f64(phi_old, I + 2), _f64(J_old, I + 1), _f64(F_old, I + 2), _f64(F_new, I + 2)
+    qo = _f64(q_old, I) if q_old is not None else None
+    qn = _f64(q_new, I) if q_new is not None else None
+    phi, J = np.empty(I + 2), np.empty(I + 1)
+    null = C.POINTER(C.c_double)()
+    rc = load().hww_losm_solve(I, _dp(dx), _dp(st), _dp(sa), float(v), float(dt), float(theta),
+                               int(bc_left), int(bc_right), _dp(po), _dp(Jo), _dp(Fo), _dp(Fn),
+                               float(PL_new), float(PR_new), _dp(qo) if qo is not None else null,
+                               _dp(qn) if qn is not None else null, _dp(phi), _dp(J))
+    _check(rc, "hww_losm_solve")
+    return phi, J
+
+
+def hww_philox_block(ctr, key, n):
+    """Philox4x32-10 of counters (ctr[0]+i, ctr[1], ctr[2], ctr[3]), i < n."""
+    out = np.empty(4 * int(n), dtype=np.uint32)
+    rc = load().hww_philox_block(*[int(c) & 0xFFFFFFFF for c in ctr], *[int(k) & 0xFFFFFFFF for k in key],
+                                 int(n), out.ctypes.data_as(C.POINTER(C.c_uint32)))
+    _check(rc, "hww_philox_block")
+    return out.reshape(-1, 4)
+
+
+class Problem:
+    """A slab problem stepped on the GPU through the C ABI."""
+
+    def __init__(self, edges, v, dt, bc_left, bc_right, src_x, particles_per_step, seed,
+                 precision=FP64, theta=0.5, filter=FILTER_NONE, filter_k=3, n_var_batches=16,
+                 deriv_regions=0, bank_capacity=0, stream=None, device=0):
+        L = load()
+        self.edges = _f64(edges)
+        self.I = self.edges.size - 1
+        self.B = int(n_var_batches)
+        self.N = int(particles_per_step)
+        self.device = int(device)
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream(self.device).cuda_stream
+            except Exception:
+                stream = 0
+        self.stream = int(stream)
+        d = ProblemDesc(self.I, _dp(self.edges), float(v), float(dt), int(bc_left), int(bc_right),
+                        float(src_x), self.N, int(seed), int(precision), float(theta), int(filter),
+                        int(filter_k), self.B, int(deriv_regions), int(bank_capacity),
+                        C.c_void_p(self.stream), self.device)
+        h = C.c_void_p()
+        _check(L.create_problem(C.byref(d), C.byref(h)), "create_problem")
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, wl, particles_per_step=None, seed=None, precision=None, stream=None,
+                      bank_capacity=0):
+        prec = precision if precision is not None else (FP32_TRACK if wl.get("precision") == "fp32" else FP64)
+        p = cls(wl["edges"], wl["v"], wl["dt"], wl["bc_left"], wl["bc_right"], wl["src_x"],
+                particles_per_step or wl["particles_per_step"], wl["seed"] if seed is None else seed,
+                precision=prec, theta=wl.get("theta", 0.5), filter=wl.get("filter", 0),
+                filter_k=wl.get("filter_k", 3), n_var_batches=wl.get("n_var_batches", 16),
+                bank_capacity=bank_capacity, stream=stream)
+        p.set_cross_sections(wl["sigma_t"], wl["c"])
+        p.set_ww_params(wl["rho"], wl["eps_min"], wl.get("mode", MODE_HWW),
+                        wl.get("center_scaling", SCALE_MEAN_WEIGHT))
+        return p
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().destroy_problem(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_cross_sections(self, sigma_t, c, region=None):
+        st, cc = _f64(sigma_t, self.I), _f64(c, self.I)
+        reg = None
+        if region is not None:
+            reg = np.ascontiguousarray(region, dtype=np.int32)
+        rp = reg.ctypes.data_as(C.POINTER(C.c_int32)) if reg is not None else C.POINTER(C.c_int32)()
+        _check(load().set_cross_sections(self._h, _dp(st), _dp(cc), rp), "set_cross_sections")
+
+    def set_ww_params(self, rho, eps_min, mode=MODE_HWW, center_scaling=SCALE_MEAN_WEIGHT):
+        _check(load().set_ww_params(self._h, float(rho), float(eps_min), int(mode), int(center_scaling)),
+               "set_ww_params")
+
+    def set_ww_centers(self, centers):
+        c = _f64(centers, self.I)
+        _check(load().set_ww_centers(self._h, _dp(c)), "set_ww_centers")
+
+    def run_step(self, stats=True):
+        if not stats:
+            _check(load().run_step(self._h, None), "run_step")
+            return None
+        st = StepStats()
+        rc = load().run_step(self._h, C.byref(st))
+        _check(rc, "run_step")
+        out = {f: int(getattr(st, f)) for f in STAT_FIELDS}
+        out["w_bar_next"] = st.w_bar_next
+        out["waves"] = st.waves
+        return out
+
+    def _len(self, kind):
+        return {BATCH_PHI: self.B * self.I, BOUNDARY: 6, CLOSURE_PHI: self.I + 2,
+                CLOSURE_J: self.I + 1, CLOSURE_F: self.I + 2}.get(kind, self.I)
+
+    def get_tallies(self, kind, out=None):
+        """Tally `kind` as a numpy array, or into `out` (a CUDA torch tensor of
+        float64) without leaving the device."""
+        n = self._len(kind)
+        if out is not None:
+            _check(load().get_tallies(self._h, int(kind), C.c_void_p(out.data_ptr()), n, 1), "get_tallies")
+            return out
+        a = np.empty(n)
+        _check(load().get_tallies(self._h, int(kind), a.ctypes.data_as(C.c_void_p), n, 0), "get_tallies")
+        if kind == BATCH_PHI:
+            a = a.reshape(self.B, self.I)
+        return a
+
+    def get_tallies_raw(self, kind):
+        n = {BATCH_PHI: self.B * self.I, BOUNDARY: 6}.get(kind, self.I)
+        a = np.empty(2 * n, dtype=np.int64)
+        _check(load().get_tallies_raw(self._h, int(kind), a.ctypes.data_as(C.POINTER(C.c_int64)), 2 * n),
+               "get_tallies_raw")
+        return a.reshape(n, 2)
+
+    def get_losm_solution(self, which=LOSM_FULL):
+        phi, J = np.empty(self.I + 2), np.empty(self.I + 1)
+        _check(load().get_losm_solution(self._h, int(which), phi.ctypes.data_as(C.c_void_p),
+                                        J.ctypes.data_as(C.c_void_p), 0), "get_losm_solution")
+        return phi, J
+
+    def get_bank(self):
+        n = C.c_int64()
+        _check(load().get_bank(self._h, None, None, None, 0, C.byref(n)), "get_bank")
+        m = n.value
+        x, mu, cell = np.empty(m), np.empty(m), np.empty(m, dtype=np.int32)
+        if m:
+            _check(load().get_bank(self._h, _dp(x), _dp(mu), cell.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   m, C.byref(n)), "get_bank")
+        return x, mu, cell
+
+    def get_census(self):
+        """Census bank of the last step as a dict of arrays (storage order)."""
+        n = C.c_int64()
+        L = load()
+        _check(L.get_census(self._h, None, None, None, None, None, None, 0, C.byref(n)), "get_census")
+        m = n.value
+        out = dict(x=np.empty(m), mu=np.empty(m), w=np.empty(m), cell=np.empty(m, np.int32),
+                   id=np.empty(m, np.uint32), lin=np.empty(m, np.uint64))
+        if m:
+            _check(L.get_census(self._h, _dp(out["x"]), _dp(out["mu"]), _dp(out["w"]),
+                                out["cell"].ctypes.data_as(C.POINTER(C.c_int32)),
+                                out["id"].ctypes.data_as(C.POINTER(C.c_uint32)),
+                                out["lin"].ctypes.data_as(C.POINTER(C.c_uint64)), m, C.byref(n)),
+                   "get_census")
+        return out
+
+
+def create_problem(desc: ProblemDesc):
+    h = C.c_void_p()
+    _check(load().create_problem(C.byref(desc), C.byref(h)), "create_problem")
+    return h
+
+
+def destroy_problem(h):
+    load().destroy_problem(h)
+
+
+def status_string(code: int) -> str:
+    return load().hww_status_string(int(code)).decode()

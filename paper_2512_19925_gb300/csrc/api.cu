@@ -1,0 +1,942 @@
+// api.cu -- the C ABI (include/hww.h) and the host-side step orchestration.
+//
+// A time step is a fixed sequence of stream-ordered launches:
+//   clear accumulators -> prestep (semi-implicit HLOSM, windows) ->
+//   tracking wave 0 over the start bank -> tracking waves over the record
+//   queue until it is empty -> poststep (closures, fully implicit HLOSM) ->
+//   comb (group scan, member scatter, tooth writes, next-step scalars).
+// Only the queue-empty test between waves reads a device counter back.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/hww.h"
+#include "hww_internal.cuh"
+#include "step_kernels.cuh"
+
+using namespace hww;
+
+namespace {
+
+constexpr int TRACK_BLOCK = 256;
+constexpr int MAX_CELLS = 4000;
+constexpr int MAX_WAVES = 100000;
+
+template <class Real>
+struct Banks {
+    Real *bx = nullptr, *bmu = nullptr;
+    int32_t* bcell = nullptr;
+    RecQ<Real> q[2] = {};
+    CenQ<Real> cen = {};
+};
+
+}  // namespace
+
+struct hww_problem {
+    hww_problem_desc d{};
+    int I = 0, B = 0;
+    long long N = 0;
+    int fp32 = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int nsm = 0;
+    long long cen_cap = 0, q_cap = 0;
+    std::vector<double> edges, dx;
+    std::vector<void*> allocs;
+    // mesh and cross sections
+    double *d_edges = nullptr, *d_dx = nullptr, *d_sigt = nullptr, *d_inv_sigt = nullptr, *d_c = nullptr,
+           *d_siga = nullptr;
+    float *d_dxf = nullptr, *d_inv_sigt_f = nullptr;
+    int32_t* d_region = nullptr;
+    double *ww_c = nullptr, *ww_hi = nullptr, *ww_lo = nullptr, *ww_override = nullptr;
+    Banks<double> b64;
+    Banks<float> b32;
+    // per-step accumulators (one clear)
+    void* acc = nullptr;
+    size_t acc_bytes = 0;
+    Acc128 *tl = nullptr, *cent = nullptr, *batch = nullptr, *bnd = nullptr;
+    unsigned long long* stats = nullptr;
+    unsigned long long* counts = nullptr;  // [0] census, [1] q0, [2] q1
+    // comb groups (one clear)
+    void* grp = nullptr;
+    size_t grp_bytes = 0;
+    unsigned long long* gw = nullptr;
+    uint32_t *gcnt = nullptr, *gcur = nullptr;
+    unsigned long long *goff = nullptr, *goff_w = nullptr, *tile_c = nullptr, *tile_w = nullptr;
+    uint32_t* member = nullptr;
+    // closures and LOSM
+    double *ophi = nullptr, *oJ = nullptr, *oF = nullptr, *oP = nullptr;
+    double *nphi = nullptr, *nJ = nullptr, *nF = nullptr, *nP = nullptr, *cJ = nullptr, *tmp = nullptr;
+    double *prev_tl = nullptr, *semi_phi = nullptr, *semi_J = nullptr, *full_phi = nullptr,
+           *full_J = nullptr, *work = nullptr, *norm = nullptr;
+    StepDev* sd = nullptr;
+    unsigned* err = nullptr;
+    unsigned long long* h_count = nullptr;  // pinned
+    // host state
+    int xs_set = 0, ww_set = 0, has_override = 0, has_prev_tl = 0;
+    double rho = 1.0, eps = 1e-3;
+    int mode = 0, scaling = 0;
+    long long steps = 0;
+    int birth_pos = 0, birth_neg = 0;
+    int track_grid = 0;
+    size_t track_smem = 0;
+    int last_waves = 0;
+};
+
+namespace {
+
+hww_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return HWW_OK;
+    if (e == cudaErrorMemoryAllocation) return HWW_ERR_OOM;
+    return HWW_ERR_CUDA;
+}
+
+#define HWW_CK(call)                                   \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+template <class T>
+hww_status dalloc(hww_problem* p, T** ptr, size_t count) {
+    void* v = nullptr;
+    const size_t bytes = (count ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMallocAsync(&v, bytes, p->stream);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return cuda_status(e);
+    }
+    p->allocs.push_back(v);
+    *ptr = (T*)v;
+    return HWW_OK;
+}
+
+int bit_length(long long n) {
+    int l = 0;
+    while (n > 0) {
+        ++l;
+        n >>= 1;
+    }
+    return l;
+}
+
+// birth cell of the pulse: x_k <= x < x_{k+1}, the left cell on an interior
+// edge for mu < 0, the end cell on a domain end
+int birth_cell(const std::vector<double>& e, int I, double x, double mu) {
+    if (x <= e[0]) return 0;
+    if (x >= e[I]) return I - 1;
+    for (int i = 0; i < I; ++i) {
+        if (x == e[i] && i > 0) return mu < 0.0 ? i - 1 : i;
+        if (x > e[i] && x < e[i + 1]) return i;
+    }
+    return I - 1;
+}
+
+// exact moments of the unit isotropic pulse at t = 0 (step-1 initial condition)
+void source_moments(const hww_problem* p, std::vector<double>& phi) {
+    const int I = p->I;
+    phi.assign(I + 2, 0.0);
+    const double xs = p->d.src_x, v = p->d.v;
+    int edge = -1;
+    for (int i = 0; i <= I; ++i)
+        if (p->edges[i] == xs) edge = i;
+    if (edge == 0) {
+        phi[1] = v / p->dx[0];
+    } else if (edge == I) {
+        phi[I] = v / p->dx[I - 1];
+    } else if (edge > 0) {
+        phi[edge] = 0.5 * v / p->dx[edge - 1];
+        phi[edge + 1] = 0.5 * v / p->dx[edge];
+    } else {
+        for (int i = 0; i < I; ++i)
+            if (xs > p->edges[i] && xs < p->edges[i + 1]) phi[i + 1] = v / p->dx[i];
+    }
+    phi[0] = phi[1];
+    phi[I + 1] = phi[I];
+}
+
+template <class Real>
+hww_status alloc_banks(hww_problem* p, Banks<Real>& b) {
+    hww_status s;
+    const long long N = p->N, C = p->cen_cap, Q = p->q_cap;
+    if ((s = dalloc(p, &b.bx, N)) || (s = dalloc(p, &b.bmu, N)) || (s = dalloc(p, &b.bcell, N))) return s;
+    if ((s = dalloc(p, &b.cen.x, C)) || (s = dalloc(p, &b.cen.mu, C)) || (s = dalloc(p, &b.cen.w, C)) ||
+        (s = dalloc(p, &b.cen.cell, C)) || (s = dalloc(p, &b.cen.id, C)) || (s = dalloc(p, &b.cen.lin, C)))
+        return s;
+    b.cen.cap = C;
+    b.cen.count = p->counts + 0;
+    for (int k = 0; k < 2; ++k) {
+        RecQ<Real>& q = b.q[k];
+        if ((s = dalloc(p, &q.x, Q)) || (s = dalloc(p, &q.mu, Q)) || (s = dalloc(p, &q.tau, Q)) ||
+            (s = dalloc(p, &q.w, Q)) || (s = dalloc(p, &q.cell, Q)) || (s = dalloc(p, &q.id, Q)) ||
+            (s = dalloc(p, &q.lin, Q)) || (s = dalloc(p, &q.e, Q)) || (s = dalloc(p, &q.jstart, Q)) ||
+            (s = dalloc(p, &q.jcount, Q)))
+            return s;
+        q.cap = Q;
+        q.count = p->counts + 1 + k;
+    }
+    return HWW_OK;
+}
+
+template <class Real>
+TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b, uint32_t k0, uint32_t k1) {
+    TrackArgs<Real> a{};
+    a.I = p->I;
+    a.B = p->B;
+    a.emax = 64;
+    a.ww_on = (p->mode == HWW_MODE_HWW) || (p->mode == HWW_MODE_LWW && p->has_prev_tl) || p->has_override;
+    a.bc_l = p->d.bc_left;
+    a.bc_r = p->d.bc_right;
+    a.birth_cell_pos = p->birth_pos;
+    a.birth_cell_neg = p->birth_neg;
+    a.k0 = k0;
+    a.k1 = k1;
+    a.tau0 = p->d.v * p->d.dt;
+    a.src_x = p->d.src_x;
+    a.edges = p->d_edges;
+    a.inv_sigt = p->d_inv_sigt;
+    a.c = p->d_c;
+    a.dxf = p->d_dxf;
+    a.inv_sigt_f = p->d_inv_sigt_f;
+    a.ww_c = p->ww_c;
+    a.ww_hi = p->ww_hi;
+    a.ww_lo = p->ww_lo;
+    a.sd = p->sd;
+    a.bx = b.bx;
+    a.bmu = b.bmu;
+    a.bcell = b.bcell;
+    a.cen = b.cen;
+    a.gcnt = p->gcnt;
+    a.gw = p->gw;
+    a.tl = p->tl;
+    a.cent = p->cent;
+    a.batch = p->batch;
+    a.bnd = p->bnd;
+    a.stats = p->stats;
+    a.err = p->err;
+    return a;
+}
+
+void launch_track(hww_problem* p, const TrackArgs<double>& a) {
+    launch_track_fp64(a, p->track_grid, TRACK_BLOCK, p->track_smem, p->stream);
+}
+void launch_track(hww_problem* p, const TrackArgs<float>& a) {
+    launch_track_fp32(a, p->track_grid, TRACK_BLOCK, p->track_smem, p->stream);
+}
+
+template <class Real>
+hww_status track_waves(hww_problem* p, Banks<Real>& b, uint32_t k0, uint32_t k1, int birth) {
+    TrackArgs<Real> a = base_track_args(p, b, k0, k1);
+    a.from_bank = 1;
+    a.birth = birth;
+    a.rin = b.q[1];
+    a.rout = b.q[0];
+    launch_track(p, a);
+    HWW_CK(cudaGetLastError());
+    int cur = 0, waves = 1;
+    for (;;) {
+        HWW_CK(cudaMemcpyAsync(p->h_count, b.q[cur].count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               p->stream));
+        HWW_CK(cudaStreamSynchronize(p->stream));
+        if (*p->h_count == 0) break;
+        if (waves >= MAX_WAVES) {
+            p->last_waves = waves;
+            return HWW_ERR_TIMEOUT;
+        }
+        const int other = 1 - cur;
+        HWW_CK(cudaMemsetAsync(b.q[other].count, 0, sizeof(unsigned long long), p->stream));
+        a.from_bank = 0;
+        a.birth = 0;
+        a.rin = b.q[cur];
+        a.rout = b.q[other];
+        launch_track(p, a);
+        HWW_CK(cudaGetLastError());
+        cur = other;
+        ++waves;
+    }
+    p->last_waves = waves;
+    return HWW_OK;
+}
+
+template <class Real>
+hww_status comb_step(hww_problem* p, Banks<Real>& b) {
+    ScanArgs s{};
+    s.cnt = p->gcnt;
+    s.w = p->gw;
+    s.n = p->N;
+    s.tile_c = p->tile_c;
+    s.tile_w = p->tile_w;
+    s.out_c = p->goff;
+    s.out_w = p->goff_w;
+    launch_group_scan(s, p->stream);
+    HWW_CK(cudaGetLastError());
+    CombArgs<Real> c{};
+    c.sd = p->sd;
+    c.N = p->N;
+    c.ncensus_ptr = p->counts + 0;
+    c.cen_cap = p->cen_cap;
+    c.cx = b.cen.x;
+    c.cmu = b.cen.mu;
+    c.cw = b.cen.w;
+    c.ccell = b.cen.cell;
+    c.cid = b.cen.id;
+    c.clin = b.cen.lin;
+    c.gcnt = p->gcnt;
+    c.goff = p->goff;
+    c.goff_w = p->goff_w;
+    c.gcur = p->gcur;
+    c.member = p->member;
+    c.bx = b.bx;
+    c.bmu = b.bmu;
+    c.bcell = b.bcell;
+    c.stats = p->stats;
+    c.err = p->err;
+    launch_comb(c, p->nsm * 8, p->stream);
+    HWW_CK(cudaGetLastError());
+    return HWW_OK;
+}
+
+LosmIn losm_in(const hww_problem* p) {
+    LosmIn in{};
+    in.I = p->I;
+    in.dx = p->d_dx;
+    in.sigt = p->d_sigt;
+    in.siga = p->d_siga;
+    in.v = p->d.v;
+    in.dt = p->d.dt;
+    in.theta = p->d.theta;
+    in.bc_l = p->d.bc_left;
+    in.bc_r = p->d.bc_right;
+    in.phi_old = p->ophi;
+    in.J_old = p->oJ;
+    in.F_old = p->oF;
+    in.F_new = p->oF;
+    in.q_old = nullptr;
+    in.q_new = nullptr;
+    return in;
+}
+
+hww_status err_to_status(unsigned e) {
+    if (e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW)) return HWW_ERR_BANK_OVERFLOW;
+    if (e) return HWW_ERR_NUMERIC;
+    return HWW_OK;
+}
+
+// read and clear the sticky device error word (synchronizes the stream)
+hww_status take_device_error(const hww_problem* p) {
+    unsigned e = 0;
+    HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    if (e) HWW_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    return err_to_status(e);
+}
+
+__global__ void normalize_kernel(int kind, const Acc128* a, int n, int I, int B, long long N, const double* dx,
+                                 double v, double dt, const StepDev* sd, double* out) {
+    const double isc = pow2(-sd->S);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double val = acc_to_double(a[i]) * isc;
+        double r;
+        if (kind <= HWW_TL_F) {
+            r = val / (((double)N * dx[i]) * dt);
+        } else if (kind <= HWW_CENSUS_F) {
+            r = (v * val) / ((double)N * dx[i]);
+        } else if (kind == HWW_BATCH_PHI) {
+            const int b = i / I, k = i % I;
+            const long long nb = (b < N) ? (N - b - 1) / B + 1 : 0;
+            r = nb ? val / (((double)nb * dx[k]) * dt) : 0.0;
+        } else {
+            r = val / ((double)N * dt);
+        }
+        out[i] = r;
+    }
+}
+
+template <class Real>
+__global__ void bank_to_x_kernel(const Real* bx, const int32_t* bcell, const double* edges, long long n,
+                                 double* out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (sizeof(Real) == sizeof(float))
+            out[i] = edges[bcell[i]] + (double)bx[i];
+        else
+            out[i] = (double)bx[i];
+    }
+}
+
+template <class Real>
+__global__ void to_double_kernel(const Real* in, long long n, double* out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+hww_status copy_out(const hww_problem* p, double* out, const double* src, size_t n, int on_device) {
+    HWW_CK(cudaMemcpyAsync(out, src, n * sizeof(double),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+    if (!on_device) HWW_CK(cudaStreamSynchronize(p->stream));
+    return HWW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hww_status_string(hww_status s) {
+    switch (s) {
+    case HWW_OK: return "ok";
+    case HWW_ERR_ARG: return "invalid argument";
+    case HWW_ERR_STATE: return "call out of order";
+    case HWW_ERR_OOM: return "out of memory";
+    case HWW_ERR_BANK_OVERFLOW: return "particle bank or queue overflow";
+    case HWW_ERR_TIMEOUT: return "bounded wait gave up";
+    case HWW_ERR_NUMERIC: return "numeric guard fired";
+    case HWW_ERR_CUDA: return "CUDA runtime error";
+    case HWW_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+void destroy_problem(hww_problem* p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    for (void* v : p->allocs) cudaFreeAsync(v, p->stream);
+    cudaStreamSynchronize(p->stream);
+    if (p->h_count) cudaFreeHost(p->h_count);
+    delete p;
+}
+
+hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
+    if (!out) return HWW_ERR_ARG;
+    *out = nullptr;
+    if (!d || !d->edges) return HWW_ERR_ARG;
+    const int I = d->n_cells;
+    if (I < 1 || I > MAX_CELLS || !(d->v > 0) || !(d->dt > 0) || !std::isfinite(d->v * d->dt) ||
+        d->particles_per_step < 1 || d->particles_per_step >= (1LL << 31) ||
+        (d->theta != 0.5 && d->theta != 1.0) || d->n_var_batches < 1 || d->n_var_batches > 64 ||
+        d->bc_left < 0 || d->bc_left > 1 || d->bc_right < 0 || d->bc_right > 1 || d->filter < 0 ||
+        d->filter > 1 || (d->filter == 1 && d->filter_k < 1) || d->precision < 0 || d->precision > 1 ||
+        d->deriv_regions < 0 || d->bank_capacity < 0)
+        return HWW_ERR_ARG;
+    for (int i = 0; i < I; ++i)
+        if (!(d->edges[i + 1] > d->edges[i]) || !std::isfinite(d->edges[i + 1])) return HWW_ERR_ARG;
+    if (!(d->src_x >= d->edges[0] && d->src_x <= d->edges[I])) return HWW_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return HWW_ERR_NO_DEVICE;
+    if (d->device < 0 || d->device >= ndev) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(d->device));
+
+    hww_problem* p = new (std::nothrow) hww_problem();
+    if (!p) return HWW_ERR_OOM;
+    p->d = *d;
+    p->d.edges = nullptr;
+    p->I = I;
+    p->B = d->n_var_batches;
+    p->N = d->particles_per_step;
+    p->fp32 = d->precision == HWW_FP32_TRACK;
+    p->stream = (cudaStream_t)d->cuda_stream;
+    p->device = d->device;
+    p->edges.assign(d->edges, d->edges + I + 1);
+    p->dx.resize(I);
+    for (int i = 0; i < I; ++i) p->dx[i] = p->edges[i + 1] - p->edges[i];
+    p->cen_cap = d->bank_capacity ? d->bank_capacity : 4 * p->N;
+    p->q_cap = d->bank_capacity ? d->bank_capacity / 2 + 1 : 2 * p->N;
+    cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
+    p->birth_pos = birth_cell(p->edges, I, d->src_x, 1.0);
+    p->birth_neg = birth_cell(p->edges, I, d->src_x, -1.0);
+
+    hww_status s = HWW_OK;
+    const int B = p->B;
+    p->acc_bytes = sizeof(Acc128) * (6 * (size_t)I + (size_t)B * I + 6) + sizeof(unsigned long long) * (ST_COUNT + 3);
+    p->grp_bytes = (sizeof(unsigned long long) + 2 * sizeof(uint32_t)) * (size_t)p->N;
+    const long long ntiles = group_scan_tiles(p->N);
+    if ((s = dalloc(p, (char**)&p->acc, p->acc_bytes)) || (s = dalloc(p, (char**)&p->grp, p->grp_bytes)) ||
+        (s = dalloc(p, &p->d_edges, I + 1)) || (s = dalloc(p, &p->d_dx, I)) || (s = dalloc(p, &p->d_sigt, I)) ||
+        (s = dalloc(p, &p->d_inv_sigt, I)) || (s = dalloc(p, &p->d_c, I)) || (s = dalloc(p, &p->d_siga, I)) ||
+        (s = dalloc(p, &p->d_dxf, I)) || (s = dalloc(p, &p->d_inv_sigt_f, I)) || (s = dalloc(p, &p->d_region, I)) ||
+        (s = dalloc(p, &p->ww_c, I)) || (s = dalloc(p, &p->ww_hi, I)) || (s = dalloc(p, &p->ww_lo, I)) ||
+        (s = dalloc(p, &p->ww_override, I)) || (s = dalloc(p, &p->goff, p->N + 1)) ||
+        (s = dalloc(p, &p->goff_w, p->N + 1)) || (s = dalloc(p, &p->tile_c, ntiles + 1)) ||
+        (s = dalloc(p, &p->tile_w, ntiles + 1)) || (s = dalloc(p, &p->member, p->cen_cap)) ||
+        (s = dalloc(p, &p->ophi, I + 2)) || (s = dalloc(p, &p->oJ, I + 1)) || (s = dalloc(p, &p->oF, I + 2)) ||
+        (s = dalloc(p, &p->oP, 2)) || (s = dalloc(p, &p->nphi, I + 2)) || (s = dalloc(p, &p->nJ, I + 1)) ||
+        (s = dalloc(p, &p->nF, I + 2)) || (s = dalloc(p, &p->nP, 2)) || (s = dalloc(p, &p->cJ, I)) ||
+        (s = dalloc(p, &p->tmp, I + 1)) || (s = dalloc(p, &p->prev_tl, I)) || (s = dalloc(p, &p->semi_phi, I + 2)) ||
+        (s = dalloc(p, &p->semi_J, I + 1)) || (s = dalloc(p, &p->full_phi, I + 2)) ||
+        (s = dalloc(p, &p->full_J, I + 1)) || (s = dalloc(p, &p->work, 4 * (I + 2))) ||
+        (s = dalloc(p, &p->norm, (size_t)B * I + 6 * (size_t)I + 8)) || (s = dalloc(p, &p->sd, 1)) ||
+        (s = dalloc(p, &p->err, 1))) {
+        destroy_problem(p);
+        return s;
+    }
+    char* acc = (char*)p->acc;
+    p->tl = (Acc128*)acc;
+    p->cent = p->tl + 3 * I;
+    p->batch = p->cent + 3 * I;
+    p->bnd = p->batch + (size_t)B * I;
+    p->stats = (unsigned long long*)(p->bnd + 6);
+    p->counts = p->stats + ST_COUNT;
+    p->gw = (unsigned long long*)p->grp;
+    p->gcnt = (uint32_t*)(p->gw + p->N);
+    p->gcur = p->gcnt + p->N;
+    s = p->fp32 ? alloc_banks(p, p->b32) : alloc_banks(p, p->b64);
+    if (s) {
+        destroy_problem(p);
+        return s;
+    }
+    if (cudaMallocHost(&p->h_count, sizeof(unsigned long long)) != cudaSuccess) {
+        p->h_count = nullptr;
+        destroy_problem(p);
+        return HWW_ERR_OOM;
+    }
+    // mesh, initial condition and step scalars
+    std::vector<float> dxf(I);
+    for (int i = 0; i < I; ++i) dxf[i] = (float)p->dx[i];
+    std::vector<double> phi0;
+    source_moments(p, phi0);
+    std::vector<double> zeros(I + 2, 0.0);
+    StepDev sd{};
+    sd.wbar = 1.0;
+    sd.nbank = (unsigned long long)p->N;
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, p->stream);
+    };
+    up(p->d_edges, p->edges.data(), sizeof(double) * (I + 1));
+    up(p->d_dx, p->dx.data(), sizeof(double) * I);
+    up(p->d_dxf, dxf.data(), sizeof(float) * I);
+    up(p->ophi, phi0.data(), sizeof(double) * (I + 2));
+    up(p->oJ, zeros.data(), sizeof(double) * (I + 1));
+    up(p->oF, zeros.data(), sizeof(double) * (I + 2));
+    up(p->oP, zeros.data(), sizeof(double) * 2);
+    up(p->sd, &sd, sizeof(StepDev));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        destroy_problem(p);
+        return cuda_status(e);
+    }
+    // tracking launch shape: persistent grid of resident blocks
+    p->track_smem = sizeof(long long) * 6 * (size_t)I;
+    if (p->track_smem > 48 * 1024) {
+        if ((p->fp32 ? track_smem_optin_fp32(p->track_smem) : track_smem_optin_fp64(p->track_smem)) != 0) {
+            destroy_problem(p);
+            return HWW_ERR_CUDA;
+        }
+    }
+    int per_sm = p->fp32 ? track_blocks_per_sm_fp32(TRACK_BLOCK, p->track_smem)
+                         : track_blocks_per_sm_fp64(TRACK_BLOCK, p->track_smem);
+    if (per_sm < 1) per_sm = 1;
+    p->track_grid = p->nsm * per_sm;
+    *out = p;
+    return HWW_OK;
+}
+
+hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const double* c, const int32_t* region) {
+    if (!p || !sigma_t || !c) return HWW_ERR_ARG;
+    const int I = p->I;
+    for (int i = 0; i < I; ++i) {
+        if (!(sigma_t[i] > 0) || !std::isfinite(sigma_t[i]) || !(c[i] >= 0 && c[i] <= 1)) return HWW_ERR_ARG;
+        if (region && (region[i] < 0 || (p->d.deriv_regions > 0 && region[i] >= p->d.deriv_regions)))
+            return HWW_ERR_ARG;
+    }
+    HWW_CK(cudaSetDevice(p->device));
+    std::vector<double> st(sigma_t, sigma_t + I), inv(I), cc(c, c + I), sa(I);
+    std::vector<float> invf(I);
+    std::vector<int32_t> reg(I, 0);
+    for (int i = 0; i < I; ++i) {
+        inv[i] = 1.0 / st[i];
+        invf[i] = (float)(1.0 / st[i]);
+        sa[i] = st[i] * (1.0 - cc[i]);
+        if (region) reg[i] = region[i];
+    }
+    HWW_CK(cudaMemcpyAsync(p->d_sigt, st.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(cudaMemcpyAsync(p->d_inv_sigt, inv.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(cudaMemcpyAsync(p->d_inv_sigt_f, invf.data(), sizeof(float) * I, cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(cudaMemcpyAsync(p->d_c, cc.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(cudaMemcpyAsync(p->d_siga, sa.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(cudaMemcpyAsync(p->d_region, reg.data(), sizeof(int32_t) * I, cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    p->xs_set = 1;
+    return HWW_OK;
+}
+
+hww_status set_ww_params(hww_problem* p, double rho, double eps_min, int32_t mode, int32_t scaling) {
+    if (!p || !(rho >= 1.0) || !std::isfinite(rho) || !(eps_min > 0.0 && eps_min <= 1.0) || mode < 0 ||
+        mode > 2 || scaling < 0 || scaling > 1)
+        return HWW_ERR_ARG;
+    p->rho = rho;
+    p->eps = eps_min;
+    p->mode = mode;
+    p->scaling = scaling;
+    p->ww_set = 1;
+    return HWW_OK;
+}
+
+hww_status set_ww_centers(hww_problem* p, const double* centers) {
+    if (!p || !centers) return HWW_ERR_ARG;
+    for (int i = 0; i < p->I; ++i)
+        if (!(centers[i] > 0) || !std::isfinite(centers[i])) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(p->device));
+    HWW_CK(cudaMemcpyAsync(p->ww_override, centers, sizeof(double) * p->I, cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    p->has_override = 1;
+    return HWW_OK;
+}
+
+hww_status run_step(hww_problem* p, hww_step_stats* st) {
+    if (!p) return HWW_ERR_ARG;
+    if (!p->xs_set || !p->ww_set) return HWW_ERR_STATE;
+    HWW_CK(cudaSetDevice(p->device));
+    const long long n = p->steps + 1;
+    const uint32_t k0 = (uint32_t)p->d.seed;
+    const uint32_t k1 = (uint32_t)(p->d.seed >> 32) ^ (uint32_t)n;
+    HWW_CK(cudaMemsetAsync(p->acc, 0, p->acc_bytes, p->stream));
+    HWW_CK(cudaMemsetAsync(p->grp, 0, p->grp_bytes, p->stream));
+
+    PreArgs pa{};
+    pa.sd = p->sd;
+    pa.nbits = bit_length(p->N);
+    pa.k0 = k0;
+    pa.k1 = k1;
+    pa.losm = losm_in(p);
+    pa.P_old = p->oP;
+    pa.semi_phi = p->semi_phi;
+    pa.semi_J = p->semi_J;
+    pa.w_d = p->work;
+    pa.w_m = p->work + (p->I + 2);
+    pa.w_c = p->work + 2 * (p->I + 2);
+    pa.w_r = p->work + 3 * (p->I + 2);
+    pa.err = p->err;
+    pa.ww_source = p->has_override ? 3
+                   : p->mode == HWW_MODE_HWW ? 1
+                   : (p->mode == HWW_MODE_LWW && p->has_prev_tl) ? 2
+                                                                 : 0;
+    pa.scaling = p->scaling;
+    pa.eps = p->eps;
+    pa.rho = p->rho;
+    pa.prev_tl = p->prev_tl;
+    pa.ww_override = p->ww_override;
+    pa.ww_c = p->ww_c;
+    pa.ww_hi = p->ww_hi;
+    pa.ww_lo = p->ww_lo;
+    pa.stats = p->stats;
+    launch_prestep(pa, p->stream);
+    HWW_CK(cudaGetLastError());
+
+    hww_status s = p->fp32 ? track_waves(p, p->b32, k0, k1, n == 1) : track_waves(p, p->b64, k0, k1, n == 1);
+    p->has_override = 0;
+    if (s) return s;
+
+    PostArgs po{};
+    po.I = p->I;
+    po.sd = p->sd;
+    po.v = p->d.v;
+    po.dt = p->d.dt;
+    po.N = p->N;
+    po.bc_l = p->d.bc_left;
+    po.bc_r = p->d.bc_right;
+    po.filter_k = p->d.filter == HWW_FILTER_MA ? p->d.filter_k : 0;
+    po.dx = p->d_dx;
+    po.cent = p->cent;
+    po.tl = p->tl;
+    po.bnd = p->bnd;
+    po.nphi = p->nphi;
+    po.nJ = p->nJ;
+    po.nF = p->nF;
+    po.nP = p->nP;
+    po.cJ = p->cJ;
+    po.tmp = p->tmp;
+    po.prev_tl = p->prev_tl;
+    po.ophi = p->ophi;
+    po.oJ = p->oJ;
+    po.oF = p->oF;
+    po.oP = p->oP;
+    po.losm = losm_in(p);
+    po.full_phi = p->full_phi;
+    po.full_J = p->full_J;
+    po.w_d = pa.w_d;
+    po.w_m = pa.w_m;
+    po.w_c = pa.w_c;
+    po.w_r = pa.w_r;
+    po.err = p->err;
+    launch_poststep(po, p->stream);
+    HWW_CK(cudaGetLastError());
+
+    s = p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);
+    if (s) return s;
+    p->steps = n;
+    p->has_prev_tl = 1;
+
+    if (st) {
+        unsigned long long h[ST_COUNT];
+        StepDev sdh;
+        unsigned e = 0;
+        HWW_CK(cudaMemcpyAsync(h, p->stats, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaStreamSynchronize(p->stream));
+        std::memset(st, 0, sizeof(*st));
+        st->segments = (int64_t)h[ST_SEGMENTS];
+        st->collisions = (int64_t)h[ST_COLLISIONS];
+        st->crossings = (int64_t)h[ST_CROSSINGS];
+        st->reflections = (int64_t)h[ST_REFLECTIONS];
+        st->leaked = (int64_t)h[ST_LEAKED];
+        st->absorbed = (int64_t)h[ST_ABSORBED];
+        st->scatters = (int64_t)h[ST_SCATTERS];
+        st->split_events = (int64_t)h[ST_SPLIT_EVENTS];
+        st->daughters = (int64_t)h[ST_DAUGHTERS];
+        st->roulette_kills = (int64_t)h[ST_RKILLS];
+        st->roulette_survivals = (int64_t)h[ST_RSURVIVE];
+        st->census = (int64_t)h[ST_CENSUS];
+        st->lineage_collisions = (int64_t)h[ST_LINEAGE];
+        st->max_events = (int64_t)h[ST_MAX_EVENTS];
+        st->n_next = (int64_t)sdh.nbank;
+        st->n_start = (int64_t)h[ST_NSTART];
+        st->w_bar_next = sdh.wbar;
+        st->waves = p->last_waves;
+        if (e) HWW_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+        st->status = err_to_status(e);
+        return (hww_status)st->status;
+    }
+    return HWW_OK;
+}
+
+hww_status get_tallies(const hww_problem* p, int32_t kind, double* out, int64_t n, int32_t on_device) {
+    if (!p || !out || kind < 0 || kind > HWW_CLOSURE_F) return HWW_ERR_ARG;
+    if (p->steps < 1) return HWW_ERR_STATE;
+    HWW_CK(cudaSetDevice(p->device));
+    const int I = p->I, B = p->B;
+    const Acc128* src = nullptr;
+    int len = I;
+    switch (kind) {
+    case HWW_TL_PHI: src = p->tl; break;
+    case HWW_TL_J: src = p->tl + I; break;
+    case HWW_TL_F: src = p->tl + 2 * I; break;
+    case HWW_CENSUS_PHI: src = p->cent; break;
+    case HWW_CENSUS_J: src = p->cent + I; break;
+    case HWW_CENSUS_F: src = p->cent + 2 * I; break;
+    case HWW_BATCH_PHI: src = p->batch; len = B * I; break;
+    case HWW_BOUNDARY: src = p->bnd; len = 6; break;
+    case HWW_WW_CENTER: return n < I ? HWW_ERR_ARG : copy_out(p, out, p->ww_c, I, on_device);
+    case HWW_CLOSURE_PHI: return n < I + 2 ? HWW_ERR_ARG : copy_out(p, out, p->ophi, I + 2, on_device);
+    case HWW_CLOSURE_J: return n < I + 1 ? HWW_ERR_ARG : copy_out(p, out, p->oJ, I + 1, on_device);
+    case HWW_CLOSURE_F: return n < I + 2 ? HWW_ERR_ARG : copy_out(p, out, p->oF, I + 2, on_device);
+    }
+    if (n < len) return HWW_ERR_ARG;
+    normalize_kernel<<<(len + 255) / 256, 256, 0, p->stream>>>(kind, src, len, I, B, p->N, p->d_dx, p->d.v,
+                                                                p->d.dt, p->sd, p->norm);
+    HWW_CK(cudaGetLastError());
+    return copy_out(p, out, p->norm, len, on_device);
+}
+
+hww_status get_tallies_raw(const hww_problem* p, int32_t kind, int64_t* out, int64_t n) {
+    if (!p || !out || kind < 0 || kind > HWW_BOUNDARY) return HWW_ERR_ARG;
+    if (p->steps < 1) return HWW_ERR_STATE;
+    HWW_CK(cudaSetDevice(p->device));
+    const int I = p->I, B = p->B;
+    const Acc128* src = nullptr;
+    long long len = I;
+    switch (kind) {
+    case HWW_TL_PHI: src = p->tl; break;
+    case HWW_TL_J: src = p->tl + I; break;
+    case HWW_TL_F: src = p->tl + 2 * I; break;
+    case HWW_CENSUS_PHI: src = p->cent; break;
+    case HWW_CENSUS_J: src = p->cent + I; break;
+    case HWW_CENSUS_F: src = p->cent + 2 * I; break;
+    case HWW_BATCH_PHI: src = p->batch; len = (long long)B * I; break;
+    case HWW_BOUNDARY: src = p->bnd; len = 6; break;
+    }
+    if (n < 2 * len) return HWW_ERR_ARG;
+    HWW_CK(cudaMemcpyAsync(out, src, sizeof(Acc128) * len, cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    return HWW_OK;
+}
+
+hww_status get_losm_solution(const hww_problem* p, int32_t which, double* phi, double* J, int32_t on_device) {
+    if (!p || !phi || !J || which < 0 || which > 1) return HWW_ERR_ARG;
+    if (p->steps < 1) return HWW_ERR_STATE;
+    HWW_CK(cudaSetDevice(p->device));
+    hww_status s = copy_out(p, phi, which ? p->full_phi : p->semi_phi, p->I + 2, on_device);
+    if (s) return s;
+    return copy_out(p, J, which ? p->full_J : p->semi_J, p->I + 1, on_device);
+}
+
+hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, int64_t cap, int64_t* n) {
+    if (!p || !n) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(p->device));
+    StepDev sdh;
+    HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    const long long m = (p->steps < 1) ? 0 : (long long)sdh.nbank;
+    *n = m;
+    if (cap == 0 || m == 0) return HWW_OK;
+    if (cap < m) return HWW_ERR_ARG;
+    double* tmp = nullptr;
+    HWW_CK(cudaMallocAsync(&tmp, sizeof(double) * m, p->stream));
+    cudaError_t e = cudaSuccess;
+    const int grid = p->nsm * 4;
+    if (x) {
+        if (p->fp32)
+            bank_to_x_kernel<float><<<grid, 256, 0, p->stream>>>(p->b32.bx, p->b32.bcell, p->d_edges, m, tmp);
+        else
+            bank_to_x_kernel<double><<<grid, 256, 0, p->stream>>>(p->b64.bx, p->b64.bcell, p->d_edges, m, tmp);
+        e = cudaMemcpyAsync(x, tmp, sizeof(double) * m, cudaMemcpyDeviceToHost, p->stream);
+    }
+    if (mu && e == cudaSuccess) {
+        if (p->fp32)
+            to_double_kernel<float><<<grid, 256, 0, p->stream>>>(p->b32.bmu, m, tmp);
+        else
+            to_double_kernel<double><<<grid, 256, 0, p->stream>>>(p->b64.bmu, m, tmp);
+        e = cudaMemcpyAsync(mu, tmp, sizeof(double) * m, cudaMemcpyDeviceToHost, p->stream);
+    }
+    if (cell && e == cudaSuccess)
+        e = cudaMemcpyAsync(cell, p->fp32 ? p->b32.bcell : p->b64.bcell, sizeof(int32_t) * m,
+                            cudaMemcpyDeviceToHost, p->stream);
+    cudaFreeAsync(tmp, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return cuda_status(e);
+}
+
+hww_status get_census(const hww_problem* p, double* x, double* mu, double* w, int32_t* cell, uint32_t* id,
+                      uint64_t* lin, int64_t cap, int64_t* n) {
+    if (!p || !n) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(p->device));
+    StepDev sdh;
+    HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    long long m = (p->steps < 1) ? 0 : (long long)sdh.ncensus;
+    if (m > p->cen_cap) m = p->cen_cap;
+    *n = m;
+    if (cap == 0 || m == 0) return HWW_OK;
+    if (cap < m) return HWW_ERR_ARG;
+    double* tmp = nullptr;
+    HWW_CK(cudaMallocAsync(&tmp, sizeof(double) * m, p->stream));
+    cudaError_t e = cudaSuccess;
+    const int grid = p->nsm * 4;
+    if (x) {
+        if (p->fp32)
+            bank_to_x_kernel<float><<<grid, 256, 0, p->stream>>>(p->b32.cen.x, p->b32.cen.cell, p->d_edges, m, tmp);
+        else
+            bank_to_x_kernel<double><<<grid, 256, 0, p->stream>>>(p->b64.cen.x, p->b64.cen.cell, p->d_edges, m, tmp);
+        e = cudaMemcpyAsync(x, tmp, sizeof(double) * m, cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    }
+    if (mu && e == cudaSuccess) {
+        if (p->fp32)
+            to_double_kernel<float><<<grid, 256, 0, p->stream>>>(p->b32.cen.mu, m, tmp);
+        else
+            to_double_kernel<double><<<grid, 256, 0, p->stream>>>(p->b64.cen.mu, m, tmp);
+        e = cudaMemcpyAsync(mu, tmp, sizeof(double) * m, cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    }
+    if (w && e == cudaSuccess)
+        e = cudaMemcpyAsync(w, p->fp32 ? p->b32.cen.w : p->b64.cen.w, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                            p->stream);
+    if (cell && e == cudaSuccess)
+        e = cudaMemcpyAsync(cell, p->fp32 ? p->b32.cen.cell : p->b64.cen.cell, sizeof(int32_t) * m,
+                            cudaMemcpyDeviceToHost, p->stream);
+    if (id && e == cudaSuccess)
+        e = cudaMemcpyAsync(id, p->fp32 ? p->b32.cen.id : p->b64.cen.id, sizeof(uint32_t) * m,
+                            cudaMemcpyDeviceToHost, p->stream);
+    if (lin && e == cudaSuccess)
+        e = cudaMemcpyAsync(lin, p->fp32 ? p->b32.cen.lin : p->b64.cen.lin, sizeof(uint64_t) * m,
+                            cudaMemcpyDeviceToHost, p->stream);
+    cudaFreeAsync(tmp, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return cuda_status(e);
+}
+
+hww_status hww_losm_solve(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a, double v,
+                          double dt, double theta, int32_t bc_left, int32_t bc_right, const double* phi_old,
+                          const double* J_old, const double* F_old, const double* F_new, double PL_new,
+                          double PR_new, const double* q_old, const double* q_new, double* phi_new,
+                          double* J_new) {
+    if (I < 1 || !dx || !sigma_t || !sigma_a || !phi_old || !J_old || !F_old || !F_new || !phi_new || !J_new ||
+        !(v > 0) || !(dt > 0) || (theta != 0.5 && theta != 1.0) || bc_left < 0 || bc_left > 1 || bc_right < 0 ||
+        bc_right > 1)
+        return HWW_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return HWW_ERR_NO_DEVICE;
+    // one device buffer: 5 cell arrays, 4 (I+2) vectors, 3 (I+1) vectors, work, err
+    const size_t n2 = I + 2, n1 = I + 1;
+    const size_t total = 5 * (size_t)I + 4 * n2 + 2 * n1 + 4 * n2 + 1;
+    double* buf = nullptr;
+    HWW_CK(cudaMalloc(&buf, total * sizeof(double)));
+    double* d_dx = buf;
+    double* d_st = d_dx + I;
+    double* d_sa = d_st + I;
+    double* d_qo = d_sa + I;
+    double* d_qn = d_qo + I;
+    double* d_po = d_qn + I;
+    double* d_Fo = d_po + n2;
+    double* d_Fn = d_Fo + n2;
+    double* d_pn = d_Fn + n2;
+    double* d_Jo = d_pn + n2;
+    double* d_Jn = d_Jo + n1;
+    double* d_w = d_Jn + n1;
+    unsigned* d_err = (unsigned*)(d_w + 4 * n2);
+    cudaError_t e = cudaSuccess;
+    auto up = [&](double* dst, const double* src, size_t cnt) {
+        if (e == cudaSuccess && src) e = cudaMemcpy(dst, src, cnt * sizeof(double), cudaMemcpyHostToDevice);
+    };
+    up(d_dx, dx, I);
+    up(d_st, sigma_t, I);
+    up(d_sa, sigma_a, I);
+    up(d_qo, q_old, I);
+    up(d_qn, q_new, I);
+    up(d_po, phi_old, n2);
+    up(d_Fo, F_old, n2);
+    up(d_Fn, F_new, n2);
+    up(d_Jo, J_old, n1);
+    if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        LosmIn in{};
+        in.I = I;
+        in.dx = d_dx;
+        in.sigt = d_st;
+        in.siga = d_sa;
+        in.v = v;
+        in.dt = dt;
+        in.theta = theta;
+        in.bc_l = bc_left;
+        in.bc_r = bc_right;
+        in.phi_old = d_po;
+        in.J_old = d_Jo;
+        in.F_old = d_Fo;
+        in.F_new = d_Fn;
+        in.PL = PL_new;
+        in.PR = PR_new;
+        in.q_old = q_old ? d_qo : nullptr;
+        in.q_new = q_new ? d_qn : nullptr;
+        launch_losm_only(in, d_pn, d_Jn, d_w, d_err, 0);
+        e = cudaGetLastError();
+    }
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(phi_new, d_pn, n2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(J_new, d_Jn, n1 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_status(e);
+    return herr ? HWW_ERR_NUMERIC : HWW_OK;
+}
+
+hww_status hww_philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                            int64_t n, uint32_t* out) {
+    if (n < 0 || (n > 0 && !out) || n > (1LL << 28)) return HWW_ERR_ARG;
+    if (n == 0) return HWW_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return HWW_ERR_NO_DEVICE;
+    uint32_t* d = nullptr;
+    HWW_CK(cudaMalloc(&d, sizeof(uint32_t) * 4 * n));
+    launch_philox_block(c0, c1, c2, c3, k0, k1, n, d, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// hww_device.cuh -- device numerics of the HWW library (sm_103a).
+//
+// The library and its CPU checker agree on a written numerics contract, and
+// each implements it on its own:
+//   * counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+//     SC'11) with key (seed_lo, seed_hi ^ n) and counter
+//     (id, lineage_lo, lineage_hi, 2 e + s) for event e of a track, word s = 0
+//     giving the flight and absorption uniforms, s = 1 the new direction and
+//     the roulette uniform;
+//   * uniform on (0,1): top 52 bits of a 64-bit word plus one half, times
+//     2^-52 (FP64); top 23 bits plus one half times 2^-23 (FP32 tracking);
+//   * log: reduction to m in [sqrt(1/2), sqrt(2)) and the atanh series
+//     2s(1 + z/3 + ... + z^11/23), z = s^2, s = (m-1)/(m+1), by Horner with
+//     fused multiply-adds, plus k ln 2 (ln 2 split in a 32-bit head and a tail);
+//   * tallies: contributions rounded to nearest-even 64-bit integers at a
+//     power-of-two scale, summed as 128-bit integers, so that any order of
+//     summation gives the same bits.
+// FP64 translation units are built with contraction off, so every a*b+c
+// below is two roundings unless fma() is written.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hww {
+
+struct Acc128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c[0];
+        const uint32_t lo1 = 0xCD9E8D57u * c[2];
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]);
+#else
+        const uint32_t hi0 = (uint32_t)(((uint64_t)0xD2511F53u * c[0]) >> 32);
+        const uint32_t hi1 = (uint32_t)(((uint64_t)0xCD9E8D57u * c[2]) >> 32);
+#endif
+        const uint32_t n0 = hi1 ^ c[1] ^ k0;
+        const uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__host__ __device__ __forceinline__ double u01(uint32_t lo, uint32_t hi) {
+    const uint64_t x = ((uint64_t)hi << 32) | lo;
+    return ((double)(x >> 12) + 0.5) * 0x1p-52;
+}
+
+__host__ __device__ __forceinline__ float u01f(uint32_t hi) {
+    return ((float)(hi >> 9) + 0.5f) * 0x1p-23f;
+}
+
+__device__ __forceinline__ double hw_log(double u) {
+    const long long b = __double_as_longlong(u);
+    int k = (int)((b >> 52) & 0x7ff) - 1023;
+    double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    if (m > 0x1.6a09e667f3bcdp+0) {
+        m = m * 0.5;
+        k = k + 1;
+    }
+    const double f = m - 1.0;
+    const double s = f / (m + 1.0);
+    const double z = s * s;
+    double p = 1.0 / 23.0;
+    p = fma(p, z, 1.0 / 21.0);
+    p = fma(p, z, 1.0 / 19.0);
+    p = fma(p, z, 1.0 / 17.0);
+    p = fma(p, z, 1.0 / 15.0);
+    p = fma(p, z, 1.0 / 13.0);
+    p = fma(p, z, 1.0 / 11.0);
+    p = fma(p, z, 1.0 / 9.0);
+    p = fma(p, z, 1.0 / 7.0);
+    p = fma(p, z, 1.0 / 5.0);
+    p = fma(p, z, 1.0 / 3.0);
+    const double s2 = s + s;
+    const double tail = s2 * (z * p);
+    const double kd = (double)k;
+    const double lo = fma(kd, 0x1.a39ef35793c76p-33, tail);
+    return fma(kd, 0x1.62e42fee00000p-1, s2 + lo);
+}
+
+// lineage key of daughter j of a split at event e of a track with key `lin`
+__host__ __device__ __forceinline__ uint64_t lineage_hash(uint64_t lin, uint32_t e, uint32_t j) {
+    uint32_t c[4] = {(uint32_t)lin, (uint32_t)(lin >> 32), e, j};
+    philox4x32_10(c, 0x4C494E45u, 0x41474521u);
+    return ((uint64_t)c[1] << 32) | c[0];
+}
+
+// x * scale rounded to the nearest 64-bit integer (ties to even); scale is a
+// power of two, so the product is exact
+__device__ __forceinline__ long long to_fixed(double x, double scale) {
+    return __double2ll_rn(x * scale);
+}
+
+// 128-bit accumulation with two 64-bit atomics: the low word returns its old
+// value, so the carry out of it is known exactly
+__device__ __forceinline__ void add128(Acc128* a, long long v) {
+    if (v == 0) return;
+    const unsigned long long lo = (unsigned long long)v;
+    const unsigned long long old = atomicAdd(&a->lo, lo);
+    long long hi = (v < 0) ? -1 : 0;
+    if (old + lo < old) hi += 1;
+    if (hi != 0) atomicAdd((unsigned long long*)&a->hi, (unsigned long long)hi);
+}
+
+// 128-bit value to double: one rounding when it fits a signed 64-bit
+// integer, else hi*2^64 + lo
+__host__ __device__ __forceinline__ double acc_to_double(Acc128 a) {
+    const bool fits = (a.hi == 0 && (long long)a.lo >= 0) || (a.hi == -1 && (long long)a.lo < 0);
+    if (fits) return (double)(long long)a.lo;
+    return (double)a.hi * 0x1p64 + (double)a.lo;
+}
+
+// 2^e as a double for -1022 <= e <= 1023
+__host__ __device__ __forceinline__ double pow2(int e) {
+    union {
+        unsigned long long u;
+        double d;
+    } v;
+    v.u = (unsigned long long)(e + 1023) << 52;
+    return v.d;
+}
+
+}  // namespace hww

@@ -1,0 +1,121 @@
+// hww_internal.cuh -- data layout shared by the library's translation units.
+//
+// Device memory of one problem (all SoA, one GPU):
+//   start bank   x | mu | cell           N particles; weight w_bar each, tau = v dt,
+//                                        id = slot, lineage 0, event 0 (implicit)
+//   record queue x mu tau w cell id lin e jstart jcount   (two, ping-pong)
+//                a record is either one live track (jcount == 0) or up to
+//                SPLIT_CHUNK daughters j in [jstart, jstart+jcount) of a split
+//   census bank  x mu w cell id lin     particles that reached t^n
+//   comb groups  count / fixed-point weight per source id, their exclusive
+//                scans, and the census indices grouped by id
+//   tallies      128-bit fixed-point accumulators (Acc128)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hww_device.cuh"
+
+namespace hww {
+
+constexpr int SPLIT_CHUNK = 8;
+constexpr uint32_t MAX_DAUGHTERS = 1u << 24;
+constexpr uint32_t MAX_EVENTS = 1u << 30;
+constexpr double GRAZE_MU = 0.01;
+
+enum ErrBits : unsigned {
+    ERR_CENSUS_OVERFLOW = 1u,
+    ERR_QUEUE_OVERFLOW = 2u,
+    ERR_DAUGHTERS = 4u,
+    ERR_EVENTS = 8u,
+    ERR_LOSM = 16u,
+    ERR_COMB = 32u,
+};
+
+enum StatIdx {
+    ST_SEGMENTS = 0, ST_COLLISIONS, ST_CROSSINGS, ST_REFLECTIONS, ST_LEAKED, ST_ABSORBED,
+    ST_SCATTERS, ST_SPLIT_EVENTS, ST_DAUGHTERS, ST_RKILLS, ST_RSURVIVE, ST_CENSUS,
+    ST_LINEAGE, ST_MAX_EVENTS, ST_NSTART, ST_COUNT
+};
+
+// per-step scalars that live on the device so that no step needs the host
+struct StepDev {
+    double wbar;     // weight of each start-bank particle
+    double tscale;   // 2^S, tally fixed-point scale
+    double cscale;   // 2^Sc, comb weight fixed-point scale
+    double u_comb;   // comb offset in [0,1)
+    int S, Sc;
+    int pad0, pad1;
+    unsigned long long nbank;      // start-bank size
+    unsigned long long W;          // total census weight (fixed point)
+    unsigned long long ncensus;    // census bank size of the step
+};
+
+template <class Real>
+struct RecQ {
+    Real* x;
+    Real* mu;
+    Real* tau;
+    double* w;
+    int32_t* cell;
+    uint32_t* id;
+    uint64_t* lin;
+    uint32_t* e;
+    uint32_t* jstart;
+    uint32_t* jcount;
+    unsigned long long* count;
+    long long cap;
+};
+
+template <class Real>
+struct CenQ {
+    Real* x;
+    Real* mu;
+    double* w;
+    int32_t* cell;
+    uint32_t* id;
+    uint64_t* lin;
+    unsigned long long* count;
+    long long cap;
+};
+
+template <class Real>
+struct TrackArgs {
+    int I, B, emax;
+    int ww_on;
+    int from_bank, birth;
+    int bc_l, bc_r;
+    int birth_cell_pos, birth_cell_neg;
+    uint32_t k0, k1;
+    double tau0;      // v dt
+    double src_x;
+    const double* edges;
+    const double* inv_sigt;
+    const double* c;
+    const float* dxf;        // FP32 cell widths
+    const float* inv_sigt_f; // FP32 1/Sigma_t
+    const double* ww_c;
+    const double* ww_hi;
+    const double* ww_lo;
+    const StepDev* sd;
+    // start bank
+    const Real* bx;
+    const Real* bmu;
+    const int32_t* bcell;
+    RecQ<Real> rin, rout;
+    CenQ<Real> cen;
+    uint32_t* gcnt;
+    unsigned long long* gw;
+    Acc128* tl;     // 3 I
+    Acc128* cent;   // 3 I
+    Acc128* batch;  // B I
+    Acc128* bnd;    // 6
+    unsigned long long* stats;
+    unsigned* err;
+};
+
+// kernels implemented in the tracking translation units
+void launch_track_fp64(const TrackArgs<double>& a, int grid, int block, size_t smem, cudaStream_t s);
+void launch_track_fp32(const TrackArgs<float>& a, int grid, int block, size_t smem, cudaStream_t s);
+
+}  // namespace hww

@@ -1,0 +1,68 @@
+// track_common.cuh -- pieces shared by the FP64 and FP32 tracking kernels:
+// warp-aggregated slot reservation, per-block counters and the flush of the
+// block-private fixed-point tallies.
+#pragma once
+#include "hww_internal.cuh"
+
+namespace hww {
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// One slot per calling lane; one atomic per group of converged lanes.
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* cnt) {
+    const unsigned mask = __activemask();
+    const int leader = __ffs(mask) - 1;
+    const unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(cnt, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + (unsigned long long)__popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ void sadd(long long* s, long long v) {
+    atomicAdd((unsigned long long*)s, (unsigned long long)v);
+}
+
+struct Counters {
+    unsigned v[ST_COUNT];
+    __device__ void zero() {
+#pragma unroll
+        for (int i = 0; i < ST_COUNT; ++i) v[i] = 0;
+    }
+};
+
+// block reduction of the per-thread counters into the global 64-bit stats
+__device__ __forceinline__ void flush_counters(Counters& c, unsigned long long* stats) {
+    __shared__ unsigned long long red[ST_COUNT];
+    if (threadIdx.x < ST_COUNT) red[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ST_COUNT; ++i) {
+        unsigned x = c.v[i];
+        if (i == ST_MAX_EVENTS) {
+            for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+            if (lane_id() == 0 && x) atomicMax(&red[i], (unsigned long long)x);
+        } else {
+            unsigned long long y = x;
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            if (lane_id() == 0 && y) atomicAdd(&red[i], y);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < ST_COUNT && red[threadIdx.x]) {
+        if (threadIdx.x == ST_MAX_EVENTS)
+            atomicMax(&stats[ST_MAX_EVENTS], red[threadIdx.x]);
+        else
+            atomicAdd(&stats[threadIdx.x], red[threadIdx.x]);
+    }
+}
+
+// block-private tallies (6 I signed 64-bit) into the global 128-bit ones
+__device__ __forceinline__ void flush_tallies(const long long* sm, int I, Acc128* tl, Acc128* cent) {
+    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) {
+        const long long v = sm[i];
+        if (v != 0) add128(i < 3 * I ? &tl[i] : &cent[i - 3 * I], v);
+    }
+}
+
+}  // namespace hww

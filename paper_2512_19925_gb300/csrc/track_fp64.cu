@@ -1,0 +1,312 @@
+// track_fp64.cu -- FP64 tracking kernel: one event-loop pass over a set of
+// tracks of one time step (paper Secs. 2-3).
+//
+// Built with contraction off (-fmad=false): every floating-point operation
+// is the single IEEE double operation written, so a track takes exactly the
+// events, splits and roulette outcomes the numerics contract defines.
+//
+// Per event (Eq. HO_transport physics, one speed, isotropic scattering):
+//   flight   d_coll = -log(u_f) / Sigma_t   (as  -log(u_f) * (1/Sigma_t))
+//   edge     d_edge = (x_edge - x) / mu     (as  (x_edge - x) * (1/mu))
+//   census   d_cens = tau, the distance left to t^n
+//   the smallest wins, ties in the order census, crossing, collision;
+//   track-length tallies of w l, w l mu, w l (1/3 - mu^2) (Eq. phi-mc) and the
+//   batch tally w l in batch id mod B;
+//   census: time-crossing tallies w, w mu, w (1/3 - mu^2) (Eq. ct-mc) and the
+//   comb group of the source id;
+//   crossing: next cell, leak through a vacuum side (surface estimators for
+//   the boundary closures P_L, P_R), specular reflection on a reflecting side;
+//   collision: absorption with probability 1 - c, else a new direction;
+//   after a scatter, a cell entry or a reflection the weight window of the
+//   cell applies (Sec. 2): split into ceil(w/ww) equal daughters above the
+//   ceiling, roulette with survival w/ww below the floor.
+// A thread keeps daughter 0 of a split in registers and queues the others
+// as chunk records; after `emax` events a live track is queued as a
+// continuation record, so long histories are rebalanced between launches.
+#include "track_common.cuh"
+
+namespace hww {
+namespace {
+
+struct P64 {
+    double x, mu, inv_mu, tau, w;
+    int cell;
+    uint32_t id;
+    uint64_t lin;
+    uint32_t e;
+};
+
+__device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P64& q, double w,
+                                            uint32_t e, uint32_t jstart, uint32_t jcount,
+                                            unsigned long long slot) {
+    if ((long long)slot >= a.rout.cap) {
+        atomicOr(a.err, ERR_QUEUE_OVERFLOW);
+        return;
+    }
+    a.rout.x[slot] = q.x;
+    a.rout.mu[slot] = q.mu;
+    a.rout.tau[slot] = q.tau;
+    a.rout.w[slot] = w;
+    a.rout.cell[slot] = q.cell;
+    a.rout.id[slot] = q.id;
+    a.rout.lin[slot] = q.lin;
+    a.rout.e[slot] = e;
+    a.rout.jstart[slot] = jstart;
+    a.rout.jcount[slot] = jcount;
+}
+
+__device__ void run_track(const TrackArgs<double>& a, P64 q, long long* s_tl, long long* s_cen,
+                          Counters& cnt, double tscale, double cscale) {
+    const int I = a.I;
+    int evs = 0;
+    for (;;) {
+        if (evs == a.emax) {
+            push_record(a, q, q.w, q.e, 0u, 0u, atomicAdd(a.rout.count, 1ull));
+            return;
+        }
+        if (q.e >= MAX_EVENTS) {
+            atomicOr(a.err, ERR_EVENTS);
+            return;
+        }
+        uint32_t r[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 2u * q.e};
+        philox4x32_10(r, a.k0, a.k1);
+        const double uf = u01(r[0], r[1]);
+        const double uc = u01(r[2], r[3]);
+        const int k = q.cell;
+        const double dcoll = (-hw_log(uf)) * a.inv_sigt[k];
+        const double xl = a.edges[k], xr = a.edges[k + 1];
+        const double xe = (q.mu > 0.0) ? xr : xl;
+        const double dedge = (xe - q.x) * q.inv_mu;
+        const double dcens = q.tau;
+        int ev;
+        double l;
+        if (dcens <= dedge && dcens <= dcoll) {
+            ev = 0;
+            l = dcens;
+        } else if (dedge <= dcoll) {
+            ev = 1;
+            l = dedge;
+        } else {
+            ev = 2;
+            l = dcoll;
+        }
+        // track-length tallies
+        const double wl = q.w * l;
+        const double wlmu = wl * q.mu;
+        const double wlf = wl * (1.0 / 3.0 - q.mu * q.mu);
+        const long long fphi = to_fixed(wl, tscale);
+        sadd(&s_tl[k], fphi);
+        sadd(&s_tl[I + k], to_fixed(wlmu, tscale));
+        sadd(&s_tl[2 * I + k], to_fixed(wlf, tscale));
+        add128(&a.batch[(long long)(q.id % (uint32_t)a.B) * I + k], fphi);
+        cnt.v[ST_SEGMENTS]++;
+        // move
+        if (ev == 1) {
+            q.x = xe;
+        } else {
+            double xn = q.x + q.mu * l;
+            if (xn < xl) xn = xl;
+            if (xn > xr) xn = xr;
+            q.x = xn;
+        }
+        q.tau = (ev == 0) ? 0.0 : q.tau - l;
+        const uint32_t e_ev = q.e;
+        q.e = q.e + 1;
+        ++evs;
+        if (ev == 0) {
+            const double wmu = q.w * q.mu;
+            const double wf = q.w * (1.0 / 3.0 - q.mu * q.mu);
+            sadd(&s_cen[k], to_fixed(q.w, tscale));
+            sadd(&s_cen[I + k], to_fixed(wmu, tscale));
+            sadd(&s_cen[2 * I + k], to_fixed(wf, tscale));
+            const unsigned long long slot = warp_reserve(a.cen.count);
+            if ((long long)slot < a.cen.cap) {
+                a.cen.x[slot] = q.x;
+                a.cen.mu[slot] = q.mu;
+                a.cen.w[slot] = q.w;
+                a.cen.cell[slot] = q.cell;
+                a.cen.id[slot] = q.id;
+                a.cen.lin[slot] = q.lin;
+                atomicAdd(&a.gcnt[q.id], 1u);
+                atomicAdd(&a.gw[q.id], (unsigned long long)to_fixed(q.w, cscale));
+            } else {
+                atomicOr(a.err, ERR_CENSUS_OVERFLOW);
+            }
+            cnt.v[ST_CENSUS]++;
+            cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
+            return;
+        }
+        bool have_r2 = false;
+        uint32_t r2[4];
+        if (ev == 1) {
+            cnt.v[ST_CROSSINGS]++;
+            const int nk = (q.mu > 0.0) ? k + 1 : k - 1;
+            if (nk < 0 || nk >= I) {
+                const int side = (nk < 0) ? 0 : 1;
+                const int bc = side ? a.bc_r : a.bc_l;
+                if (bc == 0) {
+                    const double amu = fabs(q.mu);
+                    const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
+                    const double wi = q.w * ia;
+                    add128(&a.bnd[3 * side + 0], to_fixed(wi, tscale));
+                    add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu), tscale));
+                    add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), tscale));
+                    cnt.v[ST_LEAKED]++;
+                    cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
+                    return;
+                }
+                q.mu = -q.mu;
+                q.inv_mu = -q.inv_mu;
+                cnt.v[ST_REFLECTIONS]++;
+            } else {
+                q.cell = nk;
+            }
+        } else {
+            cnt.v[ST_COLLISIONS]++;
+            if (uc >= a.c[k]) {
+                cnt.v[ST_ABSORBED]++;
+                cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
+                return;
+            }
+            r2[0] = q.id;
+            r2[1] = (uint32_t)q.lin;
+            r2[2] = (uint32_t)(q.lin >> 32);
+            r2[3] = 2u * e_ev + 1u;
+            philox4x32_10(r2, a.k0, a.k1);
+            have_r2 = true;
+            q.mu = 2.0 * u01(r2[0], r2[1]) - 1.0;
+            q.inv_mu = 1.0 / q.mu;
+            cnt.v[ST_SCATTERS]++;
+        }
+        if (a.ww_on) {
+            const int kc = q.cell;
+            const double hi = a.ww_hi[kc];
+            const double lo = a.ww_lo[kc];
+            if (q.w > hi) {
+                const double ctr = a.ww_c[kc];
+                const double ndd = ceil(q.w / ctr);
+                if (ndd > (double)MAX_DAUGHTERS) {
+                    atomicOr(a.err, ERR_DAUGHTERS);
+                    return;
+                }
+                const uint32_t nd = (uint32_t)ndd;
+                const double wd = q.w / (double)nd;
+                cnt.v[ST_SPLIT_EVENTS]++;
+                cnt.v[ST_DAUGHTERS] += nd - 1;
+                const uint32_t nch = (nd - 1 + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+                const unsigned long long base = atomicAdd(a.rout.count, (unsigned long long)nch);
+                for (uint32_t ch = 0; ch < nch; ++ch) {
+                    const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
+                    const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
+                    push_record(a, q, wd, e_ev, j0, jc, base + ch);
+                }
+                q.w = wd;
+                q.lin = lineage_hash(q.lin, e_ev, 0);
+                q.e = 0;
+            } else if (q.w < lo) {
+                if (!have_r2) {
+                    r2[0] = q.id;
+                    r2[1] = (uint32_t)q.lin;
+                    r2[2] = (uint32_t)(q.lin >> 32);
+                    r2[3] = 2u * e_ev + 1u;
+                    philox4x32_10(r2, a.k0, a.k1);
+                }
+                const double ctr = a.ww_c[kc];
+                const double ur = u01(r2[2], r2[3]);
+                const double ps = q.w / ctr;
+                if (ur < ps) {
+                    q.w = ctr;
+                    cnt.v[ST_RSURVIVE]++;
+                } else {
+                    cnt.v[ST_RKILLS]++;
+                    cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
+                    return;
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) track64_kernel(TrackArgs<double> a) {
+    extern __shared__ long long sm[];
+    const int I = a.I;
+    long long* s_tl = sm;
+    long long* s_cen = sm + 3 * I;
+    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    Counters cnt;
+    cnt.zero();
+    const double tscale = a.sd->tscale;
+    const double cscale = a.sd->cscale;
+    const double wbar = a.sd->wbar;
+    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
+    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_use; i += stride) {
+        P64 p;
+        uint32_t jstart = 0, jcount = 0;
+        if (a.from_bank) {
+            p.id = (uint32_t)i;
+            p.lin = 0;
+            p.e = 0;
+            p.tau = a.tau0;
+            p.w = wbar;
+            if (a.birth) {
+                uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
+                philox4x32_10(r, a.k0, a.k1);
+                p.mu = 2.0 * u01(r[0], r[1]) - 1.0;
+                p.x = a.src_x;
+                if (p.x <= a.edges[0] && p.mu < 0.0 && a.bc_l == 1) p.mu = -p.mu;
+                if (p.x >= a.edges[I] && p.mu > 0.0 && a.bc_r == 1) p.mu = -p.mu;
+                p.cell = (p.mu < 0.0) ? a.birth_cell_neg : a.birth_cell_pos;
+            } else {
+                p.x = a.bx[i];
+                p.mu = a.bmu[i];
+                p.cell = a.bcell[i];
+            }
+        } else {
+            p.x = a.rin.x[i];
+            p.mu = a.rin.mu[i];
+            p.tau = a.rin.tau[i];
+            p.w = a.rin.w[i];
+            p.cell = a.rin.cell[i];
+            p.id = a.rin.id[i];
+            p.lin = a.rin.lin[i];
+            p.e = a.rin.e[i];
+            jstart = a.rin.jstart[i];
+            jcount = a.rin.jcount[i];
+        }
+        const uint32_t ntracks = jcount ? jcount : 1u;
+        for (uint32_t t = 0; t < ntracks; ++t) {
+            P64 q = p;
+            if (jcount) {
+                q.lin = lineage_hash(p.lin, p.e, jstart + t);
+                q.e = 0;
+            }
+            q.inv_mu = 1.0 / q.mu;
+            run_track(a, q, s_tl, s_cen, cnt, tscale, cscale);
+        }
+    }
+    __syncthreads();
+    flush_tallies(sm, I, a.tl, a.cent);
+    flush_counters(cnt, a.stats);
+}
+
+}  // namespace
+
+void launch_track_fp64(const TrackArgs<double>& a, int grid, int block, size_t smem, cudaStream_t s) {
+    track64_kernel<<<grid, block, smem, s>>>(a);
+}
+
+int track_smem_optin_fp64(size_t smem) {
+    return (int)cudaFuncSetAttribute(track64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+}
+
+int track_blocks_per_sm_fp64(int block, size_t smem) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, track64_kernel, block, smem);
+    return n;
+}
+
+}  // namespace hww
