@@ -1,0 +1,366 @@
+"""Benchmark: particle-segments per second of the HWW time step on one GB300.
+
+Workload (the plain method at scale): slab [-50, 50] mean free paths,
+Sigma_t = 1, c = 0.9, v = 1, 1000 uniform cells, dt = 0.2, 1e7 particles per
+time step, moving-average filter (k = 3) on the closures, window ratio 5,
+seeds 1..4 (rank r of a multi-GPU run takes seed r + 1: independent problems,
+weak scaling, no collective on the data path).  A bench step is one time
+step of the method: semi-implicit HLOSM + window centers, tracking with
+split/roulette and tallies, closures + fully implicit HLOSM, comb.  The
+headline path tracks in FP32 (positions, directions, flights) with FP64
+weights, tallies, closures and LOSM; the plain FP64 path runs the same steps
+for comparison.  Inputs stay resident in HBM; the per-step working set
+(start bank, census bank, split records) is several hundred MB, larger than
+the 129 MB L2.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "particle-segments/sec and FOM at fixed rel. error, 1 GB300, vs plain FP64 GPU path"
+UNIT = "particle-segments/s"
+WORKLOAD = ("plain_at_scale: slab [-50,50], Sigma_t=1, c=0.9, v=1, 1000 cells, dt=0.2, "
+            "1e7 particles/step, MA filter k=3, window ratio 5 (rho=sqrt 5), eps_min=1e-3")
+# bytes each tracking pass must move: read the start bank (cell, offset,
+# direction) and write the census bank (offset, direction, weight, cell, id,
+# lineage); FP32 tracking stores offsets and directions in 4 bytes, FP64 in 8
+BANK_BYTES = {"fp32": 12, "fp64": 20}
+CENSUS_BYTES = {"fp32": 32, "fp64": 40}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                      "sw_power_cap"), f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def fom_sigma(batch, tau_s):
+    """FOM_sigma = 1 / (tau * mean_i (sigma_i / phi_i)^2) over cells with flux
+    (Eq. FOM_sigma), sigma_i the standard error of the mean of B batch means."""
+    B = batch.shape[0]
+    m = batch.mean(axis=0)
+    s = batch.std(axis=0, ddof=1) / math.sqrt(B)
+    ok = m > 0
+    if not np.any(ok) or tau_s <= 0:
+        return None, None
+    rsd2 = float(np.mean((s[ok] / m[ok]) ** 2))
+    return (1.0 / (tau_s * rsd2) if rsd2 > 0 else None), math.sqrt(rsd2)
+
+
+def run_path(hww, torch, precision, n_particles, seed, warmup, steps, barrier):
+    wl = workloads.plain_at_scale(particles_per_step=n_particles, seed=seed, precision=precision)
+    p = hww.Problem.from_workload(wl)
+    p.set_timing(True)
+    for _ in range(warmup):
+        p.run_step()
+    p.reset_counters()
+    stream = torch.cuda.current_stream()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    segs = 0
+    census = 0
+    for _ in range(steps):
+        s = p.run_step()
+        segs += s["segments"]
+        census += s["census"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    cnt = p.counters()
+    batch = p.get_tallies(hww.BATCH_PHI)
+    p.close()
+    return dict(ms=ms, segments=segs, census=census, counters=cnt, batch=batch, n=n_particles)
+
+
+def run_e2e(hww, torch, precision, n_particles, seed, warmup, steps):
+    """The same steps through the public API with host buffers: each step
+    copies its cross sections from pinned host memory and reads the
+    track-length flux back to the host."""
+    wl = workloads.plain_at_scale(particles_per_step=n_particles, seed=seed, precision=precision)
+    p = hww.Problem.from_workload(wl)
+    st = torch.from_numpy(np.asarray(wl["sigma_t"], dtype=np.float64)).pin_memory().numpy()
+    cc = torch.from_numpy(np.asarray(wl["c"], dtype=np.float64)).pin_memory().numpy()
+    for _ in range(warmup):
+        p.run_step(stats=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    segs = 0
+    for _ in range(steps):
+        p.set_cross_sections(st, cc)
+        s = p.run_step()
+        segs += s["segments"]
+        phi = p.get_tallies(hww.TL_PHI)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    p.close()
+    I = wl["edges"].size - 1
+    return dict(value=segs / dt, h2d=2 * I * 8, d2h=I * 8 + 8 * 20, phi_sum=float(phi.sum()))
+
+
+def cpu_oracle_sample(n_particles, max_steps, budget_s):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    same workload: segments per second over the first steps."""
+    import oracle
+
+    wl = workloads.plain_at_scale(particles_per_step=n_particles, seed=1, precision="fp64")
+    o = oracle.problem_from_workload(wl)
+    segs = 0
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps:
+        s = o.run_step()
+        segs += s["segments"]
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    o.close()
+    return segs / dt, n, dt
+
+
+def main_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    n_ref = args.ref_particles
+    wl = workloads.plain_at_scale(particles_per_step=n_ref, seed=1, precision="fp64")
+    o = oracle.problem_from_workload(wl)
+    for _ in range(args.warmup):
+        o.run_step()
+    t0 = time.perf_counter()
+    segs = 0
+    for _ in range(args.steps):
+        segs += o.run_step()["segments"]
+    dt = time.perf_counter() - t0
+    value = segs / dt
+    sample = "plain_at_scale physics at %d particles/step (1/%d of the workload), steps %d..%d" % (
+        n_ref, 10_000_000 // n_ref, args.warmup + 1, args.warmup + args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "CPU oracle (plain C, FP64)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main(args):
+    ws, rank, local = dist_env()
+    import torch
+
+    import paper_2512_19925_gb300 as hww
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+        def barrier():
+            dist.barrier()
+    else:
+        dist = None
+
+        def barrier():
+            pass
+
+    hww.load()
+    seed = 1 + rank
+    N = args.particles
+    with ClockSampler(local) as clk:
+        fast = run_path(hww, torch, "fp32", N, seed, args.warmup, args.steps, barrier)
+    clocks = clk.summary()
+    base = run_path(hww, torch, "fp64", N, seed, args.warmup, args.steps, barrier) if not args.no_fp64 else None
+
+    def reduce_max(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def reduce_sum(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    ms = reduce_max(fast["ms"])
+    total_segs = reduce_sum(fast["segments"])
+    value = total_segs / (ms * 1e-3)
+    out = {}
+    if base is not None:
+        ms64 = reduce_max(base["ms"])
+        segs64 = reduce_sum(base["segments"])
+        out["fp64_path"] = {"value": segs64 / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps}
+        f32, r32 = fom_sigma(fast["batch"], fast["ms"] * 1e-3 / args.steps)
+        f64, r64 = fom_sigma(base["batch"], base["ms"] * 1e-3 / args.steps)
+        out["fom"] = {"kind": "FOM_sigma (batch variance, B=16) at the last timed step",
+                      "fp32_track": f32, "fp64": f64, "rsd_fp32": r32, "rsd_fp64": r64,
+                      "gain_fp32_over_fp64": (f32 / f64) if (f32 and f64) else None}
+
+    e2e = run_e2e(hww, torch, "fp32", N, seed, args.warmup, args.steps) if not args.no_e2e else None
+    e2e_val = reduce_sum(e2e["value"]) if e2e else None
+
+    # roofline of the dominant kernel (tracking), bank-streaming bytes
+    peak, peak_kind = load_peaks()
+    cnt = fast["counters"]
+    track_ms = cnt["track_ms"]
+    bytes_alg = N * args.steps * BANK_BYTES["fp32"] + fast["census"] * CENSUS_BYTES["fp32"]
+    achieved = (bytes_alg / (track_ms * 1e-3)) / 1e9 if track_ms > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": peak_kind, "kernel": "track32_kernel",
+            "launches": cnt["track_launches"], "kernel_ms_per_step": track_ms / args.steps,
+            "algorithmic_bytes_per_step": bytes_alg / args.steps}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        v, nst, dt = cpu_oracle_sample(args.cpu_particles, 50, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "plain_at_scale physics at %d particles/step, steps 1..%d (%.1f s)" % (
+                   args.cpu_particles, nst, dt)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 tracking / f64 tallies",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles_per_step": N, "precision": "fp32-track",
+                   "seeds": "rank+1", "time_steps": "%d..%d" % (args.warmup + 1, args.warmup + args.steps),
+                   "l2": "working set per step > 129 MB L2 (no flush needed)", "parallelism": "dp%d" % ws},
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"] if e2e else None,
+                "d2h_bytes_per_step": e2e["d2h"] if e2e else None},
+        "gpu_launches": cnt["kernel_launches"],
+    }
+    line.update(out)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--particles", type=int, default=10_000_000)
+    ap.add_argument("--ref-particles", type=int, default=1_000_000)
+    ap.add_argument("--cpu-particles", type=int, default=1_000_000)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args(argv)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.warmup < 3:
+        a.warmup = 3
+    sys.exit(main_reference(a) if a.impl == "reference" else main(a))

@@ -170,6 +170,14 @@ hww_status get_losm_solution(const hww_problem* p, int32_t which, double* phi, d
 hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, int64_t cap,
                     int64_t* n);
 
+/* Replace the start bank of the next step (a checkpoint restart, or a
+ * comparison from a known state): n <= N particles at positions x (inside
+ * their cells), directions mu (nonzero, |mu| <= 1) and cells, each of weight
+ * w_bar > 0, taking source ids 0..n-1.  Host arrays.  Synchronous.  The
+ * next step starts from this bank instead of the pulse or the last comb. */
+hww_status set_bank(hww_problem* p, const double* x, const double* mu, const int32_t* cell, int64_t n,
+                    double w_bar);
+
 /* Copy the census bank of the last step (the particles that reached t^n,
  * before combing): positions, directions, weights, cells, source ids and
  * lineage keys, in the device's storage order.  Host arrays of capacity
@@ -177,6 +185,23 @@ hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, 
  * queries it).  Used to check individual histories. */
 hww_status get_census(const hww_problem* p, double* x, double* mu, double* w, int32_t* cell,
                       uint32_t* id, uint64_t* lin, int64_t cap, int64_t* n);
+
+/* Launch accounting of a problem since creation or the last reset: kernels
+ * the library launched, tracking-kernel launches, and (when timing is on)
+ * the device time of the tracking launches measured with CUDA events on the
+ * problem's stream. */
+typedef struct {
+    int64_t kernel_launches;
+    int64_t track_launches;
+    double track_ms;
+    int64_t steps;
+    int64_t census_capacity, queue_capacity;
+} hww_counters;
+
+/* Turn CUDA-event timing of the tracking launches on (1) or off (0). */
+hww_status hww_set_timing(hww_problem* p, int32_t enable);
+hww_status hww_get_counters(const hww_problem* p, hww_counters* out);
+hww_status hww_reset_counters(hww_problem* p);
 
 /* Release the problem and its device memory (NULL is allowed). */
 void destroy_problem(hww_problem* p);

@@ -194,6 +194,7 @@ struct or_problem {
     /* previous-step track-length flux (for lagged windows) */
     double* prev_tl_phi;
     int has_prev_tl;
+    int bank_loaded; /* the next step starts from a loaded bank */
     /* census bank of the last step */
     or_census* census;
     int64_t ncensus;
@@ -633,6 +634,21 @@ static void source_moments(or_problem* p) {
     p->clo_phi[I + 1] = p->clo_phi[I];
 }
 
+/* Window centers are rounded to 20 significant bits (round half up on the
+ * bit pattern) before use.  Reading: the center only places the window to
+ * within a factor rho, so this changes nothing in the method, but it makes
+ * the windows identical for two algebraically equivalent LOSM solvers whose
+ * solutions differ in the last bits (a survivor of roulette takes the
+ * center as its weight, so the last bits would otherwise reach the
+ * tallies). */
+static double quantize_center(double c) {
+    uint64_t b;
+    memcpy(&b, &c, sizeof b);
+    b = (b + (1ull << 31)) & ~((1ull << 32) - 1ull);
+    memcpy(&c, &b, sizeof c);
+    return c;
+}
+
 /* WW centers, Eq. (ww-center), from a cell vector phi_tilde (length I):
  * phi_tilde clamped at 0 (a CN solution can undershoot ahead of a front),
  * normalised by its maximum, floored by eps, scaled by w_bar
@@ -650,7 +666,7 @@ static void ww_from_flux(or_problem* p, const double* phit) {
         double f = phit[i] > 0.0 ? phit[i] : 0.0;
         double ratio = (mx > 0.0) ? f / mx : 1.0;
         double b = ratio * (1.0 - p->eps) + p->eps;
-        double ctr = scale * b;
+        double ctr = quantize_center(scale * b);
         p->ww_c[i] = ctr;
         p->ww_hi[i] = ctr * p->rho;
         p->ww_lo[i] = ctr / p->rho;
@@ -704,7 +720,7 @@ int or_run_step(or_problem* p, or_stats* st) {
     /* 3. weight windows */
     if (p->has_override) {
         for (int32_t i = 0; i < I; ++i) {
-            double ctr = p->ww_override[i];
+            double ctr = quantize_center(p->ww_override[i]);
             p->ww_c[i] = ctr;
             p->ww_hi[i] = ctr * p->rho;
             p->ww_lo[i] = ctr / p->rho;
@@ -732,7 +748,9 @@ int or_run_step(or_problem* p, or_stats* st) {
 
     pstack stack = {0};
     cbank census = {0};
-    int64_t nstart = (n == 1) ? N : p->nbank;
+    const int birth = (n == 1 && !p->bank_loaded);
+    p->bank_loaded = 0;
+    int64_t nstart = birth ? N : p->nbank;
     s.n_start = nstart;
     for (int64_t k = nstart - 1; k >= 0; --k) {
         or_particle q;
@@ -741,7 +759,7 @@ int or_run_step(or_problem* p, or_stats* st) {
         q.e = 0;
         q.tau = tau0;
         q.w = p->wbar;
-        if (n == 1) {
+        if (birth) {
             uint32_t ctr[4] = {(uint32_t)k, 0u, 0u, 0xFFFFFFFFu}, r[4];
             or_philox4x32_10(ctr, key, r);
             q.mu = 2.0 * or_u01(r[0], r[1]) - 1.0;
@@ -1078,7 +1096,7 @@ int or_get_ww(const or_problem* p, double* center, double* ceil_, double* floor_
 }
 
 int or_set_bank(or_problem* p, const double* x, const double* mu, const int32_t* cell, int64_t n, double wbar) {
-    if (!p || n < 0 || n > p->N || (n > 0 && (!x || !mu || !cell)) || !(wbar > 0.0) || p->n < 1) return E_ARG;
+    if (!p || n < 0 || n > p->N || (n > 0 && (!x || !mu || !cell)) || !(wbar > 0.0)) return E_ARG;
     for (int64_t k = 0; k < n; ++k)
         if (cell[k] < 0 || cell[k] >= p->I || !(mu[k] != 0.0) || !(mu[k] >= -1.0 && mu[k] <= 1.0)) return E_ARG;
     free(p->bx); free(p->bmu); free(p->bcell);
@@ -1091,6 +1109,7 @@ int or_set_bank(or_problem* p, const double* x, const double* mu, const int32_t*
     memcpy(p->bcell, cell, sizeof(int32_t) * n);
     p->nbank = n;
     p->wbar = wbar;
+    p->bank_loaded = 1;
     return 0;
 }
 

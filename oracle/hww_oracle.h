@@ -55,8 +55,8 @@ int or_get_tallies_raw(const or_problem* p, int32_t kind, int64_t* out, int64_t 
 int or_get_losm_solution(const or_problem* p, int32_t which, double* phi, double* J);
 int or_get_ww(const or_problem* p, double* center, double* ceil_, double* floor_);
 int or_get_bank(const or_problem* p, double* x, double* mu, int32_t* cell, int64_t cap, int64_t* n);
-/* replace the start bank of the next step (n > 1 only): n particles with
- * ids 0..n-1, weight w_bar each */
+/* replace the start bank of the next step: n particles with ids 0..n-1,
+ * weight w_bar each (also before the first step, instead of the pulse) */
 int or_set_bank(or_problem* p, const double* x, const double* mu, const int32_t* cell, int64_t n, double wbar);
 int or_get_census(const or_problem* p, double* x, double* mu, double* w, int32_t* cell, uint32_t* id,
                   uint64_t* lin, int64_t cap, int64_t* n);

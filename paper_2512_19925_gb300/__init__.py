@@ -55,6 +55,11 @@ class StepStats(C.Structure):
         ("w_bar_next", C.c_double), ("waves", C.c_int32), ("status", C.c_int32)]
 
 
+class Counters(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("track_launches", C.c_int64), ("track_ms", C.c_double),
+                ("steps", C.c_int64), ("census_capacity", C.c_int64), ("queue_capacity", C.c_int64)]
+
+
 class HWWError(RuntimeError):
     def __init__(self, code, what):
         super().__init__("%s: %s (status %d)" % (what, STATUS.get(code, "unknown"), code))
@@ -65,8 +70,9 @@ _lock = threading.Lock()
 _lib = None
 
 SYMBOLS = ["create_problem", "set_cross_sections", "set_ww_params", "set_ww_centers", "run_step",
-           "get_tallies", "get_tallies_raw", "get_losm_solution", "get_bank", "get_census", "destroy_problem",
-           "hww_status_string", "hww_losm_solve", "hww_philox_block"]
+           "get_tallies", "get_tallies_raw", "get_losm_solution", "get_bank", "set_bank", "get_census", "destroy_problem",
+           "hww_status_string", "hww_losm_solve", "hww_philox_block", "hww_set_timing",
+           "hww_get_counters", "hww_reset_counters"]
 
 
 def library_path() -> str:
@@ -95,8 +101,12 @@ def load(build_if_missing: bool = True):
         L.get_tallies_raw.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), C.c_int64]
         L.get_losm_solution.argtypes = [vp, C.c_int32, vp, vp, C.c_int32]
         L.get_bank.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.POINTER(C.c_int64)]
+        L.set_bank.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.c_double]
         L.get_census.argtypes = [vp, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
                                  C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_int64)]
+        L.hww_set_timing.argtypes = [vp, C.c_int32]
+        L.hww_get_counters.argtypes = [vp, C.POINTER(Counters)]
+        L.hww_reset_counters.argtypes = [vp]
         L.destroy_problem.argtypes = [vp]
         L.destroy_problem.restype = None
         L.hww_status_string.argtypes = [C.c_int32]
@@ -277,6 +287,24 @@ class Problem:
             _check(load().get_bank(self._h, _dp(x), _dp(mu), cell.ctypes.data_as(C.POINTER(C.c_int32)),
                                    m, C.byref(n)), "get_bank")
         return x, mu, cell
+
+    def set_bank(self, x, mu, cell, w_bar):
+        """Start the next step from this bank (ids 0..n-1, weight w_bar each)."""
+        x, mu = _f64(x), _f64(mu)
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        _check(load().set_bank(self._h, _dp(x), _dp(mu), cell.ctypes.data_as(C.POINTER(C.c_int32)), x.size,
+                               float(w_bar)), "set_bank")
+
+    def set_timing(self, enable=True):
+        _check(load().hww_set_timing(self._h, 1 if enable else 0), "hww_set_timing")
+
+    def counters(self):
+        c = Counters()
+        _check(load().hww_get_counters(self._h, C.byref(c)), "hww_get_counters")
+        return {f: getattr(c, f) for f, _ in Counters._fields_}
+
+    def reset_counters(self):
+        _check(load().hww_reset_counters(self._h), "hww_reset_counters")
 
     def get_census(self):
         """Census bank of the last step as a dict of arrays (storage order)."""

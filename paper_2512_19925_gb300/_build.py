@@ -25,6 +25,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 UNITS = {
     "api.cu": ["-fmad=false"],
     "step.cu": ["-fmad=false"],
+    "losm.cu": ["-fmad=false"],
     "track_fp64.cu": ["-fmad=false"],
     "track_fp32.cu": [],
 }

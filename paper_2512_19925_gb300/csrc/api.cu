@@ -9,12 +9,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
 
 #include "../../include/hww.h"
 #include "hww_internal.cuh"
+#include "losm_kernels.cuh"
 #include "step_kernels.cuh"
 
 using namespace hww;
@@ -24,6 +26,7 @@ namespace {
 constexpr int TRACK_BLOCK = 256;
 constexpr int MAX_CELLS = 4000;
 constexpr int MAX_WAVES = 100000;
+constexpr int MAX_REGROW = 12;
 
 template <class Real>
 struct Banks {
@@ -45,7 +48,8 @@ struct hww_problem {
     int nsm = 0;
     long long cen_cap = 0, q_cap = 0;
     std::vector<double> edges, dx;
-    std::vector<void*> allocs;
+    std::vector<void*> allocs;       // freed at destroy
+    std::vector<void*> bank_allocs;  // census bank, record queues, comb members: regrown on overflow
     // mesh and cross sections
     double *d_edges = nullptr, *d_dx = nullptr, *d_sigt = nullptr, *d_inv_sigt = nullptr, *d_c = nullptr,
            *d_siga = nullptr;
@@ -68,15 +72,20 @@ struct hww_problem {
     unsigned long long *goff = nullptr, *goff_w = nullptr, *tile_c = nullptr, *tile_w = nullptr;
     uint32_t* member = nullptr;
     // closures and LOSM
-    double *ophi = nullptr, *oJ = nullptr, *oF = nullptr, *oP = nullptr;
-    double *nphi = nullptr, *nJ = nullptr, *nF = nullptr, *nP = nullptr, *cJ = nullptr, *tmp = nullptr;
+    // two closure sets (phi I+2, J I+1, F I+2, P 2): `cur` holds the
+    // initial conditions of the next step, the other is built at t^n
+    double *cl_phi[2] = {}, *cl_J[2] = {}, *cl_F[2] = {}, *cl_P[2] = {};
+    int cur = 0;
+    double *rphi = nullptr, *rJ = nullptr, *rF = nullptr, *mx = nullptr;
     double *prev_tl = nullptr, *semi_phi = nullptr, *semi_J = nullptr, *full_phi = nullptr,
-           *full_J = nullptr, *work = nullptr, *norm = nullptr;
+           *full_J = nullptr, *norm = nullptr;
+    LosmMat mat{};
+    LosmWork work{};
     StepDev* sd = nullptr;
     unsigned* err = nullptr;
     unsigned long long* h_count = nullptr;  // pinned
     // host state
-    int xs_set = 0, ww_set = 0, has_override = 0, has_prev_tl = 0;
+    int xs_set = 0, ww_set = 0, has_override = 0, has_prev_tl = 0, bank_loaded = 0;
     double rho = 1.0, eps = 1e-3;
     int mode = 0, scaling = 0;
     long long steps = 0;
@@ -84,6 +93,12 @@ struct hww_problem {
     int track_grid = 0;
     size_t track_smem = 0;
     int last_waves = 0;
+    long long q_peak = 0;  // largest record count a wave produced in the last pass
+    // launch accounting
+    int timing = 0;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    long long kernel_launches = 0, track_launches = 0;
+    double track_ms = 0.0;
 };
 
 namespace {
@@ -101,7 +116,7 @@ hww_status cuda_status(cudaError_t e) {
     } while (0)
 
 template <class T>
-hww_status dalloc(hww_problem* p, T** ptr, size_t count) {
+hww_status dalloc(hww_problem* p, T** ptr, size_t count, bool bank = false) {
     void* v = nullptr;
     const size_t bytes = (count ? count : 1) * sizeof(T);
     cudaError_t e = cudaMallocAsync(&v, bytes, p->stream);
@@ -109,7 +124,7 @@ hww_status dalloc(hww_problem* p, T** ptr, size_t count) {
         *ptr = nullptr;
         return cuda_status(e);
     }
-    p->allocs.push_back(v);
+    (bank ? p->bank_allocs : p->allocs).push_back(v);
     *ptr = (T*)v;
     return HWW_OK;
 }
@@ -159,26 +174,54 @@ void source_moments(const hww_problem* p, std::vector<double>& phi) {
 }
 
 template <class Real>
+hww_status alloc_start_bank(hww_problem* p, Banks<Real>& b) {
+    hww_status s;
+    const long long N = p->N;
+    if ((s = dalloc(p, &b.bx, N)) || (s = dalloc(p, &b.bmu, N)) || (s = dalloc(p, &b.bcell, N))) return s;
+    return HWW_OK;
+}
+
+// census bank, both record queues and the comb member list, sized by the
+// current capacities
+template <class Real>
 hww_status alloc_banks(hww_problem* p, Banks<Real>& b) {
     hww_status s;
-    const long long N = p->N, C = p->cen_cap, Q = p->q_cap;
-    if ((s = dalloc(p, &b.bx, N)) || (s = dalloc(p, &b.bmu, N)) || (s = dalloc(p, &b.bcell, N))) return s;
-    if ((s = dalloc(p, &b.cen.x, C)) || (s = dalloc(p, &b.cen.mu, C)) || (s = dalloc(p, &b.cen.w, C)) ||
-        (s = dalloc(p, &b.cen.cell, C)) || (s = dalloc(p, &b.cen.id, C)) || (s = dalloc(p, &b.cen.lin, C)))
+    const long long C = p->cen_cap, Q = p->q_cap;
+    if ((s = dalloc(p, &b.cen.x, C, true)) || (s = dalloc(p, &b.cen.mu, C, true)) ||
+        (s = dalloc(p, &b.cen.w, C, true)) || (s = dalloc(p, &b.cen.cell, C, true)) ||
+        (s = dalloc(p, &b.cen.id, C, true)) || (s = dalloc(p, &b.cen.lin, C, true)) ||
+        (s = dalloc(p, &p->member, C, true)))
         return s;
     b.cen.cap = C;
     b.cen.count = p->counts + 0;
     for (int k = 0; k < 2; ++k) {
         RecQ<Real>& q = b.q[k];
-        if ((s = dalloc(p, &q.x, Q)) || (s = dalloc(p, &q.mu, Q)) || (s = dalloc(p, &q.tau, Q)) ||
-            (s = dalloc(p, &q.w, Q)) || (s = dalloc(p, &q.cell, Q)) || (s = dalloc(p, &q.id, Q)) ||
-            (s = dalloc(p, &q.lin, Q)) || (s = dalloc(p, &q.e, Q)) || (s = dalloc(p, &q.jstart, Q)) ||
-            (s = dalloc(p, &q.jcount, Q)))
+        if ((s = dalloc(p, &q.x, Q, true)) || (s = dalloc(p, &q.mu, Q, true)) || (s = dalloc(p, &q.tau, Q, true)) ||
+            (s = dalloc(p, &q.w, Q, true)) || (s = dalloc(p, &q.cell, Q, true)) || (s = dalloc(p, &q.id, Q, true)) ||
+            (s = dalloc(p, &q.lin, Q, true)) || (s = dalloc(p, &q.e, Q, true)) ||
+            (s = dalloc(p, &q.jstart, Q, true)) || (s = dalloc(p, &q.jcount, Q, true)))
             return s;
         q.cap = Q;
         q.count = p->counts + 1 + k;
     }
     return HWW_OK;
+}
+
+void free_banks(hww_problem* p) {
+    for (void* v : p->bank_allocs) cudaFreeAsync(v, p->stream);
+    p->bank_allocs.clear();
+}
+
+// grow the census and queue capacities to at least twice their size and at
+// least 5/4 of the demand the failed pass saw (the start bank is kept)
+hww_status regrow_banks(hww_problem* p, long long cen_need, long long q_need) {
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    free_banks(p);
+    p->cen_cap = std::max(2 * p->cen_cap, cen_need + cen_need / 4);
+    p->q_cap = std::max(2 * p->q_cap, q_need + q_need / 4);
+    hww_status s = p->fp32 ? alloc_banks(p, p->b32) : alloc_banks(p, p->b64);
+    if (s == HWW_OK) HWW_CK(cudaStreamSynchronize(p->stream));
+    return s;
 }
 
 template <class Real>
@@ -221,10 +264,25 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b, uint32_t k
 }
 
 void launch_track(hww_problem* p, const TrackArgs<double>& a) {
+    if (p->timing) cudaEventRecord(p->ev_a, p->stream);
     launch_track_fp64(a, p->track_grid, TRACK_BLOCK, p->track_smem, p->stream);
+    if (p->timing) cudaEventRecord(p->ev_b, p->stream);
+    ++p->kernel_launches;
+    ++p->track_launches;
 }
 void launch_track(hww_problem* p, const TrackArgs<float>& a) {
+    if (p->timing) cudaEventRecord(p->ev_a, p->stream);
     launch_track_fp32(a, p->track_grid, TRACK_BLOCK, p->track_smem, p->stream);
+    if (p->timing) cudaEventRecord(p->ev_b, p->stream);
+    ++p->kernel_launches;
+    ++p->track_launches;
+}
+
+// after a synchronize: add the last tracking launch's device time
+void account_track_time(hww_problem* p) {
+    if (!p->timing) return;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev_a, p->ev_b) == cudaSuccess) p->track_ms += ms;
 }
 
 template <class Real>
@@ -241,6 +299,8 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b, uint32_t k0, uint32_t k1,
         HWW_CK(cudaMemcpyAsync(p->h_count, b.q[cur].count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                p->stream));
         HWW_CK(cudaStreamSynchronize(p->stream));
+        account_track_time(p);
+        p->q_peak = std::max(p->q_peak, (long long)*p->h_count);
         if (*p->h_count == 0) break;
         if (waves >= MAX_WAVES) {
             p->last_waves = waves;
@@ -273,6 +333,7 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     s.out_w = p->goff_w;
     launch_group_scan(s, p->stream);
     HWW_CK(cudaGetLastError());
+    p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
     CombArgs<Real> c{};
     c.sd = p->sd;
     c.N = p->N;
@@ -296,27 +357,8 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     c.err = p->err;
     launch_comb(c, p->nsm * 8, p->stream);
     HWW_CK(cudaGetLastError());
+    p->kernel_launches += 3;
     return HWW_OK;
-}
-
-LosmIn losm_in(const hww_problem* p) {
-    LosmIn in{};
-    in.I = p->I;
-    in.dx = p->d_dx;
-    in.sigt = p->d_sigt;
-    in.siga = p->d_siga;
-    in.v = p->d.v;
-    in.dt = p->d.dt;
-    in.theta = p->d.theta;
-    in.bc_l = p->d.bc_left;
-    in.bc_r = p->d.bc_right;
-    in.phi_old = p->ophi;
-    in.J_old = p->oJ;
-    in.F_old = p->oF;
-    in.F_new = p->oF;
-    in.q_old = nullptr;
-    in.q_new = nullptr;
-    return in;
 }
 
 hww_status err_to_status(unsigned e) {
@@ -360,9 +402,12 @@ __global__ void bank_to_x_kernel(const Real* bx, const int32_t* bcell, const dou
                                  double* out) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        if (sizeof(Real) == sizeof(float))
-            out[i] = edges[bcell[i]] + (double)bx[i];
-        else
+        if (sizeof(Real) == sizeof(float)) {
+            // offset from the cell's left edge; the FP32 cell width may round
+            // above the FP64 one, so the position is clamped into the cell
+            const int c = bcell[i];
+            out[i] = fmin(fmax(edges[c] + (double)bx[i], edges[c]), edges[c + 1]);
+        } else
             out[i] = (double)bx[i];
     }
 }
@@ -404,8 +449,11 @@ void destroy_problem(hww_problem* p) {
     if (!p) return;
     cudaSetDevice(p->device);
     for (void* v : p->allocs) cudaFreeAsync(v, p->stream);
+    free_banks(p);
     cudaStreamSynchronize(p->stream);
     if (p->h_count) cudaFreeHost(p->h_count);
+    if (p->ev_a) cudaEventDestroy(p->ev_a);
+    if (p->ev_b) cudaEventDestroy(p->ev_b);
     delete p;
 }
 
@@ -460,13 +508,21 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         (s = dalloc(p, &p->ww_c, I)) || (s = dalloc(p, &p->ww_hi, I)) || (s = dalloc(p, &p->ww_lo, I)) ||
         (s = dalloc(p, &p->ww_override, I)) || (s = dalloc(p, &p->goff, p->N + 1)) ||
         (s = dalloc(p, &p->goff_w, p->N + 1)) || (s = dalloc(p, &p->tile_c, ntiles + 1)) ||
-        (s = dalloc(p, &p->tile_w, ntiles + 1)) || (s = dalloc(p, &p->member, p->cen_cap)) ||
-        (s = dalloc(p, &p->ophi, I + 2)) || (s = dalloc(p, &p->oJ, I + 1)) || (s = dalloc(p, &p->oF, I + 2)) ||
-        (s = dalloc(p, &p->oP, 2)) || (s = dalloc(p, &p->nphi, I + 2)) || (s = dalloc(p, &p->nJ, I + 1)) ||
-        (s = dalloc(p, &p->nF, I + 2)) || (s = dalloc(p, &p->nP, 2)) || (s = dalloc(p, &p->cJ, I)) ||
-        (s = dalloc(p, &p->tmp, I + 1)) || (s = dalloc(p, &p->prev_tl, I)) || (s = dalloc(p, &p->semi_phi, I + 2)) ||
+        (s = dalloc(p, &p->tile_w, ntiles + 1)) ||
+        (s = dalloc(p, &p->cl_phi[0], I + 2)) || (s = dalloc(p, &p->cl_J[0], I + 1)) ||
+        (s = dalloc(p, &p->cl_F[0], I + 2)) || (s = dalloc(p, &p->cl_P[0], 2)) ||
+        (s = dalloc(p, &p->cl_phi[1], I + 2)) || (s = dalloc(p, &p->cl_J[1], I + 1)) ||
+        (s = dalloc(p, &p->cl_F[1], I + 2)) || (s = dalloc(p, &p->cl_P[1], 2)) || (s = dalloc(p, &p->rphi, I)) ||
+        (s = dalloc(p, &p->rJ, I + 1)) || (s = dalloc(p, &p->rF, I)) || (s = dalloc(p, &p->mx, 1)) ||
+        (s = dalloc(p, &p->prev_tl, I)) || (s = dalloc(p, &p->semi_phi, I + 2)) ||
         (s = dalloc(p, &p->semi_J, I + 1)) || (s = dalloc(p, &p->full_phi, I + 2)) ||
-        (s = dalloc(p, &p->full_J, I + 1)) || (s = dalloc(p, &p->work, 4 * (I + 2))) ||
+        (s = dalloc(p, &p->full_J, I + 1)) || (s = dalloc(p, &p->work.u, I + 2)) ||
+        (s = dalloc(p, &p->work.mom, I + 1)) || (s = dalloc(p, &p->work.y, I + 2)) ||
+        (s = dalloc(p, &p->mat.eJ, I + 1)) || (s = dalloc(p, &p->mat.eS, I + 1)) ||
+        (s = dalloc(p, &p->mat.invd, I + 1)) || (s = dalloc(p, &p->mat.g, I + 1)) ||
+        (s = dalloc(p, &p->mat.cP, I)) || (s = dalloc(p, &p->mat.cA, I)) || (s = dalloc(p, &p->mat.cB, I)) ||
+        (s = dalloc(p, &p->mat.inv_den, I + 2)) || (s = dalloc(p, &p->mat.vf, I + 2)) ||
+        (s = dalloc(p, &p->mat.cp, I + 2)) ||
         (s = dalloc(p, &p->norm, (size_t)B * I + 6 * (size_t)I + 8)) || (s = dalloc(p, &p->sd, 1)) ||
         (s = dalloc(p, &p->err, 1))) {
         destroy_problem(p);
@@ -482,7 +538,8 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     p->gw = (unsigned long long*)p->grp;
     p->gcnt = (uint32_t*)(p->gw + p->N);
     p->gcur = p->gcnt + p->N;
-    s = p->fp32 ? alloc_banks(p, p->b32) : alloc_banks(p, p->b64);
+    s = p->fp32 ? alloc_start_bank(p, p->b32) : alloc_start_bank(p, p->b64);
+    if (s == HWW_OK) s = p->fp32 ? alloc_banks(p, p->b32) : alloc_banks(p, p->b64);
     if (s) {
         destroy_problem(p);
         return s;
@@ -508,10 +565,14 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     up(p->d_edges, p->edges.data(), sizeof(double) * (I + 1));
     up(p->d_dx, p->dx.data(), sizeof(double) * I);
     up(p->d_dxf, dxf.data(), sizeof(float) * I);
-    up(p->ophi, phi0.data(), sizeof(double) * (I + 2));
-    up(p->oJ, zeros.data(), sizeof(double) * (I + 1));
-    up(p->oF, zeros.data(), sizeof(double) * (I + 2));
-    up(p->oP, zeros.data(), sizeof(double) * 2);
+    up(p->cl_phi[0], phi0.data(), sizeof(double) * (I + 2));
+    up(p->cl_J[0], zeros.data(), sizeof(double) * (I + 1));
+    up(p->cl_F[0], zeros.data(), sizeof(double) * (I + 2));
+    up(p->cl_P[0], zeros.data(), sizeof(double) * 2);
+    p->mat.I = I;
+    p->mat.theta = d->theta;
+    p->mat.bc_l = d->bc_left;
+    p->mat.bc_r = d->bc_right;
     up(p->sd, &sd, sizeof(StepDev));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
@@ -559,7 +620,15 @@ hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const doubl
     HWW_CK(cudaMemcpyAsync(p->d_c, cc.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_siga, sa.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_region, reg.data(), sizeof(int32_t) * I, cudaMemcpyHostToDevice, p->stream));
+    // the LOSM matrix depends on the cross sections: refactor it
+    launch_losm_setup(p->mat, p->d_dx, p->d_sigt, p->d_siga, p->d.v, p->d.dt, p->d.theta, p->d.bc_left,
+                      p->d.bc_right, p->err, p->stream);
+    HWW_CK(cudaGetLastError());
+    p->kernel_launches += 2;
+    unsigned e = 0;
+    HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
     HWW_CK(cudaStreamSynchronize(p->stream));
+    if (e & ERR_LOSM) return HWW_ERR_NUMERIC;
     p->xs_set = 1;
     return HWW_OK;
 }
@@ -594,77 +663,94 @@ hww_status run_step(hww_problem* p, hww_step_stats* st) {
     const long long n = p->steps + 1;
     const uint32_t k0 = (uint32_t)p->d.seed;
     const uint32_t k1 = (uint32_t)(p->d.seed >> 32) ^ (uint32_t)n;
-    HWW_CK(cudaMemsetAsync(p->acc, 0, p->acc_bytes, p->stream));
-    HWW_CK(cudaMemsetAsync(p->grp, 0, p->grp_bytes, p->stream));
-
-    PreArgs pa{};
-    pa.sd = p->sd;
-    pa.nbits = bit_length(p->N);
-    pa.k0 = k0;
-    pa.k1 = k1;
-    pa.losm = losm_in(p);
-    pa.P_old = p->oP;
-    pa.semi_phi = p->semi_phi;
-    pa.semi_J = p->semi_J;
-    pa.w_d = p->work;
-    pa.w_m = p->work + (p->I + 2);
-    pa.w_c = p->work + 2 * (p->I + 2);
-    pa.w_r = p->work + 3 * (p->I + 2);
-    pa.err = p->err;
-    pa.ww_source = p->has_override ? 3
-                   : p->mode == HWW_MODE_HWW ? 1
-                   : (p->mode == HWW_MODE_LWW && p->has_prev_tl) ? 2
-                                                                 : 0;
-    pa.scaling = p->scaling;
-    pa.eps = p->eps;
-    pa.rho = p->rho;
-    pa.prev_tl = p->prev_tl;
-    pa.ww_override = p->ww_override;
-    pa.ww_c = p->ww_c;
-    pa.ww_hi = p->ww_hi;
-    pa.ww_lo = p->ww_lo;
-    pa.stats = p->stats;
-    launch_prestep(pa, p->stream);
-    HWW_CK(cudaGetLastError());
-
-    hww_status s = p->fp32 ? track_waves(p, p->b32, k0, k1, n == 1) : track_waves(p, p->b64, k0, k1, n == 1);
+    const int c0 = p->cur, c1 = 1 - p->cur;
+    // semi-implicit HLOSM with the lagged closure (Eqs. losm-0,
+    // losm-1-semi, losm-disc-bc-semi), then the window centers
+    LosmRhsIn semi{};
+    semi.phi_old = p->cl_phi[c0];
+    semi.J_old = p->cl_J[c0];
+    semi.F_old = p->cl_F[c0];
+    semi.F_new = p->cl_F[c0];
+    semi.P_new = p->cl_P[c0];
+    WwArgs wa{};
+    wa.I = p->I;
+    wa.source = p->has_override ? 3
+                : p->mode == HWW_MODE_HWW ? 1
+                : (p->mode == HWW_MODE_LWW && p->has_prev_tl) ? 2
+                                                              : 0;
+    wa.scaling = p->scaling;
+    wa.eps = p->eps;
+    wa.rho = p->rho;
+    wa.sd = p->sd;
+    wa.phit = (wa.source == 2) ? p->prev_tl : p->semi_phi + 1;
+    wa.mx_ptr = p->mx;
+    wa.override_c = p->ww_override;
+    wa.ww_c = p->ww_c;
+    wa.ww_hi = p->ww_hi;
+    wa.ww_lo = p->ww_lo;
+    // Tracking.  A census or queue overflow leaves the start bank and the
+    // closure vectors untouched, so the step is replayed from the start with
+    // doubled capacities; the replay is bit-identical to a run that had the
+    // room from the beginning.
+    hww_status s = HWW_OK;
+    for (int attempt = 0;; ++attempt) {
+        HWW_CK(cudaMemsetAsync(p->acc, 0, p->acc_bytes, p->stream));
+        HWW_CK(cudaMemsetAsync(p->grp, 0, p->grp_bytes, p->stream));
+        launch_step_scalars(p->sd, bit_length(p->N), k0, k1, p->stats, p->stream);
+        p->kernel_launches += 1 + launch_losm_solve(p->mat, semi, p->work, p->semi_phi, p->semi_J, p->mx, p->stream);
+        if (wa.source) p->kernel_launches += launch_ww_centers(wa, p->stream);
+        HWW_CK(cudaGetLastError());
+        p->q_peak = 0;
+        const int birth = (n == 1 && !p->bank_loaded);
+        s = p->fp32 ? track_waves(p, p->b32, k0, k1, birth) : track_waves(p, p->b64, k0, k1, birth);
+        if (s) break;
+        unsigned e = 0;
+        unsigned long long ncen = 0;
+        HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaMemcpyAsync(&ncen, p->counts, sizeof(ncen), cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaStreamSynchronize(p->stream));
+        if (!(e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW)) || attempt >= MAX_REGROW) break;
+        s = regrow_banks(p, (long long)ncen, p->q_peak);
+        if (s) break;
+        const unsigned keep = e & ~(unsigned)(ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW);
+        HWW_CK(cudaMemcpyAsync(p->err, &keep, sizeof(unsigned), cudaMemcpyHostToDevice, p->stream));
+        HWW_CK(cudaStreamSynchronize(p->stream));
+        // the comb member list moved with the census bank
+    }
     p->has_override = 0;
+    p->bank_loaded = 0;
     if (s) return s;
 
-    PostArgs po{};
-    po.I = p->I;
-    po.sd = p->sd;
-    po.v = p->d.v;
-    po.dt = p->d.dt;
-    po.N = p->N;
-    po.bc_l = p->d.bc_left;
-    po.bc_r = p->d.bc_right;
-    po.filter_k = p->d.filter == HWW_FILTER_MA ? p->d.filter_k : 0;
-    po.dx = p->d_dx;
-    po.cent = p->cent;
-    po.tl = p->tl;
-    po.bnd = p->bnd;
-    po.nphi = p->nphi;
-    po.nJ = p->nJ;
-    po.nF = p->nF;
-    po.nP = p->nP;
-    po.cJ = p->cJ;
-    po.tmp = p->tmp;
-    po.prev_tl = p->prev_tl;
-    po.ophi = p->ophi;
-    po.oJ = p->oJ;
-    po.oF = p->oF;
-    po.oP = p->oP;
-    po.losm = losm_in(p);
-    po.full_phi = p->full_phi;
-    po.full_J = p->full_J;
-    po.w_d = pa.w_d;
-    po.w_m = pa.w_m;
-    po.w_c = pa.w_c;
-    po.w_r = pa.w_r;
-    po.err = p->err;
-    launch_poststep(po, p->stream);
+    // closures and initial conditions at t^n, then the fully implicit HLOSM
+    // (Eqs. losm-0, losm-1, losm-disc-bc)
+    ClosureArgs ca{};
+    ca.I = p->I;
+    ca.sd = p->sd;
+    ca.v = p->d.v;
+    ca.dt = p->d.dt;
+    ca.N = p->N;
+    ca.bc_l = p->d.bc_left;
+    ca.bc_r = p->d.bc_right;
+    ca.filter_k = p->d.filter == HWW_FILTER_MA ? p->d.filter_k : 0;
+    ca.dx = p->d_dx;
+    ca.cent = p->cent;
+    ca.tl = p->tl;
+    ca.bnd = p->bnd;
+    ca.rphi = p->rphi;
+    ca.rJ = p->rJ;
+    ca.rF = p->rF;
+    ca.nphi = p->cl_phi[c1];
+    ca.nJ = p->cl_J[c1];
+    ca.nF = p->cl_F[c1];
+    ca.nP = p->cl_P[c1];
+    ca.prev_tl = p->prev_tl;
+    p->kernel_launches += launch_closures(ca, p->stream);
+    LosmRhsIn full = semi;
+    full.F_new = p->cl_F[c1];
+    full.P_new = p->cl_P[c1];
+    p->kernel_launches += launch_losm_solve(p->mat, full, p->work, p->full_phi, p->full_J, nullptr, p->stream);
     HWW_CK(cudaGetLastError());
+    p->cur = c1;
 
     s = p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);
     if (s) return s;
@@ -722,9 +808,9 @@ hww_status get_tallies(const hww_problem* p, int32_t kind, double* out, int64_t 
     case HWW_BATCH_PHI: src = p->batch; len = B * I; break;
     case HWW_BOUNDARY: src = p->bnd; len = 6; break;
     case HWW_WW_CENTER: return n < I ? HWW_ERR_ARG : copy_out(p, out, p->ww_c, I, on_device);
-    case HWW_CLOSURE_PHI: return n < I + 2 ? HWW_ERR_ARG : copy_out(p, out, p->ophi, I + 2, on_device);
-    case HWW_CLOSURE_J: return n < I + 1 ? HWW_ERR_ARG : copy_out(p, out, p->oJ, I + 1, on_device);
-    case HWW_CLOSURE_F: return n < I + 2 ? HWW_ERR_ARG : copy_out(p, out, p->oF, I + 2, on_device);
+    case HWW_CLOSURE_PHI: return n < I + 2 ? HWW_ERR_ARG : copy_out(p, out, p->cl_phi[p->cur], I + 2, on_device);
+    case HWW_CLOSURE_J: return n < I + 1 ? HWW_ERR_ARG : copy_out(p, out, p->cl_J[p->cur], I + 1, on_device);
+    case HWW_CLOSURE_F: return n < I + 2 ? HWW_ERR_ARG : copy_out(p, out, p->cl_F[p->cur], I + 2, on_device);
     }
     if (n < len) return HWW_ERR_ARG;
     normalize_kernel<<<(len + 255) / 256, 256, 0, p->stream>>>(kind, src, len, I, B, p->N, p->d_dx, p->d.v,
@@ -801,6 +887,76 @@ hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, 
     return cuda_status(e);
 }
 
+hww_status hww_set_timing(hww_problem* p, int32_t enable) {
+    if (!p || enable < 0 || enable > 1) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(p->device));
+    if (enable && !p->ev_a) {
+        HWW_CK(cudaEventCreate(&p->ev_a));
+        HWW_CK(cudaEventCreate(&p->ev_b));
+    }
+    p->timing = enable;
+    return HWW_OK;
+}
+
+hww_status hww_get_counters(const hww_problem* p, hww_counters* out) {
+    if (!p || !out) return HWW_ERR_ARG;
+    out->kernel_launches = p->kernel_launches;
+    out->track_launches = p->track_launches;
+    out->track_ms = p->track_ms;
+    out->steps = p->steps;
+    out->census_capacity = p->cen_cap;
+    out->queue_capacity = p->q_cap;
+    return HWW_OK;
+}
+
+hww_status hww_reset_counters(hww_problem* p) {
+    if (!p) return HWW_ERR_ARG;
+    p->kernel_launches = 0;
+    p->track_launches = 0;
+    p->track_ms = 0.0;
+    return HWW_OK;
+}
+
+hww_status set_bank(hww_problem* p, const double* x, const double* mu, const int32_t* cell, int64_t n,
+                    double w_bar) {
+    if (!p || n < 0 || n > p->N || (n > 0 && (!x || !mu || !cell)) || !(w_bar > 0.0) || !std::isfinite(w_bar))
+        return HWW_ERR_ARG;
+    for (int64_t k = 0; k < n; ++k) {
+        const int c = cell[k];
+        if (c < 0 || c >= p->I || !(mu[k] != 0.0) || !(mu[k] >= -1.0 && mu[k] <= 1.0) ||
+            !(x[k] >= p->edges[c] && x[k] <= p->edges[c + 1]))
+            return HWW_ERR_ARG;
+    }
+    HWW_CK(cudaSetDevice(p->device));
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        if (p->fp32) {
+            std::vector<float> xo(n), mf(n);
+            for (int64_t k = 0; k < n; ++k) {
+                xo[k] = (float)(x[k] - p->edges[cell[k]]);
+                mf[k] = (float)mu[k];
+            }
+            e = cudaMemcpy(p->b32.bx, xo.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(p->b32.bmu, mf.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(p->b32.bcell, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemcpy(p->b64.bx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(p->b64.bmu, mu, sizeof(double) * n, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(p->b64.bcell, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+        }
+    }
+    StepDev sdh;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    sdh.nbank = (unsigned long long)n;
+    sdh.wbar = w_bar;
+    HWW_CK(cudaMemcpyAsync(p->sd, &sdh, sizeof(StepDev), cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    p->bank_loaded = 1;
+    return HWW_OK;
+}
+
 hww_status get_census(const hww_problem* p, double* x, double* mu, double* w, int32_t* cell, uint32_t* id,
                       uint64_t* lin, int64_t cap, int64_t* n) {
     if (!p || !n) return HWW_ERR_ARG;
@@ -861,24 +1017,48 @@ hww_status hww_losm_solve(int32_t I, const double* dx, const double* sigma_t, co
         return HWW_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return HWW_ERR_NO_DEVICE;
-    // one device buffer: 5 cell arrays, 4 (I+2) vectors, 3 (I+1) vectors, work, err
+    // one device buffer: cell arrays, vectors, the matrix, work and the error word
     const size_t n2 = I + 2, n1 = I + 1;
-    const size_t total = 5 * (size_t)I + 4 * n2 + 2 * n1 + 4 * n2 + 1;
+    const size_t total = 5 * (size_t)I + 4 * n2 + 2 * n1 + (4 * n1 + 3 * (size_t)I + 3 * n2) + (2 * n2 + n1) + 1;
     double* buf = nullptr;
     HWW_CK(cudaMalloc(&buf, total * sizeof(double)));
-    double* d_dx = buf;
-    double* d_st = d_dx + I;
-    double* d_sa = d_st + I;
-    double* d_qo = d_sa + I;
-    double* d_qn = d_qo + I;
-    double* d_po = d_qn + I;
-    double* d_Fo = d_po + n2;
-    double* d_Fn = d_Fo + n2;
-    double* d_pn = d_Fn + n2;
-    double* d_Jo = d_pn + n2;
-    double* d_Jn = d_Jo + n1;
-    double* d_w = d_Jn + n1;
-    unsigned* d_err = (unsigned*)(d_w + 4 * n2);
+    double* q = buf;
+    auto take = [&](size_t k) {
+        double* r = q;
+        q += k;
+        return r;
+    };
+    double* d_dx = take(I);
+    double* d_st = take(I);
+    double* d_sa = take(I);
+    double* d_qo = take(I);
+    double* d_qn = take(I);
+    double* d_po = take(n2);
+    double* d_Fo = take(n2);
+    double* d_Fn = take(n2);
+    double* d_pn = take(n2);
+    double* d_Jo = take(n1);
+    double* d_Jn = take(n1);
+    LosmMat m{};
+    m.I = I;
+    m.theta = theta;
+    m.bc_l = bc_left;
+    m.bc_r = bc_right;
+    m.eJ = take(n1);
+    m.eS = take(n1);
+    m.invd = take(n1);
+    m.g = take(n1);
+    m.cP = take(I);
+    m.cA = take(I);
+    m.cB = take(I);
+    m.inv_den = take(n2);
+    m.vf = take(n2);
+    m.cp = take(n2);
+    LosmWork w{};
+    w.u = take(n2);
+    w.y = take(n2);
+    w.mom = take(n1);
+    unsigned* d_err = (unsigned*)take(1);
     cudaError_t e = cudaSuccess;
     auto up = [&](double* dst, const double* src, size_t cnt) {
         if (e == cudaSuccess && src) e = cudaMemcpy(dst, src, cnt * sizeof(double), cudaMemcpyHostToDevice);
@@ -894,25 +1074,18 @@ hww_status hww_losm_solve(int32_t I, const double* dx, const double* sigma_t, co
     up(d_Jo, J_old, n1);
     if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(unsigned));
     if (e == cudaSuccess) {
-        LosmIn in{};
-        in.I = I;
-        in.dx = d_dx;
-        in.sigt = d_st;
-        in.siga = d_sa;
-        in.v = v;
-        in.dt = dt;
-        in.theta = theta;
-        in.bc_l = bc_left;
-        in.bc_r = bc_right;
+        launch_losm_setup(m, d_dx, d_st, d_sa, v, dt, theta, bc_left, bc_right, d_err, 0);
+        LosmRhsIn in{};
         in.phi_old = d_po;
         in.J_old = d_Jo;
         in.F_old = d_Fo;
         in.F_new = d_Fn;
+        in.P_new = nullptr;
         in.PL = PL_new;
         in.PR = PR_new;
         in.q_old = q_old ? d_qo : nullptr;
         in.q_new = q_new ? d_qn : nullptr;
-        launch_losm_only(in, d_pn, d_Jn, d_w, d_err, 0);
+        launch_losm_solve(m, in, w, d_pn, d_Jn, nullptr, 0);
         e = cudaGetLastError();
     }
     unsigned herr = 0;

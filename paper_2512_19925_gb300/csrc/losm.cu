@@ -1,0 +1,381 @@
+// losm.cu -- closures, moving-average filter, HLOSM solves and window
+// centers, laid out for GB300's FP64 units (few per SM, long latency):
+// every FP64 stage is spread over many threads and blocks, and the only
+// inherently sequential part, the tridiagonal substitution, runs as two
+// chunked affine scans.
+//
+// The discrete LOSM equations (Eqs. losm-0, losm-1, losm-disc-bc and their
+// semi-implicit form, Eqs. losm-1-semi, losm-disc-bc-semi) share one matrix:
+// it depends on the cross sections, dt, v and theta only.  Eliminating J with
+// the first-moment rows, J_i = m_i/d_i + g_i (phi_i - phi_{i+1}),
+// g_i = theta / (3 d_i), leaves a diagonally dominant tridiagonal system in
+// phi of size I+2.  Its Thomas factorization (pivots and multipliers) is
+// computed once per cross-section set; a solve then needs
+//   1. the right-hand side (m_i on edges, R_r on rows), pure multiply-adds;
+//   2. forward substitution y_r = R_r/den_r - (A_r/den_r) y_{r-1} and back
+//      substitution phi_r = y_r - c'_r phi_{r+1}, both first-order linear
+//      recurrences evaluated by a chunked scan of affine maps.
+// Built with contraction off.
+#include "hww_internal.cuh"
+#include "losm_kernels.cuh"
+
+namespace hww {
+namespace {
+
+constexpr int SCAN_T = 256;  // threads of the substitution kernel
+
+// ---------------------------------------------------------------------------
+// setup: constant coefficients and the factorization
+// ---------------------------------------------------------------------------
+__global__ void losm_coef_kernel(LosmMat m, const double* dx, const double* sigt, const double* siga, double v,
+                                 double dt, double theta) {
+    const int I = m.I;
+    const double vdt = v * dt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= I; i += gridDim.x * blockDim.x) {
+        const double dxl = (i >= 1) ? dx[i - 1] : 0.0;
+        const double dxr = (i <= I - 1) ? dx[i] : 0.0;
+        const double stl = (i >= 1) ? sigt[i - 1] : 0.0;
+        const double str = (i <= I - 1) ? sigt[i] : 0.0;
+        const double dxh = 0.5 * (dxl + dxr);
+        const double sth = (stl * dxl + str * dxr) / (dxl + dxr);
+        const double d = dxh / vdt + theta * sth * dxh;
+        m.eJ[i] = dxh / vdt;
+        m.eS[i] = sth * dxh;
+        m.invd[i] = 1.0 / d;
+        m.g[i] = theta / (3.0 * d);
+        if (i < I) {
+            m.cP[i] = dx[i] / vdt;
+            m.cA[i] = siga[i] * dx[i];
+            m.cB[i] = dx[i] / vdt + theta * siga[i] * dx[i];
+        }
+    }
+}
+
+// Thomas factorization of the eliminated matrix (rows 0..I+1); one thread,
+// run once per cross-section set
+__global__ void losm_factor_kernel(LosmMat m, double theta, int bc_l, int bc_r, unsigned* err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int I = m.I;
+    double cprev = 0.0;
+    for (int r = 0; r <= I + 1; ++r) {
+        double A, B, C;
+        if (r == 0) {
+            A = 0.0;
+            C = -m.g[0];
+            B = (bc_l == 1) ? m.g[0] : 0.5 + m.g[0];
+        } else if (r == I + 1) {
+            A = -m.g[I];
+            C = 0.0;
+            B = (bc_r == 1) ? m.g[I] : m.g[I] + 0.5;
+        } else {
+            A = -theta * m.g[r - 1];
+            C = -theta * m.g[r];
+            B = m.cB[r - 1] + theta * m.g[r - 1] + theta * m.g[r];
+        }
+        const double den = B - A * cprev;
+        if (den == 0.0 || !isfinite(den)) {
+            atomicOr(err, ERR_LOSM);
+            return;
+        }
+        const double inv = 1.0 / den;
+        cprev = C * inv;
+        m.inv_den[r] = inv;
+        m.vf[r] = -A * inv;
+        m.cp[r] = cprev;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// right-hand side
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double moment_rhs(const LosmMat& m, const LosmRhsIn& in, int i) {
+    const double th = m.theta, tm1 = th - 1.0;
+    const double old = (in.phi_old[i + 1] - in.phi_old[i]) * (1.0 / 3.0) + m.eS[i] * in.J_old[i] -
+                       in.F_old[i + 1] + in.F_old[i];
+    return m.eJ[i] * in.J_old[i] + th * (in.F_new[i + 1] - in.F_new[i]) + tm1 * old;
+}
+
+__global__ void losm_rhs_kernel(LosmMat m, LosmRhsIn in, double* u, double* mom) {
+    const int I = m.I;
+    const double th = m.theta, tm1 = th - 1.0;
+    const double PL = in.P_new ? in.P_new[0] : in.PL;
+    const double PR = in.P_new ? in.P_new[1] : in.PR;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= I + 1; r += gridDim.x * blockDim.x) {
+        double R;
+        if (r == 0) {
+            const double m0 = moment_rhs(m, in, 0);
+            mom[0] = m0;
+            R = (m.bc_l == 1) ? -m0 * m.invd[0] : PL - m0 * m.invd[0];
+        } else if (r == I + 1) {
+            const double mI = moment_rhs(m, in, I);
+            R = (m.bc_r == 1) ? mI * m.invd[I] : PR + mI * m.invd[I];
+        } else {
+            const double ml = moment_rhs(m, in, r - 1);
+            const double mr = moment_rhs(m, in, r);
+            mom[r] = mr;
+            const double qn = in.q_new ? in.q_new[r - 1] : 0.0;
+            const double qo = in.q_old ? in.q_old[r - 1] : 0.0;
+            const double oldb = in.J_old[r] - in.J_old[r - 1] + m.cA[r - 1] * in.phi_old[r] - qo;
+            const double rr = m.cP[r - 1] * in.phi_old[r] + th * qn + tm1 * oldb;
+            R = rr + th * ml * m.invd[r - 1] - th * mr * m.invd[r];
+        }
+        u[r] = R * m.inv_den[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// substitution: y_r = u_r + vf_r y_{r-1} (forward), phi_r = y_r - cp_r phi_{r+1}
+// (backward), by chunked scans of affine maps x -> a + b x
+// ---------------------------------------------------------------------------
+struct Aff {
+    double a, b;
+};
+
+// compose: apply f first, then g
+__device__ __forceinline__ Aff compose(Aff f, Aff g) { return Aff{g.a + g.b * f.a, g.b * f.b}; }
+
+// inclusive scan of one affine map per thread (Hillis-Steele in shared memory)
+__device__ Aff block_scan_aff(Aff x, Aff* sh) {
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = 1; o < SCAN_T; o <<= 1) {
+        Aff y = x;
+        if ((int)threadIdx.x >= o) y = compose(sh[threadIdx.x - o], x);
+        __syncthreads();
+        sh[threadIdx.x] = y;
+        x = y;
+        __syncthreads();
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(SCAN_T) losm_scan_kernel(LosmMat m, const double* u, const double* mom,
+                                                           double* y, double* phi, double* J, double* red_max,
+                                                           int want_max) {
+    __shared__ Aff sh[SCAN_T];
+    __shared__ double smax[SCAN_T];
+    const int n = m.I + 2;
+    const int L = (n + SCAN_T - 1) / SCAN_T;
+    const int r0 = threadIdx.x * L;
+    const int r1 = min(n, r0 + L);
+    // forward: y_r = u_r + vf_r y_{r-1}
+    Aff f{0.0, 1.0};
+    for (int r = r0; r < r1; ++r) f = compose(f, Aff{u[r], m.vf[r]});
+    Aff inc = block_scan_aff(f, sh);
+    Aff exc = (threadIdx.x > 0) ? sh[threadIdx.x - 1] : Aff{0.0, 1.0};
+    (void)inc;
+    double yy = exc.a;  // y_{r0-1} with y_{-1} = 0
+    for (int r = r0; r < r1; ++r) {
+        yy = u[r] + m.vf[r] * yy;
+        y[r] = yy;
+    }
+    __syncthreads();
+    // backward over the reversed order: phi_r = y_r - cp_r phi_{r+1}; thread t
+    // takes the chunk of reversed position t
+    const int q0 = threadIdx.x * L;
+    const int q1 = min(n, q0 + L);
+    Aff g{0.0, 1.0};
+    for (int q = q0; q < q1; ++q) {
+        const int r = n - 1 - q;
+        g = compose(g, Aff{y[r], -m.cp[r]});
+    }
+    block_scan_aff(g, sh);
+    Aff gexc = (threadIdx.x > 0) ? sh[threadIdx.x - 1] : Aff{0.0, 1.0};
+    double pp = gexc.a;  // phi_{r+1} of the first row of this chunk, phi_{n} = 0
+    for (int q = q0; q < q1; ++q) {
+        const int r = n - 1 - q;
+        pp = y[r] - m.cp[r] * pp;
+        phi[r] = pp;
+    }
+    __syncthreads();
+    // J on edges and the maximum of the clamped cell flux
+    double mx = 0.0;
+    for (int i = threadIdx.x; i <= m.I; i += SCAN_T) {
+        J[i] = mom[i] * m.invd[i] + m.g[i] * (phi[i] - phi[i + 1]);
+        if (i >= 1) mx = fmax(mx, phi[i] > 0.0 ? phi[i] : 0.0);
+    }
+    if (want_max) {
+        smax[threadIdx.x] = mx;
+        __syncthreads();
+        for (int s = SCAN_T / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *red_max = smax[0];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// window centers, Eq. (ww-center) with the clamp at 0 and Eq. (ww-c&f).
+// Centers are rounded to 20 significant bits (half up on the bit pattern):
+// the window only needs the center to within a factor rho, and the rounding
+// keeps the windows independent of last-bit differences between equivalent
+// LOSM solvers (a roulette survivor takes the center as its weight).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double quantize_center(double c) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(c);
+    return __longlong_as_double((long long)((b + (1ull << 31)) & ~((1ull << 32) - 1ull)));
+}
+
+__global__ void ww_centers_kernel(WwArgs a) {
+    const double mx = a.mx_ptr ? *a.mx_ptr : 0.0;
+    const double scale = (a.scaling == 0) ? a.sd->wbar : 1.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.I; i += gridDim.x * blockDim.x) {
+        double ctr;
+        if (a.source == 3) {
+            ctr = a.override_c[i];
+        } else {
+            const double f = a.phit[i] > 0.0 ? a.phit[i] : 0.0;
+            const double ratio = (mx > 0.0) ? f / mx : 1.0;
+            const double b = ratio * (1.0 - a.eps) + a.eps;
+            ctr = scale * b;
+        }
+        ctr = quantize_center(ctr);
+        a.ww_c[i] = ctr;
+        a.ww_hi[i] = ctr * a.rho;
+        a.ww_lo[i] = ctr / a.rho;
+    }
+}
+
+// maximum of a clamped cell vector (lagged windows take the previous step's
+// track-length flux)
+__global__ void vec_max_kernel(const double* x, int n, double* out) {
+    __shared__ double s[256];
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, x[i] > 0.0 ? x[i] : 0.0);
+    s[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+// step scalars: tally and comb fixed-point scales, comb offset
+__global__ void step_scalars_kernel(StepDev* sd, int nbits, uint32_t k0, uint32_t k1, unsigned long long* stats) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int E = 0;
+    if (sd->wbar > 0.0) {
+        int e;
+        frexp(sd->wbar, &e);
+        E = e - 1;
+    }
+    sd->S = 40 - E;
+    sd->Sc = 59 - E - nbits;
+    sd->tscale = pow2(sd->S);
+    sd->cscale = pow2(sd->Sc);
+    uint32_t r[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xC0B0u};
+    philox4x32_10(r, k0, k1);
+    sd->u_comb = u01(r[0], r[1]);
+    stats[ST_NSTART] = sd->nbank;
+}
+
+// ---------------------------------------------------------------------------
+// closures from the census tallies (Eq. ct-mc), then the filter
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cen_val(const ClosureArgs& a, int q, int i, double isc) {
+    return (a.v * (acc_to_double(a.cent[q * a.I + i]) * isc)) / ((double)a.N * a.dx[i]);
+}
+
+__global__ void closure_kernel(ClosureArgs a) {
+    const int I = a.I;
+    const double isc = pow2(-a.sd->S);
+    const double PL = (a.bc_l == 1) ? 0.0 : (acc_to_double(a.bnd[2]) * isc) / ((double)a.N * a.dt);
+    const double PR = (a.bc_r == 1) ? 0.0 : (acc_to_double(a.bnd[5]) * isc) / ((double)a.N * a.dt);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= I; i += gridDim.x * blockDim.x) {
+        if (i < I) {
+            a.rphi[i] = cen_val(a, 0, i, isc);
+            a.rF[i] = cen_val(a, 2, i, isc);
+            a.prev_tl[i] = (acc_to_double(a.tl[i]) * isc) / (((double)a.N * a.dx[i]) * a.dt);
+        }
+        double J;
+        if (i == 0) {
+            J = (a.bc_l == 1) ? 0.0 : (-0.5 * cen_val(a, 0, 0, isc) + PL);
+        } else if (i == I) {
+            J = (a.bc_r == 1) ? 0.0 : (0.5 * cen_val(a, 0, I - 1, isc) - PR);
+        } else {
+            const double dl = a.dx[i - 1], dr = a.dx[i];
+            J = (cen_val(a, 1, i - 1, isc) * dr + cen_val(a, 1, i, isc) * dl) / (dl + dr);
+        }
+        a.rJ[i] = J;
+        if (i == 0) {
+            a.nP[0] = PL;
+            a.nP[1] = PR;
+        }
+    }
+}
+
+// moving average with the symmetric shrink at the ends (k = 0: copy); the
+// window sum runs from its right end to its left end
+__device__ __forceinline__ double ma_at(const double* in, int m, int j, int k) {
+    int kk = k;
+    if (j - 1 < kk) kk = j - 1;
+    if (m - j < kk) kk = m - j;
+    double s = 0.0;
+    for (int l = -kk; l <= kk; ++l) s = s + in[j - l - 1];
+    return s / (double)(2 * kk + 1);
+}
+
+__global__ void filter_kernel(ClosureArgs a) {
+    const int I = a.I, k = a.filter_k;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= I + 1; i += gridDim.x * blockDim.x) {
+        if (i >= 1 && i <= I) {
+            a.nphi[i] = k ? ma_at(a.rphi, I, i, k) : a.rphi[i - 1];
+            a.nF[i] = k ? ma_at(a.rF, I, i, k) : a.rF[i - 1];
+        }
+        if (i <= I) a.nJ[i] = k ? ma_at(a.rJ, I + 1, i + 1, k) : a.rJ[i];
+        if (i == 0) {
+            // end values are kept by the filter, so the boundary copies use them
+            a.nphi[0] = a.rphi[0];
+            a.nF[0] = a.rF[0];
+        }
+        if (i == I + 1) {
+            a.nphi[I + 1] = a.rphi[I - 1];
+            a.nF[I + 1] = a.rF[I - 1];
+        }
+    }
+}
+
+int small_grid(int n) {
+    const int b = (n + 127) / 128;
+    return b < 1 ? 1 : (b > 64 ? 64 : b);
+}
+
+}  // namespace
+
+void launch_losm_setup(const LosmMat& m, const double* dx, const double* sigt, const double* siga, double v,
+                       double dt, double theta, int bc_l, int bc_r, unsigned* err, cudaStream_t s) {
+    losm_coef_kernel<<<small_grid(m.I + 1), 128, 0, s>>>(m, dx, sigt, siga, v, dt, theta);
+    losm_factor_kernel<<<1, 32, 0, s>>>(m, theta, bc_l, bc_r, err);
+}
+
+int launch_losm_solve(const LosmMat& m, const LosmRhsIn& in, const LosmWork& w, double* phi, double* J,
+                      double* mx, cudaStream_t s) {
+    losm_rhs_kernel<<<small_grid(m.I + 2), 128, 0, s>>>(m, in, w.u, w.mom);
+    losm_scan_kernel<<<1, SCAN_T, 0, s>>>(m, w.u, w.mom, w.y, phi, J, mx, mx != nullptr);
+    return 2;
+}
+
+int launch_ww_centers(const WwArgs& a, cudaStream_t s) {
+    int n = 0;
+    if (a.source == 2) {
+        vec_max_kernel<<<1, 256, 0, s>>>(a.phit, a.I, (double*)a.mx_ptr);
+        ++n;
+    }
+    ww_centers_kernel<<<small_grid(a.I), 128, 0, s>>>(a);
+    return n + 1;
+}
+
+void launch_step_scalars(StepDev* sd, int nbits, uint32_t k0, uint32_t k1, unsigned long long* stats,
+                         cudaStream_t s) {
+    step_scalars_kernel<<<1, 32, 0, s>>>(sd, nbits, k0, k1, stats);
+}
+
+int launch_closures(const ClosureArgs& a, cudaStream_t s) {
+    closure_kernel<<<small_grid(a.I + 1), 128, 0, s>>>(a);
+    filter_kernel<<<small_grid(a.I + 2), 128, 0, s>>>(a);
+    return 2;
+}
+
+}  // namespace hww

@@ -1,258 +1,14 @@
-// step.cu -- the O(I) and O(N) stages around the tracking kernel:
-//   prestep   step scalars, semi-implicit HLOSM solve (Eqs. losm-0,
-//             losm-1-semi, losm-disc-bc-semi) and window centers (Eq.
-//             ww-center, Eq. ww-c&f);
-//   poststep  census tallies -> closures and initial conditions (Eq. ct-mc,
-//             linear edge-current interpolation, moving-average filter Eq.
-//             moving_average) and the fully implicit HLOSM solve (Eqs.
-//             losm-0, losm-1, losm-disc-bc);
+// step.cu -- the O(N) stage after tracking:
 //   comb      uniform combing of the census bank back to N (Sec. 5.1):
 //             canonical order by (source id, lineage key) via per-id groups,
 //             exact fixed-point cumulative weights, teeth (k + u) W / N.
-// Built with contraction off so that the closure arithmetic and the comb
-// positions are the single IEEE operations written.
+// Built with contraction off so that the comb positions are the single IEEE
+// operations written.
 #include "hww_internal.cuh"
 #include "step_kernels.cuh"
 
 namespace hww {
 namespace {
-
-__device__ __forceinline__ int wbar_exponent(double wbar) {
-    if (!(wbar > 0.0)) return 0;
-    int e;
-    frexp(wbar, &e);
-    return e - 1;
-}
-
-// ---------------------------------------------------------------------------
-// LOSM solver.  The interleaved system of Eqs. (losm-0), (losm-1),
-// (losm-disc-bc) is reduced to a tridiagonal system in phi alone: each
-// first-moment row gives J_i = m_i/d_i + g_i (phi_i - phi_{i+1}) with
-// g_i = theta / (3 d_i), which substituted into the balance rows and the
-// boundary rows leaves a diagonally dominant tridiagonal system of size I+2,
-// solved by the Thomas algorithm; J then follows from the same relation.
-// Assembly terms are formed exactly as the interleaved rows are.
-// ---------------------------------------------------------------------------
-__device__ void losm_solve_serial(const LosmIn in, double* phi_new, double* J_new, double* w_d,
-                                  double* w_m, double* w_c, double* w_r, unsigned* err) {
-    const int I = in.I;
-    const double vdt = in.v * in.dt;
-    const double th = in.theta;
-    const double tm1 = th - 1.0;
-    // first-moment rows: d_i (diagonal), m_i (right-hand side)
-    for (int i = 0; i <= I; ++i) {
-        const double dxl = (i >= 1) ? in.dx[i - 1] : 0.0;
-        const double dxr = (i <= I - 1) ? in.dx[i] : 0.0;
-        const double stl = (i >= 1) ? in.sigt[i - 1] : 0.0;
-        const double str = (i <= I - 1) ? in.sigt[i] : 0.0;
-        const double dxh = 0.5 * (dxl + dxr);
-        const double sth = (stl * dxl + str * dxr) / (dxl + dxr);
-        const double d = dxh / vdt + th * sth * dxh;
-        const double old = (in.phi_old[i + 1] - in.phi_old[i]) / 3.0 + sth * dxh * in.J_old[i] -
-                           in.F_old[i + 1] + in.F_old[i];
-        const double m = dxh / vdt * in.J_old[i] + th * (in.F_new[i + 1] - in.F_new[i]) + tm1 * old;
-        w_d[i] = d;
-        w_m[i] = m;
-    }
-    // Thomas forward sweep over rows 0..I+1 (c' in w_c, r' in w_r)
-    double cprev = 0.0, rprev = 0.0;
-    for (int i = 0; i <= I + 1; ++i) {
-        double A, B, C, R;
-        if (i == 0) {
-            const double g = th / (3.0 * w_d[0]);
-            A = 0.0;
-            C = -g;
-            if (in.bc_l == 1) {
-                B = g;
-                R = -w_m[0] / w_d[0];
-            } else {
-                B = 0.5 + g;
-                R = in.PL - w_m[0] / w_d[0];
-            }
-        } else if (i == I + 1) {
-            const double g = th / (3.0 * w_d[I]);
-            A = -g;
-            C = 0.0;
-            if (in.bc_r == 1) {
-                B = g;
-                R = w_m[I] / w_d[I];
-            } else {
-                B = g + 0.5;
-                R = in.PR + w_m[I] / w_d[I];
-            }
-        } else {
-            const double dxi = in.dx[i - 1];
-            const double gl = th / (3.0 * w_d[i - 1]);
-            const double gr = th / (3.0 * w_d[i]);
-            const double b = dxi / vdt + th * in.siga[i - 1] * dxi;
-            const double qn = in.q_new ? in.q_new[i - 1] : 0.0;
-            const double qo = in.q_old ? in.q_old[i - 1] : 0.0;
-            const double oldb = in.J_old[i] - in.J_old[i - 1] + in.siga[i - 1] * dxi * in.phi_old[i] - qo;
-            const double r = dxi / vdt * in.phi_old[i] + th * qn + tm1 * oldb;
-            A = -th * gl;
-            C = -th * gr;
-            B = b + th * gl + th * gr;
-            R = r + th * w_m[i - 1] / w_d[i - 1] - th * w_m[i] / w_d[i];
-        }
-        const double den = B - A * cprev;
-        if (den == 0.0 || !isfinite(den)) {
-            atomicOr(err, ERR_LOSM);
-            return;
-        }
-        const double inv = 1.0 / den;
-        cprev = C * inv;
-        rprev = (R - A * rprev) * inv;
-        w_c[i] = cprev;
-        w_r[i] = rprev;
-    }
-    phi_new[I + 1] = w_r[I + 1];
-    for (int i = I; i >= 0; --i) phi_new[i] = w_r[i] - w_c[i] * phi_new[i + 1];
-    for (int i = 0; i <= I; ++i) {
-        const double g = th / (3.0 * w_d[i]);
-        J_new[i] = w_m[i] / w_d[i] + g * (phi_new[i] - phi_new[i + 1]);
-    }
-}
-
-// window centers from a cell vector (Eq. ww-center with the clamp at 0)
-__device__ void ww_centers(const double* phit, int I, double scale, double eps, double rho,
-                           double* ww_c, double* ww_hi, double* ww_lo, double* red) {
-    double mx = 0.0;
-    for (int i = threadIdx.x; i < I; i += blockDim.x) {
-        const double f = phit[i] > 0.0 ? phit[i] : 0.0;
-        mx = fmax(mx, f);
-    }
-    red[threadIdx.x] = mx;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    mx = red[0];
-    __syncthreads();
-    for (int i = threadIdx.x; i < I; i += blockDim.x) {
-        const double f = phit[i] > 0.0 ? phit[i] : 0.0;
-        const double ratio = (mx > 0.0) ? f / mx : 1.0;
-        const double b = ratio * (1.0 - eps) + eps;
-        const double ctr = scale * b;
-        ww_c[i] = ctr;
-        ww_hi[i] = ctr * rho;
-        ww_lo[i] = ctr / rho;
-    }
-}
-
-__global__ void prestep_kernel(PreArgs a) {
-    __shared__ double red[256];
-    StepDev* sd = a.sd;
-    if (threadIdx.x == 0) {
-        const int E = wbar_exponent(sd->wbar);
-        sd->S = 40 - E;
-        sd->Sc = 59 - E - a.nbits;
-        sd->tscale = pow2(sd->S);
-        sd->cscale = pow2(sd->Sc);
-        uint32_t r[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xC0B0u};
-        philox4x32_10(r, a.k0, a.k1);
-        sd->u_comb = u01(r[0], r[1]);
-        a.stats[ST_NSTART] = sd->nbank;
-        LosmIn in = a.losm;
-        in.PL = a.P_old[0];
-        in.PR = a.P_old[1];
-        losm_solve_serial(in, a.semi_phi, a.semi_J, a.w_d, a.w_m, a.w_c, a.w_r, a.err);
-    }
-    __syncthreads();
-    const double scale = (a.scaling == 0) ? sd->wbar : 1.0;
-    if (a.ww_source == 1) {
-        ww_centers(a.semi_phi + 1, a.losm.I, scale, a.eps, a.rho, a.ww_c, a.ww_hi, a.ww_lo, red);
-    } else if (a.ww_source == 2) {
-        ww_centers(a.prev_tl, a.losm.I, scale, a.eps, a.rho, a.ww_c, a.ww_hi, a.ww_lo, red);
-    } else if (a.ww_source == 3) {
-        for (int i = threadIdx.x; i < a.losm.I; i += blockDim.x) {
-            const double ctr = a.ww_override[i];
-            a.ww_c[i] = ctr;
-            a.ww_hi[i] = ctr * a.rho;
-            a.ww_lo[i] = ctr / a.rho;
-        }
-    }
-}
-
-// moving average with the symmetric shrink at the ends; the sum runs over
-// the window from its right end to its left end
-__device__ void ma_filter_dev(const double* in, double* out, int m, int k) {
-    for (int j = 1 + threadIdx.x; j <= m; j += blockDim.x) {
-        int kk = k;
-        if (j - 1 < kk) kk = j - 1;
-        if (m - j < kk) kk = m - j;
-        double s = 0.0;
-        for (int l = -kk; l <= kk; ++l) s = s + in[j - l - 1];
-        out[j - 1] = s / (double)(2 * kk + 1);
-    }
-}
-
-__global__ void poststep_kernel(PostArgs a) {
-    const int I = a.I;
-    const StepDev* sd = a.sd;
-    const double isc = pow2(-sd->S);
-    const double v = a.v;
-    const double N = (double)a.N;
-    // normalised census tallies (cell vectors, 0-based) into the new closure
-    // vectors (paper layout)
-    for (int i = threadIdx.x; i < I; i += blockDim.x) {
-        const double den = N * a.dx[i];
-        a.nphi[i + 1] = (v * (acc_to_double(a.cent[i]) * isc)) / den;
-        a.nF[i + 1] = (v * (acc_to_double(a.cent[2 * I + i]) * isc)) / den;
-        a.cJ[i] = (v * (acc_to_double(a.cent[I + i]) * isc)) / den;
-        a.prev_tl[i] = (acc_to_double(a.tl[i]) * isc) / ((N * a.dx[i]) * a.dt);
-    }
-    __syncthreads();
-    const double PL = (a.bc_l == 1) ? 0.0 : (acc_to_double(a.bnd[2]) * isc) / (N * a.dt);
-    const double PR = (a.bc_r == 1) ? 0.0 : (acc_to_double(a.bnd[5]) * isc) / (N * a.dt);
-    for (int i = 1 + threadIdx.x; i <= I - 1; i += blockDim.x) {
-        const double dl = a.dx[i - 1], dr = a.dx[i];
-        a.nJ[i] = (a.cJ[i - 1] * dr + a.cJ[i] * dl) / (dl + dr);
-    }
-    if (threadIdx.x == 0) {
-        a.nphi[0] = a.nphi[1];
-        a.nphi[I + 1] = a.nphi[I];
-        a.nF[0] = a.nF[1];
-        a.nF[I + 1] = a.nF[I];
-        a.nJ[0] = (a.bc_l == 1) ? 0.0 : (-0.5 * a.nphi[0] + PL);
-        a.nJ[I] = (a.bc_r == 1) ? 0.0 : (0.5 * a.nphi[I + 1] - PR);
-        a.nP[0] = PL;
-        a.nP[1] = PR;
-    }
-    __syncthreads();
-    if (a.filter_k > 0) {
-        ma_filter_dev(a.nphi + 1, a.tmp, I, a.filter_k);
-        __syncthreads();
-        for (int i = threadIdx.x; i < I; i += blockDim.x) a.nphi[i + 1] = a.tmp[i];
-        __syncthreads();
-        ma_filter_dev(a.nF + 1, a.tmp, I, a.filter_k);
-        __syncthreads();
-        for (int i = threadIdx.x; i < I; i += blockDim.x) a.nF[i + 1] = a.tmp[i];
-        __syncthreads();
-        ma_filter_dev(a.nJ, a.tmp, I + 1, a.filter_k);
-        __syncthreads();
-        for (int i = threadIdx.x; i <= I; i += blockDim.x) a.nJ[i] = a.tmp[i];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        LosmIn in = a.losm;  // old-level vectors are the closure set of the step start
-        in.F_new = a.nF;
-        in.PL = a.nP[0];
-        in.PR = a.nP[1];
-        losm_solve_serial(in, a.full_phi, a.full_J, a.w_d, a.w_m, a.w_c, a.w_r, a.err);
-    }
-}
-
-// copy the new closure set over the old one (next step's initial conditions)
-__global__ void closure_commit_kernel(PostArgs a) {
-    const int I = a.I;
-    for (int i = threadIdx.x; i < I + 2; i += blockDim.x) {
-        a.ophi[i] = a.nphi[i];
-        a.oF[i] = a.nF[i];
-    }
-    for (int i = threadIdx.x; i < I + 1; i += blockDim.x) a.oJ[i] = a.nJ[i];
-    if (threadIdx.x < 2) a.oP[threadIdx.x] = a.nP[threadIdx.x];
-}
 
 // ---------------------------------------------------------------------------
 // Exclusive scan of (count, weight) pairs over the N source ids, in three
@@ -452,13 +208,6 @@ __global__ void comb_finalize_kernel(StepDev* sd, const unsigned long long* goff
 
 }  // namespace
 
-void launch_prestep(const PreArgs& a, cudaStream_t s) { prestep_kernel<<<1, 256, 0, s>>>(a); }
-
-void launch_poststep(const PostArgs& a, cudaStream_t s) {
-    poststep_kernel<<<1, 256, 0, s>>>(a);
-    closure_commit_kernel<<<1, 256, 0, s>>>(a);
-}
-
 void launch_group_scan(const ScanArgs& a, cudaStream_t s) {
     const long long ntiles = (a.n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntiles > 0) scan_tiles_kernel<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(a);
@@ -477,18 +226,6 @@ void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
 
 template void launch_comb<double>(const CombArgs<double>&, int, cudaStream_t);
 template void launch_comb<float>(const CombArgs<float>&, int, cudaStream_t);
-
-// standalone LOSM solve for checking the solver
-__global__ void losm_only_kernel(LosmIn in, double* phi, double* J, double* w_d, double* w_m,
-                                 double* w_c, double* w_r, unsigned* err) {
-    if (threadIdx.x == 0) losm_solve_serial(in, phi, J, w_d, w_m, w_c, w_r, err);
-}
-
-void launch_losm_only(const LosmIn& in, double* phi, double* J, double* work, unsigned* err,
-                      cudaStream_t s) {
-    const int n = in.I + 2;
-    losm_only_kernel<<<1, 32, 0, s>>>(in, phi, J, work, work + n, work + 2 * n, work + 3 * n, err);
-}
 
 __global__ void philox_block_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                     uint32_t k1, long long n, uint32_t* out) {

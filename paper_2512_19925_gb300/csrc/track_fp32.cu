@@ -4,9 +4,17 @@
 // the top 23 bits of the same Philox words), but the geometry runs in FP32:
 // a track keeps its cell index and an FP32 offset from the cell's left edge,
 // an FP32 direction, an FP32 distance to census and FP32 flight distances.
-// Weights, the window tests, every tally contribution and all downstream
-// steps (closures, filter, LOSM solves, comb) stay in FP64, the steps whose
-// accuracy the estimators rest on.
+// Weights and the window tests stay FP64; tally contributions are formed in
+// exact integer arithmetic from a fixed-point copy of the weight,
+//     round(W * f),   W = round(w 2^S) (64-bit),  f = l, l mu, l (1/3 - mu^2) (FP32),
+// i.e. the exact product of the 64-bit weight and the 24-bit mantissa of f,
+// rounded once (half up) at the tally scale.  The FP64 pipe, of which GB300
+// has little, is left to rare events (splits, roulette, leaks, census).
+//
+// The event loop is flattened: a lane whose track ends (census, absorption,
+// leak, roulette kill, event budget) loads its next track in the same loop
+// iteration the other lanes spend on their next event, so a warp stays full
+// until the work runs out.
 #include "track_common.cuh"
 
 namespace hww {
@@ -15,15 +23,49 @@ namespace {
 struct P32 {
     float xo, mu, inv_mu, tau;
     double w;
+    long long W;  // w 2^S rounded
     int cell;
     uint32_t id;
     uint64_t lin;
     uint32_t e;
 };
 
-__device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32& q, double w,
-                                            uint32_t e, uint32_t jstart, uint32_t jcount,
-                                            unsigned long long slot) {
+// round(W * f) for W >= 0 and an FP32 f, from the exact 128-bit product of W
+// and the mantissa of f (round half up); subnormal f counts as 0
+__device__ __forceinline__ long long fx_mul(long long W, float f) {
+    const unsigned b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 0xFFu);
+    if (ex == 0) return 0;
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int s = 150 - ex;  // value = m 2^-s
+    const unsigned long long uw = (unsigned long long)W;
+    const unsigned long long lo = uw * m;
+    const unsigned long long hi = __umul64hi(uw, m);
+    unsigned long long r, rb;
+    if (s <= 0) {
+        r = lo << (-s);
+        rb = 0;
+    } else if (s < 64) {
+        r = (lo >> s) | (hi << (64 - s));
+        rb = (lo >> (s - 1)) & 1ull;
+    } else if (s == 64) {
+        r = hi;
+        rb = lo >> 63;
+    } else if (s < 128) {
+        r = hi >> (s - 64);
+        rb = (hi >> (s - 65)) & 1ull;
+    } else {
+        return 0;
+    }
+    r += rb;
+    return (b >> 31) ? -(long long)r : (long long)r;
+}
+
+// positive doubles order like their bit patterns
+__device__ __forceinline__ bool dgt(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
+
+__device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32& q, double w, uint32_t e,
+                                            uint32_t jstart, uint32_t jcount, unsigned long long slot) {
     if ((long long)slot >= a.rout.cap) {
         atomicOr(a.err, ERR_QUEUE_OVERFLOW);
         return;
@@ -40,18 +82,98 @@ __device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32
     a.rout.jcount[slot] = jcount;
 }
 
-__device__ void run_track(const TrackArgs<float>& a, P32 q, long long* s_tl, long long* s_cen,
-                          Counters& cnt, double tscale, double cscale) {
+__global__ void __launch_bounds__(256) track32_kernel(TrackArgs<float> a) {
+    extern __shared__ long long sm[];
     const int I = a.I;
+    long long* s_tl = sm;
+    long long* s_cen = sm + 3 * I;
+    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    Counters cnt;
+    cnt.zero();
+    const double tscale = a.sd->tscale;
+    const double cscale = a.sd->cscale;
+    const double wbar = a.sd->wbar;
+    const float tau0 = (float)a.tau0;
+    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
+    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long Wbar = to_fixed(wbar, tscale);
+
+    long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    P32 q;
+    P32 base;  // record whose daughters are being expanded
+    uint32_t jnext = 0, jend = 0;
+    bool have = false;
     int evs = 0;
     for (;;) {
+        if (!have) {
+            if (jnext < jend) {
+                q = base;
+                q.lin = lineage_hash(base.lin, base.e, jnext);
+                q.e = 0;
+                ++jnext;
+            } else if (item < n_use) {
+                const long long i = item;
+                item += stride;
+                if (a.from_bank) {
+                    q.id = (uint32_t)i;
+                    q.lin = 0;
+                    q.e = 0;
+                    q.tau = tau0;
+                    q.w = wbar;
+                    q.W = Wbar;
+                    if (a.birth) {
+                        uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
+                        philox4x32_10(r, a.k0, a.k1);
+                        q.mu = 2.0f * u01f(r[1]) - 1.0f;
+                        const double x = a.src_x;
+                        if (x <= a.edges[0] && q.mu < 0.0f && a.bc_l == 1) q.mu = -q.mu;
+                        if (x >= a.edges[I] && q.mu > 0.0f && a.bc_r == 1) q.mu = -q.mu;
+                        q.cell = (q.mu < 0.0f) ? a.birth_cell_neg : a.birth_cell_pos;
+                        q.xo = (float)(x - a.edges[q.cell]);
+                    } else {
+                        q.xo = a.bx[i];
+                        q.mu = a.bmu[i];
+                        q.cell = a.bcell[i];
+                    }
+                } else {
+                    q.xo = a.rin.x[i];
+                    q.mu = a.rin.mu[i];
+                    q.tau = a.rin.tau[i];
+                    q.w = a.rin.w[i];
+                    q.W = to_fixed(q.w, tscale);
+                    q.cell = a.rin.cell[i];
+                    q.id = a.rin.id[i];
+                    q.lin = a.rin.lin[i];
+                    q.e = a.rin.e[i];
+                    const uint32_t jc = a.rin.jcount[i];
+                    if (jc) {
+                        base = q;
+                        jnext = a.rin.jstart[i];
+                        jend = jnext + jc;
+                        q.lin = lineage_hash(base.lin, base.e, jnext);
+                        q.e = 0;
+                        ++jnext;
+                    }
+                }
+            } else {
+                break;
+            }
+            q.inv_mu = 1.0f / q.mu;
+            have = true;
+            evs = 0;
+        }
+        // ---- one event ----
         if (evs == a.emax) {
             push_record(a, q, q.w, q.e, 0u, 0u, atomicAdd(a.rout.count, 1ull));
-            return;
+            have = false;
+            continue;
         }
         if (q.e >= MAX_EVENTS) {
             atomicOr(a.err, ERR_EVENTS);
-            return;
+            have = false;
+            continue;
         }
         uint32_t r[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 2u * q.e};
         philox4x32_10(r, a.k0, a.k1);
@@ -74,28 +196,23 @@ __device__ void run_track(const TrackArgs<float>& a, P32 q, long long* s_tl, lon
             ev = 2;
             l = dcoll;
         }
-        const double wl = q.w * (double)l;
-        const long long fphi = to_fixed(wl, tscale);
+        const float m2 = q.mu * q.mu;
+        const float f3 = 1.0f / 3.0f - m2;
+        const long long fphi = fx_mul(q.W, l);
         sadd(&s_tl[k], fphi);
-        sadd(&s_tl[I + k], to_fixed(wl * (double)q.mu, tscale));
-        sadd(&s_tl[2 * I + k], to_fixed(wl * (double)(1.0f / 3.0f - q.mu * q.mu), tscale));
+        sadd(&s_tl[I + k], fx_mul(q.W, l * q.mu));
+        sadd(&s_tl[2 * I + k], fx_mul(q.W, l * f3));
         add128(&a.batch[(long long)(q.id % (uint32_t)a.B) * I + k], fphi);
         cnt.v[ST_SEGMENTS]++;
-        if (ev != 1) {
-            float xn = fmaf(q.mu, l, q.xo);
-            xn = fminf(fmaxf(xn, 0.0f), dxk);
-            q.xo = xn;
-        }
+        if (ev != 1) q.xo = fminf(fmaxf(fmaf(q.mu, l, q.xo), 0.0f), dxk);
         q.tau = (ev == 0) ? 0.0f : q.tau - l;
         const uint32_t e_ev = q.e;
         q.e = q.e + 1;
         ++evs;
         if (ev == 0) {
-            const double wmu = q.w * (double)q.mu;
-            const double wf = q.w * (double)(1.0f / 3.0f - q.mu * q.mu);
-            sadd(&s_cen[k], to_fixed(q.w, tscale));
-            sadd(&s_cen[I + k], to_fixed(wmu, tscale));
-            sadd(&s_cen[2 * I + k], to_fixed(wf, tscale));
+            sadd(&s_cen[k], q.W);
+            sadd(&s_cen[I + k], fx_mul(q.W, q.mu));
+            sadd(&s_cen[2 * I + k], fx_mul(q.W, f3));
             const unsigned long long slot = warp_reserve(a.cen.count);
             if ((long long)slot < a.cen.cap) {
                 a.cen.x[slot] = q.xo;
@@ -111,7 +228,8 @@ __device__ void run_track(const TrackArgs<float>& a, P32 q, long long* s_tl, lon
             }
             cnt.v[ST_CENSUS]++;
             cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-            return;
+            have = false;
+            continue;
         }
         bool have_r2 = false;
         uint32_t r2[4];
@@ -125,13 +243,14 @@ __device__ void run_track(const TrackArgs<float>& a, P32 q, long long* s_tl, lon
                     const double amu = fabs((double)q.mu);
                     const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
                     const double wi = q.w * ia;
-                    const double m2 = (double)q.mu * (double)q.mu;
+                    const double dm2 = (double)q.mu * (double)q.mu;
                     add128(&a.bnd[3 * side + 0], to_fixed(wi, tscale));
-                    add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - m2), tscale));
+                    add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - dm2), tscale));
                     add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), tscale));
                     cnt.v[ST_LEAKED]++;
                     cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                    return;
+                    have = false;
+                    continue;
                 }
                 q.mu = -q.mu;
                 q.inv_mu = -q.inv_mu;
@@ -146,7 +265,8 @@ __device__ void run_track(const TrackArgs<float>& a, P32 q, long long* s_tl, lon
             if ((double)uc >= a.c[k]) {
                 cnt.v[ST_ABSORBED]++;
                 cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                return;
+                have = false;
+                continue;
             }
             r2[0] = q.id;
             r2[1] = (uint32_t)q.lin;
@@ -160,30 +280,30 @@ __device__ void run_track(const TrackArgs<float>& a, P32 q, long long* s_tl, lon
         }
         if (a.ww_on) {
             const int kc = q.cell;
-            const double hi = a.ww_hi[kc];
-            const double lo = a.ww_lo[kc];
-            if (q.w > hi) {
+            if (dgt(q.w, a.ww_hi[kc])) {
                 const double ctr = a.ww_c[kc];
                 const double ndd = ceil(q.w / ctr);
                 if (ndd > (double)MAX_DAUGHTERS) {
                     atomicOr(a.err, ERR_DAUGHTERS);
-                    return;
+                    have = false;
+                    continue;
                 }
                 const uint32_t nd = (uint32_t)ndd;
                 const double wd = q.w / (double)nd;
                 cnt.v[ST_SPLIT_EVENTS]++;
                 cnt.v[ST_DAUGHTERS] += nd - 1;
                 const uint32_t nch = (nd - 1 + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
-                const unsigned long long base = atomicAdd(a.rout.count, (unsigned long long)nch);
+                const unsigned long long b0 = atomicAdd(a.rout.count, (unsigned long long)nch);
                 for (uint32_t ch = 0; ch < nch; ++ch) {
                     const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
                     const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
-                    push_record(a, q, wd, e_ev, j0, jc, base + ch);
+                    push_record(a, q, wd, e_ev, j0, jc, b0 + ch);
                 }
                 q.w = wd;
+                q.W = to_fixed(wd, tscale);
                 q.lin = lineage_hash(q.lin, e_ev, 0);
                 q.e = 0;
-            } else if (q.w < lo) {
+            } else if (dgt(a.ww_lo[kc], q.w)) {
                 if (!have_r2) {
                     r2[0] = q.id;
                     r2[1] = (uint32_t)q.lin;
@@ -196,77 +316,15 @@ __device__ void run_track(const TrackArgs<float>& a, P32 q, long long* s_tl, lon
                 const double ps = q.w / ctr;
                 if (ur < ps) {
                     q.w = ctr;
+                    q.W = to_fixed(ctr, tscale);
                     cnt.v[ST_RSURVIVE]++;
                 } else {
                     cnt.v[ST_RKILLS]++;
                     cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                    return;
+                    have = false;
+                    continue;
                 }
             }
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) track32_kernel(TrackArgs<float> a) {
-    extern __shared__ long long sm[];
-    const int I = a.I;
-    long long* s_tl = sm;
-    long long* s_cen = sm + 3 * I;
-    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) sm[i] = 0;
-    __syncthreads();
-    Counters cnt;
-    cnt.zero();
-    const double tscale = a.sd->tscale;
-    const double cscale = a.sd->cscale;
-    const double wbar = a.sd->wbar;
-    const float tau0 = (float)a.tau0;
-    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
-    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_use; i += stride) {
-        P32 p;
-        uint32_t jstart = 0, jcount = 0;
-        if (a.from_bank) {
-            p.id = (uint32_t)i;
-            p.lin = 0;
-            p.e = 0;
-            p.tau = tau0;
-            p.w = wbar;
-            if (a.birth) {
-                uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
-                philox4x32_10(r, a.k0, a.k1);
-                p.mu = 2.0f * u01f(r[1]) - 1.0f;
-                const double x = a.src_x;
-                if (x <= a.edges[0] && p.mu < 0.0f && a.bc_l == 1) p.mu = -p.mu;
-                if (x >= a.edges[I] && p.mu > 0.0f && a.bc_r == 1) p.mu = -p.mu;
-                p.cell = (p.mu < 0.0f) ? a.birth_cell_neg : a.birth_cell_pos;
-                p.xo = (float)(x - a.edges[p.cell]);
-            } else {
-                p.xo = a.bx[i];
-                p.mu = a.bmu[i];
-                p.cell = a.bcell[i];
-            }
-        } else {
-            p.xo = a.rin.x[i];
-            p.mu = a.rin.mu[i];
-            p.tau = a.rin.tau[i];
-            p.w = a.rin.w[i];
-            p.cell = a.rin.cell[i];
-            p.id = a.rin.id[i];
-            p.lin = a.rin.lin[i];
-            p.e = a.rin.e[i];
-            jstart = a.rin.jstart[i];
-            jcount = a.rin.jcount[i];
-        }
-        const uint32_t ntracks = jcount ? jcount : 1u;
-        for (uint32_t t = 0; t < ntracks; ++t) {
-            P32 q = p;
-            if (jcount) {
-                q.lin = lineage_hash(p.lin, p.e, jstart + t);
-                q.e = 0;
-            }
-            q.inv_mu = 1.0f / q.mu;
-            run_track(a, q, s_tl, s_cen, cnt, tscale, cscale);
         }
     }
     __syncthreads();
@@ -281,8 +339,7 @@ void launch_track_fp32(const TrackArgs<float>& a, int grid, int block, size_t sm
 }
 
 int track_smem_optin_fp32(size_t smem) {
-    return (int)cudaFuncSetAttribute(track32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
+    return (int)cudaFuncSetAttribute(track32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 int track_blocks_per_sm_fp32(int block, size_t smem) {

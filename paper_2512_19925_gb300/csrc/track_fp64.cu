@@ -23,6 +23,8 @@
 // A thread keeps daughter 0 of a split in registers and queues the others
 // as chunk records; after `emax` events a live track is queued as a
 // continuation record, so long histories are rebalanced between launches.
+// The event loop is flattened: a lane whose track ends loads its next track
+// while the other lanes take their next event.
 #include "track_common.cuh"
 
 namespace hww {
@@ -55,18 +57,95 @@ __device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P6
     a.rout.jcount[slot] = jcount;
 }
 
-__device__ void run_track(const TrackArgs<double>& a, P64 q, long long* s_tl, long long* s_cen,
-                          Counters& cnt, double tscale, double cscale) {
+__global__ void __launch_bounds__(256) track64_kernel(TrackArgs<double> a) {
+    extern __shared__ long long sm[];
     const int I = a.I;
+    long long* s_tl = sm;
+    long long* s_cen = sm + 3 * I;
+    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    Counters cnt;
+    cnt.zero();
+    const double tscale = a.sd->tscale;
+    const double cscale = a.sd->cscale;
+    const double wbar = a.sd->wbar;
+    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
+    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+
+    // flattened event loop: a lane whose track ends loads its next one while
+    // the other lanes take their next event
+    long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    P64 q;
+    P64 base;  // record whose daughters are being expanded
+    uint32_t jnext = 0, jend = 0;
+    bool have = false;
     int evs = 0;
     for (;;) {
+        if (!have) {
+            if (jnext < jend) {
+                q = base;
+                q.lin = lineage_hash(base.lin, base.e, jnext);
+                q.e = 0;
+                ++jnext;
+            } else if (item < n_use) {
+                const long long i = item;
+                item += stride;
+                if (a.from_bank) {
+                    q.id = (uint32_t)i;
+                    q.lin = 0;
+                    q.e = 0;
+                    q.tau = a.tau0;
+                    q.w = wbar;
+                    if (a.birth) {
+                        uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
+                        philox4x32_10(r, a.k0, a.k1);
+                        q.mu = 2.0 * u01(r[0], r[1]) - 1.0;
+                        q.x = a.src_x;
+                        if (q.x <= a.edges[0] && q.mu < 0.0 && a.bc_l == 1) q.mu = -q.mu;
+                        if (q.x >= a.edges[I] && q.mu > 0.0 && a.bc_r == 1) q.mu = -q.mu;
+                        q.cell = (q.mu < 0.0) ? a.birth_cell_neg : a.birth_cell_pos;
+                    } else {
+                        q.x = a.bx[i];
+                        q.mu = a.bmu[i];
+                        q.cell = a.bcell[i];
+                    }
+                } else {
+                    q.x = a.rin.x[i];
+                    q.mu = a.rin.mu[i];
+                    q.tau = a.rin.tau[i];
+                    q.w = a.rin.w[i];
+                    q.cell = a.rin.cell[i];
+                    q.id = a.rin.id[i];
+                    q.lin = a.rin.lin[i];
+                    q.e = a.rin.e[i];
+                    const uint32_t jc = a.rin.jcount[i];
+                    if (jc) {
+                        base = q;
+                        jnext = a.rin.jstart[i];
+                        jend = jnext + jc;
+                        q.lin = lineage_hash(base.lin, base.e, jnext);
+                        q.e = 0;
+                        ++jnext;
+                    }
+                }
+            } else {
+                break;
+            }
+            q.inv_mu = 1.0 / q.mu;
+            have = true;
+            evs = 0;
+        }
+        // ---- one event ----
         if (evs == a.emax) {
             push_record(a, q, q.w, q.e, 0u, 0u, atomicAdd(a.rout.count, 1ull));
-            return;
+            have = false;
+            continue;
         }
         if (q.e >= MAX_EVENTS) {
             atomicOr(a.err, ERR_EVENTS);
-            return;
+            have = false;
+            continue;
         }
         uint32_t r[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 2u * q.e};
         philox4x32_10(r, a.k0, a.k1);
@@ -134,7 +213,8 @@ __device__ void run_track(const TrackArgs<double>& a, P64 q, long long* s_tl, lo
             }
             cnt.v[ST_CENSUS]++;
             cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-            return;
+            have = false;
+            continue;
         }
         bool have_r2 = false;
         uint32_t r2[4];
@@ -153,7 +233,8 @@ __device__ void run_track(const TrackArgs<double>& a, P64 q, long long* s_tl, lo
                     add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), tscale));
                     cnt.v[ST_LEAKED]++;
                     cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                    return;
+                    have = false;
+                    continue;
                 }
                 q.mu = -q.mu;
                 q.inv_mu = -q.inv_mu;
@@ -166,7 +247,8 @@ __device__ void run_track(const TrackArgs<double>& a, P64 q, long long* s_tl, lo
             if (uc >= a.c[k]) {
                 cnt.v[ST_ABSORBED]++;
                 cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                return;
+                have = false;
+                continue;
             }
             r2[0] = q.id;
             r2[1] = (uint32_t)q.lin;
@@ -187,18 +269,19 @@ __device__ void run_track(const TrackArgs<double>& a, P64 q, long long* s_tl, lo
                 const double ndd = ceil(q.w / ctr);
                 if (ndd > (double)MAX_DAUGHTERS) {
                     atomicOr(a.err, ERR_DAUGHTERS);
-                    return;
+                    have = false;
+                    continue;
                 }
                 const uint32_t nd = (uint32_t)ndd;
                 const double wd = q.w / (double)nd;
                 cnt.v[ST_SPLIT_EVENTS]++;
                 cnt.v[ST_DAUGHTERS] += nd - 1;
                 const uint32_t nch = (nd - 1 + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
-                const unsigned long long base = atomicAdd(a.rout.count, (unsigned long long)nch);
+                const unsigned long long b0 = atomicAdd(a.rout.count, (unsigned long long)nch);
                 for (uint32_t ch = 0; ch < nch; ++ch) {
                     const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
                     const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
-                    push_record(a, q, wd, e_ev, j0, jc, base + ch);
+                    push_record(a, q, wd, e_ev, j0, jc, b0 + ch);
                 }
                 q.w = wd;
                 q.lin = lineage_hash(q.lin, e_ev, 0);
@@ -220,71 +303,10 @@ __device__ void run_track(const TrackArgs<double>& a, P64 q, long long* s_tl, lo
                 } else {
                     cnt.v[ST_RKILLS]++;
                     cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                    return;
+                    have = false;
+                    continue;
                 }
             }
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) track64_kernel(TrackArgs<double> a) {
-    extern __shared__ long long sm[];
-    const int I = a.I;
-    long long* s_tl = sm;
-    long long* s_cen = sm + 3 * I;
-    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) sm[i] = 0;
-    __syncthreads();
-    Counters cnt;
-    cnt.zero();
-    const double tscale = a.sd->tscale;
-    const double cscale = a.sd->cscale;
-    const double wbar = a.sd->wbar;
-    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
-    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_use; i += stride) {
-        P64 p;
-        uint32_t jstart = 0, jcount = 0;
-        if (a.from_bank) {
-            p.id = (uint32_t)i;
-            p.lin = 0;
-            p.e = 0;
-            p.tau = a.tau0;
-            p.w = wbar;
-            if (a.birth) {
-                uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
-                philox4x32_10(r, a.k0, a.k1);
-                p.mu = 2.0 * u01(r[0], r[1]) - 1.0;
-                p.x = a.src_x;
-                if (p.x <= a.edges[0] && p.mu < 0.0 && a.bc_l == 1) p.mu = -p.mu;
-                if (p.x >= a.edges[I] && p.mu > 0.0 && a.bc_r == 1) p.mu = -p.mu;
-                p.cell = (p.mu < 0.0) ? a.birth_cell_neg : a.birth_cell_pos;
-            } else {
-                p.x = a.bx[i];
-                p.mu = a.bmu[i];
-                p.cell = a.bcell[i];
-            }
-        } else {
-            p.x = a.rin.x[i];
-            p.mu = a.rin.mu[i];
-            p.tau = a.rin.tau[i];
-            p.w = a.rin.w[i];
-            p.cell = a.rin.cell[i];
-            p.id = a.rin.id[i];
-            p.lin = a.rin.lin[i];
-            p.e = a.rin.e[i];
-            jstart = a.rin.jstart[i];
-            jcount = a.rin.jcount[i];
-        }
-        const uint32_t ntracks = jcount ? jcount : 1u;
-        for (uint32_t t = 0; t < ntracks; ++t) {
-            P64 q = p;
-            if (jcount) {
-                q.lin = lineage_hash(p.lin, p.e, jstart + t);
-                q.e = 0;
-            }
-            q.inv_mu = 1.0 / q.mu;
-            run_track(a, q, s_tl, s_cen, cnt, tscale, cscale);
         }
     }
     __syncthreads();

@@ -1,0 +1,97 @@
+"""FP32-tracking path: stated tally error against the FP64 results.
+
+The FP32 path draws the same Philox words as the FP64 path (its uniforms are
+their top 23 bits), keeps weights, tallies, closures and the LOSM in FP64 and
+only tracks geometry in FP32.  From the same start a history therefore takes
+the same events unless two of its distances lie within FP32 rounding of each
+other, and the tallies differ by those few diverged histories plus rounding.
+
+Stated bound, per tally kind and step, relative L2 error over cells:
+    || t_fp32 - t_fp64 ||_2 / || phi_fp64 ||_2 <= 1e-5
+for the flux, current and closure tallies (J and F are measured against the
+flux norm because they change sign).  Checked against the oracle on the
+200-cell slab, and against the library's own bit-exact FP64 path on the
+1000-cell slab at its full size of 1e7 particles per step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+hww = pytest.importorskip("paper_2512_19925_gb300")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+BOUND = 1e-5
+KINDS = {"tl_phi": hww.TL_PHI, "tl_J": hww.TL_J, "tl_F": hww.TL_F, "census_phi": hww.CENSUS_PHI,
+         "census_J": hww.CENSUS_J, "census_F": hww.CENSUS_F}
+
+
+def rel_errors(t32, t64):
+    ref = np.linalg.norm(t64["tl_phi"])
+    refc = np.linalg.norm(t64["census_phi"])
+    out = {}
+    for name in KINDS:
+        den = refc if name.startswith("census") else ref
+        out[name] = float(np.linalg.norm(t32[name] - t64[name]) / den)
+    return out
+
+
+def grab(p):
+    return {name: p.get_tallies(kind) for name, kind in KINDS.items()}
+
+
+def step_from_same_state(g, o, w_bar, first):
+    """One step of both from the same start bank and the same windows: the
+    FP32 problem's bank is loaded into the FP64 one, and the windows the FP32
+    step used are imposed on the FP64 step."""
+    if not first:
+        x, mu, cell = g.get_bank()
+        o.set_bank(x, mu, cell, w_bar)
+    s = g.run_step()
+    o.set_ww_centers(g.get_tallies(hww.WW_CENTER))
+    o.run_step()
+    return s
+
+
+@pytest.mark.parametrize("wl_fn,n", [(workloads.plain_slab, 20000), (workloads.shield, 20000)])
+def test_fp32_within_stated_error_of_oracle(wl_fn, n):
+    wl = wl_fn(particles_per_step=n)
+    wl["precision"] = "fp32"
+    g = hww.Problem.from_workload(wl)
+    o = oracle.problem_from_workload(wl)
+    w_bar = 1.0
+    for step in range(1, 6):
+        s = step_from_same_state(g, o, w_bar, step == 1)
+        w_bar = s["w_bar_next"]
+        t64 = {name: o.get_tallies(kind) for name, kind in KINDS.items()}
+        err = rel_errors(grab(g), t64)
+        assert max(err.values()) <= BOUND, (step, err)
+
+
+def test_fp32_full_size_against_fp64_path():
+    # the 1000-cell slab at 1e7 particles per step, the benchmark's launch
+    # configuration; the FP64 library path equals the oracle bit for bit
+    wl = workloads.plain_at_scale(particles_per_step=10_000_000)
+    p32 = hww.Problem.from_workload(wl, precision=hww.FP32_TRACK)
+    p64 = hww.Problem.from_workload(wl, precision=hww.FP64)
+    w_bar = 1.0
+    for step in range(1, 4):
+        if step > 1:
+            x, mu, cell = p32.get_bank()
+            p64.set_bank(x, mu, cell, w_bar)
+        s32 = p32.run_step()
+        p64.set_ww_centers(p32.get_tallies(hww.WW_CENTER))
+        s64 = p64.run_step()
+        w_bar = s32["w_bar_next"]
+        for s in (s32, s64):
+            assert s["n_start"] + s["daughters"] - s["absorbed"] - s["roulette_kills"] - s["leaked"] == s["census"]
+            assert s["n_next"] == wl["particles_per_step"]
+        # diverged histories are a tiny fraction of the population
+        assert abs(s32["segments"] - s64["segments"]) <= 1e-4 * s64["segments"]
+        err = rel_errors(grab(p32), grab(p64))
+        assert max(err.values()) <= BOUND, (step, err)

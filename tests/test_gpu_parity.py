@@ -200,3 +200,26 @@ def test_census_bank_matches_oracle_histories():
         ko = np.lexsort((co["lin"], co["id"]))
         for f in ("x", "mu", "w", "cell", "id", "lin"):
             assert np.array_equal(cg[f][kg], co[f][ko]), (n, f)
+
+
+def test_overflow_regrow_replays_bit_identically():
+    # a census/queue capacity far below what the step needs: the library
+    # doubles its buffers and replays the step, with the oracle's result
+    wl = workloads.shield(particles_per_step=6007, precision="fp64")
+    g = hww.Problem.from_workload(wl, bank_capacity=512)
+    o = oracle.problem_from_workload(wl)
+    for n in range(4):
+        assert_step_parity(g, o, n + 1)
+    c = g.counters()
+    assert c["census_capacity"] > 512
+
+
+def test_launch_accounting():
+    wl = workloads.plain_slab(particles_per_step=3001)
+    g = hww.Problem.from_workload(wl)
+    g.set_timing(True)
+    s = g.run_step()
+    c = g.counters()
+    assert c["track_launches"] == s["waves"]
+    assert c["kernel_launches"] >= s["waves"] + 6
+    assert c["track_ms"] > 0.0
