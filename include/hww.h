@@ -78,7 +78,7 @@ enum {
     HWW_CENSUS_PHI = 3,  /* [[phi]]_i^n, Eq. (ct-mc)                       [I]   */
     HWW_CENSUS_J = 4,    /* census current                                [I]   */
     HWW_CENSUS_F = 5,    /* census closure F_i^n, Eq. (F)                  [I]   */
-    HWW_BATCH_PHI = 6,   /* <phi> per variance batch b = id mod B          [B*I] */
+    HWW_BATCH_PHI = 6,   /* <phi> per variance batch b = floor(id B / N)   [B*I] */
     HWW_BOUNDARY = 7,    /* phi_L, F_L, P_L, phi_R, F_R, P_R time averages [6]   */
     HWW_WW_CENTER = 8,   /* window centers used in the step               [I]   */
     HWW_CLOSURE_PHI = 9, /* IC / closure vectors built at t^n            [I+2] */
@@ -94,7 +94,7 @@ typedef struct {
     double dt;                /* time step > 0 */
     int32_t bc_left, bc_right;/* HWW_BC_VACUUM | HWW_BC_REFLECT */
     double src_x;             /* unit isotropic plane pulse at t = 0, in [edges[0], edges[I]] */
-    int64_t particles_per_step; /* N, 1 <= N < 2^31 */
+    int64_t particles_per_step; /* N, 1 <= N < 2^30 */
     uint64_t seed;            /* Philox key (with the step index) */
     int32_t precision;        /* HWW_FP64 | HWW_FP32_TRACK */
     double theta;             /* 0.5 Crank-Nicolson | 1.0 backward Euler */

@@ -109,7 +109,7 @@ def lib():
                                         C.c_int32, C.c_int32, dp, dp, dp, dp, C.c_double,
                                         C.c_double, dp, dp, dp, dp]
             L.or_comb.argtypes = [C.c_int64, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64),
-                                  C.POINTER(C.c_uint64), C.c_int64, C.c_double,
+                                  C.POINTER(C.c_uint64), C.c_int64, C.c_uint32,
                                   C.POINTER(C.c_int32)]
             _lib = L
     return _lib
@@ -179,15 +179,16 @@ def losm_solve(dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, phi_old, J
     return phi, J
 
 
-def comb(ids, lins, wfx, n, u):
-    """Uniform comb; returns for each of the n new slots the index of its source."""
+def comb(ids, lins, wfx, n, U):
+    """Uniform comb with tooth offset (2U+1)/2^33 (U a 32-bit word); returns
+    for each of the n new slots the index of its source."""
     ids = np.ascontiguousarray(ids, dtype=np.uint32)
     lins = np.ascontiguousarray(lins, dtype=np.uint64)
     wfx = np.ascontiguousarray(wfx, dtype=np.uint64)
     out = np.empty(int(n), dtype=np.int32)
     rc = lib().or_comb(ids.size, ids.ctypes.data_as(C.POINTER(C.c_uint32)),
                        lins.ctypes.data_as(C.POINTER(C.c_uint64)),
-                       wfx.ctypes.data_as(C.POINTER(C.c_uint64)), int(n), float(u),
+                       wfx.ctypes.data_as(C.POINTER(C.c_uint64)), int(n), int(U) & 0xFFFFFFFF,
                        out.ctypes.data_as(C.POINTER(C.c_int32)))
     _check(rc, "comb")
     return out

@@ -207,7 +207,7 @@ int or_create(const or_desc* d, or_problem** out) {
     *out = NULL;
     int32_t I = d->n_cells;
     if (I < 1 || !d->edges || !(d->v > 0) || !(d->dt > 0) || d->particles_per_step < 1 ||
-        d->particles_per_step > 0x7fffffffLL || (d->theta != 0.5 && d->theta != 1.0) ||
+        d->particles_per_step >= (1LL << 30) || (d->theta != 0.5 && d->theta != 1.0) ||
         d->n_var_batches < 1 || d->bc_left < 0 || d->bc_left > 1 || d->bc_right < 0 ||
         d->bc_right > 1 || d->filter < 0 || d->filter > 1 || (d->filter == 1 && d->filter_k < 1))
         return E_ARG;
@@ -451,11 +451,12 @@ int or_losm_solve(int32_t I, const double* dx, const double* sigma_t, const doub
 /* ------------------------------------------------------------------------ */
 /* Uniform comb (Sec. 5.1)                                                   */
 /* Census particles in canonical order (source id, then lineage key) occupy */
-/* consecutive intervals of their fixed-point weights on [0, W).  Teeth sit */
-/* at (k + u) W / N, k = 0..N-1; tooth k becomes particle k of the next     */
-/* step.  The first tooth at or after a cumulative weight C is              */
-/* ceil(N C / W - u) evaluated in doubles (monotone in C), with C = W       */
-/* mapped to N so the copy counts sum to exactly N.                         */
+/* consecutive intervals of their fixed-point weights on [0, W).  Tooth k   */
+/* sits at T_k = (k + (2U+1)/2^33) W / N, k = 0..N-1, with U a 32-bit      */
+/* uniform word; tooth k becomes particle k of the next step.  The first    */
+/* tooth at or after a cumulative weight C is the least k with T_k >= C,    */
+/* i.e. ceil((N C 2^33 - (2U+1) W) / (W 2^33)) clamped to [0, N], computed  */
+/* exactly in 128-bit integers, so the copy counts sum to exactly N.        */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     uint32_t id;
@@ -471,17 +472,19 @@ static int key_cmp(const void* A, const void* B) {
     return 0;
 }
 
-static int64_t first_tooth(uint64_t C, uint64_t W, int64_t N, double u) {
-    if (C == W) return N;
-    double q = ((double)N * (double)C) / (double)W - u;
-    double k = ceil(q);
-    if (k < 0.0) return 0;
-    if (k > (double)N) return N;
+static int64_t first_tooth(uint64_t C, uint64_t W, int64_t N, uint32_t U) {
+    typedef unsigned __int128 u128;
+    const u128 num = ((u128)(uint64_t)N * C) << 33;
+    const u128 sub = (u128)(2ull * U + 1ull) * W;
+    if (num <= sub) return 0;
+    const u128 den = (u128)W << 33;
+    const u128 k = (num - sub + den - 1) / den;
+    if (k > (u128)N) return N;
     return (int64_t)k;
 }
 
 int or_comb(int64_t m, const uint32_t* id, const uint64_t* lin, const uint64_t* wfx, int64_t n,
-            double u, int32_t* src_of_slot) {
+            uint32_t U, int32_t* src_of_slot) {
     if (m < 0 || n < 0 || !src_of_slot || (m > 0 && (!id || !lin || !wfx))) return E_ARG;
     or_key* k = (or_key*)xcalloc(m, sizeof(or_key));
     if (!k) return E_OOM;
@@ -500,9 +503,9 @@ int or_comb(int64_t m, const uint32_t* id, const uint64_t* lin, const uint64_t* 
     }
     uint64_t C = 0;
     for (int64_t j = 0; j < m; ++j) {
-        int64_t k0 = first_tooth(C, W, n, u);
+        int64_t k0 = first_tooth(C, W, n, U);
         C += wfx[k[j].idx];
-        int64_t k1 = first_tooth(C, W, n, u);
+        int64_t k1 = first_tooth(C, W, n, U);
         for (int64_t s = k0; s < k1; ++s) src_of_slot[s] = (int32_t)k[j].idx;
     }
     free(k);
@@ -801,7 +804,7 @@ int or_run_step(or_problem* p, or_stats* st) {
             p->tl_phi[k] += to_fixed(wl, S);
             p->tl_j[k] += to_fixed(wlmu, S);
             p->tl_f[k] += to_fixed(wlf, S);
-            p->batch[(int64_t)(q.id % (uint32_t)B) * I + k] += to_fixed(wl, S);
+            p->batch[(int64_t)(((uint64_t)q.id * (uint64_t)B) / (uint64_t)N) * I + k] += to_fixed(wl, S);
             s.segments++;
             /* move */
             if (ev == 1) {
@@ -957,8 +960,7 @@ int or_run_step(or_problem* p, or_stats* st) {
         }
         uint32_t cctr[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xC0B0u}, r[4];
         or_philox4x32_10(cctr, key, r);
-        const double u = or_u01(r[0], r[1]);
-        or_comb(m, ids, lins, wfx, N, u, src);
+        or_comb(m, ids, lins, wfx, N, r[1], src);
         free(p->bx); free(p->bmu); free(p->bcell);
         p->bx = xcalloc(N, sizeof(double));
         p->bmu = xcalloc(N, sizeof(double));
@@ -1022,7 +1024,8 @@ int or_get_tallies(const or_problem* p, int32_t kind, double* out, int64_t n) {
     case K_BATCH_PHI: {
         if (n < (int64_t)I * B) return E_ARG;
         for (int32_t b = 0; b < B; ++b) {
-            const int64_t nb = (b < N) ? (N - b - 1) / B + 1 : 0; /* ids with id mod B == b */
+            /* ids with floor(id B / N) == b: ceil(b N / B) .. ceil((b+1) N / B) - 1 */
+            const int64_t nb = ((b + 1) * N + B - 1) / B - (b * N + B - 1) / B;
             for (int32_t i = 0; i < I; ++i)
                 out[(int64_t)b * I + i] =
                     nb ? ldexp(conv128(p->batch[(int64_t)b * I + i]), -S) / (((double)nb * p->dx[i]) * dt)

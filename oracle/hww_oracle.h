@@ -28,7 +28,7 @@ typedef struct {
     double v, dt;
     int32_t bc_left, bc_right;    /* 0 vacuum, 1 reflecting */
     double src_x;                 /* unit isotropic plane pulse at t = 0 */
-    int64_t particles_per_step;
+    int64_t particles_per_step;  /* 1 <= N < 2^30 */
     uint64_t seed;
     double theta;                 /* 0.5 Crank-Nicolson, 1.0 backward Euler */
     int32_t filter, filter_k;     /* 0 none, 1 moving average of base k */
@@ -74,7 +74,7 @@ int or_losm_solve(int32_t n_cells, const double* dx, const double* sigma_t, cons
                   const double* q_old, const double* q_new,
                   double* phi_new, double* J_new);
 int or_comb(int64_t m, const uint32_t* id, const uint64_t* lin, const uint64_t* wfx,
-            int64_t n, double u, int32_t* src_of_slot);
+            int64_t n, uint32_t U, int32_t* src_of_slot);
 
 #ifdef __cplusplus
 }

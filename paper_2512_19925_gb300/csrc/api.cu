@@ -229,6 +229,7 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b, uint32_t k
     TrackArgs<Real> a{};
     a.I = p->I;
     a.B = p->B;
+    a.N = p->N;
     a.emax = 64;
     a.ww_on = (p->mode == HWW_MODE_HWW) || (p->mode == HWW_MODE_LWW && p->has_prev_tl) || p->has_override;
     a.bc_l = p->d.bc_left;
@@ -388,7 +389,7 @@ __global__ void normalize_kernel(int kind, const Acc128* a, int n, int I, int B,
             r = (v * val) / ((double)N * dx[i]);
         } else if (kind == HWW_BATCH_PHI) {
             const int b = i / I, k = i % I;
-            const long long nb = (b < N) ? (N - b - 1) / B + 1 : 0;
+            const long long nb = ((b + 1) * N + B - 1) / B - (b * N + B - 1) / B;
             r = nb ? val / (((double)nb * dx[k]) * dt) : 0.0;
         } else {
             r = val / ((double)N * dt);
@@ -463,7 +464,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     if (!d || !d->edges) return HWW_ERR_ARG;
     const int I = d->n_cells;
     if (I < 1 || I > MAX_CELLS || !(d->v > 0) || !(d->dt > 0) || !std::isfinite(d->v * d->dt) ||
-        d->particles_per_step < 1 || d->particles_per_step >= (1LL << 31) ||
+        d->particles_per_step < 1 || d->particles_per_step >= (1LL << 30) ||
         (d->theta != 0.5 && d->theta != 1.0) || d->n_var_batches < 1 || d->n_var_batches > 64 ||
         d->bc_left < 0 || d->bc_left > 1 || d->bc_right < 0 || d->bc_right > 1 || d->filter < 0 ||
         d->filter > 1 || (d->filter == 1 && d->filter_k < 1) || d->precision < 0 || d->precision > 1 ||
@@ -837,8 +838,15 @@ hww_status get_tallies_raw(const hww_problem* p, int32_t kind, int64_t* out, int
     case HWW_BOUNDARY: src = p->bnd; len = 6; break;
     }
     if (n < 2 * len) return HWW_ERR_ARG;
-    HWW_CK(cudaMemcpyAsync(out, src, sizeof(Acc128) * len, cudaMemcpyDeviceToHost, p->stream));
+    // the device keeps split sums; report the exact 128-bit values
+    std::vector<Acc128> h(len);
+    HWW_CK(cudaMemcpyAsync(h.data(), src, sizeof(Acc128) * len, cudaMemcpyDeviceToHost, p->stream));
     HWW_CK(cudaStreamSynchronize(p->stream));
+    for (long long i = 0; i < len; ++i) {
+        const I128 v = acc_value(h[i]);
+        out[2 * i] = (int64_t)v.lo;
+        out[2 * i + 1] = (int64_t)v.hi;
+    }
     return HWW_OK;
 }
 

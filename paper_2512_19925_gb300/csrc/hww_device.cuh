@@ -12,9 +12,9 @@
 //   * log: reduction to m in [sqrt(1/2), sqrt(2)) and the atanh series
 //     2s(1 + z/3 + ... + z^11/23), z = s^2, s = (m-1)/(m+1), by Horner with
 //     fused multiply-adds, plus k ln 2 (ln 2 split in a 32-bit head and a tail);
-//   * tallies: contributions rounded to nearest-even 64-bit integers at a
-//     power-of-two scale, summed as 128-bit integers, so that any order of
-//     summation gives the same bits.
+//   * tallies: contributions rounded to 64-bit integers at a power-of-two
+//     scale, summed as 128-bit integers, so that any order of summation
+//     gives the same bits.
 // FP64 translation units are built with contraction off, so every a*b+c
 // below is two roundings unless fma() is written.
 #pragma once
@@ -23,10 +23,29 @@
 
 namespace hww {
 
+// A 128-bit sum kept in split form so that every update is a pair of
+// fire-and-forget reductions (no returned value, no carry test):
+//   lo = sum of the low 32-bit halves of the addends (unsigned),
+//   hi = sum of the high 32-bit halves (signed, arithmetic shift),
+// value = hi 2^32 + lo exactly, as long as fewer than 2^32 addends reach one
+// accumulator (each low half is below 2^32).
 struct Acc128 {
     unsigned long long lo;
     long long hi;
 };
+
+// exact 128-bit value (high word, low word) of a split accumulator
+struct I128 {
+    long long hi;
+    unsigned long long lo;
+};
+
+__host__ __device__ __forceinline__ I128 acc_value(Acc128 a) {
+    const unsigned long long shifted = (unsigned long long)a.hi << 32;
+    const unsigned long long low = shifted + a.lo;
+    const long long carry = (low < a.lo) ? 1 : 0;
+    return I128{(a.hi >> 32) + carry, low};
+}
 
 __host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -102,24 +121,23 @@ __device__ __forceinline__ long long to_fixed(double x, double scale) {
     return __double2ll_rn(x * scale);
 }
 
-// 128-bit accumulation with two 64-bit atomics: the low word returns its old
-// value, so the carry out of it is known exactly
+// add a signed 64-bit value to a split accumulator
 __device__ __forceinline__ void add128(Acc128* a, long long v) {
     if (v == 0) return;
-    const unsigned long long lo = (unsigned long long)v;
-    const unsigned long long old = atomicAdd(&a->lo, lo);
-    long long hi = (v < 0) ? -1 : 0;
-    if (old + lo < old) hi += 1;
-    if (hi != 0) atomicAdd((unsigned long long*)&a->hi, (unsigned long long)hi);
+    atomicAdd(&a->lo, (unsigned long long)(unsigned)(v & 0xFFFFFFFFll));
+    const long long h = v >> 32;
+    if (h != 0) atomicAdd((unsigned long long*)&a->hi, (unsigned long long)h);
 }
 
 // 128-bit value to double: one rounding when it fits a signed 64-bit
 // integer, else hi*2^64 + lo
-__host__ __device__ __forceinline__ double acc_to_double(Acc128 a) {
-    const bool fits = (a.hi == 0 && (long long)a.lo >= 0) || (a.hi == -1 && (long long)a.lo < 0);
-    if (fits) return (double)(long long)a.lo;
-    return (double)a.hi * 0x1p64 + (double)a.lo;
+__host__ __device__ __forceinline__ double i128_to_double(I128 v) {
+    const bool fits = (v.hi == 0 && (long long)v.lo >= 0) || (v.hi == -1 && (long long)v.lo < 0);
+    if (fits) return (double)(long long)v.lo;
+    return (double)v.hi * 0x1p64 + (double)v.lo;
 }
+
+__host__ __device__ __forceinline__ double acc_to_double(Acc128 a) { return i128_to_double(acc_value(a)); }
 
 // 2^e as a double for -1022 <= e <= 1023
 __host__ __device__ __forceinline__ double pow2(int e) {

@@ -43,9 +43,10 @@ struct StepDev {
     double wbar;     // weight of each start-bank particle
     double tscale;   // 2^S, tally fixed-point scale
     double cscale;   // 2^Sc, comb weight fixed-point scale
-    double u_comb;   // comb offset in [0,1)
     int S, Sc;
-    int pad0, pad1;
+    unsigned U_comb; // comb offset word: teeth at (k + (2U+1)/2^33) W / N
+    int pad0;
+    double pad1;
     unsigned long long nbank;      // start-bank size
     unsigned long long W;          // total census weight (fixed point)
     unsigned long long ncensus;    // census bank size of the step
@@ -82,6 +83,7 @@ struct CenQ {
 template <class Real>
 struct TrackArgs {
     int I, B, emax;
+    long long N;      // source particles per step (variance batches)
     int ww_on;
     int from_bank, birth;
     int bc_l, bc_r;

@@ -267,7 +267,7 @@ __global__ void step_scalars_kernel(StepDev* sd, int nbits, uint32_t k0, uint32_
     sd->cscale = pow2(sd->Sc);
     uint32_t r[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xC0B0u};
     philox4x32_10(r, k0, k1);
-    sd->u_comb = u01(r[0], r[1]);
+    sd->U_comb = r[1];
     stats[ST_NSTART] = sd->nbank;
 }
 

@@ -138,14 +138,28 @@ __global__ void comb_scatter_kernel(CombArgs<Real> a) {
     }
 }
 
-__device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned long long W,
-                                                 long long N, double u) {
-    if (C == W) return N;
-    const double q = ((double)N * (double)C) / (double)W - u;
-    const double k = ceil(q);
-    if (k < 0.0) return 0;
-    if (k > (double)N) return N;
-    return (long long)k;
+// T_k >= C for tooth k at T_k = (k + (2U+1)/2^33) W / N, decided exactly:
+// (k 2^33 + 2U + 1) W >= N C 2^33 in 128-bit integers
+__device__ __forceinline__ bool tooth_at_or_after(long long k, unsigned long long C, unsigned long long W,
+                                                  long long N, unsigned U) {
+    const unsigned long long a = ((unsigned long long)k << 33) + 2ull * U + 1ull;
+    const unsigned long long lh = __umul64hi(a, W), ll = a * W;
+    const unsigned long long th = __umul64hi((unsigned long long)N, C), tl = (unsigned long long)N * C;
+    const unsigned long long rh = (th << 33) | (tl >> 31), rl = tl << 33;
+    return (lh > rh) || (lh == rh && ll >= rl);
+}
+
+// least k in [0, N] with T_k >= C: an integer estimate from the top 32 bits
+// of W and C, then exact steps (the estimate is within two of the answer)
+__device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned long long W, long long N,
+                                                 unsigned U) {
+    const int sh = max(0, 64 - __clzll((long long)W) - 32);
+    const unsigned long long Wr = W >> sh, Cr = C >> sh;
+    long long k = Wr ? (long long)((Cr * (unsigned long long)N) / Wr) : 0;
+    if (k > N) k = N;
+    for (int it = 0; it < 64 && k > 0 && tooth_at_or_after(k - 1, C, W, N, U); ++it) --k;
+    for (int it = 0; it < 64 && k < N && !tooth_at_or_after(k, C, W, N, U); ++it) ++k;
+    return k;
 }
 
 template <class Real>
@@ -154,7 +168,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
     const unsigned long long W = a.goff_w[a.N];
     const double cscale = a.sd->cscale;
-    const double u = a.sd->u_comb;
+    const unsigned U = a.sd->U_comb;
     unsigned long long coll = 0;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
@@ -175,8 +189,8 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
                 }
             }
         }
-        const long long k0 = first_tooth(C0, W, a.N, u);
-        const long long k1 = first_tooth(C0 + wj, W, a.N, u);
+        const long long k0 = first_tooth(C0, W, a.N, U);
+        const long long k1 = first_tooth(C0 + wj, W, a.N, U);
         const Real x = a.cx[j];
         const Real mu = a.cmu[j];
         const int32_t cell = a.ccell[j];

@@ -82,7 +82,7 @@ __device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32
     a.rout.jcount[slot] = jcount;
 }
 
-__global__ void __launch_bounds__(256) track32_kernel(TrackArgs<float> a) {
+__global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
     extern __shared__ long long sm[];
     const int I = a.I;
     long long* s_tl = sm;
@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(256) track32_kernel(TrackArgs<float> a) {
     uint32_t jnext = 0, jend = 0;
     bool have = false;
     int evs = 0;
+    int qb = 0;  // variance batch of the current track's source id
     for (;;) {
         if (!have) {
             if (jnext < jend) {
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(256) track32_kernel(TrackArgs<float> a) {
             q.inv_mu = 1.0f / q.mu;
             have = true;
             evs = 0;
+            qb = batch_of(q.id, a.B, a.N);
         }
         // ---- one event ----
         if (evs == a.emax) {
@@ -198,11 +200,16 @@ __global__ void __launch_bounds__(256) track32_kernel(TrackArgs<float> a) {
         }
         const float m2 = q.mu * q.mu;
         const float f3 = 1.0f / 3.0f - m2;
-        const long long fphi = fx_mul(q.W, l);
-        sadd(&s_tl[k], fphi);
-        sadd(&s_tl[I + k], fx_mul(q.W, l * q.mu));
-        sadd(&s_tl[2 * I + k], fx_mul(q.W, l * f3));
-        add128(&a.batch[(long long)(q.id % (uint32_t)a.B) * I + k], fphi);
+        {
+            const int b = qb;
+            const Agg3 g = warp_agg3(k * a.B + b, fx_mul(q.W, l), fx_mul(q.W, l * q.mu), fx_mul(q.W, l * f3));
+            if (g.leader) {
+                sadd(&s_tl[k], g.s0);
+                sadd(&s_tl[I + k], g.s1);
+                sadd(&s_tl[2 * I + k], g.s2);
+                add128(&a.batch[(long long)b * I + k], g.s0);
+            }
+        }
         cnt.v[ST_SEGMENTS]++;
         if (ev != 1) q.xo = fminf(fmaxf(fmaf(q.mu, l, q.xo), 0.0f), dxk);
         q.tau = (ev == 0) ? 0.0f : q.tau - l;
@@ -210,9 +217,14 @@ __global__ void __launch_bounds__(256) track32_kernel(TrackArgs<float> a) {
         q.e = q.e + 1;
         ++evs;
         if (ev == 0) {
-            sadd(&s_cen[k], q.W);
-            sadd(&s_cen[I + k], fx_mul(q.W, q.mu));
-            sadd(&s_cen[2 * I + k], fx_mul(q.W, f3));
+            {
+                const Agg3 g = warp_agg3(k, q.W, fx_mul(q.W, q.mu), fx_mul(q.W, f3));
+                if (g.leader) {
+                    sadd(&s_cen[k], g.s0);
+                    sadd(&s_cen[I + k], g.s1);
+                    sadd(&s_cen[2 * I + k], g.s2);
+                }
+            }
             const unsigned long long slot = warp_reserve(a.cen.count);
             if ((long long)slot < a.cen.cap) {
                 a.cen.x[slot] = q.xo;

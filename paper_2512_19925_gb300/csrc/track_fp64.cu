@@ -57,7 +57,7 @@ __device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P6
     a.rout.jcount[slot] = jcount;
 }
 
-__global__ void __launch_bounds__(256) track64_kernel(TrackArgs<double> a) {
+__global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
     extern __shared__ long long sm[];
     const int I = a.I;
     long long* s_tl = sm;
@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(256) track64_kernel(TrackArgs<double> a) {
     uint32_t jnext = 0, jend = 0;
     bool have = false;
     int evs = 0;
+    int qb = 0;  // variance batch of the current track's source id
     for (;;) {
         if (!have) {
             if (jnext < jend) {
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(256) track64_kernel(TrackArgs<double> a) {
             q.inv_mu = 1.0 / q.mu;
             have = true;
             evs = 0;
+            qb = batch_of(q.id, a.B, a.N);
         }
         // ---- one event ----
         if (evs == a.emax) {
@@ -173,11 +175,17 @@ __global__ void __launch_bounds__(256) track64_kernel(TrackArgs<double> a) {
         const double wl = q.w * l;
         const double wlmu = wl * q.mu;
         const double wlf = wl * (1.0 / 3.0 - q.mu * q.mu);
-        const long long fphi = to_fixed(wl, tscale);
-        sadd(&s_tl[k], fphi);
-        sadd(&s_tl[I + k], to_fixed(wlmu, tscale));
-        sadd(&s_tl[2 * I + k], to_fixed(wlf, tscale));
-        add128(&a.batch[(long long)(q.id % (uint32_t)a.B) * I + k], fphi);
+        {
+            const int b = qb;
+            const Agg3 g = warp_agg3(k * a.B + b, to_fixed(wl, tscale), to_fixed(wlmu, tscale),
+                                     to_fixed(wlf, tscale));
+            if (g.leader) {
+                sadd(&s_tl[k], g.s0);
+                sadd(&s_tl[I + k], g.s1);
+                sadd(&s_tl[2 * I + k], g.s2);
+                add128(&a.batch[(long long)b * I + k], g.s0);
+            }
+        }
         cnt.v[ST_SEGMENTS]++;
         // move
         if (ev == 1) {
@@ -195,9 +203,14 @@ __global__ void __launch_bounds__(256) track64_kernel(TrackArgs<double> a) {
         if (ev == 0) {
             const double wmu = q.w * q.mu;
             const double wf = q.w * (1.0 / 3.0 - q.mu * q.mu);
-            sadd(&s_cen[k], to_fixed(q.w, tscale));
-            sadd(&s_cen[I + k], to_fixed(wmu, tscale));
-            sadd(&s_cen[2 * I + k], to_fixed(wf, tscale));
+            {
+                const Agg3 g = warp_agg3(k, to_fixed(q.w, tscale), to_fixed(wmu, tscale), to_fixed(wf, tscale));
+                if (g.leader) {
+                    sadd(&s_cen[k], g.s0);
+                    sadd(&s_cen[I + k], g.s1);
+                    sadd(&s_cen[2 * I + k], g.s2);
+                }
+            }
             const unsigned long long slot = warp_reserve(a.cen.count);
             if ((long long)slot < a.cen.cap) {
                 a.cen.x[slot] = q.x;

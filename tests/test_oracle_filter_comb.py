@@ -7,9 +7,11 @@ symmetrically (the reading of "adaptively decreased"), so constants and
 linear data pass unchanged everywhere.
 
 Comb: teeth spaced W/N apart give every particle floor or ceil of
-N w_j / W copies for every offset u, exactly N copies in total, the
-expected copy count N w_j / W when u is uniform, and a result that does not
-depend on the order the census particles are handed in."""
+N w_j / W copies for every offset, exactly N copies in total, the expected
+copy count N w_j / W when the offset is uniform, a result that does not
+depend on the order the census particles are handed in, and teeth that sit
+where the definition T_k = (k + (2U+1)/2^33) W / N puts them (checked with
+Python's exact integers)."""
 import numpy as np
 import pytest
 
@@ -60,8 +62,8 @@ def _census(m, seed):
 def test_comb_copy_counts_are_floor_or_ceil(m, n):
     ids, lins, wfx = _census(m, m * 7 + n)
     W = int(wfx.sum())
-    for u in (0.0, 0.1234, 0.5, 0.999999):
-        src = oracle.comb(ids, lins, wfx, n, u)
+    for U in (0, 529984421, 2 ** 31, 2 ** 32 - 1):
+        src = oracle.comb(ids, lins, wfx, n, U)
         assert np.all(src >= 0)  # all n slots filled
         counts = np.bincount(src, minlength=m)
         assert counts.sum() == n
@@ -74,33 +76,55 @@ def test_comb_expected_counts_over_uniform_offset():
     m, n = 40, 25
     ids, lins, wfx = _census(m, 4)
     W = float(wfx.sum())
-    us = (np.arange(4000) + 0.5) / 4000.0
+    Us = (np.arange(4000) * (2 ** 32 // 4000)).astype(np.int64)
     acc = np.zeros(m)
-    for u in us:
-        acc += np.bincount(oracle.comb(ids, lins, wfx, n, u), minlength=m)
-    assert np.allclose(acc / len(us), n * wfx / W, atol=2e-3)
+    for U in Us:
+        acc += np.bincount(oracle.comb(ids, lins, wfx, n, int(U)), minlength=m)
+    assert np.allclose(acc / len(Us), n * wfx / W, atol=2e-3)
 
 
 def test_comb_is_order_independent():
     m, n = 300, 120
     ids, lins, wfx = _census(m, 9)
-    src = oracle.comb(ids, lins, wfx, n, 0.37)
+    src = oracle.comb(ids, lins, wfx, n, 1589137899)
     perm = np.random.default_rng(1).permutation(m)
-    src_p = oracle.comb(ids[perm], lins[perm], wfx[perm], n, 0.37)
+    src_p = oracle.comb(ids[perm], lins[perm], wfx[perm], n, 1589137899)
     assert np.array_equal(perm[src_p], src)
 
 
 def test_comb_slots_follow_canonical_order():
     m, n = 120, 300
     ids, lins, wfx = _census(m, 2)
-    src = oracle.comb(ids, lins, wfx, n, 0.61)
+    src = oracle.comb(ids, lins, wfx, n, 2619930050)
     keys = [(int(ids[j]), int(lins[j])) for j in src]
     assert keys == sorted(keys)
 
 
+def test_comb_teeth_sit_at_the_defined_positions():
+    # brute force with exact integers: tooth k belongs to the particle whose
+    # interval [C_j, C_j + w_j) contains T_k = (k + (2U+1)/2^33) W / N
+    m, n = 60, 97
+    ids, lins, wfx = _census(m, 12)
+    order = sorted(range(m), key=lambda j: (int(ids[j]), int(lins[j])))
+    for U in (0, 12345, 2 ** 32 - 1):
+        src = oracle.comb(ids, lins, wfx, n, U)
+        W = sum(int(w) for w in wfx)
+        C = 0
+        owner = {}
+        for j in order:
+            lo, hi = C, C + int(wfx[j])
+            C = hi
+            for k in range(n):
+                # T_k in [lo, hi)  <=>  lo N 2^33 <= (k 2^33 + 2U + 1) W < hi N 2^33
+                t = (k * 2 ** 33 + 2 * U + 1) * W
+                if lo * n * 2 ** 33 <= t < hi * n * 2 ** 33:
+                    owner[k] = j
+        assert [owner[k] for k in range(n)] == list(src)
+
+
 def test_comb_empty_and_zero_weight():
-    src = oracle.comb(np.zeros(0, np.uint32), np.zeros(0, np.uint64), np.zeros(0, np.uint64), 5, 0.3)
+    src = oracle.comb(np.zeros(0, np.uint32), np.zeros(0, np.uint64), np.zeros(0, np.uint64), 5, 77)
     assert np.all(src == -1)
     src = oracle.comb(np.array([1, 2], np.uint32), np.array([0, 0], np.uint64),
-                      np.array([0, 7], np.uint64), 4, 0.3)
+                      np.array([0, 7], np.uint64), 4, 77)
     assert np.all(src == 1)
