@@ -221,6 +221,33 @@ hww_status hww_losm_solve(int32_t n_cells, const double* dx, const double* sigma
                           double PL_new, double PR_new, const double* q_old, const double* q_new,
                           double* phi_new, double* J_new);
 
+/* The same LOSM solve as hww_losm_solve, for callers that cannot let the
+ * library allocate device memory: an application whose device memory is
+ * handed out up front by its own pool, a latency-critical loop in which
+ * cudaMalloc / cudaFree would synchronize the device, or a process whose
+ * policy forbids new device allocations after start-up.  The paper has no
+ * counterpart; this is a service of the library.
+ *
+ * Arguments, layouts and results are those of hww_losm_solve (host arrays,
+ * synchronous, on the current device).  Instead of allocating, the call
+ * stages everything in a fixed device array compiled into the library,
+ * sized for n_cells <= HWW_NOALLOC_MAX_CELLS (about 0.8 MB, held on every
+ * GPU that loads the library until the process exits); larger n_cells
+ * return HWW_ERR_ARG.  The first call on a device looks up that array's
+ * device address, with the device current; make this first call before
+ * any stream capture.  The call uses no cudaMalloc, cudaFree or other
+ * allocating routine.  All calls on a device share the array, which keeps
+ * the previous call's contents (the call clears what must start at zero),
+ * so calls that overlap on the GPU, for instance from two host threads at
+ * the same time, race. */
+#define HWW_NOALLOC_MAX_CELLS 4096
+hww_status hww_losm_solve_noalloc(int32_t n_cells, const double* dx, const double* sigma_t,
+                                  const double* sigma_a, double v, double dt, double theta,
+                                  int32_t bc_left, int32_t bc_right, const double* phi_old,
+                                  const double* J_old, const double* F_old, const double* F_new,
+                                  double PL_new, double PR_new, const double* q_old,
+                                  const double* q_new, double* phi_new, double* J_new);
+
 /* Philox4x32-10 of n consecutive counters {c0 + i, c1, c2, c3} under key
  * (k0, k1), computed by the library's device generator; out holds 4 n
  * words (host).  Synchronous.  Used to check the generator. */

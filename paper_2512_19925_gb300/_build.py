@@ -26,6 +26,7 @@ UNITS = {
     "api.cu": ["-fmad=false"],
     "step.cu": ["-fmad=false"],
     "losm.cu": ["-fmad=false"],
+    "noalloc.cu": ["-fmad=false"],
     "track_fp64.cu": ["-fmad=false"],
     "track_fp32.cu": [],
 }
