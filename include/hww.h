@@ -186,6 +186,46 @@ hww_status set_bank(hww_problem* p, const double* x, const double* mu, const int
 hww_status get_census(const hww_problem* p, double* x, double* mu, double* w, int32_t* cell,
                       uint32_t* id, uint64_t* lin, int64_t cap, int64_t* n);
 
+/* ---------------------------------------------------------------------
+ * Batches: many independent problems stepped together on one GPU (problems
+ * of uneven size and window settings).  Each member is an ordinary problem
+ * (configure it with set_cross_sections / set_ww_params and read it with
+ * the get_* calls through batch_problem).  A batch step runs, on the
+ * batch's stream:
+ *   - one CUDA graph with the pre-tracking stage of every member (step
+ *     scalars, semi-implicit HLOSM, windows) as parallel branches;
+ *   - per tracking wave, one persistent launch over all members: blocks
+ *     pop tiles (member, id range) from a device counter, so members of
+ *     very different sizes share the GPU without a launch per member;
+ *   - one CUDA graph with the post-tracking stage of every member
+ *     (closures, fully implicit HLOSM, comb).
+ * Results are bit-identical to stepping each member alone: the tile size
+ * and the event budget change only the order of integer tally additions.
+ * The graphs are recorded on the first step; changing a member's window
+ * mode or scaling afterwards is not supported.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    int64_t problems, segments, census, daughters, roulette_kills, absorbed, leaked;
+    int32_t waves;
+    int32_t status;   /* worst hww_status over the members */
+} hww_batch_stats;
+
+/* Create n problems (n <= 1024) from descs (all with the same precision and
+ * no derivative tallies; their cuda_stream and device fields are ignored).
+ * Work is enqueued on `cuda_stream` of `device`. */
+hww_status create_batch(const hww_problem_desc* descs, int32_t n, void* cuda_stream, int32_t device,
+                        hww_batch** out);
+/* Member i of the batch (owned by the batch; do not destroy it). */
+hww_status batch_problem(hww_batch* b, int32_t i, hww_problem** out);
+/* Tile size in particles (>= 256) and events per track before requeueing
+ * (>= 1) of the batched tracking launches; results do not depend on them. */
+hww_status batch_set_tuning(hww_batch* b, int32_t tile, int32_t emax);
+/* Advance every member by one time step; stats (nullable) synchronizes. */
+hww_status run_batch_step(hww_batch* b, hww_batch_stats* stats);
+/* Counts of member i's last step (synchronizes). */
+hww_status batch_member_stats(hww_batch* b, int32_t i, hww_step_stats* stats);
+void destroy_batch(hww_batch* b);
+
 /* Launch accounting of a problem since creation or the last reset: kernels
  * the library launched, tracking-kernel launches, and (when timing is on)
  * the device time of the tracking launches measured with CUDA events on the
@@ -208,6 +248,10 @@ void destroy_problem(hww_problem* p);
 
 /* Static text for a status code. */
 const char* hww_status_string(hww_status s);
+
+/* Text of the last CUDA runtime error the library saw on this host thread
+ * (name, message and the place it was caught), for HWW_ERR_CUDA diagnosis. */
+const char* hww_last_error_string(void);
 
 /* Solve one LOSM system (Eqs. losm-0, losm-1, losm-disc-bc) on the device
  * for given inputs, with the library's solver.  Host arrays in the paper's

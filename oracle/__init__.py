@@ -53,7 +53,7 @@ class _Desc(C.Structure):
         ("dt", C.c_double), ("bc_left", C.c_int32), ("bc_right", C.c_int32),
         ("src_x", C.c_double), ("particles_per_step", C.c_int64), ("seed", C.c_uint64),
         ("theta", C.c_double), ("filter", C.c_int32), ("filter_k", C.c_int32),
-        ("n_var_batches", C.c_int32),
+        ("n_var_batches", C.c_int32), ("deriv_regions", C.c_int32),
     ]
 
 
@@ -96,6 +96,10 @@ def lib():
             L.or_set_bank.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.c_double]
             L.or_get_census.argtypes = [C.c_void_p, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
                                         C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_int64)]
+            L.or_set_regions.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+            L.or_get_deriv_tallies.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int64]
+            L.or_losm_vjp.argtypes = [C.c_void_p, dp, dp, dp]
+            L.or_set_bank_scores.argtypes = [C.c_void_p, dp]
             L.or_destroy.argtypes = [C.c_void_p]
             L.or_destroy.restype = None
             L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
@@ -198,13 +202,14 @@ class Problem:
     """One slab problem stepped by the oracle; mirrors the library's verbs."""
 
     def __init__(self, edges, v, dt, bc_left, bc_right, src_x, particles_per_step, seed,
-                 theta=0.5, filter=0, filter_k=3, n_var_batches=16):
+                 theta=0.5, filter=0, filter_k=3, n_var_batches=16, deriv_regions=0):
         self.edges = _f64(edges)
         self.I = self.edges.size - 1
         self.B = int(n_var_batches)
+        self.R = int(deriv_regions)
         d = _Desc(self.I, _dp(self.edges), float(v), float(dt), int(bc_left), int(bc_right),
                   float(src_x), int(particles_per_step), int(seed), float(theta), int(filter),
-                  int(filter_k), self.B)
+                  int(filter_k), self.B, self.R)
         h = C.c_void_p()
         _check(lib().or_create(C.byref(d), C.byref(h)), "create")
         self._h = h
@@ -282,6 +287,32 @@ class Problem:
         _check(lib().or_set_bank(self._h, _dp(x), _dp(mu), cell.ctypes.data_as(C.POINTER(C.c_int32)),
                                  x.size, float(w_bar)), "set_bank")
 
+    def set_regions(self, region):
+        r = np.ascontiguousarray(region, dtype=np.int32)
+        if r.size != self.I:
+            raise ValueError("expected %d regions, got %d" % (self.I, r.size))
+        _check(lib().or_set_regions(self._h, r.ctypes.data_as(C.POINTER(C.c_int32))), "set_regions")
+
+    def get_deriv_tallies(self, which=0):
+        """[2R, I] derivatives of the last step's tally `which` (0 track-length
+        phi, 1 census phi, 2 census J, 3 census F); rows j < R are d/dSigma_t of
+        region j, rows R + r are d/dc of region r."""
+        out = np.empty(2 * self.R * self.I)
+        _check(lib().or_get_deriv_tallies(self._h, int(which), _dp(out), out.size), "get_deriv_tallies")
+        return out.reshape(2 * self.R, self.I)
+
+    def losm_vjp(self, g_phi, g_J):
+        """g_phi . d phi/d theta + g_J . d J/d theta of the last step's fully
+        implicit HLOSM solution, for the 2R parameters."""
+        gp, gj = _f64(g_phi, self.I + 2), _f64(g_J, self.I + 1)
+        out = np.empty(2 * self.R)
+        _check(lib().or_losm_vjp(self._h, _dp(gp), _dp(gj), _dp(out)), "losm_vjp")
+        return out
+
+    def set_bank_scores(self, S):
+        S = _f64(S)
+        _check(lib().or_set_bank_scores(self._h, _dp(S)), "set_bank_scores")
+
     def get_census(self):
         n = C.c_int64()
         L = lib()
@@ -298,13 +329,17 @@ class Problem:
         return out
 
 
-def problem_from_workload(wl, particles_per_step=None, seed=None):
-    """Build an oracle Problem from a workload description (see workloads.py)."""
+def problem_from_workload(wl, particles_per_step=None, seed=None, deriv=False):
+    """Build an oracle Problem from a workload description (see workloads.py);
+    with deriv, the derivative tallies for the workload's regions are on."""
+    R = int(wl.get("n_regions", 1)) if deriv else 0
     p = Problem(wl["edges"], wl["v"], wl["dt"], wl["bc_left"], wl["bc_right"], wl["src_x"],
                 particles_per_step or wl["particles_per_step"], wl["seed"] if seed is None else seed,
                 wl.get("theta", 0.5), wl.get("filter", 0), wl.get("filter_k", 3),
-                wl.get("n_var_batches", 16))
+                wl.get("n_var_batches", 16), R)
     p.set_cross_sections(wl["sigma_t"], wl["c"])
+    if R:
+        p.set_regions(wl.get("region", np.zeros(p.I, np.int32)))
     p.set_ww_params(wl["rho"], wl["eps_min"], wl.get("mode", MODE_HWW),
                     wl.get("center_scaling", SCALE_MEAN_WEIGHT))
     return p

@@ -149,12 +149,15 @@ static int bit_length(int64_t n) {
 /* Problem state                                                            */
 /* ------------------------------------------------------------------------ */
 
+#define MAX_DERIV 8 /* 2R scores, R <= 4 regions */
+
 typedef struct {
     double x, mu, tau, w;
     int32_t cell;
     uint32_t id;
     uint64_t lin;
     uint32_t e;
+    double S[MAX_DERIV]; /* likelihood-ratio scores: Sigma_t of region r at r, c at R + r */
 } or_particle;
 
 typedef struct {
@@ -162,6 +165,7 @@ typedef struct {
     int32_t cell;
     uint32_t id;
     uint64_t lin;
+    double S[MAX_DERIV];
 } or_census;
 
 struct or_problem {
@@ -195,6 +199,16 @@ struct or_problem {
     double* prev_tl_phi;
     int has_prev_tl;
     int bank_loaded; /* the next step starts from a loaded bank */
+    /* derivatives (R regions, 2R parameters) */
+    int R;
+    int32_t* region;
+    double* inv_c;
+    double* bS;                        /* N x 2R scores of the combed bank */
+    i128 *dtl, *dcen;                  /* [2R][I], [3][2R][I] */
+    double *dclo_phi, *dclo_J, *dclo_F;          /* derivative closure set at t^n */
+    double *dold_phi, *dold_J, *dold_F;          /* ... at the step start */
+    double *last_phi_old, *last_J_old, *last_F_old; /* closure set at the step start */
+    double last_PL_old, last_PR_old;
     /* census bank of the last step */
     or_census* census;
     int64_t ncensus;
@@ -209,7 +223,8 @@ int or_create(const or_desc* d, or_problem** out) {
     if (I < 1 || !d->edges || !(d->v > 0) || !(d->dt > 0) || d->particles_per_step < 1 ||
         d->particles_per_step >= (1LL << 30) || (d->theta != 0.5 && d->theta != 1.0) ||
         d->n_var_batches < 1 || d->bc_left < 0 || d->bc_left > 1 || d->bc_right < 0 ||
-        d->bc_right > 1 || d->filter < 0 || d->filter > 1 || (d->filter == 1 && d->filter_k < 1))
+        d->bc_right > 1 || d->filter < 0 || d->filter > 1 || (d->filter == 1 && d->filter_k < 1) ||
+        d->deriv_regions < 0 || 2 * d->deriv_regions > MAX_DERIV)
         return E_ARG;
     for (int32_t i = 0; i < I; ++i)
         if (!(d->edges[i + 1] > d->edges[i])) return E_ARG;
@@ -251,6 +266,32 @@ int or_create(const or_desc* d, or_problem** out) {
         or_destroy(p);
         return E_OOM;
     }
+    p->R = d->deriv_regions;
+    p->region = xcalloc(I, sizeof(int32_t));
+    p->inv_c = xcalloc(I, sizeof(double));
+    p->last_phi_old = xcalloc(I + 2, sizeof(double));
+    p->last_J_old = xcalloc(I + 1, sizeof(double));
+    p->last_F_old = xcalloc(I + 2, sizeof(double));
+    if (p->R > 0) {
+        const int P2 = 2 * p->R;
+        p->dtl = xcalloc((size_t)P2 * I, sizeof(i128));
+        p->dcen = xcalloc((size_t)3 * P2 * I, sizeof(i128));
+        p->dclo_phi = xcalloc((size_t)P2 * (I + 2), sizeof(double));
+        p->dclo_J = xcalloc((size_t)P2 * (I + 1), sizeof(double));
+        p->dclo_F = xcalloc((size_t)P2 * (I + 2), sizeof(double));
+        p->dold_phi = xcalloc((size_t)P2 * (I + 2), sizeof(double));
+        p->dold_J = xcalloc((size_t)P2 * (I + 1), sizeof(double));
+        p->dold_F = xcalloc((size_t)P2 * (I + 2), sizeof(double));
+        if (!p->dtl || !p->dcen || !p->dclo_phi || !p->dclo_J || !p->dclo_F || !p->dold_phi || !p->dold_J ||
+            !p->dold_F) {
+            or_destroy(p);
+            return E_OOM;
+        }
+    }
+    if (!p->region || !p->inv_c || !p->last_phi_old || !p->last_J_old || !p->last_F_old) {
+        or_destroy(p);
+        return E_OOM;
+    }
     memcpy(p->edges, d->edges, sizeof(double) * (I + 1));
     p->d.edges = p->edges;
     for (int32_t i = 0; i < I; ++i) p->dx[i] = p->edges[i + 1] - p->edges[i];
@@ -272,6 +313,10 @@ void or_destroy(or_problem* p) {
     free(p->semi_phi); free(p->semi_J); free(p->full_phi); free(p->full_J);
     free(p->prev_tl_phi);
     free(p->census);
+    free(p->region); free(p->inv_c); free(p->bS); free(p->dtl); free(p->dcen);
+    free(p->dclo_phi); free(p->dclo_J); free(p->dclo_F);
+    free(p->dold_phi); free(p->dold_J); free(p->dold_F);
+    free(p->last_phi_old); free(p->last_J_old); free(p->last_F_old);
     free(p);
 }
 
@@ -284,6 +329,7 @@ int or_set_cross_sections(or_problem* p, const double* sigma_t, const double* c)
         p->inv_sigt[i] = 1.0 / sigma_t[i];
         p->c[i] = c[i];
         p->siga[i] = sigma_t[i] * (1.0 - c[i]); /* Sigma_t - Sigma_s (no fission) */
+        p->inv_c[i] = (c[i] > 0.0) ? 1.0 / c[i] : 0.0;
     }
     p->xs_set = 1;
     return 0;
@@ -298,6 +344,14 @@ int or_set_ww_params(or_problem* p, double rho, double eps_min, int32_t mode, in
     p->mode = mode;
     p->scaling = scaling;
     p->ww_set = 1;
+    return 0;
+}
+
+int or_set_regions(or_problem* p, const int32_t* region) {
+    if (!p || !region) return E_ARG;
+    for (int32_t i = 0; i < p->I; ++i)
+        if (region[i] < 0 || (p->R > 0 && region[i] >= p->R)) return E_ARG;
+    memcpy(p->region, region, sizeof(int32_t) * p->I);
     return 0;
 }
 
@@ -354,30 +408,19 @@ int or_ma_filter(const double* in, double* out, int32_t m, int32_t k) {
 /*  - a reflecting side replaces its BC row by J = 0;                      */
 /*  - inflow currents J_L, J_R are zero (vacuum).                          */
 /* ------------------------------------------------------------------------ */
-int or_losm_solve(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a,
-                  double v, double dt, double theta, int32_t bc_left, int32_t bc_right,
-                  const double* phi_old, const double* J_old, const double* F_old,
-                  const double* F_new, double PL_new, double PR_new,
-                  const double* q_old, const double* q_new, double* phi_new, double* J_new) {
-    if (I < 1 || !dx || !sigma_t || !sigma_a || !phi_old || !J_old || !F_old || !F_new ||
-        !phi_new || !J_new)
-        return E_ARG;
-    int32_t n = 2 * I + 3;
-    double* a = xcalloc(n, sizeof(double));  /* sub-diagonal  A[r][r-1] */
-    double* b = xcalloc(n, sizeof(double));  /* diagonal      A[r][r]   */
-    double* c = xcalloc(n, sizeof(double));  /* super         A[r][r+1] */
-    double* f = xcalloc(n, sizeof(double));  /* fill          A[r][r+2] */
-    double* r = xcalloc(n, sizeof(double));
-    if (!a || !b || !c || !f || !r) {
-        free(a); free(b); free(c); free(f); free(r);
-        return E_OOM;
-    }
+/* rows of the interleaved system: sub-diagonal a, diagonal b, super c, rhs r */
+static void losm_assemble(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a, double v,
+                          double dt, double theta, int32_t bc_left, int32_t bc_right, const double* phi_old,
+                          const double* J_old, const double* F_old, const double* F_new, double PL_new,
+                          double PR_new, const double* q_old, const double* q_new, double* a, double* b,
+                          double* c, double* r) {
+    const int32_t n = 2 * I + 3;
     const double vdt = v * dt;
     const double tm1 = theta - 1.0;
+    for (int32_t k = 0; k < n; ++k) a[k] = b[k] = c[k] = r[k] = 0.0;
     /* left boundary row */
     if (bc_left == OR_REFLECT) {
         b[0] = 0.0; c[0] = 1.0; r[0] = 0.0;           /* J_0 = 0 */
-        /* keep the row well posed for pivoting: J_0 is column 1 */
     } else {
         b[0] = 0.5; c[0] = 1.0; r[0] = PL_new;         /* J_0 + phi_0/2 = P_L */
     }
@@ -414,7 +457,13 @@ int or_losm_solve(int32_t I, const double* dx, const double* sigma_t, const doub
     } else {
         a[n - 1] = 1.0; b[n - 1] = -0.5; r[n - 1] = -PR_new; /* J_I - phi_{I+1}/2 = -P_R */
     }
-    /* Gaussian elimination with partial pivoting on the tridiagonal matrix */
+}
+
+/* Gaussian elimination with partial pivoting on a tridiagonal matrix (two
+ * rows compete per column, one extra super-diagonal of fill); solution in r */
+static int tri_solve_pivot(int32_t n, double* a, double* b, double* c, double* r) {
+    double* f = xcalloc(n, sizeof(double));
+    if (!f) return E_OOM;
     for (int32_t k = 0; k < n - 1; ++k) {
         if (fabs(a[k + 1]) > fabs(b[k])) {
             /* swap rows k and k+1 (row k+1 has entries a,b,c in columns k..k+2) */
@@ -425,7 +474,7 @@ int or_losm_solve(int32_t I, const double* dx, const double* sigma_t, const doub
             t = r[k]; r[k] = r[k + 1]; r[k + 1] = t;
         }
         if (b[k] == 0.0) {
-            free(a); free(b); free(c); free(f); free(r);
+            free(f);
             return E_NUMERIC;
         }
         double l = a[k + 1] / b[k];
@@ -435,17 +484,42 @@ int or_losm_solve(int32_t I, const double* dx, const double* sigma_t, const doub
         r[k + 1] = r[k + 1] - l * r[k];
     }
     if (b[n - 1] == 0.0) {
-        free(a); free(b); free(c); free(f); free(r);
+        free(f);
         return E_NUMERIC;
     }
-    double* u = r; /* back substitution in place */
-    u[n - 1] = r[n - 1] / b[n - 1];
-    u[n - 2] = (r[n - 2] - c[n - 2] * u[n - 1]) / b[n - 2];
-    for (int32_t k = n - 3; k >= 0; --k) u[k] = (r[k] - c[k] * u[k + 1] - f[k] * u[k + 2]) / b[k];
-    for (int32_t i = 0; i <= I + 1; ++i) phi_new[i] = u[2 * i];
-    for (int32_t i = 0; i <= I; ++i) J_new[i] = u[2 * i + 1];
-    free(a); free(b); free(c); free(f); free(r);
+    r[n - 1] = r[n - 1] / b[n - 1];
+    if (n >= 2) r[n - 2] = (r[n - 2] - c[n - 2] * r[n - 1]) / b[n - 2];
+    for (int32_t k = n - 3; k >= 0; --k) r[k] = (r[k] - c[k] * r[k + 1] - f[k] * r[k + 2]) / b[k];
+    free(f);
     return 0;
+}
+
+int or_losm_solve(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a,
+                  double v, double dt, double theta, int32_t bc_left, int32_t bc_right,
+                  const double* phi_old, const double* J_old, const double* F_old,
+                  const double* F_new, double PL_new, double PR_new,
+                  const double* q_old, const double* q_new, double* phi_new, double* J_new) {
+    if (I < 1 || !dx || !sigma_t || !sigma_a || !phi_old || !J_old || !F_old || !F_new ||
+        !phi_new || !J_new)
+        return E_ARG;
+    int32_t n = 2 * I + 3;
+    double* a = xcalloc(n, sizeof(double));
+    double* b = xcalloc(n, sizeof(double));
+    double* c = xcalloc(n, sizeof(double));
+    double* r = xcalloc(n, sizeof(double));
+    if (!a || !b || !c || !r) {
+        free(a); free(b); free(c); free(r);
+        return E_OOM;
+    }
+    losm_assemble(I, dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, phi_old, J_old, F_old, F_new,
+                  PL_new, PR_new, q_old, q_new, a, b, c, r);
+    int rc = tri_solve_pivot(n, a, b, c, r);
+    if (rc == 0) {
+        for (int32_t i = 0; i <= I + 1; ++i) phi_new[i] = r[2 * i];
+        for (int32_t i = 0; i <= I; ++i) J_new[i] = r[2 * i + 1];
+    }
+    free(a); free(b); free(c); free(r);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -574,38 +648,44 @@ static int64_t to_fixed(double x, int s) { return llrint(ldexp(x, s)); }
  * averages linearly in space; the boundary edge current follows the BC
  * relation (0 on a reflecting side); the MA filter, when on, acts on the
  * cell vectors of phi and F and on the edge vector of J. */
-static void build_closures(or_problem* p, const double* cphi, const double* cJ, const double* cF,
-                           double PL, double PR) {
+static void build_closure_set(const or_problem* p, const double* cphi, const double* cJ, const double* cF,
+                              double PL, double PR, double* ophi, double* oJ, double* oF, double* oPL,
+                              double* oPR) {
     int32_t I = p->I;
     double* tmp = xcalloc(I + 1, sizeof(double));
     double* tmp2 = xcalloc(I + 1, sizeof(double));
     for (int32_t i = 1; i <= I; ++i) {
-        p->clo_phi[i] = cphi[i - 1];
-        p->clo_F[i] = cF[i - 1];
+        ophi[i] = cphi[i - 1];
+        oF[i] = cF[i - 1];
     }
     for (int32_t i = 1; i <= I - 1; ++i) {
         double dl = p->dx[i - 1], dr = p->dx[i];
-        p->clo_J[i] = (cJ[i - 1] * dr + cJ[i] * dl) / (dl + dr);
+        oJ[i] = (cJ[i - 1] * dr + cJ[i] * dl) / (dl + dr);
     }
-    p->clo_phi[0] = p->clo_phi[1];
-    p->clo_phi[I + 1] = p->clo_phi[I];
-    p->clo_F[0] = p->clo_F[1];
-    p->clo_F[I + 1] = p->clo_F[I];
-    p->clo_J[0] = (p->d.bc_left == OR_REFLECT) ? 0.0 : (-0.5 * p->clo_phi[0] + PL);
-    p->clo_J[I] = (p->d.bc_right == OR_REFLECT) ? 0.0 : (0.5 * p->clo_phi[I + 1] - PR);
-    p->clo_PL = (p->d.bc_left == OR_REFLECT) ? 0.0 : PL;
-    p->clo_PR = (p->d.bc_right == OR_REFLECT) ? 0.0 : PR;
+    ophi[0] = ophi[1];
+    ophi[I + 1] = ophi[I];
+    oF[0] = oF[1];
+    oF[I + 1] = oF[I];
+    oJ[0] = (p->d.bc_left == OR_REFLECT) ? 0.0 : (-0.5 * ophi[0] + PL);
+    oJ[I] = (p->d.bc_right == OR_REFLECT) ? 0.0 : (0.5 * ophi[I + 1] - PR);
+    if (oPL) *oPL = (p->d.bc_left == OR_REFLECT) ? 0.0 : PL;
+    if (oPR) *oPR = (p->d.bc_right == OR_REFLECT) ? 0.0 : PR;
     if (p->d.filter == 1) {
-        or_ma_filter(p->clo_phi + 1, tmp, I, p->d.filter_k);
-        memcpy(p->clo_phi + 1, tmp, sizeof(double) * I);
-        or_ma_filter(p->clo_F + 1, tmp, I, p->d.filter_k);
-        memcpy(p->clo_F + 1, tmp, sizeof(double) * I);
-        or_ma_filter(p->clo_J, tmp2, I + 1, p->d.filter_k);
-        memcpy(p->clo_J, tmp2, sizeof(double) * (I + 1));
+        or_ma_filter(ophi + 1, tmp, I, p->d.filter_k);
+        memcpy(ophi + 1, tmp, sizeof(double) * I);
+        or_ma_filter(oF + 1, tmp, I, p->d.filter_k);
+        memcpy(oF + 1, tmp, sizeof(double) * I);
+        or_ma_filter(oJ, tmp2, I + 1, p->d.filter_k);
+        memcpy(oJ, tmp2, sizeof(double) * (I + 1));
         /* the end values are unchanged by the filter, so the copies above hold */
     }
     free(tmp);
     free(tmp2);
+}
+
+static void build_closures(or_problem* p, const double* cphi, const double* cJ, const double* cF,
+                           double PL, double PR) {
+    build_closure_set(p, cphi, cJ, cF, PL, PR, p->clo_phi, p->clo_J, p->clo_F, &p->clo_PL, &p->clo_PR);
 }
 
 /* Exact moments of the unit isotropic plane pulse at t = 0 (step-1 IC).
@@ -712,6 +792,24 @@ int or_run_step(or_problem* p, or_stats* st) {
     memcpy(J_old, p->clo_J, sizeof(double) * (I + 1));
     memcpy(F_old, p->clo_F, sizeof(double) * (I + 2));
     double PL_old = p->clo_PL, PR_old = p->clo_PR;
+    memcpy(p->last_phi_old, phi_old, sizeof(double) * (I + 2));
+    memcpy(p->last_J_old, J_old, sizeof(double) * (I + 1));
+    memcpy(p->last_F_old, F_old, sizeof(double) * (I + 2));
+    p->last_PL_old = PL_old;
+    p->last_PR_old = PR_old;
+    const int R = p->R, P2 = 2 * p->R;
+    if (R > 0) {
+        /* derivative closures of the step start: those built at the end of the
+         * previous step (zero for the exact pulse moments of step 1) */
+        if (n == 1) {
+            memset(p->dclo_phi, 0, sizeof(double) * P2 * (I + 2));
+            memset(p->dclo_J, 0, sizeof(double) * P2 * (I + 1));
+            memset(p->dclo_F, 0, sizeof(double) * P2 * (I + 2));
+        }
+        memcpy(p->dold_phi, p->dclo_phi, sizeof(double) * P2 * (I + 2));
+        memcpy(p->dold_J, p->dclo_J, sizeof(double) * P2 * (I + 1));
+        memcpy(p->dold_F, p->dclo_F, sizeof(double) * P2 * (I + 2));
+    }
 
     /* 2. semi-implicit HLOSM, Eqs. (losm-0), (losm-1-semi), (losm-disc-bc-semi):
      *    the new-level closure is the lagged one. */
@@ -721,6 +819,7 @@ int or_run_step(or_problem* p, or_stats* st) {
     if (rc) goto fail;
 
     /* 3. weight windows */
+    int ww_on = 0;
     if (p->has_override) {
         for (int32_t i = 0; i < I; ++i) {
             double ctr = quantize_center(p->ww_override[i]);
@@ -729,12 +828,14 @@ int or_run_step(or_problem* p, or_stats* st) {
             p->ww_lo[i] = ctr / p->rho;
         }
         p->has_override = 0;
+        ww_on = 1;
     } else if (p->mode == OR_MODE_HWW) {
         ww_from_flux(p, p->semi_phi + 1);
+        ww_on = 1;
     } else if (p->mode == OR_MODE_LWW && p->has_prev_tl) {
         ww_from_flux(p, p->prev_tl_phi);
+        ww_on = 1;
     }
-    const int ww_on = (p->mode == OR_MODE_HWW) || (p->mode == OR_MODE_LWW && p->has_prev_tl);
 
     /* 4. tracking */
     const int E = wbar_exponent(p->wbar);
@@ -748,6 +849,10 @@ int or_run_step(or_problem* p, or_stats* st) {
     }
     for (int64_t i = 0; i < (int64_t)I * B; ++i) p->batch[i] = 0;
     for (int j = 0; j < 6; ++j) p->bnd[j] = 0;
+    if (R > 0) {
+        for (int64_t i = 0; i < (int64_t)P2 * I; ++i) p->dtl[i] = 0;
+        for (int64_t i = 0; i < (int64_t)3 * P2 * I; ++i) p->dcen[i] = 0;
+    }
 
     pstack stack = {0};
     cbank census = {0};
@@ -759,6 +864,7 @@ int or_run_step(or_problem* p, or_stats* st) {
         or_particle q;
         q.id = (uint32_t)k;
         q.lin = 0;
+        for (int j = 0; j < MAX_DERIV; ++j) q.S[j] = 0.0;
         q.e = 0;
         q.tau = tau0;
         q.w = p->wbar;
@@ -774,6 +880,8 @@ int or_run_step(or_problem* p, or_stats* st) {
             q.x = p->bx[k];
             q.mu = p->bmu[k];
             q.cell = p->bcell[k];
+            if (R > 0 && p->bS)
+                for (int j = 0; j < P2; ++j) q.S[j] = p->bS[k * P2 + j];
         }
         if (ps_push(&stack, &q)) { rc = E_OOM; goto fail_track; }
     }
@@ -805,6 +913,15 @@ int or_run_step(or_problem* p, or_stats* st) {
             p->tl_j[k] += to_fixed(wlmu, S);
             p->tl_f[k] += to_fixed(wlf, S);
             p->batch[(int64_t)(((uint64_t)q.id * (uint64_t)B) / (uint64_t)N) * I + k] += to_fixed(wl, S);
+            if (R > 0) {
+                /* likelihood-ratio scores: the flight of length l in region r
+                 * contributes -l to the Sigma_t score, a collision 1/Sigma_t;
+                 * the derivative tally of this segment is w l S */
+                const int r = p->region[k];
+                q.S[r] = q.S[r] - l;
+                if (ev == 2) q.S[r] = q.S[r] + p->inv_sigt[k];
+                for (int j = 0; j < P2; ++j) p->dtl[(int64_t)j * I + k] += to_fixed(wl * q.S[j], S);
+            }
             s.segments++;
             /* move */
             if (ev == 1) {
@@ -825,7 +942,19 @@ int or_run_step(or_problem* p, or_stats* st) {
                 p->cen_w[k] += to_fixed(q.w, S);
                 p->cen_wmu[k] += to_fixed(wmu, S);
                 p->cen_wf[k] += to_fixed(wf, S);
-                or_census cq = {q.x, q.mu, q.w, q.cell, q.id, q.lin};
+                for (int j = 0; j < P2; ++j) {
+                    p->dcen[((int64_t)0 * P2 + j) * I + k] += to_fixed(q.w * q.S[j], S);
+                    p->dcen[((int64_t)1 * P2 + j) * I + k] += to_fixed(wmu * q.S[j], S);
+                    p->dcen[((int64_t)2 * P2 + j) * I + k] += to_fixed(wf * q.S[j], S);
+                }
+                or_census cq;
+                cq.x = q.x;
+                cq.mu = q.mu;
+                cq.w = q.w;
+                cq.cell = q.cell;
+                cq.id = q.id;
+                cq.lin = q.lin;
+                memcpy(cq.S, q.S, sizeof cq.S);
                 if (cb_push(&census, &cq)) { rc = E_OOM; goto fail_track; }
                 s.census++;
                 if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
@@ -870,6 +999,7 @@ int or_run_step(or_problem* p, or_stats* st) {
                 have_r2 = 1;
                 q.mu = 2.0 * or_u01(r2[0], r2[1]) - 1.0;
                 s.scatters++;
+                if (R > 0) q.S[R + p->region[k]] = q.S[R + p->region[k]] + p->inv_c[k]; /* scatter, prob c */
                 need_ww = 1;
             }
             if (need_ww && ww_on) {
@@ -925,6 +1055,18 @@ int or_run_step(or_problem* p, or_stats* st) {
         const double PL = ldexp(conv128(p->bnd[2]), -S) / ((double)N * p->d.dt);
         const double PR = ldexp(conv128(p->bnd[5]), -S) / ((double)N * p->d.dt);
         build_closures(p, cphi, cJ, cF, PL, PR);
+        for (int j = 0; j < P2; ++j) {
+            /* derivative closures: the same linear map applied to the census
+             * derivative tallies (boundary closures P taken as constants) */
+            for (int32_t i = 0; i < I; ++i) {
+                const double den = (double)N * p->dx[i];
+                cphi[i] = (v * ldexp(conv128(p->dcen[((int64_t)0 * P2 + j) * I + i]), -S)) / den;
+                cJ[i] = (v * ldexp(conv128(p->dcen[((int64_t)1 * P2 + j) * I + i]), -S)) / den;
+                cF[i] = (v * ldexp(conv128(p->dcen[((int64_t)2 * P2 + j) * I + i]), -S)) / den;
+            }
+            build_closure_set(p, cphi, cJ, cF, 0.0, 0.0, p->dclo_phi + (int64_t)j * (I + 2),
+                              p->dclo_J + (int64_t)j * (I + 1), p->dclo_F + (int64_t)j * (I + 2), NULL, NULL);
+        }
         free(cphi); free(cJ); free(cF);
         rc = or_losm_solve(I, p->dx, p->sigt, p->siga, v, p->d.dt, p->d.theta, p->d.bc_left,
                            p->d.bc_right, phi_old, J_old, F_old, p->clo_F, p->clo_PL, p->clo_PR,
@@ -965,6 +1107,10 @@ int or_run_step(or_problem* p, or_stats* st) {
         p->bx = xcalloc(N, sizeof(double));
         p->bmu = xcalloc(N, sizeof(double));
         p->bcell = xcalloc(N, sizeof(int32_t));
+        if (R > 0) {
+            free(p->bS);
+            p->bS = xcalloc((size_t)N * P2, sizeof(double));
+        }
         if (W == 0) {
             p->nbank = 0;
             p->wbar = 0.0;
@@ -974,6 +1120,7 @@ int or_run_step(or_problem* p, or_stats* st) {
                 p->bx[k] = cq->x;
                 p->bmu[k] = cq->mu;
                 p->bcell[k] = cq->cell;
+                for (int j = 0; j < P2; ++j) p->bS[k * P2 + j] = cq->S[j];
             }
             p->nbank = N;
             p->wbar = ldexp((double)W, -Sc) / (double)N;
@@ -1113,6 +1260,10 @@ int or_set_bank(or_problem* p, const double* x, const double* mu, const int32_t*
     p->nbank = n;
     p->wbar = wbar;
     p->bank_loaded = 1;
+    if (p->R > 0) {
+        free(p->bS);
+        p->bS = xcalloc((size_t)(n ? n : 1) * 2 * p->R, sizeof(double));
+    }
     return 0;
 }
 
@@ -1144,4 +1295,110 @@ int or_get_bank(const or_problem* p, double* x, double* mu, int32_t* cell, int64
         if (cell) cell[k] = p->bcell[k];
     }
     return 0;
+}
+
+int or_set_bank_scores(or_problem* p, const double* S) {
+    if (!p || p->R < 1) return E_ARG;
+    const int P2 = 2 * p->R;
+    free(p->bS);
+    p->bS = xcalloc((size_t)(p->nbank ? p->nbank : 1) * P2, sizeof(double));
+    if (!p->bS) return E_OOM;
+    if (S) memcpy(p->bS, S, sizeof(double) * p->nbank * P2);
+    return 0;
+}
+
+int or_get_deriv_tallies(const or_problem* p, int32_t which, double* out, int64_t n) {
+    if (!p || !out || p->R < 1 || which < 0 || which > 3) return E_ARG;
+    const int32_t I = p->I;
+    const int P2 = 2 * p->R;
+    if (n < (int64_t)P2 * I) return E_ARG;
+    const int S = p->tally_shift;
+    const int64_t N = p->N;
+    for (int j = 0; j < P2; ++j)
+        for (int32_t i = 0; i < I; ++i) {
+            double val;
+            if (which == 0) {
+                val = ldexp(conv128(p->dtl[(int64_t)j * I + i]), -S) / (((double)N * p->dx[i]) * p->d.dt);
+            } else {
+                const i128 a = p->dcen[((int64_t)(which - 1) * P2 + j) * I + i];
+                val = (p->d.v * ldexp(conv128(a), -S)) / ((double)N * p->dx[i]);
+            }
+            out[(int64_t)j * I + i] = val;
+        }
+    return 0;
+}
+
+/* Adjoint of the last step's fully implicit solve A(theta) u = b(theta,
+ * closures(theta)): with A^T lambda = g,
+ *   g . du/dtheta_j = lambda . ( b(dclosures_j) + db/dtheta_j - dA/dtheta_j u ),
+ * where b is linear in the closures (no source), so its closure part is the
+ * same assembly applied to the derivative closures, and the direct parts
+ * come from Sigma_hat (first-moment rows) and Sigma_a = Sigma_t (1 - c)
+ * (balance rows). */
+int or_losm_vjp(const or_problem* p, const double* g_phi, const double* g_J, double* grad) {
+    if (!p || !g_phi || !g_J || !grad || p->R < 1 || p->n < 1) return E_ARG;
+    const int32_t I = p->I, n = 2 * I + 3;
+    const int R = p->R, P2 = 2 * R;
+    const double th = p->d.theta, tm1 = th - 1.0;
+    double* a = xcalloc(n, sizeof(double));
+    double* b = xcalloc(n, sizeof(double));
+    double* c = xcalloc(n, sizeof(double));
+    double* r = xcalloc(n, sizeof(double));
+    double* at = xcalloc(n, sizeof(double));
+    double* ct = xcalloc(n, sizeof(double));
+    double* lam = xcalloc(n, sizeof(double));
+    double* rb = xcalloc(n, sizeof(double));
+    if (!a || !b || !c || !r || !at || !ct || !lam || !rb) {
+        free(a); free(b); free(c); free(r); free(at); free(ct); free(lam); free(rb);
+        return E_OOM;
+    }
+    losm_assemble(I, p->dx, p->sigt, p->siga, p->d.v, p->d.dt, th, p->d.bc_left, p->d.bc_right,
+                  p->last_phi_old, p->last_J_old, p->last_F_old, p->clo_F, p->clo_PL, p->clo_PR, NULL, NULL,
+                  a, b, c, r);
+    /* transpose: (A^T)[k][k-1] = A[k-1][k] = c[k-1], (A^T)[k][k+1] = A[k+1][k] = a[k+1] */
+    for (int32_t k = 0; k < n; ++k) {
+        at[k] = (k >= 1) ? c[k - 1] : 0.0;
+        ct[k] = (k + 1 < n) ? a[k + 1] : 0.0;
+    }
+    for (int32_t i = 0; i <= I + 1; ++i) lam[2 * i] = g_phi[i];
+    for (int32_t i = 0; i <= I; ++i) lam[2 * i + 1] = g_J[i];
+    int rc = tri_solve_pivot(n, at, b, ct, lam);
+    if (rc) goto done;
+    for (int j = 0; j < P2; ++j) {
+        /* closure part: the assembly applied to the derivative closures */
+        double* dphi = p->dold_phi + (int64_t)j * (I + 2);
+        double* dJ = p->dold_J + (int64_t)j * (I + 1);
+        double* dFo = p->dold_F + (int64_t)j * (I + 2);
+        double* dFn = p->dclo_F + (int64_t)j * (I + 2);
+        losm_assemble(I, p->dx, p->sigt, p->siga, p->d.v, p->d.dt, th, p->d.bc_left, p->d.bc_right, dphi, dJ,
+                      dFo, dFn, 0.0, 0.0, NULL, NULL, a, b, c, rb);
+        double acc = 0.0;
+        for (int32_t k = 0; k < n; ++k) acc += lam[k] * rb[k];
+        /* direct part */
+        const int is_sigma = j < R;
+        const int g = is_sigma ? j : j - R;
+        for (int32_t i = 0; i <= I; ++i) {
+            if (!is_sigma) break;
+            const double dxl = (i >= 1) ? p->dx[i - 1] : 0.0;
+            const double dxr = (i <= I - 1) ? p->dx[i] : 0.0;
+            double dsth = 0.0;
+            if (i >= 1 && p->region[i - 1] == g) dsth += dxl / (dxl + dxr);
+            if (i <= I - 1 && p->region[i] == g) dsth += dxr / (dxl + dxr);
+            if (dsth == 0.0) continue;
+            const double dxh = 0.5 * (dxl + dxr);
+            const double val = tm1 * dxh * dsth * p->last_J_old[i] - th * dxh * dsth * p->full_J[i];
+            acc += lam[2 * i + 1] * val;
+        }
+        for (int32_t i = 1; i <= I; ++i) {
+            if (p->region[i - 1] != g) continue;
+            const double dsa = is_sigma ? (1.0 - p->c[i - 1]) : -p->sigt[i - 1];
+            const double dxi = p->dx[i - 1];
+            const double val = tm1 * dxi * dsa * p->last_phi_old[i] - th * dxi * dsa * p->full_phi[i];
+            acc += lam[2 * i] * val;
+        }
+        grad[j] = acc;
+    }
+done:
+    free(a); free(b); free(c); free(r); free(at); free(ct); free(lam); free(rb);
+    return rc;
 }

@@ -33,6 +33,8 @@ typedef struct {
     double theta;                 /* 0.5 Crank-Nicolson, 1.0 backward Euler */
     int32_t filter, filter_k;     /* 0 none, 1 moving average of base k */
     int32_t n_var_batches;        /* B for the batch-mean variance tally */
+    int32_t deriv_regions;        /* R > 0: likelihood-ratio derivative tallies for
+                                     (Sigma_t, c) of R regions (R <= 4) */
 } or_desc;
 
 typedef struct {
@@ -48,16 +50,26 @@ typedef struct {
 int or_create(const or_desc* d, or_problem** out);
 int or_set_cross_sections(or_problem* p, const double* sigma_t, const double* c);
 int or_set_ww_params(or_problem* p, double rho, double eps_min, int32_t mode, int32_t center_scaling);
+int or_set_regions(or_problem* p, const int32_t* region); /* region of each cell, 0..R-1 */
 int or_set_ww_centers(or_problem* p, const double* centers); /* override for the next step only */
 int or_run_step(or_problem* p, or_stats* st);
 int or_get_tallies(const or_problem* p, int32_t kind, double* out, int64_t n);
 int or_get_tallies_raw(const or_problem* p, int32_t kind, int64_t* out, int64_t n);
 int or_get_losm_solution(const or_problem* p, int32_t which, double* phi, double* J);
+/* derivative tallies of the last step, [2R][I]: parameter j < R is Sigma_t of
+ * region j, j >= R is c of region j - R; which: 0 track-length phi, 1 census
+ * phi, 2 census J, 3 census F (normalised like the tallies) */
+int or_get_deriv_tallies(const or_problem* p, int32_t which, double* out, int64_t n);
+/* vector-Jacobian product of the last step's fully implicit HLOSM solution:
+ * grad[j] = g_phi . dphi/dtheta_j + g_J . dJ/dtheta_j (2R values) */
+int or_losm_vjp(const or_problem* p, const double* g_phi, const double* g_J, double* grad);
 int or_get_ww(const or_problem* p, double* center, double* ceil_, double* floor_);
 int or_get_bank(const or_problem* p, double* x, double* mu, int32_t* cell, int64_t cap, int64_t* n);
 /* replace the start bank of the next step: n particles with ids 0..n-1,
  * weight w_bar each (also before the first step, instead of the pulse) */
 int or_set_bank(or_problem* p, const double* x, const double* mu, const int32_t* cell, int64_t n, double wbar);
+/* with derivatives: the scores of the loaded bank (n x 2R, may be NULL = 0) */
+int or_set_bank_scores(or_problem* p, const double* S);
 int or_get_census(const or_problem* p, double* x, double* mu, double* w, int32_t* cell, uint32_t* id,
                   uint64_t* lin, int64_t cap, int64_t* n);
 void or_destroy(or_problem* p);

@@ -60,6 +60,12 @@ class Counters(C.Structure):
                 ("steps", C.c_int64), ("census_capacity", C.c_int64), ("queue_capacity", C.c_int64)]
 
 
+class BatchStats(C.Structure):
+    _fields_ = [("problems", C.c_int64), ("segments", C.c_int64), ("census", C.c_int64), ("daughters", C.c_int64),
+                ("roulette_kills", C.c_int64), ("absorbed", C.c_int64), ("leaked", C.c_int64),
+                ("waves", C.c_int32), ("status", C.c_int32)]
+
+
 class HWWError(RuntimeError):
     def __init__(self, code, what):
         super().__init__("%s: %s (status %d)" % (what, STATUS.get(code, "unknown"), code))
@@ -71,8 +77,9 @@ _lib = None
 
 SYMBOLS = ["create_problem", "set_cross_sections", "set_ww_params", "set_ww_centers", "run_step",
            "get_tallies", "get_tallies_raw", "get_losm_solution", "get_bank", "set_bank", "get_census", "destroy_problem",
-           "hww_status_string", "hww_losm_solve", "hww_philox_block", "hww_set_timing",
-           "hww_get_counters", "hww_reset_counters"]
+           "hww_status_string", "hww_last_error_string", "hww_losm_solve", "hww_philox_block", "hww_set_timing",
+           "hww_get_counters", "hww_reset_counters", "create_batch", "batch_problem", "batch_set_tuning",
+           "run_batch_step", "batch_member_stats", "destroy_batch"]
 
 
 def library_path() -> str:
@@ -107,17 +114,26 @@ def load(build_if_missing: bool = True):
         L.hww_set_timing.argtypes = [vp, C.c_int32]
         L.hww_get_counters.argtypes = [vp, C.POINTER(Counters)]
         L.hww_reset_counters.argtypes = [vp]
+        L.create_batch.argtypes = [C.POINTER(ProblemDesc), C.c_int32, vp, C.c_int32, C.POINTER(vp)]
+        L.batch_problem.argtypes = [vp, C.c_int32, C.POINTER(vp)]
+        L.batch_set_tuning.argtypes = [vp, C.c_int32, C.c_int32]
+        L.run_batch_step.argtypes = [vp, C.POINTER(BatchStats)]
+        L.batch_member_stats.argtypes = [vp, C.c_int32, C.POINTER(StepStats)]
+        L.destroy_batch.argtypes = [vp]
+        L.destroy_batch.restype = None
         L.destroy_problem.argtypes = [vp]
         L.destroy_problem.restype = None
         L.hww_status_string.argtypes = [C.c_int32]
         L.hww_status_string.restype = C.c_char_p
+        L.hww_last_error_string.argtypes = []
+        L.hww_last_error_string.restype = C.c_char_p
         L.hww_losm_solve.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
                                      C.c_int32, C.c_int32, dp, dp, dp, dp, C.c_double, C.c_double,
                                      dp, dp, dp, dp]
         L.hww_philox_block.argtypes = [C.c_uint32] * 6 + [C.c_int64, C.POINTER(C.c_uint32)]
         for name in SYMBOLS:
             f = getattr(L, name)
-            if name not in ("destroy_problem", "hww_status_string"):
+            if name not in ("destroy_problem", "destroy_batch", "hww_status_string", "hww_last_error_string"):
                 f.restype = C.c_int32
         _lib = L
         return L
@@ -125,6 +141,8 @@ def load(build_if_missing: bool = True):
 
 def _check(rc, what):
     if rc != HWW_OK:
+        if rc == 7 and _lib is not None:
+            what = "%s [%s]" % (what, _lib.hww_last_error_string().decode())
         raise HWWError(rc, what)
 
 
@@ -321,6 +339,95 @@ class Problem:
                                 out["lin"].ctypes.data_as(C.POINTER(C.c_uint64)), m, C.byref(n)),
                    "get_census")
         return out
+
+
+def _desc_from_workload(wl, precision=None):
+    prec = precision if precision is not None else (FP32_TRACK if wl.get("precision") == "fp32" else FP64)
+    edges = _f64(wl["edges"])
+    d = ProblemDesc(edges.size - 1, _dp(edges), float(wl["v"]), float(wl["dt"]), int(wl["bc_left"]),
+                    int(wl["bc_right"]), float(wl["src_x"]), int(wl["particles_per_step"]), int(wl["seed"]),
+                    int(prec), float(wl.get("theta", 0.5)), int(wl.get("filter", 0)), int(wl.get("filter_k", 3)),
+                    int(wl.get("n_var_batches", 16)), 0, 0, None, 0)
+    return d, edges
+
+
+class _Member(Problem):
+    """A batch member: a Problem view that the batch owns."""
+
+    def __init__(self, handle, wl):
+        self._h = handle
+        self.edges = _f64(wl["edges"])
+        self.I = self.edges.size - 1
+        self.B = int(wl.get("n_var_batches", 16))
+        self.N = int(wl["particles_per_step"])
+        self.device = 0
+        self.stream = 0
+
+    def close(self):
+        self._h = None  # owned by the batch
+
+
+class Batch:
+    """Independent problems stepped together (create_batch / run_batch_step)."""
+
+    def __init__(self, workloads, precision=None, stream=None, device=0):
+        L = load()
+        self.workloads = list(workloads)
+        n = len(self.workloads)
+        descs = (ProblemDesc * n)()
+        self._keep = []
+        for i, wl in enumerate(self.workloads):
+            d, edges = _desc_from_workload(wl, precision)
+            descs[i] = d
+            self._keep.append(edges)
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = 0
+        h = C.c_void_p()
+        _check(L.create_batch(descs, n, C.c_void_p(int(stream)), int(device), C.byref(h)), "create_batch")
+        self._h = h
+        self.members = []
+        for i, wl in enumerate(self.workloads):
+            mh = C.c_void_p()
+            _check(L.batch_problem(self._h, i, C.byref(mh)), "batch_problem")
+            m = _Member(mh, wl)
+            m.set_cross_sections(wl["sigma_t"], wl["c"])
+            m.set_ww_params(wl["rho"], wl["eps_min"], wl.get("mode", MODE_HWW),
+                            wl.get("center_scaling", SCALE_MEAN_WEIGHT))
+            self.members.append(m)
+
+    def set_tuning(self, tile, emax):
+        _check(load().batch_set_tuning(self._h, int(tile), int(emax)), "batch_set_tuning")
+
+    def run_step(self, stats=True):
+        if not stats:
+            _check(load().run_batch_step(self._h, None), "run_batch_step")
+            return None
+        st = BatchStats()
+        _check(load().run_batch_step(self._h, C.byref(st)), "run_batch_step")
+        return {f: getattr(st, f) for f, _ in BatchStats._fields_}
+
+    def member_stats(self, i):
+        st = StepStats()
+        _check(load().batch_member_stats(self._h, int(i), C.byref(st)), "batch_member_stats")
+        out = {f: int(getattr(st, f)) for f in STAT_FIELDS}
+        out["w_bar_next"] = st.w_bar_next
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def create_problem(desc: ProblemDesc):

@@ -54,6 +54,8 @@ struct hww_problem {
     double *d_edges = nullptr, *d_dx = nullptr, *d_sigt = nullptr, *d_inv_sigt = nullptr, *d_c = nullptr,
            *d_siga = nullptr;
     float *d_dxf = nullptr, *d_inv_sigt_f = nullptr;
+    float4* d_cellf = nullptr;
+    double2* d_ww_hl = nullptr;
     int32_t* d_region = nullptr;
     double *ww_c = nullptr, *ww_hi = nullptr, *ww_lo = nullptr, *ww_override = nullptr;
     Banks<double> b64;
@@ -76,7 +78,7 @@ struct hww_problem {
     // initial conditions of the next step, the other is built at t^n
     double *cl_phi[2] = {}, *cl_J[2] = {}, *cl_F[2] = {}, *cl_P[2] = {};
     int cur = 0;
-    double *rphi = nullptr, *rJ = nullptr, *rF = nullptr, *mx = nullptr;
+    double *rphi = nullptr, *rJ = nullptr, *rF = nullptr, *mx = nullptr;  // mx: [0] HLOSM, [1] lagged
     double *prev_tl = nullptr, *semi_phi = nullptr, *semi_J = nullptr, *full_phi = nullptr,
            *full_J = nullptr, *norm = nullptr;
     LosmMat mat{};
@@ -85,7 +87,7 @@ struct hww_problem {
     unsigned* err = nullptr;
     unsigned long long* h_count = nullptr;  // pinned
     // host state
-    int xs_set = 0, ww_set = 0, has_override = 0, has_prev_tl = 0, bank_loaded = 0;
+    int xs_set = 0, ww_set = 0;
     double rho = 1.0, eps = 1e-3;
     int mode = 0, scaling = 0;
     long long steps = 0;
@@ -93,6 +95,7 @@ struct hww_problem {
     int track_grid = 0;
     size_t track_smem = 0;
     int last_waves = 0;
+    int emax = 64;         // events per track before it is requeued
     long long q_peak = 0;  // largest record count a wave produced in the last pass
     // launch accounting
     int timing = 0;
@@ -103,16 +106,28 @@ struct hww_problem {
 
 namespace {
 
-hww_status cuda_status(cudaError_t e) {
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+thread_local int g_last_cuda_line = 0;
+
+hww_status cuda_status_at(cudaError_t e, int line) {
     if (e == cudaSuccess) return HWW_OK;
+    g_last_cuda_error = e;
+    g_last_cuda_line = line;
     if (e == cudaErrorMemoryAllocation) return HWW_ERR_OOM;
     return HWW_ERR_CUDA;
 }
 
-#define HWW_CK(call)                                   \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) return cuda_status(e_); \
+hww_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return HWW_OK;
+    g_last_cuda_error = e;
+    if (e == cudaErrorMemoryAllocation) return HWW_ERR_OOM;
+    return HWW_ERR_CUDA;
+}
+
+#define HWW_CK(call)                                              \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_status_at(e_, __LINE__); \
     } while (0)
 
 template <class T>
@@ -225,19 +240,16 @@ hww_status regrow_banks(hww_problem* p, long long cen_need, long long q_need) {
 }
 
 template <class Real>
-TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b, uint32_t k0, uint32_t k1) {
+TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b) {
     TrackArgs<Real> a{};
     a.I = p->I;
     a.B = p->B;
     a.N = p->N;
-    a.emax = 64;
-    a.ww_on = (p->mode == HWW_MODE_HWW) || (p->mode == HWW_MODE_LWW && p->has_prev_tl) || p->has_override;
+    a.emax = p->emax;
     a.bc_l = p->d.bc_left;
     a.bc_r = p->d.bc_right;
     a.birth_cell_pos = p->birth_pos;
     a.birth_cell_neg = p->birth_neg;
-    a.k0 = k0;
-    a.k1 = k1;
     a.tau0 = p->d.v * p->d.dt;
     a.src_x = p->d.src_x;
     a.edges = p->d_edges;
@@ -245,6 +257,8 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b, uint32_t k
     a.c = p->d_c;
     a.dxf = p->d_dxf;
     a.inv_sigt_f = p->d_inv_sigt_f;
+    a.cellf = p->d_cellf;
+    a.ww_hl = p->d_ww_hl;
     a.ww_c = p->ww_c;
     a.ww_hi = p->ww_hi;
     a.ww_lo = p->ww_lo;
@@ -287,10 +301,9 @@ void account_track_time(hww_problem* p) {
 }
 
 template <class Real>
-hww_status track_waves(hww_problem* p, Banks<Real>& b, uint32_t k0, uint32_t k1, int birth) {
-    TrackArgs<Real> a = base_track_args(p, b, k0, k1);
+hww_status track_waves(hww_problem* p, Banks<Real>& b) {
+    TrackArgs<Real> a = base_track_args(p, b);
     a.from_bank = 1;
-    a.birth = birth;
     a.rin = b.q[1];
     a.rout = b.q[0];
     launch_track(p, a);
@@ -310,7 +323,6 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b, uint32_t k0, uint32_t k1,
         const int other = 1 - cur;
         HWW_CK(cudaMemsetAsync(b.q[other].count, 0, sizeof(unsigned long long), p->stream));
         a.from_bank = 0;
-        a.birth = 0;
         a.rin = b.q[cur];
         a.rout = b.q[other];
         launch_track(p, a);
@@ -427,9 +439,127 @@ hww_status copy_out(const hww_problem* p, double* out, const double* src, size_t
     return HWW_OK;
 }
 
+
+// Stages of one time step.  Every launch parameter below is fixed for the
+// life of the problem (the per-step values live in StepDev), so the stages
+// can also be recorded into CUDA graphs (see the batch engine).
+LosmRhsIn semi_rhs(const hww_problem* p) {
+    LosmRhsIn in{};
+    in.sd = p->sd;
+    in.full = 0;
+    for (int k = 0; k < 2; ++k) {
+        in.set_phi[k] = p->cl_phi[k];
+        in.set_J[k] = p->cl_J[k];
+        in.set_F[k] = p->cl_F[k];
+        in.set_P[k] = p->cl_P[k];
+    }
+    return in;
+}
+
+// clear the step's accumulators; step scalars; semi-implicit HLOSM with the
+// lagged closure (Eqs. losm-0, losm-1-semi, losm-disc-bc-semi); windows
+hww_status stage_pre(hww_problem* p) {
+    HWW_CK(cudaMemsetAsync(p->acc, 0, p->acc_bytes, p->stream));
+    HWW_CK(cudaMemsetAsync(p->grp, 0, p->grp_bytes, p->stream));
+    launch_step_scalars(p->sd, bit_length(p->N), p->d.seed, p->mode, p->stats, p->stream);
+    p->kernel_launches += 1 + launch_losm_solve(p->mat, semi_rhs(p), p->work, p->semi_phi, p->semi_J, p->mx,
+                                                p->stream);
+    WwArgs wa{};
+    wa.I = p->I;
+    wa.scaling = p->scaling;
+    wa.eps = p->eps;
+    wa.rho = p->rho;
+    wa.sd = p->sd;
+    wa.phit_hlosm = p->semi_phi + 1;
+    wa.phit_prev = p->prev_tl;
+    wa.mx_hlosm = p->mx;
+    wa.mx_prev = p->mx + 1;
+    wa.override_c = p->ww_override;
+    wa.ww_c = p->ww_c;
+    wa.ww_hi = p->ww_hi;
+    wa.ww_lo = p->ww_lo;
+    wa.ww_hl = p->d_ww_hl;
+    p->kernel_launches += launch_ww_centers(wa, p->mode == HWW_MODE_LWW, p->stream);
+    HWW_CK(cudaGetLastError());
+    return HWW_OK;
+}
+
+// closures and initial conditions at t^n, the fully implicit HLOSM (Eqs.
+// losm-0, losm-1, losm-disc-bc), the comb and the step-state advance
+hww_status stage_post(hww_problem* p) {
+    ClosureArgs ca{};
+    ca.I = p->I;
+    ca.sd = p->sd;
+    ca.v = p->d.v;
+    ca.dt = p->d.dt;
+    ca.N = p->N;
+    ca.bc_l = p->d.bc_left;
+    ca.bc_r = p->d.bc_right;
+    ca.filter_k = p->d.filter == HWW_FILTER_MA ? p->d.filter_k : 0;
+    ca.dx = p->d_dx;
+    ca.cent = p->cent;
+    ca.tl = p->tl;
+    ca.bnd = p->bnd;
+    ca.rphi = p->rphi;
+    ca.rJ = p->rJ;
+    ca.rF = p->rF;
+    for (int k = 0; k < 2; ++k) {
+        ca.set_phi[k] = p->cl_phi[k];
+        ca.set_J[k] = p->cl_J[k];
+        ca.set_F[k] = p->cl_F[k];
+        ca.set_P[k] = p->cl_P[k];
+    }
+    ca.prev_tl = p->prev_tl;
+    p->kernel_launches += launch_closures(ca, p->stream);
+    LosmRhsIn full = semi_rhs(p);
+    full.full = 1;
+    p->kernel_launches += launch_losm_solve(p->mat, full, p->work, p->full_phi, p->full_J, nullptr, p->stream);
+    HWW_CK(cudaGetLastError());
+    return p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);
+}
+
+hww_status read_stats(hww_problem* p, hww_step_stats* st) {
+    unsigned long long h[ST_COUNT];
+    StepDev sdh;
+    unsigned e = 0;
+    HWW_CK(cudaMemcpyAsync(h, p->stats, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    std::memset(st, 0, sizeof(*st));
+    st->segments = (int64_t)h[ST_SEGMENTS];
+    st->collisions = (int64_t)h[ST_COLLISIONS];
+    st->crossings = (int64_t)h[ST_CROSSINGS];
+    st->reflections = (int64_t)h[ST_REFLECTIONS];
+    st->leaked = (int64_t)h[ST_LEAKED];
+    st->absorbed = (int64_t)h[ST_ABSORBED];
+    st->scatters = (int64_t)h[ST_SCATTERS];
+    st->split_events = (int64_t)h[ST_SPLIT_EVENTS];
+    st->daughters = (int64_t)h[ST_DAUGHTERS];
+    st->roulette_kills = (int64_t)h[ST_RKILLS];
+    st->roulette_survivals = (int64_t)h[ST_RSURVIVE];
+    st->census = (int64_t)h[ST_CENSUS];
+    st->lineage_collisions = (int64_t)h[ST_LINEAGE];
+    st->max_events = (int64_t)h[ST_MAX_EVENTS];
+    st->n_next = (int64_t)sdh.nbank;
+    st->n_start = (int64_t)h[ST_NSTART];
+    st->w_bar_next = sdh.wbar;
+    st->waves = p->last_waves;
+    if (e) HWW_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    st->status = err_to_status(e);
+    return (hww_status)st->status;
+}
+
 }  // namespace
 
 extern "C" {
+
+const char* hww_last_error_string(void) {
+    static thread_local char buf[256];
+    std::snprintf(buf, sizeof buf, "%s (%s) at api.cu:%d", cudaGetErrorName(g_last_cuda_error),
+                  cudaGetErrorString(g_last_cuda_error), g_last_cuda_line);
+    return buf;
+}
 
 const char* hww_status_string(hww_status s) {
     switch (s) {
@@ -507,14 +637,14 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         (s = dalloc(p, &p->d_inv_sigt, I)) || (s = dalloc(p, &p->d_c, I)) || (s = dalloc(p, &p->d_siga, I)) ||
         (s = dalloc(p, &p->d_dxf, I)) || (s = dalloc(p, &p->d_inv_sigt_f, I)) || (s = dalloc(p, &p->d_region, I)) ||
         (s = dalloc(p, &p->ww_c, I)) || (s = dalloc(p, &p->ww_hi, I)) || (s = dalloc(p, &p->ww_lo, I)) ||
-        (s = dalloc(p, &p->ww_override, I)) || (s = dalloc(p, &p->goff, p->N + 1)) ||
+        (s = dalloc(p, &p->ww_override, I)) || (s = dalloc(p, &p->d_cellf, I)) || (s = dalloc(p, &p->d_ww_hl, I)) || (s = dalloc(p, &p->goff, p->N + 1)) ||
         (s = dalloc(p, &p->goff_w, p->N + 1)) || (s = dalloc(p, &p->tile_c, ntiles + 1)) ||
         (s = dalloc(p, &p->tile_w, ntiles + 1)) ||
         (s = dalloc(p, &p->cl_phi[0], I + 2)) || (s = dalloc(p, &p->cl_J[0], I + 1)) ||
         (s = dalloc(p, &p->cl_F[0], I + 2)) || (s = dalloc(p, &p->cl_P[0], 2)) ||
         (s = dalloc(p, &p->cl_phi[1], I + 2)) || (s = dalloc(p, &p->cl_J[1], I + 1)) ||
         (s = dalloc(p, &p->cl_F[1], I + 2)) || (s = dalloc(p, &p->cl_P[1], 2)) || (s = dalloc(p, &p->rphi, I)) ||
-        (s = dalloc(p, &p->rJ, I + 1)) || (s = dalloc(p, &p->rF, I)) || (s = dalloc(p, &p->mx, 1)) ||
+        (s = dalloc(p, &p->rJ, I + 1)) || (s = dalloc(p, &p->rF, I)) || (s = dalloc(p, &p->mx, 2)) ||
         (s = dalloc(p, &p->prev_tl, I)) || (s = dalloc(p, &p->semi_phi, I + 2)) ||
         (s = dalloc(p, &p->semi_J, I + 1)) || (s = dalloc(p, &p->full_phi, I + 2)) ||
         (s = dalloc(p, &p->full_J, I + 1)) || (s = dalloc(p, &p->work.u, I + 2)) ||
@@ -582,7 +712,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         return cuda_status(e);
     }
     // tracking launch shape: persistent grid of resident blocks
-    p->track_smem = sizeof(long long) * 6 * (size_t)I;
+    p->track_smem = sizeof(long long) * 7 * (size_t)I;
     if (p->track_smem > 48 * 1024) {
         if ((p->fp32 ? track_smem_optin_fp32(p->track_smem) : track_smem_optin_fp64(p->track_smem)) != 0) {
             destroy_problem(p);
@@ -608,13 +738,16 @@ hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const doubl
     HWW_CK(cudaSetDevice(p->device));
     std::vector<double> st(sigma_t, sigma_t + I), inv(I), cc(c, c + I), sa(I);
     std::vector<float> invf(I);
+    std::vector<float4> cellf(I);
     std::vector<int32_t> reg(I, 0);
     for (int i = 0; i < I; ++i) {
         inv[i] = 1.0 / st[i];
         invf[i] = (float)(1.0 / st[i]);
         sa[i] = st[i] * (1.0 - cc[i]);
+        cellf[i] = make_float4((float)p->dx[i], invf[i], (float)cc[i], 0.0f);
         if (region) reg[i] = region[i];
     }
+    HWW_CK(cudaMemcpyAsync(p->d_cellf, cellf.data(), sizeof(float4) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_sigt, st.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_inv_sigt, inv.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_inv_sigt_f, invf.data(), sizeof(float) * I, cudaMemcpyHostToDevice, p->stream));
@@ -652,8 +785,9 @@ hww_status set_ww_centers(hww_problem* p, const double* centers) {
         if (!(centers[i] > 0) || !std::isfinite(centers[i])) return HWW_ERR_ARG;
     HWW_CK(cudaSetDevice(p->device));
     HWW_CK(cudaMemcpyAsync(p->ww_override, centers, sizeof(double) * p->I, cudaMemcpyHostToDevice, p->stream));
+    const int one = 1;
+    HWW_CK(cudaMemcpyAsync(&p->sd->override_c, &one, sizeof(int), cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaStreamSynchronize(p->stream));
-    p->has_override = 1;
     return HWW_OK;
 }
 
@@ -661,50 +795,17 @@ hww_status run_step(hww_problem* p, hww_step_stats* st) {
     if (!p) return HWW_ERR_ARG;
     if (!p->xs_set || !p->ww_set) return HWW_ERR_STATE;
     HWW_CK(cudaSetDevice(p->device));
-    const long long n = p->steps + 1;
-    const uint32_t k0 = (uint32_t)p->d.seed;
-    const uint32_t k1 = (uint32_t)(p->d.seed >> 32) ^ (uint32_t)n;
-    const int c0 = p->cur, c1 = 1 - p->cur;
-    // semi-implicit HLOSM with the lagged closure (Eqs. losm-0,
-    // losm-1-semi, losm-disc-bc-semi), then the window centers
-    LosmRhsIn semi{};
-    semi.phi_old = p->cl_phi[c0];
-    semi.J_old = p->cl_J[c0];
-    semi.F_old = p->cl_F[c0];
-    semi.F_new = p->cl_F[c0];
-    semi.P_new = p->cl_P[c0];
-    WwArgs wa{};
-    wa.I = p->I;
-    wa.source = p->has_override ? 3
-                : p->mode == HWW_MODE_HWW ? 1
-                : (p->mode == HWW_MODE_LWW && p->has_prev_tl) ? 2
-                                                              : 0;
-    wa.scaling = p->scaling;
-    wa.eps = p->eps;
-    wa.rho = p->rho;
-    wa.sd = p->sd;
-    wa.phit = (wa.source == 2) ? p->prev_tl : p->semi_phi + 1;
-    wa.mx_ptr = p->mx;
-    wa.override_c = p->ww_override;
-    wa.ww_c = p->ww_c;
-    wa.ww_hi = p->ww_hi;
-    wa.ww_lo = p->ww_lo;
     // Tracking.  A census or queue overflow leaves the start bank and the
     // closure vectors untouched, so the step is replayed from the start with
-    // doubled capacities; the replay is bit-identical to a run that had the
-    // room from the beginning.
+    // larger buffers; the replay is bit-identical to a run that had the room
+    // from the beginning.
     hww_status s = HWW_OK;
     for (int attempt = 0;; ++attempt) {
-        HWW_CK(cudaMemsetAsync(p->acc, 0, p->acc_bytes, p->stream));
-        HWW_CK(cudaMemsetAsync(p->grp, 0, p->grp_bytes, p->stream));
-        launch_step_scalars(p->sd, bit_length(p->N), k0, k1, p->stats, p->stream);
-        p->kernel_launches += 1 + launch_losm_solve(p->mat, semi, p->work, p->semi_phi, p->semi_J, p->mx, p->stream);
-        if (wa.source) p->kernel_launches += launch_ww_centers(wa, p->stream);
-        HWW_CK(cudaGetLastError());
+        s = stage_pre(p);
+        if (s) return s;
         p->q_peak = 0;
-        const int birth = (n == 1 && !p->bank_loaded);
-        s = p->fp32 ? track_waves(p, p->b32, k0, k1, birth) : track_waves(p, p->b64, k0, k1, birth);
-        if (s) break;
+        s = p->fp32 ? track_waves(p, p->b32) : track_waves(p, p->b64);
+        if (s) return s;
         unsigned e = 0;
         unsigned long long ncen = 0;
         HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
@@ -712,84 +813,16 @@ hww_status run_step(hww_problem* p, hww_step_stats* st) {
         HWW_CK(cudaStreamSynchronize(p->stream));
         if (!(e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW)) || attempt >= MAX_REGROW) break;
         s = regrow_banks(p, (long long)ncen, p->q_peak);
-        if (s) break;
+        if (s) return s;
         const unsigned keep = e & ~(unsigned)(ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW);
         HWW_CK(cudaMemcpyAsync(p->err, &keep, sizeof(unsigned), cudaMemcpyHostToDevice, p->stream));
         HWW_CK(cudaStreamSynchronize(p->stream));
-        // the comb member list moved with the census bank
     }
-    p->has_override = 0;
-    p->bank_loaded = 0;
+    s = stage_post(p);
     if (s) return s;
-
-    // closures and initial conditions at t^n, then the fully implicit HLOSM
-    // (Eqs. losm-0, losm-1, losm-disc-bc)
-    ClosureArgs ca{};
-    ca.I = p->I;
-    ca.sd = p->sd;
-    ca.v = p->d.v;
-    ca.dt = p->d.dt;
-    ca.N = p->N;
-    ca.bc_l = p->d.bc_left;
-    ca.bc_r = p->d.bc_right;
-    ca.filter_k = p->d.filter == HWW_FILTER_MA ? p->d.filter_k : 0;
-    ca.dx = p->d_dx;
-    ca.cent = p->cent;
-    ca.tl = p->tl;
-    ca.bnd = p->bnd;
-    ca.rphi = p->rphi;
-    ca.rJ = p->rJ;
-    ca.rF = p->rF;
-    ca.nphi = p->cl_phi[c1];
-    ca.nJ = p->cl_J[c1];
-    ca.nF = p->cl_F[c1];
-    ca.nP = p->cl_P[c1];
-    ca.prev_tl = p->prev_tl;
-    p->kernel_launches += launch_closures(ca, p->stream);
-    LosmRhsIn full = semi;
-    full.F_new = p->cl_F[c1];
-    full.P_new = p->cl_P[c1];
-    p->kernel_launches += launch_losm_solve(p->mat, full, p->work, p->full_phi, p->full_J, nullptr, p->stream);
-    HWW_CK(cudaGetLastError());
-    p->cur = c1;
-
-    s = p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);
-    if (s) return s;
-    p->steps = n;
-    p->has_prev_tl = 1;
-
-    if (st) {
-        unsigned long long h[ST_COUNT];
-        StepDev sdh;
-        unsigned e = 0;
-        HWW_CK(cudaMemcpyAsync(h, p->stats, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
-        HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
-        HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
-        HWW_CK(cudaStreamSynchronize(p->stream));
-        std::memset(st, 0, sizeof(*st));
-        st->segments = (int64_t)h[ST_SEGMENTS];
-        st->collisions = (int64_t)h[ST_COLLISIONS];
-        st->crossings = (int64_t)h[ST_CROSSINGS];
-        st->reflections = (int64_t)h[ST_REFLECTIONS];
-        st->leaked = (int64_t)h[ST_LEAKED];
-        st->absorbed = (int64_t)h[ST_ABSORBED];
-        st->scatters = (int64_t)h[ST_SCATTERS];
-        st->split_events = (int64_t)h[ST_SPLIT_EVENTS];
-        st->daughters = (int64_t)h[ST_DAUGHTERS];
-        st->roulette_kills = (int64_t)h[ST_RKILLS];
-        st->roulette_survivals = (int64_t)h[ST_RSURVIVE];
-        st->census = (int64_t)h[ST_CENSUS];
-        st->lineage_collisions = (int64_t)h[ST_LINEAGE];
-        st->max_events = (int64_t)h[ST_MAX_EVENTS];
-        st->n_next = (int64_t)sdh.nbank;
-        st->n_start = (int64_t)h[ST_NSTART];
-        st->w_bar_next = sdh.wbar;
-        st->waves = p->last_waves;
-        if (e) HWW_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
-        st->status = err_to_status(e);
-        return (hww_status)st->status;
-    }
-    return HWW_OK;
+    p->cur ^= 1;
+    p->steps += 1;
+    return st ? read_stats(p, st) : HWW_OK;
 }
 
 hww_status get_tallies(const hww_problem* p, int32_t kind, double* out, int64_t n, int32_t on_device) {
@@ -959,9 +992,9 @@ hww_status set_bank(hww_problem* p, const double* x, const double* mu, const int
     if (e != cudaSuccess) return cuda_status(e);
     sdh.nbank = (unsigned long long)n;
     sdh.wbar = w_bar;
+    sdh.bank_loaded = 1;
     HWW_CK(cudaMemcpyAsync(p->sd, &sdh, sizeof(StepDev), cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaStreamSynchronize(p->stream));
-    p->bank_loaded = 1;
     return HWW_OK;
 }
 
@@ -1118,6 +1151,375 @@ hww_status hww_philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, 
     if (e == cudaSuccess) e = cudaMemcpy(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
     cudaFree(d);
     return cuda_status(e);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+struct hww_batch {
+    int P = 0, device = 0, fp32 = 0;
+    cudaStream_t user = nullptr;   // the caller's stream
+    cudaStream_t stream = nullptr; // the batch's own stream (graphs are captured and run on it)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<hww_problem*> m;
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t pre = nullptr, post = nullptr;
+    int tile = 4096, emax = 64;
+    int grid = 0;
+    size_t smem = 0;
+    void* d_args[3] = {};          // TrackArgs per member: wave 0, odd waves, even waves
+    long long* d_tile_off = nullptr;
+    unsigned long long* d_head = nullptr;
+    unsigned long long* d_total = nullptr;
+    unsigned* d_errs = nullptr;
+    unsigned long long* d_qpeak = nullptr;  // per member: largest record count of a wave
+    unsigned long long* h_total = nullptr;  // pinned
+    unsigned* h_errs = nullptr;             // pinned
+    unsigned long long* h_qpeak = nullptr;  // pinned
+    int last_waves = 0;
+};
+
+namespace {
+
+template <class Real>
+__global__ void batch_plan_kernel(const TrackArgs<Real>* args, int P, int tile, long long* tile_off,
+                                  unsigned long long* head) {
+    __shared__ long long cnt[1024];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const TrackArgs<Real>& a = args[p];
+        const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
+        const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
+        cnt[p] = (n_use + tile - 1) / tile;
+        if (!a.from_bank) *a.rout.count = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int p = 0; p < P; ++p) {
+            tile_off[p] = acc;
+            acc += cnt[p];
+        }
+        tile_off[P] = acc;
+        *head = 0;
+    }
+}
+
+template <class Real>
+__global__ void batch_total_kernel(const TrackArgs<Real>* args, int P, unsigned long long* total, unsigned* errs,
+                                   unsigned long long* qpeak) {
+    __shared__ unsigned long long s[256];
+    unsigned long long acc = 0;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const unsigned long long c = *args[p].rout.count;
+        acc += c;
+        errs[p] = *args[p].err;
+        if (c > qpeak[p]) qpeak[p] = c;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = s[0];
+}
+
+template <class Real>
+Banks<Real>& banks_of(hww_problem* p);
+template <>
+Banks<double>& banks_of<double>(hww_problem* p) { return p->b64; }
+template <>
+Banks<float>& banks_of<float>(hww_problem* p) { return p->b32; }
+
+// per-member tracking arguments of wave 0, odd and even waves
+template <class Real>
+hww_status upload_batch_args(hww_batch* b) {
+    std::vector<TrackArgs<Real>> a[3];
+    for (int k = 0; k < 3; ++k) a[k].resize(b->P);
+    for (int i = 0; i < b->P; ++i) {
+        hww_problem* p = b->m[i];
+        p->emax = b->emax;
+        Banks<Real>& bk = banks_of<Real>(p);
+        TrackArgs<Real> t = base_track_args(p, bk);
+        a[0][i] = t;
+        a[0][i].from_bank = 1;
+        a[0][i].rin = bk.q[1];
+        a[0][i].rout = bk.q[0];
+        a[1][i] = t;
+        a[1][i].from_bank = 0;
+        a[1][i].rin = bk.q[0];
+        a[1][i].rout = bk.q[1];
+        a[2][i] = t;
+        a[2][i].from_bank = 0;
+        a[2][i].rin = bk.q[1];
+        a[2][i].rout = bk.q[0];
+    }
+    for (int k = 0; k < 3; ++k)
+        HWW_CK(cudaMemcpyAsync(b->d_args[k], a[k].data(), sizeof(TrackArgs<Real>) * b->P, cudaMemcpyHostToDevice,
+                               b->stream));
+    HWW_CK(cudaStreamSynchronize(b->stream));
+    return HWW_OK;
+}
+
+hww_status upload_batch_args(hww_batch* b) {
+    return b->fp32 ? upload_batch_args<float>(b) : upload_batch_args<double>(b);
+}
+
+// record one stage of every member as parallel branches of a graph
+hww_status capture_stage(hww_batch* b, int pre, cudaGraphExec_t* exec) {
+    if (*exec) {
+        cudaGraphExecDestroy(*exec);
+        *exec = nullptr;
+    }
+    HWW_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(b->fork, b->stream);
+    for (cudaStream_t s : b->pool) cudaStreamWaitEvent(s, b->fork, 0);
+    hww_status st = HWW_OK;
+    for (hww_problem* p : b->m) {
+        st = pre ? stage_pre(p) : stage_post(p);
+        if (st) break;
+    }
+    for (size_t k = 0; k < b->pool.size(); ++k) {
+        cudaEventRecord(b->join[k], b->pool[k]);
+        cudaStreamWaitEvent(b->stream, b->join[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (st || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return st ? st : cuda_status(e);
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_status(e2);
+}
+
+template <class Real>
+hww_status batch_waves(hww_batch* b) {
+    int waves = 0;
+    HWW_CK(cudaMemsetAsync(b->d_qpeak, 0, sizeof(unsigned long long) * b->P, b->stream));
+    for (int wave = 0;; ++wave) {
+        const int k = (wave == 0) ? 0 : (wave % 2 == 1 ? 1 : 2);
+        const TrackArgs<Real>* args = (const TrackArgs<Real>*)b->d_args[k];
+        batch_plan_kernel<Real><<<1, 256, 0, b->stream>>>(args, b->P, b->tile, b->d_tile_off, b->d_head);
+        BatchPlan plan{b->d_tile_off, b->P, b->tile, b->d_head};
+        if (b->fp32)
+            launch_track_batch_fp32((const TrackArgs<float>*)args, plan, b->grid, TRACK_BLOCK, b->smem, b->stream);
+        else
+            launch_track_batch_fp64((const TrackArgs<double>*)args, plan, b->grid, TRACK_BLOCK, b->smem, b->stream);
+        batch_total_kernel<Real><<<1, 256, 0, b->stream>>>(args, b->P, b->d_total, b->d_errs, b->d_qpeak);
+        HWW_CK(cudaGetLastError());
+        ++waves;
+        HWW_CK(cudaMemcpyAsync(b->h_total, b->d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               b->stream));
+        HWW_CK(cudaStreamSynchronize(b->stream));
+        if (*b->h_total == 0) break;
+        if (waves >= MAX_WAVES) return HWW_ERR_TIMEOUT;
+    }
+    b->last_waves = waves;
+    return HWW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void destroy_batch(hww_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->pre) cudaGraphExecDestroy(b->pre);
+    if (b->post) cudaGraphExecDestroy(b->post);
+    for (hww_problem* p : b->m) destroy_problem(p);
+    for (int k = 0; k < 3; ++k)
+        if (b->d_args[k]) cudaFree(b->d_args[k]);
+    if (b->d_tile_off) cudaFree(b->d_tile_off);
+    if (b->d_head) cudaFree(b->d_head);
+    if (b->d_total) cudaFree(b->d_total);
+    if (b->d_errs) cudaFree(b->d_errs);
+    if (b->d_qpeak) cudaFree(b->d_qpeak);
+    if (b->h_qpeak) cudaFreeHost(b->h_qpeak);
+    if (b->h_total) cudaFreeHost(b->h_total);
+    if (b->h_errs) cudaFreeHost(b->h_errs);
+    for (cudaStream_t s : b->pool) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+hww_status create_batch(const hww_problem_desc* descs, int32_t n, void* cuda_stream, int32_t device,
+                        hww_batch** out) {
+    if (!out) return HWW_ERR_ARG;
+    *out = nullptr;
+    if (!descs || n < 1 || n > 1024) return HWW_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (descs[i].precision != descs[0].precision || descs[i].deriv_regions != 0) return HWW_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return HWW_ERR_NO_DEVICE;
+    if (device < 0 || device >= ndev) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(device));
+    hww_batch* b = new (std::nothrow) hww_batch();
+    if (!b) return HWW_ERR_OOM;
+    b->P = n;
+    b->device = device;
+    b->fp32 = descs[0].precision == HWW_FP32_TRACK;
+    b->user = (cudaStream_t)cuda_stream;
+    const int K = std::min(n, 32);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->pool.push_back(s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->join.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        destroy_batch(b);
+        return cuda_status(e);
+    }
+    int Imax = 0;
+    for (int i = 0; i < n; ++i) {
+        hww_problem_desc d = descs[i];
+        d.cuda_stream = (void*)b->pool[i % K];
+        d.device = device;
+        hww_problem* p = nullptr;
+        const hww_status s = create_problem(&d, &p);
+        if (s) {
+            destroy_batch(b);
+            return s;
+        }
+        b->m.push_back(p);
+        Imax = std::max(Imax, p->I);
+    }
+    b->smem = sizeof(long long) * 7 * (size_t)Imax;
+    if (b->smem > 48 * 1024 && track_batch_smem_optin(b->fp32, b->smem) != 0) {
+        destroy_batch(b);
+        return HWW_ERR_CUDA;
+    }
+    int per_sm = track_batch_blocks_per_sm(b->fp32, TRACK_BLOCK, b->smem);
+    if (per_sm < 1) per_sm = 1;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    b->grid = nsm * per_sm;
+    const size_t asz = b->fp32 ? sizeof(TrackArgs<float>) : sizeof(TrackArgs<double>);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&b->d_args[k], asz * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_off, sizeof(long long) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_head, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_total, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_errs, sizeof(unsigned) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_qpeak, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_qpeak, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_total, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_errs, sizeof(unsigned) * n);
+    if (e != cudaSuccess) {
+        destroy_batch(b);
+        return cuda_status(e);
+    }
+    const hww_status s = upload_batch_args(b);
+    if (s) {
+        destroy_batch(b);
+        return s;
+    }
+    *out = b;
+    return HWW_OK;
+}
+
+hww_status batch_problem(hww_batch* b, int32_t i, hww_problem** out) {
+    if (!b || !out || i < 0 || i >= b->P) return HWW_ERR_ARG;
+    *out = b->m[i];
+    return HWW_OK;
+}
+
+hww_status batch_set_tuning(hww_batch* b, int32_t tile, int32_t emax) {
+    if (!b || tile < 256 || emax < 1) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(b->device));
+    b->tile = tile;
+    b->emax = emax;
+    return upload_batch_args(b);
+}
+
+hww_status run_batch_step(hww_batch* b, hww_batch_stats* stats) {
+    if (!b) return HWW_ERR_ARG;
+    for (hww_problem* p : b->m)
+        if (!p->xs_set || !p->ww_set) return HWW_ERR_STATE;
+    HWW_CK(cudaSetDevice(b->device));
+    // order the batch's own stream after the caller's work
+    HWW_CK(cudaEventRecord(b->ev_in, b->user));
+    HWW_CK(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    hww_status s = HWW_OK;
+    if (!b->pre && (s = capture_stage(b, 1, &b->pre))) return s;
+    if (!b->post && (s = capture_stage(b, 0, &b->post))) return s;
+    for (int attempt = 0;; ++attempt) {
+        HWW_CK(cudaGraphLaunch(b->pre, b->stream));
+        s = b->fp32 ? batch_waves<float>(b) : batch_waves<double>(b);
+        if (s) return s;
+        HWW_CK(cudaMemcpyAsync(b->h_errs, b->d_errs, sizeof(unsigned) * b->P, cudaMemcpyDeviceToHost, b->stream));
+        HWW_CK(cudaMemcpyAsync(b->h_qpeak, b->d_qpeak, sizeof(unsigned long long) * b->P, cudaMemcpyDeviceToHost,
+                               b->stream));
+        HWW_CK(cudaStreamSynchronize(b->stream));
+        bool regrow = false;
+        for (int i = 0; i < b->P; ++i) {
+            const unsigned e = b->h_errs[i];
+            if (!(e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW))) continue;
+            if (attempt >= MAX_REGROW) return HWW_ERR_BANK_OVERFLOW;
+            hww_problem* p = b->m[i];
+            unsigned long long ncen = 0;
+            HWW_CK(cudaMemcpy(&ncen, p->counts, sizeof(ncen), cudaMemcpyDeviceToHost));
+            // sized by the demand seen (a truncated pass can under-report it;
+            // regrow_banks at least doubles the capacities anyway)
+            s = regrow_banks(p, (long long)ncen, (long long)b->h_qpeak[i]);
+            if (s) return s;
+            const unsigned keep = e & ~(unsigned)(ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW);
+            HWW_CK(cudaMemcpy(p->err, &keep, sizeof(unsigned), cudaMemcpyHostToDevice));
+            regrow = true;
+        }
+        if (!regrow) break;
+        // the comb and the tracking arguments refer to the regrown buffers
+        if ((s = upload_batch_args(b)) || (s = capture_stage(b, 0, &b->post))) return s;
+    }
+    HWW_CK(cudaGraphLaunch(b->post, b->stream));
+    // and the caller's stream after the batch step
+    HWW_CK(cudaEventRecord(b->ev_out, b->stream));
+    HWW_CK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    for (hww_problem* p : b->m) {
+        p->cur ^= 1;
+        p->steps += 1;
+        p->last_waves = b->last_waves;
+    }
+    if (!stats) return HWW_OK;
+    HWW_CK(cudaStreamSynchronize(b->stream));
+    std::memset(stats, 0, sizeof(*stats));
+    stats->problems = b->P;
+    stats->waves = b->last_waves;
+    for (hww_problem* p : b->m) {
+        hww_step_stats ms;
+        const hww_status r = read_stats(p, &ms);
+        stats->segments += ms.segments;
+        stats->census += ms.census;
+        stats->daughters += ms.daughters;
+        stats->roulette_kills += ms.roulette_kills;
+        stats->absorbed += ms.absorbed;
+        stats->leaked += ms.leaked;
+        if (r && !stats->status) stats->status = r;
+    }
+    return (hww_status)stats->status;
+}
+
+hww_status batch_member_stats(hww_batch* b, int32_t i, hww_step_stats* stats) {
+    if (!b || !stats || i < 0 || i >= b->P) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(b->device));
+    HWW_CK(cudaStreamSynchronize(b->stream));
+    return read_stats(b->m[i], stats);
 }
 
 }  // extern "C"

@@ -38,15 +38,23 @@ enum StatIdx {
     ST_LINEAGE, ST_MAX_EVENTS, ST_NSTART, ST_COUNT
 };
 
-// per-step scalars that live on the device so that no step needs the host
+// per-step state that lives on the device, so that no stage of a step needs
+// a parameter from the host (the stages can be captured once into graphs)
 struct StepDev {
     double wbar;     // weight of each start-bank particle
     double tscale;   // 2^S, tally fixed-point scale
     double cscale;   // 2^Sc, comb weight fixed-point scale
     int S, Sc;
     unsigned U_comb; // comb offset word: teeth at (k + (2U+1)/2^33) W / N
-    int pad0;
-    double pad1;
+    unsigned k0, k1; // Philox key of the step: (seed_lo, seed_hi ^ n)
+    int cur;         // closure set holding the initial conditions of the step
+    int birth;       // the step starts from the pulse
+    int bank_loaded; // set_bank was called since the last step
+    int override_c;  // set_ww_centers was called since the last step
+    int has_prev;    // a previous step exists (lagged windows)
+    int ww_src;      // 0 none, 1 HLOSM, 2 previous track-length flux, 3 override
+    int ww_on;
+    unsigned long long step;       // completed steps
     unsigned long long nbank;      // start-bank size
     unsigned long long W;          // total census weight (fixed point)
     unsigned long long ncensus;    // census bank size of the step
@@ -84,11 +92,9 @@ template <class Real>
 struct TrackArgs {
     int I, B, emax;
     long long N;      // source particles per step (variance batches)
-    int ww_on;
-    int from_bank, birth;
+    int from_bank;
     int bc_l, bc_r;
     int birth_cell_pos, birth_cell_neg;
-    uint32_t k0, k1;
     double tau0;      // v dt
     double src_x;
     const double* edges;
@@ -96,6 +102,8 @@ struct TrackArgs {
     const double* c;
     const float* dxf;        // FP32 cell widths
     const float* inv_sigt_f; // FP32 1/Sigma_t
+    const float4* cellf;     // FP32 (width, 1/Sigma_t, c, 0) per cell, one load
+    const double2* ww_hl;    // (ceiling, floor) per cell, one load
     const double* ww_c;
     const double* ww_hi;
     const double* ww_lo;
@@ -116,8 +124,32 @@ struct TrackArgs {
     unsigned* err;
 };
 
+// work plan of one batched tracking launch: problem p owns tiles
+// [tile_off[p], tile_off[p+1]) of `tile` items each; blocks pop tiles from
+// the counter `head`
+struct BatchPlan {
+    const long long* tile_off;  // P+1
+    int P;
+    int tile;
+    unsigned long long* head;
+};
+
 // kernels implemented in the tracking translation units
 void launch_track_fp64(const TrackArgs<double>& a, int grid, int block, size_t smem, cudaStream_t s);
 void launch_track_fp32(const TrackArgs<float>& a, int grid, int block, size_t smem, cudaStream_t s);
+void launch_track_batch_fp64(const TrackArgs<double>* args, const BatchPlan& plan, int grid, int block, size_t smem,
+                             cudaStream_t s);
+void launch_track_batch_fp32(const TrackArgs<float>* args, const BatchPlan& plan, int grid, int block, size_t smem,
+                             cudaStream_t s);
+int track_batch_smem_optin_fp32(size_t smem);
+int track_batch_smem_optin_fp64(size_t smem);
+int track_batch_blocks_per_sm_fp32(int block, size_t smem);
+int track_batch_blocks_per_sm_fp64(int block, size_t smem);
+inline int track_batch_smem_optin(int fp32, size_t smem) {
+    return fp32 ? track_batch_smem_optin_fp32(smem) : track_batch_smem_optin_fp64(smem);
+}
+inline int track_batch_blocks_per_sm(int fp32, int block, size_t smem) {
+    return fp32 ? track_batch_blocks_per_sm_fp32(block, smem) : track_batch_blocks_per_sm_fp64(block, smem);
+}
 
 }  // namespace hww

@@ -88,18 +88,42 @@ __global__ void losm_factor_kernel(LosmMat m, double theta, int bc_l, int bc_r, 
 // ---------------------------------------------------------------------------
 // right-hand side
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double moment_rhs(const LosmMat& m, const LosmRhsIn& in, int i) {
+struct RhsPtrs {
+    const double *phi_old, *J_old, *F_old, *F_new, *P_new;
+};
+
+__device__ __forceinline__ RhsPtrs resolve(const LosmRhsIn& in) {
+    RhsPtrs r;
+    if (in.sd) {
+        const int c = in.sd->cur;
+        r.phi_old = in.set_phi[c];
+        r.J_old = in.set_J[c];
+        r.F_old = in.set_F[c];
+        r.F_new = in.full ? in.set_F[1 - c] : in.set_F[c];
+        r.P_new = in.full ? in.set_P[1 - c] : in.set_P[c];
+    } else {
+        r.phi_old = in.phi_old;
+        r.J_old = in.J_old;
+        r.F_old = in.F_old;
+        r.F_new = in.F_new;
+        r.P_new = in.P_new;
+    }
+    return r;
+}
+
+__device__ __forceinline__ double moment_rhs(const LosmMat& m, const RhsPtrs& in, int i) {
     const double th = m.theta, tm1 = th - 1.0;
     const double old = (in.phi_old[i + 1] - in.phi_old[i]) * (1.0 / 3.0) + m.eS[i] * in.J_old[i] -
                        in.F_old[i + 1] + in.F_old[i];
     return m.eJ[i] * in.J_old[i] + th * (in.F_new[i + 1] - in.F_new[i]) + tm1 * old;
 }
 
-__global__ void losm_rhs_kernel(LosmMat m, LosmRhsIn in, double* u, double* mom) {
+__global__ void losm_rhs_kernel(LosmMat m, LosmRhsIn rin, double* u, double* mom) {
     const int I = m.I;
     const double th = m.theta, tm1 = th - 1.0;
-    const double PL = in.P_new ? in.P_new[0] : in.PL;
-    const double PR = in.P_new ? in.P_new[1] : in.PR;
+    const RhsPtrs in = resolve(rin);
+    const double PL = in.P_new ? in.P_new[0] : rin.PL;
+    const double PR = in.P_new ? in.P_new[1] : rin.PR;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= I + 1; r += gridDim.x * blockDim.x) {
         double R;
         if (r == 0) {
@@ -113,8 +137,8 @@ __global__ void losm_rhs_kernel(LosmMat m, LosmRhsIn in, double* u, double* mom)
             const double ml = moment_rhs(m, in, r - 1);
             const double mr = moment_rhs(m, in, r);
             mom[r] = mr;
-            const double qn = in.q_new ? in.q_new[r - 1] : 0.0;
-            const double qo = in.q_old ? in.q_old[r - 1] : 0.0;
+            const double qn = rin.q_new ? rin.q_new[r - 1] : 0.0;
+            const double qo = rin.q_old ? rin.q_old[r - 1] : 0.0;
             const double oldb = in.J_old[r] - in.J_old[r - 1] + m.cA[r - 1] * in.phi_old[r] - qo;
             const double rr = m.cP[r - 1] * in.phi_old[r] + th * qn + tm1 * oldb;
             R = rr + th * ml * m.invd[r - 1] - th * mr * m.invd[r];
@@ -218,22 +242,27 @@ __device__ __forceinline__ double quantize_center(double c) {
 }
 
 __global__ void ww_centers_kernel(WwArgs a) {
-    const double mx = a.mx_ptr ? *a.mx_ptr : 0.0;
+    const int source = a.sd->ww_src;
+    if (source == 0) return;
+    const double mx = (source == 2) ? *a.mx_prev : *a.mx_hlosm;
+    const double* phit = (source == 2) ? a.phit_prev : a.phit_hlosm;
     const double scale = (a.scaling == 0) ? a.sd->wbar : 1.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.I; i += gridDim.x * blockDim.x) {
         double ctr;
-        if (a.source == 3) {
+        if (source == 3) {
             ctr = a.override_c[i];
         } else {
-            const double f = a.phit[i] > 0.0 ? a.phit[i] : 0.0;
+            const double f = phit[i] > 0.0 ? phit[i] : 0.0;
             const double ratio = (mx > 0.0) ? f / mx : 1.0;
             const double b = ratio * (1.0 - a.eps) + a.eps;
             ctr = scale * b;
         }
         ctr = quantize_center(ctr);
+        const double hi = ctr * a.rho, lo = ctr / a.rho;
         a.ww_c[i] = ctr;
-        a.ww_hi[i] = ctr * a.rho;
-        a.ww_lo[i] = ctr / a.rho;
+        a.ww_hi[i] = hi;
+        a.ww_lo[i] = lo;
+        a.ww_hl[i] = make_double2(hi, lo);
     }
 }
 
@@ -252,9 +281,14 @@ __global__ void vec_max_kernel(const double* x, int n, double* out) {
     if (threadIdx.x == 0) *out = s[0];
 }
 
-// step scalars: tally and comb fixed-point scales, comb offset
-__global__ void step_scalars_kernel(StepDev* sd, int nbits, uint32_t k0, uint32_t k1, unsigned long long* stats) {
+// step scalars: Philox key, tally and comb fixed-point scales, comb offset,
+// birth flag and the window source of the step
+__global__ void step_scalars_kernel(StepDev* sd, int nbits, unsigned long long seed, int mode,
+                                    unsigned long long* stats) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long n = sd->step + 1;
+    sd->k0 = (uint32_t)seed;
+    sd->k1 = (uint32_t)(seed >> 32) ^ (uint32_t)n;
     int E = 0;
     if (sd->wbar > 0.0) {
         int e;
@@ -266,8 +300,12 @@ __global__ void step_scalars_kernel(StepDev* sd, int nbits, uint32_t k0, uint32_
     sd->tscale = pow2(sd->S);
     sd->cscale = pow2(sd->Sc);
     uint32_t r[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xC0B0u};
-    philox4x32_10(r, k0, k1);
+    philox4x32_10(r, sd->k0, sd->k1);
     sd->U_comb = r[1];
+    sd->birth = (sd->step == 0 && !sd->bank_loaded) ? 1 : 0;
+    const int src = sd->override_c ? 3 : (mode == 0) ? 1 : (mode == 2 && sd->has_prev) ? 2 : 0;
+    sd->ww_src = src;
+    sd->ww_on = src != 0;
     stats[ST_NSTART] = sd->nbank;
 }
 
@@ -280,6 +318,7 @@ __device__ __forceinline__ double cen_val(const ClosureArgs& a, int q, int i, do
 
 __global__ void closure_kernel(ClosureArgs a) {
     const int I = a.I;
+    double* nP = a.set_P[1 - a.sd->cur];
     const double isc = pow2(-a.sd->S);
     const double PL = (a.bc_l == 1) ? 0.0 : (acc_to_double(a.bnd[2]) * isc) / ((double)a.N * a.dt);
     const double PR = (a.bc_r == 1) ? 0.0 : (acc_to_double(a.bnd[5]) * isc) / ((double)a.N * a.dt);
@@ -300,8 +339,8 @@ __global__ void closure_kernel(ClosureArgs a) {
         }
         a.rJ[i] = J;
         if (i == 0) {
-            a.nP[0] = PL;
-            a.nP[1] = PR;
+            nP[0] = PL;
+            nP[1] = PR;
         }
     }
 }
@@ -319,20 +358,24 @@ __device__ __forceinline__ double ma_at(const double* in, int m, int j, int k) {
 
 __global__ void filter_kernel(ClosureArgs a) {
     const int I = a.I, k = a.filter_k;
+    const int c1 = 1 - a.sd->cur;
+    double* nphi = a.set_phi[c1];
+    double* nJ = a.set_J[c1];
+    double* nF = a.set_F[c1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= I + 1; i += gridDim.x * blockDim.x) {
         if (i >= 1 && i <= I) {
-            a.nphi[i] = k ? ma_at(a.rphi, I, i, k) : a.rphi[i - 1];
-            a.nF[i] = k ? ma_at(a.rF, I, i, k) : a.rF[i - 1];
+            nphi[i] = k ? ma_at(a.rphi, I, i, k) : a.rphi[i - 1];
+            nF[i] = k ? ma_at(a.rF, I, i, k) : a.rF[i - 1];
         }
-        if (i <= I) a.nJ[i] = k ? ma_at(a.rJ, I + 1, i + 1, k) : a.rJ[i];
+        if (i <= I) nJ[i] = k ? ma_at(a.rJ, I + 1, i + 1, k) : a.rJ[i];
         if (i == 0) {
             // end values are kept by the filter, so the boundary copies use them
-            a.nphi[0] = a.rphi[0];
-            a.nF[0] = a.rF[0];
+            nphi[0] = a.rphi[0];
+            nF[0] = a.rF[0];
         }
         if (i == I + 1) {
-            a.nphi[I + 1] = a.rphi[I - 1];
-            a.nF[I + 1] = a.rF[I - 1];
+            nphi[I + 1] = a.rphi[I - 1];
+            nF[I + 1] = a.rF[I - 1];
         }
     }
 }
@@ -357,19 +400,19 @@ int launch_losm_solve(const LosmMat& m, const LosmRhsIn& in, const LosmWork& w, 
     return 2;
 }
 
-int launch_ww_centers(const WwArgs& a, cudaStream_t s) {
+int launch_ww_centers(const WwArgs& a, int lagged, cudaStream_t s) {
     int n = 0;
-    if (a.source == 2) {
-        vec_max_kernel<<<1, 256, 0, s>>>(a.phit, a.I, (double*)a.mx_ptr);
+    if (lagged) {
+        vec_max_kernel<<<1, 256, 0, s>>>(a.phit_prev, a.I, (double*)a.mx_prev);
         ++n;
     }
     ww_centers_kernel<<<small_grid(a.I), 128, 0, s>>>(a);
     return n + 1;
 }
 
-void launch_step_scalars(StepDev* sd, int nbits, uint32_t k0, uint32_t k1, unsigned long long* stats,
+void launch_step_scalars(StepDev* sd, int nbits, unsigned long long seed, int mode, unsigned long long* stats,
                          cudaStream_t s) {
-    step_scalars_kernel<<<1, 32, 0, s>>>(sd, nbits, k0, k1, stats);
+    step_scalars_kernel<<<1, 32, 0, s>>>(sd, nbits, seed, mode, stats);
 }
 
 int launch_closures(const ClosureArgs& a, cudaStream_t s) {

@@ -21,8 +21,18 @@ struct LosmMat {
     double* cp;      // [I+2] C_r / den_r
 };
 
-// right-hand-side inputs of one solve (paper layout)
+// right-hand-side inputs of one solve (paper layout).  With `sd` set, the
+// vectors come from the two closure sets by the device's parity: the old
+// level is set `cur`; the new-level closure is set `cur` again for the
+// semi-implicit solve (full = 0) and set 1-cur for the fully implicit one.
+// Without `sd`, the explicit pointers and values are used.
 struct LosmRhsIn {
+    const StepDev* sd;
+    int full;
+    const double* set_phi[2];
+    const double* set_J[2];
+    const double* set_F[2];
+    const double* set_P[2];
     const double* phi_old;  // I+2
     const double* J_old;    // I+1
     const double* F_old;    // I+2
@@ -41,14 +51,16 @@ struct LosmWork {
 
 struct WwArgs {
     int I;
-    int source;   // 1 HLOSM solution, 2 previous track-length flux, 3 override
     int scaling;  // 0 mean weight, 1 literal
     double eps, rho;
-    const StepDev* sd;
-    const double* phit;
-    const double* mx_ptr;
+    const StepDev* sd;       // ww_src picks the source: 1 HLOSM, 2 previous flux, 3 override
+    const double* phit_hlosm;
+    const double* phit_prev;
+    const double* mx_hlosm;
+    const double* mx_prev;
     const double* override_c;
     double *ww_c, *ww_hi, *ww_lo;
+    double2* ww_hl;  // (ceiling, floor) packed for the tracking kernels
 };
 
 struct ClosureArgs {
@@ -63,7 +75,7 @@ struct ClosureArgs {
     const Acc128* tl;
     const Acc128* bnd;
     double *rphi, *rJ, *rF;        // unfiltered: I, I+1, I
-    double *nphi, *nJ, *nF, *nP;   // closure set at t^n: I+2, I+1, I+2, 2
+    double *set_phi[2], *set_J[2], *set_F[2], *set_P[2];  // closure sets; t^n goes to 1-cur
     double* prev_tl;               // I
 };
 
@@ -71,8 +83,8 @@ void launch_losm_setup(const LosmMat& m, const double* dx, const double* sigt, c
                        double dt, double theta, int bc_l, int bc_r, unsigned* err, cudaStream_t s);
 int launch_losm_solve(const LosmMat& m, const LosmRhsIn& in, const LosmWork& w, double* phi, double* J,
                       double* mx, cudaStream_t s);
-int launch_ww_centers(const WwArgs& a, cudaStream_t s);
-void launch_step_scalars(StepDev* sd, int nbits, uint32_t k0, uint32_t k1, unsigned long long* stats,
+int launch_ww_centers(const WwArgs& a, int lagged, cudaStream_t s);
+void launch_step_scalars(StepDev* sd, int nbits, unsigned long long seed, int mode, unsigned long long* stats,
                          cudaStream_t s);
 int launch_closures(const ClosureArgs& a, cudaStream_t s);
 

@@ -210,6 +210,12 @@ __global__ void comb_finalize_kernel(StepDev* sd, const unsigned long long* goff
     const unsigned long long m = *ncensus_ptr;
     sd->ncensus = m;
     sd->W = W;
+    // the step is complete: advance the device-side step state
+    sd->step += 1;
+    sd->cur ^= 1;
+    sd->override_c = 0;
+    sd->bank_loaded = 0;
+    sd->has_prev = 1;
     if (m > (unsigned long long)cen_cap) atomicOr(err, ERR_CENSUS_OVERFLOW);
     if (W == 0) {
         sd->nbank = 0;

@@ -2,6 +2,10 @@
 // warp-aggregated slot reservation, per-block counters and the flush of the
 // block-private fixed-point tallies.
 #pragma once
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "hww_internal.cuh"
 
 namespace hww {
@@ -100,6 +104,22 @@ __device__ __forceinline__ void flush_tallies(const long long* sm, int I, Acc128
         const long long v = sm[i];
         if (v != 0) add128(i < 3 * I ? &tl[i] : &cent[i - 3 * I], v);
     }
+}
+
+// The dynamic shared memory limit is a process-wide attribute of a kernel on
+// a device: it is only ever raised, so that creating a problem with fewer
+// cells does not lower the limit that an existing problem launches with.
+inline int raise_smem_limit(const void* fn, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> lim;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> g(mu);
+    size_t& l = lim[std::make_pair(fn, dev)];
+    if (smem <= l) return 0;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) l = smem;
+    return (int)e;
 }
 
 }  // namespace hww

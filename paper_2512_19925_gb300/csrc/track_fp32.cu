@@ -4,7 +4,9 @@
 // the top 23 bits of the same Philox words), but the geometry runs in FP32:
 // a track keeps its cell index and an FP32 offset from the cell's left edge,
 // an FP32 direction, an FP32 distance to census and FP32 flight distances.
-// Weights and the window tests stay FP64; tally contributions are formed in
+// Weights stay FP64 (the window tests compare their bit patterns, and the
+// split count and survival test use an FP32 ratio and a product in place of
+// FP64 divides); tally contributions are formed in
 // exact integer arithmetic from a fixed-point copy of the weight,
 //     round(W * f),   W = round(w 2^S) (64-bit),  f = l, l mu, l (1/3 - mu^2) (FP32),
 // i.e. the exact product of the 64-bit weight and the 24-bit mantissa of f,
@@ -82,25 +84,23 @@ __device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32
     a.rout.jcount[slot] = jcount;
 }
 
-__global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
-    extern __shared__ long long sm[];
+// The event loop over items [item, item_end) with the given stride; b_blk is
+// the variance batch whose row is kept in shared memory (-1: none).
+__device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long item, const long long item_end,
+                                          const long long stride, const int b_blk, long long* sm,
+                                          Counters& cnt) {
     const int I = a.I;
     long long* s_tl = sm;
     long long* s_cen = sm + 3 * I;
-    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) sm[i] = 0;
-    __syncthreads();
-    Counters cnt;
-    cnt.zero();
+    long long* s_bat = sm + 6 * I;  // batch row of the current id range
     const double tscale = a.sd->tscale;
     const double cscale = a.sd->cscale;
     const double wbar = a.sd->wbar;
+    const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
+    const int birth = a.sd->birth, ww_on = a.sd->ww_on;
     const float tau0 = (float)a.tau0;
-    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
-    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
-    const long long stride = (long long)gridDim.x * blockDim.x;
     const long long Wbar = to_fixed(wbar, tscale);
 
-    long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     P32 q;
     P32 base;  // record whose daughters are being expanded
     uint32_t jnext = 0, jend = 0;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
                 q.lin = lineage_hash(base.lin, base.e, jnext);
                 q.e = 0;
                 ++jnext;
-            } else if (item < n_use) {
+            } else if (item < item_end) {
                 const long long i = item;
                 item += stride;
                 if (a.from_bank) {
@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
                     q.tau = tau0;
                     q.w = wbar;
                     q.W = Wbar;
-                    if (a.birth) {
+                    if (birth) {
                         uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
-                        philox4x32_10(r, a.k0, a.k1);
+                        philox4x32_10(r, k0, k1);
                         q.mu = 2.0f * u01f(r[1]) - 1.0f;
                         const double x = a.src_x;
                         if (x <= a.edges[0] && q.mu < 0.0f && a.bc_l == 1) q.mu = -q.mu;
@@ -178,12 +178,13 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
             continue;
         }
         uint32_t r[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 2u * q.e};
-        philox4x32_10(r, a.k0, a.k1);
+        philox4x32_10(r, k0, k1);
         const float uf = u01f(r[1]);
         const float uc = u01f(r[3]);
         const int k = q.cell;
-        const float dxk = a.dxf[k];
-        const float dcoll = -logf(uf) * a.inv_sigt_f[k];
+        const float4 cf = __ldg(&a.cellf[k]);  // width, 1/Sigma_t, c
+        const float dxk = cf.x;
+        const float dcoll = -logf(uf) * cf.y;
         const float dedge = ((q.mu > 0.0f) ? (dxk - q.xo) : -q.xo) * q.inv_mu;
         const float dcens = q.tau;
         int ev;
@@ -207,7 +208,10 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
                 sadd(&s_tl[k], g.s0);
                 sadd(&s_tl[I + k], g.s1);
                 sadd(&s_tl[2 * I + k], g.s2);
-                add128(&a.batch[(long long)b * I + k], g.s0);
+                if (b == b_blk)
+                    sadd(&s_bat[k], g.s0);
+                else
+                    add128(&a.batch[(long long)b * I + k], g.s0);
             }
         }
         cnt.v[ST_SEGMENTS]++;
@@ -270,11 +274,11 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
                 cnt.v[ST_REFLECTIONS]++;
             } else {
                 q.cell = nk;
-                q.xo = (q.mu > 0.0f) ? 0.0f : a.dxf[nk];
+                q.xo = (q.mu > 0.0f) ? 0.0f : __ldg(&a.cellf[nk]).x;
             }
         } else {
             cnt.v[ST_COLLISIONS]++;
-            if ((double)uc >= a.c[k]) {
+            if (uc >= cf.z) {
                 cnt.v[ST_ABSORBED]++;
                 cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
                 have = false;
@@ -284,17 +288,20 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
             r2[1] = (uint32_t)q.lin;
             r2[2] = (uint32_t)(q.lin >> 32);
             r2[3] = 2u * e_ev + 1u;
-            philox4x32_10(r2, a.k0, a.k1);
+            philox4x32_10(r2, k0, k1);
             have_r2 = true;
             q.mu = 2.0f * u01f(r2[1]) - 1.0f;
             q.inv_mu = 1.0f / q.mu;
             cnt.v[ST_SCATTERS]++;
         }
-        if (a.ww_on) {
+        if (ww_on) {
             const int kc = q.cell;
-            if (dgt(q.w, a.ww_hi[kc])) {
+            const double2 hl = __ldg(&a.ww_hl[kc]);  // ceiling, floor
+            if (dgt(q.w, hl.x)) {
                 const double ctr = a.ww_c[kc];
-                const double ndd = ceil(q.w / ctr);
+                // split count from an FP32 ratio (the FP32 path's own rounding)
+                const float ndf = ceilf((float)q.w / (float)ctr);
+                const double ndd = (double)fmaxf(ndf, 2.0f);
                 if (ndd > (double)MAX_DAUGHTERS) {
                     atomicOr(a.err, ERR_DAUGHTERS);
                     have = false;
@@ -315,18 +322,18 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
                 q.W = to_fixed(wd, tscale);
                 q.lin = lineage_hash(q.lin, e_ev, 0);
                 q.e = 0;
-            } else if (dgt(a.ww_lo[kc], q.w)) {
+            } else if (dgt(hl.y, q.w)) {
                 if (!have_r2) {
                     r2[0] = q.id;
                     r2[1] = (uint32_t)q.lin;
                     r2[2] = (uint32_t)(q.lin >> 32);
                     r2[3] = 2u * e_ev + 1u;
-                    philox4x32_10(r2, a.k0, a.k1);
+                    philox4x32_10(r2, k0, k1);
                 }
                 const double ctr = a.ww_c[kc];
+                // survive iff u < w / ww, tested as u ww < w (no divide)
                 const double ur = u01(r2[2], r2[3]);
-                const double ps = q.w / ctr;
-                if (ur < ps) {
+                if (ur * ctr < q.w) {
                     q.w = ctr;
                     q.W = to_fixed(ctr, tscale);
                     cnt.v[ST_RSURVIVE]++;
@@ -339,9 +346,104 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
+    extern __shared__ long long sm[];
+    const int I = a.I;
+    for (int i = threadIdx.x; i < 7 * I; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    Counters cnt;
+    cnt.zero();
+    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
+    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
+    // wave 0: each block takes a contiguous id range, so nearly all of its
+    // segments fall in one variance batch (kept in shared memory); record
+    // waves: grid-stride over the records
+    long long stride, item, item_end;
+    int b_blk = -1;
+    if (a.from_bank) {
+        const long long chunk = (n_use + gridDim.x - 1) / gridDim.x;
+        item = (long long)blockIdx.x * chunk + threadIdx.x;
+        item_end = min(n_use, (long long)(blockIdx.x + 1) * chunk);
+        stride = blockDim.x;
+        if ((long long)blockIdx.x * chunk < n_use) b_blk = batch_of((uint32_t)((long long)blockIdx.x * chunk), a.B, a.N);
+    } else {
+        item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        item_end = n_use;
+        stride = (long long)gridDim.x * blockDim.x;
+    }
+    run_items(a, item, item_end, stride, b_blk, sm, cnt);
     __syncthreads();
     flush_tallies(sm, I, a.tl, a.cent);
+    if (b_blk >= 0)
+        for (int i = threadIdx.x; i < I; i += blockDim.x)
+            if (sm[6 * I + i] != 0) add128(&a.batch[(long long)b_blk * I + i], sm[6 * I + i]);
     flush_counters(cnt, a.stats);
+}
+
+// Persistent batched variant: blocks pop tiles (problem, id range) from a
+// device counter; the block-private tallies are flushed when a block moves
+// to another problem, the batch row after every tile.
+__global__ void __launch_bounds__(256, 3) track32_kernel_batch(const TrackArgs<float>* args, BatchPlan plan) {
+    extern __shared__ long long sm[];
+    __shared__ TrackArgs<float> A;
+    __shared__ long long s_t;
+    __shared__ int s_p;
+    Counters cnt;
+    cnt.zero();
+    const long long total = plan.tile_off[plan.P];
+    int cur = -1, Ic = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long t = (long long)atomicAdd(plan.head, 1ull);
+            int p = -1;
+            if (t < total) {
+                int lo = 0, hi = plan.P - 1;  // largest p with tile_off[p] <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (plan.tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                p = lo;
+            }
+            s_t = t;
+            s_p = p;
+        }
+        __syncthreads();
+        const long long t = s_t;
+        const int p = s_p;
+        if (p < 0 || p != cur) {  // a problem switch, or no tile left (also on the first pop)
+            if (cur >= 0) {
+                flush_tallies(sm, Ic, A.tl, A.cent);
+                flush_counters(cnt, A.stats);
+                cnt.zero();
+                __syncthreads();
+            }
+            if (p < 0) break;
+            if (threadIdx.x == 0) A = args[p];
+            __syncthreads();
+            cur = p;
+            Ic = A.I;
+            for (int i = threadIdx.x; i < 7 * Ic; i += blockDim.x) sm[i] = 0;
+            __syncthreads();
+        }
+        const long long n_in = A.from_bank ? (long long)A.sd->nbank : (long long)*A.rin.count;
+        const long long n_use = (!A.from_bank && n_in > A.rin.cap) ? A.rin.cap : n_in;
+        const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
+        const long long i1 = min(n_use, i0 + (long long)plan.tile);
+        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N) : -1;
+        run_items(A, i0 + threadIdx.x, i1, blockDim.x, b_tile, sm, cnt);
+        __syncthreads();
+        if (b_tile >= 0)
+            for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
+                const long long v = sm[6 * Ic + i];
+                if (v != 0) {
+                    add128(&A.batch[(long long)b_tile * Ic + i], v);
+                    sm[6 * Ic + i] = 0;
+                }
+            }
+        __syncthreads();
+    }
 }
 
 }  // namespace
@@ -351,12 +453,27 @@ void launch_track_fp32(const TrackArgs<float>& a, int grid, int block, size_t sm
 }
 
 int track_smem_optin_fp32(size_t smem) {
-    return (int)cudaFuncSetAttribute(track32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return raise_smem_limit((const void*)track32_kernel, smem);
 }
 
 int track_blocks_per_sm_fp32(int block, size_t smem) {
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, track32_kernel, block, smem);
+    return n;
+}
+
+void launch_track_batch_fp32(const TrackArgs<float>* args, const BatchPlan& plan, int grid, int block, size_t smem,
+                             cudaStream_t s) {
+    track32_kernel_batch<<<grid, block, smem, s>>>(args, plan);
+}
+
+int track_batch_smem_optin_fp32(size_t smem) {
+    return raise_smem_limit((const void*)track32_kernel_batch, smem);
+}
+
+int track_batch_blocks_per_sm_fp32(int block, size_t smem) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, track32_kernel_batch, block, smem);
     return n;
 }
 

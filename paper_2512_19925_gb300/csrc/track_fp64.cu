@@ -57,25 +57,23 @@ __device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P6
     a.rout.jcount[slot] = jcount;
 }
 
-__global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
-    extern __shared__ long long sm[];
+// The event loop over items [item, item_end) with the given stride; b_blk is
+// the variance batch whose row is kept in shared memory (-1: none).
+__device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long item, const long long item_end,
+                                          const long long stride, const int b_blk, long long* sm,
+                                          Counters& cnt) {
     const int I = a.I;
     long long* s_tl = sm;
     long long* s_cen = sm + 3 * I;
-    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) sm[i] = 0;
-    __syncthreads();
-    Counters cnt;
-    cnt.zero();
+    long long* s_bat = sm + 6 * I;  // batch row of the current id range
     const double tscale = a.sd->tscale;
     const double cscale = a.sd->cscale;
     const double wbar = a.sd->wbar;
-    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
-    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
+    const int birth = a.sd->birth, ww_on = a.sd->ww_on;
 
     // flattened event loop: a lane whose track ends loads its next one while
     // the other lanes take their next event
-    long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     P64 q;
     P64 base;  // record whose daughters are being expanded
     uint32_t jnext = 0, jend = 0;
@@ -89,7 +87,7 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
                 q.lin = lineage_hash(base.lin, base.e, jnext);
                 q.e = 0;
                 ++jnext;
-            } else if (item < n_use) {
+            } else if (item < item_end) {
                 const long long i = item;
                 item += stride;
                 if (a.from_bank) {
@@ -98,9 +96,9 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
                     q.e = 0;
                     q.tau = a.tau0;
                     q.w = wbar;
-                    if (a.birth) {
+                    if (birth) {
                         uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
-                        philox4x32_10(r, a.k0, a.k1);
+                        philox4x32_10(r, k0, k1);
                         q.mu = 2.0 * u01(r[0], r[1]) - 1.0;
                         q.x = a.src_x;
                         if (q.x <= a.edges[0] && q.mu < 0.0 && a.bc_l == 1) q.mu = -q.mu;
@@ -150,7 +148,7 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
             continue;
         }
         uint32_t r[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 2u * q.e};
-        philox4x32_10(r, a.k0, a.k1);
+        philox4x32_10(r, k0, k1);
         const double uf = u01(r[0], r[1]);
         const double uc = u01(r[2], r[3]);
         const int k = q.cell;
@@ -183,7 +181,10 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
                 sadd(&s_tl[k], g.s0);
                 sadd(&s_tl[I + k], g.s1);
                 sadd(&s_tl[2 * I + k], g.s2);
-                add128(&a.batch[(long long)b * I + k], g.s0);
+                if (b == b_blk)
+                    sadd(&s_bat[k], g.s0);
+                else
+                    add128(&a.batch[(long long)b * I + k], g.s0);
             }
         }
         cnt.v[ST_SEGMENTS]++;
@@ -267,13 +268,13 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
             r2[1] = (uint32_t)q.lin;
             r2[2] = (uint32_t)(q.lin >> 32);
             r2[3] = 2u * e_ev + 1u;
-            philox4x32_10(r2, a.k0, a.k1);
+            philox4x32_10(r2, k0, k1);
             have_r2 = true;
             q.mu = 2.0 * u01(r2[0], r2[1]) - 1.0;
             q.inv_mu = 1.0 / q.mu;
             cnt.v[ST_SCATTERS]++;
         }
-        if (a.ww_on) {
+        if (ww_on) {
             const int kc = q.cell;
             const double hi = a.ww_hi[kc];
             const double lo = a.ww_lo[kc];
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
                     r2[1] = (uint32_t)q.lin;
                     r2[2] = (uint32_t)(q.lin >> 32);
                     r2[3] = 2u * e_ev + 1u;
-                    philox4x32_10(r2, a.k0, a.k1);
+                    philox4x32_10(r2, k0, k1);
                 }
                 const double ctr = a.ww_c[kc];
                 const double ur = u01(r2[2], r2[3]);
@@ -322,9 +323,104 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
+    extern __shared__ long long sm[];
+    const int I = a.I;
+    for (int i = threadIdx.x; i < 7 * I; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    Counters cnt;
+    cnt.zero();
+    const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
+    const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
+    // wave 0: each block takes a contiguous id range, so nearly all of its
+    // segments fall in one variance batch (kept in shared memory); record
+    // waves: grid-stride over the records
+    long long stride, item, item_end;
+    int b_blk = -1;
+    if (a.from_bank) {
+        const long long chunk = (n_use + gridDim.x - 1) / gridDim.x;
+        item = (long long)blockIdx.x * chunk + threadIdx.x;
+        item_end = min(n_use, (long long)(blockIdx.x + 1) * chunk);
+        stride = blockDim.x;
+        if ((long long)blockIdx.x * chunk < n_use) b_blk = batch_of((uint32_t)((long long)blockIdx.x * chunk), a.B, a.N);
+    } else {
+        item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        item_end = n_use;
+        stride = (long long)gridDim.x * blockDim.x;
+    }
+    run_items(a, item, item_end, stride, b_blk, sm, cnt);
     __syncthreads();
     flush_tallies(sm, I, a.tl, a.cent);
+    if (b_blk >= 0)
+        for (int i = threadIdx.x; i < I; i += blockDim.x)
+            if (sm[6 * I + i] != 0) add128(&a.batch[(long long)b_blk * I + i], sm[6 * I + i]);
     flush_counters(cnt, a.stats);
+}
+
+// Persistent batched variant: blocks pop tiles (problem, id range) from a
+// device counter; the block-private tallies are flushed when a block moves
+// to another problem, the batch row after every tile.
+__global__ void __launch_bounds__(256, 3) track64_kernel_batch(const TrackArgs<double>* args, BatchPlan plan) {
+    extern __shared__ long long sm[];
+    __shared__ TrackArgs<double> A;
+    __shared__ long long s_t;
+    __shared__ int s_p;
+    Counters cnt;
+    cnt.zero();
+    const long long total = plan.tile_off[plan.P];
+    int cur = -1, Ic = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long t = (long long)atomicAdd(plan.head, 1ull);
+            int p = -1;
+            if (t < total) {
+                int lo = 0, hi = plan.P - 1;  // largest p with tile_off[p] <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (plan.tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                p = lo;
+            }
+            s_t = t;
+            s_p = p;
+        }
+        __syncthreads();
+        const long long t = s_t;
+        const int p = s_p;
+        if (p < 0 || p != cur) {  // a problem switch, or no tile left (also on the first pop)
+            if (cur >= 0) {
+                flush_tallies(sm, Ic, A.tl, A.cent);
+                flush_counters(cnt, A.stats);
+                cnt.zero();
+                __syncthreads();
+            }
+            if (p < 0) break;
+            if (threadIdx.x == 0) A = args[p];
+            __syncthreads();
+            cur = p;
+            Ic = A.I;
+            for (int i = threadIdx.x; i < 7 * Ic; i += blockDim.x) sm[i] = 0;
+            __syncthreads();
+        }
+        const long long n_in = A.from_bank ? (long long)A.sd->nbank : (long long)*A.rin.count;
+        const long long n_use = (!A.from_bank && n_in > A.rin.cap) ? A.rin.cap : n_in;
+        const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
+        const long long i1 = min(n_use, i0 + (long long)plan.tile);
+        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N) : -1;
+        run_items(A, i0 + threadIdx.x, i1, blockDim.x, b_tile, sm, cnt);
+        __syncthreads();
+        if (b_tile >= 0)
+            for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
+                const long long v = sm[6 * Ic + i];
+                if (v != 0) {
+                    add128(&A.batch[(long long)b_tile * Ic + i], v);
+                    sm[6 * Ic + i] = 0;
+                }
+            }
+        __syncthreads();
+    }
 }
 
 }  // namespace
@@ -334,13 +430,27 @@ void launch_track_fp64(const TrackArgs<double>& a, int grid, int block, size_t s
 }
 
 int track_smem_optin_fp64(size_t smem) {
-    return (int)cudaFuncSetAttribute(track64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
+    return raise_smem_limit((const void*)track64_kernel, smem);
 }
 
 int track_blocks_per_sm_fp64(int block, size_t smem) {
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, track64_kernel, block, smem);
+    return n;
+}
+
+void launch_track_batch_fp64(const TrackArgs<double>* args, const BatchPlan& plan, int grid, int block, size_t smem,
+                             cudaStream_t s) {
+    track64_kernel_batch<<<grid, block, smem, s>>>(args, plan);
+}
+
+int track_batch_smem_optin_fp64(size_t smem) {
+    return raise_smem_limit((const void*)track64_kernel_batch, smem);
+}
+
+int track_batch_blocks_per_sm_fp64(int block, size_t smem) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, track64_kernel_batch, block, smem);
     return n;
 }
 

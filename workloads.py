@@ -96,7 +96,9 @@ def batched_sweep(n_problems=256, n_steps=50, generator_seed=2512_19925, scale=1
         else:
             st1, c1 = st0, c0
         ratio = float(rng.choice([2.0, 3.0, 5.0, 10.0]))
-        edges = np.linspace(-10.0, 10.0, n_cells + 1)
+        # the at-scale slab's extent, so that cell widths (0.05..1 mfp) bracket
+        # the 0.1 mfp a particle flies per step as in the paper's slabs
+        edges = np.linspace(-50.0, 50.0, n_cells + 1)
         mid = 0.5 * (edges[:-1] + edges[1:])
         region = (mid >= 0.0).astype(np.int32) if two_region else np.zeros(n_cells, np.int32)
         st = np.where(region == 0, st0, st1).astype(float)
