@@ -100,6 +100,11 @@ def lib():
             L.or_get_deriv_tallies.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int64]
             L.or_losm_vjp.argtypes = [C.c_void_p, dp, dp, dp]
             L.or_set_bank_scores.argtypes = [C.c_void_p, dp]
+            L.or_losm_adjoint.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                          C.c_int32, C.c_int32, dp, dp, dp]
+            L.or_losm_directional.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                              C.c_int32, C.c_int32, dp, dp, dp, dp, dp, dp, dp, dp, dp,
+                                              dp, dp, C.c_double, C.c_double, dp]
             L.or_destroy.argtypes = [C.c_void_p]
             L.or_destroy.restype = None
             L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
@@ -181,6 +186,33 @@ def losm_solve(dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, phi_old, J
                              _dp(phi), _dp(J))
     _check(rc, "losm_solve")
     return phi, J
+
+
+def losm_adjoint(dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, g_phi, g_J):
+    """lambda (2I+3, interleaved phi_0, J_0, phi_1, ...) with A^T lambda = g."""
+    dx = _f64(dx)
+    I = dx.size
+    st, sa = _f64(sigma_t, I), _f64(sigma_a, I)
+    gp, gj = _f64(g_phi, I + 2), _f64(g_J, I + 1)
+    lam = np.empty(2 * I + 3)
+    _check(lib().or_losm_adjoint(I, _dp(dx), _dp(st), _dp(sa), v, dt, theta, bc_left, bc_right, _dp(gp),
+                                 _dp(gj), _dp(lam)), "losm_adjoint")
+    return lam
+
+
+def losm_directional(dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, lam, phi_old, J_old, phi_new,
+                     J_new, dsigma_t, dsigma_a, dphi_old, dJ_old, dF_old, dF_new, dPL=0.0, dPR=0.0):
+    """g . du of a LOSM solve along a change of the cross sections and data."""
+    dx = _f64(dx)
+    I = dx.size
+    a = [_f64(sigma_t, I), _f64(sigma_a, I), _f64(lam, 2 * I + 3), _f64(phi_old, I + 2), _f64(J_old, I + 1),
+         _f64(phi_new, I + 2), _f64(J_new, I + 1), _f64(dsigma_t, I), _f64(dsigma_a, I),
+         _f64(dphi_old, I + 2), _f64(dJ_old, I + 1), _f64(dF_old, I + 2), _f64(dF_new, I + 2)]
+    out = C.c_double()
+    _check(lib().or_losm_directional(I, _dp(dx), _dp(a[0]), _dp(a[1]), v, dt, theta, bc_left, bc_right,
+                                     *[_dp(x) for x in a[2:]], float(dPL), float(dPR), C.byref(out)),
+           "losm_directional")
+    return out.value
 
 
 def comb(ids, lins, wfx, n, U):

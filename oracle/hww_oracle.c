@@ -19,6 +19,11 @@
  *   semi-implicit HLOSM .......... Sec. 3, Eqs. (losm-1-semi), (losm-disc-bc-semi)
  *   moving-average filter ........ Sec. 4, Eq. (moving_average)
  *   uniform combing .............. Sec. 5.1 (population control)
+ *   derivatives .................. not in the paper: likelihood-ratio (score
+ *                                  function) tallies of d/d(Sigma_t, c) per
+ *                                  region, carried through the games and the
+ *                                  comb, and the adjoint of the fully implicit
+ *                                  LOSM solve of Sec. 3 (its transpose system)
  * Readings of passages the paper leaves open are listed next to the code
  * that takes them.
  *
@@ -204,8 +209,9 @@ struct or_problem {
     int32_t* region;
     double* inv_c;
     double* bS;                        /* N x 2R scores of the combed bank */
-    i128 *dtl, *dcen;                  /* [2R][I], [3][2R][I] */
+    i128 *dtl, *dcen, *dbnd;           /* [2R][I], [3][2R][I], [2R][6] */
     double *dclo_phi, *dclo_J, *dclo_F;          /* derivative closure set at t^n */
+    double *dclo_PL, *dclo_PR;                   /* [2R] */
     double *dold_phi, *dold_J, *dold_F;          /* ... at the step start */
     double *last_phi_old, *last_J_old, *last_F_old; /* closure set at the step start */
     double last_PL_old, last_PR_old;
@@ -276,13 +282,16 @@ int or_create(const or_desc* d, or_problem** out) {
         const int P2 = 2 * p->R;
         p->dtl = xcalloc((size_t)P2 * I, sizeof(i128));
         p->dcen = xcalloc((size_t)3 * P2 * I, sizeof(i128));
+        p->dbnd = xcalloc((size_t)6 * P2, sizeof(i128));
+        p->dclo_PL = xcalloc((size_t)P2, sizeof(double));
+        p->dclo_PR = xcalloc((size_t)P2, sizeof(double));
         p->dclo_phi = xcalloc((size_t)P2 * (I + 2), sizeof(double));
         p->dclo_J = xcalloc((size_t)P2 * (I + 1), sizeof(double));
         p->dclo_F = xcalloc((size_t)P2 * (I + 2), sizeof(double));
         p->dold_phi = xcalloc((size_t)P2 * (I + 2), sizeof(double));
         p->dold_J = xcalloc((size_t)P2 * (I + 1), sizeof(double));
         p->dold_F = xcalloc((size_t)P2 * (I + 2), sizeof(double));
-        if (!p->dtl || !p->dcen || !p->dclo_phi || !p->dclo_J || !p->dclo_F || !p->dold_phi || !p->dold_J ||
+        if (!p->dtl || !p->dcen || !p->dbnd || !p->dclo_PL || !p->dclo_PR || !p->dclo_phi || !p->dclo_J || !p->dclo_F || !p->dold_phi || !p->dold_J ||
             !p->dold_F) {
             or_destroy(p);
             return E_OOM;
@@ -313,7 +322,7 @@ void or_destroy(or_problem* p) {
     free(p->semi_phi); free(p->semi_J); free(p->full_phi); free(p->full_J);
     free(p->prev_tl_phi);
     free(p->census);
-    free(p->region); free(p->inv_c); free(p->bS); free(p->dtl); free(p->dcen);
+    free(p->region); free(p->inv_c); free(p->bS); free(p->dtl); free(p->dcen); free(p->dbnd); free(p->dclo_PL); free(p->dclo_PR);
     free(p->dclo_phi); free(p->dclo_J); free(p->dclo_F);
     free(p->dold_phi); free(p->dold_J); free(p->dold_F);
     free(p->last_phi_old); free(p->last_J_old); free(p->last_F_old);
@@ -852,6 +861,7 @@ int or_run_step(or_problem* p, or_stats* st) {
     if (R > 0) {
         for (int64_t i = 0; i < (int64_t)P2 * I; ++i) p->dtl[i] = 0;
         for (int64_t i = 0; i < (int64_t)3 * P2 * I; ++i) p->dcen[i] = 0;
+        for (int64_t i = 0; i < (int64_t)6 * P2; ++i) p->dbnd[i] = 0;
     }
 
     pstack stack = {0};
@@ -978,6 +988,11 @@ int or_run_step(or_problem* p, or_stats* st) {
                         p->bnd[3 * side + 0] += to_fixed(wi, S);
                         p->bnd[3 * side + 1] += to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu), S);
                         p->bnd[3 * side + 2] += to_fixed(wi * (0.5 - amu), S);
+                        for (int j = 0; j < P2; ++j) {
+                            p->dbnd[6 * j + 3 * side + 0] += to_fixed(wi * q.S[j], S);
+                            p->dbnd[6 * j + 3 * side + 1] += to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu) * q.S[j], S);
+                            p->dbnd[6 * j + 3 * side + 2] += to_fixed(wi * (0.5 - amu) * q.S[j], S);
+                        }
                         s.leaked++;
                         if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
                         break;
@@ -1057,15 +1072,18 @@ int or_run_step(or_problem* p, or_stats* st) {
         build_closures(p, cphi, cJ, cF, PL, PR);
         for (int j = 0; j < P2; ++j) {
             /* derivative closures: the same linear map applied to the census
-             * derivative tallies (boundary closures P taken as constants) */
+             * and boundary derivative tallies */
             for (int32_t i = 0; i < I; ++i) {
                 const double den = (double)N * p->dx[i];
                 cphi[i] = (v * ldexp(conv128(p->dcen[((int64_t)0 * P2 + j) * I + i]), -S)) / den;
                 cJ[i] = (v * ldexp(conv128(p->dcen[((int64_t)1 * P2 + j) * I + i]), -S)) / den;
                 cF[i] = (v * ldexp(conv128(p->dcen[((int64_t)2 * P2 + j) * I + i]), -S)) / den;
             }
-            build_closure_set(p, cphi, cJ, cF, 0.0, 0.0, p->dclo_phi + (int64_t)j * (I + 2),
-                              p->dclo_J + (int64_t)j * (I + 1), p->dclo_F + (int64_t)j * (I + 2), NULL, NULL);
+            const double dPL = ldexp(conv128(p->dbnd[6 * j + 2]), -S) / ((double)N * p->d.dt);
+            const double dPR = ldexp(conv128(p->dbnd[6 * j + 5]), -S) / ((double)N * p->d.dt);
+            build_closure_set(p, cphi, cJ, cF, dPL, dPR, p->dclo_phi + (int64_t)j * (I + 2),
+                              p->dclo_J + (int64_t)j * (I + 1), p->dclo_F + (int64_t)j * (I + 2), &p->dclo_PL[j],
+                              &p->dclo_PR[j]);
         }
         free(cphi); free(cJ); free(cF);
         rc = or_losm_solve(I, p->dx, p->sigt, p->siga, v, p->d.dt, p->d.theta, p->d.bc_left,
@@ -1308,12 +1326,17 @@ int or_set_bank_scores(or_problem* p, const double* S) {
 }
 
 int or_get_deriv_tallies(const or_problem* p, int32_t which, double* out, int64_t n) {
-    if (!p || !out || p->R < 1 || which < 0 || which > 3) return E_ARG;
+    if (!p || !out || p->R < 1 || which < 0 || which > 4) return E_ARG;
     const int32_t I = p->I;
     const int P2 = 2 * p->R;
-    if (n < (int64_t)P2 * I) return E_ARG;
     const int S = p->tally_shift;
     const int64_t N = p->N;
+    if (which == 4) {
+        if (n < (int64_t)P2 * 6) return E_ARG;
+        for (int64_t k = 0; k < (int64_t)P2 * 6; ++k) out[k] = ldexp(conv128(p->dbnd[k]), -S) / ((double)N * p->d.dt);
+        return 0;
+    }
+    if (n < (int64_t)P2 * I) return E_ARG;
     for (int j = 0; j < P2; ++j)
         for (int32_t i = 0; i < I; ++i) {
             double val;
@@ -1328,77 +1351,121 @@ int or_get_deriv_tallies(const or_problem* p, int32_t which, double* out, int64_
     return 0;
 }
 
-/* Adjoint of the last step's fully implicit solve A(theta) u = b(theta,
- * closures(theta)): with A^T lambda = g,
- *   g . du/dtheta_j = lambda . ( b(dclosures_j) + db/dtheta_j - dA/dtheta_j u ),
- * where b is linear in the closures (no source), so its closure part is the
- * same assembly applied to the derivative closures, and the direct parts
- * come from Sigma_hat (first-moment rows) and Sigma_a = Sigma_t (1 - c)
- * (balance rows). */
-int or_losm_vjp(const or_problem* p, const double* g_phi, const double* g_J, double* grad) {
-    if (!p || !g_phi || !g_J || !grad || p->R < 1 || p->n < 1) return E_ARG;
-    const int32_t I = p->I, n = 2 * I + 3;
-    const int R = p->R, P2 = 2 * R;
-    const double th = p->d.theta, tm1 = th - 1.0;
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the LOSM solve (differentiation of the HLOSM step)            */
+/*                                                                          */
+/* The solve is A(Sigma) u = b(Sigma, data), with data = (phi_old, J_old,   */
+/* F_old, F_new, P_L, P_R) entering b linearly.  For a scalar g . u the    */
+/* change along a direction (dSigma_t, dSigma_a, d data) is                */
+/*   g . du = lambda . ( b(Sigma, d data) + db/dSigma - dA/dSigma u ),     */
+/* with A^T lambda = g.  Sigma_t enters only the first-moment rows, through */
+/* Sigma_hat at the edges, and Sigma_a only the balance rows.               */
+/* ------------------------------------------------------------------------ */
+int or_losm_adjoint(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a, double v,
+                    double dt, double theta, int32_t bc_left, int32_t bc_right, const double* g_phi,
+                    const double* g_J, double* lam) {
+    if (I < 1 || !dx || !sigma_t || !sigma_a || !g_phi || !g_J || !lam) return E_ARG;
+    const int32_t n = 2 * I + 3;
     double* a = xcalloc(n, sizeof(double));
     double* b = xcalloc(n, sizeof(double));
     double* c = xcalloc(n, sizeof(double));
     double* r = xcalloc(n, sizeof(double));
+    double* z = xcalloc(I + 2, sizeof(double));
     double* at = xcalloc(n, sizeof(double));
     double* ct = xcalloc(n, sizeof(double));
-    double* lam = xcalloc(n, sizeof(double));
-    double* rb = xcalloc(n, sizeof(double));
-    if (!a || !b || !c || !r || !at || !ct || !lam || !rb) {
-        free(a); free(b); free(c); free(r); free(at); free(ct); free(lam); free(rb);
+    int rc = E_OOM;
+    if (a && b && c && r && z && at && ct) {
+        /* the matrix does not depend on the data: assemble with zero data */
+        losm_assemble(I, dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, z, z, z, z, 0.0, 0.0, NULL,
+                      NULL, a, b, c, r);
+        /* transpose: (A^T)[k][k-1] = A[k-1][k] = c[k-1], (A^T)[k][k+1] = A[k+1][k] = a[k+1] */
+        for (int32_t k = 0; k < n; ++k) {
+            at[k] = (k >= 1) ? c[k - 1] : 0.0;
+            ct[k] = (k + 1 < n) ? a[k + 1] : 0.0;
+        }
+        for (int32_t i = 0; i <= I + 1; ++i) lam[2 * i] = g_phi[i];
+        for (int32_t i = 0; i <= I; ++i) lam[2 * i + 1] = g_J[i];
+        rc = tri_solve_pivot(n, at, b, ct, lam);
+    }
+    free(a); free(b); free(c); free(r); free(z); free(at); free(ct);
+    return rc;
+}
+
+int or_losm_directional(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a, double v,
+                        double dt, double theta, int32_t bc_left, int32_t bc_right, const double* lam,
+                        const double* phi_old, const double* J_old, const double* phi_new, const double* J_new,
+                        const double* dsigma_t, const double* dsigma_a, const double* dphi_old,
+                        const double* dJ_old, const double* dF_old, const double* dF_new, double dPL,
+                        double dPR, double* out) {
+    if (I < 1 || !dx || !sigma_t || !sigma_a || !lam || !phi_old || !J_old || !phi_new || !J_new ||
+        !dsigma_t || !dsigma_a || !dphi_old || !dJ_old || !dF_old || !dF_new || !out)
+        return E_ARG;
+    const int32_t n = 2 * I + 3;
+    double* a = xcalloc(n, sizeof(double));
+    double* b = xcalloc(n, sizeof(double));
+    double* c = xcalloc(n, sizeof(double));
+    double* r = xcalloc(n, sizeof(double));
+    if (!a || !b || !c || !r) {
+        free(a); free(b); free(c); free(r);
         return E_OOM;
     }
-    losm_assemble(I, p->dx, p->sigt, p->siga, p->d.v, p->d.dt, th, p->d.bc_left, p->d.bc_right,
-                  p->last_phi_old, p->last_J_old, p->last_F_old, p->clo_F, p->clo_PL, p->clo_PR, NULL, NULL,
-                  a, b, c, r);
-    /* transpose: (A^T)[k][k-1] = A[k-1][k] = c[k-1], (A^T)[k][k+1] = A[k+1][k] = a[k+1] */
-    for (int32_t k = 0; k < n; ++k) {
-        at[k] = (k >= 1) ? c[k - 1] : 0.0;
-        ct[k] = (k + 1 < n) ? a[k + 1] : 0.0;
+    /* data part: the right-hand side assembled from the data's change */
+    losm_assemble(I, dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, dphi_old, dJ_old, dF_old, dF_new,
+                  dPL, dPR, NULL, NULL, a, b, c, r);
+    double acc = 0.0;
+    for (int32_t k = 0; k < n; ++k) acc += lam[k] * r[k];
+    /* cross-section part, first-moment rows: (theta-1) dSigma_hat dxh J_old
+     * on the right, theta dSigma_hat dxh J_new moved from the left */
+    const double tm1 = theta - 1.0;
+    for (int32_t i = 0; i <= I; ++i) {
+        const double dxl = (i >= 1) ? dx[i - 1] : 0.0;
+        const double dxr = (i <= I - 1) ? dx[i] : 0.0;
+        const double dsl = (i >= 1) ? dsigma_t[i - 1] : 0.0;
+        const double dsr = (i <= I - 1) ? dsigma_t[i] : 0.0;
+        const double dsh = (dsl * dxl + dsr * dxr) / (dxl + dxr);
+        const double dxh = 0.5 * (dxl + dxr);
+        acc += lam[2 * i + 1] * (tm1 * dsh * dxh * J_old[i] - theta * dsh * dxh * J_new[i]);
     }
-    for (int32_t i = 0; i <= I + 1; ++i) lam[2 * i] = g_phi[i];
-    for (int32_t i = 0; i <= I; ++i) lam[2 * i + 1] = g_J[i];
-    int rc = tri_solve_pivot(n, at, b, ct, lam);
-    if (rc) goto done;
-    for (int j = 0; j < P2; ++j) {
-        /* closure part: the assembly applied to the derivative closures */
-        double* dphi = p->dold_phi + (int64_t)j * (I + 2);
-        double* dJ = p->dold_J + (int64_t)j * (I + 1);
-        double* dFo = p->dold_F + (int64_t)j * (I + 2);
-        double* dFn = p->dclo_F + (int64_t)j * (I + 2);
-        losm_assemble(I, p->dx, p->sigt, p->siga, p->d.v, p->d.dt, th, p->d.bc_left, p->d.bc_right, dphi, dJ,
-                      dFo, dFn, 0.0, 0.0, NULL, NULL, a, b, c, rb);
-        double acc = 0.0;
-        for (int32_t k = 0; k < n; ++k) acc += lam[k] * rb[k];
-        /* direct part */
+    /* balance rows: (theta-1) dSigma_a dx phi_old and theta dSigma_a dx phi_new */
+    for (int32_t i = 1; i <= I; ++i) {
+        const double dsa = dsigma_a[i - 1];
+        const double dxi = dx[i - 1];
+        acc += lam[2 * i] * (tm1 * dsa * dxi * phi_old[i] - theta * dsa * dxi * phi_new[i]);
+    }
+    *out = acc;
+    free(a); free(b); free(c); free(r);
+    return 0;
+}
+
+/* g . d(full HLOSM solution of the last step)/d(theta_j): the direction of
+ * theta_j is dSigma_t = 1 on region j (j < R) or 0, dSigma_a = (1 - c) on
+ * region j (Sigma_a = Sigma_t (1 - c)) or -Sigma_t on region j - R (j >= R),
+ * and the data's change is the derivative closures of the step. */
+int or_losm_vjp(const or_problem* p, const double* g_phi, const double* g_J, double* grad) {
+    if (!p || !g_phi || !g_J || !grad || p->R < 1 || p->n < 1) return E_ARG;
+    const int32_t I = p->I, n = 2 * I + 3;
+    const int R = p->R, P2 = 2 * R;
+    double* lam = xcalloc(n, sizeof(double));
+    double* dst = xcalloc(I, sizeof(double));
+    double* dsa = xcalloc(I, sizeof(double));
+    int rc = E_OOM;
+    if (lam && dst && dsa)
+        rc = or_losm_adjoint(I, p->dx, p->sigt, p->siga, p->d.v, p->d.dt, p->d.theta, p->d.bc_left,
+                             p->d.bc_right, g_phi, g_J, lam);
+    for (int j = 0; j < P2 && rc == 0; ++j) {
         const int is_sigma = j < R;
         const int g = is_sigma ? j : j - R;
-        for (int32_t i = 0; i <= I; ++i) {
-            if (!is_sigma) break;
-            const double dxl = (i >= 1) ? p->dx[i - 1] : 0.0;
-            const double dxr = (i <= I - 1) ? p->dx[i] : 0.0;
-            double dsth = 0.0;
-            if (i >= 1 && p->region[i - 1] == g) dsth += dxl / (dxl + dxr);
-            if (i <= I - 1 && p->region[i] == g) dsth += dxr / (dxl + dxr);
-            if (dsth == 0.0) continue;
-            const double dxh = 0.5 * (dxl + dxr);
-            const double val = tm1 * dxh * dsth * p->last_J_old[i] - th * dxh * dsth * p->full_J[i];
-            acc += lam[2 * i + 1] * val;
+        for (int32_t i = 0; i < I; ++i) {
+            const int in = p->region[i] == g;
+            dst[i] = (is_sigma && in) ? 1.0 : 0.0;
+            dsa[i] = in ? (is_sigma ? 1.0 - p->c[i] : -p->sigt[i]) : 0.0;
         }
-        for (int32_t i = 1; i <= I; ++i) {
-            if (p->region[i - 1] != g) continue;
-            const double dsa = is_sigma ? (1.0 - p->c[i - 1]) : -p->sigt[i - 1];
-            const double dxi = p->dx[i - 1];
-            const double val = tm1 * dxi * dsa * p->last_phi_old[i] - th * dxi * dsa * p->full_phi[i];
-            acc += lam[2 * i] * val;
-        }
-        grad[j] = acc;
+        rc = or_losm_directional(I, p->dx, p->sigt, p->siga, p->d.v, p->d.dt, p->d.theta, p->d.bc_left,
+                                 p->d.bc_right, lam, p->last_phi_old, p->last_J_old, p->full_phi, p->full_J,
+                                 dst, dsa, p->dold_phi + (int64_t)j * (I + 2), p->dold_J + (int64_t)j * (I + 1),
+                                 p->dold_F + (int64_t)j * (I + 2), p->dclo_F + (int64_t)j * (I + 2),
+                                 p->dclo_PL[j], p->dclo_PR[j], &grad[j]);
     }
-done:
-    free(a); free(b); free(c); free(r); free(at); free(ct); free(lam); free(rb);
+    free(lam); free(dst); free(dsa);
     return rc;
 }

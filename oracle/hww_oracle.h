@@ -58,11 +58,25 @@ int or_get_tallies_raw(const or_problem* p, int32_t kind, int64_t* out, int64_t 
 int or_get_losm_solution(const or_problem* p, int32_t which, double* phi, double* J);
 /* derivative tallies of the last step, [2R][I]: parameter j < R is Sigma_t of
  * region j, j >= R is c of region j - R; which: 0 track-length phi, 1 census
- * phi, 2 census J, 3 census F (normalised like the tallies) */
+ * phi, 2 census J, 3 census F, 4 boundary ([2R][6]) (normalised like the
+ * tallies) */
 int or_get_deriv_tallies(const or_problem* p, int32_t which, double* out, int64_t n);
 /* vector-Jacobian product of the last step's fully implicit HLOSM solution:
  * grad[j] = g_phi . dphi/dtheta_j + g_J . dJ/dtheta_j (2R values) */
 int or_losm_vjp(const or_problem* p, const double* g_phi, const double* g_J, double* grad);
+/* adjoint of a LOSM solve: lambda (2I+3, interleaved phi_0, J_0, phi_1, ...)
+ * with A^T lambda = (g_phi, g_J) interleaved */
+int or_losm_adjoint(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a, double v,
+                    double dt, double theta, int32_t bc_left, int32_t bc_right, const double* g_phi,
+                    const double* g_J, double* lam);
+/* g . du of a LOSM solve along a change of the cross sections and of the
+ * data, given lambda, the data's old vectors and the solution u */
+int or_losm_directional(int32_t I, const double* dx, const double* sigma_t, const double* sigma_a, double v,
+                        double dt, double theta, int32_t bc_left, int32_t bc_right, const double* lam,
+                        const double* phi_old, const double* J_old, const double* phi_new, const double* J_new,
+                        const double* dsigma_t, const double* dsigma_a, const double* dphi_old,
+                        const double* dJ_old, const double* dF_old, const double* dF_new, double dPL,
+                        double dPR, double* out);
 int or_get_ww(const or_problem* p, double* center, double* ceil_, double* floor_);
 int or_get_bank(const or_problem* p, double* x, double* mu, int32_t* cell, int64_t cap, int64_t* n);
 /* replace the start bank of the next step: n particles with ids 0..n-1,
