@@ -100,7 +100,9 @@ typedef struct {
     double theta;             /* 0.5 Crank-Nicolson | 1.0 backward Euler */
     int32_t filter, filter_k; /* HWW_FILTER_NONE | HWW_FILTER_MA with base k >= 1 */
     int32_t n_var_batches;    /* B >= 1 batches for the batch-mean variance tally */
-    int32_t deriv_regions;    /* 0, or R >= 1 regions for derivative tallies (FP64 only) */
+    int32_t deriv_regions;    /* 0, or 1 <= R <= 4 regions for derivative tallies (FP64 only; the
+                                 tracking needs (7 + 2R) I 8 bytes of shared memory per block,
+                                 at most 227 KB) */
     int64_t bank_capacity;    /* census slots; each record queue gets half; 0 = 4 N census, 2 N per queue */
     void* cuda_stream;        /* cudaStream_t; NULL = legacy default stream */
     int32_t device;           /* CUDA device ordinal */
@@ -163,6 +165,49 @@ hww_status get_tallies_raw(const hww_problem* p, int32_t kind, int64_t* out, int
  * losm-disc).  phi has I+2 entries and J has I+1. */
 hww_status get_losm_solution(const hww_problem* p, int32_t which, double* phi, double* J,
                              int32_t on_device);
+
+/* ------------------------------------------------------------------------
+ * Derivatives (not in the paper).  With deriv_regions = R > 0 the step also
+ * estimates the derivatives of its tallies with respect to the 2R parameters
+ * theta_j: j < R is Sigma_t of region j, j = R + r is c of region r (Sigma_s =
+ * c Sigma_t, so Sigma_a = (1 - c) Sigma_t moves with both).  Estimator:
+ * likelihood-ratio scores carried by every particle (a flight of length l
+ * adds -l, a collision 1/Sigma_t, a scatter 1/c to the scores of the cell's
+ * region), inherited by daughters, roulette survivors and comb copies; the
+ * windows' centers count as constants (the games are unbiased for any
+ * centers).  The c derivative needs c > 0 in the region.
+ * ------------------------------------------------------------------------ */
+
+/* Derivative tallies of the last step, normalised like the tallies:
+ * which 0 track-length phi, 1 census phi, 2 census J, 3 census F (each
+ * [2R][I], row j = d/dtheta_j), 4 boundary ([2R][6], the HWW_BOUNDARY
+ * layout).  n is the capacity of out in doubles.  HWW_ERR_STATE without
+ * derivatives or before the first step. */
+hww_status get_deriv_tallies(const hww_problem* p, int32_t which, double* out, int64_t n, int32_t on_device);
+
+/* Doubles of the state block that losm_vjp needs for one step. */
+hww_status vjp_state_size(const hww_problem* p, int64_t* n);
+
+/* Save the last step's state block (the step's closures at both levels, its
+ * derivative closures, its fully implicit solution and its normalised
+ * derivative track-length tally) into `state` (n doubles, host or device
+ * memory by on_device), so that the adjoint of that step can run after later
+ * steps. */
+hww_status save_vjp_state(hww_problem* p, double* state, int64_t n, int32_t on_device);
+
+/* Vector-Jacobian product of one step:
+ *   grad[j] = g_mc . d<phi>/dtheta_j + g_phi . dphi_H/dtheta_j + g_J . dJ_H/dtheta_j
+ * with <phi> the step's track-length flux (I), (phi_H, J_H) its fully
+ * implicit HLOSM solution (I+2, I+1; Eqs. losm-0, losm-1, losm-disc-bc).
+ * The HLOSM part is the adjoint of the solve: lambda = A^{-T} g by a
+ * transposed Thomas sweep, contracted with the derivative closures and with
+ * dA/dtheta, db/dtheta (recomputed per call, nothing stored but the state
+ * block).  state: NULL for the last step, else a block from save_vjp_state of
+ * this problem under its current cross sections (HWW_ERR_STATE otherwise).
+ * g_mc, g_phi, g_J may be NULL (zero).  All vectors and grad (2R) are host or
+ * device memory by on_device. */
+hww_status losm_vjp(hww_problem* p, const double* state, const double* g_mc, const double* g_phi,
+                    const double* g_J, double* grad, int32_t on_device);
 
 /* Copy the combed bank that will start the next step (positions, directions,
  * cells; each particle carries weight stats.w_bar_next).  Host arrays of

@@ -327,11 +327,11 @@ class Problem:
 
     def get_deriv_tallies(self, which=0):
         """[2R, I] derivatives of the last step's tally `which` (0 track-length
-        phi, 1 census phi, 2 census J, 3 census F); rows j < R are d/dSigma_t of
-        region j, rows R + r are d/dc of region r."""
-        out = np.empty(2 * self.R * self.I)
+        phi, 1 census phi, 2 census J, 3 census F) or [2R, 6] (4, boundary);
+        rows j < R are d/dSigma_t of region j, rows R + r are d/dc of region r."""
+        out = np.empty(2 * self.R * (6 if which == 4 else self.I))
         _check(lib().or_get_deriv_tallies(self._h, int(which), _dp(out), out.size), "get_deriv_tallies")
-        return out.reshape(2 * self.R, self.I)
+        return out.reshape(2 * self.R, -1)
 
     def losm_vjp(self, g_phi, g_J):
         """g_phi . d phi/d theta + g_J . d J/d theta of the last step's fully

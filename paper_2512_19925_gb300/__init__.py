@@ -79,7 +79,8 @@ SYMBOLS = ["create_problem", "set_cross_sections", "set_ww_params", "set_ww_cent
            "get_tallies", "get_tallies_raw", "get_losm_solution", "get_bank", "set_bank", "get_census", "destroy_problem",
            "hww_status_string", "hww_last_error_string", "hww_losm_solve", "hww_philox_block", "hww_set_timing",
            "hww_get_counters", "hww_reset_counters", "create_batch", "batch_problem", "batch_set_tuning",
-           "run_batch_step", "batch_member_stats", "destroy_batch"]
+           "run_batch_step", "batch_member_stats", "destroy_batch", "get_deriv_tallies", "vjp_state_size",
+           "save_vjp_state", "losm_vjp"]
 
 
 def library_path() -> str:
@@ -107,6 +108,10 @@ def load(build_if_missing: bool = True):
         L.get_tallies.argtypes = [vp, C.c_int32, vp, C.c_int64, C.c_int32]
         L.get_tallies_raw.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), C.c_int64]
         L.get_losm_solution.argtypes = [vp, C.c_int32, vp, vp, C.c_int32]
+        L.get_deriv_tallies.argtypes = [vp, C.c_int32, vp, C.c_int64, C.c_int32]
+        L.vjp_state_size.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.save_vjp_state.argtypes = [vp, vp, C.c_int64, C.c_int32]
+        L.losm_vjp.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int32]
         L.get_bank.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.POINTER(C.c_int64)]
         L.set_bank.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.c_double]
         L.get_census.argtypes = [vp, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
@@ -196,6 +201,7 @@ class Problem:
         self.I = self.edges.size - 1
         self.B = int(n_var_batches)
         self.N = int(particles_per_step)
+        self.R = int(deriv_regions)
         self.device = int(device)
         if stream is None:
             try:
@@ -215,14 +221,17 @@ class Problem:
 
     @classmethod
     def from_workload(cls, wl, particles_per_step=None, seed=None, precision=None, stream=None,
-                      bank_capacity=0):
+                      bank_capacity=0, deriv=False):
+        """A problem from a workload description; with deriv, derivative
+        tallies for the workload's regions (FP64)."""
         prec = precision if precision is not None else (FP32_TRACK if wl.get("precision") == "fp32" else FP64)
+        R = int(wl.get("n_regions", 1)) if deriv else 0
         p = cls(wl["edges"], wl["v"], wl["dt"], wl["bc_left"], wl["bc_right"], wl["src_x"],
                 particles_per_step or wl["particles_per_step"], wl["seed"] if seed is None else seed,
                 precision=prec, theta=wl.get("theta", 0.5), filter=wl.get("filter", 0),
                 filter_k=wl.get("filter_k", 3), n_var_batches=wl.get("n_var_batches", 16),
-                bank_capacity=bank_capacity, stream=stream)
-        p.set_cross_sections(wl["sigma_t"], wl["c"])
+                deriv_regions=R, bank_capacity=bank_capacity, stream=stream)
+        p.set_cross_sections(wl["sigma_t"], wl["c"], wl.get("region") if R else None)
         p.set_ww_params(wl["rho"], wl["eps_min"], wl.get("mode", MODE_HWW),
                         wl.get("center_scaling", SCALE_MEAN_WEIGHT))
         return p
@@ -243,6 +252,7 @@ class Problem:
         reg = None
         if region is not None:
             reg = np.ascontiguousarray(region, dtype=np.int32)
+            self.region = reg
         rp = reg.ctypes.data_as(C.POINTER(C.c_int32)) if reg is not None else C.POINTER(C.c_int32)()
         _check(load().set_cross_sections(self._h, _dp(st), _dp(cc), rp), "set_cross_sections")
 
@@ -283,6 +293,73 @@ class Problem:
             a = a.reshape(self.B, self.I)
         return a
 
+    def get_deriv_tallies(self, which=0, out=None):
+        """Derivative tallies [2R, I] (which 0 track length, 1..3 census phi,
+        J, F) or [2R, 6] (4, boundary); into `out` (a CUDA float64 tensor)
+        without leaving the device."""
+        n = 2 * self.R * (6 if which == 4 else self.I)
+        if out is not None:
+            if out.numel() < n or not out.is_cuda:
+                raise ValueError("out must be a CUDA float64 tensor of %d values" % n)
+            _check(load().get_deriv_tallies(self._h, int(which), C.c_void_p(out.data_ptr()), n, 1),
+                   "get_deriv_tallies")
+            return out
+        a = np.empty(n)
+        _check(load().get_deriv_tallies(self._h, int(which), a.ctypes.data_as(C.c_void_p), n, 0),
+               "get_deriv_tallies")
+        return a.reshape(2 * self.R, -1)
+
+    def vjp_state_size(self):
+        n = C.c_int64()
+        _check(load().vjp_state_size(self._h, C.byref(n)), "vjp_state_size")
+        return n.value
+
+    def save_vjp_state(self, out=None):
+        """The last step's adjoint state: into `out` (a CUDA float64 tensor),
+        else a numpy array."""
+        n = self.vjp_state_size()
+        if out is not None:
+            if out.numel() < n or not out.is_cuda:
+                raise ValueError("out must be a CUDA float64 tensor of %d values" % n)
+            _check(load().save_vjp_state(self._h, C.c_void_p(out.data_ptr()), n, 1), "save_vjp_state")
+            return out
+        a = np.empty(n)
+        _check(load().save_vjp_state(self._h, a.ctypes.data_as(C.c_void_p), n, 0), "save_vjp_state")
+        return a
+
+    def losm_vjp(self, g_mc=None, g_phi=None, g_J=None, state=None, out=None):
+        """grad[2R] = g_mc . d<phi>/dtheta + g_phi . dphi_H/dtheta + g_J . dJ_H/dtheta
+        for the last step (state None) or a saved state.  With `out` (a CUDA
+        float64 tensor) every vector is a CUDA tensor; else numpy arrays."""
+        L = load()
+        if out is not None:
+            sizes = ((state, self.vjp_state_size()), (g_mc, self.I), (g_phi, self.I + 2), (g_J, self.I + 1),
+                     (out, 2 * self.R))
+            for t, n in sizes:
+                if t is not None and (t.numel() < n or not t.is_cuda or not t.is_contiguous()):
+                    raise ValueError("device vectors must be contiguous CUDA float64 tensors of the right size")
+            ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+            _check(L.losm_vjp(self._h, ptr(state), ptr(g_mc), ptr(g_phi), ptr(g_J), ptr(out), 1), "losm_vjp")
+            return out
+        keep = []
+
+        def host(a, n):
+            if a is None:
+                return None
+            a = _f64(a, n)
+            keep.append(a)
+            return a.ctypes.data_as(C.c_void_p)
+
+        st = None
+        if state is not None:
+            st = np.ascontiguousarray(state, dtype=np.float64)
+            keep.append(st)
+            st = st.ctypes.data_as(C.c_void_p)
+        grad = np.empty(2 * self.R)
+        _check(L.losm_vjp(self._h, st, host(g_mc, self.I), host(g_phi, self.I + 2), host(g_J, self.I + 1),
+                          grad.ctypes.data_as(C.c_void_p), 0), "losm_vjp")
+        return grad
+
     def get_tallies_raw(self, kind):
         n = {BATCH_PHI: self.B * self.I, BOUNDARY: 6}.get(kind, self.I)
         a = np.empty(2 * n, dtype=np.int64)
@@ -290,7 +367,14 @@ class Problem:
                "get_tallies_raw")
         return a.reshape(n, 2)
 
-    def get_losm_solution(self, which=LOSM_FULL):
+    def get_losm_solution(self, which=LOSM_FULL, out=None):
+        """(phi [I+2], J [I+1]) of the last step's HLOSM solve: numpy arrays,
+        or into `out` = (phi, J) CUDA float64 tensors without leaving the device."""
+        if out is not None:
+            phi, J = out
+            _check(load().get_losm_solution(self._h, int(which), C.c_void_p(phi.data_ptr()),
+                                            C.c_void_p(J.data_ptr()), 1), "get_losm_solution")
+            return phi, J
         phi, J = np.empty(self.I + 2), np.empty(self.I + 1)
         _check(load().get_losm_solution(self._h, int(which), phi.ctypes.data_as(C.c_void_p),
                                         J.ctypes.data_as(C.c_void_p), 0), "get_losm_solution")
@@ -360,6 +444,7 @@ class _Member(Problem):
         self.I = self.edges.size - 1
         self.B = int(wl.get("n_var_batches", 16))
         self.N = int(wl["particles_per_step"])
+        self.R = 0
         self.device = 0
         self.stream = 0
 

@@ -96,6 +96,16 @@ struct hww_problem {
     size_t track_smem = 0;
     int last_waves = 0;
     int emax = 64;         // events per track before it is requeued
+    // likelihood-ratio derivatives (P2 = 2R parameters; 0: off)
+    int R = 0, P2 = 0;
+    double* d_inv_c = nullptr;                 // I, 1/c (0 where c = 0)
+    double* bS = nullptr;                      // [P2][N] start-bank scores
+    Acc128 *dtl = nullptr, *dcen = nullptr, *dbnd = nullptr;  // in the accumulator block
+    double *dcl_phi[2] = {}, *dcl_J[2] = {}, *dcl_F[2] = {}, *dcl_P[2] = {};  // derivative closure sets
+    double *drphi = nullptr, *drJ = nullptr, *drF = nullptr;  // [P2][I+1] scratch
+    double* vjp_state = nullptr;               // state block of the last step
+    double* vjp_work = nullptr;                // psi, z, g_mc, g_phi, g_J, grad
+    unsigned long long xs_version = 0;         // bumped by set_cross_sections
     long long q_peak = 0;  // largest record count a wave produced in the last pass
     // launch accounting
     int timing = 0;
@@ -218,7 +228,9 @@ hww_status alloc_banks(hww_problem* p, Banks<Real>& b) {
             return s;
         q.cap = Q;
         q.count = p->counts + 1 + k;
+        if (p->P2 > 0 && (s = dalloc(p, &q.S, (size_t)p->P2 * Q, true))) return s;
     }
+    if (p->P2 > 0 && (s = dalloc(p, &b.cen.S, (size_t)p->P2 * C, true))) return s;
     return HWW_OK;
 }
 
@@ -229,6 +241,28 @@ void free_banks(hww_problem* p) {
 
 // grow the census and queue capacities to at least twice their size and at
 // least 5/4 of the demand the failed pass saw (the start bank is kept)
+// adjoint work vectors: psi (I+2), z (I+2), g_mc (I), g_phi (I+2), g_J (I+1),
+// grad (P2)
+size_t vjp_work_doubles(int I, int P2) { return 5 * (size_t)I + 7 + (size_t)P2; }
+
+// scores of the start bank, derivative closure sets and their scratch, and
+// the adjoint's state block and work vectors
+hww_status alloc_deriv(hww_problem* p) {
+    const size_t I = (size_t)p->I, P2 = (size_t)p->P2;
+    const VjpLayout L = vjp_layout(p->I, p->P2);
+    hww_status s;
+    if ((s = dalloc(p, &p->d_inv_c, I)) || (s = dalloc(p, &p->bS, P2 * (size_t)p->N)) ||
+        (s = dalloc(p, &p->drphi, P2 * (I + 1))) || (s = dalloc(p, &p->drJ, P2 * (I + 1))) ||
+        (s = dalloc(p, &p->drF, P2 * (I + 1))) || (s = dalloc(p, &p->vjp_state, (size_t)L.total)) ||
+        (s = dalloc(p, &p->vjp_work, vjp_work_doubles(p->I, p->P2))))
+        return s;
+    for (int k = 0; k < 2; ++k)
+        if ((s = dalloc(p, &p->dcl_phi[k], P2 * (I + 2))) || (s = dalloc(p, &p->dcl_J[k], P2 * (I + 1))) ||
+            (s = dalloc(p, &p->dcl_F[k], P2 * (I + 2))) || (s = dalloc(p, &p->dcl_P[k], P2 * 2)))
+            return s;
+    return HWW_OK;
+}
+
 hww_status regrow_banks(hww_problem* p, long long cen_need, long long q_need) {
     HWW_CK(cudaStreamSynchronize(p->stream));
     free_banks(p);
@@ -275,6 +309,14 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b) {
     a.bnd = p->bnd;
     a.stats = p->stats;
     a.err = p->err;
+    a.R = p->R;
+    a.P2 = p->P2;
+    a.region = p->d_region;
+    a.inv_c = p->d_inv_c;
+    a.bS = p->bS;
+    a.dtl = p->dtl;
+    a.dcen = p->dcen;
+    a.dbnd = p->dbnd;
     return a;
 }
 
@@ -368,6 +410,9 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     c.bcell = b.bcell;
     c.stats = p->stats;
     c.err = p->err;
+    c.P2 = p->P2;
+    c.cS = b.cen.S;
+    c.bS = p->bS;
     launch_comb(c, p->nsm * 8, p->stream);
     HWW_CK(cudaGetLastError());
     p->kernel_launches += 3;
@@ -440,6 +485,62 @@ hww_status copy_out(const hww_problem* p, double* out, const double* src, size_t
 }
 
 
+// normalised derivative tallies: which 0 track length [P2][I], 1..3 census
+// phi, J, F [P2][I], 4 boundary [P2][6]; the same scalings as the tallies
+__global__ void deriv_normalize_kernel(int which, int P2, int I, long long N, const double* dx, double v, double dt,
+                                       const StepDev* sd, const Acc128* dtl, const Acc128* dcen,
+                                       const Acc128* dbnd, double* out) {
+    const double isc = pow2(-sd->S);
+    const int n = (which == 4) ? 6 * P2 : P2 * I;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        if (which == 4) {
+            out[t] = (acc_to_double(dbnd[t]) * isc) / ((double)N * dt);
+            continue;
+        }
+        const int j = t / I, i = t % I;
+        if (which == 0) {
+            out[t] = (acc_to_double(dtl[t]) * isc) / (((double)N * dx[i]) * dt);
+        } else {
+            const Acc128 a = dcen[(long long)j * 3 * I + (long long)(which - 1) * I + i];
+            out[t] = (v * (acc_to_double(a) * isc)) / ((double)N * dx[i]);
+        }
+    }
+}
+
+void launch_deriv_normalize(const hww_problem* p, int which, double* out) {
+    const int n = (which == 4) ? 6 * p->P2 : p->P2 * p->I;
+    const int grid = std::max(1, std::min(64, (n + 255) / 256));
+    deriv_normalize_kernel<<<grid, 256, 0, p->stream>>>(which, p->P2, p->I, p->N, p->d_dx, p->d.v, p->d.dt, p->sd,
+                                                         p->dtl, p->dcen, p->dbnd, out);
+}
+
+// the adjoint's state block of the last step (device, p->vjp_state)
+hww_status fill_vjp_state(hww_problem* p) {
+    const int I = p->I, P2 = p->P2;
+    const VjpLayout L = vjp_layout(I, P2);
+    const int nw = p->cur, od = 1 - p->cur;  // after a step: set `cur` was built at t^n
+    double* st = p->vjp_state;
+    const double hdr[4] = {(double)I, (double)P2, (double)p->xs_version, (double)p->steps};
+    auto d2d = [&](double* dst, const double* src, size_t n) {
+        return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream);
+    };
+    HWW_CK(cudaMemcpyAsync(st, hdr, sizeof(hdr), cudaMemcpyHostToDevice, p->stream));
+    HWW_CK(d2d(st + L.phi_old, p->cl_phi[od], I + 2));
+    HWW_CK(d2d(st + L.J_old, p->cl_J[od], I + 1));
+    HWW_CK(d2d(st + L.phi_new, p->full_phi, I + 2));
+    HWW_CK(d2d(st + L.J_new, p->full_J, I + 1));
+    launch_deriv_normalize(p, 0, st + L.dtl);
+    HWW_CK(cudaGetLastError());
+    HWW_CK(d2d(st + L.dphi_old, p->dcl_phi[od], (size_t)P2 * (I + 2)));
+    HWW_CK(d2d(st + L.dJ_old, p->dcl_J[od], (size_t)P2 * (I + 1)));
+    HWW_CK(d2d(st + L.dF_old, p->dcl_F[od], (size_t)P2 * (I + 2)));
+    HWW_CK(d2d(st + L.dF_new, p->dcl_F[nw], (size_t)P2 * (I + 2)));
+    HWW_CK(d2d(st + L.dP_new, p->dcl_P[nw], (size_t)P2 * 2));
+    // the header is read back from pageable memory: wait before it goes
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    return HWW_OK;
+}
+
 // Stages of one time step.  Every launch parameter below is fixed for the
 // life of the problem (the per-step values live in StepDev), so the stages
 // can also be recorded into CUDA graphs (see the batch engine).
@@ -510,7 +611,27 @@ hww_status stage_post(hww_problem* p) {
         ca.set_P[k] = p->cl_P[k];
     }
     ca.prev_tl = p->prev_tl;
+    ca.nsets = 1;
     p->kernel_launches += launch_closures(ca, p->stream);
+    if (p->P2 > 0) {
+        // derivative closures: the same linear map on the derivative census
+        // and boundary tallies, one set per parameter
+        ClosureArgs dc = ca;
+        dc.cent = p->dcen;
+        dc.bnd = p->dbnd;
+        dc.tl = nullptr;
+        dc.rphi = p->drphi;
+        dc.rJ = p->drJ;
+        dc.rF = p->drF;
+        for (int k = 0; k < 2; ++k) {
+            dc.set_phi[k] = p->dcl_phi[k];
+            dc.set_J[k] = p->dcl_J[k];
+            dc.set_F[k] = p->dcl_F[k];
+            dc.set_P[k] = p->dcl_P[k];
+        }
+        dc.nsets = p->P2;
+        p->kernel_launches += launch_closures(dc, p->stream);
+    }
     LosmRhsIn full = semi_rhs(p);
     full.full = 1;
     p->kernel_launches += launch_losm_solve(p->mat, full, p->work, p->full_phi, p->full_J, nullptr, p->stream);
@@ -598,7 +719,8 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         (d->theta != 0.5 && d->theta != 1.0) || d->n_var_batches < 1 || d->n_var_batches > 64 ||
         d->bc_left < 0 || d->bc_left > 1 || d->bc_right < 0 || d->bc_right > 1 || d->filter < 0 ||
         d->filter > 1 || (d->filter == 1 && d->filter_k < 1) || d->precision < 0 || d->precision > 1 ||
-        d->deriv_regions < 0 || d->bank_capacity < 0)
+        d->deriv_regions < 0 || d->deriv_regions > MAX_SCORES / 2 ||
+        (d->deriv_regions > 0 && d->precision != HWW_FP64) || d->bank_capacity < 0)
         return HWW_ERR_ARG;
     for (int i = 0; i < I; ++i)
         if (!(d->edges[i + 1] > d->edges[i]) || !std::isfinite(d->edges[i + 1])) return HWW_ERR_ARG;
@@ -616,6 +738,8 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     p->B = d->n_var_batches;
     p->N = d->particles_per_step;
     p->fp32 = d->precision == HWW_FP32_TRACK;
+    p->R = d->deriv_regions;
+    p->P2 = 2 * p->R;
     p->stream = (cudaStream_t)d->cuda_stream;
     p->device = d->device;
     p->edges.assign(d->edges, d->edges + I + 1);
@@ -629,7 +753,12 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
 
     hww_status s = HWW_OK;
     const int B = p->B;
-    p->acc_bytes = sizeof(Acc128) * (6 * (size_t)I + (size_t)B * I + 6) + sizeof(unsigned long long) * (ST_COUNT + 3);
+    const size_t P2 = (size_t)p->P2;
+    const size_t acc_main = sizeof(Acc128) * (6 * (size_t)I + (size_t)B * I + 6) +
+                            sizeof(unsigned long long) * (ST_COUNT + 3);
+    // derivative accumulators after the main block (16-byte aligned)
+    const size_t acc_off = (acc_main + 15) / 16 * 16;
+    p->acc_bytes = acc_off + sizeof(Acc128) * (P2 * I + 3 * P2 * I + 6 * P2);
     p->grp_bytes = (sizeof(unsigned long long) + 2 * sizeof(uint32_t)) * (size_t)p->N;
     const long long ntiles = group_scan_tiles(p->N);
     if ((s = dalloc(p, (char**)&p->acc, p->acc_bytes)) || (s = dalloc(p, (char**)&p->grp, p->grp_bytes)) ||
@@ -653,7 +782,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         (s = dalloc(p, &p->mat.invd, I + 1)) || (s = dalloc(p, &p->mat.g, I + 1)) ||
         (s = dalloc(p, &p->mat.cP, I)) || (s = dalloc(p, &p->mat.cA, I)) || (s = dalloc(p, &p->mat.cB, I)) ||
         (s = dalloc(p, &p->mat.inv_den, I + 2)) || (s = dalloc(p, &p->mat.vf, I + 2)) ||
-        (s = dalloc(p, &p->mat.cp, I + 2)) ||
+        (s = dalloc(p, &p->mat.cp, I + 2)) || (s = dalloc(p, &p->mat.nA, I + 2)) ||
         (s = dalloc(p, &p->norm, (size_t)B * I + 6 * (size_t)I + 8)) || (s = dalloc(p, &p->sd, 1)) ||
         (s = dalloc(p, &p->err, 1))) {
         destroy_problem(p);
@@ -666,11 +795,17 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     p->bnd = p->batch + (size_t)B * I;
     p->stats = (unsigned long long*)(p->bnd + 6);
     p->counts = p->stats + ST_COUNT;
+    if (p->P2 > 0) {
+        p->dtl = (Acc128*)(acc + acc_off);
+        p->dcen = p->dtl + P2 * I;
+        p->dbnd = p->dcen + 3 * P2 * I;
+    }
     p->gw = (unsigned long long*)p->grp;
     p->gcnt = (uint32_t*)(p->gw + p->N);
     p->gcur = p->gcnt + p->N;
     s = p->fp32 ? alloc_start_bank(p, p->b32) : alloc_start_bank(p, p->b64);
     if (s == HWW_OK) s = p->fp32 ? alloc_banks(p, p->b32) : alloc_banks(p, p->b64);
+    if (s == HWW_OK && p->P2 > 0) s = alloc_deriv(p);
     if (s) {
         destroy_problem(p);
         return s;
@@ -700,6 +835,17 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     up(p->cl_J[0], zeros.data(), sizeof(double) * (I + 1));
     up(p->cl_F[0], zeros.data(), sizeof(double) * (I + 2));
     up(p->cl_P[0], zeros.data(), sizeof(double) * 2);
+    if (p->P2 > 0) {
+        // derivative closures of the exact pulse moments, and the scores of
+        // the first start bank: zero
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaMemsetAsync(p->dcl_phi[k], 0, sizeof(double) * P2 * (I + 2), p->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->dcl_J[k], 0, sizeof(double) * P2 * (I + 1), p->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->dcl_F[k], 0, sizeof(double) * P2 * (I + 2), p->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->dcl_P[k], 0, sizeof(double) * P2 * 2, p->stream);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->bS, 0, sizeof(double) * P2 * p->N, p->stream);
+    }
     p->mat.I = I;
     p->mat.theta = d->theta;
     p->mat.bc_l = d->bc_left;
@@ -712,15 +858,16 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         return cuda_status(e);
     }
     // tracking launch shape: persistent grid of resident blocks
-    p->track_smem = sizeof(long long) * 7 * (size_t)I;
+    p->track_smem = sizeof(long long) * (7 + P2) * (size_t)I;
     if (p->track_smem > 48 * 1024) {
-        if ((p->fp32 ? track_smem_optin_fp32(p->track_smem) : track_smem_optin_fp64(p->track_smem)) != 0) {
+        if ((p->fp32 ? track_smem_optin_fp32(p->track_smem) : track_smem_optin_fp64(p->track_smem, p->P2 > 0)) !=
+            0) {
             destroy_problem(p);
             return HWW_ERR_CUDA;
         }
     }
     int per_sm = p->fp32 ? track_blocks_per_sm_fp32(TRACK_BLOCK, p->track_smem)
-                         : track_blocks_per_sm_fp64(TRACK_BLOCK, p->track_smem);
+                         : track_blocks_per_sm_fp64(TRACK_BLOCK, p->track_smem, p->P2 > 0);
     if (per_sm < 1) per_sm = 1;
     p->track_grid = p->nsm * per_sm;
     *out = p;
@@ -754,6 +901,11 @@ hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const doubl
     HWW_CK(cudaMemcpyAsync(p->d_c, cc.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_siga, sa.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_region, reg.data(), sizeof(int32_t) * I, cudaMemcpyHostToDevice, p->stream));
+    std::vector<double> ic(I);
+    if (p->P2 > 0) {
+        for (int i = 0; i < I; ++i) ic[i] = (cc[i] > 0.0) ? 1.0 / cc[i] : 0.0;
+        HWW_CK(cudaMemcpyAsync(p->d_inv_c, ic.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
+    }
     // the LOSM matrix depends on the cross sections: refactor it
     launch_losm_setup(p->mat, p->d_dx, p->d_sigt, p->d_siga, p->d.v, p->d.dt, p->d.theta, p->d.bc_left,
                       p->d.bc_right, p->err, p->stream);
@@ -764,6 +916,7 @@ hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const doubl
     HWW_CK(cudaStreamSynchronize(p->stream));
     if (e & ERR_LOSM) return HWW_ERR_NUMERIC;
     p->xs_set = 1;
+    ++p->xs_version;
     return HWW_OK;
 }
 
@@ -892,6 +1045,111 @@ hww_status get_losm_solution(const hww_problem* p, int32_t which, double* phi, d
     return copy_out(p, J, which ? p->full_J : p->semi_J, p->I + 1, on_device);
 }
 
+hww_status get_deriv_tallies(const hww_problem* p, int32_t which, double* out, int64_t n, int32_t on_device) {
+    if (!p || !out || which < 0 || which > 4) return HWW_ERR_ARG;
+    if (p->P2 < 1 || p->steps < 1) return HWW_ERR_STATE;
+    const int64_t need = (which == 4) ? 6LL * p->P2 : (int64_t)p->P2 * p->I;
+    if (n < need) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(p->device));
+    // host output: staged through the adjoint's state block (larger than
+    // [P2][I]; it is refilled whenever the adjoint runs on the last step)
+    double* dst = on_device ? out : p->vjp_state;
+    launch_deriv_normalize(p, which, dst);
+    HWW_CK(cudaGetLastError());
+    if (!on_device) {
+        HWW_CK(cudaMemcpyAsync(out, dst, sizeof(double) * need, cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaStreamSynchronize(p->stream));
+    }
+    return HWW_OK;
+}
+
+hww_status vjp_state_size(const hww_problem* p, int64_t* n) {
+    if (!p || !n) return HWW_ERR_ARG;
+    if (p->P2 < 1) return HWW_ERR_STATE;
+    *n = vjp_layout(p->I, p->P2).total;
+    return HWW_OK;
+}
+
+hww_status save_vjp_state(hww_problem* p, double* state, int64_t n, int32_t on_device) {
+    if (!p || !state) return HWW_ERR_ARG;
+    if (p->P2 < 1 || p->steps < 1) return HWW_ERR_STATE;
+    const VjpLayout L = vjp_layout(p->I, p->P2);
+    if (n < L.total) return HWW_ERR_ARG;
+    HWW_CK(cudaSetDevice(p->device));
+    hww_status s = fill_vjp_state(p);
+    if (s) return s;
+    HWW_CK(cudaMemcpyAsync(state, p->vjp_state, sizeof(double) * L.total,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+    if (!on_device) HWW_CK(cudaStreamSynchronize(p->stream));
+    return HWW_OK;
+}
+
+hww_status losm_vjp(hww_problem* p, const double* state, const double* g_mc, const double* g_phi,
+                    const double* g_J, double* grad, int32_t on_device) {
+    if (!p || !grad) return HWW_ERR_ARG;
+    if (p->P2 < 1 || p->steps < 1) return HWW_ERR_STATE;
+    HWW_CK(cudaSetDevice(p->device));
+    const int I = p->I, P2 = p->P2;
+    const VjpLayout L = vjp_layout(I, P2);
+    const double* st = p->vjp_state;
+    hww_status s = HWW_OK;
+    if (!state) {
+        if ((s = fill_vjp_state(p))) return s;
+    } else {
+        double hdr[4];
+        if (on_device) {
+            HWW_CK(cudaMemcpyAsync(hdr, state, sizeof(hdr), cudaMemcpyDeviceToHost, p->stream));
+            HWW_CK(cudaStreamSynchronize(p->stream));
+            st = state;
+        } else {
+            std::memcpy(hdr, state, sizeof(hdr));
+            HWW_CK(cudaMemcpyAsync(p->vjp_state, state, sizeof(double) * L.total, cudaMemcpyHostToDevice,
+                                   p->stream));
+        }
+        // the state must come from this problem, with its current cross sections
+        if (hdr[0] != (double)I || hdr[1] != (double)P2) return HWW_ERR_ARG;
+        if (hdr[2] != (double)p->xs_version) return HWW_ERR_STATE;
+    }
+    double* w = p->vjp_work;  // laid out as vjp_work_doubles counts
+    double *psi = w, *z = w + (I + 2), *wmc = w + 2 * (I + 2), *wphi = wmc + I, *wJ = wphi + (I + 2),
+           *wgrad = wJ + (I + 1);
+    VjpArgs a{};
+    a.m = p->mat;
+    a.dx = p->d_dx;
+    a.sigt = p->d_sigt;
+    a.c = p->d_c;
+    a.region = p->d_region;
+    a.R = p->R;
+    a.P2 = P2;
+    a.state = st;
+    a.psi = psi;
+    a.z = z;
+    // upstream vectors: used in place on the device, else staged; NULL is zero
+    cudaError_t e = cudaSuccess;
+    auto stage = [&](const double* src, double* dst, size_t n) -> const double* {
+        if (!src) {
+            if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, n * sizeof(double), p->stream);
+            return dst;
+        }
+        if (on_device) return src;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, p->stream);
+        return dst;
+    };
+    a.g_mc = g_mc ? stage(g_mc, wmc, I) : nullptr;
+    a.g_phi = stage(g_phi, wphi, I + 2);
+    a.g_J = stage(g_J, wJ, I + 1);
+    HWW_CK(e);
+    a.grad = on_device ? grad : wgrad;
+    HWW_CK(cudaPeekAtLastError());
+    p->kernel_launches += launch_losm_vjp(a, p->stream);
+    HWW_CK(cudaGetLastError());
+    if (!on_device) {
+        HWW_CK(cudaMemcpyAsync(grad, wgrad, sizeof(double) * P2, cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaStreamSynchronize(p->stream));
+    }
+    return HWW_OK;
+}
+
 hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, int64_t cap, int64_t* n) {
     if (!p || !n) return HWW_ERR_ARG;
     HWW_CK(cudaSetDevice(p->device));
@@ -990,6 +1248,8 @@ hww_status set_bank(hww_problem* p, const double* x, const double* mu, const int
     if (e == cudaSuccess) e = cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    if (p->P2 > 0 && n > 0)  // a loaded bank starts with zero scores
+        HWW_CK(cudaMemsetAsync(p->bS, 0, sizeof(double) * (size_t)p->P2 * p->N, p->stream));
     sdh.nbank = (unsigned long long)n;
     sdh.wbar = w_bar;
     sdh.bank_loaded = 1;

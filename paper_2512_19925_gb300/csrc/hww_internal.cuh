@@ -22,6 +22,7 @@ constexpr int SPLIT_CHUNK = 8;
 constexpr uint32_t MAX_DAUGHTERS = 1u << 24;
 constexpr uint32_t MAX_EVENTS = 1u << 30;
 constexpr double GRAZE_MU = 0.01;
+constexpr int MAX_SCORES = 8;  // likelihood-ratio scores per particle: (Sigma_t, c) of up to 4 regions
 
 enum ErrBits : unsigned {
     ERR_CENSUS_OVERFLOW = 1u,
@@ -72,6 +73,7 @@ struct RecQ {
     uint32_t* e;
     uint32_t* jstart;
     uint32_t* jcount;
+    double* S;  // [P2][cap] scores (derivative runs only)
     unsigned long long* count;
     long long cap;
 };
@@ -84,6 +86,7 @@ struct CenQ {
     int32_t* cell;
     uint32_t* id;
     uint64_t* lin;
+    double* S;  // [P2][cap] scores (derivative runs only)
     unsigned long long* count;
     long long cap;
 };
@@ -122,6 +125,15 @@ struct TrackArgs {
     Acc128* bnd;    // 6
     unsigned long long* stats;
     unsigned* err;
+    // likelihood-ratio derivatives (P2 = 2R > 0): score j < R is that of
+    // Sigma_t of region j, R + r that of c of region r
+    int R, P2;
+    const int32_t* region;  // I
+    const double* inv_c;    // I, 1/c (scatter score)
+    const double* bS;       // [P2][N] scores of the start bank
+    Acc128* dtl;            // [P2][I]
+    Acc128* dcen;           // [P2][3][I]
+    Acc128* dbnd;           // [P2][6]
 };
 
 // work plan of one batched tracking launch: problem p owns tiles

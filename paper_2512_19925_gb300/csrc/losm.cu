@@ -82,6 +82,7 @@ __global__ void losm_factor_kernel(LosmMat m, double theta, int bc_l, int bc_r, 
         m.inv_den[r] = inv;
         m.vf[r] = -A * inv;
         m.cp[r] = cprev;
+        if (m.nA) m.nA[r] = -A;
     }
 }
 
@@ -316,7 +317,27 @@ __device__ __forceinline__ double cen_val(const ClosureArgs& a, int q, int i, do
     return (a.v * (acc_to_double(a.cent[q * a.I + i]) * isc)) / ((double)a.N * a.dx[i]);
 }
 
-__global__ void closure_kernel(ClosureArgs a) {
+// offsets of closure set blockIdx.y (see ClosureArgs)
+__device__ __forceinline__ ClosureArgs closure_set(const ClosureArgs& in) {
+    ClosureArgs a = in;
+    const long long y = blockIdx.y, I = a.I;
+    if (y == 0) return a;
+    a.cent += y * 3 * I;
+    a.bnd += y * 6;
+    a.rphi += y * (I + 1);
+    a.rJ += y * (I + 1);
+    a.rF += y * (I + 1);
+    for (int k = 0; k < 2; ++k) {
+        a.set_phi[k] += y * (I + 2);
+        a.set_J[k] += y * (I + 1);
+        a.set_F[k] += y * (I + 2);
+        a.set_P[k] += y * 2;
+    }
+    return a;
+}
+
+__global__ void closure_kernel(ClosureArgs a_in) {
+    const ClosureArgs a = closure_set(a_in);
     const int I = a.I;
     double* nP = a.set_P[1 - a.sd->cur];
     const double isc = pow2(-a.sd->S);
@@ -326,7 +347,7 @@ __global__ void closure_kernel(ClosureArgs a) {
         if (i < I) {
             a.rphi[i] = cen_val(a, 0, i, isc);
             a.rF[i] = cen_val(a, 2, i, isc);
-            a.prev_tl[i] = (acc_to_double(a.tl[i]) * isc) / (((double)a.N * a.dx[i]) * a.dt);
+            if (a.tl) a.prev_tl[i] = (acc_to_double(a.tl[i]) * isc) / (((double)a.N * a.dx[i]) * a.dt);
         }
         double J;
         if (i == 0) {
@@ -356,7 +377,8 @@ __device__ __forceinline__ double ma_at(const double* in, int m, int j, int k) {
     return s / (double)(2 * kk + 1);
 }
 
-__global__ void filter_kernel(ClosureArgs a) {
+__global__ void filter_kernel(ClosureArgs a_in) {
+    const ClosureArgs a = closure_set(a_in);
     const int I = a.I, k = a.filter_k;
     const int c1 = 1 - a.sd->cur;
     double* nphi = a.set_phi[c1];
@@ -377,6 +399,145 @@ __global__ void filter_kernel(ClosureArgs a) {
             nphi[I + 1] = a.rphi[I - 1];
             nF[I + 1] = a.rF[I - 1];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the fully implicit solve (differentiation; not in the paper)
+//
+// lambda = A^{-T} g for the interleaved system A u = b, u = (phi_0, J_0,
+// phi_1, ..., J_I, phi_{I+1}).  Eliminating the J-rows of A^T (one per edge,
+// diagonal d_i) leaves, for the multipliers psi of the phi-rows, the
+// transpose M^T of the eliminated matrix M = L U that the forward solve
+// factorized (with the sign of the last row's multiplier flipped, because
+// the forward solve negates that row):
+//   M^T psi' = h,  h_r = g_phi,r - g_{r-1} g_J,r-1 + g_r g_J,r,
+//   psi_r = psi'_r (r <= I), psi_{I+1} = -psi'_{I+1},
+//   chi_i = (g_J,i - alpha_i psi_i - beta_i psi_{i+1}) / d_i,
+// alpha_0 = 1 (the left boundary row), alpha_i = theta; beta_I = 1 (the right
+// boundary row), beta_i = -theta.  M^T = U^T L^T turns into two first-order
+// recurrences, evaluated by the same chunked affine scans as the forward
+// solve:  z_r = h_r - c'_{r-1} z_{r-1},  psi'_r = (z_r + (-A_{r+1}) psi'_{r+1}) / den_r.
+// The parameter gradients contract lambda with the right-hand side of the
+// step's derivative data (old closures, new F and boundary closures) and with
+// the explicit dependence of A and b on Sigma_t (through Sigma_hat at the
+// edges) and on Sigma_a = Sigma_t (1 - c) (balance rows).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double vjp_block_sum(double x, double* sh) {
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = SCAN_T / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_T) losm_vjp_kernel(VjpArgs a) {
+    __shared__ Aff sh[SCAN_T];
+    __shared__ double sred[SCAN_T];
+    const LosmMat& m = a.m;
+    const int I = m.I, n = I + 2;
+    const double th = m.theta, tm1 = th - 1.0;
+    const VjpLayout L = vjp_layout(I, a.P2);
+    const double* st = a.state;
+    // h
+    for (int r = threadIdx.x; r < n; r += SCAN_T) {
+        double h = a.g_phi[r];
+        if (r >= 1) h = h - m.g[r - 1] * a.g_J[r - 1];
+        if (r <= I) h = h + m.g[r] * a.g_J[r];
+        a.z[r] = h;
+    }
+    __syncthreads();
+    const int Lc = (n + SCAN_T - 1) / SCAN_T;
+    // forward: z_r = h_r - cp_{r-1} z_{r-1}
+    {
+        const int r0 = threadIdx.x * Lc, r1 = min(n, r0 + Lc);
+        Aff f{0.0, 1.0};
+        for (int r = r0; r < r1; ++r) f = compose(f, Aff{a.z[r], r ? -m.cp[r - 1] : 0.0});
+        block_scan_aff(f, sh);
+        const Aff exc = (threadIdx.x > 0) ? sh[threadIdx.x - 1] : Aff{0.0, 1.0};
+        double zz = exc.a;
+        for (int r = r0; r < r1; ++r) {
+            zz = a.z[r] + (r ? -m.cp[r - 1] : 0.0) * zz;
+            a.z[r] = zz;
+        }
+    }
+    __syncthreads();
+    // backward: psi'_r = inv_den_r z_r + inv_den_r (-A_{r+1}) psi'_{r+1}
+    {
+        const int q0 = threadIdx.x * Lc, q1 = min(n, q0 + Lc);
+        Aff g{0.0, 1.0};
+        for (int q = q0; q < q1; ++q) {
+            const int r = n - 1 - q;
+            const double nb = (r + 1 < n) ? m.inv_den[r] * m.nA[r + 1] : 0.0;
+            g = compose(g, Aff{m.inv_den[r] * a.z[r], nb});
+        }
+        block_scan_aff(g, sh);
+        const Aff gexc = (threadIdx.x > 0) ? sh[threadIdx.x - 1] : Aff{0.0, 1.0};
+        double pp = gexc.a;
+        for (int q = q0; q < q1; ++q) {
+            const int r = n - 1 - q;
+            const double nb = (r + 1 < n) ? m.inv_den[r] * m.nA[r + 1] : 0.0;
+            pp = m.inv_den[r] * a.z[r] + nb * pp;
+            a.psi[r] = (r == n - 1) ? -pp : pp;
+        }
+    }
+    __syncthreads();
+    // contractions, one parameter at a time
+    const double* phi_old = st + L.phi_old;
+    const double* J_old = st + L.J_old;
+    const double* phi_new = st + L.phi_new;
+    const double* J_new = st + L.J_new;
+    for (int j = 0; j < a.P2; ++j) {
+        const bool is_sigma = j < a.R;
+        const int gr = is_sigma ? j : j - a.R;
+        RhsPtrs d;
+        d.phi_old = st + L.dphi_old + (long long)j * (I + 2);
+        d.J_old = st + L.dJ_old + (long long)j * (I + 1);
+        d.F_old = st + L.dF_old + (long long)j * (I + 2);
+        d.F_new = st + L.dF_new + (long long)j * (I + 2);
+        const double dPL = st[L.dP_new + 2 * j], dPR = st[L.dP_new + 2 * j + 1];
+        double acc = 0.0;
+        // first-moment rows (lambda_{2i+1} = chi_i)
+        for (int i = threadIdx.x; i <= I; i += SCAN_T) {
+            const double al = (i == 0) ? 1.0 : th;
+            const double be = (i == I) ? 1.0 : -th;
+            const double chi = (a.g_J[i] - al * a.psi[i] - be * a.psi[i + 1]) * m.invd[i];
+            double rhs = moment_rhs(m, d, i);
+            const double dxl = (i >= 1) ? a.dx[i - 1] : 0.0;
+            const double dxr = (i <= I - 1) ? a.dx[i] : 0.0;
+            const double dsl = (is_sigma && i >= 1 && a.region[i - 1] == gr) ? 1.0 : 0.0;
+            const double dsr = (is_sigma && i <= I - 1 && a.region[i] == gr) ? 1.0 : 0.0;
+            const double dES = 0.5 * (dsl * dxl + dsr * dxr);  // d(Sigma_hat dxhat)
+            rhs = rhs + tm1 * dES * J_old[i] - th * dES * J_new[i];
+            acc = acc + chi * rhs;
+        }
+        // balance rows (lambda_{2r} = psi_r), r = 1..I
+        for (int r = threadIdx.x + 1; r <= I; r += SCAN_T) {
+            const double oldb = d.J_old[r] - d.J_old[r - 1] + m.cA[r - 1] * d.phi_old[r];
+            double rhs = m.cP[r - 1] * d.phi_old[r] + tm1 * oldb;
+            if (a.region[r - 1] == gr) {
+                const double dsa = is_sigma ? 1.0 - a.c[r - 1] : -a.sigt[r - 1];
+                const double dxi = a.dx[r - 1];
+                rhs = rhs + tm1 * dsa * dxi * phi_old[r] - th * dsa * dxi * phi_new[r];
+            }
+            acc = acc + a.psi[r] * rhs;
+        }
+        // boundary rows (natural form: P_L on the left, -P_R on the right)
+        if (threadIdx.x == 0) {
+            if (m.bc_l != 1) acc = acc + a.psi[0] * dPL;
+            if (m.bc_r != 1) acc = acc - a.psi[I + 1] * dPR;
+        }
+        // Monte Carlo flux part
+        if (a.g_mc) {
+            const double* dtl = st + L.dtl + (long long)j * I;
+            for (int i = threadIdx.x; i < I; i += SCAN_T) acc = acc + dtl[i] * a.g_mc[i];
+        }
+        const double tot = vjp_block_sum(acc, sred);
+        if (threadIdx.x == 0) a.grad[j] = tot;
     }
 }
 
@@ -416,9 +577,15 @@ void launch_step_scalars(StepDev* sd, int nbits, unsigned long long seed, int mo
 }
 
 int launch_closures(const ClosureArgs& a, cudaStream_t s) {
-    closure_kernel<<<small_grid(a.I + 1), 128, 0, s>>>(a);
-    filter_kernel<<<small_grid(a.I + 2), 128, 0, s>>>(a);
+    const unsigned ny = a.nsets > 1 ? (unsigned)a.nsets : 1u;
+    closure_kernel<<<dim3(small_grid(a.I + 1), ny), 128, 0, s>>>(a);
+    filter_kernel<<<dim3(small_grid(a.I + 2), ny), 128, 0, s>>>(a);
     return 2;
+}
+
+int launch_losm_vjp(const VjpArgs& a, cudaStream_t s) {
+    losm_vjp_kernel<<<1, SCAN_T, 0, s>>>(a);
+    return 1;
 }
 
 }  // namespace hww

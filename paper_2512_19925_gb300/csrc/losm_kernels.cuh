@@ -19,6 +19,7 @@ struct LosmMat {
     double* inv_den; // [I+2] Thomas pivots, inverted
     double* vf;      // [I+2] -A_r / den_r
     double* cp;      // [I+2] C_r / den_r
+    double* nA;      // [I+2] -A_r, for the transposed solve (nullable)
 };
 
 // right-hand-side inputs of one solve (paper layout).  With `sd` set, the
@@ -76,8 +77,53 @@ struct ClosureArgs {
     const Acc128* bnd;
     double *rphi, *rJ, *rF;        // unfiltered: I, I+1, I
     double *set_phi[2], *set_J[2], *set_F[2], *set_P[2];  // closure sets; t^n goes to 1-cur
-    double* prev_tl;               // I
+    double* prev_tl;               // I (written when tl is set)
+    // several closure sets at once (the derivative closures, one per
+    // parameter; blockIdx.y picks the set): consecutive sets are 3I
+    // accumulators apart in cent, 6 in bnd, I+1 in the scratch vectors and
+    // I+2 / I+1 / I+2 / 2 in the phi / J / F / P sets
+    int nsets;
 };
+
+// adjoint of the fully implicit solve of the last step (transpose Thomas)
+// contracted with the parameter directions; the step's vectors come from a
+// state block laid out by vjp_state_offsets
+struct VjpArgs {
+    LosmMat m;
+    const double* dx;
+    const double* sigt;
+    const double* c;
+    const int32_t* region;
+    int R, P2;
+    const double* state;
+    const double* g_mc;   // I or NULL
+    const double* g_phi;  // I+2
+    const double* g_J;    // I+1
+    double* psi;          // work: I+2 (even unknowns of lambda)
+    double* z;            // work: I+2
+    double* grad;         // P2
+};
+
+// doubles of a state block and the offsets of its parts
+struct VjpLayout {
+    long long phi_old, J_old, phi_new, J_new, dtl, dphi_old, dJ_old, dF_old, dF_new, dP_new, total;
+};
+__host__ __device__ inline VjpLayout vjp_layout(int I, int P2) {
+    VjpLayout L;
+    long long o = 4;  // header: I, P2, cross-section version, spare
+    L.phi_old = o; o += I + 2;
+    L.J_old = o; o += I + 1;
+    L.phi_new = o; o += I + 2;
+    L.J_new = o; o += I + 1;
+    L.dtl = o; o += (long long)P2 * I;
+    L.dphi_old = o; o += (long long)P2 * (I + 2);
+    L.dJ_old = o; o += (long long)P2 * (I + 1);
+    L.dF_old = o; o += (long long)P2 * (I + 2);
+    L.dF_new = o; o += (long long)P2 * (I + 2);
+    L.dP_new = o; o += (long long)P2 * 2;
+    L.total = o;
+    return L;
+}
 
 void launch_losm_setup(const LosmMat& m, const double* dx, const double* sigt, const double* siga, double v,
                        double dt, double theta, int bc_l, int bc_r, unsigned* err, cudaStream_t s);
@@ -87,5 +133,6 @@ int launch_ww_centers(const WwArgs& a, int lagged, cudaStream_t s);
 void launch_step_scalars(StepDev* sd, int nbits, unsigned long long seed, int mode, unsigned long long* stats,
                          cudaStream_t s);
 int launch_closures(const ClosureArgs& a, cudaStream_t s);
+int launch_losm_vjp(const VjpArgs& a, cudaStream_t s);
 
 }  // namespace hww

@@ -199,6 +199,11 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
             a.bmu[k] = mu;
             a.bcell[k] = cell;
         }
+        // derivative runs: every copy keeps the scores of its source
+        for (int q = 0; q < a.P2; ++q) {
+            const double sq = a.cS[(long long)q * a.cen_cap + j];
+            for (long long k = k0; k < k1; ++k) a.bS[(long long)q * a.N + k] = sq;
+        }
     }
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }

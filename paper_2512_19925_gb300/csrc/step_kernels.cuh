@@ -36,6 +36,9 @@ struct CombArgs {
     int32_t* bcell;
     unsigned long long* stats;
     unsigned* err;
+    int P2;            // scores per particle (0: none)
+    const double* cS;  // [P2][cen_cap] census scores
+    double* bS;        // [P2][N] start-bank scores
 };
 
 void launch_group_scan(const ScanArgs& a, cudaStream_t s);
@@ -45,9 +48,9 @@ void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s);
 void launch_philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
                          long long n, uint32_t* out, cudaStream_t s);
 
-int track_smem_optin_fp64(size_t smem);
+int track_smem_optin_fp64(size_t smem, int deriv);
 int track_smem_optin_fp32(size_t smem);
-int track_blocks_per_sm_fp64(int block, size_t smem);
+int track_blocks_per_sm_fp64(int block, size_t smem, int deriv);
 int track_blocks_per_sm_fp32(int block, size_t smem);
 
 }  // namespace hww

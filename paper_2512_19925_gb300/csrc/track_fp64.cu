@@ -25,6 +25,17 @@
 // continuation record, so long histories are rebalanced between launches.
 // The event loop is flattened: a lane whose track ends loads its next track
 // while the other lanes take their next event.
+//
+// Derivative runs (a separate instantiation, DERIV = true) also carry the
+// likelihood-ratio scores of (Sigma_t, c) per region: a flight of length l in
+// region r adds -l to the Sigma_t score of r and a collision 1/Sigma_t; a
+// scatter adds 1/c to the c score of r (an absorption ends the history, so its
+// score never reaches a tally).  Each tally gets w l S_j (track length), w S_j,
+// w mu S_j, w (1/3 - mu^2) S_j (census) and the surface terms times S_j, with
+// the scores after the segment's own flight term.  Daughters, roulette
+// survivors, records and census particles keep the scores; the games' own
+// probabilities do not depend on the parameters (their centers are held
+// fixed), so they add nothing.
 #include "track_common.cuh"
 
 namespace hww {
@@ -38,12 +49,18 @@ struct P64 {
     uint32_t e;
 };
 
-__device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P64& q, double w,
+template <bool DERIV>
+__device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P64& q, const double* S, double w,
                                             uint32_t e, uint32_t jstart, uint32_t jcount,
                                             unsigned long long slot) {
     if ((long long)slot >= a.rout.cap) {
         atomicOr(a.err, ERR_QUEUE_OVERFLOW);
         return;
+    }
+    if constexpr (DERIV) {
+#pragma unroll
+        for (int j = 0; j < MAX_SCORES; ++j)
+            if (j < a.P2) a.rout.S[(long long)j * a.rout.cap + (long long)slot] = S[j];
     }
     a.rout.x[slot] = q.x;
     a.rout.mu[slot] = q.mu;
@@ -59,6 +76,9 @@ __device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P6
 
 // The event loop over items [item, item_end) with the given stride; b_blk is
 // the variance batch whose row is kept in shared memory (-1: none).
+// In derivative runs the shared row block after the batch row holds the
+// derivative track-length tallies [P2][I].
+template <bool DERIV>
 __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long item, const long long item_end,
                                           const long long stride, const int b_blk, long long* sm,
                                           Counters& cnt) {
@@ -66,6 +86,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
     long long* s_tl = sm;
     long long* s_cen = sm + 3 * I;
     long long* s_bat = sm + 6 * I;  // batch row of the current id range
+    long long* s_dtl = sm + 7 * I;  // derivative runs: [P2][I]
+    const int R = a.R, P2 = a.P2;
+    double S[DERIV ? MAX_SCORES : 1];     // scores of the current track
+    double bS[DERIV ? MAX_SCORES : 1];    // scores of the record being expanded
     const double tscale = a.sd->tscale;
     const double cscale = a.sd->cscale;
     const double wbar = a.sd->wbar;
@@ -87,6 +111,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 q.lin = lineage_hash(base.lin, base.e, jnext);
                 q.e = 0;
                 ++jnext;
+                if constexpr (DERIV) {
+#pragma unroll
+                    for (int j = 0; j < MAX_SCORES; ++j) S[j] = bS[j];
+                }
             } else if (item < item_end) {
                 const long long i = item;
                 item += stride;
@@ -96,6 +124,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     q.e = 0;
                     q.tau = a.tau0;
                     q.w = wbar;
+                    if constexpr (DERIV) {
+#pragma unroll
+                        for (int j = 0; j < MAX_SCORES; ++j)
+                            S[j] = (!birth && j < P2) ? a.bS[(long long)j * a.N + i] : 0.0;
+                    }
                     if (birth) {
                         uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
                         philox4x32_10(r, k0, k1);
@@ -118,9 +151,18 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     q.id = a.rin.id[i];
                     q.lin = a.rin.lin[i];
                     q.e = a.rin.e[i];
+                    if constexpr (DERIV) {
+#pragma unroll
+                        for (int j = 0; j < MAX_SCORES; ++j)
+                            S[j] = (j < P2) ? a.rin.S[(long long)j * a.rin.cap + i] : 0.0;
+                    }
                     const uint32_t jc = a.rin.jcount[i];
                     if (jc) {
                         base = q;
+                        if constexpr (DERIV) {
+#pragma unroll
+                            for (int j = 0; j < MAX_SCORES; ++j) bS[j] = S[j];
+                        }
                         jnext = a.rin.jstart[i];
                         jend = jnext + jc;
                         q.lin = lineage_hash(base.lin, base.e, jnext);
@@ -138,7 +180,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
         }
         // ---- one event ----
         if (evs == a.emax) {
-            push_record(a, q, q.w, q.e, 0u, 0u, atomicAdd(a.rout.count, 1ull));
+            push_record<DERIV>(a, q, S, q.w, q.e, 0u, 0u, atomicAdd(a.rout.count, 1ull));
             have = false;
             continue;
         }
@@ -187,6 +229,20 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     add128(&a.batch[(long long)b * I + k], g.s0);
             }
         }
+        if constexpr (DERIV) {
+            // scores after this segment's flight, then w l S_j per parameter
+            const int rg = a.region[k];
+#pragma unroll
+            for (int j = 0; j < MAX_SCORES; ++j) {
+                if (j == rg) {
+                    S[j] = S[j] - l;
+                    if (ev == 2) S[j] = S[j] + a.inv_sigt[k];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < MAX_SCORES; ++j)
+                if (j < P2) sadd(&s_dtl[j * I + k], to_fixed(wl * S[j], tscale));
+        }
         cnt.v[ST_SEGMENTS]++;
         // move
         if (ev == 1) {
@@ -212,8 +268,24 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     sadd(&s_cen[2 * I + k], g.s2);
                 }
             }
+            if constexpr (DERIV) {
+#pragma unroll
+                for (int j = 0; j < MAX_SCORES; ++j) {
+                    if (j < P2) {
+                        Acc128* d = a.dcen + (long long)j * 3 * I;
+                        add128(&d[k], to_fixed(q.w * S[j], tscale));
+                        add128(&d[I + k], to_fixed(wmu * S[j], tscale));
+                        add128(&d[2 * I + k], to_fixed(wf * S[j], tscale));
+                    }
+                }
+            }
             const unsigned long long slot = warp_reserve(a.cen.count);
             if ((long long)slot < a.cen.cap) {
+                if constexpr (DERIV) {
+#pragma unroll
+                    for (int j = 0; j < MAX_SCORES; ++j)
+                        if (j < P2) a.cen.S[(long long)j * a.cen.cap + (long long)slot] = S[j];
+                }
                 a.cen.x[slot] = q.x;
                 a.cen.mu[slot] = q.mu;
                 a.cen.w[slot] = q.w;
@@ -245,6 +317,17 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     add128(&a.bnd[3 * side + 0], to_fixed(wi, tscale));
                     add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu), tscale));
                     add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), tscale));
+                    if constexpr (DERIV) {
+#pragma unroll
+                        for (int j = 0; j < MAX_SCORES; ++j) {
+                            if (j < P2) {
+                                Acc128* d = a.dbnd + 6 * j + 3 * side;
+                                add128(&d[0], to_fixed(wi * S[j], tscale));
+                                add128(&d[1], to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu) * S[j], tscale));
+                                add128(&d[2], to_fixed(wi * (0.5 - amu) * S[j], tscale));
+                            }
+                        }
+                    }
                     cnt.v[ST_LEAKED]++;
                     cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
                     have = false;
@@ -273,6 +356,12 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             q.mu = 2.0 * u01(r2[0], r2[1]) - 1.0;
             q.inv_mu = 1.0 / q.mu;
             cnt.v[ST_SCATTERS]++;
+            if constexpr (DERIV) {
+                const int jc = R + a.region[k];
+#pragma unroll
+                for (int j = 0; j < MAX_SCORES; ++j)
+                    if (j == jc) S[j] = S[j] + a.inv_c[k];
+            }
         }
         if (ww_on) {
             const int kc = q.cell;
@@ -295,7 +384,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 for (uint32_t ch = 0; ch < nch; ++ch) {
                     const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
                     const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
-                    push_record(a, q, wd, e_ev, j0, jc, b0 + ch);
+                    push_record<DERIV>(a, q, S, wd, e_ev, j0, jc, b0 + ch);
                 }
                 q.w = wd;
                 q.lin = lineage_hash(q.lin, e_ev, 0);
@@ -325,10 +414,12 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
     }
 }
 
+template <bool DERIV>
 __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
     extern __shared__ long long sm[];
     const int I = a.I;
-    for (int i = threadIdx.x; i < 7 * I; i += blockDim.x) sm[i] = 0;
+    const int rows = DERIV ? 7 + a.P2 : 7;
+    for (int i = threadIdx.x; i < rows * I; i += blockDim.x) sm[i] = 0;
     __syncthreads();
     Counters cnt;
     cnt.zero();
@@ -350,9 +441,13 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
         item_end = n_use;
         stride = (long long)gridDim.x * blockDim.x;
     }
-    run_items(a, item, item_end, stride, b_blk, sm, cnt);
+    run_items<DERIV>(a, item, item_end, stride, b_blk, sm, cnt);
     __syncthreads();
     flush_tallies(sm, I, a.tl, a.cent);
+    if constexpr (DERIV) {
+        for (int i = threadIdx.x; i < a.P2 * I; i += blockDim.x)
+            if (sm[7 * I + i] != 0) add128(&a.dtl[i], sm[7 * I + i]);
+    }
     if (b_blk >= 0)
         for (int i = threadIdx.x; i < I; i += blockDim.x)
             if (sm[6 * I + i] != 0) add128(&a.batch[(long long)b_blk * I + i], sm[6 * I + i]);
@@ -409,7 +504,7 @@ __global__ void __launch_bounds__(256, 3) track64_kernel_batch(const TrackArgs<d
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
         const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N) : -1;
-        run_items(A, i0 + threadIdx.x, i1, blockDim.x, b_tile, sm, cnt);
+        run_items<false>(A, i0 + threadIdx.x, i1, blockDim.x, b_tile, sm, cnt);
         __syncthreads();
         if (b_tile >= 0)
             for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
@@ -426,16 +521,23 @@ __global__ void __launch_bounds__(256, 3) track64_kernel_batch(const TrackArgs<d
 }  // namespace
 
 void launch_track_fp64(const TrackArgs<double>& a, int grid, int block, size_t smem, cudaStream_t s) {
-    track64_kernel<<<grid, block, smem, s>>>(a);
+    if (a.P2 > 0)
+        track64_kernel<true><<<grid, block, smem, s>>>(a);
+    else
+        track64_kernel<false><<<grid, block, smem, s>>>(a);
 }
 
-int track_smem_optin_fp64(size_t smem) {
-    return raise_smem_limit((const void*)track64_kernel, smem);
+int track_smem_optin_fp64(size_t smem, int deriv) {
+    return deriv ? raise_smem_limit((const void*)track64_kernel<true>, smem)
+                 : raise_smem_limit((const void*)track64_kernel<false>, smem);
 }
 
-int track_blocks_per_sm_fp64(int block, size_t smem) {
+int track_blocks_per_sm_fp64(int block, size_t smem, int deriv) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, track64_kernel, block, smem);
+    if (deriv)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, track64_kernel<true>, block, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, track64_kernel<false>, block, smem);
     return n;
 }
 
