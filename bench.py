@@ -44,6 +44,11 @@ WORKLOAD = ("plain_at_scale: slab [-50,50], Sigma_t=1, c=0.9, v=1, 1000 cells, d
 # lineage); FP32 tracking stores offsets and directions in 4 bytes, FP64 in 8
 BANK_BYTES = {"fp32": 12, "fp64": 20}
 CENSUS_BYTES = {"fp32": 32, "fp64": 40}
+# DRAM bytes (read + write) that one wave-0 tracking launch moves per start
+# particle, measured by ncu on the 4e6-particle case of this workload
+# (profiles/track32_kernel_plain_at_scale_fp32.txt; traffic grows with the
+# particle count).  Set to None whenever track32_kernel changes.
+TRACK32_DRAM_BYTES_PER_START = 237.8e6 / 4e6
 
 
 def dist_env():
@@ -189,6 +194,73 @@ def run_e2e(hww, torch, precision, n_particles, seed, warmup, steps):
     return dict(value=segs / dt, h2d=2 * I * 8, d2h=I * 8 + 8 * 20, phi_sum=float(phi.sum()))
 
 
+def run_batch(hww, torch, warmup, steps, tune):
+    """The batched sweep: 256 independent slabs stepped together (persistent
+    tile-queue tracking, one graph per pre/post stage).  The autotuner's trial
+    steps are ordinary steps and run before the warm-up."""
+    from paper_2512_19925_gb300 import autotune
+
+    wls = workloads.batched_sweep()
+    b = hww.Batch(wls)
+    best = None
+    if tune:
+        best, _ = autotune.autotune_batch(b, steps_per_trial=1, sync=torch.cuda.synchronize,
+                                          gpu_name=torch.cuda.get_device_name())
+    for _ in range(warmup):
+        b.run_step()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    segs = 0
+    for _ in range(steps):
+        segs += b.run_step()["segments"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n = sum(int(w["particles_per_step"]) for w in wls)
+    b.close()
+    return {"value": segs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "problems": len(wls),
+            "particles_per_step": n, "tuning": list(best) if best else None,
+            "workload": "batched_sweep: 256 slabs [-50,50], cells U[100,2000], particles logU[1e4,1e6], "
+                        "Sigma_t U[0.5,5], c U[0.3,0.999], ratio {2,3,5,10}, dt 0.1, FP32 tracking"}
+
+
+def run_deriv(hww, torch, n_particles, warmup, steps):
+    """The differentiation workload (three-region shield, FP64, derivative
+    tallies for the 6 parameters): time per step with the derivative tallies
+    and per adjoint call."""
+    wl = workloads.differentiation(particles_per_step=n_particles)
+    p = hww.Problem.from_workload(wl, deriv=True)
+    for _ in range(warmup):
+        p.run_step()
+    I = len(wl["edges"]) - 1
+    g_mc = torch.ones(I, dtype=torch.float64, device="cuda")
+    g_phi = torch.ones(I + 2, dtype=torch.float64, device="cuda")
+    g_j = torch.zeros(I + 1, dtype=torch.float64, device="cuda")
+    grad = torch.empty(2 * p.R, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    segs = 0
+    for _ in range(steps):
+        segs += p.run_step()["segments"]
+    ev[1].record(stream)
+    ev[2].record(stream)
+    for _ in range(steps):
+        p.losm_vjp(g_mc, g_phi, g_j, out=grad)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    ms, ms_vjp = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    p.close()
+    return {"value": segs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "vjp_ms": ms_vjp / steps, "parameters": 2 * int(wl["n_regions"]), "particles_per_step": n_particles,
+            "workload": "differentiation: shield [0,40] (3 regions), 800 cells, dt 0.1, FP64 with "
+                        "derivative tallies for (Sigma_t, c) of each region"}
+
+
 def cpu_oracle_sample(n_particles, max_steps, budget_s):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     same workload: segments per second over the first steps."""
@@ -299,6 +371,10 @@ def main(args):
                       "gain_fp32_over_fp64": (f32 / f64) if (f32 and f64) else None}
 
     e2e = run_e2e(hww, torch, "fp32", N, seed, args.warmup, args.steps) if not args.no_e2e else None
+    if not args.no_batch:
+        out["batched"] = run_batch(hww, torch, args.warmup, args.steps, tune=not args.no_tune)
+    if not args.no_deriv:
+        out["differentiation"] = run_deriv(hww, torch, args.deriv_particles, args.warmup, args.steps)
     e2e_val = reduce_sum(e2e["value"]) if e2e else None
 
     # roofline of the dominant kernel (tracking), bank-streaming bytes
@@ -307,8 +383,11 @@ def main(args):
     track_ms = cnt["track_ms"]
     bytes_alg = N * args.steps * BANK_BYTES["fp32"] + fast["census"] * CENSUS_BYTES["fp32"]
     achieved = (bytes_alg / (track_ms * 1e-3)) / 1e9 if track_ms > 0 else None
+    traffic = TRACK32_DRAM_BYTES_PER_START * N if TRACK32_DRAM_BYTES_PER_START else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_note": "DRAM bytes of the wave-0 launch per step, scaled by particles from the 4e6 capture",
+            "limiter": "issue/latency (ncu: 31% issue active, 42% long-scoreboard stalls, 2.4% DRAM)",
             "peak_source": peak_kind, "kernel": "track32_kernel",
             "launches": cnt["track_launches"], "kernel_ms_per_step": track_ms / args.steps,
             "algorithmic_bytes_per_step": bytes_alg / args.steps}
@@ -356,6 +435,10 @@ def parse(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-deriv", action="store_true")
+    ap.add_argument("--deriv-particles", type=int, default=10_000_000)
     return ap.parse_args(argv)
 
 

@@ -639,14 +639,16 @@ hww_status stage_post(hww_problem* p) {
     return p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);
 }
 
-hww_status read_stats(hww_problem* p, hww_step_stats* st) {
-    unsigned long long h[ST_COUNT];
-    StepDev sdh;
-    unsigned e = 0;
-    HWW_CK(cudaMemcpyAsync(h, p->stats, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
-    HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
-    HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
-    HWW_CK(cudaStreamSynchronize(p->stream));
+double bits_to_double(unsigned long long b) {
+    double d;
+    std::memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+// step statistics from the raw counters, the start-bank size and weight of
+// the next step and the device error word
+void fill_stats(const unsigned long long* h, unsigned long long nbank, double wbar, unsigned e, int waves,
+                hww_step_stats* st) {
     std::memset(st, 0, sizeof(*st));
     st->segments = (int64_t)h[ST_SEGMENTS];
     st->collisions = (int64_t)h[ST_COLLISIONS];
@@ -662,12 +664,23 @@ hww_status read_stats(hww_problem* p, hww_step_stats* st) {
     st->census = (int64_t)h[ST_CENSUS];
     st->lineage_collisions = (int64_t)h[ST_LINEAGE];
     st->max_events = (int64_t)h[ST_MAX_EVENTS];
-    st->n_next = (int64_t)sdh.nbank;
+    st->n_next = (int64_t)nbank;
     st->n_start = (int64_t)h[ST_NSTART];
-    st->w_bar_next = sdh.wbar;
-    st->waves = p->last_waves;
-    if (e) HWW_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    st->w_bar_next = wbar;
+    st->waves = waves;
     st->status = err_to_status(e);
+}
+
+hww_status read_stats(hww_problem* p, hww_step_stats* st) {
+    unsigned long long h[ST_COUNT];
+    StepDev sdh;
+    unsigned e = 0;
+    HWW_CK(cudaMemcpyAsync(h, p->stats, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    fill_stats(h, sdh.nbank, sdh.wbar, e, p->last_waves, st);
+    if (e) HWW_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
     return (hww_status)st->status;
 }
 
@@ -1440,6 +1453,11 @@ struct hww_batch {
     unsigned long long* h_total = nullptr;  // pinned
     unsigned* h_errs = nullptr;             // pinned
     unsigned long long* h_qpeak = nullptr;  // pinned
+    // every member's step statistics gathered by one kernel: per member
+    // ST_COUNT counters, start-bank size, weight bits, error word
+    unsigned long long* d_gather = nullptr;
+    unsigned long long* h_gather = nullptr;  // pinned
+    int gathered = 0;                        // h_gather holds the last step
     int last_waves = 0;
 };
 
@@ -1486,6 +1504,30 @@ __global__ void batch_total_kernel(const TrackArgs<Real>* args, int P, unsigned 
         __syncthreads();
     }
     if (threadIdx.x == 0) *total = s[0];
+}
+
+constexpr int GATHER = ST_COUNT + 3;
+
+// gather the members' statistics of the step and clear their error words
+// (each step reports its errors once, as read_stats does)
+template <class Real>
+__global__ void batch_gather_kernel(const TrackArgs<Real>* args, int P, unsigned long long* out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P * GATHER; t += gridDim.x * blockDim.x) {
+        const int p = t / GATHER, k = t % GATHER;
+        const TrackArgs<Real>& a = args[p];
+        unsigned long long v;
+        if (k < ST_COUNT)
+            v = a.stats[k];
+        else if (k == ST_COUNT)
+            v = a.sd->nbank;
+        else if (k == ST_COUNT + 1)
+            v = (unsigned long long)__double_as_longlong(a.sd->wbar);
+        else {
+            v = *a.err;  // read and cleared by this thread only
+            *a.err = 0;
+        }
+        out[t] = v;
+    }
 }
 
 template <class Real>
@@ -1601,6 +1643,8 @@ void destroy_batch(hww_batch* b) {
     if (b->d_total) cudaFree(b->d_total);
     if (b->d_errs) cudaFree(b->d_errs);
     if (b->d_qpeak) cudaFree(b->d_qpeak);
+    if (b->d_gather) cudaFree(b->d_gather);
+    if (b->h_gather) cudaFreeHost(b->h_gather);
     if (b->h_qpeak) cudaFreeHost(b->h_qpeak);
     if (b->h_total) cudaFreeHost(b->h_total);
     if (b->h_errs) cudaFreeHost(b->h_errs);
@@ -1679,6 +1723,8 @@ hww_status create_batch(const hww_problem_desc* descs, int32_t n, void* cuda_str
     if (e == cudaSuccess) e = cudaMalloc(&b->d_errs, sizeof(unsigned) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_qpeak, sizeof(unsigned long long) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_qpeak, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_gather, sizeof(unsigned long long) * GATHER * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_gather, sizeof(unsigned long long) * GATHER * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_total, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_errs, sizeof(unsigned) * n);
     if (e != cudaSuccess) {
@@ -1756,14 +1802,29 @@ hww_status run_batch_step(hww_batch* b, hww_batch_stats* stats) {
         p->steps += 1;
         p->last_waves = b->last_waves;
     }
+    b->gathered = 0;
     if (!stats) return HWW_OK;
+    // one gather kernel and one copy for all members' statistics
+    if (b->fp32)
+        batch_gather_kernel<float><<<(b->P * GATHER + 255) / 256, 256, 0, b->stream>>>(
+            (const TrackArgs<float>*)b->d_args[0], b->P, b->d_gather);
+    else
+        batch_gather_kernel<double><<<(b->P * GATHER + 255) / 256, 256, 0, b->stream>>>(
+            (const TrackArgs<double>*)b->d_args[0], b->P, b->d_gather);
+    HWW_CK(cudaGetLastError());
+    HWW_CK(cudaMemcpyAsync(b->h_gather, b->d_gather, sizeof(unsigned long long) * GATHER * b->P,
+                           cudaMemcpyDeviceToHost, b->stream));
     HWW_CK(cudaStreamSynchronize(b->stream));
+    b->gathered = 1;
     std::memset(stats, 0, sizeof(*stats));
     stats->problems = b->P;
     stats->waves = b->last_waves;
-    for (hww_problem* p : b->m) {
+    for (int i = 0; i < b->P; ++i) {
+        const unsigned long long* g = b->h_gather + (size_t)i * GATHER;
         hww_step_stats ms;
-        const hww_status r = read_stats(p, &ms);
+        fill_stats(g, g[ST_COUNT], bits_to_double(g[ST_COUNT + 1]), (unsigned)g[ST_COUNT + 2],
+                   b->last_waves, &ms);
+        const hww_status r = (hww_status)ms.status;
         stats->segments += ms.segments;
         stats->census += ms.census;
         stats->daughters += ms.daughters;
@@ -1779,6 +1840,13 @@ hww_status batch_member_stats(hww_batch* b, int32_t i, hww_step_stats* stats) {
     if (!b || !stats || i < 0 || i >= b->P) return HWW_ERR_ARG;
     HWW_CK(cudaSetDevice(b->device));
     HWW_CK(cudaStreamSynchronize(b->stream));
+    if (b->gathered) {
+        // the statistics gathered at the end of the step (errors already reported there)
+        const unsigned long long* g = b->h_gather + (size_t)i * GATHER;
+        fill_stats(g, g[ST_COUNT], bits_to_double(g[ST_COUNT + 1]), (unsigned)g[ST_COUNT + 2],
+                   b->last_waves, stats);
+        return (hww_status)stats->status;
+    }
     return read_stats(b->m[i], stats);
 }
 

@@ -348,7 +348,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
     }
 }
 
-__global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
+// Two resident blocks of 256 threads per SM: the event loop wants about 120
+// registers; at three blocks it spills to local memory, whose traffic (the
+// L1 left beside the shared tallies hits ~20% of it) costs more time than
+// the extra warps hide.
+__global__ void __launch_bounds__(256, 2) track32_kernel(TrackArgs<float> a) {
     extern __shared__ long long sm[];
     const int I = a.I;
     for (int i = threadIdx.x; i < 7 * I; i += blockDim.x) sm[i] = 0;
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(256, 3) track32_kernel(TrackArgs<float> a) {
 // Persistent batched variant: blocks pop tiles (problem, id range) from a
 // device counter; the block-private tallies are flushed when a block moves
 // to another problem, the batch row after every tile.
-__global__ void __launch_bounds__(256, 3) track32_kernel_batch(const TrackArgs<float>* args, BatchPlan plan) {
+__global__ void __launch_bounds__(256, 2) track32_kernel_batch(const TrackArgs<float>* args, BatchPlan plan) {
     extern __shared__ long long sm[];
     __shared__ TrackArgs<float> A;
     __shared__ long long s_t;

@@ -415,7 +415,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
 }
 
 template <bool DERIV>
-__global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
+// Two resident blocks of 256 threads per SM: the event loop wants about 120
+// registers; at three blocks it spills to local memory, whose traffic (the
+// L1 left beside the shared tallies hits ~20% of it) costs more time than
+// the extra warps hide.
+__global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
     extern __shared__ long long sm[];
     const int I = a.I;
     const int rows = DERIV ? 7 + a.P2 : 7;
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(256, 3) track64_kernel(TrackArgs<double> a) {
 // Persistent batched variant: blocks pop tiles (problem, id range) from a
 // device counter; the block-private tallies are flushed when a block moves
 // to another problem, the batch row after every tile.
-__global__ void __launch_bounds__(256, 3) track64_kernel_batch(const TrackArgs<double>* args, BatchPlan plan) {
+__global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<double>* args, BatchPlan plan) {
     extern __shared__ long long sm[];
     __shared__ TrackArgs<double> A;
     __shared__ long long s_t;
