@@ -65,7 +65,7 @@ struct hww_problem {
     size_t acc_bytes = 0;
     Acc128 *tl = nullptr, *cent = nullptr, *batch = nullptr, *bnd = nullptr;
     unsigned long long* stats = nullptr;
-    unsigned long long* counts = nullptr;  // [0] census, [1] q0, [2] q1
+    unsigned long long* counts = nullptr;  // [0] census, [1] q0, [2] q1, [3..7] comb group list lengths
     // comb groups (one clear)
     void* grp = nullptr;
     size_t grp_bytes = 0;
@@ -73,6 +73,8 @@ struct hww_problem {
     uint32_t *gcnt = nullptr, *gcur = nullptr;
     unsigned long long *goff = nullptr, *goff_w = nullptr, *tile_c = nullptr, *tile_w = nullptr;
     uint32_t* member = nullptr;
+    unsigned long long* cpre = nullptr;    // comb prefix of members of multi-member groups (census-sized)
+    uint32_t* glist = nullptr;             // ids of comb groups of 3+ members by size class (census-sized)
     // closures and LOSM
     // two closure sets (phi I+2, J I+1, F I+2, P 2): `cur` holds the
     // initial conditions of the next step, the other is built at t^n
@@ -206,6 +208,23 @@ hww_status alloc_start_bank(hww_problem* p, Banks<Real>& b) {
     return HWW_OK;
 }
 
+// lists of comb groups of 3+ members by size class (3-4, 5-8, 9-16, 17-32,
+// more): a class whose groups have at least m members holds at most
+// census / m of them
+void glist_offsets(long long C, long long off[5]) {
+    const long long minm[5] = {3, 5, 9, 17, 33};
+    long long o = 0;
+    for (int k = 0; k < 5; ++k) {
+        off[k] = o;
+        o += C / minm[k] + 1;
+    }
+}
+size_t glist_len(long long C) {
+    long long off[5];
+    glist_offsets(C, off);
+    return (size_t)(off[4] + C / 33 + 1);
+}
+
 // census bank, both record queues and the comb member list, sized by the
 // current capacities
 template <class Real>
@@ -215,7 +234,8 @@ hww_status alloc_banks(hww_problem* p, Banks<Real>& b) {
     if ((s = dalloc(p, &b.cen.x, C, true)) || (s = dalloc(p, &b.cen.mu, C, true)) ||
         (s = dalloc(p, &b.cen.w, C, true)) || (s = dalloc(p, &b.cen.cell, C, true)) ||
         (s = dalloc(p, &b.cen.id, C, true)) || (s = dalloc(p, &b.cen.lin, C, true)) ||
-        (s = dalloc(p, &p->member, C, true)))
+        (s = dalloc(p, &p->member, C, true)) || (s = dalloc(p, &b.cen.wfx, C, true)) ||
+        (s = dalloc(p, &p->cpre, C, true)) || (s = dalloc(p, &p->glist, glist_len(C), true)))
         return s;
     b.cen.cap = C;
     b.cen.count = p->counts + 0;
@@ -405,6 +425,11 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     c.goff_w = p->goff_w;
     c.gcur = p->gcur;
     c.member = p->member;
+    c.cwfx = b.cen.wfx;
+    c.cpre = p->cpre;
+    c.glist = p->glist;
+    glist_offsets(p->cen_cap, c.glist_off);
+    c.glist_n = p->counts + 3;
     c.bx = b.bx;
     c.bmu = b.bmu;
     c.bcell = b.bcell;
@@ -415,7 +440,7 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     c.bS = p->bS;
     launch_comb(c, p->nsm * 8, p->stream);
     HWW_CK(cudaGetLastError());
-    p->kernel_launches += 3;
+    p->kernel_launches += 9;
     return HWW_OK;
 }
 
@@ -768,7 +793,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     const int B = p->B;
     const size_t P2 = (size_t)p->P2;
     const size_t acc_main = sizeof(Acc128) * (6 * (size_t)I + (size_t)B * I + 6) +
-                            sizeof(unsigned long long) * (ST_COUNT + 3);
+                            sizeof(unsigned long long) * (ST_COUNT + 8);
     // derivative accumulators after the main block (16-byte aligned)
     const size_t acc_off = (acc_main + 15) / 16 * 16;
     p->acc_bytes = acc_off + sizeof(Acc128) * (P2 * I + 3 * P2 * I + 6 * P2);

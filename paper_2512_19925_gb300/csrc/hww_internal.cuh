@@ -86,6 +86,7 @@ struct CenQ {
     int32_t* cell;
     uint32_t* id;
     uint64_t* lin;
+    unsigned long long* wfx;  // weight in fixed point at the comb scale 2^Sc
     double* S;  // [P2][cap] scores (derivative runs only)
     unsigned long long* count;
     long long cap;

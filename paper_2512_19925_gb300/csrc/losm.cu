@@ -51,27 +51,90 @@ __global__ void losm_coef_kernel(LosmMat m, const double* dx, const double* sigt
     }
 }
 
-// Thomas factorization of the eliminated matrix (rows 0..I+1); one thread,
-// run once per cross-section set
-__global__ void losm_factor_kernel(LosmMat m, double theta, int bc_l, int bc_r, unsigned* err) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Thomas factorization of the eliminated matrix (rows 0..I+1), run once per
+// cross-section set.  The pivot recurrence den_r = B_r - A_r C_{r-1} / den_{r-1}
+// is a linear-fractional map of den_{r-1}, x -> (B_r x - A_r C_{r-1}) / x, i.e.
+// the 2x2 matrix [[B_r, -A_r C_{r-1}], [1, 0]] acting on x = p/q.  Each thread
+// composes the maps of its chunk of rows (rescaled: only the ratio p/q
+// matters), a block scan composes the chunks, and each thread then runs the
+// exact recurrence over its chunk from the pivot entering it.
+__device__ __forceinline__ void factor_row(const LosmMat& m, int r, double theta, int bc_l, int bc_r, double& A,
+                                           double& B, double& C) {
     const int I = m.I;
+    if (r == 0) {
+        A = 0.0;
+        C = -m.g[0];
+        B = (bc_l == 1) ? m.g[0] : 0.5 + m.g[0];
+    } else if (r == I + 1) {
+        A = -m.g[I];
+        C = 0.0;
+        B = (bc_r == 1) ? m.g[I] : m.g[I] + 0.5;
+    } else {
+        A = -theta * m.g[r - 1];
+        C = -theta * m.g[r];
+        B = m.cB[r - 1] + theta * m.g[r - 1] + theta * m.g[r];
+    }
+}
+
+struct Mob {
+    double a, b, c, d;  // [[a, b], [c, d]]
+};
+
+// g after f (the product g f), rescaled by its largest entry
+__device__ __forceinline__ Mob mob_then(Mob f, Mob g) {
+    Mob h{g.a * f.a + g.b * f.c, g.a * f.b + g.b * f.d, g.c * f.a + g.d * f.c, g.c * f.b + g.d * f.d};
+    const double s = fmax(fmax(fabs(h.a), fabs(h.b)), fmax(fabs(h.c), fabs(h.d)));
+    if (s > 0.0 && isfinite(s)) {
+        const double inv = 1.0 / s;
+        h.a *= inv;
+        h.b *= inv;
+        h.c *= inv;
+        h.d *= inv;
+    }
+    return h;
+}
+
+__global__ void __launch_bounds__(SCAN_T) losm_factor_kernel(LosmMat m, double theta, int bc_l, int bc_r,
+                                                             unsigned* err) {
+    __shared__ Mob sh[SCAN_T];
+    const int n = m.I + 2;
+    const int L = (n + SCAN_T - 1) / SCAN_T;
+    const int r0 = threadIdx.x * L, r1 = min(n, r0 + L);
+    // the chunk's composite map
+    Mob f{1.0, 0.0, 0.0, 1.0};
+    double A, B, C, Cprev = 0.0;
+    if (r0 > 0 && r0 < n) {
+        double A0, B0;
+        factor_row(m, r0 - 1, theta, bc_l, bc_r, A0, B0, Cprev);
+    }
+    for (int r = r0; r < r1; ++r) {
+        factor_row(m, r, theta, bc_l, bc_r, A, B, C);
+        f = mob_then(f, Mob{B, -A * Cprev, 1.0, 0.0});
+        Cprev = C;
+    }
+    // inclusive scan of the chunk maps (Hillis-Steele)
+    sh[threadIdx.x] = f;
+    __syncthreads();
+    for (int o = 1; o < SCAN_T; o <<= 1) {
+        Mob y = f;
+        if ((int)threadIdx.x >= o) y = mob_then(sh[threadIdx.x - o], f);
+        __syncthreads();
+        sh[threadIdx.x] = y;
+        f = y;
+        __syncthreads();
+    }
+    // the pivot entering the chunk: the maps of all earlier chunks applied
+    // to any start (row 0 ignores its predecessor)
     double cprev = 0.0;
-    for (int r = 0; r <= I + 1; ++r) {
-        double A, B, C;
-        if (r == 0) {
-            A = 0.0;
-            C = -m.g[0];
-            B = (bc_l == 1) ? m.g[0] : 0.5 + m.g[0];
-        } else if (r == I + 1) {
-            A = -m.g[I];
-            C = 0.0;
-            B = (bc_r == 1) ? m.g[I] : m.g[I] + 0.5;
-        } else {
-            A = -theta * m.g[r - 1];
-            C = -theta * m.g[r];
-            B = m.cB[r - 1] + theta * m.g[r - 1] + theta * m.g[r];
-        }
+    if (threadIdx.x > 0 && r0 < n) {
+        const Mob e = sh[threadIdx.x - 1];
+        const double p = e.a + e.b, q = e.c + e.d;
+        double A0, B0, Cm;
+        factor_row(m, r0 - 1, theta, bc_l, bc_r, A0, B0, Cm);
+        cprev = Cm * (q / p);
+    }
+    for (int r = r0; r < r1; ++r) {
+        factor_row(m, r, theta, bc_l, bc_r, A, B, C);
         const double den = B - A * cprev;
         if (den == 0.0 || !isfinite(den)) {
             atomicOr(err, ERR_LOSM);
@@ -551,7 +614,7 @@ int small_grid(int n) {
 void launch_losm_setup(const LosmMat& m, const double* dx, const double* sigt, const double* siga, double v,
                        double dt, double theta, int bc_l, int bc_r, unsigned* err, cudaStream_t s) {
     losm_coef_kernel<<<small_grid(m.I + 1), 128, 0, s>>>(m, dx, sigt, siga, v, dt, theta);
-    losm_factor_kernel<<<1, 32, 0, s>>>(m, theta, bc_l, bc_r, err);
+    losm_factor_kernel<<<1, SCAN_T, 0, s>>>(m, theta, bc_l, bc_r, err);
 }
 
 int launch_losm_solve(const LosmMat& m, const LosmRhsIn& in, const LosmWork& w, double* phi, double* J,

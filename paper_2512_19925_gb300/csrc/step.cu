@@ -1,7 +1,8 @@
 // step.cu -- the O(N) stage after tracking:
 //   comb      uniform combing of the census bank back to N (Sec. 5.1):
 //             canonical order by (source id, lineage key) via per-id groups,
-//             exact fixed-point cumulative weights, teeth (k + u) W / N.
+//             exact fixed-point cumulative weights, teeth (k + (2U+1)/2^33) W / N
+//             decided in integers.
 // Built with contraction off so that the comb positions are the single IEEE
 // operations written.
 #include "hww_internal.cuh"
@@ -125,7 +126,22 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
 
 // ---------------------------------------------------------------------------
 // Comb
+//
+// The census particles of one source id form a group (count gcnt[id], start
+// goff[id] in the member list, fixed-point weight offset goff_w[id] from the
+// scan).  Within a group the canonical order is (lineage key, census slot).
+// Census particle j owns the teeth in [C0_j, C0_j + w_j), C0_j = goff_w[id]
+// plus the weights of the group members before it.  Most groups have one
+// member (C0_j = goff_w[id]); the prefix of a larger group is found once per
+// group and stored per member: pairs by one thread, groups of up to 32 by a
+// warp segment of 4 to 32 lanes (a rank count over shuffles), larger ones by
+// a block (bitonic sort and scan in shared memory).  The copies are then
+// written in census order, reading the census bank coalesced.
 // ---------------------------------------------------------------------------
+constexpr int NCLASS = 4;      // group size classes handled by warp segments of 4, 8, 16, 32 lanes
+constexpr int BIG_CAP = 2048;  // members a block sorts in shared memory
+constexpr int BIG_T = 256;
+
 template <class Real>
 __global__ void comb_scatter_kernel(CombArgs<Real> a) {
     const long long m = (long long)*a.ncensus_ptr;
@@ -136,6 +152,189 @@ __global__ void comb_scatter_kernel(CombArgs<Real> a) {
         const unsigned long long slot = a.goff[id] + atomicAdd(&a.gcur[id], 1u);
         a.member[slot] = (uint32_t)j;
     }
+}
+
+__device__ __forceinline__ bool key_less(uint64_t la, uint32_t ja, uint64_t lb, uint32_t jb) {
+    return la < lb || (la == lb && ja < jb);
+}
+
+// size class of a group: 3-4, 5-8, 9-16, 17-32 members -> 0..3, larger -> 4
+__device__ __forceinline__ int size_class(uint32_t g) {
+    return g <= 4 ? 0 : g <= 8 ? 1 : g <= 16 ? 2 : g <= 32 ? 3 : 4;
+}
+
+// one thread per source id: a pair is ordered on the spot; groups of three
+// or more go to the list of their size class
+template <class Real>
+__global__ void comb_groups_kernel(CombArgs<Real> a) {
+    unsigned long long coll = 0;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < a.N;
+         id += (long long)gridDim.x * blockDim.x) {
+        const uint32_t g = a.gcnt[id];
+        if (g < 2) continue;
+        const unsigned long long base = a.goff[id];
+        if (g == 2) {
+            const uint32_t j0 = a.member[base], j1 = a.member[base + 1];
+            const uint64_t l0 = a.clin[j0], l1 = a.clin[j1];
+            const bool first0 = key_less(l0, j0, l1, j1);
+            const unsigned long long C = a.goff_w[id];
+            a.cpre[first0 ? j0 : j1] = C;
+            a.cpre[first0 ? j1 : j0] = C + a.cwfx[first0 ? j0 : j1];
+            if (l0 == l1) ++coll;
+            continue;
+        }
+        // one atomic per class among the converged lanes
+        const int k = size_class(g);
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, k);
+        const unsigned lane = threadIdx.x & 31u;
+        const int leader = __ffs(peers) - 1;
+        unsigned long long b = 0;
+        if ((int)lane == leader) b = atomicAdd(&a.glist_n[k], (unsigned long long)__popc(peers));
+        b = __shfl_sync(peers, b, leader);
+        a.glist[a.glist_off[k] + b + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)id;
+    }
+    if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
+}
+
+// warp segments of S lanes, one group of at most S members per segment:
+// lane i holds member i; its prefix is the weight of the segment's members
+// with a smaller (lineage, slot) key, gathered by S shuffles
+template <class Real, int S>
+__global__ void comb_seg_kernel(CombArgs<Real> a, int k) {
+    const unsigned long long n = a.glist_n[k];
+    const uint32_t* list = a.glist + a.glist_off[k];
+    const int lane = threadIdx.x & 31, seg = lane / S, li = lane % S;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long coll = 0;
+    for (unsigned long long e0 = (unsigned long long)warp * (32 / S); e0 < n;
+         e0 += (unsigned long long)nwarp * (32 / S)) {
+        const unsigned long long e = e0 + seg;
+        uint32_t g = 0;
+        unsigned long long base = 0, C = 0;
+        if (e < n) {
+            const uint32_t id = list[e];
+            g = a.gcnt[id];
+            base = a.goff[id];
+            C = a.goff_w[id];
+        }
+        uint64_t lin = ~0ull;
+        uint32_t jj = 0xFFFFFFFFu;
+        unsigned long long w = 0;
+        if ((uint32_t)li < g) {
+            jj = a.member[base + li];
+            lin = a.clin[jj];
+            w = a.cwfx[jj];
+        }
+        unsigned long long C0 = 0;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const uint64_t lt = __shfl_sync(0xffffffffu, lin, t, S);
+            const uint32_t jt = __shfl_sync(0xffffffffu, jj, t, S);
+            const unsigned long long wt = __shfl_sync(0xffffffffu, w, t, S);
+            if (key_less(lt, jt, lin, jj)) {
+                C0 += wt;
+                if (lt == lin && (uint32_t)t < g && (uint32_t)li < g) ++coll;
+            }
+        }
+        if ((uint32_t)li < g) a.cpre[jj] = C + C0;
+    }
+    if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
+}
+
+// one block per group of more than 32 members: bitonic sort by (lineage,
+// slot) in shared memory and an exclusive scan of the weights; groups beyond
+// BIG_CAP members take the rank count with the block's threads
+template <class Real>
+__global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
+    __shared__ uint64_t s_lin[BIG_CAP];
+    __shared__ uint32_t s_j[BIG_CAP];
+    __shared__ unsigned long long s_part[BIG_T];
+    const unsigned long long nbig = a.glist_n[NCLASS];
+    const uint32_t* list = a.glist + a.glist_off[NCLASS];
+    unsigned long long coll = 0;
+    for (unsigned long long e = blockIdx.x; e < nbig; e += gridDim.x) {
+        const uint32_t id = list[e];
+        const uint32_t g = a.gcnt[id];
+        const unsigned long long base = a.goff[id];
+        const unsigned long long C = a.goff_w[id];
+        if (g > (uint32_t)BIG_CAP) {
+            for (uint32_t t = threadIdx.x; t < g; t += blockDim.x) {
+                const uint32_t jt = a.member[base + t];
+                const uint64_t lt = a.clin[jt];
+                unsigned long long C0 = C;
+                for (uint32_t u = 0; u < g; ++u) {
+                    const uint32_t ju = a.member[base + u];
+                    const uint64_t lu = a.clin[ju];
+                    if (key_less(lu, ju, lt, jt)) {
+                        C0 += a.cwfx[ju];
+                        if (lu == lt) ++coll;
+                    }
+                }
+                a.cpre[jt] = C0;
+            }
+            continue;
+        }
+        int P = 1;
+        while (P < (int)g) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            if (i < (int)g) {
+                const uint32_t jj = a.member[base + i];
+                s_j[i] = jj;
+                s_lin[i] = a.clin[jj];
+            } else {  // padding sorts last
+                s_lin[i] = ~0ull;
+                s_j[i] = 0xFFFFFFFFu;
+            }
+        }
+        __syncthreads();
+        for (int kk = 2; kk <= P; kk <<= 1) {
+            for (int h = kk >> 1; h > 0; h >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    const int l = i ^ h;
+                    if (l > i) {
+                        const bool up = (i & kk) == 0;
+                        if (key_less(s_lin[l], s_j[l], s_lin[i], s_j[i]) == up) {
+                            const uint64_t tl = s_lin[i];
+                            s_lin[i] = s_lin[l];
+                            s_lin[l] = tl;
+                            const uint32_t tj = s_j[i];
+                            s_j[i] = s_j[l];
+                            s_j[l] = tj;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // exclusive scan of the sorted weights: each thread a contiguous run
+        const int per = (P + BIG_T - 1) / BIG_T;
+        const int i0 = threadIdx.x * per, i1 = min((int)g, i0 + per);
+        unsigned long long run = 0;
+        for (int i = i0; i < i1; ++i) run += a.cwfx[s_j[i]];
+        s_part[threadIdx.x] = run;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long acc = 0;
+            for (int t = 0; t < BIG_T; ++t) {
+                const unsigned long long v = s_part[t];
+                s_part[t] = acc;
+                acc += v;
+            }
+        }
+        __syncthreads();
+        unsigned long long C0 = C + s_part[threadIdx.x];
+        for (int i = i0; i < i1; ++i) {
+            // members with an equal lineage before this one (collisions)
+            for (int b = i - 1; b >= 0 && s_lin[b] == s_lin[i]; --b) ++coll;
+            const uint32_t jj = s_j[i];
+            a.cpre[jj] = C0;
+            C0 += a.cwfx[jj];
+        }
+        __syncthreads();
+    }
+    if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
 
 // T_k >= C for tooth k at T_k = (k + (2U+1)/2^33) W / N, decided exactly:
@@ -149,48 +348,48 @@ __device__ __forceinline__ bool tooth_at_or_after(long long k, unsigned long lon
     return (lh > rh) || (lh == rh && ll >= rl);
 }
 
-// least k in [0, N] with T_k >= C: an integer estimate from the top 32 bits
-// of W and C, then exact steps (the estimate is within two of the answer)
+// the scale of the tooth estimate: W reduced to its top 32 bits (shift sh)
+// and R = floor(N 2^32 / W_r), computed once per thread
+struct ToothScale {
+    int sh;
+    unsigned long long R;
+};
+__device__ __forceinline__ ToothScale tooth_scale(unsigned long long W, long long N) {
+    ToothScale t;
+    t.sh = max(0, 64 - __clzll((long long)W) - 32);
+    const unsigned long long Wr = W >> t.sh;
+    t.R = Wr ? (((unsigned long long)N << 32) / Wr) : 0ull;
+    return t;
+}
+
+// least k in [0, N] with T_k >= C: the estimate (C_r R) / 2^32 from the top
+// 32 bits of C and W is within two of the answer; exact steps finish it
 __device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned long long W, long long N,
-                                                 unsigned U) {
-    const int sh = max(0, 64 - __clzll((long long)W) - 32);
-    const unsigned long long Wr = W >> sh, Cr = C >> sh;
-    long long k = Wr ? (long long)((Cr * (unsigned long long)N) / Wr) : 0;
+                                                 unsigned U, const ToothScale& ts) {
+    const unsigned long long Cr = C >> ts.sh;
+    long long k = (long long)((Cr * ts.R) >> 32);
     if (k > N) k = N;
     for (int it = 0; it < 64 && k > 0 && tooth_at_or_after(k - 1, C, W, N, U); ++it) --k;
     for (int it = 0; it < 64 && k < N && !tooth_at_or_after(k, C, W, N, U); ++it) ++k;
     return k;
 }
 
+// census order: each census particle's teeth and its copies
 template <class Real>
 __global__ void comb_write_kernel(CombArgs<Real> a) {
     const long long m = (long long)*a.ncensus_ptr;
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
     const unsigned long long W = a.goff_w[a.N];
-    const double cscale = a.sd->cscale;
     const unsigned U = a.sd->U_comb;
-    unsigned long long coll = 0;
+    const ToothScale ts = tooth_scale(W, a.N);
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
         const uint32_t id = a.cid[j];
-        const uint32_t g = a.gcnt[id];
-        unsigned long long C0 = a.goff_w[id];
-        const unsigned long long wj = (unsigned long long)to_fixed(a.cw[j], cscale);
-        if (g > 1) {
-            const unsigned long long base = a.goff[id];
-            const uint64_t lj = a.clin[j];
-            for (uint32_t t = 0; t < g; ++t) {
-                const uint32_t jj = a.member[base + t];
-                if ((long long)jj == j) continue;
-                const uint64_t lm = a.clin[jj];
-                if (lm < lj || (lm == lj && (long long)jj < j)) {
-                    C0 += (unsigned long long)to_fixed(a.cw[jj], cscale);
-                    if (lm == lj) ++coll;
-                }
-            }
-        }
-        const long long k0 = first_tooth(C0, W, a.N, U);
-        const long long k1 = first_tooth(C0 + wj, W, a.N, U);
+        const unsigned long long C0 = (a.gcnt[id] > 1) ? a.cpre[j] : a.goff_w[id];
+        const unsigned long long wj = a.cwfx[j];
+        const long long k0 = first_tooth(C0, W, a.N, U, ts);
+        const long long k1 = first_tooth(C0 + wj, W, a.N, U, ts);
+        if (k1 <= k0) continue;
         const Real x = a.cx[j];
         const Real mu = a.cmu[j];
         const int32_t cell = a.ccell[j];
@@ -205,7 +404,6 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
             for (long long k = k0; k < k1; ++k) a.bS[(long long)q * a.N + k] = sq;
         }
     }
-    if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
 
 __global__ void comb_finalize_kernel(StepDev* sd, const unsigned long long* goff_w,
@@ -245,6 +443,12 @@ long long group_scan_tiles(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE
 template <class Real>
 void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
     comb_scatter_kernel<Real><<<grid, 256, 0, s>>>(a);
+    comb_groups_kernel<Real><<<grid, 256, 0, s>>>(a);
+    comb_seg_kernel<Real, 4><<<grid, 256, 0, s>>>(a, 0);
+    comb_seg_kernel<Real, 8><<<grid, 256, 0, s>>>(a, 1);
+    comb_seg_kernel<Real, 16><<<grid, 256, 0, s>>>(a, 2);
+    comb_seg_kernel<Real, 32><<<grid, 256, 0, s>>>(a, 3);
+    comb_big_kernel<Real><<<grid, BIG_T, 0, s>>>(a);
     comb_write_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_finalize_kernel<<<1, 1, 0, s>>>(a.sd, a.goff_w, a.ncensus_ptr, a.N, a.cen_cap, a.err);
 }

@@ -36,6 +36,11 @@ struct CombArgs {
     int32_t* bcell;
     unsigned long long* stats;
     unsigned* err;
+    const unsigned long long* cwfx;  // [cen_cap] census weights in fixed point (comb scale)
+    unsigned long long* cpre;        // [cen_cap] prefix C0 of members of multi-member groups
+    uint32_t* glist;                 // ids of groups of 3+ members, by size class (5 lists)
+    long long glist_off[5];          // start of each class's list in glist
+    unsigned long long* glist_n;     // [5] list lengths (cleared with the step's accumulators)
     int P2;            // scores per particle (0: none)
     const double* cS;  // [P2][cen_cap] census scores
     double* bS;        // [P2][N] start-bank scores

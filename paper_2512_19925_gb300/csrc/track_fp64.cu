@@ -292,8 +292,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 a.cen.cell[slot] = q.cell;
                 a.cen.id[slot] = q.id;
                 a.cen.lin[slot] = q.lin;
+                const unsigned long long wfx = (unsigned long long)to_fixed(q.w, cscale);
+                a.cen.wfx[slot] = wfx;
                 atomicAdd(&a.gcnt[q.id], 1u);
-                atomicAdd(&a.gw[q.id], (unsigned long long)to_fixed(q.w, cscale));
+                atomicAdd(&a.gw[q.id], wfx);
             } else {
                 atomicOr(a.err, ERR_CENSUS_OVERFLOW);
             }
