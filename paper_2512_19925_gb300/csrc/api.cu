@@ -397,18 +397,7 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b) {
 }
 
 template <class Real>
-hww_status comb_step(hww_problem* p, Banks<Real>& b) {
-    ScanArgs s{};
-    s.cnt = p->gcnt;
-    s.w = p->gw;
-    s.n = p->N;
-    s.tile_c = p->tile_c;
-    s.tile_w = p->tile_w;
-    s.out_c = p->goff;
-    s.out_w = p->goff_w;
-    launch_group_scan(s, p->stream);
-    HWW_CK(cudaGetLastError());
-    p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
+CombArgs<Real> comb_args(hww_problem* p, Banks<Real>& b) {
     CombArgs<Real> c{};
     c.sd = p->sd;
     c.N = p->N;
@@ -435,12 +424,41 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     c.bcell = b.bcell;
     c.stats = p->stats;
     c.err = p->err;
+    c.I = p->I;
+    c.cent = p->cent;
     c.P2 = p->P2;
     c.cS = b.cen.S;
     c.bS = p->bS;
-    launch_comb(c, p->nsm * 8, p->stream);
+    return c;
+}
+
+// the comb up to the copies, with the census tallies (Eq. ct-mc): group
+// scan, member lists, in-group prefixes, teeth and copies
+template <class Real>
+hww_status comb_step(hww_problem* p, Banks<Real>& b) {
+    ScanArgs s{};
+    s.cnt = p->gcnt;
+    s.w = p->gw;
+    s.n = p->N;
+    s.tile_c = p->tile_c;
+    s.tile_w = p->tile_w;
+    s.out_c = p->goff;
+    s.out_w = p->goff_w;
+    launch_group_scan(s, p->stream);
     HWW_CK(cudaGetLastError());
-    p->kernel_launches += 9;
+    p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
+    launch_comb(comb_args(p, b), p->nsm * 8, p->stream);
+    HWW_CK(cudaGetLastError());
+    p->kernel_launches += 8;
+    return HWW_OK;
+}
+
+// the comb's last kernel: next start-bank size and weight, step-state advance
+template <class Real>
+hww_status comb_finalize(hww_problem* p, Banks<Real>& b) {
+    launch_comb_finalize(comb_args(p, b), p->stream);
+    HWW_CK(cudaGetLastError());
+    ++p->kernel_launches;
     return HWW_OK;
 }
 
@@ -610,9 +628,12 @@ hww_status stage_pre(hww_problem* p) {
     return HWW_OK;
 }
 
-// closures and initial conditions at t^n, the fully implicit HLOSM (Eqs.
-// losm-0, losm-1, losm-disc-bc), the comb and the step-state advance
+// the comb with the census tallies (Eq. ct-mc; the comb does not depend on
+// the closures), closures and initial conditions at t^n, the fully implicit
+// HLOSM (Eqs. losm-0, losm-1, losm-disc-bc), and the step-state advance
 hww_status stage_post(hww_problem* p) {
+    hww_status st = p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);
+    if (st) return st;
     ClosureArgs ca{};
     ca.I = p->I;
     ca.sd = p->sd;
@@ -661,7 +682,7 @@ hww_status stage_post(hww_problem* p) {
     full.full = 1;
     p->kernel_launches += launch_losm_solve(p->mat, full, p->work, p->full_phi, p->full_J, nullptr, p->stream);
     HWW_CK(cudaGetLastError());
-    return p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);
+    return p->fp32 ? comb_finalize(p, p->b32) : comb_finalize(p, p->b64);
 }
 
 double bits_to_double(unsigned long long b) {
@@ -896,13 +917,19 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         return cuda_status(e);
     }
     // tracking launch shape: persistent grid of resident blocks
-    p->track_smem = sizeof(long long) * (7 + P2) * (size_t)I;
+    p->track_smem = sizeof(long long) * (TALLY_ROWS + P2) * (size_t)I;
     if (p->track_smem > 48 * 1024) {
         if ((p->fp32 ? track_smem_optin_fp32(p->track_smem) : track_smem_optin_fp64(p->track_smem, p->P2 > 0)) !=
             0) {
             destroy_problem(p);
             return HWW_ERR_CUDA;
         }
+    }
+    const size_t cen_smem = sizeof(long long) * 3 * (size_t)I;
+    if (cen_smem > 48 * 1024 &&
+        (p->fp32 ? comb_write_smem_optin<float>(cen_smem) : comb_write_smem_optin<double>(cen_smem)) != 0) {
+        destroy_problem(p);
+        return HWW_ERR_CUDA;
     }
     int per_sm = p->fp32 ? track_blocks_per_sm_fp32(TRACK_BLOCK, p->track_smem)
                          : track_blocks_per_sm_fp64(TRACK_BLOCK, p->track_smem, p->P2 > 0);
@@ -1730,7 +1757,7 @@ hww_status create_batch(const hww_problem_desc* descs, int32_t n, void* cuda_str
         b->m.push_back(p);
         Imax = std::max(Imax, p->I);
     }
-    b->smem = sizeof(long long) * 7 * (size_t)Imax;
+    b->smem = sizeof(long long) * TALLY_ROWS * (size_t)Imax;
     if (b->smem > 48 * 1024 && track_batch_smem_optin(b->fp32, b->smem) != 0) {
         destroy_batch(b);
         return HWW_ERR_CUDA;

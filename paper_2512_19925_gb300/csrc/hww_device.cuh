@@ -149,4 +149,37 @@ __host__ __device__ __forceinline__ double pow2(int e) {
     return v.d;
 }
 
+// FP32 path: the tally contribution of an FP32 factor f to a fixed-point
+// weight W.
+// round(W * f) for W >= 0 and an FP32 f, from the exact 128-bit product of W
+// and the mantissa of f (round half up); subnormal f counts as 0
+__device__ __forceinline__ long long fx_mul(long long W, float f) {
+    const unsigned b = __float_as_uint(f);
+    const int ex = (int)((b >> 23) & 0xFFu);
+    if (ex == 0) return 0;
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int s = 150 - ex;  // value = m 2^-s
+    const unsigned long long uw = (unsigned long long)W;
+    const unsigned long long lo = uw * m;
+    const unsigned long long hi = __umul64hi(uw, m);
+    unsigned long long r, rb;
+    if (s <= 0) {
+        r = lo << (-s);
+        rb = 0;
+    } else if (s < 64) {
+        r = (lo >> s) | (hi << (64 - s));
+        rb = (lo >> (s - 1)) & 1ull;
+    } else if (s == 64) {
+        r = hi;
+        rb = lo >> 63;
+    } else if (s < 128) {
+        r = hi >> (s - 64);
+        rb = (hi >> (s - 65)) & 1ull;
+    } else {
+        return 0;
+    }
+    r += rb;
+    return (b >> 31) ? -(long long)r : (long long)r;
+}
+
 }  // namespace hww

@@ -154,6 +154,12 @@ void launch_track_batch_fp64(const TrackArgs<double>* args, const BatchPlan& pla
                              cudaStream_t s);
 void launch_track_batch_fp32(const TrackArgs<float>* args, const BatchPlan& plan, int grid, int block, size_t smem,
                              cudaStream_t s);
+// Rows of the tracking kernels' block-private 64-bit tallies in shared
+// memory, each I long: track-length phi, J, F, then the batch row of the
+// block's current id range; derivative runs append their [2R][I]
+// track-length rows.
+constexpr int TALLY_ROWS = 4;
+
 int track_batch_smem_optin_fp32(size_t smem);
 int track_batch_smem_optin_fp64(size_t smem);
 int track_batch_blocks_per_sm_fp32(int block, size_t smem);

@@ -7,6 +7,7 @@
 // operations written.
 #include "hww_internal.cuh"
 #include "step_kernels.cuh"
+#include "track_common.cuh"
 
 namespace hww {
 namespace {
@@ -374,16 +375,50 @@ __device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned 
     return k;
 }
 
-// census order: each census particle's teeth and its copies
+// census (time-crossing) tally contributions of one census particle, formed
+// exactly as the precision's event loop forms them at a census event:
+// FP64 round(x 2^S) of the FP64 products w, w mu, w (1/3 - mu^2); FP32 the
+// fixed-point weight W = round(w 2^S) and round(W mu), round(W (1/3 - mu^2))
+__device__ __forceinline__ void census_terms(double w, double mu, double tscale, long long& c0, long long& c1,
+                                             long long& c2) {
+    c0 = to_fixed(w, tscale);
+    c1 = to_fixed(w * mu, tscale);
+    c2 = to_fixed(w * (1.0 / 3.0 - mu * mu), tscale);
+}
+__device__ __forceinline__ void census_terms(double w, float mu, double tscale, long long& c0, long long& c1,
+                                             long long& c2) {
+    c0 = to_fixed(w, tscale);
+    c1 = fx_mul(c0, mu);
+    c2 = fx_mul(c0, 1.0f / 3.0f - mu * mu);
+}
+
+// census order: each census particle's census tallies (Eq. ct-mc; block-
+// private in shared memory, warp-aggregated by cell), its teeth and its copies
 template <class Real>
 __global__ void comb_write_kernel(CombArgs<Real> a) {
+    extern __shared__ long long s_cen[];  // 3 I
+    const int I = a.I;
+    for (int i = threadIdx.x; i < 3 * I; i += blockDim.x) s_cen[i] = 0;
+    __syncthreads();
     const long long m = (long long)*a.ncensus_ptr;
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
     const unsigned long long W = a.goff_w[a.N];
     const unsigned U = a.sd->U_comb;
+    const double tscale = a.sd->tscale;
     const ToothScale ts = tooth_scale(W, a.N);
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
+        {
+            const int k = a.ccell[j];
+            long long c0, c1, c2;
+            census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
+            const Agg3 g = warp_agg3(k, c0, c1, c2);
+            if (g.leader) {
+                sadd(&s_cen[k], g.s0);
+                sadd(&s_cen[I + k], g.s1);
+                sadd(&s_cen[2 * I + k], g.s2);
+            }
+        }
         const uint32_t id = a.cid[j];
         const unsigned long long C0 = (a.gcnt[id] > 1) ? a.cpre[j] : a.goff_w[id];
         const unsigned long long wj = a.cwfx[j];
@@ -404,6 +439,9 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
             for (long long k = k0; k < k1; ++k) a.bS[(long long)q * a.N + k] = sq;
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * I; i += blockDim.x)
+        if (s_cen[i] != 0) add128(&a.cent[i], s_cen[i]);
 }
 
 __global__ void comb_finalize_kernel(StepDev* sd, const unsigned long long* goff_w,
@@ -449,12 +487,25 @@ void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
     comb_seg_kernel<Real, 16><<<grid, 256, 0, s>>>(a, 2);
     comb_seg_kernel<Real, 32><<<grid, 256, 0, s>>>(a, 3);
     comb_big_kernel<Real><<<grid, BIG_T, 0, s>>>(a);
-    comb_write_kernel<Real><<<grid, 256, 0, s>>>(a);
+    comb_write_kernel<Real><<<grid, 256, sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
+}
+
+template <class Real>
+void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s) {
     comb_finalize_kernel<<<1, 1, 0, s>>>(a.sd, a.goff_w, a.ncensus_ptr, a.N, a.cen_cap, a.err);
+}
+
+template <class Real>
+int comb_write_smem_optin(size_t smem) {
+    return raise_smem_limit((const void*)comb_write_kernel<Real>, smem);
 }
 
 template void launch_comb<double>(const CombArgs<double>&, int, cudaStream_t);
 template void launch_comb<float>(const CombArgs<float>&, int, cudaStream_t);
+template void launch_comb_finalize<double>(const CombArgs<double>&, cudaStream_t);
+template void launch_comb_finalize<float>(const CombArgs<float>&, cudaStream_t);
+template int comb_write_smem_optin<double>(size_t);
+template int comb_write_smem_optin<float>(size_t);
 
 __global__ void philox_block_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                     uint32_t k1, long long n, uint32_t* out) {

@@ -41,6 +41,8 @@ struct CombArgs {
     uint32_t* glist;                 // ids of groups of 3+ members, by size class (5 lists)
     long long glist_off[5];          // start of each class's list in glist
     unsigned long long* glist_n;     // [5] list lengths (cleared with the step's accumulators)
+    int I;             // cells (census tallies)
+    Acc128* cent;      // census tallies 3 I
     int P2;            // scores per particle (0: none)
     const double* cS;  // [P2][cen_cap] census scores
     double* bS;        // [P2][N] start-bank scores
@@ -48,8 +50,14 @@ struct CombArgs {
 
 void launch_group_scan(const ScanArgs& a, cudaStream_t s);
 long long group_scan_tiles(long long n);
+// the comb up to the copies (group scan excluded), with the census tallies;
+// the finalize step (which advances the step state) runs separately, last
 template <class Real>
 void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s);
+template <class Real>
+void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s);
+template <class Real>
+int comb_write_smem_optin(size_t smem);
 void launch_philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
                          long long n, uint32_t* out, cudaStream_t s);
 

@@ -55,9 +55,21 @@ __device__ __forceinline__ Agg3 warp_agg3(int key, long long v0, long long v1, l
     return Agg3{rank == 0, v0, v1, v2};
 }
 
-// variance batch of a source id: contiguous id ranges, b = floor(id B / N)
-__device__ __forceinline__ int batch_of(uint32_t id, int B, long long N) {
-    return (int)(((unsigned long long)id * (unsigned long long)B) / (unsigned long long)N);
+// variance batch of a source id: contiguous id ranges, b = floor(id B / N),
+// without a division: q = (x m) / 2^64 with m = floor((2^64 - 1) / N) is
+// floor(x / N) or one less (x = id B < 2^37), and one comparison decides
+struct BatchDiv {
+    unsigned long long N, m;
+    int B;
+};
+__device__ __forceinline__ BatchDiv batch_div(int B, long long N) {
+    return BatchDiv{(unsigned long long)N, ~0ull / (unsigned long long)N, B};
+}
+__device__ __forceinline__ int batch_of(uint32_t id, const BatchDiv& d) {
+    const unsigned long long x = (unsigned long long)id * (unsigned long long)d.B;
+    unsigned long long q = __umul64hi(x, d.m);
+    if ((q + 1) * d.N <= x) ++q;
+    return (int)q;
 }
 
 __device__ __forceinline__ void sadd(long long* s, long long v) {
@@ -98,13 +110,15 @@ __device__ __forceinline__ void flush_counters(Counters& c, unsigned long long* 
     }
 }
 
-// block-private tallies (6 I signed 64-bit) into the global 128-bit ones
-__device__ __forceinline__ void flush_tallies(const long long* sm, int I, Acc128* tl, Acc128* cent) {
-    for (int i = threadIdx.x; i < 6 * I; i += blockDim.x) {
+// block-private track-length tallies (3 I signed 64-bit) into the global
+// 128-bit ones
+__device__ __forceinline__ void flush_tallies(const long long* sm, int I, Acc128* tl) {
+    for (int i = threadIdx.x; i < 3 * I; i += blockDim.x) {
         const long long v = sm[i];
-        if (v != 0) add128(i < 3 * I ? &tl[i] : &cent[i - 3 * I], v);
+        if (v != 0) add128(&tl[i], v);
     }
 }
+
 
 // The dynamic shared memory limit is a process-wide attribute of a kernel on
 // a device: it is only ever raised, so that creating a problem with fewer

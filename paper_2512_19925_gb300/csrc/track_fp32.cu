@@ -32,37 +32,6 @@ struct P32 {
     uint32_t e;
 };
 
-// round(W * f) for W >= 0 and an FP32 f, from the exact 128-bit product of W
-// and the mantissa of f (round half up); subnormal f counts as 0
-__device__ __forceinline__ long long fx_mul(long long W, float f) {
-    const unsigned b = __float_as_uint(f);
-    const int ex = (int)((b >> 23) & 0xFFu);
-    if (ex == 0) return 0;
-    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int s = 150 - ex;  // value = m 2^-s
-    const unsigned long long uw = (unsigned long long)W;
-    const unsigned long long lo = uw * m;
-    const unsigned long long hi = __umul64hi(uw, m);
-    unsigned long long r, rb;
-    if (s <= 0) {
-        r = lo << (-s);
-        rb = 0;
-    } else if (s < 64) {
-        r = (lo >> s) | (hi << (64 - s));
-        rb = (lo >> (s - 1)) & 1ull;
-    } else if (s == 64) {
-        r = hi;
-        rb = lo >> 63;
-    } else if (s < 128) {
-        r = hi >> (s - 64);
-        rb = (hi >> (s - 65)) & 1ull;
-    } else {
-        return 0;
-    }
-    r += rb;
-    return (b >> 31) ? -(long long)r : (long long)r;
-}
-
 // positive doubles order like their bit patterns
 __device__ __forceinline__ bool dgt(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
 
@@ -91,8 +60,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                                           Counters& cnt) {
     const int I = a.I;
     long long* s_tl = sm;
-    long long* s_cen = sm + 3 * I;
-    long long* s_bat = sm + 6 * I;  // batch row of the current id range
+    long long* s_bat = sm + 3 * I;  // batch row of the current id range
     const double tscale = a.sd->tscale;
     const double cscale = a.sd->cscale;
     const double wbar = a.sd->wbar;
@@ -100,6 +68,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
     const int birth = a.sd->birth, ww_on = a.sd->ww_on;
     const float tau0 = (float)a.tau0;
     const long long Wbar = to_fixed(wbar, tscale);
+    const BatchDiv bd = batch_div(a.B, a.N);
 
     P32 q;
     P32 base;  // record whose daughters are being expanded
@@ -161,10 +130,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
             } else {
                 break;
             }
-            q.inv_mu = 1.0f / q.mu;
+            q.inv_mu = __frcp_rn(q.mu);  // the correctly rounded 1/mu
             have = true;
             evs = 0;
-            qb = batch_of(q.id, a.B, a.N);
+            qb = batch_of(q.id, bd);
         }
         // ---- one event ----
         if (evs == a.emax) {
@@ -221,14 +190,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
         q.e = q.e + 1;
         ++evs;
         if (ev == 0) {
-            {
-                const Agg3 g = warp_agg3(k, q.W, fx_mul(q.W, q.mu), fx_mul(q.W, f3));
-                if (g.leader) {
-                    sadd(&s_cen[k], g.s0);
-                    sadd(&s_cen[I + k], g.s1);
-                    sadd(&s_cen[2 * I + k], g.s2);
-                }
-            }
+            // census: the bank record (its tallies come from the census pass)
             const unsigned long long slot = warp_reserve(a.cen.count);
             if ((long long)slot < a.cen.cap) {
                 a.cen.x[slot] = q.xo;
@@ -293,7 +255,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
             philox4x32_10(r2, k0, k1);
             have_r2 = true;
             q.mu = 2.0f * u01f(r2[1]) - 1.0f;
-            q.inv_mu = 1.0f / q.mu;
+            q.inv_mu = __frcp_rn(q.mu);
             cnt.v[ST_SCATTERS]++;
         }
         if (ww_on) {
@@ -357,7 +319,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
 __global__ void __launch_bounds__(256, 2) track32_kernel(TrackArgs<float> a) {
     extern __shared__ long long sm[];
     const int I = a.I;
-    for (int i = threadIdx.x; i < 7 * I; i += blockDim.x) sm[i] = 0;
+    for (int i = threadIdx.x; i < TALLY_ROWS * I; i += blockDim.x) sm[i] = 0;
     __syncthreads();
     Counters cnt;
     cnt.zero();
@@ -373,7 +335,8 @@ __global__ void __launch_bounds__(256, 2) track32_kernel(TrackArgs<float> a) {
         item = (long long)blockIdx.x * chunk + threadIdx.x;
         item_end = min(n_use, (long long)(blockIdx.x + 1) * chunk);
         stride = blockDim.x;
-        if ((long long)blockIdx.x * chunk < n_use) b_blk = batch_of((uint32_t)((long long)blockIdx.x * chunk), a.B, a.N);
+        if ((long long)blockIdx.x * chunk < n_use)
+            b_blk = batch_of((uint32_t)((long long)blockIdx.x * chunk), batch_div(a.B, a.N));
     } else {
         item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         item_end = n_use;
@@ -381,10 +344,10 @@ __global__ void __launch_bounds__(256, 2) track32_kernel(TrackArgs<float> a) {
     }
     run_items(a, item, item_end, stride, b_blk, sm, cnt);
     __syncthreads();
-    flush_tallies(sm, I, a.tl, a.cent);
+    flush_tallies(sm, I, a.tl);
     if (b_blk >= 0)
         for (int i = threadIdx.x; i < I; i += blockDim.x)
-            if (sm[6 * I + i] != 0) add128(&a.batch[(long long)b_blk * I + i], sm[6 * I + i]);
+            if (sm[3 * I + i] != 0) add128(&a.batch[(long long)b_blk * I + i], sm[3 * I + i]);
     flush_counters(cnt, a.stats);
 }
 
@@ -420,7 +383,7 @@ __global__ void __launch_bounds__(256, 2) track32_kernel_batch(const TrackArgs<f
         const int p = s_p;
         if (p < 0 || p != cur) {  // a problem switch, or no tile left (also on the first pop)
             if (cur >= 0) {
-                flush_tallies(sm, Ic, A.tl, A.cent);
+                flush_tallies(sm, Ic, A.tl);
                 flush_counters(cnt, A.stats);
                 cnt.zero();
                 __syncthreads();
@@ -430,22 +393,22 @@ __global__ void __launch_bounds__(256, 2) track32_kernel_batch(const TrackArgs<f
             __syncthreads();
             cur = p;
             Ic = A.I;
-            for (int i = threadIdx.x; i < 7 * Ic; i += blockDim.x) sm[i] = 0;
+            for (int i = threadIdx.x; i < TALLY_ROWS * Ic; i += blockDim.x) sm[i] = 0;
             __syncthreads();
         }
         const long long n_in = A.from_bank ? (long long)A.sd->nbank : (long long)*A.rin.count;
         const long long n_use = (!A.from_bank && n_in > A.rin.cap) ? A.rin.cap : n_in;
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
-        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N) : -1;
+        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, batch_div(A.B, A.N)) : -1;
         run_items(A, i0 + threadIdx.x, i1, blockDim.x, b_tile, sm, cnt);
         __syncthreads();
         if (b_tile >= 0)
             for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
-                const long long v = sm[6 * Ic + i];
+                const long long v = sm[3 * Ic + i];
                 if (v != 0) {
                     add128(&A.batch[(long long)b_tile * Ic + i], v);
-                    sm[6 * Ic + i] = 0;
+                    sm[3 * Ic + i] = 0;
                 }
             }
         __syncthreads();

@@ -84,9 +84,8 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                                           Counters& cnt) {
     const int I = a.I;
     long long* s_tl = sm;
-    long long* s_cen = sm + 3 * I;
-    long long* s_bat = sm + 6 * I;  // batch row of the current id range
-    long long* s_dtl = sm + 7 * I;  // derivative runs: [P2][I]
+    long long* s_bat = sm + 3 * I;                // batch row of the current id range
+    long long* s_dtl = sm + TALLY_ROWS * I;       // derivative runs: [P2][I]
     const int R = a.R, P2 = a.P2;
     double S[DERIV ? MAX_SCORES : 1];     // scores of the current track
     double bS[DERIV ? MAX_SCORES : 1];    // scores of the record being expanded
@@ -95,6 +94,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
     const double wbar = a.sd->wbar;
     const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
     const int birth = a.sd->birth, ww_on = a.sd->ww_on;
+    const BatchDiv bd = batch_div(a.B, a.N);
 
     // flattened event loop: a lane whose track ends loads its next one while
     // the other lanes take their next event
@@ -176,7 +176,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             q.inv_mu = 1.0 / q.mu;
             have = true;
             evs = 0;
-            qb = batch_of(q.id, a.B, a.N);
+            qb = batch_of(q.id, bd);
         }
         // ---- one event ----
         if (evs == a.emax) {
@@ -258,17 +258,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
         q.e = q.e + 1;
         ++evs;
         if (ev == 0) {
-            const double wmu = q.w * q.mu;
-            const double wf = q.w * (1.0 / 3.0 - q.mu * q.mu);
-            {
-                const Agg3 g = warp_agg3(k, to_fixed(q.w, tscale), to_fixed(wmu, tscale), to_fixed(wf, tscale));
-                if (g.leader) {
-                    sadd(&s_cen[k], g.s0);
-                    sadd(&s_cen[I + k], g.s1);
-                    sadd(&s_cen[2 * I + k], g.s2);
-                }
-            }
+            // census: the bank record (its tallies come from the census pass;
+            // derivative runs tally their census derivatives here)
             if constexpr (DERIV) {
+                const double wmu = q.w * q.mu;
+                const double wf = q.w * (1.0 / 3.0 - q.mu * q.mu);
 #pragma unroll
                 for (int j = 0; j < MAX_SCORES; ++j) {
                     if (j < P2) {
@@ -424,7 +418,7 @@ template <bool DERIV>
 __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
     extern __shared__ long long sm[];
     const int I = a.I;
-    const int rows = DERIV ? 7 + a.P2 : 7;
+    const int rows = DERIV ? TALLY_ROWS + a.P2 : TALLY_ROWS;
     for (int i = threadIdx.x; i < rows * I; i += blockDim.x) sm[i] = 0;
     __syncthreads();
     Counters cnt;
@@ -441,7 +435,8 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
         item = (long long)blockIdx.x * chunk + threadIdx.x;
         item_end = min(n_use, (long long)(blockIdx.x + 1) * chunk);
         stride = blockDim.x;
-        if ((long long)blockIdx.x * chunk < n_use) b_blk = batch_of((uint32_t)((long long)blockIdx.x * chunk), a.B, a.N);
+        if ((long long)blockIdx.x * chunk < n_use)
+            b_blk = batch_of((uint32_t)((long long)blockIdx.x * chunk), batch_div(a.B, a.N));
     } else {
         item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         item_end = n_use;
@@ -449,14 +444,14 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
     }
     run_items<DERIV>(a, item, item_end, stride, b_blk, sm, cnt);
     __syncthreads();
-    flush_tallies(sm, I, a.tl, a.cent);
+    flush_tallies(sm, I, a.tl);
     if constexpr (DERIV) {
         for (int i = threadIdx.x; i < a.P2 * I; i += blockDim.x)
-            if (sm[7 * I + i] != 0) add128(&a.dtl[i], sm[7 * I + i]);
+            if (sm[TALLY_ROWS * I + i] != 0) add128(&a.dtl[i], sm[TALLY_ROWS * I + i]);
     }
     if (b_blk >= 0)
         for (int i = threadIdx.x; i < I; i += blockDim.x)
-            if (sm[6 * I + i] != 0) add128(&a.batch[(long long)b_blk * I + i], sm[6 * I + i]);
+            if (sm[3 * I + i] != 0) add128(&a.batch[(long long)b_blk * I + i], sm[3 * I + i]);
     flush_counters(cnt, a.stats);
 }
 
@@ -492,7 +487,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<d
         const int p = s_p;
         if (p < 0 || p != cur) {  // a problem switch, or no tile left (also on the first pop)
             if (cur >= 0) {
-                flush_tallies(sm, Ic, A.tl, A.cent);
+                flush_tallies(sm, Ic, A.tl);
                 flush_counters(cnt, A.stats);
                 cnt.zero();
                 __syncthreads();
@@ -502,22 +497,22 @@ __global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<d
             __syncthreads();
             cur = p;
             Ic = A.I;
-            for (int i = threadIdx.x; i < 7 * Ic; i += blockDim.x) sm[i] = 0;
+            for (int i = threadIdx.x; i < TALLY_ROWS * Ic; i += blockDim.x) sm[i] = 0;
             __syncthreads();
         }
         const long long n_in = A.from_bank ? (long long)A.sd->nbank : (long long)*A.rin.count;
         const long long n_use = (!A.from_bank && n_in > A.rin.cap) ? A.rin.cap : n_in;
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
-        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N) : -1;
+        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, batch_div(A.B, A.N)) : -1;
         run_items<false>(A, i0 + threadIdx.x, i1, blockDim.x, b_tile, sm, cnt);
         __syncthreads();
         if (b_tile >= 0)
             for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
-                const long long v = sm[6 * Ic + i];
+                const long long v = sm[3 * Ic + i];
                 if (v != 0) {
                     add128(&A.batch[(long long)b_tile * Ic + i], v);
-                    sm[6 * Ic + i] = 0;
+                    sm[3 * Ic + i] = 0;
                 }
             }
         __syncthreads();
