@@ -23,6 +23,21 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
     return base + (unsigned long long)__popc(mask & ((1u << lane) - 1u));
 }
 
+// n consecutive slots per calling lane: lanes asking for the same n share
+// one atomic (a split of up to 8 daughters asks for one record, so nearly
+// all splitting lanes of a warp do); the counter is global and hot, so
+// fewer atomics on it matter more than the match.
+__device__ __forceinline__ unsigned long long warp_reserve_n(unsigned long long* cnt, unsigned n) {
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, n);
+    const int leader = __ffs(peers) - 1;
+    const unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(cnt, (unsigned long long)n * (unsigned long long)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + (unsigned long long)n * (unsigned long long)__popc(peers & ((1u << lane) - 1u));
+}
+
 // Warp aggregation of three 64-bit contributions per lane by an integer key:
 // lanes with equal keys are combined by a binomial tree over their ranks in
 // the key group (shuffles among the converged lanes), and the lowest lane of

@@ -180,7 +180,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
         }
         // ---- one event ----
         if (evs == a.emax) {
-            push_record<DERIV>(a, q, S, q.w, q.e, 0u, 0u, atomicAdd(a.rout.count, 1ull));
+            push_record<DERIV>(a, q, S, q.w, q.e, 0u, 0u, warp_reserve(a.rout.count));
             have = false;
             continue;
         }
@@ -376,7 +376,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 cnt.v[ST_SPLIT_EVENTS]++;
                 cnt.v[ST_DAUGHTERS] += nd - 1;
                 const uint32_t nch = (nd - 1 + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
-                const unsigned long long b0 = atomicAdd(a.rout.count, (unsigned long long)nch);
+                const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
                 for (uint32_t ch = 0; ch < nch; ++ch) {
                     const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
                     const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
