@@ -48,7 +48,7 @@ CENSUS_BYTES = {"fp32": 32, "fp64": 40}
 # particle, measured by ncu on the 4e6-particle case of this workload
 # (profiles/track32_kernel_plain_at_scale_fp32.txt; traffic grows with the
 # particle count).  Set to None whenever track32_kernel changes.
-TRACK32_DRAM_BYTES_PER_START = 237.8e6 / 4e6
+TRACK32_DRAM_BYTES_PER_START = 269.1e6 / 4e6
 
 
 def dist_env():
@@ -387,7 +387,7 @@ def main(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "traffic_note": "DRAM bytes of the wave-0 launch per step, scaled by particles from the 4e6 capture",
-            "limiter": "issue/latency (ncu: 31% issue active, 42% long-scoreboard stalls, 2.4% DRAM)",
+            "limiter": "issue/latency (ncu: 30% issue active, 44% long-scoreboard stalls, 3.5% DRAM)",
             "peak_source": peak_kind, "kernel": "track32_kernel",
             "launches": cnt["track_launches"], "kernel_ms_per_step": track_ms / args.steps,
             "algorithmic_bytes_per_step": bytes_alg / args.steps}
