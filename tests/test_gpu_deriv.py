@@ -123,3 +123,75 @@ def test_autograd_step_sums_the_vjps():
         want += o.get_deriv_tallies(0) @ a + o.losm_vjp(b, c)
     loss.backward()
     np.testing.assert_allclose(theta.grad.cpu().numpy(), want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
+
+
+def _shield_run(theta, seed, N, nsteps, deriv):
+    """The three-region shield with region parameters theta = (Sigma_t x3, c x3);
+    returns, after nsteps, the track-length flux integral, the HLOSM flux
+    integral and (with deriv) their derivatives from the library."""
+    wl = workloads.shield(particles_per_step=N, seed=seed, precision="fp64", n_cells=800)
+    reg = wl["region"]
+    p = hww.Problem(wl["edges"], wl["v"], wl["dt"], wl["bc_left"], wl["bc_right"], wl["src_x"], N, seed,
+                    precision=hww.FP64, theta=0.5, n_var_batches=16, deriv_regions=3 if deriv else 0)
+    p.set_cross_sections(np.asarray(theta[:3])[reg], np.asarray(theta[3:])[reg], reg)
+    p.set_ww_params(wl["rho"], wl["eps_min"], hww.MODE_HWW)
+    dx = np.diff(wl["edges"])
+    for _ in range(nsteps):
+        p.run_step()
+    q_mc = p.get_tallies(hww.TL_PHI) @ dx
+    phi, _ = p.get_losm_solution(hww.LOSM_FULL)
+    q_h = phi[1:-1] @ dx
+    d = None
+    if deriv:
+        g_phi = np.concatenate([[0.0], dx, [0.0]])
+        d = (p.losm_vjp(dx, None, None), p.losm_vjp(None, g_phi, None))
+    p.close()
+    return q_mc, q_h, d
+
+
+THETA0 = np.array([1.0, 5.0, 0.5, 0.99, 0.5, 0.9])
+
+
+def test_lr_derivative_matches_closed_form():
+    # By t = 0.6 the pulse has not left the first region, a reflecting
+    # half-space with Sigma_t = 1, c = 0.99: the step's track-length integral
+    # is the infinite-medium closed form, and the two unreached regions have
+    # derivative zero exactly.
+    from oracle import analytic
+
+    K, N = 4, 1_000_000
+    d = np.array([_shield_run(THETA0, s + 1, N, 6, True)[2][0] for s in range(K)])
+    mean, se = d.mean(0), d.std(0, ddof=1) / np.sqrt(K)
+    t0, t1 = 0.5, 0.6
+    want_s = (analytic.tl_sum(t0, t1, 1 + 1e-6, 0.99) - analytic.tl_sum(t0, t1, 1 - 1e-6, 0.99)) / 2e-6
+    want_c = (analytic.tl_sum(t0, t1, 1.0, 0.99 + 1e-6) - analytic.tl_sum(t0, t1, 1.0, 0.99 - 1e-6)) / 2e-6
+    assert abs(mean[0] - want_s) < 4.5 * se[0] + 1e-9, (mean[0], se[0], want_s)
+    assert abs(mean[3] - want_c) < 4.5 * se[3] + 1e-9, (mean[3], se[3], want_c)
+    assert np.all(d[:, [1, 2, 4, 5]] == 0.0)
+
+
+def test_correlated_central_differences_agree():
+    # Central differences of the same runs (same seeds) at theta (1 +- h) for
+    # the first region's parameters.  Event-order flips decorrelate a few
+    # histories per run, so the difference quotient is noisy (its error grows
+    # like 1/sqrt(N h)); h = 1e-3 resolves the c derivative.
+    K, N, h = 6, 1_000_000, 1e-3
+    lr, fd = [], []
+    for s in range(K):
+        _, _, (dmc, dh) = _shield_run(THETA0, s + 1, N, 6, True)
+        row = []
+        for j in (0, 3):
+            tp, tm = THETA0.copy(), THETA0.copy()
+            tp[j] *= 1 + h
+            tm[j] *= 1 - h
+            qp, qm = _shield_run(tp, s + 1, N, 6, False), _shield_run(tm, s + 1, N, 6, False)
+            row += [(qp[0] - qm[0]) / (2 * h * THETA0[j]), (qp[1] - qm[1]) / (2 * h * THETA0[j])]
+        lr.append([dmc[0], dh[0], dmc[3], dh[3]])
+        fd.append(row)
+    lr, fd = np.array(lr), np.array(fd)
+    ml, sl = lr.mean(0), lr.std(0, ddof=1) / np.sqrt(K)
+    mf, sf = fd.mean(0), fd.std(0, ddof=1) / np.sqrt(K)
+    z = np.abs(ml - mf) / np.sqrt(sl ** 2 + sf ** 2)
+    assert z.max() < 4.0, (ml, mf, sf)
+    # the c derivatives are resolved (the comparison is not vacuous)
+    assert mf[2] > 3 * sf[2] and mf[3] > 3 * sf[3]
