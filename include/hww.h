@@ -142,6 +142,18 @@ hww_status set_ww_params(hww_problem* p, double rho, double eps_min, int32_t mod
  * from identical windows. */
 hww_status set_ww_centers(hww_problem* p, const double* centers);
 
+/* In-step window updates (Sec. 3, Eq. Hpn): during a step whose windows
+ * come from the HLOSM solution (HWW mode, no set_ww_centers override), the
+ * start bank is tracked in n + 1 chunks of source ids [H_{p-1}, H_p),
+ * H_p = floor(f_p H) of the step's H start particles; after each of the
+ * first n chunks (all their descendants tracked) the windows are re-derived
+ * from the fully implicit HLOSM solution closed with the census and boundary
+ * tallies of the histories so far (normalised per history).  n <= 16;
+ * fractions strictly increasing in (0, 1), NULL for f_p = p / (n + 1);
+ * n = 0 turns the updates off (HWW_ERR_ARG for invalid fractions).  Not
+ * supported for batch members (run_batch_step returns HWW_ERR_STATE). */
+hww_status set_ww_updates(hww_problem* p, int32_t n, const double* fractions);
+
 /* Advance the problem by one time step (steps 1-4 above).  Asynchronous on
  * the problem's stream unless `stats` is non-NULL, in which case the stream
  * is synchronized and the counts of the step are returned.  A bank overflow

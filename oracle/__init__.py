@@ -97,6 +97,7 @@ def lib():
             L.or_get_census.argtypes = [C.c_void_p, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
                                         C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_int64)]
             L.or_set_regions.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+            L.or_set_ww_updates.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]
             L.or_get_deriv_tallies.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int64]
             L.or_losm_vjp.argtypes = [C.c_void_p, dp, dp, dp]
             L.or_set_bank_scores.argtypes = [C.c_void_p, dp]
@@ -269,6 +270,13 @@ class Problem:
         c = _f64(centers, self.I)
         _check(lib().or_set_ww_centers(self._h, _dp(c)), "set_ww_centers")
 
+    def set_ww_updates(self, n, fractions=None):
+        """In-step window updates: n updates after the history fractions
+        (default p/(n+1))."""
+        f = _f64(fractions, int(n)) if fractions is not None else None
+        _check(lib().or_set_ww_updates(self._h, int(n), _dp(f) if f is not None else C.POINTER(C.c_double)()),
+               "set_ww_updates")
+
     def run_step(self):
         st = _Stats()
         rc = lib().or_run_step(self._h, C.byref(st))
@@ -374,4 +382,6 @@ def problem_from_workload(wl, particles_per_step=None, seed=None, deriv=False):
         p.set_regions(wl.get("region", np.zeros(p.I, np.int32)))
     p.set_ww_params(wl["rho"], wl["eps_min"], wl.get("mode", MODE_HWW),
                     wl.get("center_scaling", SCALE_MEAN_WEIGHT))
+    if wl.get("ww_updates"):
+        p.set_ww_updates(wl["ww_updates"], wl.get("ww_fractions"))
     return p

@@ -46,6 +46,7 @@
 enum { OR_VACUUM = 0, OR_REFLECT = 1 };
 enum { OR_MODE_HWW = 0, OR_MODE_ANALOG = 1, OR_MODE_LWW = 2 };
 enum { OR_SCALE_MEAN_WEIGHT = 0, OR_SCALE_LITERAL = 1 };
+#define OR_MAX_UPDATES 16
 enum {
     K_TL_PHI = 0, K_TL_J, K_TL_F, K_CEN_PHI, K_CEN_J, K_CEN_F, K_BATCH_PHI, K_BOUNDARY,
     K_WW_CENTER, K_CLOSURE_PHI, K_CLOSURE_J, K_CLOSURE_F
@@ -180,6 +181,8 @@ struct or_problem {
     int xs_set, ww_set;
     double rho, eps;
     int32_t mode, scaling;
+    int32_t n_updates;                 /* in-step window updates u_ww (Sec. 3, Eq. Hpn) */
+    double ww_frac[OR_MAX_UPDATES];    /* their history fractions f_p */
     int64_t N;           /* particles per step = source particles */
     int64_t n;           /* completed steps */
     /* combed bank for the next step (x, mu, cell); weight w_bar each */
@@ -341,6 +344,18 @@ int or_set_cross_sections(or_problem* p, const double* sigma_t, const double* c)
         p->inv_c[i] = (c[i] > 0.0) ? 1.0 / c[i] : 0.0;
     }
     p->xs_set = 1;
+    return 0;
+}
+
+int or_set_ww_updates(or_problem* p, int32_t n, const double* fractions) {
+    if (!p || n < 0 || n > OR_MAX_UPDATES) return E_ARG;
+    for (int32_t k = 0; k < n; ++k) {
+        /* default f_p = p / (u + 1) (the fractions the paper uses) */
+        const double f = fractions ? fractions[k] : (double)(k + 1) / (double)(n + 1);
+        if (!(f > 0.0 && f < 1.0) || (k > 0 && !(f > p->ww_frac[k - 1]))) return E_ARG;
+        p->ww_frac[k] = f;
+    }
+    p->n_updates = n;
     return 0;
 }
 
@@ -779,6 +794,41 @@ static int32_t birth_cell(const or_problem* p, double x, double mu) {
     return I - 1;
 }
 
+/* windows of an in-step update: closures from the census and boundary
+ * tallies of the histories so far (normalised by their number Hp), the fully
+ * implicit HLOSM solution with them as the new level, centers from it */
+static int update_windows(or_problem* p, int64_t Hp, const double* phi_old, const double* J_old,
+                          const double* F_old, int S) {
+    const int32_t I = p->I;
+    const double v = p->d.v;
+    double* cphi = xcalloc(I, sizeof(double));
+    double* cJ = xcalloc(I, sizeof(double));
+    double* cF = xcalloc(I, sizeof(double));
+    double* tphi = xcalloc(I + 2, sizeof(double));
+    double* tJ = xcalloc(I + 1, sizeof(double));
+    double* tF = xcalloc(I + 2, sizeof(double));
+    double* uphi = xcalloc(I + 2, sizeof(double));
+    double* uJ = xcalloc(I + 1, sizeof(double));
+    int rc = E_OOM;
+    if (cphi && cJ && cF && tphi && tJ && tF && uphi && uJ) {
+        for (int32_t i = 0; i < I; ++i) {
+            const double den = (double)Hp * p->dx[i];
+            cphi[i] = (v * ldexp(conv128(p->cen_w[i]), -S)) / den;
+            cJ[i] = (v * ldexp(conv128(p->cen_wmu[i]), -S)) / den;
+            cF[i] = (v * ldexp(conv128(p->cen_wf[i]), -S)) / den;
+        }
+        const double PL = ldexp(conv128(p->bnd[2]), -S) / ((double)Hp * p->d.dt);
+        const double PR = ldexp(conv128(p->bnd[5]), -S) / ((double)Hp * p->d.dt);
+        double tPL = 0.0, tPR = 0.0;
+        build_closure_set(p, cphi, cJ, cF, PL, PR, tphi, tJ, tF, &tPL, &tPR);
+        rc = or_losm_solve(I, p->dx, p->sigt, p->siga, v, p->d.dt, p->d.theta, p->d.bc_left, p->d.bc_right,
+                           phi_old, J_old, F_old, tF, tPL, tPR, NULL, NULL, uphi, uJ);
+        if (rc == 0) ww_from_flux(p, uphi + 1);
+    }
+    free(cphi); free(cJ); free(cF); free(tphi); free(tJ); free(tF); free(uphi); free(uJ);
+    return rc;
+}
+
 int or_run_step(or_problem* p, or_stats* st) {
     if (!p) return E_ARG;
     if (!p->xs_set || !p->ww_set) return E_STATE;
@@ -829,6 +879,7 @@ int or_run_step(or_problem* p, or_stats* st) {
 
     /* 3. weight windows */
     int ww_on = 0;
+    const int override_step = p->has_override;
     if (p->has_override) {
         for (int32_t i = 0; i < I; ++i) {
             double ctr = quantize_center(p->ww_override[i]);
@@ -870,187 +921,203 @@ int or_run_step(or_problem* p, or_stats* st) {
     p->bank_loaded = 0;
     int64_t nstart = birth ? N : p->nbank;
     s.n_start = nstart;
-    for (int64_t k = nstart - 1; k >= 0; --k) {
-        or_particle q;
-        q.id = (uint32_t)k;
-        q.lin = 0;
-        for (int j = 0; j < MAX_DERIV; ++j) q.S[j] = 0.0;
-        q.e = 0;
-        q.tau = tau0;
-        q.w = p->wbar;
-        if (birth) {
-            uint32_t ctr[4] = {(uint32_t)k, 0u, 0u, 0xFFFFFFFFu}, r[4];
-            or_philox4x32_10(ctr, key, r);
-            q.mu = 2.0 * or_u01(r[0], r[1]) - 1.0;
-            q.x = p->d.src_x;
-            if (q.x <= p->edges[0] && q.mu < 0.0 && p->d.bc_left == OR_REFLECT) q.mu = -q.mu;
-            if (q.x >= p->edges[I] && q.mu > 0.0 && p->d.bc_right == OR_REFLECT) q.mu = -q.mu;
-            q.cell = birth_cell(p, q.x, q.mu);
-        } else {
-            q.x = p->bx[k];
-            q.mu = p->bmu[k];
-            q.cell = p->bcell[k];
-            if (R > 0 && p->bS)
-                for (int j = 0; j < P2; ++j) q.S[j] = p->bS[k * P2 + j];
+    /* In-step window updates (Sec. 3, Eq. Hpn): the start bank is tracked in
+     * u_ww + 1 chunks of source ids, [H_{p-1}, H_p) with H_p = floor(f_p H);
+     * after each of the first u_ww chunks (all their descendants done) the
+     * windows are re-derived from the fully implicit HLOSM solution whose
+     * new-level closures come from the histories so far, normalised per
+     * history (H_p).  Only HLOSM windows are updated (not an override, not
+     * the lagged or analog modes). */
+    const int nupd = (ww_on && p->mode == OR_MODE_HWW && !override_step) ? p->n_updates : 0;
+    for (int chunk = 0; chunk <= nupd; ++chunk) {
+        const int64_t lo = (chunk == 0) ? 0 : (int64_t)(p->ww_frac[chunk - 1] * (double)nstart);
+        const int64_t hi = (chunk == nupd) ? nstart : (int64_t)(p->ww_frac[chunk] * (double)nstart);
+        for (int64_t k = hi - 1; k >= lo; --k) {
+            or_particle q;
+            q.id = (uint32_t)k;
+            q.lin = 0;
+            for (int j = 0; j < MAX_DERIV; ++j) q.S[j] = 0.0;
+            q.e = 0;
+            q.tau = tau0;
+            q.w = p->wbar;
+            if (birth) {
+                uint32_t ctr[4] = {(uint32_t)k, 0u, 0u, 0xFFFFFFFFu}, r[4];
+                or_philox4x32_10(ctr, key, r);
+                q.mu = 2.0 * or_u01(r[0], r[1]) - 1.0;
+                q.x = p->d.src_x;
+                if (q.x <= p->edges[0] && q.mu < 0.0 && p->d.bc_left == OR_REFLECT) q.mu = -q.mu;
+                if (q.x >= p->edges[I] && q.mu > 0.0 && p->d.bc_right == OR_REFLECT) q.mu = -q.mu;
+                q.cell = birth_cell(p, q.x, q.mu);
+            } else {
+                q.x = p->bx[k];
+                q.mu = p->bmu[k];
+                q.cell = p->bcell[k];
+                if (R > 0 && p->bS)
+                    for (int j = 0; j < P2; ++j) q.S[j] = p->bS[k * P2 + j];
+            }
+            if (ps_push(&stack, &q)) { rc = E_OOM; goto fail_track; }
         }
-        if (ps_push(&stack, &q)) { rc = E_OOM; goto fail_track; }
-    }
 
-    while (stack.n > 0) {
-        or_particle q = stack.v[--stack.n];
-        for (;;) {
-            if (q.e >= MAX_EVENTS_PER_TRACK) { s.error = E_NUMERIC; break; }
-            uint32_t r[4];
-            philox_event(&q, 2u * q.e, key, r);
-            const double uf = or_u01(r[0], r[1]);
-            const double uc = or_u01(r[2], r[3]);
-            const int32_t k = q.cell;
-            const double inv_mu = 1.0 / q.mu;
-            const double dcoll = (-or_log(uf)) * p->inv_sigt[k];
-            const double xe = (q.mu > 0.0) ? p->edges[k + 1] : p->edges[k];
-            const double dedge = (xe - q.x) * inv_mu;
-            const double dcens = q.tau;
-            int ev; /* 0 census, 1 crossing, 2 collision */
-            double l;
-            if (dcens <= dedge && dcens <= dcoll) { ev = 0; l = dcens; }
-            else if (dedge <= dcoll) { ev = 1; l = dedge; }
-            else { ev = 2; l = dcoll; }
-            /* track-length tallies, Eq. (phi-mc) */
-            const double wl = q.w * l;
-            const double wlmu = wl * q.mu;
-            const double wlf = wl * (1.0 / 3.0 - q.mu * q.mu);
-            p->tl_phi[k] += to_fixed(wl, S);
-            p->tl_j[k] += to_fixed(wlmu, S);
-            p->tl_f[k] += to_fixed(wlf, S);
-            p->batch[(int64_t)(((uint64_t)q.id * (uint64_t)B) / (uint64_t)N) * I + k] += to_fixed(wl, S);
-            if (R > 0) {
-                /* likelihood-ratio scores: the flight of length l in region r
-                 * contributes -l to the Sigma_t score, a collision 1/Sigma_t;
-                 * the derivative tally of this segment is w l S */
-                const int r = p->region[k];
-                q.S[r] = q.S[r] - l;
-                if (ev == 2) q.S[r] = q.S[r] + p->inv_sigt[k];
-                for (int j = 0; j < P2; ++j) p->dtl[(int64_t)j * I + k] += to_fixed(wl * q.S[j], S);
-            }
-            s.segments++;
-            /* move */
-            if (ev == 1) {
-                q.x = xe;
-            } else {
-                double xn = q.x + q.mu * l;
-                if (xn < p->edges[k]) xn = p->edges[k];
-                if (xn > p->edges[k + 1]) xn = p->edges[k + 1];
-                q.x = xn;
-            }
-            q.tau = (ev == 0) ? 0.0 : q.tau - l;
-            const uint32_t e_ev = q.e;
-            q.e = q.e + 1;
-            if (ev == 0) {
-                /* census: time-crossing tallies, Eq. (ct-mc) */
-                const double wmu = q.w * q.mu;
-                const double wf = q.w * (1.0 / 3.0 - q.mu * q.mu);
-                p->cen_w[k] += to_fixed(q.w, S);
-                p->cen_wmu[k] += to_fixed(wmu, S);
-                p->cen_wf[k] += to_fixed(wf, S);
-                for (int j = 0; j < P2; ++j) {
-                    p->dcen[((int64_t)0 * P2 + j) * I + k] += to_fixed(q.w * q.S[j], S);
-                    p->dcen[((int64_t)1 * P2 + j) * I + k] += to_fixed(wmu * q.S[j], S);
-                    p->dcen[((int64_t)2 * P2 + j) * I + k] += to_fixed(wf * q.S[j], S);
+        while (stack.n > 0) {
+            or_particle q = stack.v[--stack.n];
+            for (;;) {
+                if (q.e >= MAX_EVENTS_PER_TRACK) { s.error = E_NUMERIC; break; }
+                uint32_t r[4];
+                philox_event(&q, 2u * q.e, key, r);
+                const double uf = or_u01(r[0], r[1]);
+                const double uc = or_u01(r[2], r[3]);
+                const int32_t k = q.cell;
+                const double inv_mu = 1.0 / q.mu;
+                const double dcoll = (-or_log(uf)) * p->inv_sigt[k];
+                const double xe = (q.mu > 0.0) ? p->edges[k + 1] : p->edges[k];
+                const double dedge = (xe - q.x) * inv_mu;
+                const double dcens = q.tau;
+                int ev; /* 0 census, 1 crossing, 2 collision */
+                double l;
+                if (dcens <= dedge && dcens <= dcoll) { ev = 0; l = dcens; }
+                else if (dedge <= dcoll) { ev = 1; l = dedge; }
+                else { ev = 2; l = dcoll; }
+                /* track-length tallies, Eq. (phi-mc) */
+                const double wl = q.w * l;
+                const double wlmu = wl * q.mu;
+                const double wlf = wl * (1.0 / 3.0 - q.mu * q.mu);
+                p->tl_phi[k] += to_fixed(wl, S);
+                p->tl_j[k] += to_fixed(wlmu, S);
+                p->tl_f[k] += to_fixed(wlf, S);
+                p->batch[(int64_t)(((uint64_t)q.id * (uint64_t)B) / (uint64_t)N) * I + k] += to_fixed(wl, S);
+                if (R > 0) {
+                    /* likelihood-ratio scores: the flight of length l in region r
+                     * contributes -l to the Sigma_t score, a collision 1/Sigma_t;
+                     * the derivative tally of this segment is w l S */
+                    const int r = p->region[k];
+                    q.S[r] = q.S[r] - l;
+                    if (ev == 2) q.S[r] = q.S[r] + p->inv_sigt[k];
+                    for (int j = 0; j < P2; ++j) p->dtl[(int64_t)j * I + k] += to_fixed(wl * q.S[j], S);
                 }
-                or_census cq;
-                cq.x = q.x;
-                cq.mu = q.mu;
-                cq.w = q.w;
-                cq.cell = q.cell;
-                cq.id = q.id;
-                cq.lin = q.lin;
-                memcpy(cq.S, q.S, sizeof cq.S);
-                if (cb_push(&census, &cq)) { rc = E_OOM; goto fail_track; }
-                s.census++;
-                if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
-                break;
-            }
-            int need_ww = 0;
-            int have_r2 = 0;
-            uint32_t r2[4];
-            if (ev == 1) {
-                s.crossings++;
-                const int32_t nk = (q.mu > 0.0) ? k + 1 : k - 1;
-                if (nk < 0 || nk >= I) {
-                    const int side = (nk < 0) ? 0 : 1;
-                    const int32_t bc = side ? p->d.bc_right : p->d.bc_left;
-                    const double amu = fabs(q.mu);
-                    const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
-                    if (bc == OR_VACUUM) {
-                        /* surface estimators for the boundary closures:
-                         * phi_b ~ w/|mu|, F_b ~ w(1/3-mu^2)/|mu|, P_b ~ w(1/2-|mu|)/|mu| */
-                        const double wi = q.w * ia;
-                        p->bnd[3 * side + 0] += to_fixed(wi, S);
-                        p->bnd[3 * side + 1] += to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu), S);
-                        p->bnd[3 * side + 2] += to_fixed(wi * (0.5 - amu), S);
-                        for (int j = 0; j < P2; ++j) {
-                            p->dbnd[6 * j + 3 * side + 0] += to_fixed(wi * q.S[j], S);
-                            p->dbnd[6 * j + 3 * side + 1] += to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu) * q.S[j], S);
-                            p->dbnd[6 * j + 3 * side + 2] += to_fixed(wi * (0.5 - amu) * q.S[j], S);
-                        }
-                        s.leaked++;
-                        if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
-                        break;
-                    }
-                    q.mu = -q.mu; /* specular reflection, stays in cell k */
-                    s.reflections++;
+                s.segments++;
+                /* move */
+                if (ev == 1) {
+                    q.x = xe;
                 } else {
-                    q.cell = nk;
+                    double xn = q.x + q.mu * l;
+                    if (xn < p->edges[k]) xn = p->edges[k];
+                    if (xn > p->edges[k + 1]) xn = p->edges[k + 1];
+                    q.x = xn;
                 }
-                need_ww = 1;
-            } else {
-                s.collisions++;
-                if (uc >= p->c[k]) {
-                    s.absorbed++;
+                q.tau = (ev == 0) ? 0.0 : q.tau - l;
+                const uint32_t e_ev = q.e;
+                q.e = q.e + 1;
+                if (ev == 0) {
+                    /* census: time-crossing tallies, Eq. (ct-mc) */
+                    const double wmu = q.w * q.mu;
+                    const double wf = q.w * (1.0 / 3.0 - q.mu * q.mu);
+                    p->cen_w[k] += to_fixed(q.w, S);
+                    p->cen_wmu[k] += to_fixed(wmu, S);
+                    p->cen_wf[k] += to_fixed(wf, S);
+                    for (int j = 0; j < P2; ++j) {
+                        p->dcen[((int64_t)0 * P2 + j) * I + k] += to_fixed(q.w * q.S[j], S);
+                        p->dcen[((int64_t)1 * P2 + j) * I + k] += to_fixed(wmu * q.S[j], S);
+                        p->dcen[((int64_t)2 * P2 + j) * I + k] += to_fixed(wf * q.S[j], S);
+                    }
+                    or_census cq;
+                    cq.x = q.x;
+                    cq.mu = q.mu;
+                    cq.w = q.w;
+                    cq.cell = q.cell;
+                    cq.id = q.id;
+                    cq.lin = q.lin;
+                    memcpy(cq.S, q.S, sizeof cq.S);
+                    if (cb_push(&census, &cq)) { rc = E_OOM; goto fail_track; }
+                    s.census++;
                     if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
                     break;
                 }
-                philox_event(&q, 2u * e_ev + 1u, key, r2);
-                have_r2 = 1;
-                q.mu = 2.0 * or_u01(r2[0], r2[1]) - 1.0;
-                s.scatters++;
-                if (R > 0) q.S[R + p->region[k]] = q.S[R + p->region[k]] + p->inv_c[k]; /* scatter, prob c */
-                need_ww = 1;
-            }
-            if (need_ww && ww_on) {
-                const int32_t kc = q.cell;
-                if (q.w > p->ww_hi[kc]) {
-                    const double ratio = q.w / p->ww_c[kc];
-                    const double ndd = ceil(ratio);
-                    if (ndd > (double)MAX_DAUGHTERS) { s.error = E_NUMERIC; break; }
-                    const uint32_t nd = (uint32_t)ndd;
-                    const double wd = q.w / (double)nd;
-                    s.split_events++;
-                    s.daughters += nd - 1;
-                    for (uint32_t j = nd - 1; j >= 1; --j) {
-                        or_particle dq = q;
-                        dq.w = wd;
-                        dq.lin = lineage_hash(q.lin, e_ev, j);
-                        dq.e = 0;
-                        if (ps_push(&stack, &dq)) { rc = E_OOM; goto fail_track; }
-                    }
-                    q.w = wd;
-                    q.lin = lineage_hash(q.lin, e_ev, 0);
-                    q.e = 0;
-                } else if (q.w < p->ww_lo[kc]) {
-                    if (!have_r2) philox_event(&q, 2u * e_ev + 1u, key, r2);
-                    const double ur = or_u01(r2[2], r2[3]);
-                    const double ps = q.w / p->ww_c[kc];
-                    if (ur < ps) {
-                        q.w = p->ww_c[kc];
-                        s.roulette_survivals++;
+                int need_ww = 0;
+                int have_r2 = 0;
+                uint32_t r2[4];
+                if (ev == 1) {
+                    s.crossings++;
+                    const int32_t nk = (q.mu > 0.0) ? k + 1 : k - 1;
+                    if (nk < 0 || nk >= I) {
+                        const int side = (nk < 0) ? 0 : 1;
+                        const int32_t bc = side ? p->d.bc_right : p->d.bc_left;
+                        const double amu = fabs(q.mu);
+                        const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
+                        if (bc == OR_VACUUM) {
+                            /* surface estimators for the boundary closures:
+                             * phi_b ~ w/|mu|, F_b ~ w(1/3-mu^2)/|mu|, P_b ~ w(1/2-|mu|)/|mu| */
+                            const double wi = q.w * ia;
+                            p->bnd[3 * side + 0] += to_fixed(wi, S);
+                            p->bnd[3 * side + 1] += to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu), S);
+                            p->bnd[3 * side + 2] += to_fixed(wi * (0.5 - amu), S);
+                            for (int j = 0; j < P2; ++j) {
+                                p->dbnd[6 * j + 3 * side + 0] += to_fixed(wi * q.S[j], S);
+                                p->dbnd[6 * j + 3 * side + 1] += to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu) * q.S[j], S);
+                                p->dbnd[6 * j + 3 * side + 2] += to_fixed(wi * (0.5 - amu) * q.S[j], S);
+                            }
+                            s.leaked++;
+                            if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
+                            break;
+                        }
+                        q.mu = -q.mu; /* specular reflection, stays in cell k */
+                        s.reflections++;
                     } else {
-                        s.roulette_kills++;
+                        q.cell = nk;
+                    }
+                    need_ww = 1;
+                } else {
+                    s.collisions++;
+                    if (uc >= p->c[k]) {
+                        s.absorbed++;
                         if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
                         break;
                     }
+                    philox_event(&q, 2u * e_ev + 1u, key, r2);
+                    have_r2 = 1;
+                    q.mu = 2.0 * or_u01(r2[0], r2[1]) - 1.0;
+                    s.scatters++;
+                    if (R > 0) q.S[R + p->region[k]] = q.S[R + p->region[k]] + p->inv_c[k]; /* scatter, prob c */
+                    need_ww = 1;
+                }
+                if (need_ww && ww_on) {
+                    const int32_t kc = q.cell;
+                    if (q.w > p->ww_hi[kc]) {
+                        const double ratio = q.w / p->ww_c[kc];
+                        const double ndd = ceil(ratio);
+                        if (ndd > (double)MAX_DAUGHTERS) { s.error = E_NUMERIC; break; }
+                        const uint32_t nd = (uint32_t)ndd;
+                        const double wd = q.w / (double)nd;
+                        s.split_events++;
+                        s.daughters += nd - 1;
+                        for (uint32_t j = nd - 1; j >= 1; --j) {
+                            or_particle dq = q;
+                            dq.w = wd;
+                            dq.lin = lineage_hash(q.lin, e_ev, j);
+                            dq.e = 0;
+                            if (ps_push(&stack, &dq)) { rc = E_OOM; goto fail_track; }
+                        }
+                        q.w = wd;
+                        q.lin = lineage_hash(q.lin, e_ev, 0);
+                        q.e = 0;
+                    } else if (q.w < p->ww_lo[kc]) {
+                        if (!have_r2) philox_event(&q, 2u * e_ev + 1u, key, r2);
+                        const double ur = or_u01(r2[2], r2[3]);
+                        const double ps = q.w / p->ww_c[kc];
+                        if (ur < ps) {
+                            q.w = p->ww_c[kc];
+                            s.roulette_survivals++;
+                        } else {
+                            s.roulette_kills++;
+                            if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
+                            break;
+                        }
+                    }
                 }
             }
+        }
+        if (chunk < nupd && hi > 0) {
+            rc = update_windows(p, hi, phi_old, J_old, F_old, S);
+            if (rc) goto fail_track;
         }
     }
     free(stack.v);

@@ -51,6 +51,9 @@ int or_create(const or_desc* d, or_problem** out);
 int or_set_cross_sections(or_problem* p, const double* sigma_t, const double* c);
 int or_set_ww_params(or_problem* p, double rho, double eps_min, int32_t mode, int32_t center_scaling);
 int or_set_regions(or_problem* p, const int32_t* region); /* region of each cell, 0..R-1 */
+/* in-step window updates: n <= 16 updates after the fractions f_1 < ... < f_n
+ * in (0,1) of the step's histories (NULL: f_p = p/(n+1)); n = 0 turns them off */
+int or_set_ww_updates(or_problem* p, int32_t n, const double* fractions);
 int or_set_ww_centers(or_problem* p, const double* centers); /* override for the next step only */
 int or_run_step(or_problem* p, or_stats* st);
 int or_get_tallies(const or_problem* p, int32_t kind, double* out, int64_t n);

@@ -79,7 +79,7 @@ SYMBOLS = ["create_problem", "set_cross_sections", "set_ww_params", "set_ww_cent
            "get_tallies", "get_tallies_raw", "get_losm_solution", "get_bank", "set_bank", "get_census", "destroy_problem",
            "hww_status_string", "hww_last_error_string", "hww_losm_solve", "hww_philox_block", "hww_set_timing",
            "hww_get_counters", "hww_reset_counters", "create_batch", "batch_problem", "batch_set_tuning",
-           "run_batch_step", "batch_member_stats", "destroy_batch", "get_deriv_tallies", "vjp_state_size",
+           "run_batch_step", "batch_member_stats", "destroy_batch", "get_deriv_tallies", "vjp_state_size", "set_ww_updates",
            "save_vjp_state", "losm_vjp"]
 
 
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
         L.get_tallies_raw.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), C.c_int64]
         L.get_losm_solution.argtypes = [vp, C.c_int32, vp, vp, C.c_int32]
         L.get_deriv_tallies.argtypes = [vp, C.c_int32, vp, C.c_int64, C.c_int32]
+        L.set_ww_updates.argtypes = [vp, C.c_int32, vp]
         L.vjp_state_size.argtypes = [vp, C.POINTER(C.c_int64)]
         L.save_vjp_state.argtypes = [vp, vp, C.c_int64, C.c_int32]
         L.losm_vjp.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int32]
@@ -232,6 +233,8 @@ class Problem:
                 filter_k=wl.get("filter_k", 3), n_var_batches=wl.get("n_var_batches", 16),
                 deriv_regions=R, bank_capacity=bank_capacity, stream=stream)
         p.set_cross_sections(wl["sigma_t"], wl["c"], wl.get("region") if R else None)
+        if wl.get("ww_updates"):
+            p.set_ww_updates(wl["ww_updates"], wl.get("ww_fractions"))
         p.set_ww_params(wl["rho"], wl["eps_min"], wl.get("mode", MODE_HWW),
                         wl.get("center_scaling", SCALE_MEAN_WEIGHT))
         return p
@@ -263,6 +266,13 @@ class Problem:
     def set_ww_centers(self, centers):
         c = _f64(centers, self.I)
         _check(load().set_ww_centers(self._h, _dp(c)), "set_ww_centers")
+
+    def set_ww_updates(self, n, fractions=None):
+        """In-step window updates: n updates after the history fractions
+        (default p/(n+1))."""
+        f = _f64(fractions, int(n)) if fractions is not None else None
+        _check(load().set_ww_updates(self._h, int(n), f.ctypes.data_as(C.c_void_p) if f is not None else None),
+               "set_ww_updates")
 
     def run_step(self, stats=True):
         if not stats:

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -98,6 +99,8 @@ struct hww_problem {
     size_t track_smem = 0;
     int last_waves = 0;
     int emax = 64;         // events per track before it is requeued
+    int n_updates = 0;                 // in-step window updates (Sec. 3, Eq. Hpn)
+    double ww_frac[MAX_UPDATES] = {};  // their history fractions
     // likelihood-ratio derivatives (P2 = 2R parameters; 0: off)
     int R = 0, P2 = 0;
     double* d_inv_c = nullptr;                 // I, 1/c (0 where c = 0)
@@ -334,6 +337,8 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b) {
     a.region = p->d_region;
     a.inv_c = p->d_inv_c;
     a.bS = p->bS;
+    a.bank_lo = 0;
+    a.bank_hi = LLONG_MAX;
     a.dtl = p->dtl;
     a.dcen = p->dcen;
     a.dbnd = p->dbnd;
@@ -362,12 +367,17 @@ void account_track_time(hww_problem* p) {
     if (cudaEventElapsedTime(&ms, p->ev_a, p->ev_b) == cudaSuccess) p->track_ms += ms;
 }
 
+// the tracking waves of start-bank items [lo, hi): wave 0 from the bank,
+// then record waves until no record is left
 template <class Real>
-hww_status track_waves(hww_problem* p, Banks<Real>& b) {
+hww_status track_waves(hww_problem* p, Banks<Real>& b, long long lo = 0, long long hi = LLONG_MAX) {
     TrackArgs<Real> a = base_track_args(p, b);
     a.from_bank = 1;
+    a.bank_lo = lo;
+    a.bank_hi = hi;
     a.rin = b.q[1];
     a.rout = b.q[0];
+    if (lo > 0) HWW_CK(cudaMemsetAsync(b.q[0].count, 0, sizeof(unsigned long long), p->stream));
     launch_track(p, a);
     HWW_CK(cudaGetLastError());
     int cur = 0, waves = 1;
@@ -632,6 +642,8 @@ hww_status stage_pre(hww_problem* p) {
 // the closures), closures and initial conditions at t^n, the fully implicit
 // HLOSM (Eqs. losm-0, losm-1, losm-disc-bc), and the step-state advance
 hww_status stage_post(hww_problem* p) {
+    if (p->n_updates > 0)  // an in-step update left partial census tallies
+        HWW_CK(cudaMemsetAsync(p->cent, 0, sizeof(Acc128) * 3 * (size_t)p->I, p->stream));
     hww_status st = p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);
     if (st) return st;
     ClosureArgs ca{};
@@ -715,6 +727,93 @@ void fill_stats(const unsigned long long* h, unsigned long long nbank, double wb
     st->w_bar_next = wbar;
     st->waves = waves;
     st->status = err_to_status(e);
+}
+
+// windows of an in-step update (Sec. 3, Eq. Hpn): closures from the census
+// and boundary tallies of the first Hp histories (normalised by Hp), the
+// fully implicit HLOSM solution with them as the new level, centers from it
+hww_status update_windows(hww_problem* p, long long Hp) {
+    // the census tallies of the histories so far (the comb forms the step's
+    // own at its end)
+    HWW_CK(cudaMemsetAsync(p->cent, 0, sizeof(Acc128) * 3 * (size_t)p->I, p->stream));
+    if (p->fp32)
+        launch_census_tallies(comb_args(p, p->b32), 2 * p->nsm, p->stream);
+    else
+        launch_census_tallies(comb_args(p, p->b64), 2 * p->nsm, p->stream);
+    ++p->kernel_launches;
+    ClosureArgs ca{};
+    ca.I = p->I;
+    ca.sd = p->sd;
+    ca.v = p->d.v;
+    ca.dt = p->d.dt;
+    ca.N = Hp;
+    ca.bc_l = p->d.bc_left;
+    ca.bc_r = p->d.bc_right;
+    ca.filter_k = p->d.filter == HWW_FILTER_MA ? p->d.filter_k : 0;
+    ca.dx = p->d_dx;
+    ca.cent = p->cent;
+    ca.tl = nullptr;
+    ca.bnd = p->bnd;
+    ca.rphi = p->rphi;
+    ca.rJ = p->rJ;
+    ca.rF = p->rF;
+    for (int k = 0; k < 2; ++k) {
+        ca.set_phi[k] = p->cl_phi[k];
+        ca.set_J[k] = p->cl_J[k];
+        ca.set_F[k] = p->cl_F[k];
+        ca.set_P[k] = p->cl_P[k];
+    }
+    ca.prev_tl = p->prev_tl;
+    ca.nsets = 1;
+    p->kernel_launches += launch_closures(ca, p->stream);
+    LosmRhsIn full = semi_rhs(p);
+    full.full = 1;
+    p->kernel_launches += launch_losm_solve(p->mat, full, p->work, p->full_phi, p->full_J, p->mx, p->stream);
+    WwArgs wa{};
+    wa.I = p->I;
+    wa.scaling = p->scaling;
+    wa.eps = p->eps;
+    wa.rho = p->rho;
+    wa.sd = p->sd;
+    wa.phit_hlosm = p->full_phi + 1;
+    wa.phit_prev = p->prev_tl;
+    wa.mx_hlosm = p->mx;
+    wa.mx_prev = p->mx + 1;
+    wa.override_c = p->ww_override;
+    wa.ww_c = p->ww_c;
+    wa.ww_hi = p->ww_hi;
+    wa.ww_lo = p->ww_lo;
+    wa.ww_hl = p->d_ww_hl;
+    p->kernel_launches += launch_ww_centers(wa, 0, p->stream);
+    HWW_CK(cudaGetLastError());
+    return HWW_OK;
+}
+
+// the tracking of one step: in u_ww + 1 chunks of source ids when in-step
+// window updates are on and the step's windows come from the HLOSM solution
+template <class Real>
+hww_status track_step(hww_problem* p, Banks<Real>& b) {
+    if (p->n_updates == 0 || p->mode != HWW_MODE_HWW) return track_waves(p, b);
+    StepDev sdh;
+    HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
+    HWW_CK(cudaStreamSynchronize(p->stream));
+    if (sdh.ww_src != 1) return track_waves(p, b);  // an override step: no updates
+    const long long H = (long long)sdh.nbank;
+    const int u = p->n_updates;
+    int waves = 0;
+    for (int c = 0; c <= u; ++c) {
+        const long long lo = (c == 0) ? 0 : (long long)(p->ww_frac[c - 1] * (double)H);
+        const long long hi = (c == u) ? H : (long long)(p->ww_frac[c] * (double)H);
+        const hww_status s = track_waves(p, b, lo, hi);
+        if (s) return s;
+        waves += p->last_waves;
+        if (c < u && hi > 0) {
+            const hww_status s2 = update_windows(p, hi);
+            if (s2) return s2;
+        }
+    }
+    p->last_waves = waves;
+    return HWW_OK;
 }
 
 hww_status read_stats(hww_problem* p, hww_step_stats* st) {
@@ -927,7 +1026,8 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     }
     const size_t cen_smem = sizeof(long long) * 3 * (size_t)I;
     if (cen_smem > 48 * 1024 &&
-        (p->fp32 ? comb_write_smem_optin<float>(cen_smem) : comb_write_smem_optin<double>(cen_smem)) != 0) {
+        ((p->fp32 ? comb_write_smem_optin<float>(cen_smem) : comb_write_smem_optin<double>(cen_smem)) != 0 ||
+         (p->fp32 ? census_tally_smem_optin<float>(cen_smem) : census_tally_smem_optin<double>(cen_smem)) != 0)) {
         destroy_problem(p);
         return HWW_ERR_CUDA;
     }
@@ -1009,6 +1109,19 @@ hww_status set_ww_centers(hww_problem* p, const double* centers) {
     return HWW_OK;
 }
 
+hww_status set_ww_updates(hww_problem* p, int32_t n, const double* fractions) {
+    if (!p || n < 0 || n > MAX_UPDATES) return HWW_ERR_ARG;
+    double f[MAX_UPDATES];
+    for (int k = 0; k < n; ++k) {
+        // default f_p = p / (u + 1) (the fractions the paper uses)
+        f[k] = fractions ? fractions[k] : (double)(k + 1) / (double)(n + 1);
+        if (!(f[k] > 0.0 && f[k] < 1.0) || (k > 0 && !(f[k] > f[k - 1]))) return HWW_ERR_ARG;
+    }
+    for (int k = 0; k < n; ++k) p->ww_frac[k] = f[k];
+    p->n_updates = n;
+    return HWW_OK;
+}
+
 hww_status run_step(hww_problem* p, hww_step_stats* st) {
     if (!p) return HWW_ERR_ARG;
     if (!p->xs_set || !p->ww_set) return HWW_ERR_STATE;
@@ -1022,7 +1135,7 @@ hww_status run_step(hww_problem* p, hww_step_stats* st) {
         s = stage_pre(p);
         if (s) return s;
         p->q_peak = 0;
-        s = p->fp32 ? track_waves(p, p->b32) : track_waves(p, p->b64);
+        s = p->fp32 ? track_step(p, p->b32) : track_step(p, p->b64);
         if (s) return s;
         unsigned e = 0;
         unsigned long long ncen = 0;
@@ -1809,7 +1922,7 @@ hww_status batch_set_tuning(hww_batch* b, int32_t tile, int32_t emax) {
 hww_status run_batch_step(hww_batch* b, hww_batch_stats* stats) {
     if (!b) return HWW_ERR_ARG;
     for (hww_problem* p : b->m)
-        if (!p->xs_set || !p->ww_set) return HWW_ERR_STATE;
+        if (!p->xs_set || !p->ww_set || p->n_updates > 0) return HWW_ERR_STATE;
     HWW_CK(cudaSetDevice(b->device));
     // order the batch's own stream after the caller's work
     HWW_CK(cudaEventRecord(b->ev_in, b->user));

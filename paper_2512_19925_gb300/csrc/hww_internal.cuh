@@ -22,7 +22,8 @@ constexpr int SPLIT_CHUNK = 8;
 constexpr uint32_t MAX_DAUGHTERS = 1u << 24;
 constexpr uint32_t MAX_EVENTS = 1u << 30;
 constexpr double GRAZE_MU = 0.01;
-constexpr int MAX_SCORES = 8;  // likelihood-ratio scores per particle: (Sigma_t, c) of up to 4 regions
+constexpr int MAX_SCORES = 8;
+constexpr int MAX_UPDATES = 16;  // in-step window updates per step  // likelihood-ratio scores per particle: (Sigma_t, c) of up to 4 regions
 
 enum ErrBits : unsigned {
     ERR_CENSUS_OVERFLOW = 1u,
@@ -97,6 +98,7 @@ struct TrackArgs {
     int I, B, emax;
     long long N;      // source particles per step (variance batches)
     int from_bank;
+    long long bank_lo, bank_hi;  // wave 0 takes start-bank items [bank_lo, min(bank_hi, size))
     int bc_l, bc_r;
     int birth_cell_pos, birth_cell_neg;
     double tau0;      // v dt

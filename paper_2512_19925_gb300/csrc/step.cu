@@ -392,6 +392,34 @@ __device__ __forceinline__ void census_terms(double w, float mu, double tscale, 
     c2 = fx_mul(c0, 1.0f / 3.0f - mu * mu);
 }
 
+// census tallies alone (Eq. ct-mc) of the census bank so far: the closures
+// of an in-step window update need them before the comb
+template <class Real>
+__global__ void census_tally_kernel(CombArgs<Real> a) {
+    extern __shared__ long long s_cen[];  // 3 I
+    const int I = a.I;
+    for (int i = threadIdx.x; i < 3 * I; i += blockDim.x) s_cen[i] = 0;
+    __syncthreads();
+    const long long m = (long long)*a.ncensus_ptr;
+    const long long mm = m < a.cen_cap ? m : a.cen_cap;
+    const double tscale = a.sd->tscale;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int k = a.ccell[j];
+        long long c0, c1, c2;
+        census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
+        const Agg3 g = warp_agg3(k, c0, c1, c2);
+        if (g.leader) {
+            sadd(&s_cen[k], g.s0);
+            sadd(&s_cen[I + k], g.s1);
+            sadd(&s_cen[2 * I + k], g.s2);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * I; i += blockDim.x)
+        if (s_cen[i] != 0) add128(&a.cent[i], s_cen[i]);
+}
+
 // census order: each census particle's census tallies (Eq. ct-mc; block-
 // private in shared memory, warp-aggregated by cell), its teeth and its copies
 template <class Real>
@@ -491,6 +519,16 @@ void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
 }
 
 template <class Real>
+void launch_census_tallies(const CombArgs<Real>& a, int grid, cudaStream_t s) {
+    census_tally_kernel<Real><<<grid, 256, sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
+}
+
+template <class Real>
+int census_tally_smem_optin(size_t smem) {
+    return raise_smem_limit((const void*)census_tally_kernel<Real>, smem);
+}
+
+template <class Real>
 void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s) {
     comb_finalize_kernel<<<1, 1, 0, s>>>(a.sd, a.goff_w, a.ncensus_ptr, a.N, a.cen_cap, a.err);
 }
@@ -506,6 +544,10 @@ template void launch_comb_finalize<double>(const CombArgs<double>&, cudaStream_t
 template void launch_comb_finalize<float>(const CombArgs<float>&, cudaStream_t);
 template int comb_write_smem_optin<double>(size_t);
 template int comb_write_smem_optin<float>(size_t);
+template void launch_census_tallies<double>(const CombArgs<double>&, int, cudaStream_t);
+template void launch_census_tallies<float>(const CombArgs<float>&, int, cudaStream_t);
+template int census_tally_smem_optin<double>(size_t);
+template int census_tally_smem_optin<float>(size_t);
 
 __global__ void philox_block_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                     uint32_t k1, long long n, uint32_t* out) {

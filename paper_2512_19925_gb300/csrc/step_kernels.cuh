@@ -58,6 +58,11 @@ template <class Real>
 void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s);
 template <class Real>
 int comb_write_smem_optin(size_t smem);
+// census tallies of the census bank so far, into the (cleared) tallies
+template <class Real>
+void launch_census_tallies(const CombArgs<Real>& a, int grid, cudaStream_t s);
+template <class Real>
+int census_tally_smem_optin(size_t smem);
 void launch_philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
                          long long n, uint32_t* out, cudaStream_t s);
 

@@ -425,18 +425,21 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
     cnt.zero();
     const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
     const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
-    // wave 0: each block takes a contiguous id range, so nearly all of its
-    // segments fall in one variance batch (kept in shared memory); record
-    // waves: grid-stride over the records
+    // wave 0: each block takes a contiguous id range of [bank_lo, bank_hi), so
+    // nearly all of its segments fall in one variance batch (kept in shared
+    // memory); record waves: grid-stride over the records
     long long stride, item, item_end;
     int b_blk = -1;
     if (a.from_bank) {
-        const long long chunk = (n_use + gridDim.x - 1) / gridDim.x;
-        item = (long long)blockIdx.x * chunk + threadIdx.x;
-        item_end = min(n_use, (long long)(blockIdx.x + 1) * chunk);
+        const long long lo = a.bank_lo;
+        const long long hi = min(n_use, a.bank_hi);
+        const long long len = hi > lo ? hi - lo : 0;
+        const long long chunk = (len + gridDim.x - 1) / gridDim.x;
+        const long long first = lo + (long long)blockIdx.x * chunk;
+        item = first + threadIdx.x;
+        item_end = min(hi, first + chunk);
         stride = blockDim.x;
-        if ((long long)blockIdx.x * chunk < n_use)
-            b_blk = batch_of((uint32_t)((long long)blockIdx.x * chunk), batch_div(a.B, a.N));
+        if (first < hi) b_blk = batch_of((uint32_t)first, batch_div(a.B, a.N));
     } else {
         item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         item_end = n_use;
