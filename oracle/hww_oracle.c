@@ -47,6 +47,8 @@ enum { OR_VACUUM = 0, OR_REFLECT = 1 };
 enum { OR_MODE_HWW = 0, OR_MODE_ANALOG = 1, OR_MODE_LWW = 2 };
 enum { OR_SCALE_MEAN_WEIGHT = 0, OR_SCALE_LITERAL = 1 };
 #define OR_MAX_UPDATES 16
+#define OR_MAX_C 16.0                  /* largest mean number of particles per collision */
+#define SECONDARY_EVENT 0x80000000u    /* lineage namespace of a collision's extra particles */
 enum {
     K_TL_PHI = 0, K_TL_J, K_TL_F, K_CEN_PHI, K_CEN_J, K_CEN_F, K_BATCH_PHI, K_BOUNDARY,
     K_WW_CENTER, K_CLOSURE_PHI, K_CLOSURE_J, K_CLOSURE_F
@@ -332,15 +334,21 @@ void or_destroy(or_problem* p) {
     free(p);
 }
 
+/* c is the mean number of particles a collision emits, (Sigma_s + nu_f
+ * Sigma_f) / Sigma_t (Eq. HO_transport): c <= 1 a scattering-absorbing
+ * medium, c > 1 a multiplying one (up to OR_MAX_C); Sigma_a of the LOSM
+ * equations is Sigma_t (1 - c).  Derivative runs need c <= 1. */
 int or_set_cross_sections(or_problem* p, const double* sigma_t, const double* c) {
     if (!p || !sigma_t || !c) return E_ARG;
     for (int32_t i = 0; i < p->I; ++i)
-        if (!(sigma_t[i] > 0) || !(c[i] >= 0 && c[i] <= 1) || !isfinite(sigma_t[i])) return E_ARG;
+        if (!(sigma_t[i] > 0) || !(c[i] >= 0 && c[i] <= OR_MAX_C) || !isfinite(sigma_t[i]) ||
+            (p->R > 0 && c[i] > 1.0))
+            return E_ARG;
     for (int32_t i = 0; i < p->I; ++i) {
         p->sigt[i] = sigma_t[i];
         p->inv_sigt[i] = 1.0 / sigma_t[i];
         p->c[i] = c[i];
-        p->siga[i] = sigma_t[i] * (1.0 - c[i]); /* Sigma_t - Sigma_s (no fission) */
+        p->siga[i] = sigma_t[i] * (1.0 - c[i]); /* Sigma_t - Sigma_s - nu_f Sigma_f */
         p->inv_c[i] = (c[i] > 0.0) ? 1.0 / c[i] : 0.0;
     }
     p->xs_set = 1;
@@ -1067,7 +1075,11 @@ int or_run_step(or_problem* p, or_stats* st) {
                     need_ww = 1;
                 } else {
                     s.collisions++;
-                    if (uc >= p->c[k]) {
+                    /* the collision emits floor(c) + [u_c < c - floor(c)] particles
+                     * (mean c); none: absorbed */
+                    const double cfl = floor(p->c[k]);
+                    const uint32_t nsec = (uint32_t)cfl + ((uc < p->c[k] - cfl) ? 1u : 0u);
+                    if (nsec == 0) {
                         s.absorbed++;
                         if (q.e > (uint32_t)s.max_events) s.max_events = q.e;
                         break;
@@ -1077,6 +1089,21 @@ int or_run_step(or_problem* p, or_stats* st) {
                     q.mu = 2.0 * or_u01(r2[0], r2[1]) - 1.0;
                     s.scatters++;
                     if (R > 0) q.S[R + p->region[k]] = q.S[R + p->region[k]] + p->inv_c[k]; /* scatter, prob c */
+                    /* the other emitted particles (a multiplying medium): each with
+                     * its own lineage in the secondaries' namespace and its own
+                     * isotropic direction; the track continues as the first */
+                    if (nsec > 1) {
+                        s.daughters += nsec - 1;
+                        for (uint32_t j = nsec - 1; j >= 1; --j) {
+                            or_particle dq = q;
+                            dq.lin = lineage_hash(q.lin, e_ev | SECONDARY_EVENT, j);
+                            dq.e = 0;
+                            uint32_t ctr[4] = {dq.id, (uint32_t)dq.lin, (uint32_t)(dq.lin >> 32), 0xFFFFFFFEu}, rr[4];
+                            or_philox4x32_10(ctr, key, rr);
+                            dq.mu = 2.0 * or_u01(rr[0], rr[1]) - 1.0;
+                            if (ps_push(&stack, &dq)) { rc = E_OOM; goto fail_track; }
+                        }
+                    }
                     need_ww = 1;
                 }
                 if (need_ww && ww_on) {

@@ -75,6 +75,24 @@ def shield(particles_per_step=100_000_000, seed=1, n_steps=200, precision="fp32"
                 eps_min=1e-3, precision=precision)
 
 
+def azurv1(particles_per_step=10_000, seed=1, n_steps=20, precision="fp64"):
+    """The paper's supercritical plane-pulse problem (Sec. 5.1): an infinite
+    multiplying medium (Sigma_t = 1, Sigma_s = Sigma_f = 1/3, nu_f = 2.3, so a
+    collision emits c = 1.1 particles on average) represented by 201 cells on
+    [-20.5, 20.5], dt = 1, 20 steps, the HWW parameters the paper uses there
+    (rho = 1.25, eps_min = 1e-3, three in-step updates at p/4) and the MA
+    filter with k = 3."""
+    n_cells = 201
+    edges = np.linspace(-20.5, 20.5, n_cells + 1)
+    sig_s, sig_f, nu = 1.0 / 3.0, 1.0 / 3.0, 2.3
+    c = (sig_s + nu * sig_f) / 1.0
+    return dict(name="azurv1", edges=edges, sigma_t=np.ones(n_cells), c=np.full(n_cells, c),
+                region=np.zeros(n_cells, np.int32), n_regions=1, v=1.0, dt=1.0, n_steps=n_steps,
+                bc_left=VACUUM, bc_right=VACUUM, src_x=0.0, particles_per_step=int(particles_per_step),
+                seed=int(seed), theta=0.5, filter=1, filter_k=3, n_var_batches=16, ratio=1.25 ** 2,
+                rho=1.25, eps_min=1e-3, ww_updates=3, precision=precision)
+
+
 def differentiation(particles_per_step=10_000_000, seed=1, n_steps=200):
     wl = shield(particles_per_step=particles_per_step, seed=seed, n_steps=n_steps, precision="fp64")
     wl["name"] = "differentiation"
