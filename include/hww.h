@@ -124,8 +124,12 @@ typedef struct {
  * HWW_ERR_CUDA.  On error *out is NULL. */
 hww_status create_problem(const hww_problem_desc* desc, hww_problem** out);
 
-/* Per-cell total cross section Sigma_t > 0 and scattering ratio 0 <= c <= 1
- * (Sigma_s = c Sigma_t, no fission), Eq. (HO_transport).  `region` (nullable)
+/* Per-cell total cross section Sigma_t > 0 and the mean number of particles
+ * a collision emits, c = (Sigma_s + nu_f Sigma_f) / Sigma_t, 0 <= c <= 16
+ * (Eq. HO_transport): c <= 1 scattering and absorption, c > 1 a multiplying
+ * medium, where a collision emits floor(c) + [u < c - floor(c)] particles,
+ * the extra ones with their own isotropic directions.  Derivative runs need
+ * c <= 1.  `region` (nullable)
  * maps each cell to a region 0..R-1 for the derivative tallies.  Host arrays
  * of length I.  May be called again between steps. */
 hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const double* c,

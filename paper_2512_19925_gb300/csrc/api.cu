@@ -1017,17 +1017,12 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     }
     // tracking launch shape: persistent grid of resident blocks
     p->track_smem = sizeof(long long) * (TALLY_ROWS + P2) * (size_t)I;
-    if (p->track_smem > 48 * 1024) {
-        if ((p->fp32 ? track_smem_optin_fp32(p->track_smem) : track_smem_optin_fp64(p->track_smem, p->P2 > 0)) !=
-            0) {
-            destroy_problem(p);
-            return HWW_ERR_CUDA;
-        }
-    }
+    // the dynamic shared memory limits are set whatever the sizes: a kernel's
+    // static shared memory counts against the default 48 KB as well
     const size_t cen_smem = sizeof(long long) * 3 * (size_t)I;
-    if (cen_smem > 48 * 1024 &&
-        ((p->fp32 ? comb_write_smem_optin<float>(cen_smem) : comb_write_smem_optin<double>(cen_smem)) != 0 ||
-         (p->fp32 ? census_tally_smem_optin<float>(cen_smem) : census_tally_smem_optin<double>(cen_smem)) != 0)) {
+    if ((p->fp32 ? track_smem_optin_fp32(p->track_smem) : track_smem_optin_fp64(p->track_smem, p->P2 > 0)) != 0 ||
+        (p->fp32 ? comb_write_smem_optin<float>(cen_smem) : comb_write_smem_optin<double>(cen_smem)) != 0 ||
+        (p->fp32 ? census_tally_smem_optin<float>(cen_smem) : census_tally_smem_optin<double>(cen_smem)) != 0) {
         destroy_problem(p);
         return HWW_ERR_CUDA;
     }
@@ -1043,7 +1038,9 @@ hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const doubl
     if (!p || !sigma_t || !c) return HWW_ERR_ARG;
     const int I = p->I;
     for (int i = 0; i < I; ++i) {
-        if (!(sigma_t[i] > 0) || !std::isfinite(sigma_t[i]) || !(c[i] >= 0 && c[i] <= 1)) return HWW_ERR_ARG;
+        if (!(sigma_t[i] > 0) || !std::isfinite(sigma_t[i]) || !(c[i] >= 0 && c[i] <= MAX_C) ||
+            (p->P2 > 0 && c[i] > 1.0))
+            return HWW_ERR_ARG;
         if (region && (region[i] < 0 || (p->d.deriv_regions > 0 && region[i] >= p->d.deriv_regions)))
             return HWW_ERR_ARG;
     }
@@ -1871,7 +1868,7 @@ hww_status create_batch(const hww_problem_desc* descs, int32_t n, void* cuda_str
         Imax = std::max(Imax, p->I);
     }
     b->smem = sizeof(long long) * TALLY_ROWS * (size_t)Imax;
-    if (b->smem > 48 * 1024 && track_batch_smem_optin(b->fp32, b->smem) != 0) {
+    if (track_batch_smem_optin(b->fp32, b->smem) != 0) {  // static shared memory counts too
         destroy_batch(b);
         return HWW_ERR_CUDA;
     }

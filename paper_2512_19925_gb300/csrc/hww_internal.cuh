@@ -19,6 +19,12 @@
 namespace hww {
 
 constexpr int SPLIT_CHUNK = 8;
+// A record's jstart carries FRESH_DIRECTION for the extra particles of a
+// multiplying collision: each daughter then samples its own isotropic
+// direction.  Their lineages hash the event with SECONDARY_EVENT set.
+constexpr uint32_t FRESH_DIRECTION = 0x80000000u;
+constexpr uint32_t SECONDARY_EVENT = 0x80000000u;
+constexpr double MAX_C = 16.0;  // largest mean number of particles per collision
 constexpr uint32_t MAX_DAUGHTERS = 1u << 24;
 constexpr uint32_t MAX_EVENTS = 1u << 30;
 constexpr double GRAZE_MU = 0.01;

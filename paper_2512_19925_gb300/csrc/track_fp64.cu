@@ -101,6 +101,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
     P64 q;
     P64 base;  // record whose daughters are being expanded
     uint32_t jnext = 0, jend = 0;
+    bool fresh = false;  // the record being expanded holds a collision's extra particles
     bool have = false;
     int evs = 0;
     int qb = 0;  // variance batch of the current track's source id
@@ -111,6 +112,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 q.lin = lineage_hash(base.lin, base.e, jnext);
                 q.e = 0;
                 ++jnext;
+                if (fresh) {  // its own isotropic direction
+                    uint32_t rr[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 0xFFFFFFFEu};
+                    philox4x32_10(rr, k0, k1);
+                    q.mu = 2.0 * u01(rr[0], rr[1]) - 1.0;
+                }
                 if constexpr (DERIV) {
 #pragma unroll
                     for (int j = 0; j < MAX_SCORES; ++j) S[j] = bS[j];
@@ -163,11 +169,18 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
 #pragma unroll
                             for (int j = 0; j < MAX_SCORES; ++j) bS[j] = S[j];
                         }
-                        jnext = a.rin.jstart[i];
+                        const uint32_t js = a.rin.jstart[i];
+                        fresh = (js & FRESH_DIRECTION) != 0;
+                        jnext = js & ~FRESH_DIRECTION;
                         jend = jnext + jc;
                         q.lin = lineage_hash(base.lin, base.e, jnext);
                         q.e = 0;
                         ++jnext;
+                        if (fresh) {  // its own isotropic direction
+                            uint32_t rr[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 0xFFFFFFFEu};
+                            philox4x32_10(rr, k0, k1);
+                            q.mu = 2.0 * u01(rr[0], rr[1]) - 1.0;
+                        }
                     }
                 }
             } else {
@@ -337,7 +350,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             }
         } else {
             cnt.v[ST_COLLISIONS]++;
-            if (uc >= a.c[k]) {
+            // the collision emits floor(c) + [u_c < c - floor(c)] particles (mean c)
+            const double cc = a.c[k];
+            const double cfl = floor(cc);
+            const uint32_t nsec = (uint32_t)cfl + ((uc < cc - cfl) ? 1u : 0u);
+            if (nsec == 0) {
                 cnt.v[ST_ABSORBED]++;
                 cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
                 have = false;
@@ -352,6 +369,19 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             q.mu = 2.0 * u01(r2[0], r2[1]) - 1.0;
             q.inv_mu = 1.0 / q.mu;
             cnt.v[ST_SCATTERS]++;
+            if (nsec > 1) {
+                // the other emitted particles: records of daughters that take
+                // their own lineages and isotropic directions
+                const uint32_t nx = nsec - 1;
+                const uint32_t nch = (nx + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+                const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
+                for (uint32_t ch = 0; ch < nch; ++ch) {
+                    const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
+                    const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nsec - j0);
+                    push_record<DERIV>(a, q, S, q.w, e_ev | SECONDARY_EVENT, j0 | FRESH_DIRECTION, jc, b0 + ch);
+                }
+                cnt.v[ST_DAUGHTERS] += nx;
+            }
             if constexpr (DERIV) {
                 const int jc = R + a.region[k];
 #pragma unroll

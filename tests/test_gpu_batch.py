@@ -99,3 +99,20 @@ def test_full_sweep_bookkeeping():
             s = batch.member_stats(i)
             assert s["n_start"] + s["daughters"] - s["absorbed"] - s["roulette_kills"] - s["leaked"] == s["census"]
             assert s["n_next"] == wls[i]["particles_per_step"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_shared_memory_near_the_default_limit(precision):
+    # 4 I 8 B of dynamic shared tallies just under 48 KB: the kernels' static
+    # shared memory pushes the total over the default limit, so the library
+    # must raise the limit whatever the dynamic size
+    edges = np.linspace(-10.0, 10.0, 1535)
+    wl = dict(workloads.plain_slab(particles_per_step=2000), edges=edges, sigma_t=np.ones(1534),
+              c=np.full(1534, 0.9), precision=precision)
+    p = hww.Problem.from_workload(wl)
+    p.run_step()
+    sweep = workloads.batched_sweep(n_problems=3, n_steps=2, scale=0.01)  # largest member: 1529 cells
+    for w in sweep:
+        w["precision"] = precision
+    b = hww.Batch(sweep)
+    assert b.run_step()["status"] == 0
