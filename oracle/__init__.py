@@ -37,6 +37,7 @@ TL_PHI, TL_J, TL_F, CENSUS_PHI, CENSUS_J, CENSUS_F, BATCH_PHI, BOUNDARY = range(
 WW_CENTER, CLOSURE_PHI, CLOSURE_J, CLOSURE_F = 8, 9, 10, 11
 VACUUM, REFLECT = 0, 1
 MODE_HWW, MODE_ANALOG, MODE_LWW = 0, 1, 2
+FILTER_NONE, FILTER_MA, FILTER_FOURIER = 0, 1, 2
 SCALE_MEAN_WEIGHT, SCALE_LITERAL = 0, 1
 SEMI, FULL = 0, 1
 
@@ -115,6 +116,7 @@ def lib():
             L.or_log.argtypes = [C.c_double]
             L.or_log.restype = C.c_double
             L.or_ma_filter.argtypes = [dp, dp, C.c_int32, C.c_int32]
+            L.or_fourier_filter.argtypes = [dp, dp, C.c_int32, C.c_int32]
             L.or_losm_solve.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
                                         C.c_int32, C.c_int32, dp, dp, dp, dp, C.c_double,
                                         C.c_double, dp, dp, dp, dp]
@@ -160,6 +162,14 @@ def u01(lo, hi):
 
 def log(u):
     return lib().or_log(float(u))
+
+
+def fourier_filter(x, kappa):
+    """Fourier low-pass filter of a vector (modes of frequency <= kappa kept)."""
+    x = _f64(x)
+    out = np.empty_like(x)
+    _check(lib().or_fourier_filter(_dp(x), _dp(out), x.size, int(kappa)), "fourier_filter")
+    return out
 
 
 def ma_filter(x, k):

@@ -234,7 +234,8 @@ int or_create(const or_desc* d, or_problem** out) {
     if (I < 1 || !d->edges || !(d->v > 0) || !(d->dt > 0) || d->particles_per_step < 1 ||
         d->particles_per_step >= (1LL << 30) || (d->theta != 0.5 && d->theta != 1.0) ||
         d->n_var_batches < 1 || d->bc_left < 0 || d->bc_left > 1 || d->bc_right < 0 ||
-        d->bc_right > 1 || d->filter < 0 || d->filter > 1 || (d->filter == 1 && d->filter_k < 1) ||
+        d->bc_right > 1 || d->filter < 0 || d->filter > 2 || (d->filter == 1 && d->filter_k < 1) ||
+        (d->filter == 2 && d->filter_k < 0) ||
         d->deriv_regions < 0 || 2 * d->deriv_regions > MAX_DERIV)
         return E_ARG;
     for (int32_t i = 0; i < I; ++i)
@@ -413,6 +414,48 @@ int or_ma_filter(const double* in, double* out, int32_t m, int32_t k) {
         for (int32_t l = -kk; l <= kk; ++l) s = s + in[j - l - 1];
         out[j - 1] = s / (double)(2 * kk + 1);
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fourier low-pass filter, Eqs. (fft), (ifft) and the cutoff between them   */
+/* The DFT of the vector, the modes above the cutoff set to zero, the       */
+/* inverse DFT.  Reading: the printed sums run j = 1..M, which puts the     */
+/* constant mode at j = M; a low-pass filter keeps the constant mode and    */
+/* both signs of every frequency up to kappa, i.e. the modes with           */
+/* min(j, M - j) <= kappa (0-based j), which keeps the result real.  The    */
+/* angles are reduced exactly, 2 pi ((j m) mod M) / M.                      */
+/* ------------------------------------------------------------------------ */
+int or_fourier_filter(const double* in, double* out, int32_t M, int32_t kappa) {
+    if (!in || !out || M < 0 || kappa < 0) return E_ARG;
+    double* Xr = xcalloc(M ? M : 1, sizeof(double));
+    double* Xi = xcalloc(M ? M : 1, sizeof(double));
+    if (!Xr || !Xi) {
+        free(Xr); free(Xi);
+        return E_OOM;
+    }
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int32_t j = 0; j < M; ++j) {
+        double re = 0.0, im = 0.0;
+        for (int32_t m = 0; m < M; ++m) {
+            const double ang = two_pi * (double)(((int64_t)j * m) % M) / (double)M;
+            re = re + in[m] * cos(ang);
+            im = im - in[m] * sin(ang);
+        }
+        const int32_t f = (j < M - j) ? j : M - j;
+        Xr[j] = (f <= kappa) ? re : 0.0;
+        Xi[j] = (f <= kappa) ? im : 0.0;
+    }
+    for (int32_t m = 0; m < M; ++m) {
+        double acc = 0.0;
+        for (int32_t j = 0; j < M; ++j) {
+            const double ang = two_pi * (double)(((int64_t)j * m) % M) / (double)M;
+            acc = acc + (Xr[j] * cos(ang) - Xi[j] * sin(ang));
+        }
+        out[m] = acc / (double)M;
+    }
+    free(Xr);
+    free(Xi);
     return 0;
 }
 
@@ -702,14 +745,21 @@ static void build_closure_set(const or_problem* p, const double* cphi, const dou
     oJ[I] = (p->d.bc_right == OR_REFLECT) ? 0.0 : (0.5 * ophi[I + 1] - PR);
     if (oPL) *oPL = (p->d.bc_left == OR_REFLECT) ? 0.0 : PL;
     if (oPR) *oPR = (p->d.bc_right == OR_REFLECT) ? 0.0 : PR;
-    if (p->d.filter == 1) {
-        or_ma_filter(ophi + 1, tmp, I, p->d.filter_k);
+    if (p->d.filter == 1 || p->d.filter == 2) {
+        int (*filt)(const double*, double*, int32_t, int32_t) = (p->d.filter == 1) ? or_ma_filter : or_fourier_filter;
+        filt(ophi + 1, tmp, I, p->d.filter_k);
         memcpy(ophi + 1, tmp, sizeof(double) * I);
-        or_ma_filter(oF + 1, tmp, I, p->d.filter_k);
+        filt(oF + 1, tmp, I, p->d.filter_k);
         memcpy(oF + 1, tmp, sizeof(double) * I);
-        or_ma_filter(oJ, tmp2, I + 1, p->d.filter_k);
+        filt(oJ, tmp2, I + 1, p->d.filter_k);
         memcpy(oJ, tmp2, sizeof(double) * (I + 1));
-        /* the end values are unchanged by the filter, so the copies above hold */
+        /* the ghost values copy the filtered end cells (the MA filter keeps
+         * the end values, so for it nothing changes); the edge currents,
+         * boundary edges included, are the filtered ones */
+        ophi[0] = ophi[1];
+        ophi[I + 1] = ophi[I];
+        oF[0] = oF[1];
+        oF[I + 1] = oF[I];
     }
     free(tmp);
     free(tmp2);

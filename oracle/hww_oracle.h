@@ -31,7 +31,8 @@ typedef struct {
     int64_t particles_per_step;  /* 1 <= N < 2^30 */
     uint64_t seed;
     double theta;                 /* 0.5 Crank-Nicolson, 1.0 backward Euler */
-    int32_t filter, filter_k;     /* 0 none, 1 moving average of base k */
+    int32_t filter, filter_k;     /* 0 none, 1 moving average of base k, 2 Fourier low-pass
+                                     with cutoff k */
     int32_t n_var_batches;        /* B for the batch-mean variance tally */
     int32_t deriv_regions;        /* R > 0: likelihood-ratio derivative tallies for
                                      (Sigma_t, c) of R regions (R <= 4) */
@@ -95,6 +96,7 @@ void or_destroy(or_problem* p);
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double or_u01(uint32_t lo, uint32_t hi);
 double or_log(double u);
+int or_fourier_filter(const double* in, double* out, int32_t m, int32_t kappa);
 int or_ma_filter(const double* in, double* out, int32_t m, int32_t k);
 int or_losm_solve(int32_t n_cells, const double* dx, const double* sigma_t, const double* sigma_a,
                   double v, double dt, double theta, int32_t bc_left, int32_t bc_right,
