@@ -63,7 +63,7 @@ typedef enum {
 
 enum { HWW_BC_VACUUM = 0, HWW_BC_REFLECT = 1 };
 enum { HWW_FP64 = 0, HWW_FP32_TRACK = 1 };
-enum { HWW_FILTER_NONE = 0, HWW_FILTER_MA = 1 };
+enum { HWW_FILTER_NONE = 0, HWW_FILTER_MA = 1, HWW_FILTER_FOURIER = 2 };
 /* window modes: HLOSM centers (the paper's method), analog (no windows),
  * lagged (centers from the previous step's track-length flux) */
 enum { HWW_MODE_HWW = 0, HWW_MODE_ANALOG = 1, HWW_MODE_LWW = 2 };
@@ -98,7 +98,9 @@ typedef struct {
     uint64_t seed;            /* Philox key (with the step index) */
     int32_t precision;        /* HWW_FP64 | HWW_FP32_TRACK */
     double theta;             /* 0.5 Crank-Nicolson | 1.0 backward Euler */
-    int32_t filter, filter_k; /* HWW_FILTER_NONE | HWW_FILTER_MA with base k >= 1 */
+    int32_t filter, filter_k; /* HWW_FILTER_NONE | HWW_FILTER_MA with base k >= 1 (Eq. moving_average) |
+                                 HWW_FILTER_FOURIER with cutoff k >= 0 (Eqs. fft, ifft): the modes of
+                                 frequency min(j, M - j) <= k kept */
     int32_t n_var_batches;    /* B >= 1 batches for the batch-mean variance tally */
     int32_t deriv_regions;    /* 0, or 1 <= R <= 4 regions for derivative tallies (FP64 only; the
                                  tracking needs (7 + 2R) I 8 bytes of shared memory per block,

@@ -25,7 +25,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of mem
           7: "CUDA runtime error", 8: "no CUDA device"}
 BC_VACUUM, BC_REFLECT = 0, 1
 FP64, FP32_TRACK = 0, 1
-FILTER_NONE, FILTER_MA = 0, 1
+FILTER_NONE, FILTER_MA, FILTER_FOURIER = 0, 1, 2
 MODE_HWW, MODE_ANALOG, MODE_LWW = 0, 1, 2
 SCALE_MEAN_WEIGHT, SCALE_LITERAL = 0, 1
 TL_PHI, TL_J, TL_F, CENSUS_PHI, CENSUS_J, CENSUS_F, BATCH_PHI, BOUNDARY = range(8)

@@ -655,6 +655,8 @@ hww_status stage_post(hww_problem* p) {
     ca.bc_l = p->d.bc_left;
     ca.bc_r = p->d.bc_right;
     ca.filter_k = p->d.filter == HWW_FILTER_MA ? p->d.filter_k : 0;
+    ca.fourier = p->d.filter == HWW_FILTER_FOURIER;
+    ca.kappa = p->d.filter_k;
     ca.dx = p->d_dx;
     ca.cent = p->cent;
     ca.tl = p->tl;
@@ -750,6 +752,8 @@ hww_status update_windows(hww_problem* p, long long Hp) {
     ca.bc_l = p->d.bc_left;
     ca.bc_r = p->d.bc_right;
     ca.filter_k = p->d.filter == HWW_FILTER_MA ? p->d.filter_k : 0;
+    ca.fourier = p->d.filter == HWW_FILTER_FOURIER;
+    ca.kappa = p->d.filter_k;
     ca.dx = p->d_dx;
     ca.cent = p->cent;
     ca.tl = nullptr;
@@ -876,7 +880,8 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         d->particles_per_step < 1 || d->particles_per_step >= (1LL << 30) ||
         (d->theta != 0.5 && d->theta != 1.0) || d->n_var_batches < 1 || d->n_var_batches > 64 ||
         d->bc_left < 0 || d->bc_left > 1 || d->bc_right < 0 || d->bc_right > 1 || d->filter < 0 ||
-        d->filter > 1 || (d->filter == 1 && d->filter_k < 1) || d->precision < 0 || d->precision > 1 ||
+        d->filter > 2 || (d->filter == 1 && d->filter_k < 1) || (d->filter == 2 && d->filter_k < 0) ||
+        d->precision < 0 || d->precision > 1 ||
         d->deriv_regions < 0 || d->deriv_regions > MAX_SCORES / 2 ||
         (d->deriv_regions > 0 && d->precision != HWW_FP64) || d->bank_capacity < 0)
         return HWW_ERR_ARG;
@@ -1025,6 +1030,13 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         (p->fp32 ? census_tally_smem_optin<float>(cen_smem) : census_tally_smem_optin<double>(cen_smem)) != 0) {
         destroy_problem(p);
         return HWW_ERR_CUDA;
+    }
+    if (d->filter == HWW_FILTER_FOURIER) {
+        const long long kp = std::min<long long>(d->filter_k, (I + 1) / 2);
+        if (fourier_filter_smem_optin(sizeof(double) * ((size_t)I + 1 + 2 * ((size_t)kp + 1))) != 0) {
+            destroy_problem(p);
+            return HWW_ERR_CUDA;
+        }
     }
     int per_sm = p->fp32 ? track_blocks_per_sm_fp32(TRACK_BLOCK, p->track_smem)
                          : track_blocks_per_sm_fp64(TRACK_BLOCK, p->track_smem, p->P2 > 0);

@@ -604,6 +604,63 @@ __global__ void __launch_bounds__(SCAN_T) losm_vjp_kernel(VjpArgs a) {
     }
 }
 
+// Fourier low-pass (Eqs. fft, ifft and the cutoff): the modes of frequency
+// f <= kappa of a real vector x of length M, X_f = sum_m x_m e^{-2 pi i f m / M},
+// give the filtered x~_m = (X_0 + 2 sum_{0<f<M/2} Re(X_f e^{2 pi i f m / M})
+// [+ X_{M/2} e^{i pi m} when kappa reaches M/2]) / M.  Angles are reduced
+// exactly: sincospi(2 ((f m) mod M) / M).  One block per vector (blockIdx.x:
+// 0 phi on cells, 1 F on cells, 2 J on edges) and closure set (blockIdx.y);
+// the block writes the filtered vector and, for phi and F, the ghost values.
+__global__ void fourier_filter_kernel(ClosureArgs a_in) {
+    extern __shared__ double fsh[];  // x (M), then Xr, Xi (kappa' + 1 each)
+    const ClosureArgs a = closure_set(a_in);
+    const int I = a.I;
+    const int c1 = 1 - a.sd->cur;
+    const int which = blockIdx.x;
+    const int M = (which == 2) ? I + 1 : I;
+    const double* in = (which == 0) ? a.rphi : (which == 1) ? a.rF : a.rJ;
+    double* out = (which == 0) ? a.set_phi[c1] + 1 : (which == 1) ? a.set_F[c1] + 1 : a.set_J[c1];
+    const int kp = min(a.kappa, M / 2);
+    double* x = fsh;
+    double* Xr = fsh + M;
+    double* Xi = Xr + (kp + 1);
+    for (int m = threadIdx.x; m < M; m += blockDim.x) x[m] = in[m];
+    __syncthreads();
+    for (int f = threadIdx.x; f <= kp; f += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        long long fm = 0;  // (f m) mod M
+        for (int m = 0; m < M; ++m) {
+            double sn, cs;
+            sincospi(2.0 * (double)fm / (double)M, &sn, &cs);
+            re = re + x[m] * cs;
+            im = im - x[m] * sn;
+            fm += f;
+            if (fm >= M) fm -= M;
+        }
+        Xr[f] = re;
+        Xi[f] = im;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        double acc = Xr[0];
+        for (int f = 1; f <= kp; ++f) {
+            const long long fm = ((long long)f * m) % M;
+            double sn, cs;
+            sincospi(2.0 * (double)fm / (double)M, &sn, &cs);
+            const double t = Xr[f] * cs - Xi[f] * sn;
+            acc = acc + ((2 * f == M) ? t : 2.0 * t);
+        }
+        out[m] = acc / (double)M;
+    }
+    if (which < 2) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            out[-1] = out[0];     // ghost values copy the filtered end cells
+            out[M] = out[M - 1];
+        }
+    }
+}
+
 int small_grid(int n) {
     const int b = (n + 127) / 128;
     return b < 1 ? 1 : (b > 64 ? 64 : b);
@@ -642,8 +699,18 @@ void launch_step_scalars(StepDev* sd, int nbits, unsigned long long seed, int mo
 int launch_closures(const ClosureArgs& a, cudaStream_t s) {
     const unsigned ny = a.nsets > 1 ? (unsigned)a.nsets : 1u;
     closure_kernel<<<dim3(small_grid(a.I + 1), ny), 128, 0, s>>>(a);
-    filter_kernel<<<dim3(small_grid(a.I + 2), ny), 128, 0, s>>>(a);
+    if (a.fourier) {
+        const int kp = a.kappa < (a.I + 1) / 2 ? a.kappa : (a.I + 1) / 2;
+        const size_t smem = sizeof(double) * ((size_t)a.I + 1 + 2 * ((size_t)kp + 1));
+        fourier_filter_kernel<<<dim3(3, ny), 256, smem, s>>>(a);
+    } else {
+        filter_kernel<<<dim3(small_grid(a.I + 2), ny), 128, 0, s>>>(a);
+    }
     return 2;
+}
+
+int fourier_filter_smem_optin(size_t smem) {
+    return (int)cudaFuncSetAttribute(fourier_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 int launch_losm_vjp(const VjpArgs& a, cudaStream_t s) {

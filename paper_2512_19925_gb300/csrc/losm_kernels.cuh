@@ -70,7 +70,8 @@ struct ClosureArgs {
     double v, dt;
     long long N;
     int bc_l, bc_r;
-    int filter_k;
+    int filter_k;                  // MA base (0: no MA filter)
+    int fourier, kappa;            // Fourier low-pass with cutoff kappa instead
     const double* dx;
     const Acc128* cent;
     const Acc128* tl;
@@ -133,6 +134,7 @@ int launch_ww_centers(const WwArgs& a, int lagged, cudaStream_t s);
 void launch_step_scalars(StepDev* sd, int nbits, unsigned long long seed, int mode, unsigned long long* stats,
                          cudaStream_t s);
 int launch_closures(const ClosureArgs& a, cudaStream_t s);
+int fourier_filter_smem_optin(size_t smem);
 int launch_losm_vjp(const VjpArgs& a, cudaStream_t s);
 
 }  // namespace hww
