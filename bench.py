@@ -58,6 +58,41 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Rank r runs the workload with seed r + 1: independent problems (weak
+    scaling, no collective on the data path)."""
+    return 1 + int(rank)
+
+
+class RankReduce:
+    """Whole-job aggregates over the ranks of a weak-scaling run: the slowest
+    rank's time and the summed work (one all-reduce each, outside the timed
+    region); the identity without a process group."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist = dist
+        self.device = device
+
+    def _all(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._all(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._all(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+    def rate(self, units, ms):
+        """Whole-job throughput: the units of all ranks over the slowest rank's time."""
+        return self.sum(units) / (self.max(ms) * 1e-3)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -335,26 +370,15 @@ def main(args):
             pass
 
     hww.load()
-    seed = 1 + rank
+    seed = rank_seed(rank)
     N = args.particles
     with ClockSampler(local) as clk:
         fast = run_path(hww, torch, "fp32", N, seed, args.warmup, args.steps, barrier)
     clocks = clk.summary()
     base = run_path(hww, torch, "fp64", N, seed, args.warmup, args.steps, barrier) if not args.no_fp64 else None
 
-    def reduce_max(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def reduce_sum(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    red = RankReduce(dist, "cuda")
+    reduce_max, reduce_sum = red.max, red.sum
 
     ms = reduce_max(fast["ms"])
     total_segs = reduce_sum(fast["segments"])
