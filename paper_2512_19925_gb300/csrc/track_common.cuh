@@ -12,15 +12,17 @@ namespace hww {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-// One slot per calling lane; one atomic per group of converged lanes.
-__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* cnt) {
+// One slot per calling lane; one atomic per group of converged lanes (a
+// global counter, or a block's shared one).
+template <class T>
+__device__ __forceinline__ T warp_reserve(T* cnt) {
     const unsigned mask = __activemask();
     const int leader = __ffs(mask) - 1;
     const unsigned lane = lane_id();
-    unsigned long long base = 0;
-    if ((int)lane == leader) base = atomicAdd(cnt, (unsigned long long)__popc(mask));
+    T base = 0;
+    if ((int)lane == leader) base = atomicAdd(cnt, (T)__popc(mask));
     base = __shfl_sync(mask, base, leader);
-    return base + (unsigned long long)__popc(mask & ((1u << lane) - 1u));
+    return base + (T)__popc(mask & ((1u << lane) - 1u));
 }
 
 // n consecutive slots per calling lane: lanes asking for the same n share

@@ -74,13 +74,15 @@ __device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P6
     a.rout.jcount[slot] = jcount;
 }
 
-// The event loop over items [item, item_end) with the given stride; b_blk is
-// the variance batch whose row is kept in shared memory (-1: none).
+// The event loop over items [item, item_end): with the given stride, or, when
+// s_next is a block-shared counter, item + the next value of that counter
+// (lanes busy with many daughters then take fewer items); b_blk is the
+// variance batch whose row is kept in shared memory (-1: none).
 // In derivative runs the shared row block after the batch row holds the
 // derivative track-length tallies [P2][I].
 template <bool DERIV>
 __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long item, const long long item_end,
-                                          const long long stride, const int b_blk, long long* sm,
+                                          const long long stride, unsigned* s_next, const int b_blk, long long* sm,
                                           Counters& cnt) {
     const int I = a.I;
     long long* s_tl = sm;
@@ -121,9 +123,15 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
 #pragma unroll
                     for (int j = 0; j < MAX_SCORES; ++j) S[j] = bS[j];
                 }
-            } else if (item < item_end) {
-                const long long i = item;
-                item += stride;
+            } else {
+                long long i;
+                if (s_next) {
+                    i = item + (long long)warp_reserve(s_next);
+                } else {
+                    i = item;
+                    item += stride;
+                }
+                if (i >= item_end) break;
                 if (a.from_bank) {
                     q.id = (uint32_t)i;
                     q.lin = 0;
@@ -183,8 +191,6 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                         }
                     }
                 }
-            } else {
-                break;
             }
             q.inv_mu = 1.0 / q.mu;
             have = true;
@@ -370,15 +376,30 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             q.inv_mu = 1.0 / q.mu;
             cnt.v[ST_SCATTERS]++;
             if (nsec > 1) {
-                // the other emitted particles: records of daughters that take
-                // their own lineages and isotropic directions
+                // the other emitted particles: daughters that take their own
+                // lineages and isotropic directions, expanded by this lane
+                // after the current track, or queued as records when it is
+                // already expanding a parent
                 const uint32_t nx = nsec - 1;
-                const uint32_t nch = (nx + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
-                const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
-                for (uint32_t ch = 0; ch < nch; ++ch) {
-                    const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
-                    const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nsec - j0);
-                    push_record<DERIV>(a, q, S, q.w, e_ev | SECONDARY_EVENT, j0 | FRESH_DIRECTION, jc, b0 + ch);
+                if (jnext >= jend) {
+                    base = q;
+                    base.e = e_ev | SECONDARY_EVENT;
+                    if constexpr (DERIV) {
+#pragma unroll
+                        for (int j = 0; j < MAX_SCORES; ++j) bS[j] = S[j];
+                    }
+                    fresh = true;
+                    jnext = 1;
+                    jend = nsec;
+                } else {
+                    const uint32_t nch = (nx + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+                    const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
+                    for (uint32_t ch = 0; ch < nch; ++ch) {
+                        const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
+                        const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nsec - j0);
+                        push_record<DERIV>(a, q, S, q.w, e_ev | SECONDARY_EVENT, j0 | FRESH_DIRECTION, jc,
+                                           b0 + ch);
+                    }
                 }
                 cnt.v[ST_DAUGHTERS] += nx;
             }
@@ -405,12 +426,27 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 const double wd = q.w / (double)nd;
                 cnt.v[ST_SPLIT_EVENTS]++;
                 cnt.v[ST_DAUGHTERS] += nd - 1;
-                const uint32_t nch = (nd - 1 + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
-                const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
-                for (uint32_t ch = 0; ch < nch; ++ch) {
-                    const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
-                    const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
-                    push_record<DERIV>(a, q, S, wd, e_ev, j0, jc, b0 + ch);
+                if (jnext >= jend) {
+                    // daughters 1..nd-1 follow the current track on this lane
+                    // (same block, so their batch row stays in shared memory)
+                    base = q;
+                    base.w = wd;
+                    base.e = e_ev;
+                    if constexpr (DERIV) {
+#pragma unroll
+                        for (int j = 0; j < MAX_SCORES; ++j) bS[j] = S[j];
+                    }
+                    fresh = false;
+                    jnext = 1;
+                    jend = nd;
+                } else {
+                    const uint32_t nch = (nd - 1 + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+                    const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
+                    for (uint32_t ch = 0; ch < nch; ++ch) {
+                        const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
+                        const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
+                        push_record<DERIV>(a, q, S, wd, e_ev, j0, jc, b0 + ch);
+                    }
                 }
                 q.w = wd;
                 q.lin = lineage_hash(q.lin, e_ev, 0);
@@ -447,7 +483,9 @@ template <bool DERIV>
 // the extra warps hide.
 __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
     extern __shared__ long long sm[];
+    __shared__ unsigned s_next;
     const int I = a.I;
+    if (threadIdx.x == 0) s_next = 0;
     const int rows = DERIV ? TALLY_ROWS + a.P2 : TALLY_ROWS;
     for (int i = threadIdx.x; i < rows * I; i += blockDim.x) sm[i] = 0;
     __syncthreads();
@@ -457,8 +495,13 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
     const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
     // wave 0: each block takes a contiguous id range of [bank_lo, bank_hi), so
     // nearly all of its segments fall in one variance batch (kept in shared
-    // memory); record waves: grid-stride over the records
+    // memory), and its lanes take the range's items from a shared counter
+    // (splits leave the daughters with the splitting lane, so lanes carry
+    // uneven work); record waves: grid-stride over the records.  More,
+    // smaller ranges balance the blocks better but cost more tally flushes;
+    // one range per resident block measured fastest.
     long long stride, item, item_end;
+    unsigned* dyn = nullptr;
     int b_blk = -1;
     if (a.from_bank) {
         const long long lo = a.bank_lo;
@@ -466,16 +509,17 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
         const long long len = hi > lo ? hi - lo : 0;
         const long long chunk = (len + gridDim.x - 1) / gridDim.x;
         const long long first = lo + (long long)blockIdx.x * chunk;
-        item = first + threadIdx.x;
+        item = first;
         item_end = min(hi, first + chunk);
-        stride = blockDim.x;
+        stride = 0;
+        dyn = &s_next;
         if (first < hi) b_blk = batch_of((uint32_t)first, batch_div(a.B, a.N));
     } else {
         item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         item_end = n_use;
         stride = (long long)gridDim.x * blockDim.x;
     }
-    run_items<DERIV>(a, item, item_end, stride, b_blk, sm, cnt);
+    run_items<DERIV>(a, item, item_end, stride, dyn, b_blk, sm, cnt);
     __syncthreads();
     flush_tallies(sm, I, a.tl);
     if constexpr (DERIV) {
@@ -496,6 +540,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<d
     __shared__ TrackArgs<double> A;
     __shared__ long long s_t;
     __shared__ int s_p;
+    __shared__ unsigned s_next;
     Counters cnt;
     cnt.zero();
     const long long total = plan.tile_off[plan.P];
@@ -514,6 +559,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<d
             }
             s_t = t;
             s_p = p;
+            s_next = 0;
         }
         __syncthreads();
         const long long t = s_t;
@@ -538,7 +584,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<d
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
         const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, batch_div(A.B, A.N)) : -1;
-        run_items<false>(A, i0 + threadIdx.x, i1, blockDim.x, b_tile, sm, cnt);
+        run_items<false>(A, i0, i1, 0, &s_next, b_tile, sm, cnt);
         __syncthreads();
         if (b_tile >= 0)
             for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
