@@ -72,9 +72,10 @@ struct hww_problem {
     size_t grp_bytes = 0;
     unsigned long long* gw = nullptr;
     uint32_t *gcnt = nullptr, *gcur = nullptr;
-    unsigned long long *goff = nullptr, *goff_w = nullptr, *tile_c = nullptr, *tile_w = nullptr;
+    GroupRec* gro = nullptr;  // [N+1] census group records from the scan
+    unsigned long long *tile_c = nullptr, *tile_w = nullptr;
     uint32_t* member = nullptr;
-    unsigned long long* cpre = nullptr;    // comb prefix of members of multi-member groups (census-sized)
+    unsigned long long* cpre = nullptr;    // comb prefix C0 of every census particle (census-sized)
     uint32_t* glist = nullptr;             // ids of comb groups of 3+ members by size class (census-sized)
     // closures and LOSM
     // two closure sets (phi I+2, J I+1, F I+2, P 2): `cur` holds the
@@ -420,8 +421,7 @@ CombArgs<Real> comb_args(hww_problem* p, Banks<Real>& b) {
     c.cid = b.cen.id;
     c.clin = b.cen.lin;
     c.gcnt = p->gcnt;
-    c.goff = p->goff;
-    c.goff_w = p->goff_w;
+    c.gro = p->gro;
     c.gcur = p->gcur;
     c.member = p->member;
     c.cwfx = b.cen.wfx;
@@ -452,8 +452,7 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     s.n = p->N;
     s.tile_c = p->tile_c;
     s.tile_w = p->tile_w;
-    s.out_c = p->goff;
-    s.out_w = p->goff_w;
+    s.out = p->gro;
     launch_group_scan(s, p->stream);
     HWW_CK(cudaGetLastError());
     p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
@@ -929,8 +928,8 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         (s = dalloc(p, &p->d_inv_sigt, I)) || (s = dalloc(p, &p->d_c, I)) || (s = dalloc(p, &p->d_siga, I)) ||
         (s = dalloc(p, &p->d_dxf, I)) || (s = dalloc(p, &p->d_inv_sigt_f, I)) || (s = dalloc(p, &p->d_region, I)) ||
         (s = dalloc(p, &p->ww_c, I)) || (s = dalloc(p, &p->ww_hi, I)) || (s = dalloc(p, &p->ww_lo, I)) ||
-        (s = dalloc(p, &p->ww_override, I)) || (s = dalloc(p, &p->d_cellf, I)) || (s = dalloc(p, &p->d_ww_hl, I)) || (s = dalloc(p, &p->goff, p->N + 1)) ||
-        (s = dalloc(p, &p->goff_w, p->N + 1)) || (s = dalloc(p, &p->tile_c, ntiles + 1)) ||
+        (s = dalloc(p, &p->ww_override, I)) || (s = dalloc(p, &p->d_cellf, I)) || (s = dalloc(p, &p->d_ww_hl, I)) || (s = dalloc(p, &p->gro, p->N + 1)) ||
+        (s = dalloc(p, &p->tile_c, ntiles + 1)) ||
         (s = dalloc(p, &p->tile_w, ntiles + 1)) ||
         (s = dalloc(p, &p->cl_phi[0], I + 2)) || (s = dalloc(p, &p->cl_J[0], I + 1)) ||
         (s = dalloc(p, &p->cl_F[0], I + 2)) || (s = dalloc(p, &p->cl_P[0], 2)) ||

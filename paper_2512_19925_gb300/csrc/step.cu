@@ -99,10 +99,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_tile_sums_kernel(ScanArgs a, 
         }
         carry = padd(carry, tot);
     }
-    if (threadIdx.x == 0) {
-        a.out_c[a.n] = carry.c;
-        a.out_w[a.n] = carry.w;
-    }
+    if (threadIdx.x == 0) a.out[a.n] = GroupRec{carry.w, (uint32_t)carry.c, 0u};
 }
 
 __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
@@ -117,10 +114,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
     Pair run{a.tile_c[blockIdx.x] + s.c, a.tile_w[blockIdx.x] + s.w};
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         const long long i = base + (long long)threadIdx.x * SCAN_ITEMS + k;
-        if (i < a.n) {
-            a.out_c[i] = run.c;
-            a.out_w[i] = run.w;
-        }
+        if (i < a.n) a.out[i] = GroupRec{run.w, (uint32_t)run.c, (uint32_t)v[k].c};
         run = padd(run, v[k]);
     }
 }
@@ -128,16 +122,17 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
 // ---------------------------------------------------------------------------
 // Comb
 //
-// The census particles of one source id form a group (count gcnt[id], start
-// goff[id] in the member list, fixed-point weight offset goff_w[id] from the
-// scan).  Within a group the canonical order is (lineage key, census slot).
-// Census particle j owns the teeth in [C0_j, C0_j + w_j), C0_j = goff_w[id]
-// plus the weights of the group members before it.  Most groups have one
-// member (C0_j = goff_w[id]); the prefix of a larger group is found once per
-// group and stored per member: pairs by one thread, groups of up to 32 by a
-// warp segment of 4 to 32 lanes (a rank count over shuffles), larger ones by
-// a block (bitonic sort and scan in shared memory).  The copies are then
-// written in census order, reading the census bank coalesced.
+// The census particles of one source id form a group (its record from the
+// scan: member count, start in the member list, fixed-point weight offset).
+// Within a group the canonical order is (lineage key, census slot).  Census
+// particle j owns the teeth in [C0_j, C0_j + w_j), C0_j = the group's weight
+// offset plus the weights of the group members before it.  Most groups have
+// one member: its C0 is set by the scatter pass, which lists only the members
+// of larger groups; their prefixes are found once per group: pairs by one
+// thread, groups of up to 32 by a warp segment of 4 to 32 lanes (a rank count
+// over shuffles), larger ones by a block (bitonic sort and scan in shared
+// memory).  The copies are then written in census order, reading the census
+// bank and the stored prefixes coalesced.
 // ---------------------------------------------------------------------------
 constexpr int NCLASS = 4;      // group size classes handled by warp segments of 4, 8, 16, 32 lanes
 constexpr int BIG_CAP = 2048;  // members a block sorts in shared memory
@@ -150,7 +145,12 @@ __global__ void comb_scatter_kernel(CombArgs<Real> a) {
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
         const uint32_t id = a.cid[j];
-        const unsigned long long slot = a.goff[id] + atomicAdd(&a.gcur[id], 1u);
+        const GroupRec g = a.gro[id];
+        if (g.cnt == 1) {
+            a.cpre[j] = g.offw;
+            continue;
+        }
+        const unsigned long long slot = (unsigned long long)g.off + atomicAdd(&a.gcur[id], 1u);
         a.member[slot] = (uint32_t)j;
     }
 }
@@ -173,12 +173,13 @@ __global__ void comb_groups_kernel(CombArgs<Real> a) {
          id += (long long)gridDim.x * blockDim.x) {
         const uint32_t g = a.gcnt[id];
         if (g < 2) continue;
-        const unsigned long long base = a.goff[id];
         if (g == 2) {
+            const GroupRec G = a.gro[id];
+            const unsigned long long base = G.off;
             const uint32_t j0 = a.member[base], j1 = a.member[base + 1];
             const uint64_t l0 = a.clin[j0], l1 = a.clin[j1];
             const bool first0 = key_less(l0, j0, l1, j1);
-            const unsigned long long C = a.goff_w[id];
+            const unsigned long long C = G.offw;
             a.cpre[first0 ? j0 : j1] = C;
             a.cpre[first0 ? j1 : j0] = C + a.cwfx[first0 ? j0 : j1];
             if (l0 == l1) ++coll;
@@ -215,10 +216,10 @@ __global__ void comb_seg_kernel(CombArgs<Real> a, int k) {
         uint32_t g = 0;
         unsigned long long base = 0, C = 0;
         if (e < n) {
-            const uint32_t id = list[e];
-            g = a.gcnt[id];
-            base = a.goff[id];
-            C = a.goff_w[id];
+            const GroupRec G = a.gro[list[e]];
+            g = G.cnt;
+            base = G.off;
+            C = G.offw;
         }
         uint64_t lin = ~0ull;
         uint32_t jj = 0xFFFFFFFFu;
@@ -256,10 +257,10 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
     const uint32_t* list = a.glist + a.glist_off[NCLASS];
     unsigned long long coll = 0;
     for (unsigned long long e = blockIdx.x; e < nbig; e += gridDim.x) {
-        const uint32_t id = list[e];
-        const uint32_t g = a.gcnt[id];
-        const unsigned long long base = a.goff[id];
-        const unsigned long long C = a.goff_w[id];
+        const GroupRec G = a.gro[list[e]];
+        const uint32_t g = G.cnt;
+        const unsigned long long base = G.off;
+        const unsigned long long C = G.offw;
         if (g > (uint32_t)BIG_CAP) {
             for (uint32_t t = threadIdx.x; t < g; t += blockDim.x) {
                 const uint32_t jt = a.member[base + t];
@@ -430,7 +431,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
     __syncthreads();
     const long long m = (long long)*a.ncensus_ptr;
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
-    const unsigned long long W = a.goff_w[a.N];
+    const unsigned long long W = a.gro[a.N].offw;
     const unsigned U = a.sd->U_comb;
     const double tscale = a.sd->tscale;
     const ToothScale ts = tooth_scale(W, a.N);
@@ -447,8 +448,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
                 sadd(&s_cen[2 * I + k], g.s2);
             }
         }
-        const uint32_t id = a.cid[j];
-        const unsigned long long C0 = (a.gcnt[id] > 1) ? a.cpre[j] : a.goff_w[id];
+        const unsigned long long C0 = a.cpre[j];
         const unsigned long long wj = a.cwfx[j];
         const long long k0 = first_tooth(C0, W, a.N, U, ts);
         const long long k1 = first_tooth(C0 + wj, W, a.N, U, ts);
@@ -472,10 +472,9 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
         if (s_cen[i] != 0) add128(&a.cent[i], s_cen[i]);
 }
 
-__global__ void comb_finalize_kernel(StepDev* sd, const unsigned long long* goff_w,
-                                     const unsigned long long* ncensus_ptr, long long N, long long cen_cap,
-                                     unsigned* err) {
-    const unsigned long long W = goff_w[N];
+__global__ void comb_finalize_kernel(StepDev* sd, const GroupRec* gro, const unsigned long long* ncensus_ptr,
+                                     long long N, long long cen_cap, unsigned* err) {
+    const unsigned long long W = gro[N].offw;
     const unsigned long long m = *ncensus_ptr;
     sd->ncensus = m;
     sd->W = W;
@@ -530,7 +529,7 @@ int census_tally_smem_optin(size_t smem) {
 
 template <class Real>
 void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s) {
-    comb_finalize_kernel<<<1, 1, 0, s>>>(a.sd, a.goff_w, a.ncensus_ptr, a.N, a.cen_cap, a.err);
+    comb_finalize_kernel<<<1, 1, 0, s>>>(a.sd, a.gro, a.ncensus_ptr, a.N, a.cen_cap, a.err);
 }
 
 template <class Real>

@@ -4,14 +4,23 @@
 
 namespace hww {
 
+// One source id's census group after the scan, read with one 16-byte load:
+// exclusive prefix of the group weights (comb scale) and of the member
+// counts over the ids before it, and its own member count.  Census slots are
+// 32-bit (member lists hold them as such), so are the counts.
+struct __align__(16) GroupRec {
+    unsigned long long offw;
+    uint32_t off;
+    uint32_t cnt;
+};
+
 struct ScanArgs {
     const uint32_t* cnt;
     const unsigned long long* w;
     long long n;
     unsigned long long* tile_c;
     unsigned long long* tile_w;
-    unsigned long long* out_c;  // n+1 entries
-    unsigned long long* out_w;  // n+1 entries
+    GroupRec* out;  // n+1 entries; entry n holds the totals
 };
 
 template <class Real>
@@ -27,8 +36,7 @@ struct CombArgs {
     const uint32_t* cid;
     const uint64_t* clin;
     const uint32_t* gcnt;
-    const unsigned long long* goff;
-    const unsigned long long* goff_w;
+    const GroupRec* gro;  // [N+1] group records (entry N: totals)
     uint32_t* gcur;
     uint32_t* member;
     Real* bx;
@@ -37,7 +45,7 @@ struct CombArgs {
     unsigned long long* stats;
     unsigned* err;
     const unsigned long long* cwfx;  // [cen_cap] census weights in fixed point (comb scale)
-    unsigned long long* cpre;        // [cen_cap] prefix C0 of members of multi-member groups
+    unsigned long long* cpre;        // [cen_cap] comb prefix C0 of every census particle
     uint32_t* glist;                 // ids of groups of 3+ members, by size class (5 lists)
     long long glist_off[5];          // start of each class's list in glist
     unsigned long long* glist_n;     // [5] list lengths (cleared with the step's accumulators)

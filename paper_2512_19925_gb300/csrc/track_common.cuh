@@ -12,6 +12,14 @@ namespace hww {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// Daughters of a split (or extra particles of a multiplying collision) that
+// the single-problem kernels track on the splitting lane, after its current
+// track, when the lane holds no other pending parent; the rest go to the
+// record queue in chunks.  The persistent batched kernels, which end every
+// tile with a block barrier, queue them all (a lane with pending daughters
+// would hold its block at the barrier).
+constexpr uint32_t LOCAL_DAUGHTERS = 32;
+
 // One slot per calling lane; one atomic per group of converged lanes (a
 // global counter, or a block's shared one).
 template <class T>

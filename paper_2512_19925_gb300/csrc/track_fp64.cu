@@ -80,7 +80,7 @@ __device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P6
 // variance batch whose row is kept in shared memory (-1: none).
 // In derivative runs the shared row block after the batch row holds the
 // derivative track-length tallies [P2][I].
-template <bool DERIV>
+template <bool DERIV, uint32_t LOCAL_MAX>
 __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long item, const long long item_end,
                                           const long long stride, unsigned* s_next, const int b_blk, long long* sm,
                                           Counters& cnt) {
@@ -381,7 +381,8 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 // after the current track, or queued as records when it is
                 // already expanding a parent
                 const uint32_t nx = nsec - 1;
-                if (jnext >= jend) {
+                uint32_t jr = 1;  // the first daughter that goes to the record queue
+                if (LOCAL_MAX > 0 && jnext >= jend) {
                     base = q;
                     base.e = e_ev | SECONDARY_EVENT;
                     if constexpr (DERIV) {
@@ -390,12 +391,14 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     }
                     fresh = true;
                     jnext = 1;
-                    jend = nsec;
-                } else {
-                    const uint32_t nch = (nx + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+                    jend = min(nsec, 1u + LOCAL_MAX);
+                    jr = jend;
+                }
+                if (jr < nsec) {
+                    const uint32_t nch = (nsec - jr + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
                     const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
                     for (uint32_t ch = 0; ch < nch; ++ch) {
-                        const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
+                        const uint32_t j0 = jr + ch * SPLIT_CHUNK;
                         const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nsec - j0);
                         push_record<DERIV>(a, q, S, q.w, e_ev | SECONDARY_EVENT, j0 | FRESH_DIRECTION, jc,
                                            b0 + ch);
@@ -426,9 +429,12 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 const double wd = q.w / (double)nd;
                 cnt.v[ST_SPLIT_EVENTS]++;
                 cnt.v[ST_DAUGHTERS] += nd - 1;
-                if (jnext >= jend) {
-                    // daughters 1..nd-1 follow the current track on this lane
-                    // (same block, so their batch row stays in shared memory)
+                uint32_t jr = 1;  // the first daughter that goes to the record queue
+                if (LOCAL_MAX > 0 && jnext >= jend) {
+                    // up to LOCAL_MAX daughters follow the current track on
+                    // this lane (same block, so their batch row stays in
+                    // shared memory); the bound keeps a large split from
+                    // holding one lane while the rest of its block waits
                     base = q;
                     base.w = wd;
                     base.e = e_ev;
@@ -438,12 +444,14 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     }
                     fresh = false;
                     jnext = 1;
-                    jend = nd;
-                } else {
-                    const uint32_t nch = (nd - 1 + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+                    jend = min(nd, 1u + LOCAL_MAX);
+                    jr = jend;
+                }
+                if (jr < nd) {
+                    const uint32_t nch = (nd - jr + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
                     const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
                     for (uint32_t ch = 0; ch < nch; ++ch) {
-                        const uint32_t j0 = 1 + ch * SPLIT_CHUNK;
+                        const uint32_t j0 = jr + ch * SPLIT_CHUNK;
                         const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
                         push_record<DERIV>(a, q, S, wd, e_ev, j0, jc, b0 + ch);
                     }
@@ -519,7 +527,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
         item_end = n_use;
         stride = (long long)gridDim.x * blockDim.x;
     }
-    run_items<DERIV>(a, item, item_end, stride, dyn, b_blk, sm, cnt);
+    run_items<DERIV, LOCAL_DAUGHTERS>(a, item, item_end, stride, dyn, b_blk, sm, cnt);
     __syncthreads();
     flush_tallies(sm, I, a.tl);
     if constexpr (DERIV) {
@@ -584,7 +592,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<d
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
         const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, batch_div(A.B, A.N)) : -1;
-        run_items<false>(A, i0, i1, 0, &s_next, b_tile, sm, cnt);
+        run_items<false, 0>(A, i0, i1, 0, &s_next, b_tile, sm, cnt);
         __syncthreads();
         if (b_tile >= 0)
             for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
