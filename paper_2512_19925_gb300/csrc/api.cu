@@ -24,7 +24,7 @@ using namespace hww;
 
 namespace {
 
-constexpr int TRACK_BLOCK = 256;
+constexpr int TRACK_BLOCK = TRACK_THREADS;
 constexpr int MAX_CELLS = 4000;
 constexpr int MAX_WAVES = 100000;
 constexpr int MAX_REGROW = 12;
@@ -237,8 +237,8 @@ hww_status alloc_banks(hww_problem* p, Banks<Real>& b) {
     const long long C = p->cen_cap, Q = p->q_cap;
     if ((s = dalloc(p, &b.cen.x, C, true)) || (s = dalloc(p, &b.cen.mu, C, true)) ||
         (s = dalloc(p, &b.cen.w, C, true)) || (s = dalloc(p, &b.cen.cell, C, true)) ||
-        (s = dalloc(p, &b.cen.id, C, true)) || (s = dalloc(p, &b.cen.lin, C, true)) ||
-        (s = dalloc(p, &p->member, C, true)) || (s = dalloc(p, &b.cen.wfx, C, true)) ||
+        (s = dalloc(p, &b.cen.id, C, true)) || (s = dalloc(p, &b.cen.lw, C, true)) ||
+        (s = dalloc(p, &p->member, C, true)) ||
         (s = dalloc(p, &p->cpre, C, true)) || (s = dalloc(p, &p->glist, glist_len(C), true)))
         return s;
     b.cen.cap = C;
@@ -303,6 +303,7 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b) {
     a.I = p->I;
     a.B = p->B;
     a.N = p->N;
+    a.batch_m = p->N > 0 ? ~0ull / (unsigned long long)p->N : 0ull;
     a.emax = p->emax;
     a.bc_l = p->d.bc_left;
     a.bc_r = p->d.bc_right;
@@ -419,12 +420,11 @@ CombArgs<Real> comb_args(hww_problem* p, Banks<Real>& b) {
     c.cw = b.cen.w;
     c.ccell = b.cen.cell;
     c.cid = b.cen.id;
-    c.clin = b.cen.lin;
+    c.clw = b.cen.lw;
     c.gcnt = p->gcnt;
     c.gro = p->gro;
     c.gcur = p->gcur;
     c.member = p->member;
-    c.cwfx = b.cen.wfx;
     c.cpre = p->cpre;
     c.glist = p->glist;
     glist_offsets(p->cen_cap, c.glist_off);
@@ -1486,8 +1486,8 @@ hww_status get_census(const hww_problem* p, double* x, double* mu, double* w, in
         e = cudaMemcpyAsync(id, p->fp32 ? p->b32.cen.id : p->b64.cen.id, sizeof(uint32_t) * m,
                             cudaMemcpyDeviceToHost, p->stream);
     if (lin && e == cudaSuccess)
-        e = cudaMemcpyAsync(lin, p->fp32 ? p->b32.cen.lin : p->b64.cen.lin, sizeof(uint64_t) * m,
-                            cudaMemcpyDeviceToHost, p->stream);
+        e = cudaMemcpy2DAsync(lin, sizeof(uint64_t), p->fp32 ? (const void*)p->b32.cen.lw : (const void*)p->b64.cen.lw,
+                              sizeof(LinW), sizeof(uint64_t), (size_t)m, cudaMemcpyDeviceToHost, p->stream);
     cudaFreeAsync(tmp, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     return cuda_status(e);

@@ -19,6 +19,7 @@
 namespace hww {
 
 constexpr int SPLIT_CHUNK = 8;
+constexpr int TRACK_THREADS = 256;  // threads per tracking block
 // A record's jstart carries FRESH_DIRECTION for the extra particles of a
 // multiplying collision: each daughter then samples its own isotropic
 // direction.  Their lineages hash the event with SECONDARY_EVENT set.
@@ -52,6 +53,7 @@ struct StepDev {
     double wbar;     // weight of each start-bank particle
     double tscale;   // 2^S, tally fixed-point scale
     double cscale;   // 2^Sc, comb weight fixed-point scale
+    long long Wbar;  // wbar at the tally scale, round(wbar 2^S)
     int S, Sc;
     unsigned U_comb; // comb offset word: teeth at (k + (2U+1)/2^33) W / N
     unsigned k0, k1; // Philox key of the step: (seed_lo, seed_hi ^ n)
@@ -66,6 +68,12 @@ struct StepDev {
     unsigned long long nbank;      // start-bank size
     unsigned long long W;          // total census weight (fixed point)
     unsigned long long ncensus;    // census bank size of the step
+};
+
+// a census particle's comb key and weight, read together by the comb
+struct __align__(16) LinW {
+    uint64_t lin;              // lineage key
+    unsigned long long wfx;    // weight in fixed point at the comb scale 2^Sc
 };
 
 template <class Real>
@@ -92,8 +100,7 @@ struct CenQ {
     double* w;
     int32_t* cell;
     uint32_t* id;
-    uint64_t* lin;
-    unsigned long long* wfx;  // weight in fixed point at the comb scale 2^Sc
+    LinW* lw;  // lineage key and weight at the comb scale 2^Sc, one 16-byte word
     double* S;  // [P2][cap] scores (derivative runs only)
     unsigned long long* count;
     long long cap;
@@ -103,6 +110,7 @@ template <class Real>
 struct TrackArgs {
     int I, B, emax;
     long long N;      // source particles per step (variance batches)
+    unsigned long long batch_m;  // floor((2^64 - 1) / N): the variance-batch divisor
     int from_bank;
     long long bank_lo, bank_hi;  // wave 0 takes start-bank items [bank_lo, min(bank_hi, size))
     int bc_l, bc_r;

@@ -363,6 +363,7 @@ __global__ void step_scalars_kernel(StepDev* sd, int nbits, unsigned long long s
     sd->Sc = 59 - E - nbits;
     sd->tscale = pow2(sd->S);
     sd->cscale = pow2(sd->Sc);
+    sd->Wbar = to_fixed(sd->wbar, sd->tscale);
     uint32_t r[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xC0B0u};
     philox4x32_10(r, sd->k0, sd->k1);
     sd->U_comb = r[1];

@@ -164,37 +164,54 @@ __device__ __forceinline__ int size_class(uint32_t g) {
     return g <= 4 ? 0 : g <= 8 ? 1 : g <= 16 ? 2 : g <= 32 ? 3 : 4;
 }
 
-// one thread per source id: a pair is ordered on the spot; groups of three
-// or more go to the list of their size class
+// one block per contiguous id range: a pair is ordered on the spot; groups
+// of three or more go to the list of their size class, in two passes over
+// the range (count, then write) so that each block reserves its list space
+// with one global atomic per class
 template <class Real>
 __global__ void comb_groups_kernel(CombArgs<Real> a) {
+    __shared__ unsigned long long s_cnt[NCLASS + 1], s_pos[NCLASS + 1];
+    const long long chunk = (a.N + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = min(a.N, lo + chunk);
+    if (threadIdx.x <= NCLASS) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
     unsigned long long coll = 0;
-    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < a.N;
-         id += (long long)gridDim.x * blockDim.x) {
+    unsigned c[NCLASS + 1] = {};
+    for (long long id = lo + threadIdx.x; id < hi; id += blockDim.x) {
         const uint32_t g = a.gcnt[id];
         if (g < 2) continue;
         if (g == 2) {
             const GroupRec G = a.gro[id];
             const unsigned long long base = G.off;
             const uint32_t j0 = a.member[base], j1 = a.member[base + 1];
-            const uint64_t l0 = a.clin[j0], l1 = a.clin[j1];
+            const LinW p0 = a.clw[j0], p1 = a.clw[j1];
+            const uint64_t l0 = p0.lin, l1 = p1.lin;
             const bool first0 = key_less(l0, j0, l1, j1);
             const unsigned long long C = G.offw;
             a.cpre[first0 ? j0 : j1] = C;
-            a.cpre[first0 ? j1 : j0] = C + a.cwfx[first0 ? j0 : j1];
+            a.cpre[first0 ? j1 : j0] = C + (first0 ? p0.wfx : p1.wfx);
             if (l0 == l1) ++coll;
             continue;
         }
-        // one atomic per class among the converged lanes
         const int k = size_class(g);
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, k);
-        const unsigned lane = threadIdx.x & 31u;
-        const int leader = __ffs(peers) - 1;
-        unsigned long long b = 0;
-        if ((int)lane == leader) b = atomicAdd(&a.glist_n[k], (unsigned long long)__popc(peers));
-        b = __shfl_sync(peers, b, leader);
-        a.glist[a.glist_off[k] + b + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)id;
+#pragma unroll
+        for (int kk = 0; kk <= NCLASS; ++kk) c[kk] += (kk == k) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k <= NCLASS; ++k)
+        if (c[k]) atomicAdd(&s_cnt[k], (unsigned long long)c[k]);
+    __syncthreads();
+    if (threadIdx.x <= NCLASS) {
+        const unsigned long long n = s_cnt[threadIdx.x];
+        s_pos[threadIdx.x] = n ? atomicAdd(&a.glist_n[threadIdx.x], n) : 0ull;
+    }
+    __syncthreads();
+    for (long long id = lo + threadIdx.x; id < hi; id += blockDim.x) {
+        const uint32_t g = a.gcnt[id];
+        if (g < 3) continue;
+        const int k = size_class(g);
+        a.glist[a.glist_off[k] + atomicAdd(&s_pos[k], 1ull)] = (uint32_t)id;
     }
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
@@ -226,8 +243,9 @@ __global__ void comb_seg_kernel(CombArgs<Real> a, int k) {
         unsigned long long w = 0;
         if ((uint32_t)li < g) {
             jj = a.member[base + li];
-            lin = a.clin[jj];
-            w = a.cwfx[jj];
+            const LinW x = a.clw[jj];
+            lin = x.lin;
+            w = x.wfx;
         }
         unsigned long long C0 = 0;
 #pragma unroll
@@ -264,13 +282,14 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
         if (g > (uint32_t)BIG_CAP) {
             for (uint32_t t = threadIdx.x; t < g; t += blockDim.x) {
                 const uint32_t jt = a.member[base + t];
-                const uint64_t lt = a.clin[jt];
+                const uint64_t lt = a.clw[jt].lin;
                 unsigned long long C0 = C;
                 for (uint32_t u = 0; u < g; ++u) {
                     const uint32_t ju = a.member[base + u];
-                    const uint64_t lu = a.clin[ju];
+                    const LinW xu = a.clw[ju];
+                    const uint64_t lu = xu.lin;
                     if (key_less(lu, ju, lt, jt)) {
-                        C0 += a.cwfx[ju];
+                        C0 += xu.wfx;
                         if (lu == lt) ++coll;
                     }
                 }
@@ -284,7 +303,7 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
             if (i < (int)g) {
                 const uint32_t jj = a.member[base + i];
                 s_j[i] = jj;
-                s_lin[i] = a.clin[jj];
+                s_lin[i] = a.clw[jj].lin;
             } else {  // padding sorts last
                 s_lin[i] = ~0ull;
                 s_j[i] = 0xFFFFFFFFu;
@@ -314,7 +333,7 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
         const int per = (P + BIG_T - 1) / BIG_T;
         const int i0 = threadIdx.x * per, i1 = min((int)g, i0 + per);
         unsigned long long run = 0;
-        for (int i = i0; i < i1; ++i) run += a.cwfx[s_j[i]];
+        for (int i = i0; i < i1; ++i) run += a.clw[s_j[i]].wfx;
         s_part[threadIdx.x] = run;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -332,7 +351,7 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
             for (int b = i - 1; b >= 0 && s_lin[b] == s_lin[i]; --b) ++coll;
             const uint32_t jj = s_j[i];
             a.cpre[jj] = C0;
-            C0 += a.cwfx[jj];
+            C0 += a.clw[jj].wfx;
         }
         __syncthreads();
     }
@@ -449,7 +468,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
             }
         }
         const unsigned long long C0 = a.cpre[j];
-        const unsigned long long wj = a.cwfx[j];
+        const unsigned long long wj = a.clw[j].wfx;
         const long long k0 = first_tooth(C0, W, a.N, U, ts);
         const long long k1 = first_tooth(C0 + wj, W, a.N, U, ts);
         if (k1 <= k0) continue;

@@ -34,7 +34,7 @@ struct CombArgs {
     const double* cw;
     const int32_t* ccell;
     const uint32_t* cid;
-    const uint64_t* clin;
+    const LinW* clw;  // [cen_cap] lineage keys and comb weights
     const uint32_t* gcnt;
     const GroupRec* gro;  // [N+1] group records (entry N: totals)
     uint32_t* gcur;
@@ -44,7 +44,6 @@ struct CombArgs {
     int32_t* bcell;
     unsigned long long* stats;
     unsigned* err;
-    const unsigned long long* cwfx;  // [cen_cap] census weights in fixed point (comb scale)
     unsigned long long* cpre;        // [cen_cap] comb prefix C0 of every census particle
     uint32_t* glist;                 // ids of groups of 3+ members, by size class (5 lists)
     long long glist_off[5];          // start of each class's list in glist

@@ -81,19 +81,13 @@ __device__ __forceinline__ Agg3 warp_agg3(int key, long long v0, long long v1, l
 }
 
 // variance batch of a source id: contiguous id ranges, b = floor(id B / N),
-// without a division: q = (x m) / 2^64 with m = floor((2^64 - 1) / N) is
-// floor(x / N) or one less (x = id B < 2^37), and one comparison decides
-struct BatchDiv {
-    unsigned long long N, m;
-    int B;
-};
-__device__ __forceinline__ BatchDiv batch_div(int B, long long N) {
-    return BatchDiv{(unsigned long long)N, ~0ull / (unsigned long long)N, B};
-}
-__device__ __forceinline__ int batch_of(uint32_t id, const BatchDiv& d) {
-    const unsigned long long x = (unsigned long long)id * (unsigned long long)d.B;
-    unsigned long long q = __umul64hi(x, d.m);
-    if ((q + 1) * d.N <= x) ++q;
+// without a division: q = (x m) / 2^64 with m = floor((2^64 - 1) / N) (from
+// the host) is floor(x / N) or one less (x = id B < 2^37), and one
+// comparison decides
+__device__ __forceinline__ int batch_of(uint32_t id, int B, long long N, unsigned long long m) {
+    const unsigned long long x = (unsigned long long)id * (unsigned long long)B;
+    unsigned long long q = __umul64hi(x, m);
+    if ((q + 1) * (unsigned long long)N <= x) ++q;
     return (int)q;
 }
 
@@ -109,8 +103,13 @@ struct Counters {
     }
 };
 
-// block reduction of the per-thread counters into the global 64-bit stats
+// block reduction of the per-thread counters into the global 64-bit stats;
+// segments and scatters are not counted in the event loops but follow from
+// the event counts (every segment ends in a census, a crossing or a
+// collision; a collision that emits a particle is a scatter)
 __device__ __forceinline__ void flush_counters(Counters& c, unsigned long long* stats) {
+    c.v[ST_SEGMENTS] = c.v[ST_CENSUS] + c.v[ST_CROSSINGS] + c.v[ST_COLLISIONS];
+    c.v[ST_SCATTERS] = c.v[ST_COLLISIONS] - c.v[ST_ABSORBED];
     __shared__ unsigned long long red[ST_COUNT];
     if (threadIdx.x < ST_COUNT) red[threadIdx.x] = 0;
     __syncthreads();

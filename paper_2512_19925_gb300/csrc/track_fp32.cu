@@ -32,6 +32,40 @@ struct P32 {
     uint32_t e;
 };
 
+// The pending parent of a lane (the record whose daughters it expands), kept
+// in shared memory, one column per thread: it is written at a split and read
+// once per daughter, and registers are what limits the resident warps.
+struct PendingParent {
+    float xo[TRACK_THREADS], mu[TRACK_THREADS], tau[TRACK_THREADS];
+    double w[TRACK_THREADS];
+    long long W[TRACK_THREADS];
+    int cell[TRACK_THREADS];
+    uint32_t id[TRACK_THREADS], e[TRACK_THREADS];
+    uint64_t lin[TRACK_THREADS];
+    __device__ __forceinline__ void store(int t, const P32& q) {
+        xo[t] = q.xo;
+        mu[t] = q.mu;
+        tau[t] = q.tau;
+        w[t] = q.w;
+        W[t] = q.W;
+        cell[t] = q.cell;
+        id[t] = q.id;
+        e[t] = q.e;
+        lin[t] = q.lin;
+    }
+    __device__ __forceinline__ void load(int t, P32& q) const {
+        q.xo = xo[t];
+        q.mu = mu[t];
+        q.tau = tau[t];
+        q.w = w[t];
+        q.W = W[t];
+        q.cell = cell[t];
+        q.id = id[t];
+        q.e = e[t];
+        q.lin = lin[t];
+    }
+};
+
 // positive doubles order like their bit patterns
 __device__ __forceinline__ bool dgt(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
 
@@ -60,31 +94,27 @@ __device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32
 template <uint32_t LOCAL_MAX>
 __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long item, const long long item_end,
                                           const long long stride, unsigned* s_next, const int b_blk, long long* sm,
-                                          Counters& cnt) {
+                                          Counters& cnt, PendingParent* pp) {
     const int I = a.I;
     long long* s_tl = sm;
     long long* s_bat = sm + 3 * I;  // batch row of the current id range
-    const double tscale = a.sd->tscale;
-    const double cscale = a.sd->cscale;
-    const double wbar = a.sd->wbar;
+    // the step scalars needed only at rare events are read where they are
+    // used (registers are what limits the resident warps)
     const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
-    const int birth = a.sd->birth, ww_on = a.sd->ww_on;
-    const float tau0 = (float)a.tau0;
-    const long long Wbar = to_fixed(wbar, tscale);
-    const BatchDiv bd = batch_div(a.B, a.N);
+    const int ww_on = a.sd->ww_on;
+    const int t = threadIdx.x;
 
     P32 q;
-    P32 base;  // record whose daughters are being expanded
     uint32_t jnext = 0, jend = 0;
-    bool fresh = false;  // the record being expanded holds a collision's extra particles
+    bool fresh = false;  // the pending parent's daughters are a collision's extra particles
     bool have = false;
     int evs = 0;
     int qb = 0;  // variance batch of the current track's source id
     for (;;) {
         if (!have) {
             if (jnext < jend) {
-                q = base;
-                q.lin = lineage_hash(base.lin, base.e, jnext);
+                pp->load(t, q);
+                q.lin = lineage_hash(q.lin, q.e, jnext);
                 q.e = 0;
                 ++jnext;
                 if (fresh) {  // its own isotropic direction
@@ -105,10 +135,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                     q.id = (uint32_t)i;
                     q.lin = 0;
                     q.e = 0;
-                    q.tau = tau0;
-                    q.w = wbar;
-                    q.W = Wbar;
-                    if (birth) {
+                    q.tau = (float)a.tau0;
+                    q.w = a.sd->wbar;
+                    q.W = a.sd->Wbar;
+                    if (a.sd->birth) {
                         uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
                         philox4x32_10(r, k0, k1);
                         q.mu = 2.0f * u01f(r[1]) - 1.0f;
@@ -127,19 +157,19 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                     q.mu = a.rin.mu[i];
                     q.tau = a.rin.tau[i];
                     q.w = a.rin.w[i];
-                    q.W = to_fixed(q.w, tscale);
+                    q.W = to_fixed(q.w, a.sd->tscale);
                     q.cell = a.rin.cell[i];
                     q.id = a.rin.id[i];
                     q.lin = a.rin.lin[i];
                     q.e = a.rin.e[i];
                     const uint32_t jc = a.rin.jcount[i];
                     if (jc) {
-                        base = q;
+                        pp->store(t, q);
                         const uint32_t js = a.rin.jstart[i];
                         fresh = (js & FRESH_DIRECTION) != 0;
                         jnext = js & ~FRESH_DIRECTION;
                         jend = jnext + jc;
-                        q.lin = lineage_hash(base.lin, base.e, jnext);
+                        q.lin = lineage_hash(q.lin, q.e, jnext);
                         q.e = 0;
                         ++jnext;
                         if (fresh) {  // its own isotropic direction
@@ -153,7 +183,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
             q.inv_mu = __frcp_rn(q.mu);  // the correctly rounded 1/mu
             have = true;
             evs = 0;
-            qb = batch_of(q.id, bd);
+            qb = batch_of(q.id, a.B, a.N, a.batch_m);
         }
         // ---- one event ----
         if (evs == a.emax) {
@@ -203,7 +233,6 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                     add128(&a.batch[(long long)b * I + k], g.s0);
             }
         }
-        cnt.v[ST_SEGMENTS]++;
         if (ev != 1) q.xo = fminf(fmaxf(fmaf(q.mu, l, q.xo), 0.0f), dxk);
         q.tau = (ev == 0) ? 0.0f : q.tau - l;
         const uint32_t e_ev = q.e;
@@ -218,9 +247,9 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                 a.cen.w[slot] = q.w;
                 a.cen.cell[slot] = q.cell;
                 a.cen.id[slot] = q.id;
-                a.cen.lin[slot] = q.lin;
-                const unsigned long long wfx = (unsigned long long)to_fixed(q.w, cscale);
-                a.cen.wfx[slot] = wfx;
+
+                const unsigned long long wfx = (unsigned long long)to_fixed(q.w, a.sd->cscale);
+                a.cen.lw[slot] = LinW{q.lin, wfx};
                 atomicAdd(&a.gcnt[q.id], 1u);
                 atomicAdd(&a.gw[q.id], wfx);
             } else {
@@ -244,9 +273,9 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                     const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
                     const double wi = q.w * ia;
                     const double dm2 = (double)q.mu * (double)q.mu;
-                    add128(&a.bnd[3 * side + 0], to_fixed(wi, tscale));
-                    add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - dm2), tscale));
-                    add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), tscale));
+                    add128(&a.bnd[3 * side + 0], to_fixed(wi, a.sd->tscale));
+                    add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - dm2), a.sd->tscale));
+                    add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), a.sd->tscale));
                     cnt.v[ST_LEAKED]++;
                     cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
                     have = false;
@@ -279,7 +308,6 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
             have_r2 = true;
             q.mu = 2.0f * u01f(r2[1]) - 1.0f;
             q.inv_mu = __frcp_rn(q.mu);
-            cnt.v[ST_SCATTERS]++;
             if (nsec > 1) {
                 // the other emitted particles: daughters that take their own
                 // lineages and isotropic directions, expanded by this lane
@@ -288,8 +316,9 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                 const uint32_t nx = nsec - 1;
                 uint32_t jr = 1;  // the first daughter that goes to the record queue
                 if (LOCAL_MAX > 0 && jnext >= jend) {
-                    base = q;
-                    base.e = e_ev | SECONDARY_EVENT;
+                    P32 b = q;
+                    b.e = e_ev | SECONDARY_EVENT;
+                    pp->store(t, b);
                     fresh = true;
                     jnext = 1;
                     jend = min(nsec, 1u + LOCAL_MAX);
@@ -322,7 +351,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                 }
                 const uint32_t nd = (uint32_t)ndd;
                 const double wd = q.w / (double)nd;
-                const long long Wd = to_fixed(wd, tscale);
+                const long long Wd = to_fixed(wd, a.sd->tscale);
                 cnt.v[ST_SPLIT_EVENTS]++;
                 cnt.v[ST_DAUGHTERS] += nd - 1;
                 uint32_t jr = 1;  // the first daughter that goes to the record queue
@@ -331,10 +360,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                     // this lane (same block, so their batch row stays in
                     // shared memory); the bound keeps a large split from
                     // holding one lane while the rest of its block waits
-                    base = q;
-                    base.w = wd;
-                    base.W = Wd;
-                    base.e = e_ev;
+                    P32 b = q;
+                    b.w = wd;
+                    b.W = Wd;
+                    b.e = e_ev;
+                    pp->store(t, b);
                     fresh = false;
                     jnext = 1;
                     jend = min(nd, 1u + LOCAL_MAX);
@@ -366,7 +396,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                 const double ur = u01(r2[2], r2[3]);
                 if (ur * ctr < q.w) {
                     q.w = ctr;
-                    q.W = to_fixed(ctr, tscale);
+                    q.W = to_fixed(ctr, a.sd->tscale);
                     cnt.v[ST_RSURVIVE]++;
                 } else {
                     cnt.v[ST_RKILLS]++;
@@ -383,9 +413,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
 // registers; at three blocks it spills to local memory, whose traffic (the
 // L1 left beside the shared tallies hits ~20% of it) costs more time than
 // the extra warps hide.
-__global__ void __launch_bounds__(256, 2) track32_kernel(TrackArgs<float> a) {
+__global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel(TrackArgs<float> a) {
     extern __shared__ long long sm[];
     __shared__ unsigned s_next;
+    __shared__ PendingParent s_pp;
     const int I = a.I;
     if (threadIdx.x == 0) s_next = 0;
     for (int i = threadIdx.x; i < TALLY_ROWS * I; i += blockDim.x) sm[i] = 0;
@@ -414,13 +445,13 @@ __global__ void __launch_bounds__(256, 2) track32_kernel(TrackArgs<float> a) {
         item_end = min(hi, first + chunk);
         stride = 0;
         dyn = &s_next;
-        if (first < hi) b_blk = batch_of((uint32_t)first, batch_div(a.B, a.N));
+        if (first < hi) b_blk = batch_of((uint32_t)first, a.B, a.N, a.batch_m);
     } else {
         item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         item_end = n_use;
         stride = (long long)gridDim.x * blockDim.x;
     }
-    run_items<LOCAL_DAUGHTERS>(a, item, item_end, stride, dyn, b_blk, sm, cnt);
+    run_items<LOCAL_DAUGHTERS>(a, item, item_end, stride, dyn, b_blk, sm, cnt, &s_pp);
     __syncthreads();
     flush_tallies(sm, I, a.tl);
     if (b_blk >= 0)
@@ -432,8 +463,10 @@ __global__ void __launch_bounds__(256, 2) track32_kernel(TrackArgs<float> a) {
 // Persistent batched variant: blocks pop tiles (problem, id range) from a
 // device counter; the block-private tallies are flushed when a block moves
 // to another problem, the batch row after every tile.
-__global__ void __launch_bounds__(256, 2) track32_kernel_batch(const TrackArgs<float>* args, BatchPlan plan) {
+__global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const TrackArgs<float>* args,
+                                                                         BatchPlan plan) {
     extern __shared__ long long sm[];
+    __shared__ PendingParent s_pp;
     __shared__ TrackArgs<float> A;
     __shared__ long long s_t;
     __shared__ int s_p;
@@ -480,8 +513,8 @@ __global__ void __launch_bounds__(256, 2) track32_kernel_batch(const TrackArgs<f
         const long long n_use = (!A.from_bank && n_in > A.rin.cap) ? A.rin.cap : n_in;
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
-        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, batch_div(A.B, A.N)) : -1;
-        run_items<0>(A, i0, i1, 0, &s_next, b_tile, sm, cnt);
+        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N, A.batch_m) : -1;
+        run_items<0>(A, i0, i1, 0, &s_next, b_tile, sm, cnt, &s_pp);
         __syncthreads();
         if (b_tile >= 0)
             for (int i = threadIdx.x; i < Ic; i += blockDim.x) {

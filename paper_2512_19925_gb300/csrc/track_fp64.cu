@@ -96,8 +96,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
     const double wbar = a.sd->wbar;
     const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
     const int birth = a.sd->birth, ww_on = a.sd->ww_on;
-    const BatchDiv bd = batch_div(a.B, a.N);
-
+    
     // flattened event loop: a lane whose track ends loads its next one while
     // the other lanes take their next event
     P64 q;
@@ -195,7 +194,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             q.inv_mu = 1.0 / q.mu;
             have = true;
             evs = 0;
-            qb = batch_of(q.id, bd);
+            qb = batch_of(q.id, a.B, a.N, a.batch_m);
         }
         // ---- one event ----
         if (evs == a.emax) {
@@ -262,7 +261,6 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             for (int j = 0; j < MAX_SCORES; ++j)
                 if (j < P2) sadd(&s_dtl[j * I + k], to_fixed(wl * S[j], tscale));
         }
-        cnt.v[ST_SEGMENTS]++;
         // move
         if (ev == 1) {
             q.x = xe;
@@ -304,9 +302,9 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 a.cen.w[slot] = q.w;
                 a.cen.cell[slot] = q.cell;
                 a.cen.id[slot] = q.id;
-                a.cen.lin[slot] = q.lin;
+
                 const unsigned long long wfx = (unsigned long long)to_fixed(q.w, cscale);
-                a.cen.wfx[slot] = wfx;
+                a.cen.lw[slot] = LinW{q.lin, wfx};
                 atomicAdd(&a.gcnt[q.id], 1u);
                 atomicAdd(&a.gw[q.id], wfx);
             } else {
@@ -374,7 +372,6 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             have_r2 = true;
             q.mu = 2.0 * u01(r2[0], r2[1]) - 1.0;
             q.inv_mu = 1.0 / q.mu;
-            cnt.v[ST_SCATTERS]++;
             if (nsec > 1) {
                 // the other emitted particles: daughters that take their own
                 // lineages and isotropic directions, expanded by this lane
@@ -521,7 +518,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
         item_end = min(hi, first + chunk);
         stride = 0;
         dyn = &s_next;
-        if (first < hi) b_blk = batch_of((uint32_t)first, batch_div(a.B, a.N));
+        if (first < hi) b_blk = batch_of((uint32_t)first, a.B, a.N, a.batch_m);
     } else {
         item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         item_end = n_use;
@@ -591,7 +588,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<d
         const long long n_use = (!A.from_bank && n_in > A.rin.cap) ? A.rin.cap : n_in;
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
-        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, batch_div(A.B, A.N)) : -1;
+        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N, A.batch_m) : -1;
         run_items<false, 0>(A, i0, i1, 0, &s_next, b_tile, sm, cnt);
         __syncthreads();
         if (b_tile >= 0)
