@@ -31,8 +31,7 @@ constexpr int MAX_REGROW = 12;
 
 template <class Real>
 struct Banks {
-    Real *bx = nullptr, *bmu = nullptr;
-    int32_t* bcell = nullptr;
+    BankRec<Real>* bank = nullptr;  // start bank
     RecQ<Real> q[2] = {};
     CenQ<Real> cen = {};
 };
@@ -208,7 +207,7 @@ template <class Real>
 hww_status alloc_start_bank(hww_problem* p, Banks<Real>& b) {
     hww_status s;
     const long long N = p->N;
-    if ((s = dalloc(p, &b.bx, N)) || (s = dalloc(p, &b.bmu, N)) || (s = dalloc(p, &b.bcell, N))) return s;
+    if ((s = dalloc(p, &b.bank, N))) return s;
     return HWW_OK;
 }
 
@@ -322,9 +321,7 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b) {
     a.ww_hi = p->ww_hi;
     a.ww_lo = p->ww_lo;
     a.sd = p->sd;
-    a.bx = b.bx;
-    a.bmu = b.bmu;
-    a.bcell = b.bcell;
+    a.bank = b.bank;
     a.cen = b.cen;
     a.gcnt = p->gcnt;
     a.gw = p->gw;
@@ -429,9 +426,7 @@ CombArgs<Real> comb_args(hww_problem* p, Banks<Real>& b) {
     c.glist = p->glist;
     glist_offsets(p->cen_cap, c.glist_off);
     c.glist_n = p->counts + 3;
-    c.bx = b.bx;
-    c.bmu = b.bmu;
-    c.bcell = b.bcell;
+    c.bank = b.bank;
     c.stats = p->stats;
     c.err = p->err;
     c.I = p->I;
@@ -519,6 +514,29 @@ __global__ void bank_to_x_kernel(const Real* bx, const int32_t* bcell, const dou
             out[i] = fmin(fmax(edges[c] + (double)bx[i], edges[c]), edges[c + 1]);
         } else
             out[i] = (double)bx[i];
+    }
+}
+
+// one field of the start-bank records as doubles: 0 position, 1 direction,
+// 2 cell (an int32 copy, into out as raw words)
+template <class Real>
+__global__ void bank_field_kernel(const BankRec<Real>* bank, const double* edges, long long n, int field,
+                                  double* out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const BankRec<Real> r = bank[i];
+        if (field == 0) {
+            if (sizeof(Real) == sizeof(float)) {
+                const int c = r.cell;
+                out[i] = fmin(fmax(edges[c] + (double)r.x, edges[c]), edges[c + 1]);
+            } else {
+                out[i] = (double)r.x;
+            }
+        } else if (field == 1) {
+            out[i] = (double)r.mu;
+        } else {
+            ((int32_t*)out)[i] = r.cell;
+        }
     }
 }
 
@@ -1350,23 +1368,24 @@ hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, 
     HWW_CK(cudaMallocAsync(&tmp, sizeof(double) * m, p->stream));
     cudaError_t e = cudaSuccess;
     const int grid = p->nsm * 4;
-    if (x) {
+    auto field = [&](int f) {
         if (p->fp32)
-            bank_to_x_kernel<float><<<grid, 256, 0, p->stream>>>(p->b32.bx, p->b32.bcell, p->d_edges, m, tmp);
+            bank_field_kernel<float><<<grid, 256, 0, p->stream>>>(p->b32.bank, p->d_edges, m, f, tmp);
         else
-            bank_to_x_kernel<double><<<grid, 256, 0, p->stream>>>(p->b64.bx, p->b64.bcell, p->d_edges, m, tmp);
+            bank_field_kernel<double><<<grid, 256, 0, p->stream>>>(p->b64.bank, p->d_edges, m, f, tmp);
+    };
+    if (x) {
+        field(0);
         e = cudaMemcpyAsync(x, tmp, sizeof(double) * m, cudaMemcpyDeviceToHost, p->stream);
     }
-    if (mu && e == cudaSuccess) {
-        if (p->fp32)
-            to_double_kernel<float><<<grid, 256, 0, p->stream>>>(p->b32.bmu, m, tmp);
-        else
-            to_double_kernel<double><<<grid, 256, 0, p->stream>>>(p->b64.bmu, m, tmp);
+    if (mu && e == cudaSuccess) {  // stream order: after the copy of x
+        field(1);
         e = cudaMemcpyAsync(mu, tmp, sizeof(double) * m, cudaMemcpyDeviceToHost, p->stream);
     }
-    if (cell && e == cudaSuccess)
-        e = cudaMemcpyAsync(cell, p->fp32 ? p->b32.bcell : p->b64.bcell, sizeof(int32_t) * m,
-                            cudaMemcpyDeviceToHost, p->stream);
+    if (cell && e == cudaSuccess) {
+        field(2);
+        e = cudaMemcpyAsync(cell, tmp, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, p->stream);
+    }
     cudaFreeAsync(tmp, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     return cuda_status(e);
@@ -1416,18 +1435,23 @@ hww_status set_bank(hww_problem* p, const double* x, const double* mu, const int
     cudaError_t e = cudaSuccess;
     if (n > 0) {
         if (p->fp32) {
-            std::vector<float> xo(n), mf(n);
+            std::vector<BankRec<float>> r(n);
             for (int64_t k = 0; k < n; ++k) {
-                xo[k] = (float)(x[k] - p->edges[cell[k]]);
-                mf[k] = (float)mu[k];
+                r[k].x = (float)(x[k] - p->edges[cell[k]]);
+                r[k].mu = (float)mu[k];
+                r[k].cell = cell[k];
+                r[k].pad = 0;
             }
-            e = cudaMemcpy(p->b32.bx, xo.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(p->b32.bmu, mf.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(p->b32.bcell, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+            e = cudaMemcpy(p->b32.bank, r.data(), sizeof(BankRec<float>) * n, cudaMemcpyHostToDevice);
         } else {
-            e = cudaMemcpy(p->b64.bx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(p->b64.bmu, mu, sizeof(double) * n, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(p->b64.bcell, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+            std::vector<BankRec<double>> r(n);
+            for (int64_t k = 0; k < n; ++k) {
+                r[k] = BankRec<double>{};
+                r[k].x = x[k];
+                r[k].mu = mu[k];
+                r[k].cell = cell[k];
+            }
+            e = cudaMemcpy(p->b64.bank, r.data(), sizeof(BankRec<double>) * n, cudaMemcpyHostToDevice);
         }
     }
     StepDev sdh;

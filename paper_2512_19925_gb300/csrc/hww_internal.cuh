@@ -70,6 +70,22 @@ struct StepDev {
     unsigned long long ncensus;    // census bank size of the step
 };
 
+// one start-bank particle (position, direction, cell) in one aligned record,
+// so that a comb copy is one scattered store and a bank read one load:
+// 16 bytes for the FP32 path (cell-local offset), 32 for FP64
+template <class Real>
+struct BankRec;
+template <>
+struct __align__(16) BankRec<float> {
+    float x, mu;
+    int32_t cell, pad;
+};
+template <>
+struct __align__(32) BankRec<double> {
+    double x, mu;
+    int32_t cell, pad[3];
+};
+
 // a census particle's comb key and weight, read together by the comb
 struct __align__(16) LinW {
     uint64_t lin;              // lineage key
@@ -128,10 +144,7 @@ struct TrackArgs {
     const double* ww_hi;
     const double* ww_lo;
     const StepDev* sd;
-    // start bank
-    const Real* bx;
-    const Real* bmu;
-    const int32_t* bcell;
+    const BankRec<Real>* bank;  // start bank
     RecQ<Real> rin, rout;
     CenQ<Real> cen;
     uint32_t* gcnt;

@@ -475,11 +475,11 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
         const Real x = a.cx[j];
         const Real mu = a.cmu[j];
         const int32_t cell = a.ccell[j];
-        for (long long k = k0; k < k1; ++k) {
-            a.bx[k] = x;
-            a.bmu[k] = mu;
-            a.bcell[k] = cell;
-        }
+        BankRec<Real> rec{};
+        rec.x = x;
+        rec.mu = mu;
+        rec.cell = cell;
+        for (long long k = k0; k < k1; ++k) a.bank[k] = rec;
         // derivative runs: every copy keeps the scores of its source
         for (int q = 0; q < a.P2; ++q) {
             const double sq = a.cS[(long long)q * a.cen_cap + j];

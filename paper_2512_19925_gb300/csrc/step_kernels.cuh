@@ -39,9 +39,7 @@ struct CombArgs {
     const GroupRec* gro;  // [N+1] group records (entry N: totals)
     uint32_t* gcur;
     uint32_t* member;
-    Real* bx;
-    Real* bmu;
-    int32_t* bcell;
+    BankRec<Real>* bank;  // next start bank
     unsigned long long* stats;
     unsigned* err;
     unsigned long long* cpre;        // [cen_cap] comb prefix C0 of every census particle

@@ -148,9 +148,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                         q.cell = (q.mu < 0.0f) ? a.birth_cell_neg : a.birth_cell_pos;
                         q.xo = (float)(x - a.edges[q.cell]);
                     } else {
-                        q.xo = a.bx[i];
-                        q.mu = a.bmu[i];
-                        q.cell = a.bcell[i];
+                        const BankRec<float> r = a.bank[i];
+                        q.xo = r.x;
+                        q.mu = r.mu;
+                        q.cell = r.cell;
                     }
                 } else {
                     q.xo = a.rin.x[i];

@@ -151,9 +151,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                         if (q.x >= a.edges[I] && q.mu > 0.0 && a.bc_r == 1) q.mu = -q.mu;
                         q.cell = (q.mu < 0.0) ? a.birth_cell_neg : a.birth_cell_pos;
                     } else {
-                        q.x = a.bx[i];
-                        q.mu = a.bmu[i];
-                        q.cell = a.bcell[i];
+                        const BankRec<double> r = a.bank[i];
+                        q.x = r.x;
+                        q.mu = r.mu;
+                        q.cell = r.cell;
                     }
                 } else {
                     q.x = a.rin.x[i];
