@@ -303,12 +303,14 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b) {
     a.B = p->B;
     a.N = p->N;
     a.batch_m = p->N > 0 ? ~0ull / (unsigned long long)p->N : 0ull;
+    a.comb_shift = bit_length(p->N) - 19;  // S - Sc = (40 - E) - (59 - E - bitlen N)
     a.emax = p->emax;
     a.bc_l = p->d.bc_left;
     a.bc_r = p->d.bc_right;
     a.birth_cell_pos = p->birth_pos;
     a.birth_cell_neg = p->birth_neg;
     a.tau0 = p->d.v * p->d.dt;
+    a.tau0f = (float)a.tau0;
     a.src_x = p->d.src_x;
     a.edges = p->d_edges;
     a.inv_sigt = p->d_inv_sigt;

@@ -132,6 +132,8 @@ struct TrackArgs {
     int bc_l, bc_r;
     int birth_cell_pos, birth_cell_neg;
     double tau0;      // v dt
+    float tau0f;      // v dt rounded to FP32 (the FP32 path's distance to census at a step start)
+    int comb_shift;   // S - Sc: the tally-scale weight shifted right by this is the comb-scale weight
     double src_x;
     const double* edges;
     const double* inv_sigt;

@@ -66,6 +66,17 @@ struct PendingParent {
     }
 };
 
+// The comb-scale weight of a census particle from its tally-scale weight W:
+// W 2^(Sc - S), rounded to nearest (ties to even) when Sc < S; integer
+// arithmetic, so the common census event uses no FP64 instruction (the FP64
+// path rounds w 2^Sc directly; the two can differ in the last bit)
+__device__ __forceinline__ unsigned long long comb_weight(long long W, int shift) {
+    const unsigned long long u = (unsigned long long)W;
+    if (shift <= 0) return u << (-shift);
+    const unsigned long long q = u >> shift, r = u & ((1ull << shift) - 1ull), h = 1ull << (shift - 1);
+    return q + ((r > h || (r == h && (q & 1ull))) ? 1ull : 0ull);
+}
+
 // positive doubles order like their bit patterns
 __device__ __forceinline__ bool dgt(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
 
@@ -135,7 +146,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                     q.id = (uint32_t)i;
                     q.lin = 0;
                     q.e = 0;
-                    q.tau = (float)a.tau0;
+                    q.tau = a.tau0f;
                     q.w = a.sd->wbar;
                     q.W = a.sd->Wbar;
                     if (a.sd->birth) {
@@ -249,7 +260,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
                 a.cen.cell[slot] = q.cell;
                 a.cen.id[slot] = q.id;
 
-                const unsigned long long wfx = (unsigned long long)to_fixed(q.w, a.sd->cscale);
+                const unsigned long long wfx = comb_weight(q.W, a.comb_shift);
                 a.cen.lw[slot] = LinW{q.lin, wfx};
                 atomicAdd(&a.gcnt[q.id], 1u);
                 atomicAdd(&a.gw[q.id], wfx);
