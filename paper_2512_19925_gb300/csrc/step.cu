@@ -199,19 +199,34 @@ __global__ void comb_groups_kernel(CombArgs<Real> a) {
         for (int kk = 0; kk <= NCLASS; ++kk) c[kk] += (kk == k) ? 1u : 0u;
     }
 #pragma unroll
-    for (int k = 0; k <= NCLASS; ++k)
-        if (c[k]) atomicAdd(&s_cnt[k], (unsigned long long)c[k]);
+    for (int k = 0; k <= NCLASS; ++k) {
+        unsigned v = c[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31u) == 0 && v) atomicAdd(&s_cnt[k], (unsigned long long)v);
+    }
     __syncthreads();
     if (threadIdx.x <= NCLASS) {
         const unsigned long long n = s_cnt[threadIdx.x];
         s_pos[threadIdx.x] = n ? atomicAdd(&a.glist_n[threadIdx.x], n) : 0ull;
     }
     __syncthreads();
-    for (long long id = lo + threadIdx.x; id < hi; id += blockDim.x) {
-        const uint32_t g = a.gcnt[id];
-        if (g < 3) continue;
-        const int k = size_class(g);
-        a.glist[a.glist_off[k] + atomicAdd(&s_pos[k], 1ull)] = (uint32_t)id;
+    // the whole block walks the range in step (the loop bound is uniform), so
+    // every warp is converged at the appends: one shared atomic per class
+    // and warp
+    const unsigned lane = threadIdx.x & 31u;
+    for (long long id0 = lo; id0 < hi; id0 += blockDim.x) {
+        const long long id = id0 + threadIdx.x;
+        const uint32_t g = (id < hi) ? a.gcnt[id] : 0u;
+        const int kc = (g >= 3) ? size_class(g) : -1;
+#pragma unroll
+        for (int k = 0; k <= NCLASS; ++k) {
+            const unsigned bal = __ballot_sync(0xffffffffu, kc == k);
+            if (!bal) continue;
+            unsigned long long base = 0;
+            if (lane == (unsigned)(__ffs(bal) - 1)) base = atomicAdd(&s_pos[k], (unsigned long long)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+            if (kc == k) a.glist[a.glist_off[k] + base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)id;
+        }
     }
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
@@ -428,12 +443,9 @@ __global__ void census_tally_kernel(CombArgs<Real> a) {
         const int k = a.ccell[j];
         long long c0, c1, c2;
         census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
-        const Agg3 g = warp_agg3(k, c0, c1, c2);
-        if (g.leader) {
-            sadd(&s_cen[k], g.s0);
-            sadd(&s_cen[I + k], g.s1);
-            sadd(&s_cen[2 * I + k], g.s2);
-        }
+        sadd(&s_cen[k], c0);
+        sadd(&s_cen[I + k], c1);
+        sadd(&s_cen[2 * I + k], c2);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * I; i += blockDim.x)
@@ -441,7 +453,7 @@ __global__ void census_tally_kernel(CombArgs<Real> a) {
 }
 
 // census order: each census particle's census tallies (Eq. ct-mc; block-
-// private in shared memory, warp-aggregated by cell), its teeth and its copies
+// private in shared memory), its teeth and its copies
 template <class Real>
 __global__ void comb_write_kernel(CombArgs<Real> a) {
     extern __shared__ long long s_cen[];  // 3 I
@@ -457,15 +469,14 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
         {
+            // census order scatters the cells over a warp: one shared atomic
+            // per lane and word (a warp aggregation would rarely merge lanes)
             const int k = a.ccell[j];
             long long c0, c1, c2;
             census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
-            const Agg3 g = warp_agg3(k, c0, c1, c2);
-            if (g.leader) {
-                sadd(&s_cen[k], g.s0);
-                sadd(&s_cen[I + k], g.s1);
-                sadd(&s_cen[2 * I + k], g.s2);
-            }
+            sadd(&s_cen[k], c0);
+            sadd(&s_cen[I + k], c1);
+            sadd(&s_cen[2 * I + k], c2);
         }
         const unsigned long long C0 = a.cpre[j];
         const unsigned long long wj = a.clw[j].wfx;
