@@ -48,38 +48,6 @@ __device__ __forceinline__ unsigned long long warp_reserve_n(unsigned long long*
     return base + (unsigned long long)n * (unsigned long long)__popc(peers & ((1u << lane) - 1u));
 }
 
-// Warp aggregation of three 64-bit contributions per lane by an integer key:
-// lanes with equal keys are combined by a binomial tree over their ranks in
-// the key group (shuffles among the converged lanes), and the lowest lane of
-// each group gets the group sums.  Integer sums, so the result does not
-// depend on how the lanes are grouped.
-struct Agg3 {
-    bool leader;
-    long long s0, s1, s2;
-};
-
-__device__ __forceinline__ Agg3 warp_agg3(int key, long long v0, long long v1, long long v2) {
-    const unsigned active = __activemask();
-    const unsigned peers = __match_any_sync(active, key);
-    const unsigned lane = lane_id();
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    const int gsz = __popc(peers);
-    if (__all_sync(active, gsz == 1)) return Agg3{true, v0, v1, v2};
-    for (int d = 1; d < 32; d <<= 1) {
-        const int want = rank + d;
-        const int src = (want < gsz) ? (int)__fns(peers, 0, want + 1) : (int)lane;
-        const long long x0 = __shfl_sync(active, v0, src);
-        const long long x1 = __shfl_sync(active, v1, src);
-        const long long x2 = __shfl_sync(active, v2, src);
-        if (want < gsz && (rank & (2 * d - 1)) == 0) {
-            v0 += x0;
-            v1 += x1;
-            v2 += x2;
-        }
-    }
-    return Agg3{rank == 0, v0, v1, v2};
-}
-
 // variance batch of a source id: contiguous id ranges, b = floor(id B / N),
 // without a division: q = (x m) / 2^64 with m = floor((2^64 - 1) / N) (from
 // the host) is floor(x / N) or one less (x = id B < 2^37), and one

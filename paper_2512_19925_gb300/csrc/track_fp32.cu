@@ -233,17 +233,18 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
         const float m2 = q.mu * q.mu;
         const float f3 = 1.0f / 3.0f - m2;
         {
+            // one shared atomic per lane and word: merging the lanes of a
+            // warp that share a cell first (match + shuffle tree) measured
+            // slower than the atomics it saves
             const int b = qb;
-            const Agg3 g = warp_agg3(k * a.B + b, fx_mul(q.W, l), fx_mul(q.W, l * q.mu), fx_mul(q.W, l * f3));
-            if (g.leader) {
-                sadd(&s_tl[k], g.s0);
-                sadd(&s_tl[I + k], g.s1);
-                sadd(&s_tl[2 * I + k], g.s2);
-                if (b == b_blk)
-                    sadd(&s_bat[k], g.s0);
-                else
-                    add128(&a.batch[(long long)b * I + k], g.s0);
-            }
+            const long long c0 = fx_mul(q.W, l);
+            sadd(&s_tl[k], c0);
+            sadd(&s_tl[I + k], fx_mul(q.W, l * q.mu));
+            sadd(&s_tl[2 * I + k], fx_mul(q.W, l * f3));
+            if (b == b_blk)
+                sadd(&s_bat[k], c0);
+            else
+                add128(&a.batch[(long long)b * I + k], c0);
         }
         if (ev != 1) q.xo = fminf(fmaxf(fmaf(q.mu, l, q.xo), 0.0f), dxk);
         q.tau = (ev == 0) ? 0.0f : q.tau - l;

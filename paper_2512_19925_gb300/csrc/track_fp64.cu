@@ -235,18 +235,16 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
         const double wlmu = wl * q.mu;
         const double wlf = wl * (1.0 / 3.0 - q.mu * q.mu);
         {
+            // one shared atomic per lane and word (see the FP32 loop)
             const int b = qb;
-            const Agg3 g = warp_agg3(k * a.B + b, to_fixed(wl, tscale), to_fixed(wlmu, tscale),
-                                     to_fixed(wlf, tscale));
-            if (g.leader) {
-                sadd(&s_tl[k], g.s0);
-                sadd(&s_tl[I + k], g.s1);
-                sadd(&s_tl[2 * I + k], g.s2);
-                if (b == b_blk)
-                    sadd(&s_bat[k], g.s0);
-                else
-                    add128(&a.batch[(long long)b * I + k], g.s0);
-            }
+            const long long c0 = to_fixed(wl, tscale);
+            sadd(&s_tl[k], c0);
+            sadd(&s_tl[I + k], to_fixed(wlmu, tscale));
+            sadd(&s_tl[2 * I + k], to_fixed(wlf, tscale));
+            if (b == b_blk)
+                sadd(&s_bat[k], c0);
+            else
+                add128(&a.batch[(long long)b * I + k], c0);
         }
         if constexpr (DERIV) {
             // scores after this segment's flight, then w l S_j per parameter
