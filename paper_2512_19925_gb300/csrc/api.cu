@@ -407,6 +407,16 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b, long long lo = 0, long lo
     return HWW_OK;
 }
 
+// blocks of the comb kernels (grid-stride loops, so any size is correct):
+// about one 256-thread block per 1024 expected census particles (twice the
+// start bank), at most 8 per SM.  A small problem's comb then leaves the
+// GPU to the other members of a batch, whose stages run as parallel graph
+// branches, instead of occupying every SM with near-empty blocks.
+int comb_grid(const hww_problem* p) {
+    const long long want = (2 * p->N + 1023) / 1024;
+    return (int)std::max(1LL, std::min<long long>(want, 8LL * p->nsm));
+}
+
 template <class Real>
 CombArgs<Real> comb_args(hww_problem* p, Banks<Real>& b) {
     CombArgs<Real> c{};
@@ -453,7 +463,7 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     launch_group_scan(s, p->stream);
     HWW_CK(cudaGetLastError());
     p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
-    launch_comb(comb_args(p, b), p->nsm * 8, p->stream);
+    launch_comb(comb_args(p, b), comb_grid(p), p->stream);
     HWW_CK(cudaGetLastError());
     p->kernel_launches += 8;
     return HWW_OK;
