@@ -465,7 +465,7 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
     launch_comb(comb_args(p, b), comb_grid(p), p->stream);
     HWW_CK(cudaGetLastError());
-    p->kernel_launches += 8;
+    p->kernel_launches += 5;
     return HWW_OK;
 }
 

@@ -233,47 +233,63 @@ __global__ void comb_groups_kernel(CombArgs<Real> a) {
 
 // warp segments of S lanes, one group of at most S members per segment:
 // lane i holds member i; its prefix is the weight of the segment's members
-// with a smaller (lineage, slot) key, gathered by S shuffles
+// with a smaller (lineage, slot) key, gathered by S shuffles.  One call
+// handles the 32/S groups [e0, e0 + 32/S) of a class list (the whole warp,
+// converged).
 template <class Real, int S>
-__global__ void comb_seg_kernel(CombArgs<Real> a, int k) {
-    const unsigned long long n = a.glist_n[k];
-    const uint32_t* list = a.glist + a.glist_off[k];
+__device__ __forceinline__ void seg_groups(const CombArgs<Real>& a, const uint32_t* list, unsigned long long n,
+                                           unsigned long long e0, unsigned long long& coll) {
     const int lane = threadIdx.x & 31, seg = lane / S, li = lane % S;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
-    unsigned long long coll = 0;
-    for (unsigned long long e0 = (unsigned long long)warp * (32 / S); e0 < n;
-         e0 += (unsigned long long)nwarp * (32 / S)) {
-        const unsigned long long e = e0 + seg;
-        uint32_t g = 0;
-        unsigned long long base = 0, C = 0;
-        if (e < n) {
-            const GroupRec G = a.gro[list[e]];
-            g = G.cnt;
-            base = G.off;
-            C = G.offw;
-        }
-        uint64_t lin = ~0ull;
-        uint32_t jj = 0xFFFFFFFFu;
-        unsigned long long w = 0;
-        if ((uint32_t)li < g) {
-            jj = a.member[base + li];
-            const LinW x = a.clw[jj];
-            lin = x.lin;
-            w = x.wfx;
-        }
-        unsigned long long C0 = 0;
+    const unsigned long long e = e0 + seg;
+    uint32_t g = 0;
+    unsigned long long base = 0, C = 0;
+    if (e < n) {
+        const GroupRec G = a.gro[list[e]];
+        g = G.cnt;
+        base = G.off;
+        C = G.offw;
+    }
+    uint64_t lin = ~0ull;
+    uint32_t jj = 0xFFFFFFFFu;
+    unsigned long long w = 0;
+    if ((uint32_t)li < g) {
+        jj = a.member[base + li];
+        const LinW x = a.clw[jj];
+        lin = x.lin;
+        w = x.wfx;
+    }
+    unsigned long long C0 = 0;
 #pragma unroll
-        for (int t = 0; t < S; ++t) {
-            const uint64_t lt = __shfl_sync(0xffffffffu, lin, t, S);
-            const uint32_t jt = __shfl_sync(0xffffffffu, jj, t, S);
-            const unsigned long long wt = __shfl_sync(0xffffffffu, w, t, S);
-            if (key_less(lt, jt, lin, jj)) {
-                C0 += wt;
-                if (lt == lin && (uint32_t)t < g && (uint32_t)li < g) ++coll;
-            }
+    for (int t = 0; t < S; ++t) {
+        const uint64_t lt = __shfl_sync(0xffffffffu, lin, t, S);
+        const uint32_t jt = __shfl_sync(0xffffffffu, jj, t, S);
+        const unsigned long long wt = __shfl_sync(0xffffffffu, w, t, S);
+        if (key_less(lt, jt, lin, jj)) {
+            C0 += wt;
+            if (lt == lin && (uint32_t)t < g && (uint32_t)li < g) ++coll;
         }
-        if ((uint32_t)li < g) a.cpre[jj] = C + C0;
+    }
+    if ((uint32_t)li < g) a.cpre[jj] = C + C0;
+}
+
+// the four warp-segment classes (3-4, 5-8, 9-16, 17-32 members) in one
+// launch: warp task t takes the next 32/S groups of its class's list
+template <class Real>
+__global__ void comb_seg_kernel(CombArgs<Real> a) {
+    const unsigned long long n0 = a.glist_n[0], n1 = a.glist_n[1], n2 = a.glist_n[2], n3 = a.glist_n[3];
+    const unsigned long long t1 = (n0 + 7) / 8, t2 = t1 + (n1 + 3) / 4, t3 = t2 + (n2 + 1) / 2, t4 = t3 + n3;
+    const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarp = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long coll = 0;
+    for (unsigned long long t = warp; t < t4; t += nwarp) {  // warp-uniform branches
+        if (t < t1)
+            seg_groups<Real, 4>(a, a.glist + a.glist_off[0], n0, t * 8, coll);
+        else if (t < t2)
+            seg_groups<Real, 8>(a, a.glist + a.glist_off[1], n1, (t - t1) * 4, coll);
+        else if (t < t3)
+            seg_groups<Real, 16>(a, a.glist + a.glist_off[2], n2, (t - t2) * 2, coll);
+        else
+            seg_groups<Real, 32>(a, a.glist + a.glist_off[3], n3, t - t3, coll);
     }
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
@@ -539,10 +555,7 @@ template <class Real>
 void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
     comb_scatter_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_groups_kernel<Real><<<grid, 256, 0, s>>>(a);
-    comb_seg_kernel<Real, 4><<<grid, 256, 0, s>>>(a, 0);
-    comb_seg_kernel<Real, 8><<<grid, 256, 0, s>>>(a, 1);
-    comb_seg_kernel<Real, 16><<<grid, 256, 0, s>>>(a, 2);
-    comb_seg_kernel<Real, 32><<<grid, 256, 0, s>>>(a, 3);
+    comb_seg_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_big_kernel<Real><<<grid, BIG_T, 0, s>>>(a);
     comb_write_kernel<Real><<<grid, 256, sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
 }
