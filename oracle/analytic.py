@@ -109,3 +109,59 @@ def uncollided_track_length(edges, t0, t1, sigma, v=1.0):
                                 limit=200)
         out[i] = val / ((t1 - t0) * (xb - xa))
     return out
+
+
+# Collided solution.  With c > 0 the scalar flux of the unit pulse in an
+# infinite medium has a semi-analytic form (the benchmark of Ganapol et al.
+# that the paper's test problem comes from): in units Sigma = v = 1, for
+# |eta| < 1 with eta = x / t,
+#
+#   phi_1(x, t) = e^{-t} / (2 t) [1 + c t / (4 pi) (1 - eta^2)
+#                 * int_0^pi sec^2(u/2) Re(xi^2 e^{(c t / 2)(1 - eta^2) xi}) du],
+#   xi(u) = (ln q + i u) / (eta + i tan(u/2)),  q = (1 + eta) / (1 - eta),
+#
+# and phi_1 = 0 for |x| >= t.  Units: phi(x, t; Sigma, v) = v Sigma
+# phi_1(Sigma x, Sigma v t).  At c = 0 it is the uncollided flux above; the
+# tests pin it against the exact moment ODEs (int phi dx = v N(t) and
+# int x^2 phi dx = v A(t)), which are derived independently.
+
+def _gauss(n, a, b):
+    z, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (b - a) * z + 0.5 * (b + a), 0.5 * (b - a) * w
+
+
+def pulse_flux(x, t, sigma, c, v=1.0, n_u=128):
+    """Scalar flux phi(x, t) of the unit isotropic plane pulse at x = 0,
+    t = 0 in an infinite medium (Sigma, c, v); Gauss-Legendre in u."""
+    x = np.atleast_1d(np.asarray(x, dtype=float))
+    tau = sigma * v * t
+    eta = x / (v * t)
+    out = np.zeros_like(x)
+    inside = np.abs(eta) < 1.0
+    if not np.any(inside):
+        return out
+    e = eta[inside][:, None]
+    u, wu = _gauss(n_u, 0.0, math.pi)
+    u = u[None, :]
+    lq = np.log((1.0 + e) / (1.0 - e))
+    xi = (lq + 1j * u) / (e + 1j * np.tan(0.5 * u))
+    f = (np.real(xi * xi * np.exp(0.5 * c * tau * (1.0 - e * e) * xi)) / np.cos(0.5 * u) ** 2)
+    integral = f @ wu
+    phi1 = math.exp(-tau) / (2.0 * tau) * (1.0 + c * tau / (4.0 * math.pi) * (1.0 - e[:, 0] ** 2) * integral)
+    out[inside] = v * sigma * phi1
+    return out
+
+
+def pulse_census(edges, t, sigma, c, v=1.0, n_x=24, n_u=128):
+    """Cell averages of phi(x, t) (the expected census tally [[phi]]_i at t)
+    by Gauss-Legendre over the part of each cell inside the light cone."""
+    r = v * t
+    out = np.zeros(len(edges) - 1)
+    for i in range(len(edges) - 1):
+        xa, xb = edges[i], edges[i + 1]
+        lo, hi = max(xa, -r), min(xb, r)
+        if hi <= lo:
+            continue
+        xs, wx = _gauss(n_x, lo, hi)
+        out[i] = float(pulse_flux(xs, t, sigma, c, v, n_u) @ wx) / (xb - xa)
+    return out
