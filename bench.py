@@ -371,6 +371,10 @@ def main(args):
 
     hww.load()
     seed = rank_seed(rank)
+    if ws > 1:
+        # a scaling run times the headline path (and its end-to-end form) on
+        # every rank; the secondary legs are single-GPU measurements
+        args.no_fp64 = args.no_batch = args.no_deriv = True
     N = args.particles
     with ClockSampler(local) as clk:
         fast = run_path(hww, torch, "fp32", N, seed, args.warmup, args.steps, barrier)
