@@ -8,7 +8,7 @@ IEEE operation written in the source.  It shares no code with the CUDA path.
 
 What each function follows in the paper (arXiv 2512.19925):
   ``philox``            counter RNG both sides implement (Salmon et al., SC'11)
-  ``u01``, ``log``      the uniform map and the atanh-series logarithm of the
+  ``u01``, ``log``      the uniform map and the table-driven logarithm of the
                         numerics contract (pinned against libm)
   ``losm_solve``        Sec. 3, Eqs. (losm-0), (losm-1), (losm-disc-bc)
   ``ma_filter``         Sec. 4, Eq. (moving_average)
@@ -115,6 +115,8 @@ def lib():
             L.or_u01.restype = C.c_double
             L.or_log.argtypes = [C.c_double]
             L.or_log.restype = C.c_double
+            L.or_log_table.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.or_log_table.restype = None
             L.or_ma_filter.argtypes = [dp, dp, C.c_int32, C.c_int32]
             L.or_fourier_filter.argtypes = [dp, dp, C.c_int32, C.c_int32]
             L.or_losm_solve.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
@@ -162,6 +164,16 @@ def u01(lo, hi):
 
 def log(u):
     return lib().or_log(float(u))
+
+
+def log_table():
+    """The logarithm's reduction table: arrays IC[128], T[128]."""
+    ic, t = C.c_double(), C.c_double()
+    out_ic, out_t = np.zeros(128), np.zeros(128)
+    for j in range(128):
+        lib().or_log_table(j, C.byref(ic), C.byref(t))
+        out_ic[j], out_t[j] = ic.value, t.value
+    return out_ic, out_t
 
 
 def fourier_filter(x, kappa):

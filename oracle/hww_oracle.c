@@ -85,45 +85,133 @@ double or_u01(uint32_t lo, uint32_t hi) {
     return ((double)(x >> 12) + 0.5) * 0x1p-52;
 }
 
-/* Natural logarithm of a positive normal double by the textbook reduction
- * u = m 2^k with m in [sqrt(1/2), sqrt(2)) and log m = 2 atanh(s),
- * s = (m-1)/(m+1), summed as the odd series 2s(1 + s^2/3 + s^4/5 + ...)
- * through the s^22/23 term (|s| <= 0.1716), plus k ln 2 with ln 2 split into
- * a 32-bit head and a tail.  The series is evaluated by Horner's rule with
- * fused multiply-adds; both implementations follow this exact sequence. */
+/* Natural logarithm of a positive normal double (u in (0, 1) here) by
+ * table-driven reduction:
+ *   u = 2^e m, m in [1, 2); j = the top 7 bits of m's mantissa;
+ *   j < 64:  c = 1 + j/128,           IC_j = 1/c rounded,       K_j = 0;
+ *   j >= 64: c = (1 + (j+1)/128) / 2, IC_j = (1/c rounded) / 2, K_j = 1;
+ *   r = m IC_j - 1 (one fused multiply-add; |r| < 2^-7),
+ *   log u = (e + K_j) ln 2 + T_j + log1p(r),  T_j = -log(IC_j 2^K_j),
+ * with log1p(r) = r + r^2 (-1/2 + r/3 - ... + r^7/9) by Horner's rule
+ * (the next term is below 2^-64 of r) and ln 2 split into a 32-bit head and
+ * a tail.  The centers next to 1 are 1 itself (T = 0, r exact), and T and
+ * log1p(r) share a sign whenever e + K_j = 0, so nothing cancels; the error
+ * stays within 2 ulp.  T_j is log(IC_j 2^K_j) rounded once to double: this
+ * file computes it at first use in double-double arithmetic (atanh series),
+ * which is accurate to about 2^-100, far inside the rounding.  The device
+ * implements the same steps from its own table. */
 static const double LN2_HI = 0x1.62e42fee00000p-1;
 static const double LN2_LO = 0x1.a39ef35793c76p-33;
 
+typedef struct {
+    double hi, lo;
+} dd;
+
+static dd dd_two_sum(double a, double b) {
+    double s = a + b;
+    double bb = s - a;
+    double e = (a - (s - bb)) + (b - bb);
+    dd r = {s, e};
+    return r;
+}
+static dd dd_norm(double hi, double lo) {
+    double s = hi + lo;
+    double e = lo - (s - hi);
+    dd r = {s, e};
+    return r;
+}
+static dd dd_add(dd a, dd b) {
+    dd s = dd_two_sum(a.hi, b.hi);
+    return dd_norm(s.hi, s.lo + (a.lo + b.lo));
+}
+static dd dd_mul(dd a, dd b) {
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);
+    e = e + (a.hi * b.lo + a.lo * b.hi);
+    return dd_norm(p, e);
+}
+static dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd qb = dd_mul((dd){q1, 0.0}, b);
+    dd rem = dd_add(a, (dd){-qb.hi, -qb.lo});
+    double q2 = rem.hi / b.hi;
+    dd qqb = dd_mul((dd){q2, 0.0}, b);
+    rem = dd_add(rem, (dd){-qqb.hi, -qqb.lo});
+    double q3 = rem.hi / b.hi;
+    dd q = dd_norm(q1, q2);
+    return dd_add(q, (dd){q3, 0.0});
+}
+
+/* log(y) for y in [1/2, 2] in double-double: 2 atanh(s), s = (y-1)/(y+1) */
+static dd dd_log(double y) {
+    dd num = {y - 1.0, 0.0}; /* exact (Sterbenz) */
+    dd den = dd_two_sum(y, 1.0);
+    dd sv = dd_div(num, den);
+    dd s2 = dd_mul(sv, sv);
+    dd term = sv, sum = sv;
+    for (int n = 1; n < 40; ++n) {
+        term = dd_mul(term, s2);
+        dd t = dd_div(term, (dd){(double)(2 * n + 1), 0.0});
+        sum = dd_add(sum, t);
+        if (fabs(t.hi) < 0x1p-110 * fabs(sum.hi)) break;
+    }
+    return dd_add(sum, sum);
+}
+
+static double LOG_IC[128], LOG_T[128];
+static int log_table_ready = 0;
+
+static void log_table_init(void) {
+    for (int j = 0; j < 128; ++j) {
+        double ic, y;
+        if (j < 64) {
+            const double c = 1.0 + (double)j / 128.0;
+            ic = 1.0 / c;
+            y = ic;
+        } else {
+            const double c = (1.0 + (double)(j + 1) / 128.0) * 0.5;
+            const double inv = 1.0 / c;
+            ic = inv * 0.5;
+            y = inv;
+        }
+        LOG_IC[j] = ic;
+        /* the normalized double-double's head is the rounding; log 1 = +0 */
+        LOG_T[j] = (y == 1.0) ? 0.0 : -dd_log(y).hi;
+    }
+    log_table_ready = 1;
+}
+
+void or_log_table(int32_t j, double* ic, double* t) {
+    if (!log_table_ready) log_table_init();
+    *ic = LOG_IC[j & 127];
+    *t = LOG_T[j & 127];
+}
+
 double or_log(double u) {
+    if (!log_table_ready) log_table_init();
     uint64_t b;
     memcpy(&b, &u, sizeof b);
-    int k = (int)((b >> 52) & 0x7ff) - 1023;
-    uint64_t mb = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull; /* m in [1,2) */
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const uint64_t mant = b & 0x000fffffffffffffull;
+    const uint64_t mb = mant | 0x3ff0000000000000ull; /* m in [1,2) */
     double m;
     memcpy(&m, &mb, sizeof m);
-    if (m > 0x1.6a09e667f3bcdp+0) { /* sqrt(2) rounded */
-        m = m * 0.5;
-        k = k + 1;
-    }
-    double f = m - 1.0;
-    double s = f / (m + 1.0);
-    double z = s * s;
-    double p = 1.0 / 23.0;
-    p = fma(p, z, 1.0 / 21.0);
-    p = fma(p, z, 1.0 / 19.0);
-    p = fma(p, z, 1.0 / 17.0);
-    p = fma(p, z, 1.0 / 15.0);
-    p = fma(p, z, 1.0 / 13.0);
-    p = fma(p, z, 1.0 / 11.0);
-    p = fma(p, z, 1.0 / 9.0);
-    p = fma(p, z, 1.0 / 7.0);
-    p = fma(p, z, 1.0 / 5.0);
-    p = fma(p, z, 1.0 / 3.0);
-    double s2 = s + s;
-    double tail = s2 * (z * p);          /* 2s(z/3 + z^2/5 + ...) */
-    double kd = (double)k;
-    double lo = fma(kd, LN2_LO, tail);
-    return fma(kd, LN2_HI, s2 + lo);
+    const int j = (int)(mant >> 45);
+    const double r = fma(m, LOG_IC[j], -1.0);
+    double q = 1.0 / 9.0;
+    q = fma(q, r, -1.0 / 8.0);
+    q = fma(q, r, 1.0 / 7.0);
+    q = fma(q, r, -1.0 / 6.0);
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -1.0 / 4.0);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -1.0 / 2.0);
+    const double r2 = r * r;
+    const double p = fma(r2, q, r);
+    const double kd = (double)(e + (j >> 6));
+    const double hi = fma(kd, LN2_HI, LOG_T[j]);
+    const double lo = fma(kd, LN2_LO, p);
+    return hi + lo;
 }
 
 /* 128-bit two's-complement accumulator and its conversion to double:

@@ -7,7 +7,7 @@
  * load it.  It shares no code, header, table or constant generator with the
  * CUDA path; the only thing both sides agree on is the written numerics
  * contract (Philox4x32-10 keyed as documented, the 52-bit uniform map, the
- * atanh-series logarithm, the fixed-point tally format and the event rules),
+ * table-driven logarithm, the fixed-point tally format and the event rules),
  * which each side implements on its own.
  *
  * Every function returns 0 on success and a negative code on error.
@@ -96,6 +96,9 @@ void or_destroy(or_problem* p);
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double or_u01(uint32_t lo, uint32_t hi);
 double or_log(double u);
+/* entry j of the logarithm's reduction table: 1/c_j rounded (halved for
+ * j >= 64) and T_j = -log(IC_j 2^K_j) rounded */
+void or_log_table(int32_t j, double* ic, double* t);
 int or_fourier_filter(const double* in, double* out, int32_t m, int32_t kappa);
 int or_ma_filter(const double* in, double* out, int32_t m, int32_t k);
 int or_losm_solve(int32_t n_cells, const double* dx, const double* sigma_t, const double* sigma_a,

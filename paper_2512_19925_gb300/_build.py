@@ -46,7 +46,7 @@ def nvcc() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))] + [
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".inc"))] + [
         os.path.join(INCLUDE, "hww.h")]
 
 

@@ -9,9 +9,10 @@
 //     the roulette uniform;
 //   * uniform on (0,1): top 52 bits of a 64-bit word plus one half, times
 //     2^-52 (FP64); top 23 bits plus one half times 2^-23 (FP32 tracking);
-//   * log: reduction to m in [sqrt(1/2), sqrt(2)) and the atanh series
-//     2s(1 + z/3 + ... + z^11/23), z = s^2, s = (m-1)/(m+1), by Horner with
-//     fused multiply-adds, plus k ln 2 (ln 2 split in a 32-bit head and a tail);
+//   * log: table-driven reduction (128 entries by the top mantissa bits),
+//     r = m IC_j - 1, log1p(r) by a degree-9 Horner polynomial with fused
+//     multiply-adds, plus (e + K_j) ln 2 (ln 2 split in a 32-bit head and a
+//     tail) and the table's T_j; see hw_log;
 //   * tallies: contributions rounded to 64-bit integers at a power-of-two
 //     scale, summed as 128-bit integers, so that any order of summation
 //     gives the same bits.
@@ -66,42 +67,53 @@ __host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k
     }
 }
 
-__host__ __device__ __forceinline__ double u01(uint32_t lo, uint32_t hi) {
+// ((x >> 12) + 1/2) 2^-52 of the 64-bit word x: the 52 bits are placed in
+// the mantissa of a double m in [1, 2), then 1 is subtracted and 2^-53 added;
+// both steps are exact, so the value equals the definition, without an
+// integer-to-FP64 conversion (GB300's FP64 pipe is narrow)
+__device__ __forceinline__ double u01(uint32_t lo, uint32_t hi) {
     const uint64_t x = ((uint64_t)hi << 32) | lo;
-    return ((double)(x >> 12) + 0.5) * 0x1p-52;
+    const double m = __longlong_as_double((long long)(0x3FF0000000000000ull | (x >> 12)));
+    return (m - 1.0) + 0x1p-53;
 }
 
-__host__ __device__ __forceinline__ float u01f(uint32_t hi) {
-    return ((float)(hi >> 9) + 0.5f) * 0x1p-23f;
+// ((hi >> 9) + 1/2) 2^-23, the same way in FP32
+__device__ __forceinline__ float u01f(uint32_t hi) {
+    const float m = __int_as_float((int)(0x3F800000u | (hi >> 9)));
+    return (m - 1.0f) + 0x1p-24f;
 }
+
+// Natural logarithm of u in (0, 1), the numerics contract's steps:
+// u = 2^e m with m in [1, 2); j = the top 7 bits of m's mantissa; from the
+// table (log_table.inc) IC_j ~ 1/c_j and T_j = -log(IC_j 2^K_j), K_j = [j >= 64];
+// r = m IC_j - 1 in one fused multiply-add (|r| < 2^-7);
+// log1p(r) = r + r^2 (-1/2 + r/3 - r^2/4 + ... + r^7/9) by Horner's rule;
+// log u = (e + K_j) (ln2_hi + ln2_lo) + T_j + log1p(r), ln 2 split into a
+// 32-bit head and a tail.  No division (an FP64 divide is about ten
+// instructions on GB300's narrow FP64 pipe); within 2 ulp.
+#include "log_table.inc"
 
 __device__ __forceinline__ double hw_log(double u) {
     const long long b = __double_as_longlong(u);
-    int k = (int)((b >> 52) & 0x7ff) - 1023;
-    double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
-    if (m > 0x1.6a09e667f3bcdp+0) {
-        m = m * 0.5;
-        k = k + 1;
-    }
-    const double f = m - 1.0;
-    const double s = f / (m + 1.0);
-    const double z = s * s;
-    double p = 1.0 / 23.0;
-    p = fma(p, z, 1.0 / 21.0);
-    p = fma(p, z, 1.0 / 19.0);
-    p = fma(p, z, 1.0 / 17.0);
-    p = fma(p, z, 1.0 / 15.0);
-    p = fma(p, z, 1.0 / 13.0);
-    p = fma(p, z, 1.0 / 11.0);
-    p = fma(p, z, 1.0 / 9.0);
-    p = fma(p, z, 1.0 / 7.0);
-    p = fma(p, z, 1.0 / 5.0);
-    p = fma(p, z, 1.0 / 3.0);
-    const double s2 = s + s;
-    const double tail = s2 * (z * p);
-    const double kd = (double)k;
-    const double lo = fma(kd, 0x1.a39ef35793c76p-33, tail);
-    return fma(kd, 0x1.62e42fee00000p-1, s2 + lo);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const long long mant = b & 0x000fffffffffffffLL;
+    const double m = __longlong_as_double(mant | 0x3ff0000000000000LL);
+    const int j = (int)(mant >> 45);
+    const double r = fma(m, __ldg(&LOG_IC[j]), -1.0);
+    double q = 1.0 / 9.0;
+    q = fma(q, r, -1.0 / 8.0);
+    q = fma(q, r, 1.0 / 7.0);
+    q = fma(q, r, -1.0 / 6.0);
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -1.0 / 4.0);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -1.0 / 2.0);
+    const double r2 = r * r;
+    const double p = fma(r2, q, r);
+    const double kd = (double)(e + (j >> 6));
+    const double hi = fma(kd, 0x1.62e42fee00000p-1, __ldg(&LOG_T[j]));
+    const double lo = fma(kd, 0x1.a39ef35793c76p-33, p);
+    return hi + lo;
 }
 
 // lineage key of daughter j of a split at event e of a track with key `lin`

@@ -1,5 +1,5 @@
 """Pins of the oracle's numerics contract: Philox4x32-10, the uniform map and
-the atanh-series logarithm.  These run on the CPU only.
+the table-driven logarithm.  These run on the CPU only.
 
 The Philox function is pinned against cuRAND's device implementation in the
 GPU tests; here it is checked for the statistical and structural properties a
@@ -119,3 +119,38 @@ def test_flight_distances_are_unit_exponential():
     # tail probability P(x > 3) = e^-3
     p = float((xs > 3.0).mean())
     assert abs(p - math.exp(-3.0)) < 4.0 * math.sqrt(math.exp(-3.0) / n)
+
+
+def test_log_tables_of_both_sides_agree():
+    # the library's table (generated by csrc/gen_log_table.py with Python's
+    # decimal module) and the oracle's (double-double arithmetic at first
+    # use) are built independently; the logarithm is only the same function
+    # on both sides if they agree bit for bit
+    import os
+    import re
+    import importlib.util
+    here = os.path.dirname(os.path.abspath(__file__))
+    csrc = os.path.join(here, "..", "paper_2512_19925_gb300", "csrc")
+    text = open(os.path.join(csrc, "log_table.inc")).read()
+    blocks = re.findall(r"\{([^}]*)\}", text)
+    ic_dev = [float.fromhex(v.strip()) for v in blocks[0].split(",") if v.strip()]
+    t_dev = [float.fromhex(v.strip()) for v in blocks[1].split(",") if v.strip()]
+    ic_or, t_or = oracle.log_table()
+    assert len(ic_dev) == len(t_dev) == 128
+    assert [x.hex() for x in ic_dev] == [float(x).hex() for x in ic_or]
+    assert [x.hex() for x in t_dev] == [float(x).hex() for x in t_or]
+    # and the committed table is what its generator writes
+    spec = importlib.util.spec_from_file_location("gen_log_table", os.path.join(csrc, "gen_log_table.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    assert gen.render(gen.table()) == text
+
+
+def test_log_table_values_are_correctly_rounded():
+    import decimal
+    decimal.getcontext().prec = 60
+    ic, t = oracle.log_table()
+    for j in range(128):
+        y = ic[j] * (2.0 if j >= 64 else 1.0)
+        assert abs(float(y) - (1.0 / (1.0 + j / 128.0) if j < 64 else 1.0 / ((1.0 + (j + 1) / 128.0) * 0.5))) == 0.0
+        assert float(t[j]) == float(-decimal.Decimal(float(y)).ln())
