@@ -129,6 +129,29 @@ __device__ __forceinline__ long long to_fixed(double x, double scale) {
     return __double2ll_rn(x * scale);
 }
 
+// The same value, x 2^S rounded to the nearest integer (ties to even), from
+// the bits of x in integer arithmetic: the hot loops' FP64 pipe (two
+// instructions here) is the scarce unit on GB300, the integer ALU is not.
+// |x| 2^S must stay below 2^63 (the tally scales are chosen so).
+__device__ __forceinline__ long long fixed_bits(double x, int S) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FFu);
+    if (ex == 0) return 0;  // zero or subnormal: far below one unit
+    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = ex - 1075 + S;  // |x| 2^S = m 2^sh
+    unsigned long long v;
+    if (sh >= 0) {
+        v = m << sh;
+    } else if (sh > -64) {
+        const int s = -sh;
+        const unsigned long long q = m >> s, rem = m & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+        v = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    } else {
+        v = 0;
+    }
+    return (b >> 63) ? -(long long)v : (long long)v;
+}
+
 // add a signed 64-bit value to a split accumulator
 __device__ __forceinline__ void add128(Acc128* a, long long v) {
     if (v == 0) return;

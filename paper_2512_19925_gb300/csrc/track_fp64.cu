@@ -92,7 +92,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
     double S[DERIV ? MAX_SCORES : 1];     // scores of the current track
     double bS[DERIV ? MAX_SCORES : 1];    // scores of the record being expanded
     const double tscale = a.sd->tscale;
-    const double cscale = a.sd->cscale;
+    const int S_t = a.sd->S;  // tscale = 2^S_t
     const double wbar = a.sd->wbar;
     const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
     const int birth = a.sd->birth, ww_on = a.sd->ww_on;
@@ -237,10 +237,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
         {
             // one shared atomic per lane and word (see the FP32 loop)
             const int b = qb;
-            const long long c0 = to_fixed(wl, tscale);
+            const long long c0 = fixed_bits(wl, S_t);
             sadd(&s_tl[k], c0);
-            sadd(&s_tl[I + k], to_fixed(wlmu, tscale));
-            sadd(&s_tl[2 * I + k], to_fixed(wlf, tscale));
+            sadd(&s_tl[I + k], fixed_bits(wlmu, S_t));
+            sadd(&s_tl[2 * I + k], fixed_bits(wlf, S_t));
             if (b == b_blk)
                 sadd(&s_bat[k], c0);
             else
@@ -258,7 +258,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
             }
 #pragma unroll
             for (int j = 0; j < MAX_SCORES; ++j)
-                if (j < P2) sadd(&s_dtl[j * I + k], to_fixed(wl * S[j], tscale));
+                if (j < P2) sadd(&s_dtl[j * I + k], fixed_bits(wl * S[j], S_t));
         }
         // move
         if (ev == 1) {
@@ -302,7 +302,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 a.cen.cell[slot] = q.cell;
                 a.cen.id[slot] = q.id;
 
-                const unsigned long long wfx = (unsigned long long)to_fixed(q.w, cscale);
+                const unsigned long long wfx = (unsigned long long)fixed_bits(q.w, a.sd->Sc);
                 a.cen.lw[slot] = LinW{q.lin, wfx};
                 atomicAdd(&a.gcnt[q.id], 1u);
                 atomicAdd(&a.gw[q.id], wfx);
