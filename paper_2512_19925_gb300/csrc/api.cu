@@ -237,6 +237,7 @@ hww_status alloc_banks(hww_problem* p, Banks<Real>& b) {
     if ((s = dalloc(p, &b.cen.x, C, true)) || (s = dalloc(p, &b.cen.mu, C, true)) ||
         (s = dalloc(p, &b.cen.w, C, true)) || (s = dalloc(p, &b.cen.cell, C, true)) ||
         (s = dalloc(p, &b.cen.id, C, true)) || (s = dalloc(p, &b.cen.lw, C, true)) ||
+        (sizeof(Real) == sizeof(double) && (s = dalloc(p, &b.cen.imu, C, true))) ||
         (s = dalloc(p, &p->member, C, true)) ||
         (s = dalloc(p, &p->cpre, C, true)) || (s = dalloc(p, &p->glist, glist_len(C), true)))
         return s;
@@ -430,6 +431,7 @@ CombArgs<Real> comb_args(hww_problem* p, Banks<Real>& b) {
     c.ccell = b.cen.cell;
     c.cid = b.cen.id;
     c.clw = b.cen.lw;
+    c.cimu = b.cen.imu;
     c.gcnt = p->gcnt;
     c.gro = p->gro;
     c.gcur = p->gcur;
@@ -1461,6 +1463,7 @@ hww_status set_bank(hww_problem* p, const double* x, const double* mu, const int
                 r[k] = BankRec<double>{};
                 r[k].x = x[k];
                 r[k].mu = mu[k];
+                r[k].imu = 1.0 / mu[k];
                 r[k].cell = cell[k];
             }
             e = cudaMemcpy(p->b64.bank, r.data(), sizeof(BankRec<double>) * n, cudaMemcpyHostToDevice);

@@ -83,7 +83,8 @@ struct __align__(16) BankRec<float> {
 template <>
 struct __align__(32) BankRec<double> {
     double x, mu;
-    int32_t cell, pad[3];
+    double imu;  // 1/mu, carried so that a track start needs no FP64 divide
+    int32_t cell, pad;
 };
 
 // a census particle's comb key and weight, read together by the comb
@@ -117,6 +118,7 @@ struct CenQ {
     int32_t* cell;
     uint32_t* id;
     LinW* lw;  // lineage key and weight at the comb scale 2^Sc, one 16-byte word
+    Real* imu; // 1/mu of the FP64 path (its next start bank carries it); unused in FP32
     double* S;  // [P2][cap] scores (derivative runs only)
     unsigned long long* count;
     long long cap;

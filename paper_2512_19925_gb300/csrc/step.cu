@@ -506,6 +506,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
         rec.x = x;
         rec.mu = mu;
         rec.cell = cell;
+        if constexpr (sizeof(Real) == sizeof(double)) rec.imu = a.cimu[j];
         for (long long k = k0; k < k1; ++k) a.bank[k] = rec;
         // derivative runs: every copy keeps the scores of its source
         for (int q = 0; q < a.P2; ++q) {

@@ -35,6 +35,7 @@ struct CombArgs {
     const int32_t* ccell;
     const uint32_t* cid;
     const LinW* clw;  // [cen_cap] lineage keys and comb weights
+    const Real* cimu; // [cen_cap] 1/mu (FP64 path)
     const uint32_t* gcnt;
     const GroupRec* gro;  // [N+1] group records (entry N: totals)
     uint32_t* gcur;

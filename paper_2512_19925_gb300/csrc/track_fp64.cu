@@ -117,7 +117,8 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     uint32_t rr[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 0xFFFFFFFEu};
                     philox4x32_10(rr, k0, k1);
                     q.mu = 2.0 * u01(rr[0], rr[1]) - 1.0;
-                }
+                    q.inv_mu = 1.0 / q.mu;
+                }  // else the parent's direction and its reciprocal
                 if constexpr (DERIV) {
 #pragma unroll
                     for (int j = 0; j < MAX_SCORES; ++j) S[j] = bS[j];
@@ -150,15 +151,18 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                         if (q.x <= a.edges[0] && q.mu < 0.0 && a.bc_l == 1) q.mu = -q.mu;
                         if (q.x >= a.edges[I] && q.mu > 0.0 && a.bc_r == 1) q.mu = -q.mu;
                         q.cell = (q.mu < 0.0) ? a.birth_cell_neg : a.birth_cell_pos;
+                        q.inv_mu = 1.0 / q.mu;
                     } else {
                         const BankRec<double> r = a.bank[i];
                         q.x = r.x;
                         q.mu = r.mu;
+                        q.inv_mu = r.imu;
                         q.cell = r.cell;
                     }
                 } else {
                     q.x = a.rin.x[i];
                     q.mu = a.rin.mu[i];
+                    q.inv_mu = 1.0 / q.mu;
                     q.tau = a.rin.tau[i];
                     q.w = a.rin.w[i];
                     q.cell = a.rin.cell[i];
@@ -188,11 +192,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                             uint32_t rr[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 0xFFFFFFFEu};
                             philox4x32_10(rr, k0, k1);
                             q.mu = 2.0 * u01(rr[0], rr[1]) - 1.0;
+                            q.inv_mu = 1.0 / q.mu;
                         }
                     }
                 }
             }
-            q.inv_mu = 1.0 / q.mu;
             have = true;
             evs = 0;
             qb = batch_of(q.id, a.B, a.N, a.batch_m);
@@ -304,6 +308,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
 
                 const unsigned long long wfx = (unsigned long long)fixed_bits(q.w, a.sd->Sc);
                 a.cen.lw[slot] = LinW{q.lin, wfx};
+                a.cen.imu[slot] = q.inv_mu;
                 atomicAdd(&a.gcnt[q.id], 1u);
                 atomicAdd(&a.gw[q.id], wfx);
             } else {
