@@ -114,7 +114,7 @@ class ClockSampler:
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -133,22 +133,23 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    def summary(self, window=None):
+        """Median SM clock, maximum clock and the throttle reasons seen in
+        the samples whose timestamps fall in `window` (host epoch seconds of
+        the timed region); all samples when no window is given or none falls
+        in it (the count says which)."""
+        rows = []
         try:
             for line in open(self.path):
                 f = [x.strip() for x in line.split(",")]
                 if len(f) < 9:
                     continue
                 try:
-                    sm.append(float(f[1]))
-                    mx.append(float(f[2]))
-                except ValueError:
+                    ts = time.mktime(time.strptime(f[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + f[0].split(".")[1]) if "." in f[0] else 0.0
+                    rows.append((ts, float(f[1]), float(f[2]), f[5:9]))
+                except (ValueError, IndexError):
                     continue
-                for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
-                                      "sw_power_cap"), f[5:9]):
-                    if val.lower() == "active":
-                        reasons.add(name)
         except Exception:
             pass
         finally:
@@ -156,10 +157,20 @@ class ClockSampler:
                 os.unlink(self.path)
             except Exception:
                 pass
+        inside = [r for r in rows if window and window[0] <= r[0] <= window[1]]
+        use = inside if inside else rows
+        sm = [r[1] for r in use]
+        mx = [r[2] for r in use]
+        reasons = set()
+        for r in use:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 r[3]):
+                if val.lower() == "active":
+                    reasons.add(name)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "in_timed_region": bool(inside)}
 
 
 def fom_sigma(batch, tau_s):
@@ -187,6 +198,7 @@ def run_path(hww, torch, precision, n_particles, seed, warmup, steps, barrier):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
     e0.record(stream)
     segs = 0
     census = 0
@@ -196,12 +208,13 @@ def run_path(hww, torch, precision, n_particles, seed, warmup, steps, barrier):
         census += s["census"]
     e1.record(stream)
     torch.cuda.synchronize()
+    t1 = time.time()
     barrier()
     ms = e0.elapsed_time(e1)
     cnt = p.counters()
     batch = p.get_tallies(hww.BATCH_PHI)
     p.close()
-    return dict(ms=ms, segments=segs, census=census, counters=cnt, batch=batch, n=n_particles)
+    return dict(ms=ms, segments=segs, census=census, counters=cnt, batch=batch, n=n_particles, window=(t0, t1))
 
 
 def run_e2e(hww, torch, precision, n_particles, seed, warmup, steps):
@@ -377,8 +390,9 @@ def main(args):
         args.no_fp64 = args.no_batch = args.no_deriv = True
     N = args.particles
     with ClockSampler(local) as clk:
+        time.sleep(1.5)  # nvidia-smi is sampling by the time the timed steps start
         fast = run_path(hww, torch, "fp32", N, seed, args.warmup, args.steps, barrier)
-    clocks = clk.summary()
+    clocks = clk.summary(fast["window"])
     base = run_path(hww, torch, "fp64", N, seed, args.warmup, args.steps, barrier) if not args.no_fp64 else None
 
     red = RankReduce(dist, "cuda")
