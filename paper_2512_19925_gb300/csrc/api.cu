@@ -673,6 +673,8 @@ hww_status stage_pre(hww_problem* p) {
 // the closures), closures and initial conditions at t^n, the fully implicit
 // HLOSM (Eqs. losm-0, losm-1, losm-disc-bc), and the step-state advance
 hww_status stage_post(hww_problem* p) {
+    launch_tl_phi(p->tl, p->batch, p->B, p->I, p->stream);
+    ++p->kernel_launches;
     if (p->n_updates > 0)  // an in-step update left partial census tallies
         HWW_CK(cudaMemsetAsync(p->cent, 0, sizeof(Acc128) * 3 * (size_t)p->I, p->stream));
     hww_status st = p->fp32 ? comb_step(p, p->b32) : comb_step(p, p->b64);

@@ -519,6 +519,23 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
         if (s_cen[i] != 0) add128(&a.cent[i], s_cen[i]);
 }
 
+// the track-length flux tally as the sum of its variance-batch rows (the
+// tracking adds each segment's flux to its batch row only): split
+// accumulators add word by word, so the words equal those a direct
+// accumulation would hold
+__global__ void tl_phi_kernel(Acc128* tl, const Acc128* batch, int B, int I) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I; i += gridDim.x * blockDim.x) {
+        unsigned long long lo = 0;
+        long long hi = 0;
+        for (int b = 0; b < B; ++b) {
+            const Acc128 v = batch[(long long)b * I + i];
+            lo += v.lo;
+            hi += v.hi;
+        }
+        tl[i] = Acc128{lo, hi};
+    }
+}
+
 __global__ void comb_finalize_kernel(StepDev* sd, const GroupRec* gro, const unsigned long long* ncensus_ptr,
                                      long long N, long long cen_cap, unsigned* err) {
     const unsigned long long W = gro[N].offw;
@@ -542,6 +559,10 @@ __global__ void comb_finalize_kernel(StepDev* sd, const GroupRec* gro, const uns
 }
 
 }  // namespace
+
+void launch_tl_phi(Acc128* tl, const Acc128* batch, int B, int I, cudaStream_t s) {
+    tl_phi_kernel<<<(I + 255) / 256, 256, 0, s>>>(tl, batch, B, I);
+}
 
 void launch_group_scan(const ScanArgs& a, cudaStream_t s) {
     const long long ntiles = (a.n + SCAN_TILE - 1) / SCAN_TILE;

@@ -55,6 +55,8 @@ struct CombArgs {
 };
 
 void launch_group_scan(const ScanArgs& a, cudaStream_t s);
+// track-length flux tally = sum of its variance-batch rows
+void launch_tl_phi(Acc128* tl, const Acc128* batch, int B, int I, cudaStream_t s);
 long long group_scan_tiles(long long n);
 // the comb up to the copies (group scan excluded), with the census tallies;
 // the finalize step (which advances the step state) runs separately, last

@@ -235,10 +235,11 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
         {
             // one shared atomic per lane and word: merging the lanes of a
             // warp that share a cell first (match + shuffle tree) measured
-            // slower than the atomics it saves
+            // slower than the atomics it saves.  The flux goes to the
+            // variance-batch row only: the flux tally is the sum of the batch
+            // rows, formed after the tracking (one atomic fewer per segment)
             const int b = qb;
             const long long c0 = fx_mul(q.W, l);
-            sadd(&s_tl[k], c0);
             sadd(&s_tl[I + k], fx_mul(q.W, l * q.mu));
             sadd(&s_tl[2 * I + k], fx_mul(q.W, l * f3));
             if (b == b_blk)

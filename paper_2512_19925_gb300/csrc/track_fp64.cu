@@ -239,10 +239,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
         const double wlmu = wl * q.mu;
         const double wlf = wl * (1.0 / 3.0 - q.mu * q.mu);
         {
-            // one shared atomic per lane and word (see the FP32 loop)
+            // one shared atomic per lane and word; the flux to the batch row
+            // only (see the FP32 loop)
             const int b = qb;
             const long long c0 = fixed_bits(wl, S_t);
-            sadd(&s_tl[k], c0);
             sadd(&s_tl[I + k], fixed_bits(wlmu, S_t));
             sadd(&s_tl[2 * I + k], fixed_bits(wlf, S_t));
             if (b == b_blk)
