@@ -486,15 +486,6 @@ hww_status err_to_status(unsigned e) {
     return HWW_OK;
 }
 
-// read and clear the sticky device error word (synchronizes the stream)
-hww_status take_device_error(const hww_problem* p) {
-    unsigned e = 0;
-    HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
-    HWW_CK(cudaStreamSynchronize(p->stream));
-    if (e) HWW_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
-    return err_to_status(e);
-}
-
 __global__ void normalize_kernel(int kind, const Acc128* a, int n, int I, int B, long long N, const double* dx,
                                  double v, double dt, const StepDev* sd, double* out) {
     const double isc = pow2(-sd->S);
