@@ -447,6 +447,7 @@ CombArgs<Real> comb_args(hww_problem* p, Banks<Real>& b) {
     c.cent = p->cent;
     c.P2 = p->P2;
     c.cS = b.cen.S;
+    c.dcen = p->dcen;
     c.bS = p->bS;
     return c;
 }
@@ -467,7 +468,7 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
     launch_comb(comb_args(p, b), comb_grid(p), p->stream);
     HWW_CK(cudaGetLastError());
-    p->kernel_launches += 5;
+    p->kernel_launches += 5 + (p->P2 > 0 ? 1 : 0);
     return HWW_OK;
 }
 

@@ -5,6 +5,8 @@
 //             decided in integers.
 // Built with contraction off so that the comb positions are the single IEEE
 // operations written.
+#include <algorithm>
+
 #include "hww_internal.cuh"
 #include "step_kernels.cuh"
 #include "track_common.cuh"
@@ -468,6 +470,41 @@ __global__ void census_tally_kernel(CombArgs<Real> a) {
         if (s_cen[i] != 0) add128(&a.cent[i], s_cen[i]);
 }
 
+// census derivative tallies of a derivative run: w S_q, w mu S_q and
+// w (1/3 - mu^2) S_q of each census particle, the FP64 products of the
+// numerics contract rounded at the tally scale.  Score q is the grid's
+// y index; each block keeps its plane (3 I words) in shared memory and
+// flushes it once (a global atomic per census particle and word had the
+// atomic units serialize on the few hundred cells).
+template <class Real>
+__global__ void deriv_census_kernel(CombArgs<Real> a) {
+    extern __shared__ long long s_d[];  // 3 I
+    const int I = a.I;
+    const int q = blockIdx.y;
+    for (int i = threadIdx.x; i < 3 * I; i += blockDim.x) s_d[i] = 0;
+    __syncthreads();
+    const long long m = (long long)*a.ncensus_ptr;
+    const long long mm = m < a.cen_cap ? m : a.cen_cap;
+    const int S = a.sd->S;
+    const double* sc = a.cS + (long long)q * a.cen_cap;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
+         j += (long long)gridDim.x * blockDim.x) {
+        const double w = a.cw[j];
+        const double mu = (double)a.cmu[j];
+        const int k = a.ccell[j];
+        const double sq = sc[j];
+        const double wmu = w * mu;
+        const double wf = w * (1.0 / 3.0 - mu * mu);
+        sadd(&s_d[k], fixed_bits(w * sq, S));
+        sadd(&s_d[I + k], fixed_bits(wmu * sq, S));
+        sadd(&s_d[2 * I + k], fixed_bits(wf * sq, S));
+    }
+    __syncthreads();
+    Acc128* d = a.dcen + (long long)q * 3 * I;
+    for (int i = threadIdx.x; i < 3 * I; i += blockDim.x)
+        if (s_d[i] != 0) add128(&d[i], s_d[i]);
+}
+
 // census order: each census particle's census tallies (Eq. ct-mc; block-
 // private in shared memory), its teeth and its copies
 template <class Real>
@@ -580,6 +617,9 @@ void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
     comb_seg_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_big_kernel<Real><<<grid, BIG_T, 0, s>>>(a);
     comb_write_kernel<Real><<<grid, 256, sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
+    if (a.P2 > 0)  // about one block per SM and score: few plane flushes
+        deriv_census_kernel<Real><<<dim3((unsigned)std::max(1, grid / 8), (unsigned)a.P2), 256,
+                                    sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
 }
 
 template <class Real>
@@ -599,7 +639,8 @@ void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s) {
 
 template <class Real>
 int comb_write_smem_optin(size_t smem) {
-    return raise_smem_limit((const void*)comb_write_kernel<Real>, smem);
+    const int e = raise_smem_limit((const void*)comb_write_kernel<Real>, smem);
+    return e ? e : raise_smem_limit((const void*)deriv_census_kernel<Real>, smem);
 }
 
 template void launch_comb<double>(const CombArgs<double>&, int, cudaStream_t);

@@ -51,6 +51,7 @@ struct CombArgs {
     Acc128* cent;      // census tallies 3 I
     int P2;            // scores per particle (0: none)
     const double* cS;  // [P2][cen_cap] census scores
+    Acc128* dcen;      // [P2][3][I] census derivative tallies (derivative runs)
     double* bS;        // [P2][N] start-bank scores
 };
 

@@ -49,6 +49,49 @@ struct P64 {
     uint32_t e;
 };
 
+// The pending parent of a lane (the record whose daughters it expands) and
+// its scores, in shared memory, one column per thread: written at a split,
+// read once per daughter; registers are what limits the resident warps (the
+// derivative loop spilled with the parent in registers).
+template <bool DERIV>
+struct PendingParent64 {
+    double x[TRACK_THREADS], mu[TRACK_THREADS], imu[TRACK_THREADS], tau[TRACK_THREADS], w[TRACK_THREADS];
+    int cell[TRACK_THREADS];
+    uint32_t id[TRACK_THREADS], e[TRACK_THREADS];
+    uint64_t lin[TRACK_THREADS];
+    double S[DERIV ? MAX_SCORES : 1][TRACK_THREADS];
+    __device__ __forceinline__ void store(int t, const P64& q, const double* sc) {
+        x[t] = q.x;
+        mu[t] = q.mu;
+        imu[t] = q.inv_mu;
+        tau[t] = q.tau;
+        w[t] = q.w;
+        cell[t] = q.cell;
+        id[t] = q.id;
+        e[t] = q.e;
+        lin[t] = q.lin;
+        if constexpr (DERIV) {
+#pragma unroll
+            for (int j = 0; j < MAX_SCORES; ++j) S[j][t] = sc[j];
+        }
+    }
+    __device__ __forceinline__ void load(int t, P64& q, double* sc) const {
+        q.x = x[t];
+        q.mu = mu[t];
+        q.inv_mu = imu[t];
+        q.tau = tau[t];
+        q.w = w[t];
+        q.cell = cell[t];
+        q.id = id[t];
+        q.e = e[t];
+        q.lin = lin[t];
+        if constexpr (DERIV) {
+#pragma unroll
+            for (int j = 0; j < MAX_SCORES; ++j) sc[j] = S[j][t];
+        }
+    }
+};
+
 template <bool DERIV>
 __device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P64& q, const double* S, double w,
                                             uint32_t e, uint32_t jstart, uint32_t jcount,
@@ -83,15 +126,14 @@ __device__ __forceinline__ void push_record(const TrackArgs<double>& a, const P6
 template <bool DERIV, uint32_t LOCAL_MAX>
 __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long item, const long long item_end,
                                           const long long stride, unsigned* s_next, const int b_blk, long long* sm,
-                                          Counters& cnt) {
+                                          Counters& cnt, PendingParent64<DERIV>* pp) {
     const int I = a.I;
+    const int t = threadIdx.x;
     long long* s_tl = sm;
     long long* s_bat = sm + 3 * I;                // batch row of the current id range
     long long* s_dtl = sm + TALLY_ROWS * I;       // derivative runs: [P2][I]
     const int R = a.R, P2 = a.P2;
     double S[DERIV ? MAX_SCORES : 1];     // scores of the current track
-    double bS[DERIV ? MAX_SCORES : 1];    // scores of the record being expanded
-    const double tscale = a.sd->tscale;
     const int S_t = a.sd->S;  // tscale = 2^S_t
     const double wbar = a.sd->wbar;
     const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
@@ -100,7 +142,6 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
     // flattened event loop: a lane whose track ends loads its next one while
     // the other lanes take their next event
     P64 q;
-    P64 base;  // record whose daughters are being expanded
     uint32_t jnext = 0, jend = 0;
     bool fresh = false;  // the record being expanded holds a collision's extra particles
     bool have = false;
@@ -109,8 +150,8 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
     for (;;) {
         if (!have) {
             if (jnext < jend) {
-                q = base;
-                q.lin = lineage_hash(base.lin, base.e, jnext);
+                pp->load(t, q, S);
+                q.lin = lineage_hash(q.lin, q.e, jnext);
                 q.e = 0;
                 ++jnext;
                 if (fresh) {  // its own isotropic direction
@@ -119,10 +160,6 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     q.mu = 2.0 * u01(rr[0], rr[1]) - 1.0;
                     q.inv_mu = 1.0 / q.mu;
                 }  // else the parent's direction and its reciprocal
-                if constexpr (DERIV) {
-#pragma unroll
-                    for (int j = 0; j < MAX_SCORES; ++j) S[j] = bS[j];
-                }
             } else {
                 long long i;
                 if (s_next) {
@@ -176,16 +213,12 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     }
                     const uint32_t jc = a.rin.jcount[i];
                     if (jc) {
-                        base = q;
-                        if constexpr (DERIV) {
-#pragma unroll
-                            for (int j = 0; j < MAX_SCORES; ++j) bS[j] = S[j];
-                        }
+                        pp->store(t, q, S);
                         const uint32_t js = a.rin.jstart[i];
                         fresh = (js & FRESH_DIRECTION) != 0;
                         jnext = js & ~FRESH_DIRECTION;
                         jend = jnext + jc;
-                        q.lin = lineage_hash(base.lin, base.e, jnext);
+                        q.lin = lineage_hash(q.lin, q.e, jnext);
                         q.e = 0;
                         ++jnext;
                         if (fresh) {  // its own isotropic direction
@@ -278,21 +311,8 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
         q.e = q.e + 1;
         ++evs;
         if (ev == 0) {
-            // census: the bank record (its tallies come from the census pass;
-            // derivative runs tally their census derivatives here)
-            if constexpr (DERIV) {
-                const double wmu = q.w * q.mu;
-                const double wf = q.w * (1.0 / 3.0 - q.mu * q.mu);
-#pragma unroll
-                for (int j = 0; j < MAX_SCORES; ++j) {
-                    if (j < P2) {
-                        Acc128* d = a.dcen + (long long)j * 3 * I;
-                        add128(&d[k], to_fixed(q.w * S[j], tscale));
-                        add128(&d[I + k], to_fixed(wmu * S[j], tscale));
-                        add128(&d[2 * I + k], to_fixed(wf * S[j], tscale));
-                    }
-                }
-            }
+            // census: the bank record (its tallies, and a derivative run's
+            // census derivative tallies, come from the comb's census pass)
             const unsigned long long slot = warp_reserve(a.cen.count);
             if ((long long)slot < a.cen.cap) {
                 if constexpr (DERIV) {
@@ -331,17 +351,17 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     const double amu = fabs(q.mu);
                     const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
                     const double wi = q.w * ia;
-                    add128(&a.bnd[3 * side + 0], to_fixed(wi, tscale));
-                    add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu), tscale));
-                    add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), tscale));
+                    add128(&a.bnd[3 * side + 0], fixed_bits(wi, S_t));
+                    add128(&a.bnd[3 * side + 1], fixed_bits(wi * (1.0 / 3.0 - q.mu * q.mu), S_t));
+                    add128(&a.bnd[3 * side + 2], fixed_bits(wi * (0.5 - amu), S_t));
                     if constexpr (DERIV) {
 #pragma unroll
                         for (int j = 0; j < MAX_SCORES; ++j) {
                             if (j < P2) {
                                 Acc128* d = a.dbnd + 6 * j + 3 * side;
-                                add128(&d[0], to_fixed(wi * S[j], tscale));
-                                add128(&d[1], to_fixed(wi * (1.0 / 3.0 - q.mu * q.mu) * S[j], tscale));
-                                add128(&d[2], to_fixed(wi * (0.5 - amu) * S[j], tscale));
+                                add128(&d[0], fixed_bits(wi * S[j], S_t));
+                                add128(&d[1], fixed_bits(wi * (1.0 / 3.0 - q.mu * q.mu) * S[j], S_t));
+                                add128(&d[2], fixed_bits(wi * (0.5 - amu) * S[j], S_t));
                             }
                         }
                     }
@@ -384,12 +404,9 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                 const uint32_t nx = nsec - 1;
                 uint32_t jr = 1;  // the first daughter that goes to the record queue
                 if (LOCAL_MAX > 0 && jnext >= jend) {
-                    base = q;
-                    base.e = e_ev | SECONDARY_EVENT;
-                    if constexpr (DERIV) {
-#pragma unroll
-                        for (int j = 0; j < MAX_SCORES; ++j) bS[j] = S[j];
-                    }
+                    P64 b = q;
+                    b.e = e_ev | SECONDARY_EVENT;
+                    pp->store(t, b, S);
                     fresh = true;
                     jnext = 1;
                     jend = min(nsec, 1u + LOCAL_MAX);
@@ -436,13 +453,10 @@ __device__ __forceinline__ void run_items(const TrackArgs<double>& a, long long 
                     // this lane (same block, so their batch row stays in
                     // shared memory); the bound keeps a large split from
                     // holding one lane while the rest of its block waits
-                    base = q;
-                    base.w = wd;
-                    base.e = e_ev;
-                    if constexpr (DERIV) {
-#pragma unroll
-                        for (int j = 0; j < MAX_SCORES; ++j) bS[j] = S[j];
-                    }
+                    P64 b = q;
+                    b.w = wd;
+                    b.e = e_ev;
+                    pp->store(t, b, S);
                     fresh = false;
                     jnext = 1;
                     jend = min(nd, 1u + LOCAL_MAX);
@@ -490,9 +504,10 @@ template <bool DERIV>
 // registers; at three blocks it spills to local memory, whose traffic (the
 // L1 left beside the shared tallies hits ~20% of it) costs more time than
 // the extra warps hide.
-__global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
+__global__ void __launch_bounds__(TRACK_THREADS, 2) track64_kernel(TrackArgs<double> a) {
     extern __shared__ long long sm[];
     __shared__ unsigned s_next;
+    __shared__ PendingParent64<DERIV> s_pp;
     const int I = a.I;
     if (threadIdx.x == 0) s_next = 0;
     const int rows = DERIV ? TALLY_ROWS + a.P2 : TALLY_ROWS;
@@ -528,7 +543,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
         item_end = n_use;
         stride = (long long)gridDim.x * blockDim.x;
     }
-    run_items<DERIV, LOCAL_DAUGHTERS>(a, item, item_end, stride, dyn, b_blk, sm, cnt);
+    run_items<DERIV, LOCAL_DAUGHTERS>(a, item, item_end, stride, dyn, b_blk, sm, cnt, &s_pp);
     __syncthreads();
     flush_tallies(sm, I, a.tl);
     if constexpr (DERIV) {
@@ -544,12 +559,13 @@ __global__ void __launch_bounds__(256, 2) track64_kernel(TrackArgs<double> a) {
 // Persistent batched variant: blocks pop tiles (problem, id range) from a
 // device counter; the block-private tallies are flushed when a block moves
 // to another problem, the batch row after every tile.
-__global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<double>* args, BatchPlan plan) {
+__global__ void __launch_bounds__(TRACK_THREADS, 2) track64_kernel_batch(const TrackArgs<double>* args, BatchPlan plan) {
     extern __shared__ long long sm[];
     __shared__ TrackArgs<double> A;
     __shared__ long long s_t;
     __shared__ int s_p;
     __shared__ unsigned s_next;
+    __shared__ PendingParent64<false> s_pp;
     Counters cnt;
     cnt.zero();
     const long long total = plan.tile_off[plan.P];
@@ -593,7 +609,7 @@ __global__ void __launch_bounds__(256, 2) track64_kernel_batch(const TrackArgs<d
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
         const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N, A.batch_m) : -1;
-        run_items<false, 0>(A, i0, i1, 0, &s_next, b_tile, sm, cnt);
+        run_items<false, 0>(A, i0, i1, 0, &s_next, b_tile, sm, cnt, &s_pp);
         __syncthreads();
         if (b_tile >= 0)
             for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
