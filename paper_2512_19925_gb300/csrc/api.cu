@@ -1052,7 +1052,8 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     const size_t cen_smem = sizeof(long long) * 3 * (size_t)I;
     if ((p->fp32 ? track_smem_optin_fp32(p->track_smem) : track_smem_optin_fp64(p->track_smem, p->P2 > 0)) != 0 ||
         (p->fp32 ? comb_write_smem_optin<float>(cen_smem) : comb_write_smem_optin<double>(cen_smem)) != 0 ||
-        (p->fp32 ? census_tally_smem_optin<float>(cen_smem) : census_tally_smem_optin<double>(cen_smem)) != 0) {
+        (p->fp32 ? census_tally_smem_optin<float>(cen_smem) : census_tally_smem_optin<double>(cen_smem)) != 0 ||
+        (P2 > 0 && (p->fp32 ? deriv_census_smem_optin<float>(P2, I) : deriv_census_smem_optin<double>(P2, I)) != 0)) {
         destroy_problem(p);
         return HWW_ERR_CUDA;
     }

@@ -432,15 +432,15 @@ __device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned 
 // exactly as the precision's event loop forms them at a census event:
 // FP64 round(x 2^S) of the FP64 products w, w mu, w (1/3 - mu^2); FP32 the
 // fixed-point weight W = round(w 2^S) and round(W mu), round(W (1/3 - mu^2))
-__device__ __forceinline__ void census_terms(double w, double mu, double tscale, long long& c0, long long& c1,
+__device__ __forceinline__ void census_terms(double w, double mu, int S, long long& c0, long long& c1,
                                              long long& c2) {
-    c0 = to_fixed(w, tscale);
-    c1 = to_fixed(w * mu, tscale);
-    c2 = to_fixed(w * (1.0 / 3.0 - mu * mu), tscale);
+    c0 = fixed_bits(w, S);
+    c1 = fixed_bits(w * mu, S);
+    c2 = fixed_bits(w * (1.0 / 3.0 - mu * mu), S);
 }
-__device__ __forceinline__ void census_terms(double w, float mu, double tscale, long long& c0, long long& c1,
+__device__ __forceinline__ void census_terms(double w, float mu, int S, long long& c0, long long& c1,
                                              long long& c2) {
-    c0 = to_fixed(w, tscale);
+    c0 = fixed_bits(w, S);
     c1 = fx_mul(c0, mu);
     c2 = fx_mul(c0, 1.0f / 3.0f - mu * mu);
 }
@@ -455,12 +455,12 @@ __global__ void census_tally_kernel(CombArgs<Real> a) {
     __syncthreads();
     const long long m = (long long)*a.ncensus_ptr;
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
-    const double tscale = a.sd->tscale;
+    const int S = a.sd->S;  // the tally scale 2^S
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
         const int k = a.ccell[j];
         long long c0, c1, c2;
-        census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
+        census_terms(a.cw[j], a.cmu[j], S, c0, c1, c2);
         sadd(&s_cen[k], c0);
         sadd(&s_cen[I + k], c1);
         sadd(&s_cen[2 * I + k], c2);
@@ -505,6 +505,41 @@ __global__ void deriv_census_kernel(CombArgs<Real> a) {
         if (s_d[i] != 0) add128(&d[i], s_d[i]);
 }
 
+// The same tallies for all scores in one pass over the census bank, when
+// their planes (3 P2 I words) fit one block's shared memory: one block of
+// 1024 threads per SM, the census particle's w mu and w (1/3 - mu^2) formed
+// once for all scores.
+constexpr size_t DERIV_ALL_SMEM_MAX = 200 * 1024;
+
+template <class Real>
+__global__ void __launch_bounds__(1024) deriv_census_all_kernel(CombArgs<Real> a) {
+    extern __shared__ long long s_d[];  // [P2][3][I]
+    const int I = a.I, P2 = a.P2;
+    for (int i = threadIdx.x; i < 3 * P2 * I; i += blockDim.x) s_d[i] = 0;
+    __syncthreads();
+    const long long m = (long long)*a.ncensus_ptr;
+    const long long mm = m < a.cen_cap ? m : a.cen_cap;
+    const int S = a.sd->S;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
+         j += (long long)gridDim.x * blockDim.x) {
+        const double w = a.cw[j];
+        const double mu = (double)a.cmu[j];
+        const int k = a.ccell[j];
+        const double wmu = w * mu;
+        const double wf = w * (1.0 / 3.0 - mu * mu);
+        for (int q = 0; q < P2; ++q) {
+            const double sq = a.cS[(long long)q * a.cen_cap + j];
+            long long* d = s_d + (long long)q * 3 * I;
+            sadd(&d[k], fixed_bits(w * sq, S));
+            sadd(&d[I + k], fixed_bits(wmu * sq, S));
+            sadd(&d[2 * I + k], fixed_bits(wf * sq, S));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * P2 * I; i += blockDim.x)
+        if (s_d[i] != 0) add128(&a.dcen[i], s_d[i]);
+}
+
 // census order: each census particle's census tallies (Eq. ct-mc; block-
 // private in shared memory), its teeth and its copies
 template <class Real>
@@ -517,7 +552,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
     const unsigned long long W = a.gro[a.N].offw;
     const unsigned U = a.sd->U_comb;
-    const double tscale = a.sd->tscale;
+    const int S = a.sd->S;  // the tally scale 2^S
     const ToothScale ts = tooth_scale(W, a.N);
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
@@ -526,7 +561,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
             // per lane and word (a warp aggregation would rarely merge lanes)
             const int k = a.ccell[j];
             long long c0, c1, c2;
-            census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
+            census_terms(a.cw[j], a.cmu[j], S, c0, c1, c2);
             sadd(&s_cen[k], c0);
             sadd(&s_cen[I + k], c1);
             sadd(&s_cen[2 * I + k], c2);
@@ -617,9 +652,14 @@ void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
     comb_seg_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_big_kernel<Real><<<grid, BIG_T, 0, s>>>(a);
     comb_write_kernel<Real><<<grid, 256, sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
-    if (a.P2 > 0)  // about one block per SM and score: few plane flushes
-        deriv_census_kernel<Real><<<dim3((unsigned)std::max(1, grid / 8), (unsigned)a.P2), 256,
-                                    sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
+    if (a.P2 > 0) {  // about one block per SM (and score): few plane flushes
+        const size_t all = sizeof(long long) * 3 * (size_t)a.P2 * (size_t)a.I;
+        if (all <= DERIV_ALL_SMEM_MAX)
+            deriv_census_all_kernel<Real><<<(unsigned)std::max(1, grid / 8), 1024, all, s>>>(a);
+        else
+            deriv_census_kernel<Real><<<dim3((unsigned)std::max(1, grid / 8), (unsigned)a.P2), 256,
+                                        sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
+    }
 }
 
 template <class Real>
@@ -642,6 +682,15 @@ int comb_write_smem_optin(size_t smem) {
     const int e = raise_smem_limit((const void*)comb_write_kernel<Real>, smem);
     return e ? e : raise_smem_limit((const void*)deriv_census_kernel<Real>, smem);
 }
+
+// the all-scores census derivative pass: its planes, when they fit
+template <class Real>
+int deriv_census_smem_optin(int P2, int I) {
+    const size_t all = sizeof(long long) * 3 * (size_t)P2 * (size_t)I;
+    return (all <= DERIV_ALL_SMEM_MAX) ? raise_smem_limit((const void*)deriv_census_all_kernel<Real>, all) : 0;
+}
+template int deriv_census_smem_optin<double>(int, int);
+template int deriv_census_smem_optin<float>(int, int);
 
 template void launch_comb<double>(const CombArgs<double>&, int, cudaStream_t);
 template void launch_comb<float>(const CombArgs<float>&, int, cudaStream_t);

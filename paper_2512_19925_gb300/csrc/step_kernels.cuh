@@ -67,6 +67,8 @@ template <class Real>
 void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s);
 template <class Real>
 int comb_write_smem_optin(size_t smem);
+template <class Real>
+int deriv_census_smem_optin(int P2, int I);
 // census tallies of the census bank so far, into the (cleared) tallies
 template <class Real>
 void launch_census_tallies(const CombArgs<Real>& a, int grid, cudaStream_t s);
