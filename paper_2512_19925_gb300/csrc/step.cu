@@ -392,13 +392,12 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
 }
 
 // T_k >= C for tooth k at T_k = (k + (2U+1)/2^33) W / N, decided exactly:
-// (k 2^33 + 2U + 1) W >= N C 2^33 in 128-bit integers
-__device__ __forceinline__ bool tooth_at_or_after(long long k, unsigned long long C, unsigned long long W,
-                                                  long long N, unsigned U) {
+// (k 2^33 + 2U + 1) W >= N C 2^33 in 128-bit integers; the right-hand side
+// (rh, rl) depends on C only and is formed once per search
+__device__ __forceinline__ bool tooth_at_or_after(long long k, unsigned long long W, unsigned U,
+                                                  unsigned long long rh, unsigned long long rl) {
     const unsigned long long a = ((unsigned long long)k << 33) + 2ull * U + 1ull;
     const unsigned long long lh = __umul64hi(a, W), ll = a * W;
-    const unsigned long long th = __umul64hi((unsigned long long)N, C), tl = (unsigned long long)N * C;
-    const unsigned long long rh = (th << 33) | (tl >> 31), rl = tl << 33;
     return (lh > rh) || (lh == rh && ll >= rl);
 }
 
@@ -423,8 +422,10 @@ __device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned 
     const unsigned long long Cr = C >> ts.sh;
     long long k = (long long)((Cr * ts.R) >> 32);
     if (k > N) k = N;
-    for (int it = 0; it < 64 && k > 0 && tooth_at_or_after(k - 1, C, W, N, U); ++it) --k;
-    for (int it = 0; it < 64 && k < N && !tooth_at_or_after(k, C, W, N, U); ++it) ++k;
+    const unsigned long long th = __umul64hi((unsigned long long)N, C), tl = (unsigned long long)N * C;
+    const unsigned long long rh = (th << 33) | (tl >> 31), rl = tl << 33;  // N C 2^33
+    for (int it = 0; it < 64 && k > 0 && tooth_at_or_after(k - 1, W, U, rh, rl); ++it) --k;
+    for (int it = 0; it < 64 && k < N && !tooth_at_or_after(k, W, U, rh, rl); ++it) ++k;
     return k;
 }
 
