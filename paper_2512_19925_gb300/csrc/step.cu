@@ -433,15 +433,15 @@ __device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned 
 // exactly as the precision's event loop forms them at a census event:
 // FP64 round(x 2^S) of the FP64 products w, w mu, w (1/3 - mu^2); FP32 the
 // fixed-point weight W = round(w 2^S) and round(W mu), round(W (1/3 - mu^2))
-__device__ __forceinline__ void census_terms(double w, double mu, int S, long long& c0, long long& c1,
+__device__ __forceinline__ void census_terms(double w, double mu, double tscale, long long& c0, long long& c1,
                                              long long& c2) {
-    c0 = fixed_bits(w, S);
-    c1 = fixed_bits(w * mu, S);
-    c2 = fixed_bits(w * (1.0 / 3.0 - mu * mu), S);
+    c0 = to_fixed(w, tscale);
+    c1 = to_fixed(w * mu, tscale);
+    c2 = to_fixed(w * (1.0 / 3.0 - mu * mu), tscale);
 }
-__device__ __forceinline__ void census_terms(double w, float mu, int S, long long& c0, long long& c1,
+__device__ __forceinline__ void census_terms(double w, float mu, double tscale, long long& c0, long long& c1,
                                              long long& c2) {
-    c0 = fixed_bits(w, S);
+    c0 = to_fixed(w, tscale);
     c1 = fx_mul(c0, mu);
     c2 = fx_mul(c0, 1.0f / 3.0f - mu * mu);
 }
@@ -456,12 +456,12 @@ __global__ void census_tally_kernel(CombArgs<Real> a) {
     __syncthreads();
     const long long m = (long long)*a.ncensus_ptr;
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
-    const int S = a.sd->S;  // the tally scale 2^S
+    const double tscale = a.sd->tscale;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
         const int k = a.ccell[j];
         long long c0, c1, c2;
-        census_terms(a.cw[j], a.cmu[j], S, c0, c1, c2);
+        census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
         sadd(&s_cen[k], c0);
         sadd(&s_cen[I + k], c1);
         sadd(&s_cen[2 * I + k], c2);
@@ -553,7 +553,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
     const unsigned long long W = a.gro[a.N].offw;
     const unsigned U = a.sd->U_comb;
-    const int S = a.sd->S;  // the tally scale 2^S
+    const double tscale = a.sd->tscale;
     const ToothScale ts = tooth_scale(W, a.N);
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
@@ -562,7 +562,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
             // per lane and word (a warp aggregation would rarely merge lanes)
             const int k = a.ccell[j];
             long long c0, c1, c2;
-            census_terms(a.cw[j], a.cmu[j], S, c0, c1, c2);
+            census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
             sadd(&s_cen[k], c0);
             sadd(&s_cen[I + k], c1);
             sadd(&s_cen[2 * I + k], c2);
