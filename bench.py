@@ -48,7 +48,7 @@ CENSUS_BYTES = {"fp32": 32, "fp64": 40}
 # particle, measured by ncu on the 4e6-particle case of this workload
 # (profiles/track32_kernel_plain_at_scale_fp32.txt; traffic grows with the
 # particle count).  Set to None whenever track32_kernel changes.
-TRACK32_DRAM_BYTES_PER_START = 323.1e6 / 4e6
+TRACK32_DRAM_BYTES_PER_START = 322.5e6 / 4e6
 
 
 def dist_env():
@@ -429,8 +429,8 @@ def main(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "traffic_note": "DRAM bytes of the wave-0 launch per step, scaled by particles from the 4e6 capture",
-            "limiter": "issue/latency (ncu: 36% issue active; stalls wait 29%, long scoreboard 24%, "
-                       "short scoreboard 19%; 5.5% DRAM; 15.6 of 32 lanes active)",
+            "limiter": "issue/latency (ncu: 35% issue active; stalls wait 29%, long scoreboard 27%, "
+                       "short scoreboard 16%; 5.6% DRAM; 15.6 of 32 lanes active)",
             "peak_source": peak_kind, "kernel": "track32_kernel",
             "launches": cnt["track_launches"], "kernel_ms_per_step": track_ms / args.steps,
             "algorithmic_bytes_per_step": bytes_alg / args.steps}
