@@ -39,7 +39,14 @@ def leaky_small(N=20000, seed=5):
                 rho=np.sqrt(5.0), eps_min=1e-3, precision="fp64")
 
 
-@pytest.mark.parametrize("make", [shield_small, leaky_small])
+def shield_wide(N=5000, seed=7):
+    # 2000 cells: the census derivative planes of all six scores
+    # (3 x 6 x 2000 words) exceed one block's shared memory, so the comb's
+    # census-derivative pass takes one score plane per block
+    return workloads.shield(particles_per_step=N, seed=seed, precision="fp64", n_cells=2000)
+
+
+@pytest.mark.parametrize("make", [shield_small, leaky_small, shield_wide])
 def test_deriv_tallies_bit_exact(make):
     wl = make()
     g = hww.Problem.from_workload(wl, deriv=True)
