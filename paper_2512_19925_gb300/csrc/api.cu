@@ -53,7 +53,6 @@ struct hww_problem {
     // mesh and cross sections
     double *d_edges = nullptr, *d_dx = nullptr, *d_sigt = nullptr, *d_inv_sigt = nullptr, *d_c = nullptr,
            *d_siga = nullptr;
-    float *d_dxf = nullptr, *d_inv_sigt_f = nullptr;
     float4* d_cellf = nullptr;
     double2* d_ww_hl = nullptr;
     int32_t* d_region = nullptr;
@@ -316,8 +315,6 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b) {
     a.edges = p->d_edges;
     a.inv_sigt = p->d_inv_sigt;
     a.c = p->d_c;
-    a.dxf = p->d_dxf;
-    a.inv_sigt_f = p->d_inv_sigt_f;
     a.cellf = p->d_cellf;
     a.ww_hl = p->d_ww_hl;
     a.ww_c = p->ww_c;
@@ -952,7 +949,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     if ((s = dalloc(p, (char**)&p->acc, p->acc_bytes)) || (s = dalloc(p, (char**)&p->grp, p->grp_bytes)) ||
         (s = dalloc(p, &p->d_edges, I + 1)) || (s = dalloc(p, &p->d_dx, I)) || (s = dalloc(p, &p->d_sigt, I)) ||
         (s = dalloc(p, &p->d_inv_sigt, I)) || (s = dalloc(p, &p->d_c, I)) || (s = dalloc(p, &p->d_siga, I)) ||
-        (s = dalloc(p, &p->d_dxf, I)) || (s = dalloc(p, &p->d_inv_sigt_f, I)) || (s = dalloc(p, &p->d_region, I)) ||
+        (s = dalloc(p, &p->d_region, I)) ||
         (s = dalloc(p, &p->ww_c, I)) || (s = dalloc(p, &p->ww_hi, I)) || (s = dalloc(p, &p->ww_lo, I)) ||
         (s = dalloc(p, &p->ww_override, I)) || (s = dalloc(p, &p->d_cellf, I)) || (s = dalloc(p, &p->d_ww_hl, I)) || (s = dalloc(p, &p->gro, p->N + 1)) ||
         (s = dalloc(p, &p->tile_c, ntiles + 1)) ||
@@ -1004,8 +1001,6 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         return HWW_ERR_OOM;
     }
     // mesh, initial condition and step scalars
-    std::vector<float> dxf(I);
-    for (int i = 0; i < I; ++i) dxf[i] = (float)p->dx[i];
     std::vector<double> phi0;
     source_moments(p, phi0);
     std::vector<double> zeros(I + 2, 0.0);
@@ -1018,7 +1013,6 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     };
     up(p->d_edges, p->edges.data(), sizeof(double) * (I + 1));
     up(p->d_dx, p->dx.data(), sizeof(double) * I);
-    up(p->d_dxf, dxf.data(), sizeof(float) * I);
     up(p->cl_phi[0], phi0.data(), sizeof(double) * (I + 2));
     up(p->cl_J[0], zeros.data(), sizeof(double) * (I + 1));
     up(p->cl_F[0], zeros.data(), sizeof(double) * (I + 2));
@@ -1097,7 +1091,6 @@ hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const doubl
     HWW_CK(cudaMemcpyAsync(p->d_cellf, cellf.data(), sizeof(float4) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_sigt, st.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_inv_sigt, inv.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
-    HWW_CK(cudaMemcpyAsync(p->d_inv_sigt_f, invf.data(), sizeof(float) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_c, cc.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_siga, sa.data(), sizeof(double) * I, cudaMemcpyHostToDevice, p->stream));
     HWW_CK(cudaMemcpyAsync(p->d_region, reg.data(), sizeof(int32_t) * I, cudaMemcpyHostToDevice, p->stream));

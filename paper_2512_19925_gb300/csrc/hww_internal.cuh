@@ -140,8 +140,6 @@ struct TrackArgs {
     const double* edges;
     const double* inv_sigt;
     const double* c;
-    const float* dxf;        // FP32 cell widths
-    const float* inv_sigt_f; // FP32 1/Sigma_t
     const float4* cellf;     // FP32 (width, 1/Sigma_t, c, 0) per cell, one load
     const double2* ww_hl;    // (ceiling, floor) per cell, one load
     const double* ww_c;
