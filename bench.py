@@ -48,7 +48,7 @@ CENSUS_BYTES = {"fp32": 32, "fp64": 40}
 # particle, measured by ncu on the 4e6-particle case of this workload
 # (profiles/track32_kernel_plain_at_scale_fp32.txt; traffic grows with the
 # particle count).  Set to None whenever track32_kernel changes.
-TRACK32_DRAM_BYTES_PER_START = 322.5e6 / 4e6
+TRACK32_DRAM_BYTES_PER_START = 322.1e6 / 4e6
 
 
 def dist_env():
