@@ -242,18 +242,47 @@ def run_e2e(hww, torch, precision, n_particles, seed, warmup, steps):
     return dict(value=segs / dt, h2d=2 * I * 8, d2h=I * 8 + 8 * 20, phi_sum=float(phi.sum()))
 
 
-def run_batch(hww, torch, warmup, steps, tune):
+def run_alone(hww, torch, wls, precision, n_before, steps):
+    """The batch's members stepped one at a time through the single-problem
+    path: each problem runs the steps the batch ran before its timed steps,
+    then the same timed steps under CUDA events; the times add up.  An FP32
+    member stepped alone is bit-identical to the same member in the batch
+    (the batch tests check it), so for FP32 the time ratio is the FOM ratio at
+    equal relative error; FP64 tracking is the same estimator without the
+    FP32 rounding."""
+    stream = torch.cuda.current_stream()
+    total_ms, segs = 0.0, 0
+    for wl in wls:
+        p = hww.Problem.from_workload(wl, precision=precision)
+        for _ in range(n_before):
+            p.run_step(stats=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            segs += p.run_step()["segments"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        p.close()
+    return {"ms_per_step": total_ms / steps, "value": segs / (total_ms * 1e-3)}
+
+
+def run_batch(hww, torch, warmup, steps, tune, alone=True):
     """The batched sweep: 256 independent slabs stepped together (persistent
     tile-queue tracking, one graph per pre/post stage).  The autotuner's trial
-    steps are ordinary steps and run before the warm-up."""
+    steps are ordinary steps and run before the warm-up.  With `alone`, the
+    same problems' same steps also run one problem at a time through the
+    single-problem path, in FP32 and in FP64."""
     from paper_2512_19925_gb300 import autotune
 
     wls = workloads.batched_sweep()
     b = hww.Batch(wls)
-    best = None
+    best, rates = None, {}
     if tune:
-        best, _ = autotune.autotune_batch(b, steps_per_trial=1, sync=torch.cuda.synchronize,
-                                          gpu_name=torch.cuda.get_device_name())
+        best, rates = autotune.autotune_batch(b, steps_per_trial=1, sync=torch.cuda.synchronize,
+                                              gpu_name=torch.cuda.get_device_name())
     for _ in range(warmup):
         b.run_step()
     stream = torch.cuda.current_stream()
@@ -269,10 +298,23 @@ def run_batch(hww, torch, warmup, steps, tune):
     ms = e0.elapsed_time(e1)
     n = sum(int(w["particles_per_step"]) for w in wls)
     b.close()
-    return {"value": segs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "problems": len(wls),
-            "particles_per_step": n, "tuning": list(best) if best else None,
-            "workload": "batched_sweep: 256 slabs [-50,50], cells U[100,2000], particles logU[1e4,1e6], "
-                        "Sigma_t U[0.5,5], c U[0.3,0.999], ratio {2,3,5,10}, dt 0.1, FP32 tracking"}
+    out = {"value": segs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "problems": len(wls),
+           "particles_per_step": n, "tuning": list(best) if best else None,
+           "workload": "batched_sweep: 256 slabs [-50,50], cells U[100,2000], particles logU[1e4,1e6], "
+                       "Sigma_t U[0.5,5], c U[0.3,0.999], ratio {2,3,5,10}, dt 0.1, FP32 tracking"}
+    if alone:
+        n_before = len(rates) + warmup  # the autotuner's trial steps (one each) and the warm-up
+        try:
+            a32 = run_alone(hww, torch, wls, hww.FP32_TRACK, n_before, steps)
+            a64 = run_alone(hww, torch, wls, hww.FP64, n_before, steps)
+            out["one_at_a_time"] = {
+                "kind": "the same problems and steps through the single-problem path, one problem at a time",
+                "fp32_ms_per_step": a32["ms_per_step"], "fp64_ms_per_step": a64["ms_per_step"],
+                "fom_gain_batched_over_fp32_alone": a32["ms_per_step"] / (ms / steps),
+                "time_ratio_batched_over_fp64_alone": a64["ms_per_step"] / (ms / steps)}
+        except Exception as e:  # the batched figure above stands on its own
+            out["one_at_a_time"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    return out
 
 
 def run_deriv(hww, torch, n_particles, warmup, steps):
@@ -414,7 +456,8 @@ def main(args):
 
     e2e = run_e2e(hww, torch, "fp32", N, seed, args.warmup, args.steps) if not args.no_e2e else None
     if not args.no_batch:
-        out["batched"] = run_batch(hww, torch, args.warmup, args.steps, tune=not args.no_tune)
+        out["batched"] = run_batch(hww, torch, args.warmup, args.steps, tune=not args.no_tune,
+                                   alone=not args.no_alone)
     if not args.no_deriv:
         out["differentiation"] = run_deriv(hww, torch, args.deriv_particles, args.warmup, args.steps)
     e2e_val = reduce_sum(e2e["value"]) if e2e else None
@@ -480,6 +523,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-alone", action="store_true")
     ap.add_argument("--no-deriv", action="store_true")
     ap.add_argument("--deriv-particles", type=int, default=10_000_000)
     return ap.parse_args(argv)
