@@ -41,6 +41,14 @@ def rel_errors(t32, t64):
     return out
 
 
+def report(label, worst, err):
+    """Keep the largest error of each kind over the steps and print them (the
+    per-result figures the stated bound is checked against)."""
+    for k, v in err.items():
+        worst[k] = max(worst.get(k, 0.0), v)
+    print("\n%s: %s" % (label, ", ".join("%s %.2e" % (k, worst[k]) for k in KINDS)))
+
+
 def grab(p):
     return {name: p.get_tallies(kind) for name, kind in KINDS.items()}
 
@@ -65,12 +73,14 @@ def test_fp32_within_stated_error_of_oracle(wl_fn, n):
     g = hww.Problem.from_workload(wl)
     o = oracle.problem_from_workload(wl)
     w_bar = 1.0
+    worst = {}
     for step in range(1, 6):
         s = step_from_same_state(g, o, w_bar, step == 1)
         w_bar = s["w_bar_next"]
         t64 = {name: o.get_tallies(kind) for name, kind in KINDS.items()}
         err = rel_errors(grab(g), t64)
         assert max(err.values()) <= BOUND, (step, err)
+        report("%s, %d particles, steps 1..%d, FP32 vs oracle" % (wl_fn.__name__, n, step), worst, err)
 
 
 def test_fp32_full_size_against_fp64_path():
@@ -80,6 +90,7 @@ def test_fp32_full_size_against_fp64_path():
     p32 = hww.Problem.from_workload(wl, precision=hww.FP32_TRACK)
     p64 = hww.Problem.from_workload(wl, precision=hww.FP64)
     w_bar = 1.0
+    worst = {}
     for step in range(1, 4):
         if step > 1:
             x, mu, cell = p32.get_bank()
@@ -95,3 +106,5 @@ def test_fp32_full_size_against_fp64_path():
         assert abs(s32["segments"] - s64["segments"]) <= 1e-4 * s64["segments"]
         err = rel_errors(grab(p32), grab(p64))
         assert max(err.values()) <= BOUND, (step, err)
+        report("1000-cell slab, 1e7 particles, steps 1..%d, FP32 vs FP64 path (step %d: segments %d vs %d)"
+               % (step, step, s32["segments"], s64["segments"]), worst, err)
