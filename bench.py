@@ -272,7 +272,7 @@ def run_alone(hww, torch, wls, precision, n_before, steps):
 def run_batch(hww, torch, warmup, steps, tune, alone=True):
     """The batched sweep: 256 independent slabs stepped together (persistent
     tile-queue tracking, one graph per pre/post stage).  The autotuner's trial
-    steps are ordinary steps and run before the warm-up.  With `alone`, the
+    steps are ordinary steps and run after the warm-up.  With `alone`, the
     same problems' same steps also run one problem at a time through the
     single-problem path, in FP32 and in FP64."""
     from paper_2512_19925_gb300 import autotune
@@ -281,9 +281,10 @@ def run_batch(hww, torch, warmup, steps, tune, alone=True):
     b = hww.Batch(wls)
     best, rates = None, {}
     if tune:
+        # the warm-up steps settle the members' buffers before the trials
         best, rates = autotune.autotune_batch(b, steps_per_trial=1, sync=torch.cuda.synchronize,
-                                              gpu_name=torch.cuda.get_device_name())
-    for _ in range(warmup):
+                                              gpu_name=torch.cuda.get_device_name(), settle=warmup)
+    for _ in range(0 if rates else warmup):
         b.run_step()
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
@@ -303,7 +304,7 @@ def run_batch(hww, torch, warmup, steps, tune, alone=True):
            "workload": "batched_sweep: 256 slabs [-50,50], cells U[100,2000], particles logU[1e4,1e6], "
                        "Sigma_t U[0.5,5], c U[0.3,0.999], ratio {2,3,5,10}, dt 0.1, FP32 tracking"}
     if alone:
-        n_before = len(rates) + warmup  # the autotuner's trial steps (one each) and the warm-up
+        n_before = warmup + len(rates)  # the warm-up and the autotuner's trial steps (one each)
         try:
             a32 = run_alone(hww, torch, wls, hww.FP32_TRACK, n_before, steps)
             a64 = run_alone(hww, torch, wls, hww.FP64, n_before, steps)

@@ -44,16 +44,23 @@ def cached(batch, gpu_name: str = "", path: str | None = None):
 
 
 def autotune_batch(batch, candidates=DEFAULT_CANDIDATES, steps_per_trial=1, gpu_name: str = "",
-                   path: str | None = None, sync=None):
+                   path: str | None = None, sync=None, settle: int = 0):
     """Try each (tile, emax) on real steps, keep the fastest, cache it.
 
     `sync` is a callable that waits for the GPU (for example
-    torch.cuda.synchronize); the trial steps are part of the run."""
+    torch.cuda.synchronize); the trial steps are part of the run.  `settle`
+    ordinary steps run first (on a cache miss): in a run's first steps the
+    members' census banks and record queues are still growing to the run's
+    demand, and a step in which any member overflows tracks the whole batch
+    again with larger buffers, which would count against whichever
+    candidate ran it."""
     path = path or default_cache_path()
     hit = cached(batch, gpu_name, path)
     if hit:
         batch.set_tuning(*hit)
         return hit, {}
+    for _ in range(int(settle)):
+        batch.run_step()
     rates = {}
     for tile, emax in candidates:
         batch.set_tuning(tile, emax)

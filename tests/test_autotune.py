@@ -12,12 +12,14 @@ class FakeBatch:
         self.workloads = [{"particles_per_step": 1000, "edges": [0.0, 1.0, 2.0], "precision": "fp32"}]
         self.tuning = None
         self.log = []
+        self.steps = []
 
     def set_tuning(self, tile, emax):
         self.tuning = (tile, emax)
         self.log.append(self.tuning)
 
     def run_step(self, stats=True):
+        self.steps.append(self.tuning)
         time.sleep(0.002 if self.tuning == (8192, 64) else 0.01)
         return {"segments": 1000}
 
@@ -42,3 +44,17 @@ def test_signature_distinguishes_workloads():
     a, b = FakeBatch(), FakeBatch()
     b.workloads = b.workloads * 2
     assert autotune.signature(a, "x") != autotune.signature(b, "x")
+
+
+def test_settle_steps_run_before_the_trials(tmp_path):
+    path = str(tmp_path / "tune.json")
+    b = FakeBatch()
+    best, rates = autotune.autotune_batch(b, path=path, gpu_name="GB300", settle=3)
+    assert best == (8192, 64)
+    # three ordinary steps at the batch's own tuning, then one per candidate
+    assert b.steps[:3] == [None] * 3
+    assert b.steps[3:] == list(autotune.DEFAULT_CANDIDATES)
+    # a cache hit runs no step at all
+    b2 = FakeBatch()
+    autotune.autotune_batch(b2, path=path, gpu_name="GB300", settle=3)
+    assert b2.steps == []
