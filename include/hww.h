@@ -28,7 +28,8 @@
  *     instance a torch tensor's data_ptr()); when 0 it is host memory.
  *   - Work is enqueued on the CUDA stream given at creation (0 = the legacy
  *     default stream).  Calls that return data to host memory, and
- *     run_step with a non-NULL stats pointer, synchronize that stream.
+ *     run_step with a non-NULL stats pointer, synchronize that stream;
+ *     run_step itself waits once per step for its tracking stage (below).
  *   - A problem must be used from one host thread at a time.
  *   - Device memory is allocated by create_problem (stream-ordered
  *     allocation on the problem's stream) and released by destroy_problem.
@@ -133,19 +134,24 @@ hww_status create_problem(const hww_problem_desc* desc, hww_problem** out);
  * the extra ones with their own isotropic directions.  Derivative runs need
  * c <= 1.  `region` (nullable)
  * maps each cell to a region 0..R-1 for the derivative tallies.  Host arrays
- * of length I.  May be called again between steps. */
+ * of length I.  May be called again between steps.  Refactors the LOSM
+ * matrix and synchronizes.  Errors: HWW_ERR_ARG for a NULL array, Sigma_t
+ * not finite and > 0, c outside [0, 16] (or above 1 in a derivative run) or
+ * a region out of range (nothing is changed); HWW_ERR_NUMERIC when the LOSM
+ * factorization meets a zero pivot. */
 hww_status set_cross_sections(hww_problem* p, const double* sigma_t, const double* c,
                               const int32_t* region);
 
 /* Window width rho >= 1 (ceiling rho*ww, floor ww/rho, Eq. ww-c&f), minimum
  * center 0 < eps_min <= 1 (Eq. ww-center), mode HWW_MODE_*, center scaling
- * HWW_SCALE_*. */
+ * HWW_SCALE_*.  HWW_ERR_ARG for a value out of range. */
 hww_status set_ww_params(hww_problem* p, double rho, double eps_min, int32_t mode,
                          int32_t center_scaling);
 
 /* Replace the window centers of the next step only (I host values > 0);
  * ceiling and floor follow from rho.  Used to run both implementations
- * from identical windows. */
+ * from identical windows.  HWW_ERR_ARG for a center that is not finite and
+ * positive. */
 hww_status set_ww_centers(hww_problem* p, const double* centers);
 
 /* In-step window updates (Sec. 3, Eq. Hpn): during a step whose windows
@@ -160,11 +166,18 @@ hww_status set_ww_centers(hww_problem* p, const double* centers);
  * supported for batch members (run_batch_step returns HWW_ERR_STATE). */
 hww_status set_ww_updates(hww_problem* p, int32_t n, const double* fractions);
 
-/* Advance the problem by one time step (steps 1-4 above).  Asynchronous on
- * the problem's stream unless `stats` is non-NULL, in which case the stream
- * is synchronized and the counts of the step are returned.  A bank overflow
- * or numeric guard makes this or the next synchronizing call return the
- * error; the step's results are then invalid. */
+/* Advance the problem by one time step (steps 1-4 above).  The host waits
+ * once, after the tracking stage, for its overflow flag: a census bank or
+ * record queue that filled up leaves the start bank and the closures as they
+ * were, and the step is tracked again with larger buffers (each at least
+ * doubled, at most 12 times), bit-identical to a run that had the room from
+ * the start.  The rest of the step (closures, HLOSM, comb) is enqueued on
+ * the problem's stream without waiting, unless `stats` is non-NULL, in which
+ * case the stream is synchronized and the counts of the step are returned.
+ * HWW_ERR_STATE before set_cross_sections and set_ww_params.  An overflow
+ * that outlasts the regrowths, or a numeric guard, makes this or the next
+ * synchronizing call return the error; the step's results are then
+ * invalid. */
 hww_status run_step(hww_problem* p, hww_step_stats* stats);
 
 /* Copy tally `kind` (HWW_* kinds above) of the last completed step into
@@ -283,7 +296,12 @@ hww_status batch_problem(hww_batch* b, int32_t i, hww_problem** out);
 /* Tile size in particles (>= 256) and events per track before requeueing
  * (>= 1) of the batched tracking launches; results do not depend on them. */
 hww_status batch_set_tuning(hww_batch* b, int32_t tile, int32_t emax);
-/* Advance every member by one time step; stats (nullable) synchronizes. */
+/* Advance every member by one time step; stats (nullable) synchronizes.
+ * As in run_step the host waits for the tracking waves; if any member's
+ * census bank or record queue overflowed, that member's buffers grow and the
+ * whole batch is tracked again (HWW_ERR_BANK_OVERFLOW after 12 regrowths).
+ * HWW_ERR_STATE when a member lacks cross sections or window parameters, or
+ * has in-step window updates. */
 hww_status run_batch_step(hww_batch* b, hww_batch_stats* stats);
 /* Counts of member i's last step (synchronizes). */
 hww_status batch_member_stats(hww_batch* b, int32_t i, hww_step_stats* stats);
