@@ -10,6 +10,9 @@ pulse (Sec. 5.1 test shape) and exact bookkeeping.
 * a reflecting wall at the pulse doubles the infinite-medium solution.
 * counts balance exactly: start + daughters - absorbed - roulette kills -
   leaked = census, and the comb returns exactly N particles.
+* a population that dies out (a thick pure absorber) leaves an empty census,
+  a zero-weight comb and empty later steps with zero tallies and finite
+  LOSM solutions; its one flight per particle has the mean 1 / Sigma_t.
 """
 import math
 
@@ -164,3 +167,35 @@ def test_deterministic_given_seed():
         sa, sb = a.run_step(), b.run_step()
         assert sa == sb
     assert np.array_equal(a.get_tallies_raw(oracle.TL_PHI), b.get_tallies_raw(oracle.TL_PHI))
+
+
+def test_extinct_population():
+    # Sigma_t = 200, c = 0 in [-1, 1]: a flight reaches the census (length
+    # v dt = 1) or a boundary (length >= 1) with probability e^-200, so every
+    # particle is absorbed at its first collision
+    N = 500
+    wl = workloads.plain_slab(particles_per_step=N)
+    wl["edges"] = np.linspace(-1.0, 1.0, 5)
+    wl["sigma_t"] = np.full(4, 200.0)
+    wl["c"] = np.zeros(4)
+    wl["dt"] = 1.0
+    p = oracle.problem_from_workload(wl)
+    s = p.run_step()
+    assert (s["n_start"], s["segments"], s["absorbed"], s["collisions"]) == (N, N, N, N)
+    assert (s["census"], s["leaked"], s["n_next"], s["w_bar_next"]) == (0, 0, 0, 0.0)
+    dx = np.diff(wl["edges"])
+    # sum_i dx_i <phi>_i = (mean flight) / dt, the flight exponential with rate
+    # Sigma_t (its truncation at length 1 is below e^-200)
+    tl = float(np.dot(dx, p.get_tallies(oracle.TL_PHI))) * wl["dt"]
+    assert abs(tl - 1.0 / 200.0) < 5.0 * (1.0 / 200.0) / math.sqrt(N), tl
+    for kind in (oracle.CENSUS_PHI, oracle.CENSUS_J, oracle.CENSUS_F):
+        assert not p.get_tallies(kind).any()
+    for _ in range(3):
+        s = p.run_step()
+        assert (s["n_start"], s["segments"], s["census"], s["n_next"]) == (0, 0, 0, 0)
+        for kind in (oracle.TL_PHI, oracle.TL_J, oracle.TL_F, oracle.CENSUS_PHI, oracle.BATCH_PHI):
+            assert not p.get_tallies(kind).any()
+        phi, J = p.get_losm_solution()
+        assert np.isfinite(phi).all() and np.isfinite(J).all()
+        assert np.isfinite(p.get_ww()[0]).all()
+    p.close()
