@@ -8,6 +8,13 @@ the histories so far.
 * With acting windows the updates change the run, and the estimators stay
   unbiased: the moment integrals follow the exact infinite-medium ODEs.
 * The fractions are validated (increasing, inside (0, 1)).
+* The windows of an update are those of the histories so far: at step 1 the
+  first H_1 histories of an N-particle run are exactly the histories of an
+  H_1-particle run (a birth direction depends on the source id alone, and
+  both runs start from the same windows), so the windows after the first
+  update equal Eq. (ww-center) applied to the end-of-step HLOSM solution of
+  the H_1-particle run.  One history more or fewer moves those centers by
+  about 5e-4; the tolerance is the centers' 20-bit rounding.
 """
 import math
 
@@ -88,3 +95,29 @@ def test_fractions_are_validated():
             p.set_ww_updates(len(bad), bad)
     p.set_ww_updates(2, [0.25, 0.5])
     p.set_ww_updates(0)
+
+
+def _centers(phi, eps, w_bar=1.0):
+    f = np.maximum(phi, 0.0)
+    return w_bar * ((f / f.max()) * (1.0 - eps) + eps)
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+def test_update_windows_are_those_of_the_histories_so_far(filt):
+    N, frac = 2000, 0.5
+    wl = workloads.plain_slab(particles_per_step=N)
+    wl["filter"] = filt
+    a = oracle.problem_from_workload(wl)
+    a.set_ww_updates(1, [frac])
+    a.run_step()
+    w_update = a.get_ww()[0]  # the windows the last chunk was tracked with
+    part = workloads.plain_slab(particles_per_step=int(frac * N))
+    part["filter"] = filt
+    b = oracle.problem_from_workload(part)
+    b.run_step()
+    phi, _ = b.get_losm_solution(oracle.FULL)
+    np.testing.assert_allclose(w_update, _centers(phi[1:-1], wl["eps_min"]), rtol=2.0 ** -19, atol=0)
+    # and the update moved the windows away from those the step started with
+    assert np.max(np.abs(w_update / b.get_ww()[0] - 1.0)) > 1e-3
+    a.close()
+    b.close()
