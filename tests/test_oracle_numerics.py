@@ -29,6 +29,23 @@ def test_u01_endpoints_are_open_and_exact():
     assert oracle.u01(0xFFF, 0x12345678) == oracle.u01(0, 0x12345678)
 
 
+def test_u01_mirror_symmetry_and_moments():
+    # complementing the word mirrors the uniform exactly: u(x) + u(~x) = 1
+    # (both are odd multiples of 2^-53); a dropped 1/2 offset or a wrong shift
+    # breaks it
+    rng = np.random.default_rng(11)
+    for lo, hi in rng.integers(0, 2 ** 32, size=(2000, 2), dtype=np.uint64):
+        lo, hi = int(lo), int(hi)
+        u, v = oracle.u01(lo, hi), oracle.u01(~lo, ~hi)
+        assert 0.0 < u < 1.0 and u + v == 1.0
+    # over Philox draws: mean 1/2 and variance 1/12 of the uniform law
+    w = _words(20000)
+    u = np.array([oracle.u01(int(a), int(b)) for a, b in w[:, :2]])
+    n = u.size
+    assert abs(u.mean() - 0.5) < 5.0 * math.sqrt(1.0 / 12.0 / n)
+    assert abs(u.var() - 1.0 / 12.0) < 5.0 * math.sqrt(1.0 / 180.0 / n)
+
+
 def test_philox_uniform_and_balanced():
     w = _words(20000)
     # each 32-bit word uniform: chi-square over 64 bins
