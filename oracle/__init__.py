@@ -19,6 +19,7 @@ What each function follows in the paper (arXiv 2512.19925):
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -77,56 +78,98 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _bind(L):
+    """Declare the argument types of a loaded oracle library."""
+    dp = C.POINTER(C.c_double)
+    L.or_create.argtypes = [C.POINTER(_Desc), C.POINTER(C.c_void_p)]
+    L.or_set_cross_sections.argtypes = [C.c_void_p, dp, dp]
+    L.or_set_ww_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32]
+    L.or_set_ww_centers.argtypes = [C.c_void_p, dp]
+    L.or_run_step.argtypes = [C.c_void_p, C.POINTER(_Stats)]
+    L.or_get_tallies.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int64]
+    L.or_get_tallies_raw.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.c_int64]
+    L.or_get_losm_solution.argtypes = [C.c_void_p, C.c_int32, dp, dp]
+    L.or_get_ww.argtypes = [C.c_void_p, dp, dp, dp]
+    L.or_get_bank.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int32), C.c_int64,
+                              C.POINTER(C.c_int64)]
+    L.or_set_bank.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.c_double]
+    L.or_get_census.argtypes = [C.c_void_p, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
+                                C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_int64)]
+    L.or_set_regions.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+    L.or_set_ww_updates.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]
+    L.or_get_deriv_tallies.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int64]
+    L.or_losm_vjp.argtypes = [C.c_void_p, dp, dp, dp]
+    L.or_set_bank_scores.argtypes = [C.c_void_p, dp]
+    L.or_losm_adjoint.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                  C.c_int32, C.c_int32, dp, dp, dp]
+    L.or_losm_directional.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                      C.c_int32, C.c_int32, dp, dp, dp, dp, dp, dp, dp, dp, dp,
+                                      dp, dp, C.c_double, C.c_double, dp]
+    L.or_destroy.argtypes = [C.c_void_p]
+    L.or_destroy.restype = None
+    L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+    L.or_philox4x32_10.restype = None
+    L.or_u01.argtypes = [C.c_uint32, C.c_uint32]
+    L.or_u01.restype = C.c_double
+    L.or_log.argtypes = [C.c_double]
+    L.or_log.restype = C.c_double
+    L.or_log_table.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.or_log_table.restype = None
+    L.or_ma_filter.argtypes = [dp, dp, C.c_int32, C.c_int32]
+    L.or_fourier_filter.argtypes = [dp, dp, C.c_int32, C.c_int32]
+    L.or_losm_solve.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                C.c_int32, C.c_int32, dp, dp, dp, dp, C.c_double,
+                                C.c_double, dp, dp, dp, dp]
+    L.or_comb.argtypes = [C.c_int64, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64),
+                          C.POINTER(C.c_uint64), C.c_int64, C.c_uint32,
+                          C.POINTER(C.c_int32)]
+    L.or_build_closures.argtypes = [C.c_void_p, dp, dp, dp, C.c_double, C.c_double, dp, dp, dp, dp]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            dp = C.POINTER(C.c_double)
-            L.or_create.argtypes = [C.POINTER(_Desc), C.POINTER(C.c_void_p)]
-            L.or_set_cross_sections.argtypes = [C.c_void_p, dp, dp]
-            L.or_set_ww_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32]
-            L.or_set_ww_centers.argtypes = [C.c_void_p, dp]
-            L.or_run_step.argtypes = [C.c_void_p, C.POINTER(_Stats)]
-            L.or_get_tallies.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int64]
-            L.or_get_tallies_raw.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.c_int64]
-            L.or_get_losm_solution.argtypes = [C.c_void_p, C.c_int32, dp, dp]
-            L.or_get_ww.argtypes = [C.c_void_p, dp, dp, dp]
-            L.or_get_bank.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int32), C.c_int64,
-                                      C.POINTER(C.c_int64)]
-            L.or_set_bank.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int32), C.c_int64, C.c_double]
-            L.or_get_census.argtypes = [C.c_void_p, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
-                                        C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_int64)]
-            L.or_set_regions.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
-            L.or_set_ww_updates.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]
-            L.or_get_deriv_tallies.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int64]
-            L.or_losm_vjp.argtypes = [C.c_void_p, dp, dp, dp]
-            L.or_set_bank_scores.argtypes = [C.c_void_p, dp]
-            L.or_losm_adjoint.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
-                                          C.c_int32, C.c_int32, dp, dp, dp]
-            L.or_losm_directional.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
-                                              C.c_int32, C.c_int32, dp, dp, dp, dp, dp, dp, dp, dp, dp,
-                                              dp, dp, C.c_double, C.c_double, dp]
-            L.or_destroy.argtypes = [C.c_void_p]
-            L.or_destroy.restype = None
-            L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
-            L.or_philox4x32_10.restype = None
-            L.or_u01.argtypes = [C.c_uint32, C.c_uint32]
-            L.or_u01.restype = C.c_double
-            L.or_log.argtypes = [C.c_double]
-            L.or_log.restype = C.c_double
-            L.or_log_table.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
-            L.or_log_table.restype = None
-            L.or_ma_filter.argtypes = [dp, dp, C.c_int32, C.c_int32]
-            L.or_fourier_filter.argtypes = [dp, dp, C.c_int32, C.c_int32]
-            L.or_losm_solve.argtypes = [C.c_int32, dp, dp, dp, C.c_double, C.c_double, C.c_double,
-                                        C.c_int32, C.c_int32, dp, dp, dp, dp, C.c_double,
-                                        C.c_double, dp, dp, dp, dp]
-            L.or_comb.argtypes = [C.c_int64, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64),
-                                  C.POINTER(C.c_uint64), C.c_int64, C.c_uint32,
-                                  C.POINTER(C.c_int32)]
-            _lib = L
+            _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+def compile_variant(src_text: str, out_dir: str) -> str:
+    """Compile a variant of the oracle's source (the tests plant mistakes in
+    a copy to show that a pin catches them) with the oracle's own flags;
+    returns the library path."""
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, "hww_oracle.c")
+    with open(src, "w") as f:
+        f.write(src_text)
+    out = os.path.join(out_dir, "libhww_oracle_variant.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                           "-shared", "-I" + _HERE, "-o", out, src, "-lm"])
+    return out
+
+
+@contextlib.contextmanager
+def variant(path: str):
+    """Route every oracle call to the library at `path` (a variant built by
+    compile_variant) while the context is open.  Problems must be created and
+    closed inside it."""
+    global _lib
+    L = _bind(C.CDLL(path))
+    with _lock:
+        old = _lib
+        _lib = L
+    try:
+        yield L
+    finally:
+        with _lock:
+            _lib = old
+
+
+def source_text() -> str:
+    """The oracle's C source (the text a variant starts from)."""
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _dp(a):
@@ -370,6 +413,18 @@ class Problem:
         out = np.empty(2 * self.R)
         _check(lib().or_losm_vjp(self._h, _dp(gp), _dp(gj), _dp(out)), "losm_vjp")
         return out
+
+    def build_closures(self, cphi, cJ, cF, PL=0.0, PR=0.0):
+        """The closure vectors this problem's step forms from normalised census
+        moments (I cell averages each) and boundary closures: (phi[I+2],
+        J[I+1], F[I+2], (PL, PR)) on its mesh, boundary conditions and
+        filter."""
+        I = self.I
+        a, b, c = _f64(cphi, I), _f64(cJ, I), _f64(cF, I)
+        phi, J, F, P = np.empty(I + 2), np.empty(I + 1), np.empty(I + 2), np.empty(2)
+        _check(lib().or_build_closures(self._h, _dp(a), _dp(b), _dp(c), float(PL), float(PR), _dp(phi), _dp(J),
+                                       _dp(F), _dp(P)), "build_closures")
+        return phi, J, F, (float(P[0]), float(P[1]))
 
     def set_bank_scores(self, S):
         S = _f64(S)

@@ -853,6 +853,13 @@ static void build_closure_set(const or_problem* p, const double* cphi, const dou
     free(tmp2);
 }
 
+int or_build_closures(const or_problem* p, const double* cphi, const double* cJ, const double* cF,
+                      double PL, double PR, double* phi, double* J, double* F, double* P) {
+    if (!p || !cphi || !cJ || !cF || !phi || !J || !F || !P) return E_ARG;
+    build_closure_set(p, cphi, cJ, cF, PL, PR, phi, J, F, &P[0], &P[1]);
+    return 0;
+}
+
 static void build_closures(or_problem* p, const double* cphi, const double* cJ, const double* cF,
                            double PL, double PR) {
     build_closure_set(p, cphi, cJ, cF, PL, PR, p->clo_phi, p->clo_J, p->clo_F, &p->clo_PL, &p->clo_PR);

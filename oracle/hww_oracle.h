@@ -109,6 +109,13 @@ int or_losm_solve(int32_t n_cells, const double* dx, const double* sigma_t, cons
                   double* phi_new, double* J_new);
 int or_comb(int64_t m, const uint32_t* id, const uint64_t* lin, const uint64_t* wfx,
             int64_t n, uint32_t U, int32_t* src_of_slot);
+/* the closure and initial-condition vectors at a time layer (Eq. ct-mc, Eq.
+ * losm-disc-bc) that a step forms from its normalised census moments
+ * cphi, cJ, cF (I cell averages each) and its boundary closures PL, PR, on
+ * p's mesh, boundary conditions and filter: phi (I+2), J (I+1), F (I+2) and
+ * the boundary closures (PL, PR) the HLOSM solve takes */
+int or_build_closures(const or_problem* p, const double* cphi, const double* cJ, const double* cF,
+                      double PL, double PR, double* phi, double* J, double* F, double* P);
 
 #ifdef __cplusplus
 }

@@ -229,3 +229,22 @@ def test_launch_accounting():
     assert c["track_launches"] == s["waves"]
     assert c["kernel_launches"] >= s["waves"] + 6
     assert c["track_ms"] > 0.0
+
+
+def test_graded_mesh_leaking_parity():
+    # a non-uniform mesh (cell widths 0.01..0.1 in random order) on a narrow
+    # slab: the interior edge currents interpolate cells of unequal widths and
+    # particles leak, so the closures' interpolation weights and the boundary
+    # closures are both exercised (on a uniform mesh swapped weights would
+    # agree); the FP64 path's closures must equal the oracle's bit for bit
+    rng = np.random.default_rng(11)
+    w = rng.uniform(0.01, 0.1, 40)
+    edges = np.concatenate([[0.0], np.cumsum(w)])
+    edges = edges - edges[np.argmin(np.abs(edges - 0.45 * edges[-1]))]  # the pulse on an interior edge
+    wl = workloads.plain_slab(particles_per_step=6007)
+    wl["edges"] = edges
+    wl["sigma_t"] = np.full(40, 1.0)
+    wl["c"] = np.full(40, 0.9)
+    wl["filter"] = 1
+    stats = run_parity(wl, 12)
+    assert sum(s["leaked"] for s in stats) > 0
