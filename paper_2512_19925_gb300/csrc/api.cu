@@ -1040,7 +1040,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         return cuda_status(e);
     }
     // tracking launch shape: persistent grid of resident blocks
-    p->track_smem = sizeof(long long) * (TALLY_ROWS + P2) * (size_t)I;
+    p->track_smem = sizeof(long long) * ((p->fp32 ? TALLY_ROWS_FP32 : TALLY_ROWS) + P2) * (size_t)I;
     // the dynamic shared memory limits are set whatever the sizes: a kernel's
     // static shared memory counts against the default 48 KB as well
     const size_t cen_smem = sizeof(long long) * 3 * (size_t)I;

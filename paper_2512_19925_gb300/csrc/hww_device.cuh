@@ -181,33 +181,35 @@ __host__ __device__ __forceinline__ double pow2(int e) {
 }
 
 // FP32 path: the tally contribution of an FP32 factor f to a fixed-point
-// weight W.
-// round(W * f) for W >= 0 and an FP32 f, from the exact 128-bit product of W
-// and the mantissa of f (round half up); subnormal f counts as 0
+// weight.
+// round(W * f) for 0 <= W < 2^63 and an FP32 f, from the exact product of W
+// and the 24-bit mantissa m of f (round half up); subnormal f counts as 0.
+// The product W m = A 2^32 + B is formed from two 32 x 32 -> 64-bit products
+// (A from the high word of W, B from the low word), and shifted right by s
+// (f = m 2^-s) with the bit below the result as the rounding bit.
 __device__ __forceinline__ long long fx_mul(long long W, float f) {
     const unsigned b = __float_as_uint(f);
     const int ex = (int)((b >> 23) & 0xFFu);
     if (ex == 0) return 0;
-    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const unsigned m = (b & 0x7FFFFFu) | 0x800000u;
     const int s = 150 - ex;  // value = m 2^-s
     const unsigned long long uw = (unsigned long long)W;
-    const unsigned long long lo = uw * m;
-    const unsigned long long hi = __umul64hi(uw, m);
+    const unsigned long long A = (unsigned long long)(unsigned)(uw >> 32) * m;  // < 2^55
+    const unsigned long long B = (unsigned long long)(unsigned)uw * m;          // < 2^56
     unsigned long long r, rb;
     if (s <= 0) {
-        r = lo << (-s);
+        r = ((A << 32) + B) << (-s);
         rb = 0;
-    } else if (s < 64) {
-        r = (lo >> s) | (hi << (64 - s));
-        rb = (lo >> (s - 1)) & 1ull;
-    } else if (s == 64) {
-        r = hi;
-        rb = lo >> 63;
-    } else if (s < 128) {
-        r = hi >> (s - 64);
-        rb = (hi >> (s - 65)) & 1ull;
+    } else if (s <= 32) {
+        r = (A << (32 - s)) + (B >> s);  // A 2^32 is a multiple of 2^s
+        rb = (B >> (s - 1)) & 1ull;
+    } else if (s < 96) {
+        const unsigned long long C = A + (B >> 32);  // the product shifted right by 32, exactly
+        const int t = s - 32;
+        r = C >> t;
+        rb = (C >> (t - 1)) & 1ull;
     } else {
-        return 0;
+        return 0;  // the product is below 2^87
     }
     r += rb;
     return (b >> 31) ? -(long long)r : (long long)r;

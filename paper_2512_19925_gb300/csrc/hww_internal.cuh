@@ -190,6 +190,11 @@ void launch_track_batch_fp32(const TrackArgs<float>* args, const BatchPlan& plan
 // block's current id range; derivative runs append their [2R][I]
 // track-length rows.
 constexpr int TALLY_ROWS = 4;
+// Rows of the single-problem FP32 kernel's block-private tallies: J, F and the
+// batch row of the block's id range (the flux tally is the sum of the batch
+// rows); each row is I low words then I high words (32-bit), so that the
+// low-word atomics of a warp spread over all 32 banks.
+constexpr int TALLY_ROWS_FP32 = 3;
 
 int track_batch_smem_optin_fp32(size_t smem);
 int track_batch_smem_optin_fp64(size_t smem);

@@ -59,8 +59,17 @@ __device__ __forceinline__ int batch_of(uint32_t id, int B, long long N, unsigne
     return (int)q;
 }
 
+// Add v to a 64-bit block-private accumulator in shared memory, exactly
+// (modulo 2^64): shared memory has native 32-bit atomic adds but no 64-bit
+// one (a 64-bit add is a compare-and-swap loop, retried under contention), so
+// the low word is added with a returned old value, and the high word gets the
+// high half of v plus the carry out of the low word.
 __device__ __forceinline__ void sadd(long long* s, long long v) {
-    atomicAdd((unsigned long long*)s, (unsigned long long)v);
+    unsigned* w = reinterpret_cast<unsigned*>(s);
+    const unsigned lo = (unsigned)(unsigned long long)v;
+    const unsigned old = atomicAdd(w, lo);
+    const unsigned hi = (unsigned)((unsigned long long)v >> 32) + ((old + lo < old) ? 1u : 0u);
+    if (hi) atomicAdd(w + 1, hi);
 }
 
 struct Counters {

@@ -3,7 +3,8 @@
 // Same events, rules and random streams as the FP64 kernel (the uniforms are
 // the top 23 bits of the same Philox words), but the geometry runs in FP32:
 // a track keeps its cell index and an FP32 offset from the cell's left edge,
-// an FP32 direction, an FP32 distance to census and FP32 flight distances.
+// an FP32 direction, an FP32 distance to census and FP32 flight distances
+// (-ln u from the hardware base-2 logarithm).
 // Weights stay FP64 (the window tests compare their bit patterns, and the
 // split count and survival test use an FP32 ratio and a product in place of
 // FP64 divides); tally contributions are formed in
@@ -13,10 +14,12 @@
 // rounded once (half up) at the tally scale.  The FP64 pipe, of which GB300
 // has little, is left to rare events (splits, roulette, leaks, census).
 //
-// The event loop is flattened: a lane whose track ends (census, absorption,
-// leak, roulette kill, event budget) loads its next track in the same loop
-// iteration the other lanes spend on their next event, so a warp stays full
-// until the work runs out.
+// The single-problem kernel runs a warp-synchronous loop (run_warp): the
+// lanes of a warp take their events together and share a daughter stack, so
+// the daughters of a split spread over the warp's idle lanes.  The persistent
+// batched kernel runs a flattened per-lane loop (run_items): a lane whose
+// track ends loads its next track in the same iteration the other lanes
+// spend on their next event.
 #include "track_common.cuh"
 
 namespace hww {
@@ -215,7 +218,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
         const int k = q.cell;
         const float4 cf = __ldg(&a.cellf[k]);  // width, 1/Sigma_t, c
         const float dxk = cf.x;
-        const float dcoll = -logf(uf) * cf.y;
+        const float dcoll = -__logf(uf) * cf.y;  // as in the single-problem loop
         const float dedge = ((q.mu > 0.0f) ? (dxk - q.xo) : -q.xo) * q.inv_mu;
         const float dcens = q.tau;
         int ev;
@@ -423,55 +426,708 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
     }
 }
 
-// Two resident blocks of 256 threads per SM: the event loop wants about 120
-// registers; at three blocks it spills to local memory, whose traffic (the
-// L1 left beside the shared tallies hits ~20% of it) costs more time than
-// the extra warps hide.
-__global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel(TrackArgs<float> a) {
-    extern __shared__ long long sm[];
-    __shared__ unsigned s_next;
-    __shared__ PendingParent s_pp;
+// ---------------------------------------------------------------------------
+// The single-problem event loop, warp-synchronous.
+//
+// All 32 lanes of a warp iterate together until the warp has no work left.
+// Each iteration hands work to the lanes without a track, draws the Philox
+// blocks of every lane at one site, takes one event of every live track (or
+// one setup step of a new track), stages the iteration's census particles
+// and sums its counts.  Work comes, in this order, from the warp's daughter
+// stack in shared memory (a split leaves its daughters there, so they spread
+// over the warp's idle lanes instead of queueing behind one lane), then from
+// the block's range of start-bank items (prefetched 32 at a time into shared
+// memory with asynchronous copies, so that a new track does not wait for
+// HBM) or records.  Census particles are staged per warp in shared memory and
+// written out 32 at a time with one slot reservation on the census counter
+// (one global atomic per 32 census particles instead of one per iteration,
+// and 128-byte stores).  Counts are summed over the warp (each lane holds one
+// counter), so they take no per-lane registers.  A split whose warp stack is
+// full, and a track past its event budget, go to the record queue.
+constexpr int WARPS = TRACK_THREADS / 32;
+constexpr int WSTACK = 16;  // daughter-stack entries per warp
+constexpr int ROWS32 = TALLY_ROWS_FP32;
+
+struct WarpShared {
+    // daughter stack
+    float xo[WARPS][WSTACK], mu[WARPS][WSTACK], tau[WARPS][WSTACK];
+    double w[WARPS][WSTACK];
+    long long W[WARPS][WSTACK];
+    int cell[WARPS][WSTACK];
+    uint32_t id[WARPS][WSTACK], e[WARPS][WSTACK];
+    uint64_t lin[WARPS][WSTACK];
+    uint32_t jn[WARPS][WSTACK];  // next daughter to hand out (FRESH_DIRECTION: own isotropic directions)
+    uint32_t je[WARPS][WSTACK];  // one past the last daughter
+    int top[WARPS];              // entries in use (only atomics while tracks run)
+    // census staging
+    float cx[WARPS][32], cmu[WARPS][32];
+    double cw[WARPS][32];
+    int ccell[WARPS][32];
+    uint32_t cid[WARPS][32];
+    LinW clw[WARPS][32];
+    // start-bank records of the next items, two slots of 32: slot s holds
+    // items item0 + rb[s] .. + rn[s]; items are handed out from slot rcs
+    // starting at rpos
+    BankRec<float> ring[WARPS][2][32];
+    unsigned rb[WARPS][2];
+    int rn[WARPS][2], rcs[WARPS], rpos[WARPS];
+};
+
+// event outcome bits of one lane in one iteration (summed over the warp)
+enum EvBit : unsigned {
+    EB_CENSUS = 0, EB_CROSS, EB_COLL, EB_REFL, EB_LEAK, EB_ABS, EB_SPLIT, EB_RKILL, EB_RSURV, EB_COUNT
+};
+// the counter each lane of a warp holds
+__device__ __constant__ const int kLaneStat[EB_COUNT] = {ST_CENSUS, ST_CROSSINGS, ST_COLLISIONS, ST_REFLECTIONS,
+                                                         ST_LEAKED, ST_ABSORBED, ST_SPLIT_EVENTS, ST_RKILLS,
+                                                         ST_RSURVIVE};
+constexpr int LANE_DAUGHTERS = EB_COUNT;  // lane holding the daughter count
+constexpr int LANE_MAXEV = EB_COUNT + 1;  // lane holding the largest event count
+
+// push a parent whose daughters [jn, je) are to be handed out (jn may carry
+// FRESH_DIRECTION); false when the warp's stack is full
+__device__ __forceinline__ bool stack_push(WarpShared& ws, int wp, const P32& b, uint32_t jn, uint32_t je) {
+    const int slot = (int)warp_reserve((unsigned*)&ws.top[wp]);
+    if (slot >= WSTACK) {
+        atomicSub((unsigned*)&ws.top[wp], 1u);
+        return false;
+    }
+    ws.xo[wp][slot] = b.xo;
+    ws.mu[wp][slot] = b.mu;
+    ws.tau[wp][slot] = b.tau;
+    ws.w[wp][slot] = b.w;
+    ws.W[wp][slot] = b.W;
+    ws.cell[wp][slot] = b.cell;
+    ws.id[wp][slot] = b.id;
+    ws.e[wp][slot] = b.e;
+    ws.lin[wp][slot] = b.lin;
+    ws.jn[wp][slot] = jn;
+    ws.je[wp][slot] = je;
+    return true;
+}
+
+// daughters j0.. of a parent as chunk records of the record queue
+__device__ __forceinline__ void queue_daughters(const TrackArgs<float>& a, const P32& b, uint32_t j0, uint32_t nd,
+                                                uint32_t fresh) {
+    const uint32_t nch = (nd - j0 + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+    const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+        const uint32_t js = j0 + ch * SPLIT_CHUNK;
+        const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - js);
+        push_record(a, b, b.w, b.e, js | fresh, jc, b0 + ch);
+    }
+}
+
+// Two Philox4x32-10 blocks side by side, round by round (two independent
+// dependency chains): block r under the per-lane key (ka0, ka1), block s under
+// the step's key (k0, k1).
+__device__ __forceinline__ void philox_pair(uint32_t r[4], uint32_t s[4], uint32_t ka0, uint32_t ka1, uint32_t k0,
+                                            uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * r[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * r[2];
+        const uint64_t q0 = (uint64_t)0xD2511F53u * s[0];
+        const uint64_t q1 = (uint64_t)0xCD9E8D57u * s[2];
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ r[1] ^ ka0, n2 = (uint32_t)(p0 >> 32) ^ r[3] ^ ka1;
+        const uint32_t m0 = (uint32_t)(q1 >> 32) ^ s[1] ^ k0, m2 = (uint32_t)(q0 >> 32) ^ s[3] ^ k1;
+        r[0] = n0;
+        r[1] = (uint32_t)p1;
+        r[2] = n2;
+        r[3] = (uint32_t)p0;
+        s[0] = m0;
+        s[1] = (uint32_t)q1;
+        s[2] = m2;
+        s[3] = (uint32_t)q0;
+        ka0 += 0x9E3779B9u;
+        ka1 += 0xBB67AE85u;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// What a lane's Philox blocks compute in an iteration: the event's two words,
+// or one setup step of a new track (a daughter's lineage key, then for an
+// extra particle of a multiplying collision its own direction; a pulse
+// particle's birth direction).  A setup step takes the lane's iteration, so
+// every Philox block of the loop is drawn at one site, by all lanes at once.
+enum LaneMode : int { M_EVENT = 0, M_LINEAGE = 1, M_DIRECTION = 2, M_BIRTH = 3 };
+constexpr uint32_t LIN_K0 = 0x4C494E45u, LIN_K1 = 0x41474521u;  // the lineage hash's key
+
+// 32-bit halves of a block-private 64-bit accumulator kept as two word
+// arrays (low words, then high words, of a row of I): exact modulo 2^64
+__device__ __forceinline__ void sadd_split(unsigned* lo, unsigned* hi, long long v) {
+    const unsigned vl = (unsigned)(unsigned long long)v;
+    const unsigned old = atomicAdd(lo, vl);
+    const unsigned vh = (unsigned)((unsigned long long)v >> 32) + ((old + vl < old) ? 1u : 0u);
+    if (vh) atomicAdd(hi, vh);
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// start-bank records [i0, i0 + n) into a ring slot (lane l copies record l),
+// one commit group per call
+__device__ __forceinline__ void ring_fetch(BankRec<float>* slot, const BankRec<float>* bank, long long i0, int n,
+                                           unsigned lane) {
+    if ((int)lane < n)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(slot + lane)),
+                     "l"(bank + i0 + lane));
+    asm volatile("cp.async.commit_group;\n" ::);
+}
+
+__device__ __forceinline__ void ring_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// the warp's staged census particles [0, n) to the census bank: one slot
+// reservation, then each lane writes one particle (and its comb group sums)
+__device__ __forceinline__ void census_flush(const TrackArgs<float>& a, WarpShared& ws, int wp, unsigned n,
+                                             unsigned lane) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.cen.count, (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lane < n) {
+        const unsigned long long slot = base + lane;
+        if ((long long)slot < a.cen.cap) {
+            const uint32_t id = ws.cid[wp][lane];
+            const LinW lw = ws.clw[wp][lane];
+            a.cen.x[slot] = ws.cx[wp][lane];
+            a.cen.mu[slot] = ws.cmu[wp][lane];
+            a.cen.w[slot] = ws.cw[wp][lane];
+            a.cen.cell[slot] = ws.ccell[wp][lane];
+            a.cen.id[slot] = id;
+            a.cen.lw[slot] = lw;
+            atomicAdd(&a.gcnt[id], 1u);
+            atomicAdd(&a.gw[id], lw.wfx);
+        } else {
+            atomicOr(a.err, ERR_CENSUS_OVERFLOW);
+        }
+    }
+    __syncwarp();
+}
+
+struct BlockScalars {
+    double wbar, tscale;
+    long long Wbar;
+};
+
+// Items [item0, item_end) of the block, from a block-shared counter; wave 0
+// items are start-bank particles, later waves' items records.
+__device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long long item0, const long long item_end,
+                                         unsigned* s_next, const int b_blk, const uint32_t b_end, unsigned* tl32,
+                                         WarpShared& ws, const BlockScalars& bs, unsigned long long* s_stats) {
     const int I = a.I;
-    if (threadIdx.x == 0) s_next = 0;
-    for (int i = threadIdx.x; i < TALLY_ROWS * I; i += blockDim.x) sm[i] = 0;
+    unsigned* sJl = tl32;
+    unsigned* sJh = tl32 + I;
+    unsigned* sFl = tl32 + 2 * I;
+    unsigned* sFh = tl32 + 3 * I;
+    unsigned* sBl = tl32 + 4 * I;
+    unsigned* sBh = tl32 + 5 * I;
+    const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
+    const int ww_on = a.sd->ww_on;
+    const int birth = a.sd->birth;
+    const bool ring_on = a.from_bank && !birth;  // start-bank records prefetched
+    const unsigned lane = lane_id();
+    const int wp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+
+    if (ring_on) {
+        unsigned b = 0;
+        if (lane == 0) b = atomicAdd(s_next, 64u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        const int n0 = (int)max(0LL, min(32LL, item_end - (item0 + (long long)b)));
+        const int n1 = (int)max(0LL, min(32LL, item_end - (item0 + (long long)b + 32)));
+        ring_fetch(ws.ring[wp][0], a.bank, item0 + (long long)b, n0, lane);
+        ring_fetch(ws.ring[wp][1], a.bank, item0 + (long long)b + 32, n1, lane);
+        if (lane == 0) {
+            ws.rb[wp][0] = b;
+            ws.rb[wp][1] = b + 32u;
+            ws.rn[wp][0] = n0;
+            ws.rn[wp][1] = n1;
+            ws.rcs[wp] = 0;
+            ws.rpos[wp] = 0;
+        }
+        asm volatile("cp.async.wait_group 1;\n" ::);
+        __syncwarp();
+    }
+
+    P32 q;
+    bool have = false;
+    int mode = M_EVENT;
+    uint32_t jd = 0;     // M_LINEAGE: the daughter index hashed into the lineage
+    bool fresh = false;  // M_LINEAGE: then draw an own direction
+    bool items_left = true;
+    int evs = 0;
+    int qb = 0;
+    unsigned cfill = 0;            // staged census particles of the warp
+    unsigned long long mycnt = 0;  // lane k < EB_COUNT: counter kLaneStat[k]; then daughters, max events
+    for (;;) {
+        // ---- refill: daughters from the warp's stack, then new items ----
+        unsigned need = __ballot_sync(0xffffffffu, !have);
+        bool got = false;  // this lane took a new track this iteration
+        while (need) {
+            const int top = *(volatile int*)&ws.top[wp];
+            if (top <= 0) break;
+            const int t = top - 1;
+            const uint32_t jn0 = ws.jn[wp][t], je = ws.je[wp][t];
+            const uint32_t fr = jn0 & FRESH_DIRECTION, jn = jn0 & ~FRESH_DIRECTION;
+            const uint32_t left = je - jn;
+            const uint32_t take = min((uint32_t)__popc(need), left);
+            const uint32_t rank = __popc(need & lt);
+            const bool mine = ((need >> lane) & 1u) && rank < take;
+            if (mine) {
+                q.xo = ws.xo[wp][t];
+                q.mu = ws.mu[wp][t];
+                q.tau = ws.tau[wp][t];
+                q.w = ws.w[wp][t];
+                q.W = ws.W[wp][t];
+                q.cell = ws.cell[wp][t];
+                q.id = ws.id[wp][t];
+                q.lin = ws.lin[wp][t];
+                q.e = ws.e[wp][t];
+                jd = jn + rank;
+                fresh = fr != 0;
+                mode = M_LINEAGE;
+                have = true;
+                got = true;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                if (take == left)
+                    ws.top[wp] = t;
+                else
+                    ws.jn[wp][t] = (jn + take) | fr;
+            }
+            need &= ~__ballot_sync(0xffffffffu, mine);
+            __syncwarp();
+        }
+        if (need && ring_on) {
+            // prefetched start-bank records; when the current slot runs out,
+            // the other (already fetched) slot takes over and the emptied one
+            // fetches the next 32 items
+            int cs = ws.rcs[wp], cpos = ws.rpos[wp];
+            while (need) {
+                const int avail = ws.rn[wp][cs] - cpos;
+                if (avail <= 0) {
+                    if (ws.rn[wp][cs ^ 1] == 0) break;  // no items left
+                    ring_wait_all();
+                    __syncwarp();
+                    unsigned b = 0;
+                    if (lane == 0) b = atomicAdd(s_next, 32u);
+                    b = __shfl_sync(0xffffffffu, b, 0);
+                    const int nn = (int)max(0LL, min(32LL, item_end - (item0 + (long long)b)));
+                    ring_fetch(ws.ring[wp][cs], a.bank, item0 + (long long)b, nn, lane);
+                    __syncwarp();
+                    if (lane == 0) {
+                        ws.rb[wp][cs] = b;
+                        ws.rn[wp][cs] = nn;
+                    }
+                    __syncwarp();
+                    cs ^= 1;
+                    cpos = 0;
+                    continue;
+                }
+                const unsigned take = min((unsigned)__popc(need), (unsigned)avail);
+                const unsigned rank = __popc(need & lt);
+                const bool mine = ((need >> lane) & 1u) && rank < take;
+                if (mine) {
+                    const BankRec<float> r = ws.ring[wp][cs][cpos + (int)rank];
+                    q.id = (uint32_t)(item0 + (long long)ws.rb[wp][cs] + cpos + (long long)rank);
+                    q.lin = 0;
+                    q.e = 0;
+                    q.tau = a.tau0f;
+                    q.w = bs.wbar;
+                    q.W = bs.Wbar;
+                    q.xo = r.x;
+                    q.mu = r.mu;
+                    q.cell = r.cell;
+                    mode = M_EVENT;
+                    have = true;
+                    got = true;
+                }
+                cpos += (int)take;
+                need &= ~__ballot_sync(0xffffffffu, mine);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                ws.rcs[wp] = cs;
+                ws.rpos[wp] = cpos;
+            }
+        } else if (need && items_left) {
+            const unsigned k = __popc(need);
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(s_next, k);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (item0 + (long long)base + k >= item_end) items_left = false;
+            const long long i = item0 + (long long)base + (long long)__popc(need & lt);
+            if (((need >> lane) & 1u) && i < item_end) {
+                mode = M_EVENT;
+                if (a.from_bank) {  // the pulse (step 1)
+                    q.id = (uint32_t)i;
+                    q.lin = 0;
+                    q.e = 0;
+                    q.tau = a.tau0f;
+                    q.w = bs.wbar;
+                    q.W = bs.Wbar;
+                    mode = M_BIRTH;
+                } else {
+                    q.xo = a.rin.x[i];
+                    q.mu = a.rin.mu[i];
+                    q.tau = a.rin.tau[i];
+                    q.w = a.rin.w[i];
+                    q.W = to_fixed(q.w, bs.tscale);
+                    q.cell = a.rin.cell[i];
+                    q.id = a.rin.id[i];
+                    q.lin = a.rin.lin[i];
+                    q.e = a.rin.e[i];
+                    const uint32_t jc = a.rin.jcount[i];
+                    if (jc) {
+                        // a chunk of daughters: this lane takes the first, the
+                        // rest go to the warp's stack (or back to the queue)
+                        const uint32_t js = a.rin.jstart[i];
+                        const uint32_t j0 = js & ~FRESH_DIRECTION;
+                        if (jc > 1 && !stack_push(ws, wp, q, js + 1u, j0 + jc))
+                            queue_daughters(a, q, j0 + 1u, j0 + jc, js & FRESH_DIRECTION);
+                        jd = j0;
+                        fresh = (js & FRESH_DIRECTION) != 0;
+                        mode = M_LINEAGE;
+                    }
+                }
+                have = true;
+                got = true;
+            }
+            __syncwarp();
+        }
+        if (got) {
+            evs = 0;
+            // the block's range lies in batch b_blk up to id b_end (at most
+            // a few ids of a range reach the next batch)
+            qb = (q.id >= (uint32_t)item0 && q.id < b_end) ? b_blk : batch_of(q.id, a.B, a.N, a.batch_m);
+            if (mode == M_EVENT) q.inv_mu = __frcp_rn(q.mu);  // the correctly rounded 1/mu
+        }
+        if (!__any_sync(0xffffffffu, have)) break;
+
+        unsigned eb = 0;      // outcome bits
+        uint32_t nadd = 0;    // daughters created
+        uint32_t e_end = 0;   // event count of a track that ended
+        if (have && mode == M_EVENT) {
+            if (evs == a.emax) {  // past the event budget: a continuation record
+                push_record(a, q, q.w, q.e, 0u, 0u, warp_reserve(a.rout.count));
+                have = false;
+            } else if (q.e >= MAX_EVENTS) {
+                atomicOr(a.err, ERR_EVENTS);
+                have = false;
+            }
+        }
+        // ---- the iteration's Philox blocks, all lanes at once ----
+        uint32_t r[4], r2[4];
+        uint32_t ka0 = k0, ka1 = k1;
+        if (mode == M_EVENT) {
+            r[0] = q.id;
+            r[1] = (uint32_t)q.lin;
+            r[2] = (uint32_t)(q.lin >> 32);
+            r[3] = 2u * q.e;
+        } else if (mode == M_LINEAGE) {
+            r[0] = (uint32_t)q.lin;
+            r[1] = (uint32_t)(q.lin >> 32);
+            r[2] = q.e;
+            r[3] = jd;
+            ka0 = LIN_K0;
+            ka1 = LIN_K1;
+        } else if (mode == M_DIRECTION) {
+            r[0] = q.id;
+            r[1] = (uint32_t)q.lin;
+            r[2] = (uint32_t)(q.lin >> 32);
+            r[3] = 0xFFFFFFFEu;
+        } else {
+            r[0] = q.id;
+            r[1] = 0u;
+            r[2] = 0u;
+            r[3] = 0xFFFFFFFFu;
+        }
+        r2[0] = q.id;
+        r2[1] = (uint32_t)q.lin;
+        r2[2] = (uint32_t)(q.lin >> 32);
+        r2[3] = 2u * q.e + 1u;
+        philox_pair(r, r2, ka0, ka1, k0, k1);
+
+        if (have && mode != M_EVENT) {
+            // ---- a setup step of a new track ----
+            if (mode == M_LINEAGE) {
+                q.lin = ((uint64_t)r[1] << 32) | r[0];
+                q.e = 0;
+                mode = fresh ? M_DIRECTION : M_EVENT;
+            } else if (mode == M_DIRECTION) {
+                q.mu = 2.0f * u01f(r[1]) - 1.0f;
+                mode = M_EVENT;
+            } else {  // the pulse: isotropic birth direction, mirrored into a reflecting wall's side
+                q.mu = 2.0f * u01f(r[1]) - 1.0f;
+                const double x = a.src_x;
+                if (x <= a.edges[0] && q.mu < 0.0f && a.bc_l == 1) q.mu = -q.mu;
+                if (x >= a.edges[I] && q.mu > 0.0f && a.bc_r == 1) q.mu = -q.mu;
+                q.cell = (q.mu < 0.0f) ? a.birth_cell_neg : a.birth_cell_pos;
+                q.xo = (float)(x - a.edges[q.cell]);
+                mode = M_EVENT;
+            }
+            if (mode == M_EVENT) q.inv_mu = __frcp_rn(q.mu);
+        } else if (have) {
+            // ---- one event ----
+            const float uf = u01f(r[1]);
+            const float uc = u01f(r[3]);
+            const int k = q.cell;
+            const float4 cf = __ldg(&a.cellf[k]);  // width, 1/Sigma_t, c
+            const float dxk = cf.x;
+            // the hardware base-2 logarithm times ln 2: within 2^-21.41 absolute for
+            // u in [1/2, 1) and 3 ulp below (the CUDA intrinsic's stated bounds)
+            const float dcoll = -__logf(uf) * cf.y;
+            const float dedge = ((q.mu > 0.0f) ? (dxk - q.xo) : -q.xo) * q.inv_mu;
+            const float dcens = q.tau;
+            int ev;
+            float l;
+            if (dcens <= dedge && dcens <= dcoll) {
+                ev = 0;
+                l = dcens;
+            } else if (dedge <= dcoll) {
+                ev = 1;
+                l = dedge;
+            } else {
+                ev = 2;
+                l = dcoll;
+            }
+            const float f3 = 1.0f / 3.0f - q.mu * q.mu;
+            {
+                const long long c0 = fx_mul(q.W, l);
+                sadd_split(&sJl[k], &sJh[k], fx_mul(q.W, l * q.mu));
+                sadd_split(&sFl[k], &sFh[k], fx_mul(q.W, l * f3));
+                if (qb == b_blk)
+                    sadd_split(&sBl[k], &sBh[k], c0);
+                else
+                    add128(&a.batch[(long long)qb * I + k], c0);
+            }
+            if (ev != 1) q.xo = fminf(fmaxf(fmaf(q.mu, l, q.xo), 0.0f), dxk);
+            q.tau = (ev == 0) ? 0.0f : q.tau - l;
+            const uint32_t e_ev = q.e;
+            q.e = q.e + 1;
+            ++evs;
+            bool ww = false;
+            if (ev == 0) {
+                // census: staged below (its tallies come from the census pass)
+                eb |= 1u << EB_CENSUS;
+                e_end = q.e;
+                have = false;
+            } else if (ev == 1) {
+                eb |= 1u << EB_CROSS;
+                const int nk = (q.mu > 0.0f) ? k + 1 : k - 1;
+                if (nk < 0 || nk >= I) {
+                    const int side = (nk < 0) ? 0 : 1;
+                    const int bc = side ? a.bc_r : a.bc_l;
+                    if (bc == 0) {
+                        const double amu = fabs((double)q.mu);
+                        const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
+                        const double wi = q.w * ia;
+                        const double dm2 = (double)q.mu * (double)q.mu;
+                        add128(&a.bnd[3 * side + 0], to_fixed(wi, bs.tscale));
+                        add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - dm2), bs.tscale));
+                        add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), bs.tscale));
+                        eb |= 1u << EB_LEAK;
+                        e_end = q.e;
+                        have = false;
+                    } else {
+                        q.mu = -q.mu;
+                        q.inv_mu = -q.inv_mu;
+                        q.xo = side ? dxk : 0.0f;
+                        eb |= 1u << EB_REFL;
+                        ww = true;
+                    }
+                } else {
+                    q.cell = nk;
+                    q.xo = (q.mu > 0.0f) ? 0.0f : __ldg(&a.cellf[nk]).x;
+                    ww = true;
+                }
+            } else {
+                eb |= 1u << EB_COLL;
+                // the collision emits floor(c) + [u_c < c - floor(c)] particles (mean c)
+                const float cfl = floorf(cf.z);
+                const uint32_t nsec = (uint32_t)cfl + ((uc < cf.z - cfl) ? 1u : 0u);
+                if (nsec == 0) {
+                    eb |= 1u << EB_ABS;
+                    e_end = q.e;
+                    have = false;
+                } else {
+                    q.mu = 2.0f * u01f(r2[1]) - 1.0f;
+                    q.inv_mu = __frcp_rn(q.mu);
+                    if (nsec > 1) {
+                        // the other emitted particles: daughters with their
+                        // own lineages and isotropic directions
+                        P32 b = q;
+                        b.e = e_ev | SECONDARY_EVENT;
+                        if (!stack_push(ws, wp, b, 1u | FRESH_DIRECTION, nsec))
+                            queue_daughters(a, b, 1u, nsec, FRESH_DIRECTION);
+                        nadd += nsec - 1;
+                    }
+                    ww = true;
+                }
+            }
+            if (ww && ww_on) {
+                const int kc = q.cell;
+                const double2 hl = __ldg(&a.ww_hl[kc]);  // ceiling, floor
+                if (dgt(q.w, hl.x)) {
+                    const double ctr = a.ww_c[kc];
+                    // split count from an FP32 ratio (the FP32 path's own rounding)
+                    const float ndf = ceilf((float)q.w / (float)ctr);
+                    const double ndd = (double)fmaxf(ndf, 2.0f);
+                    if (ndd > (double)MAX_DAUGHTERS) {
+                        atomicOr(a.err, ERR_DAUGHTERS);
+                        have = false;
+                    } else {
+                        const uint32_t nd = (uint32_t)ndd;
+                        const double wd = q.w / (double)nd;
+                        const long long Wd = to_fixed(wd, bs.tscale);
+                        eb |= 1u << EB_SPLIT;
+                        nadd += nd - 1;
+                        q.w = wd;
+                        q.W = Wd;
+                        q.e = e_ev;
+                        if (!stack_push(ws, wp, q, 1u, nd)) queue_daughters(a, q, 1u, nd, 0u);
+                        // this lane goes on with daughter 0 (its lineage key next)
+                        jd = 0;
+                        fresh = false;
+                        mode = M_LINEAGE;
+                    }
+                } else if (dgt(hl.y, q.w)) {
+                    const double ctr = a.ww_c[kc];
+                    // survive iff u < w / ww, tested as u ww < w (no divide)
+                    const double ur = u01(r2[2], r2[3]);
+                    if (ur * ctr < q.w) {
+                        q.w = ctr;
+                        q.W = to_fixed(ctr, bs.tscale);
+                        eb |= 1u << EB_RSURV;
+                    } else {
+                        eb |= 1u << EB_RKILL;
+                        e_end = q.e;
+                        have = false;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // ---- census particles of the iteration: staged, written 32 at a time ----
+        {
+            const unsigned cm = __ballot_sync(0xffffffffu, (eb >> EB_CENSUS) & 1u);
+            const unsigned nc = __popc(cm);
+            if (nc) {
+                if (cfill + nc > 32u) {
+                    census_flush(a, ws, wp, cfill, lane);
+                    cfill = 0;
+                }
+                if ((cm >> lane) & 1u) {
+                    const unsigned pos = cfill + __popc(cm & lt);
+                    ws.cx[wp][pos] = q.xo;
+                    ws.cmu[wp][pos] = q.mu;
+                    ws.cw[wp][pos] = q.w;
+                    ws.ccell[wp][pos] = q.cell;
+                    ws.cid[wp][pos] = q.id;
+                    ws.clw[wp][pos] = LinW{q.lin, comb_weight(q.W, a.comb_shift)};
+                }
+                cfill += nc;
+                __syncwarp();
+            }
+        }
+        // ---- the iteration's counts, summed over the warp ----
+        {
+            // bit k of the outcome goes to bit 6k of a word (five 6-bit fields
+            // per word: a field sums at most 32 lanes); a multiply places
+            // non-overlapping 5-bit copies 5 bits apart, so bit k of copy k
+            // lands at 6k
+            const unsigned wlo = ((eb & 0x1Fu) * 0x108421u) & 0x1041041u;
+            const unsigned whi = (((eb >> 5) & 0xFu) * 0x8421u) & 0x41041u;
+            const unsigned slo = __reduce_add_sync(0xffffffffu, wlo);
+            const unsigned shi = __reduce_add_sync(0xffffffffu, whi);
+            const unsigned sd = __reduce_add_sync(0xffffffffu, nadd);
+            const unsigned smax = __reduce_max_sync(0xffffffffu, e_end);
+            const unsigned f = ((lane < 5u ? slo : shi) >> (6u * (lane < 5u ? lane : lane - 5u))) & 63u;
+            const unsigned add = lane < (unsigned)EB_COUNT ? f : (lane == (unsigned)LANE_DAUGHTERS ? sd : 0u);
+            mycnt += add;
+            if (lane == (unsigned)LANE_MAXEV) mycnt = max(mycnt, (unsigned long long)smax);
+        }
+    }
+    if (cfill) census_flush(a, ws, wp, cfill, lane);
+    if (ring_on) ring_wait_all();  // no copy outlives the block
+    // the warp's counts into the block's
+    if (lane < (unsigned)EB_COUNT) {
+        if (mycnt) atomicAdd(&s_stats[kLaneStat[lane]], mycnt);
+    } else if (lane == (unsigned)LANE_DAUGHTERS) {
+        if (mycnt) atomicAdd(&s_stats[ST_DAUGHTERS], mycnt);
+    } else if (lane == (unsigned)LANE_MAXEV) {
+        if (mycnt) atomicMax(&s_stats[ST_MAX_EVENTS], mycnt);
+    }
+}
+
+// Four resident blocks of 256 threads per SM (64 registers, no spills; the
+// warp-synchronous loop keeps no per-lane counters and no pending parent in
+// registers), 32 warps per SM to hide the event loop's latencies.
+__global__ void __launch_bounds__(TRACK_THREADS, 4) track32_kernel(TrackArgs<float> a) {
+    extern __shared__ long long sm[];  // ROWS32 rows of I 64-bit words, as 32-bit halves
+    __shared__ unsigned s_next;
+    __shared__ WarpShared s_ws;
+    __shared__ unsigned long long s_stats[ST_COUNT];
+    __shared__ BlockScalars s_bs;
+    const int I = a.I;
+    unsigned* tl32 = reinterpret_cast<unsigned*>(sm);
+    if (threadIdx.x == 0) {
+        s_next = 0;
+        s_bs.wbar = a.sd->wbar;
+        s_bs.tscale = a.sd->tscale;
+        s_bs.Wbar = a.sd->Wbar;
+    }
+    if (threadIdx.x < WARPS) s_ws.top[threadIdx.x] = 0;
+    if (threadIdx.x < ST_COUNT) s_stats[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < 2 * ROWS32 * I; i += blockDim.x) tl32[i] = 0;
     __syncthreads();
-    Counters cnt;
-    cnt.zero();
     const long long n_in = a.from_bank ? (long long)a.sd->nbank : (long long)*a.rin.count;
     const long long n_use = (!a.from_bank && n_in > a.rin.cap) ? a.rin.cap : n_in;
-    // wave 0: each block takes a contiguous id range of [bank_lo, bank_hi), so
-    // nearly all of its segments fall in one variance batch (kept in shared
-    // memory), and its lanes take the range's items from a shared counter
-    // (splits leave the daughters with the splitting lane, so lanes carry
-    // uneven work); record waves: grid-stride over the records.  More,
-    // smaller ranges balance the blocks better but cost more tally flushes;
-    // one range per resident block measured fastest.
-    long long stride, item, item_end;
-    unsigned* dyn = nullptr;
+    // each block takes a contiguous range: of [bank_lo, bank_hi) in wave 0,
+    // so that nearly all of its segments fall in one variance batch (kept in
+    // shared memory), or of the record queue in later waves
+    const long long lo = a.from_bank ? a.bank_lo : 0;
+    const long long hi = a.from_bank ? min(n_use, a.bank_hi) : n_use;
+    const long long len = hi > lo ? hi - lo : 0;
+    const long long chunk = (len + gridDim.x - 1) / gridDim.x;
+    const long long first = lo + (long long)blockIdx.x * chunk;
+    const long long last = min(hi, first + chunk);
     int b_blk = -1;
-    if (a.from_bank) {
-        const long long lo = a.bank_lo;
-        const long long hi = min(n_use, a.bank_hi);
-        const long long len = hi > lo ? hi - lo : 0;
-        const long long chunk = (len + gridDim.x - 1) / gridDim.x;
-        const long long first = lo + (long long)blockIdx.x * chunk;
-        item = first;
-        item_end = min(hi, first + chunk);
-        stride = 0;
-        dyn = &s_next;
-        if (first < hi) b_blk = batch_of((uint32_t)first, a.B, a.N, a.batch_m);
-    } else {
-        item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        item_end = n_use;
-        stride = (long long)gridDim.x * blockDim.x;
+    uint32_t b_end = 0;  // first id past batch b_blk (0: none of the range)
+    if (a.from_bank && first < hi) {
+        b_blk = batch_of((uint32_t)first, a.B, a.N, a.batch_m);
+        // ids with floor(id B / N) == b_blk end at ceil((b_blk + 1) N / B)
+        b_end = (uint32_t)min((long long)UINT32_MAX, ((long long)(b_blk + 1) * a.N + a.B - 1) / a.B);
     }
-    run_items<LOCAL_DAUGHTERS>(a, item, item_end, stride, dyn, b_blk, sm, cnt, &s_pp);
+    const BlockScalars bs = s_bs;
+    run_warp(a, first, last, &s_next, b_blk, b_end, tl32, s_ws, bs, s_stats);
     __syncthreads();
-    flush_tallies(sm, I, a.tl);
-    if (b_blk >= 0)
-        for (int i = threadIdx.x; i < I; i += blockDim.x)
-            if (sm[3 * I + i] != 0) add128(&a.batch[(long long)b_blk * I + i], sm[3 * I + i]);
-    flush_counters(cnt, a.stats);
+    // block-private tallies into the global ones (J, F; the batch row)
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        const long long vJ = (long long)(((unsigned long long)tl32[I + i] << 32) | tl32[i]);
+        const long long vF = (long long)(((unsigned long long)tl32[3 * I + i] << 32) | tl32[2 * I + i]);
+        if (vJ != 0) add128(&a.tl[I + i], vJ);
+        if (vF != 0) add128(&a.tl[2 * I + i], vF);
+        if (b_blk >= 0) {
+            const long long vB = (long long)(((unsigned long long)tl32[5 * I + i] << 32) | tl32[4 * I + i]);
+            if (vB != 0) add128(&a.batch[(long long)b_blk * I + i], vB);
+        }
+    }
+    // counts: segments and scatters follow from the event counts
+    if (threadIdx.x == 0) {
+        s_stats[ST_SEGMENTS] = s_stats[ST_CENSUS] + s_stats[ST_CROSSINGS] + s_stats[ST_COLLISIONS];
+        s_stats[ST_SCATTERS] = s_stats[ST_COLLISIONS] - s_stats[ST_ABSORBED];
+    }
+    __syncthreads();
+    if (threadIdx.x < ST_COUNT && s_stats[threadIdx.x]) {
+        if (threadIdx.x == ST_MAX_EVENTS)
+            atomicMax(&a.stats[ST_MAX_EVENTS], s_stats[threadIdx.x]);
+        else
+            atomicAdd(&a.stats[threadIdx.x], s_stats[threadIdx.x]);
+    }
 }
 
 // Persistent batched variant: blocks pop tiles (problem, id range) from a
