@@ -358,10 +358,12 @@ hww_status hww_losm_solve(int32_t n_cells, const double* dx, const double* sigma
  * stages everything in a fixed device array compiled into the library,
  * sized for n_cells <= HWW_NOALLOC_MAX_CELLS (about 0.8 MB, held on every
  * GPU that loads the library until the process exits); larger n_cells
- * return HWW_ERR_ARG.  The first call on a device looks up that array's
- * device address, with the device current; make this first call before
- * any stream capture.  The call uses no cudaMalloc, cudaFree or other
- * allocating routine.  All calls on a device share the array, which keeps
+ * return HWW_ERR_ARG.  Every call looks up that array's device address
+ * on the current device (so the address is never stale, for instance
+ * after a context reset); make the first call on a device before any
+ * stream capture.  The call uses no cudaMalloc, cudaFree or other
+ * allocating routine.  A CUDA error is recorded for
+ * hww_last_error_string, as hww_losm_solve does.  All calls on a device share the array, which keeps
  * the previous call's contents (the call clears what must start at zero),
  * so calls that overlap on the GPU, for instance from two host threads at
  * the same time, race. */

@@ -138,6 +138,13 @@ hww_status cuda_status(cudaError_t e) {
     return HWW_ERR_CUDA;
 }
 
+}  // namespace
+
+// a CUDA error of another translation unit, recorded for hww_last_error_string
+hww_status hww::record_cuda_error(cudaError_t e) { return cuda_status(e); }
+
+namespace {
+
 #define HWW_CK(call)                                              \
     do {                                                          \
         cudaError_t e_ = (call);                                  \
@@ -1531,84 +1538,15 @@ hww_status hww_losm_solve(int32_t I, const double* dx, const double* sigma_t, co
         return HWW_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return HWW_ERR_NO_DEVICE;
-    // one device buffer: cell arrays, vectors, the matrix, work and the error word
-    const size_t n2 = I + 2, n1 = I + 1;
-    const size_t total = 5 * (size_t)I + 4 * n2 + 2 * n1 + (4 * n1 + 3 * (size_t)I + 3 * n2) + (2 * n2 + n1) + 1;
     double* buf = nullptr;
-    HWW_CK(cudaMalloc(&buf, total * sizeof(double)));
-    double* q = buf;
-    auto take = [&](size_t k) {
-        double* r = q;
-        q += k;
-        return r;
-    };
-    double* d_dx = take(I);
-    double* d_st = take(I);
-    double* d_sa = take(I);
-    double* d_qo = take(I);
-    double* d_qn = take(I);
-    double* d_po = take(n2);
-    double* d_Fo = take(n2);
-    double* d_Fn = take(n2);
-    double* d_pn = take(n2);
-    double* d_Jo = take(n1);
-    double* d_Jn = take(n1);
-    LosmMat m{};
-    m.I = I;
-    m.theta = theta;
-    m.bc_l = bc_left;
-    m.bc_r = bc_right;
-    m.eJ = take(n1);
-    m.eS = take(n1);
-    m.invd = take(n1);
-    m.g = take(n1);
-    m.cP = take(I);
-    m.cA = take(I);
-    m.cB = take(I);
-    m.inv_den = take(n2);
-    m.vf = take(n2);
-    m.cp = take(n2);
-    LosmWork w{};
-    w.u = take(n2);
-    w.y = take(n2);
-    w.mom = take(n1);
-    unsigned* d_err = (unsigned*)take(1);
-    cudaError_t e = cudaSuccess;
-    auto up = [&](double* dst, const double* src, size_t cnt) {
-        if (e == cudaSuccess && src) e = cudaMemcpy(dst, src, cnt * sizeof(double), cudaMemcpyHostToDevice);
-    };
-    up(d_dx, dx, I);
-    up(d_st, sigma_t, I);
-    up(d_sa, sigma_a, I);
-    up(d_qo, q_old, I);
-    up(d_qn, q_new, I);
-    up(d_po, phi_old, n2);
-    up(d_Fo, F_old, n2);
-    up(d_Fn, F_new, n2);
-    up(d_Jo, J_old, n1);
-    if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(unsigned));
-    if (e == cudaSuccess) {
-        launch_losm_setup(m, d_dx, d_st, d_sa, v, dt, theta, bc_left, bc_right, d_err, 0);
-        LosmRhsIn in{};
-        in.phi_old = d_po;
-        in.J_old = d_Jo;
-        in.F_old = d_Fo;
-        in.F_new = d_Fn;
-        in.P_new = nullptr;
-        in.PL = PL_new;
-        in.PR = PR_new;
-        in.q_old = q_old ? d_qo : nullptr;
-        in.q_new = q_new ? d_qn : nullptr;
-        launch_losm_solve(m, in, w, d_pn, d_Jn, nullptr, 0);
-        e = cudaGetLastError();
-    }
-    unsigned herr = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(phi_new, d_pn, n2 * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(J_new, d_Jn, n1 * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    HWW_CK(cudaMalloc(&buf, losm_staged_doubles((size_t)I) * sizeof(double)));
+    bool numeric = false;
+    const cudaError_t e = losm_solve_staged(buf, I, dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, phi_old,
+                                            J_old, F_old, F_new, PL_new, PR_new, q_old, q_new, phi_new, J_new,
+                                            &numeric);
     cudaFree(buf);
     if (e != cudaSuccess) return cuda_status(e);
-    return herr ? HWW_ERR_NUMERIC : HWW_OK;
+    return numeric ? HWW_ERR_NUMERIC : HWW_OK;
 }
 
 hww_status hww_philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,

@@ -14,6 +14,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/hww.h"
 #include "hww_device.cuh"
 
 namespace hww {
@@ -177,6 +178,10 @@ struct BatchPlan {
     int tile;
     unsigned long long* head;
 };
+
+// the status of a CUDA error, recorded for hww_last_error_string (defined with
+// the C ABI)
+hww_status record_cuda_error(cudaError_t e);
 
 // kernels implemented in the tracking translation units
 void launch_track_fp64(const TrackArgs<double>& a, int grid, int block, size_t smem, cudaStream_t s);

@@ -719,4 +719,88 @@ int launch_losm_vjp(const VjpArgs& a, cudaStream_t s) {
     return 1;
 }
 
+cudaError_t losm_solve_staged(double* base, int I, const double* dx, const double* sigma_t, const double* sigma_a,
+                              double v, double dt, double theta, int bc_left, int bc_right, const double* phi_old,
+                              const double* J_old, const double* F_old, const double* F_new, double PL_new,
+                              double PR_new, const double* q_old, const double* q_new, double* phi_new,
+                              double* J_new, bool* numeric) {
+    *numeric = false;
+    double* q = base;
+    auto take = [&](size_t k) {
+        double* r = q;
+        q += k;
+        return r;
+    };
+    const size_t n2 = (size_t)I + 2, n1 = (size_t)I + 1;
+    double* d_dx = take(I);
+    double* d_st = take(I);
+    double* d_sa = take(I);
+    double* d_qo = take(I);
+    double* d_qn = take(I);
+    double* d_po = take(n2);
+    double* d_Fo = take(n2);
+    double* d_Fn = take(n2);
+    double* d_pn = take(n2);
+    double* d_Jo = take(n1);
+    double* d_Jn = take(n1);
+    LosmMat m{};
+    m.I = I;
+    m.theta = theta;
+    m.bc_l = bc_left;
+    m.bc_r = bc_right;
+    m.eJ = take(n1);
+    m.eS = take(n1);
+    m.invd = take(n1);
+    m.g = take(n1);
+    m.cP = take(I);
+    m.cA = take(I);
+    m.cB = take(I);
+    m.inv_den = take(n2);
+    m.vf = take(n2);
+    m.cp = take(n2);
+    LosmWork w{};
+    w.u = take(n2);
+    w.y = take(n2);
+    w.mom = take(n1);
+    unsigned* d_err = (unsigned*)take(1);
+    cudaError_t e = cudaSuccess;
+    auto up = [&](double* dst, const double* src, size_t cnt) {
+        if (e == cudaSuccess && src) e = cudaMemcpy(dst, src, cnt * sizeof(double), cudaMemcpyHostToDevice);
+    };
+    up(d_dx, dx, I);
+    up(d_st, sigma_t, I);
+    up(d_sa, sigma_a, I);
+    up(d_qo, q_old, I);
+    up(d_qn, q_new, I);
+    up(d_po, phi_old, n2);
+    up(d_Fo, F_old, n2);
+    up(d_Fn, F_new, n2);
+    up(d_Jo, J_old, n1);
+    // the block may hold an earlier call's contents: the error word starts at 0
+    if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        launch_losm_setup(m, d_dx, d_st, d_sa, v, dt, theta, bc_left, bc_right, d_err, 0);
+        LosmRhsIn in{};
+        in.phi_old = d_po;
+        in.J_old = d_Jo;
+        in.F_old = d_Fo;
+        in.F_new = d_Fn;
+        in.P_new = nullptr;
+        in.PL = PL_new;
+        in.PR = PR_new;
+        in.q_old = q_old ? d_qo : nullptr;
+        in.q_new = q_new ? d_qn : nullptr;
+        launch_losm_solve(m, in, w, d_pn, d_Jn, nullptr, 0);
+        e = cudaGetLastError();
+    }
+    unsigned herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(phi_new, d_pn, n2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(J_new, d_Jn, n1 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    // the carving above must stay within the block the callers size
+    if (e == cudaSuccess && (size_t)(q - base) != losm_staged_doubles(I)) e = cudaErrorInvalidValue;
+    *numeric = herr != 0;
+    return e;
+}
+
 }  // namespace hww

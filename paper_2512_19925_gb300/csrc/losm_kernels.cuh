@@ -130,6 +130,19 @@ void launch_losm_setup(const LosmMat& m, const double* dx, const double* sigt, c
                        double dt, double theta, int bc_l, int bc_r, unsigned* err, cudaStream_t s);
 int launch_losm_solve(const LosmMat& m, const LosmRhsIn& in, const LosmWork& w, double* phi, double* J,
                       double* mx, cudaStream_t s);
+// A standalone LOSM solve from host vectors (hww_losm_solve and its
+// no-allocation variant): the cell arrays, the old and new vectors, the
+// factorized matrix, the work vectors and an error word are carved from one
+// device block of losm_staged_doubles(I) doubles at `base`; the inputs are
+// copied in, the solve runs on the default stream, and phi (I+2), J (I+1) are
+// copied back.  Synchronous.  Returns the first CUDA error; *numeric is set
+// when the solver's guard fired.
+constexpr size_t losm_staged_doubles(size_t I) { return 24 * I + 26; }
+cudaError_t losm_solve_staged(double* base, int I, const double* dx, const double* sigma_t, const double* sigma_a,
+                              double v, double dt, double theta, int bc_left, int bc_right, const double* phi_old,
+                              const double* J_old, const double* F_old, const double* F_new, double PL_new,
+                              double PR_new, const double* q_old, const double* q_new, double* phi_new,
+                              double* J_new, bool* numeric);
 int launch_ww_centers(const WwArgs& a, int lagged, cudaStream_t s);
 void launch_step_scalars(StepDev* sd, int nbits, unsigned long long seed, int mode, unsigned long long* stats,
                          cudaStream_t s);

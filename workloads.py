@@ -18,7 +18,7 @@ slab with a uniform mesh.  The workloads below keep that shape:
                       x = 0, vacuum at x = 40, 800 cells, dt = 0.1, 200 steps,
                       1e8 particles/step, FP32 tracking.
 * ``batched_sweep``   256 independent homogeneous / two-region slabs on
-                      [-10,10] with cells ~ U{100..2000}, particles/step
+                      [-50,50] with cells ~ U{100..2000}, particles/step
                       log-uniform in [1e4, 1e6], Sigma_t ~ U[0.5,5],
                       c ~ U[0.3,0.999], ratio in {2,3,5,10}, dt = 0.1, 50 steps.
 * ``differentiation`` the shield slab at 1e7 particles/step in FP64 with
