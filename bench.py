@@ -13,6 +13,16 @@ for comparison.  Inputs stay resident in HBM; the per-step working set
 (start bank, census bank, split records) is several hundred MB, larger than
 the 129 MB L2.
 
+Besides the headline (K timed steps after W warm-up steps) the line carries:
+the whole 100-step run of the same workload timed step by step (early and
+late windows); FOM_Error (Eq. FOM_error, against the semi-analytic
+infinite-medium pulse, which the workload is over its 100 steps) and FOM_sigma
+(Eq. FOM_sigma, batch variance) of the FP32 and FP64 paths over 4 seeds, with
+their seed-to-seed uncertainty; the three-region shield at 1e8 particles per
+step over its 200 steps; the batched sweep and the differentiation workload;
+roofline objects for every path; the device's FP64 FMA rate measured by the
+library's own loop; and the CPU oracle on one core and on every core.
+
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 """
 from __future__ import annotations
@@ -39,16 +49,22 @@ METRIC = "particle-segments/sec and FOM at fixed rel. error, 1 GB300, vs plain F
 UNIT = "particle-segments/s"
 WORKLOAD = ("plain_at_scale: slab [-50,50], Sigma_t=1, c=0.9, v=1, 1000 cells, dt=0.2, "
             "1e7 particles/step, MA filter k=3, window ratio 5 (rho=sqrt 5), eps_min=1e-3")
-# bytes each tracking pass must move: read the start bank (cell, offset,
-# direction) and write the census bank (offset, direction, weight, cell, id,
-# lineage); FP32 tracking stores offsets and directions in 4 bytes, FP64 in 8
-BANK_BYTES = {"fp32": 12, "fp64": 20}
-CENSUS_BYTES = {"fp32": 32, "fp64": 40}
-# DRAM bytes (read + write) that one wave-0 tracking launch moves per start
-# particle, measured by ncu on the 4e6-particle case of this workload
-# (profiles/track32_kernel_plain_at_scale_fp32.txt; traffic grows with the
-# particle count).  Set to None whenever track32_kernel changes.
-TRACK32_DRAM_BYTES_PER_START = 322.1e6 / 4e6
+# Algorithmic bytes of one tracking pass per particle state moved: the bank
+# streaming the tracking must do is one read of the start bank and one write
+# of the census bank, S bytes per particle each, with the per-particle state
+# sizes the scope fixes (FP32 path: offset, direction, time left 4 B each,
+# weight 8, cell 4, id 4, lineage 8, event 4 = 40 B; FP64 path: position,
+# direction, time, weight 8 B each, cell 4, id 4, lineage 8, event 4 = 52 B;
+# derivative runs carry 48 B of scores more).
+STATE_BYTES = {"fp32": 40, "fp64": 52}
+SCORE_BYTES = 48
+# DRAM bytes (read + write) that one wave-0 launch of track32_kernel moves per
+# start particle, measured by ncu (profiles/track32_kernel_plain_at_scale_fp32.txt);
+# set to None whenever track32_kernel changes.
+TRACK32_DRAM_BYTES_PER_START = None
+TRACK32_DRAM_NOTE = None
+# the stored semi-analytic benchmark of the workload's census flux
+PULSE_REFERENCE = os.path.join(ROOT, "tests", "golden", "pulse_census_plain_at_scale.npz")
 
 
 def dist_env():
@@ -119,11 +135,17 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "5"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
+
+    def close(self):
+        try:
+            os.unlink(self.path)
+        except Exception:
+            pass
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -136,8 +158,8 @@ class ClockSampler:
     def summary(self, window=None):
         """Median SM clock, maximum clock and the throttle reasons seen in
         the samples whose timestamps fall in `window` (host epoch seconds of
-        the timed region); all samples when no window is given or none falls
-        in it (the count says which)."""
+        the timed region, or a list of such windows); all samples when no
+        window is given or none falls in it (the count says which)."""
         rows = []
         try:
             for line in open(self.path):
@@ -152,12 +174,8 @@ class ClockSampler:
                     continue
         except Exception:
             pass
-        finally:
-            try:
-                os.unlink(self.path)
-            except Exception:
-                pass
-        inside = [r for r in rows if window and window[0] <= r[0] <= window[1]]
+        wins = [] if not window else (list(window) if isinstance(window[0], (tuple, list)) else [window])
+        inside = [r for r in rows if any(w[0] <= r[0] <= w[1] for w in wins)]
         use = inside if inside else rows
         sm = [r[1] for r in use]
         mx = [r[2] for r in use]
@@ -184,6 +202,45 @@ def fom_sigma(batch, tau_s):
         return None, None
     rsd2 = float(np.mean((s[ok] / m[ok]) ** 2))
     return (1.0 / (tau_s * rsd2) if rsd2 > 0 else None), math.sqrt(rsd2)
+
+
+def fom_error(phi_mc, phi_ref, tau_s):
+    """FOM_Error = 1 / (tau * mean_i (|phi_mc,i - phi_ref,i| / phi_ref,i)^2)
+    (Eq. FOM_error) over the cells the reference reaches; returns (FOM, the
+    root-mean-square relative error).  Cells whose reference is below 1e-10
+    of its largest value are left out: they are floating-point slivers of the
+    light cone (a cell edge that rounds a few ulp inside v t), which no
+    particle can reach."""
+    ok = phi_ref > 1e-10 * (np.max(phi_ref) if phi_ref.size else 0.0)
+    if not np.any(ok) or tau_s <= 0:
+        return None, None
+    re2 = float(np.mean(((phi_mc[ok] - phi_ref[ok]) / phi_ref[ok]) ** 2))
+    return (1.0 / (tau_s * re2) if re2 > 0 else None), math.sqrt(re2)
+
+
+def load_pulse_reference(path=PULSE_REFERENCE):
+    """The stored expected census flux of the workload at t^n = n dt (cell
+    averages of the semi-analytic pulse, written by
+    tests/golden/make_pulse_reference.py): a function of n giving all cells."""
+    z = np.load(path)
+    lo, hi, vals, I = z["lo"], z["hi"], z["values"], int(z["n_cells"])
+    offs = np.concatenate([[0], np.cumsum(hi - lo)])
+
+    def ref(n):
+        out = np.zeros(I)
+        k = n - 1
+        out[lo[k]:hi[k]] = vals[offs[k]:offs[k + 1]]
+        return out
+
+    return ref, len(lo)
+
+
+def mean_se(xs):
+    xs = [x for x in xs if x is not None]
+    if not xs:
+        return None, None
+    m = statistics.fmean(xs)
+    return m, (statistics.stdev(xs) / math.sqrt(len(xs)) if len(xs) > 1 else None)
 
 
 def run_path(hww, torch, precision, n_particles, seed, warmup, steps, barrier):
@@ -215,6 +272,90 @@ def run_path(hww, torch, precision, n_particles, seed, warmup, steps, barrier):
     batch = p.get_tallies(hww.BATCH_PHI)
     p.close()
     return dict(ms=ms, segments=segs, census=census, counters=cnt, batch=batch, n=n_particles, window=(t0, t1))
+
+
+def run_stepwise(hww, torch, wl, n_steps, deriv=False):
+    """Every step of a run timed on its own (CUDA events around each step on
+    the stream), with the step's statistics and the tracking kernels' time."""
+    p = hww.Problem.from_workload(wl, deriv=deriv) if deriv else hww.Problem.from_workload(wl)
+    p.set_timing(True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps + 1)]
+    t0 = time.time()
+    ev[0].record(stream)
+    stats, track = [], []
+    for n in range(n_steps):
+        before = p.counters()["track_ms"]
+        stats.append(p.run_step())
+        ev[n + 1].record(stream)
+        track.append(p.counters()["track_ms"] - before)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    ms = [ev[n].elapsed_time(ev[n + 1]) for n in range(n_steps)]
+    cnt = p.counters()
+    p.close()
+    return dict(ms=ms, stats=stats, track_ms=track, counters=cnt, window=(t0, t1))
+
+
+def window_summary(run, lo, hi):
+    """Steps lo..hi (1-based, inclusive) of a step-wise run."""
+    ms = run["ms"][lo - 1:hi]
+    segs = sum(s["segments"] for s in run["stats"][lo - 1:hi])
+    return {"steps": "%d..%d" % (lo, hi), "ms_per_step": statistics.fmean(ms),
+            "value": segs / (sum(ms) * 1e-3), "unit": UNIT,
+            "tracking_ms_per_step": statistics.fmean(run["track_ms"][lo - 1:hi])}
+
+
+def run_fom(hww, torch, precision, n_particles, seeds, n_steps, first, ref):
+    """FOM_Error and FOM_sigma of steps first..n_steps, per seed: each step timed
+    on its own (tau of Eqs. FOM_sigma / FOM_error), its census flux compared
+    with the semi-analytic reference at t^n, its batch tallies giving the
+    variance."""
+    per_seed = []
+    for seed in seeds:
+        wl = workloads.plain_at_scale(particles_per_step=n_particles, seed=seed, precision=precision)
+        p = hww.Problem.from_workload(wl)
+        stream = torch.cuda.current_stream()
+        fe, fs, re, rsd, taus = [], [], [], [], []
+        for n in range(1, n_steps + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            p.run_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if n < first:
+                continue
+            tau = e0.elapsed_time(e1) * 1e-3
+            f1, r1 = fom_error(p.get_tallies(hww.CENSUS_PHI), ref(n), tau)
+            f2, r2 = fom_sigma(p.get_tallies(hww.BATCH_PHI), tau)
+            fe.append(f1)
+            re.append(r1)
+            fs.append(f2)
+            rsd.append(r2)
+            taus.append(tau)
+        p.close()
+        per_seed.append(dict(fom_error=statistics.fmean(fe), rel_error=math.sqrt(statistics.fmean([x * x for x in re])),
+                             fom_sigma=statistics.fmean(fs), rsd=math.sqrt(statistics.fmean([x * x for x in rsd])),
+                             tau_ms=1e3 * statistics.fmean(taus)))
+    out = {}
+    for k in ("fom_error", "rel_error", "fom_sigma", "rsd", "tau_ms"):
+        m, se = mean_se([d[k] for d in per_seed])
+        out[k] = m
+        out[k + "_se"] = se
+    out["per_seed"] = per_seed
+    return out
+
+
+def ratio_se(a, sa, b, sb):
+    """a / b and its standard error from the two relative errors."""
+    if not a or not b:
+        return None, None
+    r = a / b
+    rel = math.sqrt(((sa or 0.0) / a) ** 2 + ((sb or 0.0) / b) ** 2)
+    return r, r * rel
 
 
 def run_e2e(hww, torch, precision, n_particles, seed, warmup, steps):
@@ -291,16 +432,18 @@ def run_batch(hww, torch, warmup, steps, tune, alone=True):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    segs = 0
+    segs, census = 0, 0
     for _ in range(steps):
-        segs += b.run_step()["segments"]
+        st = b.run_step()
+        segs += st["segments"]
+        census += st["census"]
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     n = sum(int(w["particles_per_step"]) for w in wls)
     b.close()
     out = {"value": segs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "problems": len(wls),
-           "particles_per_step": n, "tuning": list(best) if best else None,
+           "particles_per_step": n, "census_per_step": census / steps, "tuning": list(best) if best else None,
            "workload": "batched_sweep: 256 slabs [-50,50], cells U[100,2000], particles logU[1e4,1e6], "
                        "Sigma_t U[0.5,5], c U[0.3,0.999], ratio {2,3,5,10}, dt 0.1, FP32 tracking"}
     if alone:
@@ -324,8 +467,10 @@ def run_deriv(hww, torch, n_particles, warmup, steps):
     and per adjoint call."""
     wl = workloads.differentiation(particles_per_step=n_particles)
     p = hww.Problem.from_workload(wl, deriv=True)
+    p.set_timing(True)
     for _ in range(warmup):
         p.run_step()
+    p.reset_counters()
     I = len(wl["edges"]) - 1
     g_mc = torch.ones(I, dtype=torch.float64, device="cuda")
     g_phi = torch.ones(I + 2, dtype=torch.float64, device="cuda")
@@ -335,9 +480,11 @@ def run_deriv(hww, torch, n_particles, warmup, steps):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     torch.cuda.synchronize()
     ev[0].record(stream)
-    segs = 0
+    segs, census = 0, 0
     for _ in range(steps):
-        segs += p.run_step()["segments"]
+        st = p.run_step()
+        segs += st["segments"]
+        census += st["census"]
     ev[1].record(stream)
     ev[2].record(stream)
     for _ in range(steps):
@@ -345,32 +492,90 @@ def run_deriv(hww, torch, n_particles, warmup, steps):
     ev[3].record(stream)
     torch.cuda.synchronize()
     ms, ms_vjp = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    track_ms = p.counters()["track_ms"]
     p.close()
     return {"value": segs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
             "vjp_ms": ms_vjp / steps, "parameters": 2 * int(wl["n_regions"]), "particles_per_step": n_particles,
+            "census_per_step": census / steps, "tracking_ms_per_step": track_ms / steps,
             "workload": "differentiation: shield [0,40] (3 regions), 800 cells, dt 0.1, FP64 with "
                         "derivative tallies for (Sigma_t, c) of each region"}
 
 
-def cpu_oracle_sample(n_particles, max_steps, budget_s):
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    same workload: segments per second over the first steps."""
+def run_shield(hww, torch, n_particles, n_steps):
+    """The heterogeneous shield at its stated size, every step timed."""
+    wl = workloads.shield(particles_per_step=n_particles, n_steps=n_steps, precision="fp32")
+    run = run_stepwise(hww, torch, wl, n_steps)
+    segs = sum(s["segments"] for s in run["stats"])
+    census = [s["census"] for s in run["stats"]]
+    out = {"workload": "shield: [0,10],[10,15],[15,40] mfp, Sigma_t (1,5,0.5), c (0.99,0.5,0.9), reflecting at 0, "
+                       "vacuum at 40, 800 cells, dt 0.1, FP32 tracking / FP64 tallies and LOSM",
+           "particles_per_step": n_particles, "steps": n_steps,
+           "value": segs / (sum(run["ms"]) * 1e-3), "unit": UNIT, "ms_per_step": statistics.fmean(run["ms"]),
+           "early": window_summary(run, 6, min(25, n_steps)),
+           "late": window_summary(run, max(1, n_steps - 19), n_steps),
+           "census_peak": max(census), "census_capacity": run["counters"]["census_capacity"],
+           "queue_capacity": run["counters"]["queue_capacity"], "waves_max": max(s["waves"] for s in run["stats"]),
+           "window": run["window"]}
+    return out, run
+
+
+def roofline_hbm(name, state_bytes, n_start, n_census, track_ms, steps, peak, peak_kind, note=None):
+    """Bank-streaming HBM roofline of the tracking over `steps` steps: the
+    start bank read and the census bank written, state_bytes per particle
+    each (n_start, n_census: totals over the steps), over the tracking
+    launches' time (track_ms: total)."""
+    alg = state_bytes * (n_start + n_census)
+    ach = alg / (track_ms * 1e-3) / 1e9 if track_ms > 0 else None
+    out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": (ach / peak) if ach else None,
+           "kernel": name, "algorithmic_bytes_per_step": alg / steps, "bytes_per_particle": state_bytes,
+           "kernel_ms_per_step": track_ms / steps, "peak_source": peak_kind}
+    if note:
+        out["note"] = note
+    return out
+
+
+def _cpu_worker(args):
+    n_particles, seed, budget_s = args
     import oracle
 
-    wl = workloads.plain_at_scale(particles_per_step=n_particles, seed=1, precision="fp64")
+    wl = workloads.plain_at_scale(particles_per_step=n_particles, seed=seed, precision="fp64")
     o = oracle.problem_from_workload(wl)
-    segs = 0
+    segs, n = 0, 0
     t0 = time.perf_counter()
-    n = 0
-    while n < max_steps:
-        s = o.run_step()
-        segs += s["segments"]
+    while n < 50:
+        segs += o.run_step()["segments"]
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
     o.close()
+    return segs, dt, n
+
+
+def cpu_oracle_sample(n_particles, max_steps, budget_s):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    same workload: segments per second over the first steps."""
+    segs, dt, n = _cpu_worker((n_particles, 1, budget_s))
     return segs / dt, n, dt
+
+
+def cpu_oracle_all_cores(n_particles, budget_s):
+    """The same on every core the process may run on: one oracle process per
+    core (spawned, independent seeds), the whole sample's segments over the
+    slowest process's time."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_cpu_worker, [(n_particles, 1 + k, budget_s) for k in range(cores)])
+    segs = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    steps = min(r[2] for r in res)
+    return segs / dt, cores, dt, steps
 
 
 def main_reference(args):
@@ -393,11 +598,14 @@ def main_reference(args):
     value = segs / dt
     sample = "plain_at_scale physics at %d particles/step (1/%d of the workload), steps %d..%d" % (
         n_ref, 10_000_000 // n_ref, args.warmup + 1, args.warmup + args.steps)
+    workload = WORKLOAD.replace("1e7 particles/step", "%.0e particles/step (a bounded sample of the "
+                                "1e7-particle workload; segments/s does not depend on the count)" % n_ref)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "CPU oracle (plain C, FP64)"},
+        "data": "synthetic", "config": {"workload": workload, "reference": "CPU oracle (plain C, FP64)",
+                                        "particles_per_step": n_ref},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -430,12 +638,38 @@ def main(args):
     if ws > 1:
         # a scaling run times the headline path (and its end-to-end form) on
         # every rank; the secondary legs are single-GPU measurements
-        args.no_fp64 = args.no_batch = args.no_deriv = True
+        args.no_fp64 = args.no_batch = args.no_deriv = args.no_full = args.no_fom = args.no_shield = True
     N = args.particles
+    peak, peak_kind = load_peaks()
+    windows = []
+    out = {}
     with ClockSampler(local) as clk:
         time.sleep(1.5)  # nvidia-smi is sampling by the time the timed steps start
         fast = run_path(hww, torch, "fp32", N, seed, args.warmup, args.steps, barrier)
+        windows.append(fast["window"])
+        if not args.no_full:
+            # the whole run of the workload, every step timed
+            full = run_stepwise(hww, torch, workloads.plain_at_scale(particles_per_step=N, seed=seed,
+                                                                     precision="fp32"), args.full_steps)
+            windows.append(full["window"])
+            segs = sum(s["segments"] for s in full["stats"])
+            out["full_run"] = {"steps": "1..%d" % args.full_steps, "value": segs / (sum(full["ms"]) * 1e-3),
+                               "unit": UNIT, "ms_per_step": statistics.fmean(full["ms"]),
+                               "early": window_summary(full, 6, 25),
+                               "late": window_summary(full, args.full_steps - 19, args.full_steps)}
+        if not args.no_shield:
+            sh, shrun = run_shield(hww, torch, args.shield_particles, args.shield_steps)
+            windows.append(sh.pop("window"))
+            sh["roofline"] = roofline_hbm("track32_kernel", STATE_BYTES["fp32"],
+                                          args.shield_particles * args.shield_steps,
+                                          sum(s["census"] for s in shrun["stats"]), sum(shrun["track_ms"]),
+                                          args.shield_steps, peak, peak_kind)
+            out["shield_1e8"] = sh
     clocks = clk.summary(fast["window"])
+    clocks_all = clk.summary(windows)
+    clk.close()
+    clocks["all_timed_windows"] = {k: clocks_all.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")}
+
     base = run_path(hww, torch, "fp64", N, seed, args.warmup, args.steps, barrier) if not args.no_fp64 else None
 
     red = RankReduce(dist, "cuda")
@@ -444,40 +678,76 @@ def main(args):
     ms = reduce_max(fast["ms"])
     total_segs = reduce_sum(fast["segments"])
     value = total_segs / (ms * 1e-3)
-    out = {}
+    dfma = None
+    if rank == 0 and ws == 1:
+        try:
+            dfma = hww.hww_dfma_rate()
+        except Exception as e:  # the measurement is context only
+            dfma = None
+            out["dfma_error"] = str(e)
     if base is not None:
         ms64 = reduce_max(base["ms"])
         segs64 = reduce_sum(base["segments"])
-        out["fp64_path"] = {"value": segs64 / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps}
-        f32, r32 = fom_sigma(fast["batch"], fast["ms"] * 1e-3 / args.steps)
-        f64, r64 = fom_sigma(base["batch"], base["ms"] * 1e-3 / args.steps)
-        out["fom"] = {"kind": "FOM_sigma (batch variance, B=16) at the last timed step",
-                      "fp32_track": f32, "fp64": f64, "rsd_fp32": r32, "rsd_fp64": r64,
-                      "gain_fp32_over_fp64": (f32 / f64) if (f32 and f64) else None}
+        cnt64 = base["counters"]
+        fp64 = {"value": segs64 / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
+                "roofline": roofline_hbm("track64_kernel", STATE_BYTES["fp64"], N * args.steps, base["census"],
+                                         cnt64["track_ms"], args.steps, peak, peak_kind)}
+        if dfma:
+            fp64["fp64_peak"] = {"value": dfma / 1e12, "unit": "TFLOP/s", "kind": "measured",
+                                 "how": "hww_dfma_rate: the library's own DFMA loop (8 chains per thread, 8 blocks "
+                                        "of 256 per SM), CUDA events"}
+        out["fp64_path"] = fp64
+
+    if not args.no_fom:
+        try:
+            ref, nref = load_pulse_reference()
+            seeds = list(range(1, args.fom_seeds + 1))
+            f32 = run_fom(hww, torch, "fp32", N, seeds, args.fom_steps, 6, ref)
+            f64 = run_fom(hww, torch, "fp64", N, seeds, args.fom_steps, 6, ref)
+            g_err, g_err_se = ratio_se(f32["fom_error"], f32["fom_error_se"], f64["fom_error"], f64["fom_error_se"])
+            g_sig, g_sig_se = ratio_se(f32["fom_sigma"], f32["fom_sigma_se"], f64["fom_sigma"], f64["fom_sigma_se"])
+            out["fom"] = {
+                "kind": "FOM_Error (census flux at t^n against the semi-analytic infinite-medium pulse, Eq. "
+                        "FOM_error) and FOM_sigma (B=16 batch variance of the track-length flux, Eq. FOM_sigma), "
+                        "steps 6..%d, each step timed on its own; mean over %d seeds, _se = seed-to-seed "
+                        "standard error" % (args.fom_steps, len(seeds)),
+                "fp32_track": {k: v for k, v in f32.items() if k != "per_seed"},
+                "fp64": {k: v for k, v in f64.items() if k != "per_seed"},
+                "gain_fom_error_fp32_over_fp64": g_err, "gain_fom_error_se": g_err_se,
+                "gain_fom_sigma_fp32_over_fp64": g_sig, "gain_fom_sigma_se": g_sig_se,
+                "time_ratio_fp64_over_fp32": f64["tau_ms"] / f32["tau_ms"],
+                "rel_error_ratio_fp32_over_fp64": f32["rel_error"] / f64["rel_error"],
+                "rsd_ratio_fp32_over_fp64": f32["rsd"] / f64["rsd"]}
+        except Exception as e:  # the headline stands on its own
+            out["fom"] = {"error": "%s: %s" % (type(e).__name__, e)}
 
     e2e = run_e2e(hww, torch, "fp32", N, seed, args.warmup, args.steps) if not args.no_e2e else None
     if not args.no_batch:
-        out["batched"] = run_batch(hww, torch, args.warmup, args.steps, tune=not args.no_tune,
-                                   alone=not args.no_alone)
+        bt = run_batch(hww, torch, args.warmup, args.steps, tune=not args.no_tune, alone=not args.no_alone)
+        # the batch's tracking waves are not timed apart from its step: the
+        # bank-streaming fraction over the whole step is a lower bound
+        bt["roofline"] = roofline_hbm("track32_kernel_batch (whole batched step)", STATE_BYTES["fp32"],
+                                      bt["particles_per_step"], bt["census_per_step"], bt["ms_per_step"], 1, peak,
+                                      peak_kind, note="denominator: the whole batched step (tracking waves, both "
+                                                      "graphs, host turnarounds), so this is a lower bound")
+        out["batched"] = bt
     if not args.no_deriv:
-        out["differentiation"] = run_deriv(hww, torch, args.deriv_particles, args.warmup, args.steps)
+        dv = run_deriv(hww, torch, args.deriv_particles, args.warmup, args.steps)
+        dv["roofline"] = roofline_hbm("track64_kernel<derivatives>", STATE_BYTES["fp64"] + SCORE_BYTES,
+                                      args.deriv_particles, dv["census_per_step"], dv["tracking_ms_per_step"], 1,
+                                      peak, peak_kind)
+        out["differentiation"] = dv
     e2e_val = reduce_sum(e2e["value"]) if e2e else None
 
-    # roofline of the dominant kernel (tracking), bank-streaming bytes
-    peak, peak_kind = load_peaks()
+    # roofline of the dominant kernel (FP32 tracking), bank-streaming bytes
     cnt = fast["counters"]
     track_ms = cnt["track_ms"]
-    bytes_alg = N * args.steps * BANK_BYTES["fp32"] + fast["census"] * CENSUS_BYTES["fp32"]
-    achieved = (bytes_alg / (track_ms * 1e-3)) / 1e9 if track_ms > 0 else None
-    traffic = TRACK32_DRAM_BYTES_PER_START * N if TRACK32_DRAM_BYTES_PER_START else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "traffic_note": "DRAM bytes of the wave-0 launch per step, scaled by particles from the 4e6 capture",
-            "limiter": "issue/latency (ncu: 35% issue active; stalls wait 29%, long scoreboard 27%, "
-                       "short scoreboard 16%; 5.6% DRAM; 15.6 of 32 lanes active)",
-            "peak_source": peak_kind, "kernel": "track32_kernel",
-            "launches": cnt["track_launches"], "kernel_ms_per_step": track_ms / args.steps,
-            "algorithmic_bytes_per_step": bytes_alg / args.steps}
+    roof = roofline_hbm("track32_kernel", STATE_BYTES["fp32"], N * args.steps, fast["census"], track_ms, args.steps,
+                        peak, peak_kind)
+    roof["launches"] = cnt["track_launches"]
+    roof["traffic"] = TRACK32_DRAM_BYTES_PER_START * N if TRACK32_DRAM_BYTES_PER_START else None
+    roof["traffic_note"] = TRACK32_DRAM_NOTE
+    roof["census_per_step"] = fast["census"] / args.steps
 
     if rank != 0:
         if dist is not None:
@@ -485,10 +755,19 @@ def main(args):
         return 0
     cpu = None
     if ws == 1 and not args.no_cpu:
-        v, nst, dt = cpu_oracle_sample(args.cpu_particles, 50, args.cpu_budget)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        v1, nst, dt1 = cpu_oracle_sample(args.cpu_particles, 50, args.cpu_budget)
+        one = {"value": v1, "cores": 1,
                "sample": "plain_at_scale physics at %d particles/step, steps 1..%d (%.1f s)" % (
-                   args.cpu_particles, nst, dt)}
+                   args.cpu_particles, nst, dt1)}
+        try:
+            va, cores, dta, nsa = cpu_oracle_all_cores(args.cpu_particles, args.cpu_budget)
+            cpu = {"value": va, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "plain_at_scale physics at %d particles/step, one process per core (seeds 1..%d), "
+                             "at least steps 1..%d each (%.1f s)" % (args.cpu_particles, cores, nsa, dta),
+                   "one_core": one}
+        except Exception as e:
+            cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": one["sample"],
+                   "all_cores_error": "%s: %s" % (type(e).__name__, e)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -519,6 +798,11 @@ def parse(argv=None):
     ap.add_argument("--ref-particles", type=int, default=1_000_000)
     ap.add_argument("--cpu-particles", type=int, default=1_000_000)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--full-steps", type=int, default=100)
+    ap.add_argument("--fom-seeds", type=int, default=4)
+    ap.add_argument("--fom-steps", type=int, default=25)
+    ap.add_argument("--shield-particles", type=int, default=100_000_000)
+    ap.add_argument("--shield-steps", type=int, default=200)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -526,6 +810,9 @@ def parse(argv=None):
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-alone", action="store_true")
     ap.add_argument("--no-deriv", action="store_true")
+    ap.add_argument("--no-full", action="store_true")
+    ap.add_argument("--no-fom", action="store_true")
+    ap.add_argument("--no-shield", action="store_true")
     ap.add_argument("--deriv-particles", type=int, default=10_000_000)
     return ap.parse_args(argv)
 

@@ -375,6 +375,14 @@ hww_status hww_losm_solve_noalloc(int32_t n_cells, const double* dx, const doubl
                                   double PL_new, double PR_new, const double* q_old,
                                   const double* q_new, double* phi_new, double* J_new);
 
+/* The current device's FP64 fused multiply-add rate in floating-point
+ * operations per second (two per DFMA), measured by the library's own loop:
+ * 8 independent DFMA chains per thread, `iters` iterations, 8 blocks of 256
+ * threads per SM, timed with CUDA events after a short warm-up.  The paper
+ * has no counterpart: it is the denominator of the FP64 path's ALU
+ * roofline.  Synchronous; allocates one double. */
+hww_status hww_dfma_rate(int64_t iters, double* flops_per_s);
+
 /* Philox4x32-10 of n consecutive counters {c0 + i, c1, c2, c3} under key
  * (k0, k1), computed by the library's device generator; out holds 4 n
  * words (host).  Synchronous.  Used to check the generator. */

@@ -80,7 +80,7 @@ SYMBOLS = ["create_problem", "set_cross_sections", "set_ww_params", "set_ww_cent
            "hww_status_string", "hww_last_error_string", "hww_losm_solve", "hww_philox_block", "hww_set_timing",
            "hww_get_counters", "hww_reset_counters", "create_batch", "batch_problem", "batch_set_tuning",
            "run_batch_step", "batch_member_stats", "destroy_batch", "get_deriv_tallies", "vjp_state_size", "set_ww_updates",
-           "save_vjp_state", "losm_vjp"]
+           "save_vjp_state", "losm_vjp", "hww_dfma_rate"]
 
 
 def library_path() -> str:
@@ -137,6 +137,7 @@ def load(build_if_missing: bool = True):
                                      C.c_int32, C.c_int32, dp, dp, dp, dp, C.c_double, C.c_double,
                                      dp, dp, dp, dp]
         L.hww_philox_block.argtypes = [C.c_uint32] * 6 + [C.c_int64, C.POINTER(C.c_uint32)]
+        L.hww_dfma_rate.argtypes = [C.c_int64, C.POINTER(C.c_double)]
         for name in SYMBOLS:
             f = getattr(L, name)
             if name not in ("destroy_problem", "destroy_batch", "hww_status_string", "hww_last_error_string"):
@@ -180,6 +181,14 @@ def hww_losm_solve(dx, sigma_t, sigma_a, v, dt, theta, bc_left, bc_right, phi_ol
                                _dp(qn) if qn is not None else null, _dp(phi), _dp(J))
     _check(rc, "hww_losm_solve")
     return phi, J
+
+
+def hww_dfma_rate(iters=1 << 14):
+    """The current device's FP64 fused multiply-add rate (FLOP/s), measured by
+    the library's own DFMA loop."""
+    out = C.c_double()
+    _check(load().hww_dfma_rate(int(iters), C.byref(out)), "hww_dfma_rate")
+    return out.value
 
 
 def hww_philox_block(ctr, key, n):

@@ -30,6 +30,7 @@ UNITS = {
     "step.cu": ["-fmad=false"],
     "losm.cu": ["-fmad=false"],
     "noalloc.cu": ["-fmad=false"],
+    "measure.cu": [],
     "track_fp64.cu": ["-fmad=false"],
     "track_fp32.cu": ["-fmad=false"],
 }
