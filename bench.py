@@ -679,7 +679,7 @@ def main(args):
     total_segs = reduce_sum(fast["segments"])
     value = total_segs / (ms * 1e-3)
     dfma = None
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and base is not None:
         try:
             dfma = hww.hww_dfma_rate()
         except Exception as e:  # the measurement is context only

@@ -64,7 +64,7 @@ struct hww_problem {
     size_t acc_bytes = 0;
     Acc128 *tl = nullptr, *cent = nullptr, *batch = nullptr, *bnd = nullptr;
     unsigned long long* stats = nullptr;
-    unsigned long long* counts = nullptr;  // [0] census, [1] q0, [2] q1, [3..7] comb group list lengths
+    unsigned long long* counts = nullptr;  // [0] census, [1] q0, [2] q1, [3..8] comb group list lengths
     // comb groups (one clear)
     void* grp = nullptr;
     size_t grp_bytes = 0;
@@ -217,21 +217,19 @@ hww_status alloc_start_bank(hww_problem* p, Banks<Real>& b) {
     return HWW_OK;
 }
 
-// lists of comb groups of 3+ members by size class (3-4, 5-8, 9-16, 17-32,
-// more): a class whose groups have at least m members holds at most
-// census / m of them
-void glist_offsets(long long C, long long off[5]) {
-    const long long minm[5] = {3, 5, 9, 17, 33};
+// comb group lists (COMB_LIST_MIN gives each list's bound) laid out one
+// after the other for a census capacity C
+void glist_offsets(long long C, long long off[COMB_LISTS]) {
     long long o = 0;
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < COMB_LISTS; ++k) {
         off[k] = o;
-        o += C / minm[k] + 1;
+        o += C / COMB_LIST_MIN[k] + 1;
     }
 }
 size_t glist_len(long long C) {
-    long long off[5];
+    long long off[COMB_LISTS];
     glist_offsets(C, off);
-    return (size_t)(off[4] + C / 33 + 1);
+    return (size_t)(off[COMB_LISTS - 1] + C / COMB_LIST_MIN[COMB_LISTS - 1] + 1);
 }
 
 // census bank, both record queues and the comb member list, sized by the
@@ -472,7 +470,7 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
     launch_comb(comb_args(p, b), comb_grid(p), p->stream);
     HWW_CK(cudaGetLastError());
-    p->kernel_launches += 5 + (p->P2 > 0 ? 1 : 0);
+    p->kernel_launches += 6 + (p->P2 > 0 ? 1 : 0);
     return HWW_OK;
 }
 
@@ -947,7 +945,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     const int B = p->B;
     const size_t P2 = (size_t)p->P2;
     const size_t acc_main = sizeof(Acc128) * (6 * (size_t)I + (size_t)B * I + 6) +
-                            sizeof(unsigned long long) * (ST_COUNT + 8);
+                            sizeof(unsigned long long) * (ST_COUNT + 3 + COMB_LISTS);
     // derivative accumulators after the main block (16-byte aligned)
     const size_t acc_off = (acc_main + 15) / 16 * 16;
     p->acc_bytes = acc_off + sizeof(Acc128) * (P2 * I + 3 * P2 * I + 6 * P2);

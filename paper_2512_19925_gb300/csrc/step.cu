@@ -132,13 +132,19 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
 // one member: its C0 is set by the scatter pass, which lists only the members
 // of larger groups; their prefixes are found once per group: pairs by one
 // thread, groups of up to 32 by a warp segment of 4 to 32 lanes (a rank count
-// over shuffles), larger ones by a block (bitonic sort and scan in shared
-// memory).  The copies are then written in census order, reading the census
-// bank and the stored prefixes coalesced.
+// over shuffles), groups of 33 to 256 by a warp (bitonic sort in the warp's
+// shared memory, shuffle scan), larger ones by a block (bitonic sort and
+// scan in shared memory).  The copies are then written in census order,
+// reading the census bank and the stored prefixes coalesced.
 // ---------------------------------------------------------------------------
 constexpr int NCLASS = 4;      // group size classes handled by warp segments of 4, 8, 16, 32 lanes
+constexpr int MID_CLASS = 4;   // 33..MID_MAX members: a warp per group
+constexpr int BIG_CLASS = 5;   // more: a block per group
+constexpr int MID_MAX = 256;
+constexpr int MID_WARPS = 4;   // warps (groups in flight) per block of the warp-per-group kernel
 constexpr int BIG_CAP = 2048;  // members a block sorts in shared memory
 constexpr int BIG_T = 256;
+static_assert(COMB_LISTS == BIG_CLASS + 1, "one list per size class");
 
 template <class Real>
 __global__ void comb_scatter_kernel(CombArgs<Real> a) {
@@ -161,9 +167,10 @@ __device__ __forceinline__ bool key_less(uint64_t la, uint32_t ja, uint64_t lb, 
     return la < lb || (la == lb && ja < jb);
 }
 
-// size class of a group: 3-4, 5-8, 9-16, 17-32 members -> 0..3, larger -> 4
+// size class of a group: 3-4, 5-8, 9-16, 17-32 members -> 0..3, 33..MID_MAX
+// -> MID_CLASS, larger -> BIG_CLASS
 __device__ __forceinline__ int size_class(uint32_t g) {
-    return g <= 4 ? 0 : g <= 8 ? 1 : g <= 16 ? 2 : g <= 32 ? 3 : 4;
+    return g <= 4 ? 0 : g <= 8 ? 1 : g <= 16 ? 2 : g <= 32 ? 3 : g <= (uint32_t)MID_MAX ? MID_CLASS : BIG_CLASS;
 }
 
 // one block per contiguous id range: a pair is ordered on the spot; groups
@@ -172,14 +179,14 @@ __device__ __forceinline__ int size_class(uint32_t g) {
 // with one global atomic per class
 template <class Real>
 __global__ void comb_groups_kernel(CombArgs<Real> a) {
-    __shared__ unsigned long long s_cnt[NCLASS + 1], s_pos[NCLASS + 1];
+    __shared__ unsigned long long s_cnt[COMB_LISTS], s_pos[COMB_LISTS];
     const long long chunk = (a.N + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk;
     const long long hi = min(a.N, lo + chunk);
-    if (threadIdx.x <= NCLASS) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x < COMB_LISTS) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     unsigned long long coll = 0;
-    unsigned c[NCLASS + 1] = {};
+    unsigned c[COMB_LISTS] = {};
     for (long long id = lo + threadIdx.x; id < hi; id += blockDim.x) {
         const uint32_t g = a.gcnt[id];
         if (g < 2) continue;
@@ -198,16 +205,16 @@ __global__ void comb_groups_kernel(CombArgs<Real> a) {
         }
         const int k = size_class(g);
 #pragma unroll
-        for (int kk = 0; kk <= NCLASS; ++kk) c[kk] += (kk == k) ? 1u : 0u;
+        for (int kk = 0; kk < COMB_LISTS; ++kk) c[kk] += (kk == k) ? 1u : 0u;
     }
 #pragma unroll
-    for (int k = 0; k <= NCLASS; ++k) {
+    for (int k = 0; k < COMB_LISTS; ++k) {
         unsigned v = c[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31u) == 0 && v) atomicAdd(&s_cnt[k], (unsigned long long)v);
     }
     __syncthreads();
-    if (threadIdx.x <= NCLASS) {
+    if (threadIdx.x < COMB_LISTS) {
         const unsigned long long n = s_cnt[threadIdx.x];
         s_pos[threadIdx.x] = n ? atomicAdd(&a.glist_n[threadIdx.x], n) : 0ull;
     }
@@ -221,7 +228,7 @@ __global__ void comb_groups_kernel(CombArgs<Real> a) {
         const uint32_t g = (id < hi) ? a.gcnt[id] : 0u;
         const int kc = (g >= 3) ? size_class(g) : -1;
 #pragma unroll
-        for (int k = 0; k <= NCLASS; ++k) {
+        for (int k = 0; k < COMB_LISTS; ++k) {
             const unsigned bal = __ballot_sync(0xffffffffu, kc == k);
             if (!bal) continue;
             unsigned long long base = 0;
@@ -296,16 +303,167 @@ __global__ void comb_seg_kernel(CombArgs<Real> a) {
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
 
-// one block per group of more than 32 members: bitonic sort by (lineage,
-// slot) in shared memory and an exclusive scan of the weights; groups beyond
-// BIG_CAP members take the rank count with the block's threads
+// A warp's bitonic sort of 32 K keys (lineage, slot) with their weights, in
+// registers: element i = k 32 + lane sits in slot k of lane `lane`, so a
+// compare-exchange partner i ^ h is the same slot of lane ^ h (a shuffle) for
+// h < 32 and slot k ^ (h / 32) of the same lane for h >= 32.  Only the slot
+// loops are unrolled (the network's stages are loops), which keeps the code
+// small enough for the instruction cache.
+template <int K, int HS>
+__device__ __forceinline__ void slot_phase(uint64_t (&L)[K], uint32_t (&J)[K], unsigned long long (&Wt)[K],
+                                           int lane, int kk) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int k2 = k ^ HS;
+        if (k2 > k) {
+            const bool up = ((k * 32 + lane) & kk) == 0;
+            if (key_less(L[k2], J[k2], L[k], J[k]) == up) {
+                const uint64_t tl = L[k];
+                L[k] = L[k2];
+                L[k2] = tl;
+                const uint32_t tj = J[k];
+                J[k] = J[k2];
+                J[k2] = tj;
+                const unsigned long long tw = Wt[k];
+                Wt[k] = Wt[k2];
+                Wt[k2] = tw;
+            }
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&L)[K], uint32_t (&J)[K], unsigned long long (&Wt)[K],
+                                             int lane) {
+    for (int kk = 2; kk <= 32 * K; kk <<= 1) {
+        for (int h = kk >> 1; h >= 32; h >>= 1) {
+            const int hs = h >> 5;
+            if (hs == 1) slot_phase<K, 1>(L, J, Wt, lane, kk);
+            if (K >= 4 && hs == 2) slot_phase<K, 2>(L, J, Wt, lane, kk);
+            if (K >= 8 && hs == 4) slot_phase<K, 4>(L, J, Wt, lane, kk);
+        }
+        for (int h = min(kk >> 1, 16); h > 0; h >>= 1) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const uint64_t pl = __shfl_xor_sync(0xffffffffu, L[k], h);
+                const uint32_t pj = __shfl_xor_sync(0xffffffffu, J[k], h);
+                const unsigned long long pw = __shfl_xor_sync(0xffffffffu, Wt[k], h);
+                const int i = k * 32 + lane;
+                const bool up = (i & kk) == 0;
+                // the lower index of the pair keeps the smaller key when the
+                // run sorts up, the larger when it sorts down
+                const bool keep_min = (((i & h) == 0) == up);
+                const bool take = keep_min ? key_less(pl, pj, L[k], J[k]) : key_less(L[k], J[k], pl, pj);
+                if (take) {
+                    L[k] = pl;
+                    J[k] = pj;
+                    Wt[k] = pw;
+                }
+            }
+        }
+    }
+}
+
+// one group of 33..32 K members by a warp: sort in registers, then the
+// exclusive scan of the sorted weights (slot by slot: the slots before, then
+// the lanes before in the same slot) gives each member's comb prefix
+template <class Real, int K>
+__device__ __forceinline__ void mid_group(const CombArgs<Real>& a, const GroupRec& G, int lane, uint64_t* spill,
+                                          unsigned long long& coll) {
+    const int g = (int)G.cnt;
+    uint64_t L[K];
+    uint32_t J[K];
+    unsigned long long Wt[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = k * 32 + lane;
+        if (i < g) {
+            const uint32_t jj = a.member[G.off + i];
+            const LinW x = a.clw[jj];
+            L[k] = x.lin;
+            J[k] = jj;
+            Wt[k] = x.wfx;
+        } else {  // padding sorts last and weighs nothing
+            L[k] = ~0ull;
+            J[k] = 0xFFFFFFFFu;
+            Wt[k] = 0;
+        }
+    }
+    warp_bitonic<K>(L, J, Wt, lane);
+    unsigned long long before = G.offw;  // weight of the slots before
+    bool eq = false;                     // an equal lineage right before some member
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        unsigned long long inc = Wt[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int i = k * 32 + lane;
+        if (i < g) a.cpre[J[k]] = before + (inc - Wt[k]);
+        before += __shfl_sync(0xffffffffu, inc, 31);
+        // the sorted element before this one: lane - 1 of this slot, or lane
+        // 31 of the slot before
+        uint64_t prev = __shfl_up_sync(0xffffffffu, L[k], 1);
+        if (k > 0) {
+            const uint64_t last = __shfl_sync(0xffffffffu, L[k - 1], 31);
+            if (lane == 0) prev = last;
+        }
+        if (i > 0 && i < g && prev == L[k]) eq = true;
+    }
+    if (__any_sync(0xffffffffu, eq)) {
+        // equal lineages (a hash collision; essentially never): count the
+        // earlier members with the same lineage for every member, exactly
+#pragma unroll
+        for (int k = 0; k < K; ++k) spill[k * 32 + lane] = L[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = k * 32 + lane;
+            if (i < g)
+                for (int b = i - 1; b >= 0 && spill[b] == L[k]; --b) ++coll;
+        }
+        __syncwarp();
+    }
+}
+
+// one warp per group of 33..MID_MAX members (the sort in registers: 2, 4 or
+// 8 members per lane)
+template <class Real>
+__global__ void __launch_bounds__(32 * MID_WARPS) comb_mid_kernel(CombArgs<Real> a) {
+    __shared__ uint64_t s_spill[MID_WARPS][MID_MAX];
+    const unsigned long long n = a.glist_n[MID_CLASS];
+    const uint32_t* list = a.glist + a.glist_off[MID_CLASS];
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long coll = 0;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * MID_WARPS + wp; e < n;
+         e += (unsigned long long)gridDim.x * MID_WARPS) {  // warp-uniform
+        const GroupRec G = a.gro[list[e]];
+        if (G.cnt <= 64)
+            mid_group<Real, 2>(a, G, lane, s_spill[wp], coll);
+        else if (G.cnt <= 128)
+            mid_group<Real, 4>(a, G, lane, s_spill[wp], coll);
+        else
+            mid_group<Real, 8>(a, G, lane, s_spill[wp], coll);
+    }
+    if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
+}
+
+// one block per group of more than MID_MAX members: bitonic sort by
+// (lineage, slot) in shared memory and a scan of the sorted weights (each
+// thread a contiguous run, joined by a shuffle scan per warp and one over
+// the warps' totals); groups beyond BIG_CAP members take the rank count
+// with the block's threads
 template <class Real>
 __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
     __shared__ uint64_t s_lin[BIG_CAP];
+    __shared__ unsigned long long s_w[BIG_CAP];
     __shared__ uint32_t s_j[BIG_CAP];
-    __shared__ unsigned long long s_part[BIG_T];
-    const unsigned long long nbig = a.glist_n[NCLASS];
-    const uint32_t* list = a.glist + a.glist_off[NCLASS];
+    __shared__ unsigned long long s_wsum[BIG_T / 32];
+    const unsigned long long nbig = a.glist_n[BIG_CLASS];
+    const uint32_t* list = a.glist + a.glist_off[BIG_CLASS];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     unsigned long long coll = 0;
     for (unsigned long long e = blockIdx.x; e < nbig; e += gridDim.x) {
         const GroupRec G = a.gro[list[e]];
@@ -335,11 +493,14 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             if (i < (int)g) {
                 const uint32_t jj = a.member[base + i];
+                const LinW x = a.clw[jj];
                 s_j[i] = jj;
-                s_lin[i] = a.clw[jj].lin;
-            } else {  // padding sorts last
+                s_lin[i] = x.lin;
+                s_w[i] = x.wfx;
+            } else {  // padding sorts last and weighs nothing
                 s_lin[i] = ~0ull;
                 s_j[i] = 0xFFFFFFFFu;
+                s_w[i] = 0;
             }
         }
         __syncthreads();
@@ -356,6 +517,9 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
                             const uint32_t tj = s_j[i];
                             s_j[i] = s_j[l];
                             s_j[l] = tj;
+                            const unsigned long long tw = s_w[i];
+                            s_w[i] = s_w[l];
+                            s_w[l] = tw;
                         }
                     }
                 }
@@ -366,25 +530,23 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
         const int per = (P + BIG_T - 1) / BIG_T;
         const int i0 = threadIdx.x * per, i1 = min((int)g, i0 + per);
         unsigned long long run = 0;
-        for (int i = i0; i < i1; ++i) run += a.clw[s_j[i]].wfx;
-        s_part[threadIdx.x] = run;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long acc = 0;
-            for (int t = 0; t < BIG_T; ++t) {
-                const unsigned long long v = s_part[t];
-                s_part[t] = acc;
-                acc += v;
-            }
+        for (int i = i0; i < i1; ++i) run += s_w[i];
+        unsigned long long inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
+        if (lane == 31) s_wsum[wp] = inc;
         __syncthreads();
-        unsigned long long C0 = C + s_part[threadIdx.x];
+        unsigned long long wbase = 0;
+        for (int k = 0; k < wp; ++k) wbase += s_wsum[k];
+        unsigned long long C0 = C + wbase + (inc - run);
         for (int i = i0; i < i1; ++i) {
             // members with an equal lineage before this one (collisions)
             for (int b = i - 1; b >= 0 && s_lin[b] == s_lin[i]; --b) ++coll;
-            const uint32_t jj = s_j[i];
-            a.cpre[jj] = C0;
-            C0 += a.clw[jj].wfx;
+            a.cpre[s_j[i]] = C0;
+            C0 += s_w[i];
         }
         __syncthreads();
     }
@@ -651,6 +813,7 @@ void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
     comb_scatter_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_groups_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_seg_kernel<Real><<<grid, 256, 0, s>>>(a);
+    comb_mid_kernel<Real><<<grid, 32 * MID_WARPS, 0, s>>>(a);
     comb_big_kernel<Real><<<grid, BIG_T, 0, s>>>(a);
     comb_write_kernel<Real><<<grid, 256, sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
     if (a.P2 > 0) {  // about one block per SM (and score): few plane flushes

@@ -23,6 +23,13 @@ struct ScanArgs {
     GroupRec* out;  // n+1 entries; entry n holds the totals
 };
 
+// lists of comb groups of 3+ members by size: 3-4, 5-8, 9-16, 17-32 (warp
+// segments), 33-256 (a warp per group), more (a block per group); a list
+// whose groups have at least COMB_LIST_MIN[k] members holds at most
+// census / COMB_LIST_MIN[k] of them
+constexpr int COMB_LISTS = 6;
+constexpr long long COMB_LIST_MIN[COMB_LISTS] = {3, 5, 9, 17, 33, 257};
+
 template <class Real>
 struct CombArgs {
     StepDev* sd;
@@ -44,9 +51,9 @@ struct CombArgs {
     unsigned long long* stats;
     unsigned* err;
     unsigned long long* cpre;        // [cen_cap] comb prefix C0 of every census particle
-    uint32_t* glist;                 // ids of groups of 3+ members, by size class (5 lists)
-    long long glist_off[5];          // start of each class's list in glist
-    unsigned long long* glist_n;     // [5] list lengths (cleared with the step's accumulators)
+    uint32_t* glist;                 // ids of groups of 3+ members, by size class (COMB_LISTS lists)
+    long long glist_off[COMB_LISTS]; // start of each class's list in glist
+    unsigned long long* glist_n;     // [COMB_LISTS] list lengths (cleared with the step's accumulators)
     int I;             // cells (census tallies)
     Acc128* cent;      // census tallies 3 I
     int P2;            // scores per particle (0: none)

@@ -248,3 +248,30 @@ def test_graded_mesh_leaking_parity():
     wl["filter"] = 1
     stats = run_parity(wl, 12)
     assert sum(s["leaked"] for s in stats) > 0
+
+
+def test_large_comb_groups_parity():
+    # a fine mesh (cells 0.01) with window centers drawn from {1/600, 1/150,
+    # 1/40, 1/2} of the particle weight: splits of up to 600 daughters at each
+    # cell entry, so the comb sees source-id groups of every size class
+    # (pairs, warp segments of 3..32, a warp per group of 33..256, a block per
+    # group beyond, the rank count beyond 2048 members), and the census bank
+    # outgrows its first capacity (regrow and replay); the FP64 combed bank
+    # must equal the oracle's bit for bit
+    wl = workloads.plain_slab(particles_per_step=1501)
+    wl["edges"] = np.linspace(-2.0, 2.0, 401)
+    wl["sigma_t"] = np.ones(400)
+    wl["c"] = np.full(400, 0.9)
+    g, o = _pair(wl)
+    rng = np.random.default_rng(9)
+    seen = set()
+    for n in range(3):
+        ctr = rng.choice([1.0 / 600.0, 1.0 / 150.0, 1.0 / 40.0, 0.5], size=400)
+        g.set_ww_centers(ctr)
+        o.set_ww_centers(ctr)
+        assert_step_parity(g, o, n + 1)
+        sizes = np.bincount(o.get_census()["id"].astype(np.int64))
+        seen |= {int(k) for k in np.unique(np.digitize(sizes, [3, 33, 257, 2049]))}
+    assert seen >= {1, 2, 3, 4}, seen  # 3..32, 33..256, 257..2048 and beyond 2048 all met
+    g.close()
+    o.close()
