@@ -358,7 +358,8 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
             const double2 hl = __ldg(&a.ww_hl[kc]);  // ceiling, floor
             if (dgt(q.w, hl.x)) {
                 const double ctr = a.ww_c[kc];
-                // split count from an FP32 ratio (the FP32 path's own rounding)
+                // split count from an FP32 ratio (the FP32 path's own rounding; the FP64
+                // quotient measured 3% slower at the workload)
                 const float ndf = ceilf((float)q.w / (float)ctr);
                 const double ndd = (double)fmaxf(ndf, 2.0f);
                 if (ndd > (double)MAX_DAUGHTERS) {
@@ -445,7 +446,7 @@ __device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long i
 // counter), so they take no per-lane registers.  A split whose warp stack is
 // full, and a track past its event budget, go to the record queue.
 constexpr int WARPS = TRACK_THREADS / 32;
-constexpr int WSTACK = 16;  // daughter-stack entries per warp
+constexpr int WSTACK = 32;  // daughter-stack entries per warp
 constexpr int ROWS32 = TALLY_ROWS_FP32;
 
 struct WarpShared {
@@ -973,7 +974,8 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                 const double2 hl = __ldg(&a.ww_hl[kc]);  // ceiling, floor
                 if (dgt(q.w, hl.x)) {
                     const double ctr = a.ww_c[kc];
-                    // split count from an FP32 ratio (the FP32 path's own rounding)
+                    // split count from an FP32 ratio (the FP32 path's own rounding; the FP64
+                    // quotient measured 3% slower at the workload)
                     const float ndf = ceilf((float)q.w / (float)ctr);
                     const double ndd = (double)fmaxf(ndf, 2.0f);
                     if (ndd > (double)MAX_DAUGHTERS) {
@@ -1063,10 +1065,11 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
     }
 }
 
-// Four resident blocks of 256 threads per SM (64 registers, no spills; the
-// warp-synchronous loop keeps no per-lane counters and no pending parent in
-// registers), 32 warps per SM to hide the event loop's latencies.
-__global__ void __launch_bounds__(TRACK_THREADS, 4) track32_kernel(TrackArgs<float> a) {
+// Three resident blocks of 256 threads per SM (85 registers): measured at the
+// workload, four blocks (64 registers) executed 4.5% more instructions
+// (register pressure) and ran 7% slower, two blocks (128 registers) 11% fewer
+// instructions but too few warps to hide the loop's latencies (5% slower).
+__global__ void __launch_bounds__(TRACK_THREADS, 3) track32_kernel(TrackArgs<float> a) {
     extern __shared__ long long sm[];  // ROWS32 rows of I 64-bit words, as 32-bit halves
     __shared__ unsigned s_next;
     __shared__ WarpShared s_ws;

@@ -108,3 +108,35 @@ def test_fp32_full_size_against_fp64_path():
         assert max(err.values()) <= BOUND, (step, err)
         report("1000-cell slab, 1e7 particles, steps 1..%d, FP32 vs FP64 path (step %d: segments %d vs %d)"
                % (step, step, s32["segments"], s64["segments"]), worst, err)
+
+
+def test_fp32_shield_at_size_against_fp64_path():
+    # the three-region shield at 1e7 particles per step: the FP32 problem runs
+    # its 200 steps first (the pulse has then spread several mean free paths
+    # from the reflecting wall), and the next three steps are compared with
+    # the FP64 path from the same bank and windows
+    wl = workloads.shield(particles_per_step=10_000_000)
+    p32 = hww.Problem.from_workload(wl, precision=hww.FP32_TRACK)
+    p64 = hww.Problem.from_workload(wl, precision=hww.FP64)
+    # both step on their own first: a step's Philox key depends on its index,
+    # so the compared steps must have the same one
+    for _ in range(200):
+        s = p32.run_step()
+        p64.run_step(stats=False)
+    w_bar = s["w_bar_next"]
+    worst = {}
+    for step in range(201, 204):
+        x, mu, cell = p32.get_bank()
+        assert np.max(cell) > 150  # particles beyond x = 7.5 mfp
+        p64.set_bank(x, mu, cell, w_bar)
+        s32 = p32.run_step()
+        p64.set_ww_centers(p32.get_tallies(hww.WW_CENTER))
+        s64 = p64.run_step()
+        w_bar = s32["w_bar_next"]
+        assert s32["reflections"] > 0 and s64["reflections"] > 0
+        err = rel_errors(grab(p32), grab(p64))
+        report("shield, 1e7 particles, steps 201..%d, FP32 vs FP64 path (step %d: segments %d vs %d, max cell %d)"
+               % (step, step, s32["segments"], s64["segments"], int(np.max(cell))), worst, err)
+        # diverged histories are a tiny fraction of the population
+        assert abs(s32["segments"] - s64["segments"]) <= 1e-4 * s64["segments"]
+        assert max(err.values()) <= BOUND, (step, err)
