@@ -432,11 +432,13 @@ def run_batch(hww, torch, warmup, steps, tune, alone=True):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    segs, census = 0, 0
+    segs, census, replays, grows = 0, 0, 0, 0
     for _ in range(steps):
         st = b.run_step()
         segs += st["segments"]
         census += st["census"]
+        replays += st["member_replays"]
+        grows += st["member_grows"]
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -444,6 +446,7 @@ def run_batch(hww, torch, warmup, steps, tune, alone=True):
     b.close()
     out = {"value": segs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "problems": len(wls),
            "particles_per_step": n, "census_per_step": census / steps, "tuning": list(best) if best else None,
+           "member_replays_in_timed_steps": replays, "member_grows_in_timed_steps": grows,
            "workload": "batched_sweep: 256 slabs [-50,50], cells U[100,2000], particles logU[1e4,1e6], "
                        "Sigma_t U[0.5,5], c U[0.3,0.999], ratio {2,3,5,10}, dt 0.1, FP32 tracking"}
     if alone:

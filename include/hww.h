@@ -284,6 +284,8 @@ typedef struct {
     int64_t problems, segments, census, daughters, roulette_kills, absorbed, leaked;
     int32_t waves;
     int32_t status;   /* worst hww_status over the members */
+    int32_t member_replays;  /* members tracked again on their own after an overflow, this step */
+    int32_t member_grows;    /* members whose buffers grew ahead of demand after this step */
 } hww_batch_stats;
 
 /* Create n problems (n <= 1024) from descs (all with the same precision and
@@ -297,11 +299,14 @@ hww_status batch_problem(hww_batch* b, int32_t i, hww_problem** out);
  * (>= 1) of the batched tracking launches; results do not depend on them. */
 hww_status batch_set_tuning(hww_batch* b, int32_t tile, int32_t emax);
 /* Advance every member by one time step; stats (nullable) synchronizes.
- * As in run_step the host waits for the tracking waves; if any member's
- * census bank or record queue overflowed, that member's buffers grow and the
- * whole batch is tracked again (HWW_ERR_BANK_OVERFLOW after 12 regrowths).
- * HWW_ERR_STATE when a member lacks cross sections or window parameters, or
- * has in-step window updates. */
+ * As in run_step the host waits for the tracking waves.  A member whose
+ * census bank or record queue overflowed gets larger buffers and is tracked
+ * again on its own through the single-problem path (same result as a batch
+ * that had the room; after 12 regrowths its status reports the overflow);
+ * the other members' tracking stands.  A member whose census or record
+ * count came within 60% of its capacity gets at least twice the capacity
+ * after the step's comb.  HWW_ERR_STATE when a member lacks cross sections or
+ * window parameters, or has in-step window updates. */
 hww_status run_batch_step(hww_batch* b, hww_batch_stats* stats);
 /* Counts of member i's last step (synchronizes). */
 hww_status batch_member_stats(hww_batch* b, int32_t i, hww_step_stats* stats);

@@ -63,7 +63,8 @@ class Counters(C.Structure):
 class BatchStats(C.Structure):
     _fields_ = [("problems", C.c_int64), ("segments", C.c_int64), ("census", C.c_int64), ("daughters", C.c_int64),
                 ("roulette_kills", C.c_int64), ("absorbed", C.c_int64), ("leaked", C.c_int64),
-                ("waves", C.c_int32), ("status", C.c_int32)]
+                ("waves", C.c_int32), ("status", C.c_int32), ("member_replays", C.c_int32),
+                ("member_grows", C.c_int32)]
 
 
 class HWWError(RuntimeError):
@@ -450,7 +451,7 @@ def _desc_from_workload(wl, precision=None):
     d = ProblemDesc(edges.size - 1, _dp(edges), float(wl["v"]), float(wl["dt"]), int(wl["bc_left"]),
                     int(wl["bc_right"]), float(wl["src_x"]), int(wl["particles_per_step"]), int(wl["seed"]),
                     int(prec), float(wl.get("theta", 0.5)), int(wl.get("filter", 0)), int(wl.get("filter_k", 3)),
-                    int(wl.get("n_var_batches", 16)), 0, 0, None, 0)
+                    int(wl.get("n_var_batches", 16)), 0, int(wl.get("bank_capacity", 0)), None, 0)
     return d, edges
 
 

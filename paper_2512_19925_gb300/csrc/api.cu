@@ -847,6 +847,32 @@ hww_status track_step(hww_problem* p, Banks<Real>& b) {
     return HWW_OK;
 }
 
+// The tracking of a step, replayed from its start with larger buffers when a
+// census bank or record queue overflowed (the start bank and the closure
+// vectors are untouched until the post stage, so a replay is bit-identical
+// to a run that had the room from the beginning).  After MAX_REGROW regrowths
+// the step goes on with the overflow flagged in its status.
+hww_status track_with_regrow(hww_problem* p) {
+    for (int attempt = 0;; ++attempt) {
+        hww_status s = stage_pre(p);
+        if (s) return s;
+        p->q_peak = 0;
+        s = p->fp32 ? track_step(p, p->b32) : track_step(p, p->b64);
+        if (s) return s;
+        unsigned e = 0;
+        unsigned long long ncen = 0;
+        HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaMemcpyAsync(&ncen, p->counts, sizeof(ncen), cudaMemcpyDeviceToHost, p->stream));
+        HWW_CK(cudaStreamSynchronize(p->stream));
+        if (!(e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW)) || attempt >= MAX_REGROW) return HWW_OK;
+        s = regrow_banks(p, (long long)ncen, p->q_peak);
+        if (s) return s;
+        const unsigned keep = e & ~(unsigned)(ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW);
+        HWW_CK(cudaMemcpyAsync(p->err, &keep, sizeof(unsigned), cudaMemcpyHostToDevice, p->stream));
+        HWW_CK(cudaStreamSynchronize(p->stream));
+    }
+}
+
 hww_status read_stats(hww_problem* p, hww_step_stats* st) {
     unsigned long long h[ST_COUNT];
     StepDev sdh;
@@ -1159,29 +1185,10 @@ hww_status run_step(hww_problem* p, hww_step_stats* st) {
     if (!p) return HWW_ERR_ARG;
     if (!p->xs_set || !p->ww_set) return HWW_ERR_STATE;
     HWW_CK(cudaSetDevice(p->device));
-    // Tracking.  A census or queue overflow leaves the start bank and the
-    // closure vectors untouched, so the step is replayed from the start with
-    // larger buffers; the replay is bit-identical to a run that had the room
-    // from the beginning.
-    hww_status s = HWW_OK;
-    for (int attempt = 0;; ++attempt) {
-        s = stage_pre(p);
-        if (s) return s;
-        p->q_peak = 0;
-        s = p->fp32 ? track_step(p, p->b32) : track_step(p, p->b64);
-        if (s) return s;
-        unsigned e = 0;
-        unsigned long long ncen = 0;
-        HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
-        HWW_CK(cudaMemcpyAsync(&ncen, p->counts, sizeof(ncen), cudaMemcpyDeviceToHost, p->stream));
-        HWW_CK(cudaStreamSynchronize(p->stream));
-        if (!(e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW)) || attempt >= MAX_REGROW) break;
-        s = regrow_banks(p, (long long)ncen, p->q_peak);
-        if (s) return s;
-        const unsigned keep = e & ~(unsigned)(ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW);
-        HWW_CK(cudaMemcpyAsync(p->err, &keep, sizeof(unsigned), cudaMemcpyHostToDevice, p->stream));
-        HWW_CK(cudaStreamSynchronize(p->stream));
-    }
+    // Tracking (replayed from the step's start with larger buffers on an
+    // overflow)
+    hww_status s = track_with_regrow(p);
+    if (s) return s;
     s = stage_post(p);
     if (s) return s;
     p->cur ^= 1;
@@ -1586,6 +1593,8 @@ struct hww_batch {
     unsigned long long* d_total = nullptr;
     unsigned* d_errs = nullptr;
     unsigned long long* d_qpeak = nullptr;  // per member: largest record count of a wave
+    unsigned long long* d_ncen = nullptr;   // per member: census count after the last wave
+    unsigned long long* h_ncen = nullptr;   // pinned
     unsigned long long* h_total = nullptr;  // pinned
     unsigned* h_errs = nullptr;             // pinned
     unsigned long long* h_qpeak = nullptr;  // pinned
@@ -1595,6 +1604,8 @@ struct hww_batch {
     unsigned long long* h_gather = nullptr;  // pinned
     int gathered = 0;                        // h_gather holds the last step
     int last_waves = 0;
+    int step_replays = 0;                    // members tracked again alone after an overflow (last step)
+    int step_grows = 0;                      // members grown ahead of demand (last step)
 };
 
 namespace {
@@ -1624,7 +1635,7 @@ __global__ void batch_plan_kernel(const TrackArgs<Real>* args, int P, int tile, 
 
 template <class Real>
 __global__ void batch_total_kernel(const TrackArgs<Real>* args, int P, unsigned long long* total, unsigned* errs,
-                                   unsigned long long* qpeak) {
+                                   unsigned long long* qpeak, unsigned long long* ncen) {
     __shared__ unsigned long long s[256];
     unsigned long long acc = 0;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
@@ -1632,6 +1643,7 @@ __global__ void batch_total_kernel(const TrackArgs<Real>* args, int P, unsigned 
         acc += c;
         errs[p] = *args[p].err;
         if (c > qpeak[p]) qpeak[p] = c;
+        ncen[p] = *args[p].cen.count;
     }
     s[threadIdx.x] = acc;
     __syncthreads();
@@ -1749,7 +1761,8 @@ hww_status batch_waves(hww_batch* b) {
             launch_track_batch_fp32((const TrackArgs<float>*)args, plan, b->grid, TRACK_BLOCK, b->smem, b->stream);
         else
             launch_track_batch_fp64((const TrackArgs<double>*)args, plan, b->grid, TRACK_BLOCK, b->smem, b->stream);
-        batch_total_kernel<Real><<<1, 256, 0, b->stream>>>(args, b->P, b->d_total, b->d_errs, b->d_qpeak);
+        batch_total_kernel<Real><<<1, 256, 0, b->stream>>>(args, b->P, b->d_total, b->d_errs, b->d_qpeak,
+                                                           b->d_ncen);
         HWW_CK(cudaGetLastError());
         ++waves;
         HWW_CK(cudaMemcpyAsync(b->h_total, b->d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
@@ -1779,6 +1792,8 @@ void destroy_batch(hww_batch* b) {
     if (b->d_total) cudaFree(b->d_total);
     if (b->d_errs) cudaFree(b->d_errs);
     if (b->d_qpeak) cudaFree(b->d_qpeak);
+    if (b->d_ncen) cudaFree(b->d_ncen);
+    if (b->h_ncen) cudaFreeHost(b->h_ncen);
     if (b->d_gather) cudaFree(b->d_gather);
     if (b->h_gather) cudaFreeHost(b->h_gather);
     if (b->h_qpeak) cudaFreeHost(b->h_qpeak);
@@ -1841,7 +1856,7 @@ hww_status create_batch(const hww_problem_desc* descs, int32_t n, void* cuda_str
         b->m.push_back(p);
         Imax = std::max(Imax, p->I);
     }
-    b->smem = sizeof(long long) * TALLY_ROWS * (size_t)Imax;
+    b->smem = sizeof(long long) * (b->fp32 ? TALLY_ROWS_FP32 : TALLY_ROWS) * (size_t)Imax;
     if (track_batch_smem_optin(b->fp32, b->smem) != 0) {  // static shared memory counts too
         destroy_batch(b);
         return HWW_ERR_CUDA;
@@ -1859,6 +1874,8 @@ hww_status create_batch(const hww_problem_desc* descs, int32_t n, void* cuda_str
     if (e == cudaSuccess) e = cudaMalloc(&b->d_errs, sizeof(unsigned) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_qpeak, sizeof(unsigned long long) * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_qpeak, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ncen, sizeof(unsigned long long) * n);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_ncen, sizeof(unsigned long long) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_gather, sizeof(unsigned long long) * GATHER * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_gather, sizeof(unsigned long long) * GATHER * n);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_total, sizeof(unsigned long long));
@@ -1901,35 +1918,54 @@ hww_status run_batch_step(hww_batch* b, hww_batch_stats* stats) {
     hww_status s = HWW_OK;
     if (!b->pre && (s = capture_stage(b, 1, &b->pre))) return s;
     if (!b->post && (s = capture_stage(b, 0, &b->post))) return s;
-    for (int attempt = 0;; ++attempt) {
-        HWW_CK(cudaGraphLaunch(b->pre, b->stream));
-        s = b->fp32 ? batch_waves<float>(b) : batch_waves<double>(b);
-        if (s) return s;
-        HWW_CK(cudaMemcpyAsync(b->h_errs, b->d_errs, sizeof(unsigned) * b->P, cudaMemcpyDeviceToHost, b->stream));
-        HWW_CK(cudaMemcpyAsync(b->h_qpeak, b->d_qpeak, sizeof(unsigned long long) * b->P, cudaMemcpyDeviceToHost,
-                               b->stream));
-        HWW_CK(cudaStreamSynchronize(b->stream));
-        bool regrow = false;
-        for (int i = 0; i < b->P; ++i) {
-            const unsigned e = b->h_errs[i];
-            if (!(e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW))) continue;
-            if (attempt >= MAX_REGROW) return HWW_ERR_BANK_OVERFLOW;
-            hww_problem* p = b->m[i];
-            unsigned long long ncen = 0;
-            HWW_CK(cudaMemcpy(&ncen, p->counts, sizeof(ncen), cudaMemcpyDeviceToHost));
-            // sized by the demand seen (a truncated pass can under-report it;
-            // regrow_banks at least doubles the capacities anyway)
-            s = regrow_banks(p, (long long)ncen, (long long)b->h_qpeak[i]);
+    HWW_CK(cudaGraphLaunch(b->pre, b->stream));
+    s = b->fp32 ? batch_waves<float>(b) : batch_waves<double>(b);
+    if (s) return s;
+    HWW_CK(cudaMemcpyAsync(b->h_errs, b->d_errs, sizeof(unsigned) * b->P, cudaMemcpyDeviceToHost, b->stream));
+    HWW_CK(cudaMemcpyAsync(b->h_qpeak, b->d_qpeak, sizeof(unsigned long long) * b->P, cudaMemcpyDeviceToHost,
+                           b->stream));
+    HWW_CK(cudaMemcpyAsync(b->h_ncen, b->d_ncen, sizeof(unsigned long long) * b->P, cudaMemcpyDeviceToHost,
+                           b->stream));
+    HWW_CK(cudaStreamSynchronize(b->stream));
+    // A member whose census bank or record queue overflowed is tracked again
+    // on its own, through the single-problem path (same per-track arithmetic,
+    // so the same result as a batch that had the room); the other members'
+    // tracking stands.  Members that came near their capacities grow after
+    // the comb (which still reads this step's census bank).
+    bool rebuilt = false;
+    std::vector<int> grow;
+    b->step_replays = 0;
+    b->step_grows = 0;
+    for (int i = 0; i < b->P; ++i) {
+        hww_problem* p = b->m[i];
+        const unsigned e = b->h_errs[i];
+        if (e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW)) {
+            s = regrow_banks(p, (long long)b->h_ncen[i], (long long)b->h_qpeak[i]);
             if (s) return s;
             const unsigned keep = e & ~(unsigned)(ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW);
             HWW_CK(cudaMemcpy(p->err, &keep, sizeof(unsigned), cudaMemcpyHostToDevice));
-            regrow = true;
+            s = track_with_regrow(p);
+            if (s) return s;
+            ++b->step_replays;
+            rebuilt = true;
+        } else if ((long long)b->h_ncen[i] * 5 > p->cen_cap * 3 || (long long)b->h_qpeak[i] * 5 > p->q_cap * 3) {
+            grow.push_back(i);
         }
-        if (!regrow) break;
-        // the comb and the tracking arguments refer to the regrown buffers
+    }
+    // the comb and the tracking arguments refer to the regrown buffers
+    if (rebuilt && ((s = upload_batch_args(b)) || (s = capture_stage(b, 0, &b->post)))) return s;
+    HWW_CK(cudaGraphLaunch(b->post, b->stream));
+    if (!grow.empty()) {
+        // twice the capacity (at least) for the members that came within 60%
+        // of it, once the comb has read their census banks
+        HWW_CK(cudaStreamSynchronize(b->stream));
+        for (int i : grow) {
+            s = regrow_banks(b->m[i], (long long)b->h_ncen[i], (long long)b->h_qpeak[i]);
+            if (s) return s;
+            ++b->step_grows;
+        }
         if ((s = upload_batch_args(b)) || (s = capture_stage(b, 0, &b->post))) return s;
     }
-    HWW_CK(cudaGraphLaunch(b->post, b->stream));
     // and the caller's stream after the batch step
     HWW_CK(cudaEventRecord(b->ev_out, b->stream));
     HWW_CK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
@@ -1955,6 +1991,8 @@ hww_status run_batch_step(hww_batch* b, hww_batch_stats* stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->problems = b->P;
     stats->waves = b->last_waves;
+    stats->member_replays = b->step_replays;
+    stats->member_grows = b->step_grows;
     for (int i = 0; i < b->P; ++i) {
         const unsigned long long* g = b->h_gather + (size_t)i * GATHER;
         hww_step_stats ms;

@@ -14,12 +14,10 @@
 // rounded once (half up) at the tally scale.  The FP64 pipe, of which GB300
 // has little, is left to rare events (splits, roulette, leaks, census).
 //
-// The single-problem kernel runs a warp-synchronous loop (run_warp): the
+// Both the single-problem kernel and the persistent batched kernel (one
+// tile of one problem at a time) run a warp-synchronous loop (run_warp): the
 // lanes of a warp take their events together and share a daughter stack, so
-// the daughters of a split spread over the warp's idle lanes.  The persistent
-// batched kernel runs a flattened per-lane loop (run_items): a lane whose
-// track ends loads its next track in the same iteration the other lanes
-// spend on their next event.
+// the daughters of a split spread over the warp's idle lanes.
 #include "track_common.cuh"
 
 namespace hww {
@@ -33,40 +31,6 @@ struct P32 {
     uint32_t id;
     uint64_t lin;
     uint32_t e;
-};
-
-// The pending parent of a lane (the record whose daughters it expands), kept
-// in shared memory, one column per thread: it is written at a split and read
-// once per daughter, and registers are what limits the resident warps.
-struct PendingParent {
-    float xo[TRACK_THREADS], mu[TRACK_THREADS], tau[TRACK_THREADS];
-    double w[TRACK_THREADS];
-    long long W[TRACK_THREADS];
-    int cell[TRACK_THREADS];
-    uint32_t id[TRACK_THREADS], e[TRACK_THREADS];
-    uint64_t lin[TRACK_THREADS];
-    __device__ __forceinline__ void store(int t, const P32& q) {
-        xo[t] = q.xo;
-        mu[t] = q.mu;
-        tau[t] = q.tau;
-        w[t] = q.w;
-        W[t] = q.W;
-        cell[t] = q.cell;
-        id[t] = q.id;
-        e[t] = q.e;
-        lin[t] = q.lin;
-    }
-    __device__ __forceinline__ void load(int t, P32& q) const {
-        q.xo = xo[t];
-        q.mu = mu[t];
-        q.tau = tau[t];
-        q.w = w[t];
-        q.W = W[t];
-        q.cell = cell[t];
-        q.id = id[t];
-        q.e = e[t];
-        q.lin = lin[t];
-    }
 };
 
 // The comb-scale weight of a census particle from its tally-scale weight W:
@@ -101,334 +65,8 @@ __device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32
     a.rout.jcount[slot] = jcount;
 }
 
-// The event loop over items [item, item_end): with the given stride, or, when
-// s_next is a block-shared counter, item + the next value of that counter
-// (lanes busy with many daughters then take fewer items); b_blk is the
-// variance batch whose row is kept in shared memory (-1: none).
-template <uint32_t LOCAL_MAX>
-__device__ __forceinline__ void run_items(const TrackArgs<float>& a, long long item, const long long item_end,
-                                          const long long stride, unsigned* s_next, const int b_blk, long long* sm,
-                                          Counters& cnt, PendingParent* pp) {
-    const int I = a.I;
-    long long* s_tl = sm;
-    long long* s_bat = sm + 3 * I;  // batch row of the current id range
-    // the step scalars needed only at rare events are read where they are
-    // used (registers are what limits the resident warps)
-    const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
-    const int ww_on = a.sd->ww_on;
-    const int t = threadIdx.x;
-
-    P32 q;
-    uint32_t jnext = 0, jend = 0;
-    bool fresh = false;  // the pending parent's daughters are a collision's extra particles
-    bool have = false;
-    int evs = 0;
-    int qb = 0;  // variance batch of the current track's source id
-    for (;;) {
-        if (!have) {
-            if (jnext < jend) {
-                pp->load(t, q);
-                q.lin = lineage_hash(q.lin, q.e, jnext);
-                q.e = 0;
-                ++jnext;
-                if (fresh) {  // its own isotropic direction
-                    uint32_t rr[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 0xFFFFFFFEu};
-                    philox4x32_10(rr, k0, k1);
-                    q.mu = 2.0f * u01f(rr[1]) - 1.0f;
-                }
-            } else {
-                long long i;
-                if (s_next) {
-                    i = item + (long long)warp_reserve(s_next);
-                } else {
-                    i = item;
-                    item += stride;
-                }
-                if (i >= item_end) break;
-                if (a.from_bank) {
-                    q.id = (uint32_t)i;
-                    q.lin = 0;
-                    q.e = 0;
-                    q.tau = a.tau0f;
-                    q.w = a.sd->wbar;
-                    q.W = a.sd->Wbar;
-                    if (a.sd->birth) {
-                        uint32_t r[4] = {(uint32_t)i, 0u, 0u, 0xFFFFFFFFu};
-                        philox4x32_10(r, k0, k1);
-                        q.mu = 2.0f * u01f(r[1]) - 1.0f;
-                        const double x = a.src_x;
-                        if (x <= a.edges[0] && q.mu < 0.0f && a.bc_l == 1) q.mu = -q.mu;
-                        if (x >= a.edges[I] && q.mu > 0.0f && a.bc_r == 1) q.mu = -q.mu;
-                        q.cell = (q.mu < 0.0f) ? a.birth_cell_neg : a.birth_cell_pos;
-                        q.xo = (float)(x - a.edges[q.cell]);
-                    } else {
-                        const BankRec<float> r = a.bank[i];
-                        q.xo = r.x;
-                        q.mu = r.mu;
-                        q.cell = r.cell;
-                    }
-                } else {
-                    q.xo = a.rin.x[i];
-                    q.mu = a.rin.mu[i];
-                    q.tau = a.rin.tau[i];
-                    q.w = a.rin.w[i];
-                    q.W = to_fixed(q.w, a.sd->tscale);
-                    q.cell = a.rin.cell[i];
-                    q.id = a.rin.id[i];
-                    q.lin = a.rin.lin[i];
-                    q.e = a.rin.e[i];
-                    const uint32_t jc = a.rin.jcount[i];
-                    if (jc) {
-                        pp->store(t, q);
-                        const uint32_t js = a.rin.jstart[i];
-                        fresh = (js & FRESH_DIRECTION) != 0;
-                        jnext = js & ~FRESH_DIRECTION;
-                        jend = jnext + jc;
-                        q.lin = lineage_hash(q.lin, q.e, jnext);
-                        q.e = 0;
-                        ++jnext;
-                        if (fresh) {  // its own isotropic direction
-                            uint32_t rr[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 0xFFFFFFFEu};
-                            philox4x32_10(rr, k0, k1);
-                            q.mu = 2.0f * u01f(rr[1]) - 1.0f;
-                        }
-                    }
-                }
-            }
-            q.inv_mu = __frcp_rn(q.mu);  // the correctly rounded 1/mu
-            have = true;
-            evs = 0;
-            qb = batch_of(q.id, a.B, a.N, a.batch_m);
-        }
-        // ---- one event ----
-        if (evs == a.emax) {
-            push_record(a, q, q.w, q.e, 0u, 0u, warp_reserve(a.rout.count));
-            have = false;
-            continue;
-        }
-        if (q.e >= MAX_EVENTS) {
-            atomicOr(a.err, ERR_EVENTS);
-            have = false;
-            continue;
-        }
-        uint32_t r[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 2u * q.e};
-        philox4x32_10(r, k0, k1);
-        const float uf = u01f(r[1]);
-        const float uc = u01f(r[3]);
-        const int k = q.cell;
-        const float4 cf = __ldg(&a.cellf[k]);  // width, 1/Sigma_t, c
-        const float dxk = cf.x;
-        const float dcoll = -__logf(uf) * cf.y;  // as in the single-problem loop
-        const float dedge = ((q.mu > 0.0f) ? (dxk - q.xo) : -q.xo) * q.inv_mu;
-        const float dcens = q.tau;
-        int ev;
-        float l;
-        if (dcens <= dedge && dcens <= dcoll) {
-            ev = 0;
-            l = dcens;
-        } else if (dedge <= dcoll) {
-            ev = 1;
-            l = dedge;
-        } else {
-            ev = 2;
-            l = dcoll;
-        }
-        const float m2 = q.mu * q.mu;
-        const float f3 = 1.0f / 3.0f - m2;
-        {
-            // one shared atomic per lane and word: merging the lanes of a
-            // warp that share a cell first (match + shuffle tree) measured
-            // slower than the atomics it saves.  The flux goes to the
-            // variance-batch row only: the flux tally is the sum of the batch
-            // rows, formed after the tracking (one atomic fewer per segment)
-            const int b = qb;
-            const long long c0 = fx_mul(q.W, l);
-            sadd(&s_tl[I + k], fx_mul(q.W, l * q.mu));
-            sadd(&s_tl[2 * I + k], fx_mul(q.W, l * f3));
-            if (b == b_blk)
-                sadd(&s_bat[k], c0);
-            else
-                add128(&a.batch[(long long)b * I + k], c0);
-        }
-        if (ev != 1) q.xo = fminf(fmaxf(fmaf(q.mu, l, q.xo), 0.0f), dxk);
-        q.tau = (ev == 0) ? 0.0f : q.tau - l;
-        const uint32_t e_ev = q.e;
-        q.e = q.e + 1;
-        ++evs;
-        if (ev == 0) {
-            // census: the bank record (its tallies come from the census pass)
-            const unsigned long long slot = warp_reserve(a.cen.count);
-            if ((long long)slot < a.cen.cap) {
-                a.cen.x[slot] = q.xo;
-                a.cen.mu[slot] = q.mu;
-                a.cen.w[slot] = q.w;
-                a.cen.cell[slot] = q.cell;
-                a.cen.id[slot] = q.id;
-
-                const unsigned long long wfx = comb_weight(q.W, a.comb_shift);
-                a.cen.lw[slot] = LinW{q.lin, wfx};
-                atomicAdd(&a.gcnt[q.id], 1u);
-                atomicAdd(&a.gw[q.id], wfx);
-            } else {
-                atomicOr(a.err, ERR_CENSUS_OVERFLOW);
-            }
-            cnt.v[ST_CENSUS]++;
-            cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-            have = false;
-            continue;
-        }
-        bool have_r2 = false;
-        uint32_t r2[4];
-        if (ev == 1) {
-            cnt.v[ST_CROSSINGS]++;
-            const int nk = (q.mu > 0.0f) ? k + 1 : k - 1;
-            if (nk < 0 || nk >= I) {
-                const int side = (nk < 0) ? 0 : 1;
-                const int bc = side ? a.bc_r : a.bc_l;
-                if (bc == 0) {
-                    const double amu = fabs((double)q.mu);
-                    const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
-                    const double wi = q.w * ia;
-                    const double dm2 = (double)q.mu * (double)q.mu;
-                    add128(&a.bnd[3 * side + 0], to_fixed(wi, a.sd->tscale));
-                    add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - dm2), a.sd->tscale));
-                    add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), a.sd->tscale));
-                    cnt.v[ST_LEAKED]++;
-                    cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                    have = false;
-                    continue;
-                }
-                q.mu = -q.mu;
-                q.inv_mu = -q.inv_mu;
-                q.xo = side ? dxk : 0.0f;
-                cnt.v[ST_REFLECTIONS]++;
-            } else {
-                q.cell = nk;
-                q.xo = (q.mu > 0.0f) ? 0.0f : __ldg(&a.cellf[nk]).x;
-            }
-        } else {
-            cnt.v[ST_COLLISIONS]++;
-            // the collision emits floor(c) + [u_c < c - floor(c)] particles (mean c)
-            const float cfl = floorf(cf.z);
-            const uint32_t nsec = (uint32_t)cfl + ((uc < cf.z - cfl) ? 1u : 0u);
-            if (nsec == 0) {
-                cnt.v[ST_ABSORBED]++;
-                cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                have = false;
-                continue;
-            }
-            r2[0] = q.id;
-            r2[1] = (uint32_t)q.lin;
-            r2[2] = (uint32_t)(q.lin >> 32);
-            r2[3] = 2u * e_ev + 1u;
-            philox4x32_10(r2, k0, k1);
-            have_r2 = true;
-            q.mu = 2.0f * u01f(r2[1]) - 1.0f;
-            q.inv_mu = __frcp_rn(q.mu);
-            if (nsec > 1) {
-                // the other emitted particles: daughters that take their own
-                // lineages and isotropic directions, expanded by this lane
-                // after the current track, or queued as records when it is
-                // already expanding a parent
-                const uint32_t nx = nsec - 1;
-                uint32_t jr = 1;  // the first daughter that goes to the record queue
-                if (LOCAL_MAX > 0 && jnext >= jend) {
-                    P32 b = q;
-                    b.e = e_ev | SECONDARY_EVENT;
-                    pp->store(t, b);
-                    fresh = true;
-                    jnext = 1;
-                    jend = min(nsec, 1u + LOCAL_MAX);
-                    jr = jend;
-                }
-                if (jr < nsec) {
-                    const uint32_t nch = (nsec - jr + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
-                    const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
-                    for (uint32_t ch = 0; ch < nch; ++ch) {
-                        const uint32_t j0 = jr + ch * SPLIT_CHUNK;
-                        const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nsec - j0);
-                        push_record(a, q, q.w, e_ev | SECONDARY_EVENT, j0 | FRESH_DIRECTION, jc, b0 + ch);
-                    }
-                }
-                cnt.v[ST_DAUGHTERS] += nx;
-            }
-        }
-        if (ww_on) {
-            const int kc = q.cell;
-            const double2 hl = __ldg(&a.ww_hl[kc]);  // ceiling, floor
-            if (dgt(q.w, hl.x)) {
-                const double ctr = a.ww_c[kc];
-                // split count from an FP32 ratio (the FP32 path's own rounding; the FP64
-                // quotient measured 3% slower at the workload)
-                const float ndf = ceilf((float)q.w / (float)ctr);
-                const double ndd = (double)fmaxf(ndf, 2.0f);
-                if (ndd > (double)MAX_DAUGHTERS) {
-                    atomicOr(a.err, ERR_DAUGHTERS);
-                    have = false;
-                    continue;
-                }
-                const uint32_t nd = (uint32_t)ndd;
-                const double wd = q.w / (double)nd;
-                const long long Wd = to_fixed(wd, a.sd->tscale);
-                cnt.v[ST_SPLIT_EVENTS]++;
-                cnt.v[ST_DAUGHTERS] += nd - 1;
-                uint32_t jr = 1;  // the first daughter that goes to the record queue
-                if (LOCAL_MAX > 0 && jnext >= jend) {
-                    // up to LOCAL_MAX daughters follow the current track on
-                    // this lane (same block, so their batch row stays in
-                    // shared memory); the bound keeps a large split from
-                    // holding one lane while the rest of its block waits
-                    P32 b = q;
-                    b.w = wd;
-                    b.W = Wd;
-                    b.e = e_ev;
-                    pp->store(t, b);
-                    fresh = false;
-                    jnext = 1;
-                    jend = min(nd, 1u + LOCAL_MAX);
-                    jr = jend;
-                }
-                if (jr < nd) {
-                    const uint32_t nch = (nd - jr + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
-                    const unsigned long long b0 = warp_reserve_n(a.rout.count, nch);
-                    for (uint32_t ch = 0; ch < nch; ++ch) {
-                        const uint32_t j0 = jr + ch * SPLIT_CHUNK;
-                        const uint32_t jc = min((uint32_t)SPLIT_CHUNK, nd - j0);
-                        push_record(a, q, wd, e_ev, j0, jc, b0 + ch);
-                    }
-                }
-                q.w = wd;
-                q.W = Wd;
-                q.lin = lineage_hash(q.lin, e_ev, 0);
-                q.e = 0;
-            } else if (dgt(hl.y, q.w)) {
-                if (!have_r2) {
-                    r2[0] = q.id;
-                    r2[1] = (uint32_t)q.lin;
-                    r2[2] = (uint32_t)(q.lin >> 32);
-                    r2[3] = 2u * e_ev + 1u;
-                    philox4x32_10(r2, k0, k1);
-                }
-                const double ctr = a.ww_c[kc];
-                // survive iff u < w / ww, tested as u ww < w (no divide)
-                const double ur = u01(r2[2], r2[3]);
-                if (ur * ctr < q.w) {
-                    q.w = ctr;
-                    q.W = to_fixed(ctr, a.sd->tscale);
-                    cnt.v[ST_RSURVIVE]++;
-                } else {
-                    cnt.v[ST_RKILLS]++;
-                    cnt.v[ST_MAX_EVENTS] = max(cnt.v[ST_MAX_EVENTS], q.e);
-                    have = false;
-                    continue;
-                }
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
-// The single-problem event loop, warp-synchronous.
+// The event loop, warp-synchronous.
 //
 // All 32 lanes of a warp iterate together until the warp has no work left.
 // Each iteration hands work to the lanes without a track, draws the Philox
@@ -1065,6 +703,48 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
     }
 }
 
+// the block-private J and F rows (32-bit halves) into the global 128-bit
+// tallies
+__device__ __forceinline__ void flush_jf(const unsigned* tl32, int I, Acc128* tl) {
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        const long long vJ = (long long)(((unsigned long long)tl32[I + i] << 32) | tl32[i]);
+        const long long vF = (long long)(((unsigned long long)tl32[3 * I + i] << 32) | tl32[2 * I + i]);
+        if (vJ != 0) add128(&tl[I + i], vJ);
+        if (vF != 0) add128(&tl[2 * I + i], vF);
+    }
+}
+
+// the block-private batch row into the global batch tally of batch b (and
+// cleared when `clear`)
+__device__ __forceinline__ void flush_batch_row(unsigned* tl32, int I, Acc128* batch, int b, bool clear) {
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        const long long vB = (long long)(((unsigned long long)tl32[5 * I + i] << 32) | tl32[4 * I + i]);
+        if (vB != 0) add128(&batch[(long long)b * I + i], vB);
+        if (clear) {
+            tl32[4 * I + i] = 0;
+            tl32[5 * I + i] = 0;
+        }
+    }
+}
+
+// the block's counts into the problem's (segments and scatters follow from
+// the event counts); a barrier first and last
+__device__ __forceinline__ void flush_block_stats(unsigned long long* s_stats, unsigned long long* stats) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_stats[ST_SEGMENTS] = s_stats[ST_CENSUS] + s_stats[ST_CROSSINGS] + s_stats[ST_COLLISIONS];
+        s_stats[ST_SCATTERS] = s_stats[ST_COLLISIONS] - s_stats[ST_ABSORBED];
+    }
+    __syncthreads();
+    if (threadIdx.x < ST_COUNT && s_stats[threadIdx.x]) {
+        if (threadIdx.x == ST_MAX_EVENTS)
+            atomicMax(&stats[ST_MAX_EVENTS], s_stats[threadIdx.x]);
+        else
+            atomicAdd(&stats[threadIdx.x], s_stats[threadIdx.x]);
+    }
+    __syncthreads();
+}
+
 // Three resident blocks of 256 threads per SM (85 registers): measured at the
 // workload, four blocks (64 registers) executed 4.5% more instructions
 // (register pressure) and ran 7% slower, two blocks (128 registers) 11% fewer
@@ -1109,43 +789,29 @@ __global__ void __launch_bounds__(TRACK_THREADS, 3) track32_kernel(TrackArgs<flo
     run_warp(a, first, last, &s_next, b_blk, b_end, tl32, s_ws, bs, s_stats);
     __syncthreads();
     // block-private tallies into the global ones (J, F; the batch row)
-    for (int i = threadIdx.x; i < I; i += blockDim.x) {
-        const long long vJ = (long long)(((unsigned long long)tl32[I + i] << 32) | tl32[i]);
-        const long long vF = (long long)(((unsigned long long)tl32[3 * I + i] << 32) | tl32[2 * I + i]);
-        if (vJ != 0) add128(&a.tl[I + i], vJ);
-        if (vF != 0) add128(&a.tl[2 * I + i], vF);
-        if (b_blk >= 0) {
-            const long long vB = (long long)(((unsigned long long)tl32[5 * I + i] << 32) | tl32[4 * I + i]);
-            if (vB != 0) add128(&a.batch[(long long)b_blk * I + i], vB);
-        }
-    }
-    // counts: segments and scatters follow from the event counts
-    if (threadIdx.x == 0) {
-        s_stats[ST_SEGMENTS] = s_stats[ST_CENSUS] + s_stats[ST_CROSSINGS] + s_stats[ST_COLLISIONS];
-        s_stats[ST_SCATTERS] = s_stats[ST_COLLISIONS] - s_stats[ST_ABSORBED];
-    }
-    __syncthreads();
-    if (threadIdx.x < ST_COUNT && s_stats[threadIdx.x]) {
-        if (threadIdx.x == ST_MAX_EVENTS)
-            atomicMax(&a.stats[ST_MAX_EVENTS], s_stats[threadIdx.x]);
-        else
-            atomicAdd(&a.stats[threadIdx.x], s_stats[threadIdx.x]);
-    }
+    flush_jf(tl32, I, a.tl);
+    if (b_blk >= 0) flush_batch_row(tl32, I, a.batch, b_blk, false);
+    flush_block_stats(s_stats, a.stats);
 }
 
 // Persistent batched variant: blocks pop tiles (problem, id range) from a
-// device counter; the block-private tallies are flushed when a block moves
-// to another problem, the batch row after every tile.
+// device counter and run the warp-synchronous loop over each tile's items;
+// the block-private tallies and counts are flushed when a block moves to
+// another problem, the batch row after every tile.  A warp leaves a tile
+// only with its daughter stack empty, so the tile's barrier waits for no
+// queued work.
 __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const TrackArgs<float>* args,
                                                                          BatchPlan plan) {
-    extern __shared__ long long sm[];
-    __shared__ PendingParent s_pp;
+    extern __shared__ long long sm[];  // ROWS32 rows of Imax 64-bit words, as 32-bit halves
+    __shared__ WarpShared s_ws;
     __shared__ TrackArgs<float> A;
+    __shared__ BlockScalars s_bs;
+    __shared__ unsigned long long s_stats[ST_COUNT];
     __shared__ long long s_t;
     __shared__ int s_p;
     __shared__ unsigned s_next;
-    Counters cnt;
-    cnt.zero();
+    unsigned* tl32 = reinterpret_cast<unsigned*>(sm);
+    if (threadIdx.x < WARPS) s_ws.top[threadIdx.x] = 0;
     const long long total = plan.tile_off[plan.P];
     int cur = -1, Ic = 0;
     for (;;) {
@@ -1169,34 +835,37 @@ __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const T
         const int p = s_p;
         if (p < 0 || p != cur) {  // a problem switch, or no tile left (also on the first pop)
             if (cur >= 0) {
-                flush_tallies(sm, Ic, A.tl);
-                flush_counters(cnt, A.stats);
-                cnt.zero();
-                __syncthreads();
+                flush_jf(tl32, Ic, A.tl);
+                flush_block_stats(s_stats, A.stats);
             }
             if (p < 0) break;
             if (threadIdx.x == 0) A = args[p];
             __syncthreads();
+            if (threadIdx.x == 0) {
+                s_bs.wbar = A.sd->wbar;
+                s_bs.tscale = A.sd->tscale;
+                s_bs.Wbar = A.sd->Wbar;
+            }
+            if (threadIdx.x < ST_COUNT) s_stats[threadIdx.x] = 0;
             cur = p;
             Ic = A.I;
-            for (int i = threadIdx.x; i < TALLY_ROWS * Ic; i += blockDim.x) sm[i] = 0;
+            for (int i = threadIdx.x; i < 2 * ROWS32 * Ic; i += blockDim.x) tl32[i] = 0;
             __syncthreads();
         }
         const long long n_in = A.from_bank ? (long long)A.sd->nbank : (long long)*A.rin.count;
         const long long n_use = (!A.from_bank && n_in > A.rin.cap) ? A.rin.cap : n_in;
         const long long i0 = (t - plan.tile_off[p]) * (long long)plan.tile;
         const long long i1 = min(n_use, i0 + (long long)plan.tile);
-        const int b_tile = (A.from_bank && i0 < n_use) ? batch_of((uint32_t)i0, A.B, A.N, A.batch_m) : -1;
-        run_items<0>(A, i0, i1, 0, &s_next, b_tile, sm, cnt, &s_pp);
+        int b_tile = -1;
+        uint32_t b_end = 0;
+        if (A.from_bank && i0 < n_use) {
+            b_tile = batch_of((uint32_t)i0, A.B, A.N, A.batch_m);
+            b_end = (uint32_t)min((long long)UINT32_MAX, ((long long)(b_tile + 1) * A.N + A.B - 1) / A.B);
+        }
+        const BlockScalars bs = s_bs;
+        run_warp(A, i0, i1, &s_next, b_tile, b_end, tl32, s_ws, bs, s_stats);
         __syncthreads();
-        if (b_tile >= 0)
-            for (int i = threadIdx.x; i < Ic; i += blockDim.x) {
-                const long long v = sm[3 * Ic + i];
-                if (v != 0) {
-                    add128(&A.batch[(long long)b_tile * Ic + i], v);
-                    sm[3 * Ic + i] = 0;
-                }
-            }
+        if (b_tile >= 0) flush_batch_row(tl32, Ic, A.batch, b_tile, true);
         __syncthreads();
     }
 }

@@ -116,3 +116,32 @@ def test_shared_memory_near_the_default_limit(precision):
         w["precision"] = precision
     b = hww.Batch(sweep)
     assert b.run_step()["status"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_overflowing_member_is_replayed_alone(precision):
+    # one member starts with room for 300 census particles: its first steps
+    # overflow, it is tracked again on its own with larger buffers (so may
+    # small members whose census outgrows four times their particles), and
+    # every member stays bit-identical to the same problem stepped alone
+    wls = small_sweep(6, precision, seed=11)
+    big = max(range(6), key=lambda i: wls[i]["particles_per_step"])
+    assert wls[big]["particles_per_step"] > 600
+    wls[big] = dict(wls[big], bank_capacity=300)
+    batch = hww.Batch(wls)
+    alone = [hww.Problem.from_workload(wl, bank_capacity=wl.get("bank_capacity", 0)) for wl in wls]
+    replays = 0
+    for step in range(4):
+        st = batch.run_step()
+        replays += st["member_replays"]
+        assert st["member_replays"] < len(wls)
+        for i, p in enumerate(alone):
+            s = p.run_step()
+            sb = batch.member_stats(i)
+            for k in oracle.STAT_FIELDS:
+                assert sb[k] == s[k], (step, i, k)
+            same(snapshot(batch.members[i]), snapshot(p))
+    assert replays >= 1
+    for p in alone:
+        p.close()
+    batch.close()
