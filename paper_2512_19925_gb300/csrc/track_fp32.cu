@@ -85,6 +85,12 @@ __device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32
 // full, and a track past its event budget, go to the record queue.
 constexpr int WARPS = TRACK_THREADS / 32;
 constexpr int WSTACK = 32;  // daughter-stack entries per warp
+// Splits are queued per warp and processed (split count, daughter weight,
+// stack push) by the whole warp once SPLIT_BATCH of them wait, or when lanes
+// run out of other work: the split's arithmetic (two divisions and a
+// fixed-point rounding in FP64) then runs for many lanes at once instead of
+// for the one or two lanes that split in a typical iteration.
+constexpr unsigned SPLIT_BATCH = 16;
 constexpr int ROWS32 = TALLY_ROWS_FP32;
 
 struct WarpShared {
@@ -104,6 +110,13 @@ struct WarpShared {
     int ccell[WARPS][32];
     uint32_t cid[WARPS][32];
     LinW clw[WARPS][32];
+    // split queue: parents whose split is pending (state before the split,
+    // the event index of the split, the window center)
+    float sx[WARPS][32], smu[WARPS][32], stau[WARPS][32];
+    double sw[WARPS][32], sctr[WARPS][32];
+    int scell[WARPS][32];
+    uint32_t sid[WARPS][32], se[WARPS][32];
+    uint64_t slin[WARPS][32];
     // start-bank records of the next items, two slots of 32: slot s holds
     // items item0 + rb[s] .. + rn[s]; items are handed out from slot rcs
     // starting at rpos
@@ -245,6 +258,42 @@ __device__ __forceinline__ void census_flush(const TrackArgs<float>& a, WarpShar
     __syncwarp();
 }
 
+// The warp's queued splits [0, n), one per lane: the split count, the
+// daughters' weight, and the daughters 0..nd-1 pushed to the daughter stack
+// (or queued as records when it is full); returns the daughters created
+// beyond the parents (this lane's share).  Whole warp, converged.
+__device__ __forceinline__ uint32_t process_splits(const TrackArgs<float>& a, WarpShared& ws, int wp, unsigned n,
+                                                   unsigned lane, double tscale) {
+    uint32_t added = 0;
+    if (lane < n) {
+        P32 b;
+        b.xo = ws.sx[wp][lane];
+        b.mu = ws.smu[wp][lane];
+        b.tau = ws.stau[wp][lane];
+        b.cell = ws.scell[wp][lane];
+        b.id = ws.sid[wp][lane];
+        b.e = ws.se[wp][lane];
+        b.lin = ws.slin[wp][lane];
+        const double w = ws.sw[wp][lane];
+        const double ctr = ws.sctr[wp][lane];
+        // split count from an FP32 ratio (the FP32 path's own rounding; the FP64
+        // quotient measured 3% slower at the workload)
+        const float ndf = ceilf((float)w / (float)ctr);
+        const double ndd = (double)fmaxf(ndf, 2.0f);
+        if (ndd > (double)MAX_DAUGHTERS) {
+            atomicOr(a.err, ERR_DAUGHTERS);
+        } else {
+            const uint32_t nd = (uint32_t)ndd;
+            b.w = w / (double)nd;
+            b.W = to_fixed(b.w, tscale);
+            added = nd - 1;
+            if (!stack_push(ws, wp, b, 0u, nd)) queue_daughters(a, b, 0u, nd, 0u);
+        }
+    }
+    __syncwarp();
+    return added;
+}
+
 struct BlockScalars {
     double wbar, tscale;
     long long Wbar;
@@ -299,8 +348,11 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
     int evs = 0;
     int qb = 0;
     unsigned cfill = 0;            // staged census particles of the warp
+    unsigned sqn = 0;              // queued splits of the warp
+    double sctr = 0.0;             // the window center of this lane's split
     unsigned long long mycnt = 0;  // lane k < EB_COUNT: counter kLaneStat[k]; then daughters, max events
     for (;;) {
+        uint32_t nadd = 0;    // daughters created in this iteration (this lane's share)
         // ---- refill: daughters from the warp's stack, then new items ----
         unsigned need = __ballot_sync(0xffffffffu, !have);
         bool got = false;  // this lane took a new track this iteration
@@ -399,7 +451,8 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
             base = __shfl_sync(0xffffffffu, base, 0);
             if (item0 + (long long)base + k >= item_end) items_left = false;
             const long long i = item0 + (long long)base + (long long)__popc(need & lt);
-            if (((need >> lane) & 1u) && i < item_end) {
+            const bool took = ((need >> lane) & 1u) && i < item_end;
+            if (took) {
                 mode = M_EVENT;
                 if (a.from_bank) {  // the pulse (step 1)
                     q.id = (uint32_t)i;
@@ -435,7 +488,48 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                 have = true;
                 got = true;
             }
-            __syncwarp();
+            need &= ~__ballot_sync(0xffffffffu, took);
+        }
+        if (need && sqn) {
+            // lanes still without work: the queued splits' daughters
+            nadd += process_splits(a, ws, wp, sqn, lane, bs.tscale);
+            sqn = 0;
+            while (need) {
+                const int top = *(volatile int*)&ws.top[wp];
+                if (top <= 0) break;
+                const int t = top - 1;
+                const uint32_t jn0 = ws.jn[wp][t], je = ws.je[wp][t];
+                const uint32_t fr = jn0 & FRESH_DIRECTION, jn = jn0 & ~FRESH_DIRECTION;
+                const uint32_t left = je - jn;
+                const uint32_t take = min((uint32_t)__popc(need), left);
+                const uint32_t rank = __popc(need & lt);
+                const bool mine = ((need >> lane) & 1u) && rank < take;
+                if (mine) {
+                    q.xo = ws.xo[wp][t];
+                    q.mu = ws.mu[wp][t];
+                    q.tau = ws.tau[wp][t];
+                    q.w = ws.w[wp][t];
+                    q.W = ws.W[wp][t];
+                    q.cell = ws.cell[wp][t];
+                    q.id = ws.id[wp][t];
+                    q.lin = ws.lin[wp][t];
+                    q.e = ws.e[wp][t];
+                    jd = jn + rank;
+                    fresh = fr != 0;
+                    mode = M_LINEAGE;
+                    have = true;
+                    got = true;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    if (take == left)
+                        ws.top[wp] = t;
+                    else
+                        ws.jn[wp][t] = (jn + take) | fr;
+                }
+                need &= ~__ballot_sync(0xffffffffu, mine);
+                __syncwarp();
+            }
         }
         if (got) {
             evs = 0;
@@ -444,10 +538,12 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
             qb = (q.id >= (uint32_t)item0 && q.id < b_end) ? b_blk : batch_of(q.id, a.B, a.N, a.batch_m);
             if (mode == M_EVENT) q.inv_mu = __frcp_rn(q.mu);  // the correctly rounded 1/mu
         }
-        if (!__any_sync(0xffffffffu, have)) break;
+        if (!__any_sync(0xffffffffu, have)) {
+            if (!sqn) break;
+            continue;  // the queued splits go to the lanes at the next refill
+        }
 
         unsigned eb = 0;      // outcome bits
-        uint32_t nadd = 0;    // daughters created
         uint32_t e_end = 0;   // event count of a track that ended
         if (have && mode == M_EVENT) {
             if (evs == a.emax) {  // past the event budget: a continuation record
@@ -611,29 +707,12 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                 const int kc = q.cell;
                 const double2 hl = __ldg(&a.ww_hl[kc]);  // ceiling, floor
                 if (dgt(q.w, hl.x)) {
-                    const double ctr = a.ww_c[kc];
-                    // split count from an FP32 ratio (the FP32 path's own rounding; the FP64
-                    // quotient measured 3% slower at the workload)
-                    const float ndf = ceilf((float)q.w / (float)ctr);
-                    const double ndd = (double)fmaxf(ndf, 2.0f);
-                    if (ndd > (double)MAX_DAUGHTERS) {
-                        atomicOr(a.err, ERR_DAUGHTERS);
-                        have = false;
-                    } else {
-                        const uint32_t nd = (uint32_t)ndd;
-                        const double wd = q.w / (double)nd;
-                        const long long Wd = to_fixed(wd, bs.tscale);
-                        eb |= 1u << EB_SPLIT;
-                        nadd += nd - 1;
-                        q.w = wd;
-                        q.W = Wd;
-                        q.e = e_ev;
-                        if (!stack_push(ws, wp, q, 1u, nd)) queue_daughters(a, q, 1u, nd, 0u);
-                        // this lane goes on with daughter 0 (its lineage key next)
-                        jd = 0;
-                        fresh = false;
-                        mode = M_LINEAGE;
-                    }
+                    // a split: the parent joins the warp's split queue (below),
+                    // all its daughters come back through the daughter stack
+                    eb |= 1u << EB_SPLIT;
+                    q.e = e_ev;
+                    sctr = a.ww_c[kc];
+                    have = false;
                 } else if (dgt(hl.y, q.w)) {
                     const double ctr = a.ww_c[kc];
                     // survive iff u < w / ww, tested as u ww < w (no divide)
@@ -651,6 +730,35 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
             }
         }
         __syncwarp();
+        // ---- splits of the iteration: queued, processed a batch at a time ----
+        {
+            const unsigned sm_ = __ballot_sync(0xffffffffu, (eb >> EB_SPLIT) & 1u);
+            const unsigned ns = __popc(sm_);
+            if (ns) {
+                if (sqn + ns > 32u) {
+                    nadd += process_splits(a, ws, wp, sqn, lane, bs.tscale);
+                    sqn = 0;
+                }
+                if ((sm_ >> lane) & 1u) {
+                    const unsigned pos = sqn + __popc(sm_ & lt);
+                    ws.sx[wp][pos] = q.xo;
+                    ws.smu[wp][pos] = q.mu;
+                    ws.stau[wp][pos] = q.tau;
+                    ws.sw[wp][pos] = q.w;
+                    ws.sctr[wp][pos] = sctr;
+                    ws.scell[wp][pos] = q.cell;
+                    ws.sid[wp][pos] = q.id;
+                    ws.se[wp][pos] = q.e;
+                    ws.slin[wp][pos] = q.lin;
+                }
+                sqn += ns;
+                __syncwarp();
+                if (sqn >= SPLIT_BATCH) {
+                    nadd += process_splits(a, ws, wp, sqn, lane, bs.tscale);
+                    sqn = 0;
+                }
+            }
+        }
         // ---- census particles of the iteration: staged, written 32 at a time ----
         {
             const unsigned cm = __ballot_sync(0xffffffffu, (eb >> EB_CENSUS) & 1u);
