@@ -180,39 +180,33 @@ __host__ __device__ __forceinline__ double pow2(int e) {
     return v.d;
 }
 
-// FP32 path: the tally contribution of an FP32 factor f to a fixed-point
-// weight.
-// round(W * f) for 0 <= W < 2^63 and an FP32 f, from the exact product of W
-// and the 24-bit mantissa m of f (round half up); subnormal f counts as 0.
-// The product W m = A 2^32 + B is formed from two 32 x 32 -> 64-bit products
-// (A from the high word of W, B from the low word), and shifted right by s
-// (f = m 2^-s) with the bit below the result as the rounding bit.
-__device__ __forceinline__ long long fx_mul(long long W, float f) {
-    const unsigned b = __float_as_uint(f);
-    const int ex = (int)((b >> 23) & 0xFFu);
-    if (ex == 0) return 0;
-    const unsigned m = (b & 0x7FFFFFu) | 0x800000u;
-    const int s = 150 - ex;  // value = m 2^-s
-    const unsigned long long uw = (unsigned long long)W;
-    const unsigned long long A = (unsigned long long)(unsigned)(uw >> 32) * m;  // < 2^55
-    const unsigned long long B = (unsigned long long)(unsigned)uw * m;          // < 2^56
-    unsigned long long r, rb;
-    if (s <= 0) {
-        r = ((A << 32) + B) << (-s);
-        rb = 0;
-    } else if (s <= 32) {
-        r = (A << (32 - s)) + (B >> s);  // A 2^32 is a multiple of 2^s
-        rb = (B >> (s - 1)) & 1ull;
-    } else if (s < 96) {
-        const unsigned long long C = A + (B >> 32);  // the product shifted right by 32, exactly
-        const int t = s - 32;
-        r = C >> t;
-        rb = (C >> (t - 1)) & 1ull;
+// FP32 path: a weight at the tally scale rounded to FP32, a = fl32(w 2^S)
+// (the scaling by 2^S is exact in FP64, so this is one rounding of w's
+// significand to 24 bits)
+__device__ __forceinline__ float tally_weight(double w, double scale) { return __double2float_rn(w * scale); }
+
+// FP32 path: the tally contribution round(a f) of an FP32 factor f to an FP32
+// weight a > 0 at the tally scale, rounded half up, from the exact 48-bit
+// product P of the two 24-bit significands (one 32 x 32 -> 64-bit multiply):
+// a f = P 2^(ea + ef - 300) with ea, ef the biased exponents.  A zero or
+// subnormal operand counts as 0.
+__device__ __forceinline__ long long fx_mul24(float a, float f) {
+    const unsigned ua = __float_as_uint(a), uf = __float_as_uint(f);
+    const int ea = (int)((ua >> 23) & 0xFFu), ef = (int)((uf >> 23) & 0xFFu);
+    const unsigned long long P =
+        (unsigned long long)((ua & 0x7FFFFFu) | 0x800000u) * (unsigned long long)((uf & 0x7FFFFFu) | 0x800000u);
+    const int s = 300 - ea - ef;  // a f = P 2^-s
+    unsigned long long r;
+    if (s > 0) {
+        // P < 2^48, so the rounding increment never carries out of 64 bits,
+        // and s >= 49 leaves 0 (the shift is capped at 63)
+        const int t = s < 63 ? s : 63;
+        r = (P + (1ull << (t - 1))) >> t;
     } else {
-        return 0;  // the product is below 2^87
+        r = P << (-s < 15 ? -s : 15);  // a f >= 2^48, far above any tally scale's contributions
     }
-    r += rb;
-    return (b >> 31) ? -(long long)r : (long long)r;
+    if (ea == 0 || ef == 0) r = 0;
+    return (uf >> 31) ? -(long long)r : (long long)r;
 }
 
 }  // namespace hww

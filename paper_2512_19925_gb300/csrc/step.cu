@@ -594,7 +594,9 @@ __device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned 
 // census (time-crossing) tally contributions of one census particle, formed
 // exactly as the precision's event loop forms them at a census event:
 // FP64 round(x 2^S) of the FP64 products w, w mu, w (1/3 - mu^2); FP32 the
-// fixed-point weight W = round(w 2^S) and round(W mu), round(W (1/3 - mu^2))
+// fixed-point weight W = round(w 2^S) and, from the FP32 tally weight
+// a = fl32(w 2^S), round(a mu) and round(a (1/3 - mu^2)) (the event loop's
+// rule for its track-length contributions)
 __device__ __forceinline__ void census_terms(double w, double mu, double tscale, long long& c0, long long& c1,
                                              long long& c2) {
     c0 = to_fixed(w, tscale);
@@ -604,8 +606,9 @@ __device__ __forceinline__ void census_terms(double w, double mu, double tscale,
 __device__ __forceinline__ void census_terms(double w, float mu, double tscale, long long& c0, long long& c1,
                                              long long& c2) {
     c0 = to_fixed(w, tscale);
-    c1 = fx_mul(c0, mu);
-    c2 = fx_mul(c0, 1.0f / 3.0f - mu * mu);
+    const float a = tally_weight(w, tscale);
+    c1 = fx_mul24(a, mu);
+    c2 = fx_mul24(a, 1.0f / 3.0f - mu * mu);
 }
 
 // census tallies alone (Eq. ct-mc) of the census bank so far: the closures

@@ -7,12 +7,13 @@
 // (-ln u from the hardware base-2 logarithm).
 // Weights stay FP64 (the window tests compare their bit patterns, and the
 // split count and survival test use an FP32 ratio and a product in place of
-// FP64 divides); tally contributions are formed in
-// exact integer arithmetic from a fixed-point copy of the weight,
-//     round(W * f),   W = round(w 2^S) (64-bit),  f = l, l mu, l (1/3 - mu^2) (FP32),
-// i.e. the exact product of the 64-bit weight and the 24-bit mantissa of f,
-// rounded once (half up) at the tally scale.  The FP64 pipe, of which GB300
-// has little, is left to rare events (splits, roulette, leaks, census).
+// FP64 divides); tally contributions are formed in exact integer arithmetic
+// from an FP32 copy of the weight at the tally scale,
+//     round(a * f),   a = fl32(w 2^S),  f = l, l mu, l (1/3 - mu^2) (FP32),
+// i.e. the exact 48-bit product of two 24-bit significands (one wide integer
+// multiply), rounded once (half up) at the tally scale.  The FP64 pipe, of
+// which GB300 has little, is left to rare events (weight changes, leaks,
+// census).
 //
 // Both the single-problem kernel and the persistent batched kernel (one
 // tile of one problem at a time) run a warp-synchronous loop (run_warp): the
@@ -26,17 +27,17 @@ namespace {
 struct P32 {
     float xo, mu, inv_mu, tau;
     double w;
-    long long W;  // w 2^S rounded
+    float tw;     // tally weight: w 2^S rounded to FP32
     int cell;
     uint32_t id;
     uint64_t lin;
     uint32_t e;
 };
 
-// The comb-scale weight of a census particle from its tally-scale weight W:
-// W 2^(Sc - S), rounded to nearest (ties to even) when Sc < S; integer
-// arithmetic, so the common census event uses no FP64 instruction (the FP64
-// path rounds w 2^Sc directly; the two can differ in the last bit)
+// The comb-scale weight of a census particle from its fixed-point weight
+// W = round(w 2^S): W 2^(Sc - S), rounded to nearest (ties to even) when
+// Sc < S (the FP64 path rounds w 2^Sc directly; the two can differ in the
+// last bit)
 __device__ __forceinline__ unsigned long long comb_weight(long long W, int shift) {
     const unsigned long long u = (unsigned long long)W;
     if (shift <= 0) return u << (-shift);
@@ -69,10 +70,11 @@ __device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32
 // The event loop, warp-synchronous.
 //
 // All 32 lanes of a warp iterate together until the warp has no work left.
-// Each iteration hands work to the lanes without a track, draws the Philox
-// blocks of every lane at one site, takes one event of every live track (or
-// one setup step of a new track), stages the iteration's census particles
-// and sums its counts.  Work comes, in this order, from the warp's daughter
+// Each iteration hands work to the lanes without a track (deriving the
+// lineage keys of the daughters it hands out), draws the Philox blocks of
+// every lane at one site, takes one event of every live track (or one
+// direction-sampling step of a new track), stages the iteration's census
+// particles and sums its counts.  Work comes, in this order, from the warp's daughter
 // stack in shared memory (a split leaves its daughters there, so they spread
 // over the warp's idle lanes instead of queueing behind one lane), then from
 // the block's range of start-bank items (prefetched 32 at a time into shared
@@ -85,6 +87,8 @@ __device__ __forceinline__ void push_record(const TrackArgs<float>& a, const P32
 // full, and a track past its event budget, go to the record queue.
 constexpr int WARPS = TRACK_THREADS / 32;
 constexpr int WSTACK = 32;  // daughter-stack entries per warp
+constexpr int KSTACK = 64;  // lineage keys per warp, for the daughters of stack entries
+constexpr uint16_t NO_KEYS = 0xFFFFu;
 // Splits are queued per warp and processed (split count, daughter weight,
 // stack push) by the whole warp once SPLIT_BATCH of them wait, or when lanes
 // run out of other work: the split's arithmetic (two divisions and a
@@ -97,13 +101,19 @@ struct WarpShared {
     // daughter stack
     float xo[WARPS][WSTACK], mu[WARPS][WSTACK], tau[WARPS][WSTACK];
     double w[WARPS][WSTACK];
-    long long W[WARPS][WSTACK];
+    float tw[WARPS][WSTACK];
     int cell[WARPS][WSTACK];
     uint32_t id[WARPS][WSTACK], e[WARPS][WSTACK];
     uint64_t lin[WARPS][WSTACK];
     uint32_t jn[WARPS][WSTACK];  // next daughter to hand out (FRESH_DIRECTION: own isotropic directions)
     uint32_t je[WARPS][WSTACK];  // one past the last daughter
+    uint16_t kb[WARPS][WSTACK];  // daughter j's lineage key is key[kb + j] (NO_KEYS: derived when taken)
     int top[WARPS];              // entries in use (only atomics while tracks run)
+    // lineage keys of the daughters of stack entries, a stack beside the
+    // entries': an entry's keys lie above those of the entries below it, and
+    // its last daughter taken frees them
+    uint64_t key[WARPS][KSTACK];
+    int ktop[WARPS];
     // census staging
     float cx[WARPS][32], cmu[WARPS][32];
     double cw[WARPS][32];
@@ -111,9 +121,9 @@ struct WarpShared {
     uint32_t cid[WARPS][32];
     LinW clw[WARPS][32];
     // split queue: parents whose split is pending (state before the split,
-    // the event index of the split, the window center)
+    // the event index of the split)
     float sx[WARPS][32], smu[WARPS][32], stau[WARPS][32];
-    double sw[WARPS][32], sctr[WARPS][32];
+    double sw[WARPS][32];
     int scell[WARPS][32];
     uint32_t sid[WARPS][32], se[WARPS][32];
     uint64_t slin[WARPS][32];
@@ -137,8 +147,10 @@ constexpr int LANE_DAUGHTERS = EB_COUNT;  // lane holding the daughter count
 constexpr int LANE_MAXEV = EB_COUNT + 1;  // lane holding the largest event count
 
 // push a parent whose daughters [jn, je) are to be handed out (jn may carry
-// FRESH_DIRECTION); false when the warp's stack is full
-__device__ __forceinline__ bool stack_push(WarpShared& ws, int wp, const P32& b, uint32_t jn, uint32_t je) {
+// FRESH_DIRECTION), with their lineage keys at key[kb + j] or NO_KEYS; false
+// when the warp's stack is full
+__device__ __forceinline__ bool stack_push(WarpShared& ws, int wp, const P32& b, uint32_t jn, uint32_t je,
+                                           uint16_t kb) {
     const int slot = (int)warp_reserve((unsigned*)&ws.top[wp]);
     if (slot >= WSTACK) {
         atomicSub((unsigned*)&ws.top[wp], 1u);
@@ -148,13 +160,14 @@ __device__ __forceinline__ bool stack_push(WarpShared& ws, int wp, const P32& b,
     ws.mu[wp][slot] = b.mu;
     ws.tau[wp][slot] = b.tau;
     ws.w[wp][slot] = b.w;
-    ws.W[wp][slot] = b.W;
+    ws.tw[wp][slot] = b.tw;
     ws.cell[wp][slot] = b.cell;
     ws.id[wp][slot] = b.id;
     ws.e[wp][slot] = b.e;
     ws.lin[wp][slot] = b.lin;
     ws.jn[wp][slot] = jn;
     ws.je[wp][slot] = je;
+    ws.kb[wp][slot] = kb;
     return true;
 }
 
@@ -198,13 +211,16 @@ __device__ __forceinline__ void philox_pair(uint32_t r[4], uint32_t s[4], uint32
     }
 }
 
-// What a lane's Philox blocks compute in an iteration: the event's two words,
-// or one setup step of a new track (a daughter's lineage key, then for an
-// extra particle of a multiplying collision its own direction; a pulse
-// particle's birth direction).  A setup step takes the lane's iteration, so
-// every Philox block of the loop is drawn at one site, by all lanes at once.
+// What a lane's track needs next.  The daughters of a split get their
+// lineage keys when the split is processed (key stack); a daughter taken
+// without one (a multiplying collision's extra particle, a chunk record, a
+// split whose keys did not fit) is in M_LINEAGE and gets its key right after
+// the refill, from one Philox block the warp draws for all such lanes at
+// once, and goes on to its first event in the same iteration.  The other setup steps take the lane's
+// iteration with the event's Philox blocks: an extra particle of a
+// multiplying collision draws its own direction (M_DIRECTION), a pulse
+// particle its birth direction (M_BIRTH).
 enum LaneMode : int { M_EVENT = 0, M_LINEAGE = 1, M_DIRECTION = 2, M_BIRTH = 3 };
-constexpr uint32_t LIN_K0 = 0x4C494E45u, LIN_K1 = 0x41474521u;  // the lineage hash's key
 
 // 32-bit halves of a block-private 64-bit accumulator kept as two word
 // arrays (low words, then high words, of a row of I): exact modulo 2^64
@@ -259,14 +275,17 @@ __device__ __forceinline__ void census_flush(const TrackArgs<float>& a, WarpShar
 }
 
 // The warp's queued splits [0, n), one per lane: the split count, the
-// daughters' weight, and the daughters 0..nd-1 pushed to the daughter stack
-// (or queued as records when it is full); returns the daughters created
-// beyond the parents (this lane's share).  Whole warp, converged.
-__device__ __forceinline__ uint32_t process_splits(const TrackArgs<float>& a, WarpShared& ws, int wp, unsigned n,
+// daughters' weight, the daughters' lineage keys (into the warp's key stack,
+// consecutive in lane order, when it has room for all of them: the warp
+// draws them round by round, daughter j of every split in round j) and the
+// parent pushed to the daughter stack with its daughters 0..nd-1 (or queued
+// as records when the stack is full); returns the daughters created beyond
+// the parents (this lane's share).  Whole warp, converged.
+__device__ __noinline__ uint32_t process_splits(const TrackArgs<float>& a, WarpShared& ws, int wp, unsigned n,
                                                    unsigned lane, double tscale) {
-    uint32_t added = 0;
+    P32 b;
+    uint32_t nd = 0;
     if (lane < n) {
-        P32 b;
         b.xo = ws.sx[wp][lane];
         b.mu = ws.smu[wp][lane];
         b.tau = ws.stau[wp][lane];
@@ -275,7 +294,7 @@ __device__ __forceinline__ uint32_t process_splits(const TrackArgs<float>& a, Wa
         b.e = ws.se[wp][lane];
         b.lin = ws.slin[wp][lane];
         const double w = ws.sw[wp][lane];
-        const double ctr = ws.sctr[wp][lane];
+        const double ctr = a.ww_c[b.cell];
         // split count from an FP32 ratio (the FP32 path's own rounding; the FP64
         // quotient measured 3% slower at the workload)
         const float ndf = ceilf((float)w / (float)ctr);
@@ -283,20 +302,99 @@ __device__ __forceinline__ uint32_t process_splits(const TrackArgs<float>& a, Wa
         if (ndd > (double)MAX_DAUGHTERS) {
             atomicOr(a.err, ERR_DAUGHTERS);
         } else {
-            const uint32_t nd = (uint32_t)ndd;
+            nd = (uint32_t)ndd;
             b.w = w / (double)nd;
-            b.W = to_fixed(b.w, tscale);
-            added = nd - 1;
-            if (!stack_push(ws, wp, b, 0u, nd)) queue_daughters(a, b, 0u, nd, 0u);
+            b.tw = tally_weight(b.w, tscale);
         }
     }
+    uint32_t incl = nd;  // daughters of lanes 0..lane
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const int kt = ws.ktop[wp];
+    const bool keyed = total <= (uint32_t)(KSTACK - kt);  // uniform over the warp
+    const uint32_t kb = (uint32_t)kt + incl - nd;
+    if (keyed) {
+        const uint32_t rounds = __reduce_max_sync(0xffffffffu, nd);
+        for (uint32_t j = 0; j < rounds; ++j)
+            if (j < nd) ws.key[wp][kb + j] = lineage_hash(b.lin, b.e, j);
+    }
+    bool kept = false;  // pushed with its keys
+    if (nd) {
+        if (stack_push(ws, wp, b, 0u, nd, keyed ? (uint16_t)kb : NO_KEYS))
+            kept = keyed;
+        else
+            queue_daughters(a, b, 0u, nd, 0u);
+    }
+    // the key stack ends after the keys of the last parent that kept them
+    // (the keys of parents that went to the record queue are dropped)
+    const uint32_t kend = __reduce_max_sync(0xffffffffu, kept ? kb + nd : 0u);
     __syncwarp();
-    return added;
+    if (lane == 0 && keyed) ws.ktop[wp] = max(kt, (int)kend);
+    __syncwarp();
+    return nd ? nd - 1 : 0u;
+}
+
+// Hands daughters from the warp's stack (top entry first) to the lanes in
+// `need` until the stack is empty or each of them has one.  A daughter whose
+// lineage key was drawn with its split starts with its first event; the
+// others take the lineage step.  An entry's last daughter taken frees its
+// keys.  Whole warp, converged.
+__device__ __forceinline__ void pop_daughters(WarpShared& ws, int wp, unsigned& need, unsigned lane, unsigned lt,
+                                              P32& q, uint32_t& jd, bool& fresh, int& mode, bool& have, bool& got) {
+    while (need) {
+        const int top = *(volatile int*)&ws.top[wp];
+        if (top <= 0) break;
+        const int t = top - 1;
+        const uint32_t jn0 = ws.jn[wp][t], je = ws.je[wp][t];
+        const uint16_t kbt = ws.kb[wp][t];
+        const uint32_t fr = jn0 & FRESH_DIRECTION, jn = jn0 & ~FRESH_DIRECTION;
+        const uint32_t left = je - jn;
+        const uint32_t take = min((uint32_t)__popc(need), left);
+        const uint32_t rank = __popc(need & lt);
+        const bool mine = ((need >> lane) & 1u) && rank < take;
+        if (mine) {
+            q.xo = ws.xo[wp][t];
+            q.mu = ws.mu[wp][t];
+            q.tau = ws.tau[wp][t];
+            q.w = ws.w[wp][t];
+            q.tw = ws.tw[wp][t];
+            q.cell = ws.cell[wp][t];
+            q.id = ws.id[wp][t];
+            jd = jn + rank;
+            fresh = fr != 0;
+            if (kbt != NO_KEYS) {
+                q.lin = ws.key[wp][kbt + jd];
+                q.e = 0;
+                mode = fresh ? M_DIRECTION : M_EVENT;
+            } else {
+                q.lin = ws.lin[wp][t];
+                q.e = ws.e[wp][t];
+                mode = M_LINEAGE;
+            }
+            have = true;
+            got = true;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            if (take == left) {
+                ws.top[wp] = t;
+                if (kbt != NO_KEYS) ws.ktop[wp] = kbt;
+            } else {
+                ws.jn[wp][t] = (jn + take) | fr;
+            }
+        }
+        need &= ~__ballot_sync(0xffffffffu, mine);
+        __syncwarp();
+    }
 }
 
 struct BlockScalars {
     double wbar, tscale;
-    long long Wbar;
+    float twbar;  // the start weight's tally weight
+    int S;        // the tally scale's exponent
 };
 
 // Items [item0, item_end) of the block, from a block-shared counter; wave 0
@@ -349,49 +447,13 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
     int qb = 0;
     unsigned cfill = 0;            // staged census particles of the warp
     unsigned sqn = 0;              // queued splits of the warp
-    double sctr = 0.0;             // the window center of this lane's split
     unsigned long long mycnt = 0;  // lane k < EB_COUNT: counter kLaneStat[k]; then daughters, max events
     for (;;) {
         uint32_t nadd = 0;    // daughters created in this iteration (this lane's share)
         // ---- refill: daughters from the warp's stack, then new items ----
         unsigned need = __ballot_sync(0xffffffffu, !have);
         bool got = false;  // this lane took a new track this iteration
-        while (need) {
-            const int top = *(volatile int*)&ws.top[wp];
-            if (top <= 0) break;
-            const int t = top - 1;
-            const uint32_t jn0 = ws.jn[wp][t], je = ws.je[wp][t];
-            const uint32_t fr = jn0 & FRESH_DIRECTION, jn = jn0 & ~FRESH_DIRECTION;
-            const uint32_t left = je - jn;
-            const uint32_t take = min((uint32_t)__popc(need), left);
-            const uint32_t rank = __popc(need & lt);
-            const bool mine = ((need >> lane) & 1u) && rank < take;
-            if (mine) {
-                q.xo = ws.xo[wp][t];
-                q.mu = ws.mu[wp][t];
-                q.tau = ws.tau[wp][t];
-                q.w = ws.w[wp][t];
-                q.W = ws.W[wp][t];
-                q.cell = ws.cell[wp][t];
-                q.id = ws.id[wp][t];
-                q.lin = ws.lin[wp][t];
-                q.e = ws.e[wp][t];
-                jd = jn + rank;
-                fresh = fr != 0;
-                mode = M_LINEAGE;
-                have = true;
-                got = true;
-            }
-            __syncwarp();
-            if (lane == 0) {
-                if (take == left)
-                    ws.top[wp] = t;
-                else
-                    ws.jn[wp][t] = (jn + take) | fr;
-            }
-            need &= ~__ballot_sync(0xffffffffu, mine);
-            __syncwarp();
-        }
+        pop_daughters(ws, wp, need, lane, lt, q, jd, fresh, mode, have, got);
         if (need && ring_on) {
             // prefetched start-bank records; when the current slot runs out,
             // the other (already fetched) slot takes over and the emptied one
@@ -428,7 +490,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                     q.e = 0;
                     q.tau = a.tau0f;
                     q.w = bs.wbar;
-                    q.W = bs.Wbar;
+                    q.tw = bs.twbar;
                     q.xo = r.x;
                     q.mu = r.mu;
                     q.cell = r.cell;
@@ -460,14 +522,14 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                     q.e = 0;
                     q.tau = a.tau0f;
                     q.w = bs.wbar;
-                    q.W = bs.Wbar;
+                    q.tw = bs.twbar;
                     mode = M_BIRTH;
                 } else {
                     q.xo = a.rin.x[i];
                     q.mu = a.rin.mu[i];
                     q.tau = a.rin.tau[i];
                     q.w = a.rin.w[i];
-                    q.W = to_fixed(q.w, bs.tscale);
+                    q.tw = tally_weight(q.w, bs.tscale);
                     q.cell = a.rin.cell[i];
                     q.id = a.rin.id[i];
                     q.lin = a.rin.lin[i];
@@ -478,7 +540,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                         // rest go to the warp's stack (or back to the queue)
                         const uint32_t js = a.rin.jstart[i];
                         const uint32_t j0 = js & ~FRESH_DIRECTION;
-                        if (jc > 1 && !stack_push(ws, wp, q, js + 1u, j0 + jc))
+                        if (jc > 1 && !stack_push(ws, wp, q, js + 1u, j0 + jc, NO_KEYS))
                             queue_daughters(a, q, j0 + 1u, j0 + jc, js & FRESH_DIRECTION);
                         jd = j0;
                         fresh = (js & FRESH_DIRECTION) != 0;
@@ -494,42 +556,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
             // lanes still without work: the queued splits' daughters
             nadd += process_splits(a, ws, wp, sqn, lane, bs.tscale);
             sqn = 0;
-            while (need) {
-                const int top = *(volatile int*)&ws.top[wp];
-                if (top <= 0) break;
-                const int t = top - 1;
-                const uint32_t jn0 = ws.jn[wp][t], je = ws.je[wp][t];
-                const uint32_t fr = jn0 & FRESH_DIRECTION, jn = jn0 & ~FRESH_DIRECTION;
-                const uint32_t left = je - jn;
-                const uint32_t take = min((uint32_t)__popc(need), left);
-                const uint32_t rank = __popc(need & lt);
-                const bool mine = ((need >> lane) & 1u) && rank < take;
-                if (mine) {
-                    q.xo = ws.xo[wp][t];
-                    q.mu = ws.mu[wp][t];
-                    q.tau = ws.tau[wp][t];
-                    q.w = ws.w[wp][t];
-                    q.W = ws.W[wp][t];
-                    q.cell = ws.cell[wp][t];
-                    q.id = ws.id[wp][t];
-                    q.lin = ws.lin[wp][t];
-                    q.e = ws.e[wp][t];
-                    jd = jn + rank;
-                    fresh = fr != 0;
-                    mode = M_LINEAGE;
-                    have = true;
-                    got = true;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    if (take == left)
-                        ws.top[wp] = t;
-                    else
-                        ws.jn[wp][t] = (jn + take) | fr;
-                }
-                need &= ~__ballot_sync(0xffffffffu, mine);
-                __syncwarp();
-            }
+            pop_daughters(ws, wp, need, lane, lt, q, jd, fresh, mode, have, got);
         }
         if (got) {
             evs = 0;
@@ -541,6 +568,18 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
         if (!__any_sync(0xffffffffu, have)) {
             if (!sqn) break;
             continue;  // the queued splits go to the lanes at the next refill
+        }
+        // ---- daughters taken in this refill without a lineage key: their
+        // keys (one Philox block for the warp), so that they take their
+        // first event now ----
+        if (__any_sync(0xffffffffu, have && mode == M_LINEAGE)) {
+            const uint64_t nl = lineage_hash(q.lin, q.e, jd);
+            if (have && mode == M_LINEAGE) {
+                q.lin = nl;
+                q.e = 0;
+                mode = fresh ? M_DIRECTION : M_EVENT;
+                if (mode == M_EVENT) q.inv_mu = __frcp_rn(q.mu);
+            }
         }
 
         unsigned eb = 0;      // outcome bits
@@ -556,19 +595,11 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
         }
         // ---- the iteration's Philox blocks, all lanes at once ----
         uint32_t r[4], r2[4];
-        uint32_t ka0 = k0, ka1 = k1;
         if (mode == M_EVENT) {
             r[0] = q.id;
             r[1] = (uint32_t)q.lin;
             r[2] = (uint32_t)(q.lin >> 32);
             r[3] = 2u * q.e;
-        } else if (mode == M_LINEAGE) {
-            r[0] = (uint32_t)q.lin;
-            r[1] = (uint32_t)(q.lin >> 32);
-            r[2] = q.e;
-            r[3] = jd;
-            ka0 = LIN_K0;
-            ka1 = LIN_K1;
         } else if (mode == M_DIRECTION) {
             r[0] = q.id;
             r[1] = (uint32_t)q.lin;
@@ -584,15 +615,11 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
         r2[1] = (uint32_t)q.lin;
         r2[2] = (uint32_t)(q.lin >> 32);
         r2[3] = 2u * q.e + 1u;
-        philox_pair(r, r2, ka0, ka1, k0, k1);
+        philox_pair(r, r2, k0, k1, k0, k1);
 
         if (have && mode != M_EVENT) {
             // ---- a setup step of a new track ----
-            if (mode == M_LINEAGE) {
-                q.lin = ((uint64_t)r[1] << 32) | r[0];
-                q.e = 0;
-                mode = fresh ? M_DIRECTION : M_EVENT;
-            } else if (mode == M_DIRECTION) {
+            if (mode == M_DIRECTION) {
                 q.mu = 2.0f * u01f(r[1]) - 1.0f;
                 mode = M_EVENT;
             } else {  // the pulse: isotropic birth direction, mirrored into a reflecting wall's side
@@ -631,9 +658,9 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
             }
             const float f3 = 1.0f / 3.0f - q.mu * q.mu;
             {
-                const long long c0 = fx_mul(q.W, l);
-                sadd_split(&sJl[k], &sJh[k], fx_mul(q.W, l * q.mu));
-                sadd_split(&sFl[k], &sFh[k], fx_mul(q.W, l * f3));
+                const long long c0 = fx_mul24(q.tw, l);
+                sadd_split(&sJl[k], &sJh[k], fx_mul24(q.tw, l * q.mu));
+                sadd_split(&sFl[k], &sFh[k], fx_mul24(q.tw, l * f3));
                 if (qb == b_blk)
                     sadd_split(&sBl[k], &sBh[k], c0);
                 else
@@ -696,7 +723,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                         // own lineages and isotropic directions
                         P32 b = q;
                         b.e = e_ev | SECONDARY_EVENT;
-                        if (!stack_push(ws, wp, b, 1u | FRESH_DIRECTION, nsec))
+                        if (!stack_push(ws, wp, b, 1u | FRESH_DIRECTION, nsec, NO_KEYS))
                             queue_daughters(a, b, 1u, nsec, FRESH_DIRECTION);
                         nadd += nsec - 1;
                     }
@@ -711,7 +738,6 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                     // all its daughters come back through the daughter stack
                     eb |= 1u << EB_SPLIT;
                     q.e = e_ev;
-                    sctr = a.ww_c[kc];
                     have = false;
                 } else if (dgt(hl.y, q.w)) {
                     const double ctr = a.ww_c[kc];
@@ -719,7 +745,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                     const double ur = u01(r2[2], r2[3]);
                     if (ur * ctr < q.w) {
                         q.w = ctr;
-                        q.W = to_fixed(ctr, bs.tscale);
+                        q.tw = tally_weight(ctr, bs.tscale);
                         eb |= 1u << EB_RSURV;
                     } else {
                         eb |= 1u << EB_RKILL;
@@ -745,7 +771,6 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                     ws.smu[wp][pos] = q.mu;
                     ws.stau[wp][pos] = q.tau;
                     ws.sw[wp][pos] = q.w;
-                    ws.sctr[wp][pos] = sctr;
                     ws.scell[wp][pos] = q.cell;
                     ws.sid[wp][pos] = q.id;
                     ws.se[wp][pos] = q.e;
@@ -775,7 +800,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                     ws.cw[wp][pos] = q.w;
                     ws.ccell[wp][pos] = q.cell;
                     ws.cid[wp][pos] = q.id;
-                    ws.clw[wp][pos] = LinW{q.lin, comb_weight(q.W, a.comb_shift)};
+                    ws.clw[wp][pos] = LinW{q.lin, comb_weight(fixed_bits(q.w, bs.S), a.comb_shift)};
                 }
                 cfill += nc;
                 __syncwarp();
@@ -869,9 +894,13 @@ __global__ void __launch_bounds__(TRACK_THREADS, 3) track32_kernel(TrackArgs<flo
         s_next = 0;
         s_bs.wbar = a.sd->wbar;
         s_bs.tscale = a.sd->tscale;
-        s_bs.Wbar = a.sd->Wbar;
+        s_bs.twbar = tally_weight(a.sd->wbar, a.sd->tscale);
+        s_bs.S = a.sd->S;
     }
-    if (threadIdx.x < WARPS) s_ws.top[threadIdx.x] = 0;
+    if (threadIdx.x < WARPS) {
+        s_ws.top[threadIdx.x] = 0;
+        s_ws.ktop[threadIdx.x] = 0;
+    }
     if (threadIdx.x < ST_COUNT) s_stats[threadIdx.x] = 0;
     for (int i = threadIdx.x; i < 2 * ROWS32 * I; i += blockDim.x) tl32[i] = 0;
     __syncthreads();
@@ -919,7 +948,10 @@ __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const T
     __shared__ int s_p;
     __shared__ unsigned s_next;
     unsigned* tl32 = reinterpret_cast<unsigned*>(sm);
-    if (threadIdx.x < WARPS) s_ws.top[threadIdx.x] = 0;
+    if (threadIdx.x < WARPS) {
+        s_ws.top[threadIdx.x] = 0;
+        s_ws.ktop[threadIdx.x] = 0;
+    }
     const long long total = plan.tile_off[plan.P];
     int cur = -1, Ic = 0;
     for (;;) {
@@ -952,7 +984,8 @@ __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const T
             if (threadIdx.x == 0) {
                 s_bs.wbar = A.sd->wbar;
                 s_bs.tscale = A.sd->tscale;
-                s_bs.Wbar = A.sd->Wbar;
+                s_bs.twbar = tally_weight(A.sd->wbar, A.sd->tscale);
+                s_bs.S = A.sd->S;
             }
             if (threadIdx.x < ST_COUNT) s_stats[threadIdx.x] = 0;
             cur = p;
