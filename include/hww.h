@@ -64,6 +64,8 @@ typedef enum {
 
 enum { HWW_BC_VACUUM = 0, HWW_BC_REFLECT = 1 };
 enum { HWW_FP64 = 0, HWW_FP32_TRACK = 1 };
+/* FP32 tracking kernels (hww_set_tracking) */
+enum { HWW_TRACK_WARP = 0, HWW_TRACK_EVENT = 1 };
 enum { HWW_FILTER_NONE = 0, HWW_FILTER_MA = 1, HWW_FILTER_FOURIER = 2 };
 /* window modes: HLOSM centers (the paper's method), analog (no windows),
  * lagged (centers from the previous step's track-length flux) */
@@ -324,6 +326,23 @@ typedef struct {
     int64_t census_capacity, queue_capacity;
 } hww_counters;
 
+/* The kernel that tracks an FP32 problem's start-bank particles (the events
+ * of Sec. 2 and the tallies of Eq. phi-mc):
+ *   HWW_TRACK_WARP  (default) a warp-synchronous history loop: each lane
+ *                   follows one track event by event and takes new work
+ *                   (daughters from its warp's stack, start particles) when
+ *                   its track ends;
+ *   HWW_TRACK_EVENT an event-based loop: two 512-thread blocks per SM each
+ *                   keep a ring of live particles in shared memory and
+ *                   advance all of them by one event per pass, appending
+ *                   survivors and daughters after a block-wide scan.
+ * Both draw the same random numbers and do the same arithmetic, so a step
+ * gives bit-identical tallies, census and next start bank with either; the
+ * record waves (overflow, multiplying collisions' extra particles) always
+ * run the warp loop.  HWW_ERR_ARG for an FP64 problem, an unknown kind, or
+ * a mesh whose tallies (24 I bytes) leave a block less than 48 KB of ring.
+ * Applies from the next step. */
+hww_status hww_set_tracking(hww_problem* p, int32_t kind);
 /* Turn CUDA-event timing of the tracking launches on (1) or off (0). */
 hww_status hww_set_timing(hww_problem* p, int32_t enable);
 hww_status hww_get_counters(const hww_problem* p, hww_counters* out);

@@ -25,6 +25,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of mem
           7: "CUDA runtime error", 8: "no CUDA device"}
 BC_VACUUM, BC_REFLECT = 0, 1
 FP64, FP32_TRACK = 0, 1
+TRACK_WARP, TRACK_EVENT = 0, 1
 FILTER_NONE, FILTER_MA, FILTER_FOURIER = 0, 1, 2
 MODE_HWW, MODE_ANALOG, MODE_LWW = 0, 1, 2
 SCALE_MEAN_WEIGHT, SCALE_LITERAL = 0, 1
@@ -81,7 +82,7 @@ SYMBOLS = ["create_problem", "set_cross_sections", "set_ww_params", "set_ww_cent
            "hww_status_string", "hww_last_error_string", "hww_losm_solve", "hww_philox_block", "hww_set_timing",
            "hww_get_counters", "hww_reset_counters", "create_batch", "batch_problem", "batch_set_tuning",
            "run_batch_step", "batch_member_stats", "destroy_batch", "get_deriv_tallies", "vjp_state_size", "set_ww_updates",
-           "save_vjp_state", "losm_vjp", "hww_dfma_rate"]
+           "save_vjp_state", "losm_vjp", "hww_dfma_rate", "hww_set_tracking"]
 
 
 def library_path() -> str:
@@ -119,6 +120,7 @@ def load(build_if_missing: bool = True):
         L.get_census.argtypes = [vp, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
                                  C.POINTER(C.c_uint64), C.c_int64, C.POINTER(C.c_int64)]
         L.hww_set_timing.argtypes = [vp, C.c_int32]
+        L.hww_set_tracking.argtypes = [vp, C.c_int32]
         L.hww_get_counters.argtypes = [vp, C.POINTER(Counters)]
         L.hww_reset_counters.argtypes = [vp]
         L.create_batch.argtypes = [C.POINTER(ProblemDesc), C.c_int32, vp, C.c_int32, C.POINTER(vp)]
@@ -419,6 +421,12 @@ class Problem:
 
     def set_timing(self, enable=True):
         _check(load().hww_set_timing(self._h, 1 if enable else 0), "hww_set_timing")
+
+    def set_tracking(self, kind):
+        """FP32 problems: TRACK_WARP (warp-synchronous history loop, the
+        default) or TRACK_EVENT (event-based pool loop) for the start-bank
+        wave; both give bit-identical steps."""
+        _check(load().hww_set_tracking(self._h, int(kind)), "hww_set_tracking")
 
     def counters(self):
         c = Counters()

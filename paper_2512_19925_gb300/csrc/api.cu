@@ -113,6 +113,8 @@ struct hww_problem {
     long long q_peak = 0;  // largest record count a wave produced in the last pass
     // launch accounting
     int timing = 0;
+    int track_kind = HWW_TRACK_WARP;  // FP32 wave-0 tracking kernel (hww_set_tracking)
+    int ev_cap = 0;                   // the event kernel's ring capacity
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     long long kernel_launches = 0, track_launches = 0;
     double track_ms = 0.0;
@@ -358,7 +360,10 @@ void launch_track(hww_problem* p, const TrackArgs<double>& a) {
 }
 void launch_track(hww_problem* p, const TrackArgs<float>& a) {
     if (p->timing) cudaEventRecord(p->ev_a, p->stream);
-    launch_track_fp32(a, p->track_grid, TRACK_BLOCK, p->track_smem, p->stream);
+    if (p->track_kind == HWW_TRACK_EVENT && a.from_bank)
+        launch_track_fp32_event(a, p->nsm, p->ev_cap, p->stream);
+    else
+        launch_track_fp32(a, p->track_grid, TRACK_BLOCK, p->track_smem, p->stream);
     if (p->timing) cudaEventRecord(p->ev_b, p->stream);
     ++p->kernel_launches;
     ++p->track_launches;
@@ -1403,6 +1408,20 @@ hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, 
     cudaFreeAsync(tmp, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     return cuda_status(e);
+}
+
+hww_status hww_set_tracking(hww_problem* p, int32_t kind) {
+    if (!p || (kind != HWW_TRACK_WARP && kind != HWW_TRACK_EVENT)) return HWW_ERR_ARG;
+    if (kind == HWW_TRACK_EVENT) {
+        if (!p->fp32) return HWW_ERR_ARG;
+        HWW_CK(cudaSetDevice(p->device));
+        const int cap = ev_ring_cap(p->I);
+        if (cap == 0) return HWW_ERR_ARG;
+        if (track_event_smem_optin_fp32(p->I, cap) != 0) return HWW_ERR_CUDA;
+        p->ev_cap = cap;
+    }
+    p->track_kind = kind;
+    return HWW_OK;
 }
 
 hww_status hww_set_timing(hww_problem* p, int32_t enable) {

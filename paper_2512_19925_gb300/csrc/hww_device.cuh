@@ -185,6 +185,26 @@ __host__ __device__ __forceinline__ double pow2(int e) {
 // significand to 24 bits)
 __device__ __forceinline__ float tally_weight(double w, double scale) { return __double2float_rn(w * scale); }
 
+// fl32(x 2^k) for x > 0 (nearest, ties to even) from the bits of x, in
+// integer arithmetic: the 53-bit significand rounded to 24 bits, the
+// exponent moved by k (a carry out of the significand moves into the
+// exponent field by itself).  Where the result would not be a normal FP32
+// number, the FP64 conversion gives it (the same value).  The hot loops use
+// this instead of FP64 instructions (GB300's FP64 pipe is narrow).
+__device__ __forceinline__ float fl32_scaled(double x, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ed = (int)(b >> 52);  // x > 0: no sign bit
+    const int e = ed - 1023 + k + 127;
+    if (ed == 0 || ed == 0x7FF || e < 1 || e > 254) return __double2float_rn(x * pow2(k));
+    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const unsigned long long q = m >> 29, r = m & 0x1FFFFFFFull;
+    const unsigned long long f = q + ((r > 0x10000000ull || (r == 0x10000000ull && (q & 1ull))) ? 1ull : 0ull);
+    return __uint_as_float(((unsigned)e << 23) + (unsigned)(f - 0x800000ull));
+}
+
+// the tally weight of the FP32 path, fl32(w 2^S), without FP64 instructions
+__device__ __forceinline__ float tally_weight_bits(double w, int S) { return fl32_scaled(w, S); }
+
 // FP32 path: the tally contribution round(a f) of an FP32 factor f to an FP32
 // weight a > 0 at the tally scale, rounded half up, from the exact 48-bit
 // product P of the two 24-bit significands (one 32 x 32 -> 64-bit multiply):

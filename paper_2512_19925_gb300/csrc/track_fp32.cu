@@ -19,6 +19,8 @@
 // tile of one problem at a time) run a warp-synchronous loop (run_warp): the
 // lanes of a warp take their events together and share a daughter stack, so
 // the daughters of a split spread over the warp's idle lanes.
+#include <algorithm>
+
 #include "track_common.cuh"
 
 namespace hww {
@@ -274,6 +276,38 @@ __device__ __forceinline__ void census_flush(const TrackArgs<float>& a, WarpShar
     __syncwarp();
 }
 
+// A split's daughter count ceil(w / ww), at least 2, from the FP32 ratio of
+// the FP32 roundings of w and ww (the FP32 path's own rounding; the
+// roundings are formed from the bits, so no FP64 instruction runs); 0, with
+// the error flag set, above MAX_DAUGHTERS.
+__device__ __forceinline__ uint32_t split_count(const TrackArgs<float>& a, double w, double ctr) {
+    const float ndf = fmaxf(ceilf(fl32_scaled(w, 0) / fl32_scaled(ctr, 0)), 2.0f);
+    if (!(ndf <= (float)MAX_DAUGHTERS)) {
+        atomicOr(a.err, ERR_DAUGHTERS);
+        return 0u;
+    }
+    return (uint32_t)ndf;
+}
+
+// 1/nd rounded to FP64 for nd = 1..64 (entry 0 unused), by the compiler
+__device__ const double kInvNd[65] = {
+    0.0,
+    1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8,
+    1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16,
+    1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24,
+    1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32,
+    1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39, 1.0 / 40,
+    1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47, 1.0 / 48,
+    1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55, 1.0 / 56,
+    1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63, 1.0 / 64};
+
+// the weight of each daughter of a split into nd: w times fl64(1/nd), one
+// FP64 multiply (the FP32 path's rule; an FP64 division is about ten
+// instructions on GB300's narrow FP64 pipe)
+__device__ __forceinline__ double daughter_weight(double w, uint32_t nd) {
+    return w * (nd <= 64u ? kInvNd[nd] : 1.0 / (double)nd);
+}
+
 // The warp's queued splits [0, n), one per lane: the split count, the
 // daughters' weight, the daughters' lineage keys (into the warp's key stack,
 // consecutive in lane order, when it has room for all of them: the warp
@@ -282,7 +316,7 @@ __device__ __forceinline__ void census_flush(const TrackArgs<float>& a, WarpShar
 // as records when the stack is full); returns the daughters created beyond
 // the parents (this lane's share).  Whole warp, converged.
 __device__ __noinline__ uint32_t process_splits(const TrackArgs<float>& a, WarpShared& ws, int wp, unsigned n,
-                                                   unsigned lane, double tscale) {
+                                                   unsigned lane, int S) {
     P32 b;
     uint32_t nd = 0;
     if (lane < n) {
@@ -294,17 +328,10 @@ __device__ __noinline__ uint32_t process_splits(const TrackArgs<float>& a, WarpS
         b.e = ws.se[wp][lane];
         b.lin = ws.slin[wp][lane];
         const double w = ws.sw[wp][lane];
-        const double ctr = a.ww_c[b.cell];
-        // split count from an FP32 ratio (the FP32 path's own rounding; the FP64
-        // quotient measured 3% slower at the workload)
-        const float ndf = ceilf((float)w / (float)ctr);
-        const double ndd = (double)fmaxf(ndf, 2.0f);
-        if (ndd > (double)MAX_DAUGHTERS) {
-            atomicOr(a.err, ERR_DAUGHTERS);
-        } else {
-            nd = (uint32_t)ndd;
-            b.w = w / (double)nd;
-            b.tw = tally_weight(b.w, tscale);
+        nd = split_count(a, w, a.ww_c[b.cell]);
+        if (nd) {
+            b.w = daughter_weight(w, nd);
+            b.tw = tally_weight_bits(b.w, S);
         }
     }
     uint32_t incl = nd;  // daughters of lanes 0..lane
@@ -397,11 +424,21 @@ struct BlockScalars {
     int S;        // the tally scale's exponent
 };
 
-// Items [item0, item_end) of the block, from a block-shared counter; wave 0
-// items are start-bank particles, later waves' items records.
-__device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long long item0, const long long item_end,
-                                         unsigned* s_next, const int b_blk, const uint32_t b_end, unsigned* tl32,
-                                         WarpShared& ws, const BlockScalars& bs, unsigned long long* s_stats) {
+// One event of a live track: the flight to the nearest of census, the
+// cell edge and a collision, its track-length tallies (block-private J, F
+// and batch-row words; another batch's row and the leak tallies in global
+// memory), the move and the outcome, with the window test after a crossing
+// or a scatter.  Sets the outcome bits in eb; a track that ended (census,
+// leak, absorption, roulette kill) or splits gets have = false (a split
+// keeps e = the split's event index, the key of its daughters' lineages,
+// and the caller places its daughters), e_end the event count of an ended
+// track.  The extra particles of a multiplying collision go to
+// emit_secondaries(state at the collision, n) (daughters 1..n-1).
+template <class EmitSecondaries>
+__device__ __forceinline__ void take_event(const TrackArgs<float>& a, const BlockScalars& bs, const int ww_on,
+                                           unsigned* tl32, const int qb, const int b_blk, const uint32_t r[4],
+                                           const uint32_t r2[4], P32& q, bool& have, unsigned& eb,
+                                           uint32_t& e_end, EmitSecondaries&& emit_secondaries) {
     const int I = a.I;
     unsigned* sJl = tl32;
     unsigned* sJh = tl32 + I;
@@ -409,6 +446,130 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
     unsigned* sFh = tl32 + 3 * I;
     unsigned* sBl = tl32 + 4 * I;
     unsigned* sBh = tl32 + 5 * I;
+    const float uf = u01f(r[1]);
+    const float uc = u01f(r[3]);
+    const int k = q.cell;
+    const float4 cf = __ldg(&a.cellf[k]);  // width, 1/Sigma_t, c
+    const float dxk = cf.x;
+    // the hardware base-2 logarithm times ln 2: within 2^-21.41 absolute for
+    // u in [1/2, 1) and 3 ulp below (the CUDA intrinsic's stated bounds)
+    const float dcoll = -__logf(uf) * cf.y;
+    const float dedge = ((q.mu > 0.0f) ? (dxk - q.xo) : -q.xo) * q.inv_mu;
+    const float dcens = q.tau;
+    int ev;
+    float l;
+    if (dcens <= dedge && dcens <= dcoll) {
+        ev = 0;
+        l = dcens;
+    } else if (dedge <= dcoll) {
+        ev = 1;
+        l = dedge;
+    } else {
+        ev = 2;
+        l = dcoll;
+    }
+    const float f3 = 1.0f / 3.0f - q.mu * q.mu;
+    {
+        const long long c0 = fx_mul24(q.tw, l);
+        sadd_split(&sJl[k], &sJh[k], fx_mul24(q.tw, l * q.mu));
+        sadd_split(&sFl[k], &sFh[k], fx_mul24(q.tw, l * f3));
+        if (qb == b_blk)
+            sadd_split(&sBl[k], &sBh[k], c0);
+        else
+            add128(&a.batch[(long long)qb * I + k], c0);
+    }
+    if (ev != 1) q.xo = fminf(fmaxf(fmaf(q.mu, l, q.xo), 0.0f), dxk);
+    q.tau = (ev == 0) ? 0.0f : q.tau - l;
+    const uint32_t e_ev = q.e;
+    q.e = q.e + 1;
+    bool ww = false;
+    if (ev == 0) {
+        // census: staged below (its tallies come from the census pass)
+        eb |= 1u << EB_CENSUS;
+        e_end = q.e;
+        have = false;
+    } else if (ev == 1) {
+        eb |= 1u << EB_CROSS;
+        const int nk = (q.mu > 0.0f) ? k + 1 : k - 1;
+        if (nk < 0 || nk >= I) {
+            const int side = (nk < 0) ? 0 : 1;
+            const int bc = side ? a.bc_r : a.bc_l;
+            if (bc == 0) {
+                const double amu = fabs((double)q.mu);
+                const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
+                const double wi = q.w * ia;
+                const double dm2 = (double)q.mu * (double)q.mu;
+                add128(&a.bnd[3 * side + 0], to_fixed(wi, bs.tscale));
+                add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - dm2), bs.tscale));
+                add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), bs.tscale));
+                eb |= 1u << EB_LEAK;
+                e_end = q.e;
+                have = false;
+            } else {
+                q.mu = -q.mu;
+                q.inv_mu = -q.inv_mu;
+                q.xo = side ? dxk : 0.0f;
+                eb |= 1u << EB_REFL;
+                ww = true;
+            }
+        } else {
+            q.cell = nk;
+            q.xo = (q.mu > 0.0f) ? 0.0f : __ldg(&a.cellf[nk]).x;
+            ww = true;
+        }
+    } else {
+        eb |= 1u << EB_COLL;
+        // the collision emits floor(c) + [u_c < c - floor(c)] particles (mean c)
+        const float cfl = floorf(cf.z);
+        const uint32_t nsec = (uint32_t)cfl + ((uc < cf.z - cfl) ? 1u : 0u);
+        if (nsec == 0) {
+            eb |= 1u << EB_ABS;
+            e_end = q.e;
+            have = false;
+        } else {
+            q.mu = 2.0f * u01f(r2[1]) - 1.0f;
+            q.inv_mu = __frcp_rn(q.mu);
+            if (nsec > 1) {
+                // the other emitted particles: daughters with their
+                // own lineages and isotropic directions
+                P32 b = q;
+                b.e = e_ev | SECONDARY_EVENT;
+                emit_secondaries(b, nsec);
+            }
+            ww = true;
+        }
+    }
+    if (ww && ww_on) {
+        const int kc = q.cell;
+        const double2 hl = __ldg(&a.ww_hl[kc]);  // ceiling, floor
+        if (dgt(q.w, hl.x)) {
+            // a split: the caller places the daughters
+            eb |= 1u << EB_SPLIT;
+            q.e = e_ev;
+            have = false;
+        } else if (dgt(hl.y, q.w)) {
+            const double ctr = a.ww_c[kc];
+            // survive iff u < w / ww, tested as u ww < w (no divide)
+            const double ur = u01(r2[2], r2[3]);
+            if (ur * ctr < q.w) {
+                q.w = ctr;
+                q.tw = tally_weight_bits(ctr, bs.S);
+                eb |= 1u << EB_RSURV;
+            } else {
+                eb |= 1u << EB_RKILL;
+                e_end = q.e;
+                have = false;
+            }
+        }
+    }
+}
+
+// Items [item0, item_end) of the block, from a block-shared counter; wave 0
+// items are start-bank particles, later waves' items records.
+__device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long long item0, const long long item_end,
+                                         unsigned* s_next, const int b_blk, const uint32_t b_end, unsigned* tl32,
+                                         WarpShared& ws, const BlockScalars& bs, unsigned long long* s_stats) {
+    const int I = a.I;
     const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
     const int ww_on = a.sd->ww_on;
     const int birth = a.sd->birth;
@@ -529,7 +690,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                     q.mu = a.rin.mu[i];
                     q.tau = a.rin.tau[i];
                     q.w = a.rin.w[i];
-                    q.tw = tally_weight(q.w, bs.tscale);
+                    q.tw = tally_weight_bits(q.w, bs.S);
                     q.cell = a.rin.cell[i];
                     q.id = a.rin.id[i];
                     q.lin = a.rin.lin[i];
@@ -554,7 +715,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
         }
         if (need && sqn) {
             // lanes still without work: the queued splits' daughters
-            nadd += process_splits(a, ws, wp, sqn, lane, bs.tscale);
+            nadd += process_splits(a, ws, wp, sqn, lane, bs.S);
             sqn = 0;
             pop_daughters(ws, wp, need, lane, lt, q, jd, fresh, mode, have, got);
         }
@@ -634,126 +795,12 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
             if (mode == M_EVENT) q.inv_mu = __frcp_rn(q.mu);
         } else if (have) {
             // ---- one event ----
-            const float uf = u01f(r[1]);
-            const float uc = u01f(r[3]);
-            const int k = q.cell;
-            const float4 cf = __ldg(&a.cellf[k]);  // width, 1/Sigma_t, c
-            const float dxk = cf.x;
-            // the hardware base-2 logarithm times ln 2: within 2^-21.41 absolute for
-            // u in [1/2, 1) and 3 ulp below (the CUDA intrinsic's stated bounds)
-            const float dcoll = -__logf(uf) * cf.y;
-            const float dedge = ((q.mu > 0.0f) ? (dxk - q.xo) : -q.xo) * q.inv_mu;
-            const float dcens = q.tau;
-            int ev;
-            float l;
-            if (dcens <= dedge && dcens <= dcoll) {
-                ev = 0;
-                l = dcens;
-            } else if (dedge <= dcoll) {
-                ev = 1;
-                l = dedge;
-            } else {
-                ev = 2;
-                l = dcoll;
-            }
-            const float f3 = 1.0f / 3.0f - q.mu * q.mu;
-            {
-                const long long c0 = fx_mul24(q.tw, l);
-                sadd_split(&sJl[k], &sJh[k], fx_mul24(q.tw, l * q.mu));
-                sadd_split(&sFl[k], &sFh[k], fx_mul24(q.tw, l * f3));
-                if (qb == b_blk)
-                    sadd_split(&sBl[k], &sBh[k], c0);
-                else
-                    add128(&a.batch[(long long)qb * I + k], c0);
-            }
-            if (ev != 1) q.xo = fminf(fmaxf(fmaf(q.mu, l, q.xo), 0.0f), dxk);
-            q.tau = (ev == 0) ? 0.0f : q.tau - l;
-            const uint32_t e_ev = q.e;
-            q.e = q.e + 1;
             ++evs;
-            bool ww = false;
-            if (ev == 0) {
-                // census: staged below (its tallies come from the census pass)
-                eb |= 1u << EB_CENSUS;
-                e_end = q.e;
-                have = false;
-            } else if (ev == 1) {
-                eb |= 1u << EB_CROSS;
-                const int nk = (q.mu > 0.0f) ? k + 1 : k - 1;
-                if (nk < 0 || nk >= I) {
-                    const int side = (nk < 0) ? 0 : 1;
-                    const int bc = side ? a.bc_r : a.bc_l;
-                    if (bc == 0) {
-                        const double amu = fabs((double)q.mu);
-                        const double ia = (amu < GRAZE_MU) ? 2.0 / GRAZE_MU : 1.0 / amu;
-                        const double wi = q.w * ia;
-                        const double dm2 = (double)q.mu * (double)q.mu;
-                        add128(&a.bnd[3 * side + 0], to_fixed(wi, bs.tscale));
-                        add128(&a.bnd[3 * side + 1], to_fixed(wi * (1.0 / 3.0 - dm2), bs.tscale));
-                        add128(&a.bnd[3 * side + 2], to_fixed(wi * (0.5 - amu), bs.tscale));
-                        eb |= 1u << EB_LEAK;
-                        e_end = q.e;
-                        have = false;
-                    } else {
-                        q.mu = -q.mu;
-                        q.inv_mu = -q.inv_mu;
-                        q.xo = side ? dxk : 0.0f;
-                        eb |= 1u << EB_REFL;
-                        ww = true;
-                    }
-                } else {
-                    q.cell = nk;
-                    q.xo = (q.mu > 0.0f) ? 0.0f : __ldg(&a.cellf[nk]).x;
-                    ww = true;
-                }
-            } else {
-                eb |= 1u << EB_COLL;
-                // the collision emits floor(c) + [u_c < c - floor(c)] particles (mean c)
-                const float cfl = floorf(cf.z);
-                const uint32_t nsec = (uint32_t)cfl + ((uc < cf.z - cfl) ? 1u : 0u);
-                if (nsec == 0) {
-                    eb |= 1u << EB_ABS;
-                    e_end = q.e;
-                    have = false;
-                } else {
-                    q.mu = 2.0f * u01f(r2[1]) - 1.0f;
-                    q.inv_mu = __frcp_rn(q.mu);
-                    if (nsec > 1) {
-                        // the other emitted particles: daughters with their
-                        // own lineages and isotropic directions
-                        P32 b = q;
-                        b.e = e_ev | SECONDARY_EVENT;
-                        if (!stack_push(ws, wp, b, 1u | FRESH_DIRECTION, nsec, NO_KEYS))
-                            queue_daughters(a, b, 1u, nsec, FRESH_DIRECTION);
-                        nadd += nsec - 1;
-                    }
-                    ww = true;
-                }
-            }
-            if (ww && ww_on) {
-                const int kc = q.cell;
-                const double2 hl = __ldg(&a.ww_hl[kc]);  // ceiling, floor
-                if (dgt(q.w, hl.x)) {
-                    // a split: the parent joins the warp's split queue (below),
-                    // all its daughters come back through the daughter stack
-                    eb |= 1u << EB_SPLIT;
-                    q.e = e_ev;
-                    have = false;
-                } else if (dgt(hl.y, q.w)) {
-                    const double ctr = a.ww_c[kc];
-                    // survive iff u < w / ww, tested as u ww < w (no divide)
-                    const double ur = u01(r2[2], r2[3]);
-                    if (ur * ctr < q.w) {
-                        q.w = ctr;
-                        q.tw = tally_weight(ctr, bs.tscale);
-                        eb |= 1u << EB_RSURV;
-                    } else {
-                        eb |= 1u << EB_RKILL;
-                        e_end = q.e;
-                        have = false;
-                    }
-                }
-            }
+            take_event(a, bs, ww_on, tl32, qb, b_blk, r, r2, q, have, eb, e_end, [&](const P32& b, uint32_t nsec) {
+                if (!stack_push(ws, wp, b, 1u | FRESH_DIRECTION, nsec, NO_KEYS))
+                    queue_daughters(a, b, 1u, nsec, FRESH_DIRECTION);
+                nadd += nsec - 1;
+            });
         }
         __syncwarp();
         // ---- splits of the iteration: queued, processed a batch at a time ----
@@ -762,7 +809,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
             const unsigned ns = __popc(sm_);
             if (ns) {
                 if (sqn + ns > 32u) {
-                    nadd += process_splits(a, ws, wp, sqn, lane, bs.tscale);
+                    nadd += process_splits(a, ws, wp, sqn, lane, bs.S);
                     sqn = 0;
                 }
                 if ((sm_ >> lane) & 1u) {
@@ -779,7 +826,7 @@ __device__ __forceinline__ void run_warp(const TrackArgs<float>& a, const long l
                 sqn += ns;
                 __syncwarp();
                 if (sqn >= SPLIT_BATCH) {
-                    nadd += process_splits(a, ws, wp, sqn, lane, bs.tscale);
+                    nadd += process_splits(a, ws, wp, sqn, lane, bs.S);
                     sqn = 0;
                 }
             }
@@ -894,7 +941,7 @@ __global__ void __launch_bounds__(TRACK_THREADS, 3) track32_kernel(TrackArgs<flo
         s_next = 0;
         s_bs.wbar = a.sd->wbar;
         s_bs.tscale = a.sd->tscale;
-        s_bs.twbar = tally_weight(a.sd->wbar, a.sd->tscale);
+        s_bs.twbar = tally_weight_bits(a.sd->wbar, a.sd->S);
         s_bs.S = a.sd->S;
     }
     if (threadIdx.x < WARPS) {
@@ -984,7 +1031,7 @@ __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const T
             if (threadIdx.x == 0) {
                 s_bs.wbar = A.sd->wbar;
                 s_bs.tscale = A.sd->tscale;
-                s_bs.twbar = tally_weight(A.sd->wbar, A.sd->tscale);
+                s_bs.twbar = tally_weight_bits(A.sd->wbar, A.sd->S);
                 s_bs.S = A.sd->S;
             }
             if (threadIdx.x < ST_COUNT) s_stats[threadIdx.x] = 0;
@@ -1011,10 +1058,368 @@ __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const T
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Event-based variant of wave 0 (start-bank particles).
+//
+// Each block of EV_THREADS threads keeps its live particles in a ring in
+// shared memory and advances them one event per pass: thread t takes the
+// t-th particle from the ring's head, draws its Philox blocks, takes its
+// event and tallies the flight (take_event, the warp loop's arithmetic, so
+// both kernels give the same tallies, census and records bit for bit).  A
+// block-wide exclusive scan of the threads' output counts then appends the
+// survivors and the daughters of splits at the ring's tail and gives the
+// pass's census particles consecutive census slots (one reservation per
+// pass); the daughters are made by their whole warp, daughter 32 r + l of
+// the warp's splits by lane l in round r (parent found by a binary search
+// over the warp's prefix of daughter counts, its state taken by shuffles,
+// its lineage key drawn by the lane).  Fresh particles from the block's
+// contiguous range of the start bank keep at least one pass of work in the
+// ring.  Outputs beyond the ring's room, and the extra particles of a
+// multiplying collision, go to the record queue (the warp loop takes them in
+// the next wave).  Every event of a pass is one SIMT lane's work, so lanes
+// idle only at divergent outcomes and in a block's last passes; the price is
+// the ring's shared-memory traffic (48 bytes read and written per event) and
+// three block barriers per pass, which the SM's second block hides.
+// ---------------------------------------------------------------------------
+constexpr int EV_THREADS = 512;
+constexpr int EV_WARPS = EV_THREADS / 32;
+constexpr int EV_BLOCKS_PER_SM = 2;
+constexpr int EV_REC_BYTES = 48;  // ring bytes per particle
+
+// the ring's field arrays over a runtime capacity (the shared memory the
+// tallies leave), 8-byte fields first
+struct EvRing {
+    double* w;
+    uint64_t* lin;
+    float *x, *mu, *imu, *tau, *tw;
+    int* cell;
+    uint32_t *id, *e;
+    __device__ EvRing(void* base, int cap) {
+        char* b = reinterpret_cast<char*>(base);
+        w = reinterpret_cast<double*>(b);
+        lin = reinterpret_cast<uint64_t*>(b + 8 * (size_t)cap);
+        x = reinterpret_cast<float*>(b + 16 * (size_t)cap);
+        mu = x + cap;
+        imu = mu + cap;
+        tau = imu + cap;
+        tw = tau + cap;
+        cell = reinterpret_cast<int*>(tw + cap);
+        id = reinterpret_cast<uint32_t*>(cell + cap);
+        e = id + cap;
+    }
+    __device__ __forceinline__ void put(int s, const P32& q) const {
+        w[s] = q.w;
+        lin[s] = q.lin;
+        x[s] = q.xo;
+        mu[s] = q.mu;
+        imu[s] = q.inv_mu;
+        tau[s] = q.tau;
+        tw[s] = q.tw;
+        cell[s] = q.cell;
+        id[s] = q.id;
+        e[s] = q.e;
+    }
+    __device__ __forceinline__ void get(int s, P32& q) const {
+        q.w = w[s];
+        q.lin = lin[s];
+        q.xo = x[s];
+        q.mu = mu[s];
+        q.inv_mu = imu[s];
+        q.tau = tau[s];
+        q.tw = tw[s];
+        q.cell = cell[s];
+        q.id = id[s];
+        q.e = e[s];
+    }
+};
+
+// start particle i (of the bank, or of the pulse at birth)
+__device__ __forceinline__ void ev_start(const TrackArgs<float>& a, const BlockScalars& bs, int birth, uint32_t k0,
+                                         uint32_t k1, long long i, P32& q) {
+    q.id = (uint32_t)i;
+    q.lin = 0;
+    q.e = 0;
+    q.tau = a.tau0f;
+    q.w = bs.wbar;
+    q.tw = bs.twbar;
+    if (birth) {
+        // the pulse: isotropic birth direction, mirrored into a reflecting wall's side
+        uint32_t r[4] = {q.id, 0u, 0u, 0xFFFFFFFFu};
+        philox4x32_10(r, k0, k1);
+        q.mu = 2.0f * u01f(r[1]) - 1.0f;
+        const double x = a.src_x;
+        if (x <= a.edges[0] && q.mu < 0.0f && a.bc_l == 1) q.mu = -q.mu;
+        if (x >= a.edges[a.I] && q.mu > 0.0f && a.bc_r == 1) q.mu = -q.mu;
+        q.cell = (q.mu < 0.0f) ? a.birth_cell_neg : a.birth_cell_pos;
+        q.xo = (float)(x - a.edges[q.cell]);
+    } else {
+        const BankRec<float> r = a.bank[i];
+        q.xo = r.x;
+        q.mu = r.mu;
+        q.cell = r.cell;
+    }
+    q.inv_mu = __frcp_rn(q.mu);  // the correctly rounded 1/mu
+}
+
+__device__ __forceinline__ int ring_slot(int s, int cap) { return s >= cap ? s - cap : s; }
+
+__global__ void __launch_bounds__(EV_THREADS, EV_BLOCKS_PER_SM) track32_event_kernel(TrackArgs<float> a, int cap) {
+    extern __shared__ long long sm[];
+    __shared__ unsigned long long s_stats[ST_COUNT];
+    __shared__ BlockScalars s_bs;
+    __shared__ unsigned s_wsum[EV_WARPS];   // per-warp output words, then their exclusive prefixes
+    __shared__ unsigned s_total;            // the pass's output word: outputs << 11 | census
+    __shared__ unsigned long long s_cbase;  // the pass's first census slot
+    const int I = a.I;
+    unsigned* tl32 = reinterpret_cast<unsigned*>(sm);
+    const EvRing R(sm + (size_t)ROWS32 * I, cap);
+    const unsigned t = threadIdx.x, lane = t & 31u, wid = t >> 5;
+    if (t == 0) {
+        s_bs.wbar = a.sd->wbar;
+        s_bs.tscale = a.sd->tscale;
+        s_bs.twbar = tally_weight_bits(a.sd->wbar, a.sd->S);
+        s_bs.S = a.sd->S;
+    }
+    if (t < ST_COUNT) s_stats[t] = 0;
+    for (int i = t; i < 2 * ROWS32 * I; i += EV_THREADS) tl32[i] = 0;
+    const uint32_t k0 = a.sd->k0, k1 = a.sd->k1;
+    const int ww_on = a.sd->ww_on;
+    const int birth = a.sd->birth;
+    // the block's contiguous range of [bank_lo, min(bank_hi, size)), as in
+    // the warp-loop kernel, so that nearly all its flights fall in one
+    // variance batch (kept in shared memory)
+    const long long n_in = (long long)a.sd->nbank;
+    const long long lo = a.bank_lo, hi = min(n_in, a.bank_hi);
+    const long long len = hi > lo ? hi - lo : 0;
+    const long long chunk = (len + gridDim.x - 1) / gridDim.x;
+    const long long first = lo + (long long)blockIdx.x * chunk;
+    const long long last = min(hi, first + chunk);
+    int b_blk = -1;
+    uint32_t b_end = 0;
+    if (first < hi) {
+        b_blk = batch_of((uint32_t)first, a.B, a.N, a.batch_m);
+        b_end = (uint32_t)min((long long)UINT32_MAX, ((long long)(b_blk + 1) * a.N + a.B - 1) / a.B);
+    }
+    __syncthreads();
+    const BlockScalars bs = s_bs;
+    // ring state, the same in every thread: particles [head, head + count)
+    long long next = first;  // the next start particle of the range
+    int head = 0, count = 0;
+    unsigned long long mycnt = 0;  // lane k < EB_COUNT: counter kLaneStat[k]; then daughters, max events
+    for (;;) {
+        // ---- keep a pass of work in the ring ----
+        const int add = (int)max(0LL, min((long long)min(EV_THREADS - count, cap - count), last - next));
+        if ((int)t < add) {
+            P32 q;
+            ev_start(a, bs, birth, k0, k1, next + t, q);
+            R.put(ring_slot(head + count + (int)t, cap), q);
+        }
+        next += add;
+        count += add;
+        if (count == 0) break;
+        __syncthreads();
+        // ---- the t-th particle from the head: one event ----
+        const int m = min(count, EV_THREADS);
+        P32 q;
+        bool have = (int)t < m;
+        if (have) {
+            R.get(ring_slot(head + (int)t, cap), q);
+            if (q.e >= MAX_EVENTS) {
+                atomicOr(a.err, ERR_EVENTS);
+                have = false;
+            }
+        } else {
+            q.id = 0;
+            q.lin = 0;
+            q.e = 0;
+        }
+        uint32_t r[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 2u * q.e};
+        uint32_t r2[4] = {q.id, (uint32_t)q.lin, (uint32_t)(q.lin >> 32), 2u * q.e + 1u};
+        philox_pair(r, r2, k0, k1, k0, k1);
+        unsigned eb = 0;
+        uint32_t e_end = 0, nadd = 0, nd = 0;
+        if (have) {
+            const int qb = (q.id >= (uint32_t)first && q.id < b_end) ? b_blk : batch_of(q.id, a.B, a.N, a.batch_m);
+            take_event(a, bs, ww_on, tl32, qb, b_blk, r, r2, q, have, eb, e_end, [&](const P32& b, uint32_t nsec) {
+                queue_daughters(a, b, 1u, nsec, FRESH_DIRECTION);
+                nadd += nsec - 1;
+            });
+            if ((eb >> EB_SPLIT) & 1u) {
+                nd = split_count(a, q.w, a.ww_c[q.cell]);
+                if (nd) nadd += nd - 1;
+            }
+        }
+        // ---- outputs (a survivor, or a split's daughters) and census: slots ----
+        const uint32_t nout = have ? 1u : nd;
+        const unsigned cen = (eb >> EB_CENSUS) & 1u;
+        // outputs past the ring's room go to the record queue, so a count is
+        // capped at cap in the scan word (EV_THREADS x cap < 2^21 outputs)
+        const unsigned v = (min(nout, (uint32_t)cap) << 11) | cen;
+        unsigned incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const unsigned x = lane < (unsigned)EV_WARPS ? s_wsum[lane] : 0u;
+            unsigned xi = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, xi, o);
+                if ((int)lane >= o) xi += y;
+            }
+            if (lane < (unsigned)EV_WARPS) s_wsum[lane] = xi - x;
+            if (lane == (unsigned)EV_WARPS - 1) {
+                s_total = xi;
+                const unsigned nc = xi & 0x7FFu;
+                s_cbase = nc ? atomicAdd(a.cen.count, (unsigned long long)nc) : 0ull;
+            }
+        }
+        __syncthreads();
+        const unsigned off = s_wsum[wid] + incl - v;
+        const unsigned tot = s_total;
+        // the pass's inputs are free now: outputs go at the ring's tail,
+        // into the room the particles not taken leave
+        const int tail = ring_slot(head + count, cap);
+        const int room = cap - (count - m);
+        if (cen) {
+            const unsigned long long slot = s_cbase + (off & 0x7FFu);
+            if ((long long)slot < a.cen.cap) {
+                const unsigned long long wfx = comb_weight(fixed_bits(q.w, bs.S), a.comb_shift);
+                a.cen.x[slot] = q.xo;
+                a.cen.mu[slot] = q.mu;
+                a.cen.w[slot] = q.w;
+                a.cen.cell[slot] = q.cell;
+                a.cen.id[slot] = q.id;
+                a.cen.lw[slot] = LinW{q.lin, wfx};
+                atomicAdd(&a.gcnt[q.id], 1u);
+                atomicAdd(&a.gw[q.id], wfx);
+            } else {
+                atomicOr(a.err, ERR_CENSUS_OVERFLOW);
+            }
+        }
+        const unsigned o0 = off >> 11;
+        if (have) {
+            if ((int)o0 < room)
+                R.put(ring_slot(tail + (int)o0, cap), q);
+            else
+                push_record(a, q, q.w, q.e, 0u, 0u, warp_reserve(a.rout.count));
+        }
+        // the warp's daughters, round by round over all its lanes
+        uint32_t dincl = nd;  // daughters of lanes 0..lane
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, dincl, o);
+            if ((int)lane >= o) dincl += y;
+        }
+        const uint32_t dtot = __shfl_sync(0xffffffffu, dincl, 31);
+        if (dtot) {
+            double wd = 0.0;
+            float twd = 0.0f;
+            if (nd) {
+                wd = daughter_weight(q.w, nd);
+                twd = tally_weight_bits(wd, bs.S);
+            }
+            for (uint32_t g0 = 0; g0 < dtot; g0 += 32) {
+                const uint32_t g = g0 + lane;
+                // parent: the number of lanes whose daughters all come before g
+                int pl = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t c = __shfl_sync(0xffffffffu, dincl, pl + step - 1);
+                    if (c <= g) pl += step;
+                }
+                pl = min(pl, 31);
+                P32 d;
+                d.xo = __shfl_sync(0xffffffffu, q.xo, pl);
+                d.mu = __shfl_sync(0xffffffffu, q.mu, pl);
+                d.inv_mu = __shfl_sync(0xffffffffu, q.inv_mu, pl);
+                d.tau = __shfl_sync(0xffffffffu, q.tau, pl);
+                d.cell = __shfl_sync(0xffffffffu, q.cell, pl);
+                d.id = __shfl_sync(0xffffffffu, q.id, pl);
+                const uint64_t plin = __shfl_sync(0xffffffffu, q.lin, pl);
+                const uint32_t pe = __shfl_sync(0xffffffffu, q.e, pl);
+                d.w = __shfl_sync(0xffffffffu, wd, pl);
+                d.tw = __shfl_sync(0xffffffffu, twd, pl);
+                const uint32_t pbase = __shfl_sync(0xffffffffu, dincl - nd, pl);  // warp prefix of the parent
+                const unsigned po = __shfl_sync(0xffffffffu, o0, pl);            // the parent's first slot
+                if (g < dtot) {
+                    const uint32_t j = g - pbase;
+                    d.lin = lineage_hash(plin, pe, j);
+                    d.e = 0;
+                    const unsigned long long sj = (unsigned long long)po + j;
+                    if (sj < (unsigned long long)room)
+                        R.put(ring_slot(tail + (int)sj, cap), d);
+                    else
+                        push_record(a, d, d.w, 0u, 0u, 0u, warp_reserve(a.rout.count));
+                }
+            }
+        }
+        // ---- the pass's counts, summed over the warp ----
+        {
+            const unsigned wlo = ((eb & 0x1Fu) * 0x108421u) & 0x1041041u;
+            const unsigned whi = (((eb >> 5) & 0xFu) * 0x8421u) & 0x41041u;
+            const unsigned slo = __reduce_add_sync(0xffffffffu, wlo);
+            const unsigned shi = __reduce_add_sync(0xffffffffu, whi);
+            const unsigned sd = __reduce_add_sync(0xffffffffu, nadd);
+            const unsigned smax = __reduce_max_sync(0xffffffffu, e_end);
+            const unsigned f = ((lane < 5u ? slo : shi) >> (6u * (lane < 5u ? lane : lane - 5u))) & 63u;
+            const unsigned cadd = lane < (unsigned)EB_COUNT ? f : (lane == (unsigned)LANE_DAUGHTERS ? sd : 0u);
+            mycnt += cadd;
+            if (lane == (unsigned)LANE_MAXEV) mycnt = max(mycnt, (unsigned long long)smax);
+        }
+        // the next pass's refill barrier orders these writes before its reads
+        head = ring_slot(head + m, cap);
+        count = count - m + min((int)(tot >> 11), room);
+    }
+    // the warp's counts into the block's
+    if (lane < (unsigned)EB_COUNT) {
+        if (mycnt) atomicAdd(&s_stats[kLaneStat[lane]], mycnt);
+    } else if (lane == (unsigned)LANE_DAUGHTERS) {
+        if (mycnt) atomicAdd(&s_stats[ST_DAUGHTERS], mycnt);
+    } else if (lane == (unsigned)LANE_MAXEV) {
+        if (mycnt) atomicMax(&s_stats[ST_MAX_EVENTS], mycnt);
+    }
+    __syncthreads();
+    flush_jf(tl32, I, a.tl);
+    if (b_blk >= 0) flush_batch_row(tl32, I, a.batch, b_blk, false);
+    flush_block_stats(s_stats, a.stats);
+}
+
 }  // namespace
 
 void launch_track_fp32(const TrackArgs<float>& a, int grid, int block, size_t smem, cudaStream_t s) {
     track32_kernel<<<grid, block, smem, s>>>(a);
+}
+
+// the event kernel's ring capacity for a mesh of I cells: the shared memory a
+// block gets with two blocks per SM, less the tallies, in whole warps of
+// particles; 0 when that leaves less than two passes of room
+int ev_ring_cap(int I) {
+    int dev = 0, per_sm = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const long long static_bytes = 1024 + 2048;  // the kernel's own variables and the per-block reserve, rounded up
+    const long long budget = std::min<long long>(optin, per_sm / EV_BLOCKS_PER_SM - static_bytes);
+    const long long tallies = (long long)sizeof(long long) * ROWS32 * I;
+    long long cap = (budget - tallies) / EV_REC_BYTES;
+    cap = cap / 32 * 32;
+    // the pass's scan word holds EV_THREADS x cap outputs in 21 bits
+    return cap >= 2 * EV_THREADS ? (int)std::min<long long>(cap, (1 << 21) / EV_THREADS - 32) : 0;
+}
+
+size_t track_event_smem_fp32(int I, int cap) {
+    return sizeof(long long) * (size_t)ROWS32 * (size_t)I + (size_t)EV_REC_BYTES * (size_t)cap;
+}
+
+void launch_track_fp32_event(const TrackArgs<float>& a, int nsm, int cap, cudaStream_t s) {
+    track32_event_kernel<<<nsm * EV_BLOCKS_PER_SM, EV_THREADS, track_event_smem_fp32(a.I, cap), s>>>(a, cap);
+}
+
+int track_event_smem_optin_fp32(int I, int cap) {
+    return raise_smem_limit((const void*)track32_event_kernel, track_event_smem_fp32(I, cap));
 }
 
 int track_smem_optin_fp32(size_t smem) {

@@ -1,0 +1,134 @@
+"""The event-based FP32 tracking kernel against the warp-loop kernel.
+
+Both kernels take the same events from the same Philox words with the same
+arithmetic (one shared event routine), the tallies are integer sums, and the
+comb orders the census canonically, so a step gives the same raw tally
+words, counts and next start bank with either kernel, whatever order the
+kernels visit particles in.  Checked bit for bit, step after step, on the
+plain slab, the reflecting and leaking shield, the multiplying medium (whose
+extra particles go through the record queue), a split storm that overflows
+the particle pools into the record queue, a ragged bank that leaves most
+blocks' pools short, and the 1000-cell slab at its full 1e7 particles per
+step.
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+hww = pytest.importorskip("paper_2512_19925_gb300")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+RAW = [hww.TL_PHI, hww.TL_J, hww.TL_F, hww.CENSUS_PHI, hww.CENSUS_J, hww.CENSUS_F, hww.BATCH_PHI, hww.BOUNDARY]
+# every count of a step except the number of record waves (the two kernels
+# send different work to the record queue)
+COUNTS = list(hww.STAT_FIELDS)
+
+
+def pair(wl):
+    a = hww.Problem.from_workload(wl)
+    b = hww.Problem.from_workload(wl)
+    b.set_tracking(hww.TRACK_EVENT)
+    return a, b
+
+
+def assert_same_step(a, b, step):
+    sa, sb = a.run_step(), b.run_step()
+    for k in COUNTS:
+        assert sa[k] == sb[k], (step, k, sa[k], sb[k])
+    for kind in RAW:
+        assert np.array_equal(a.get_tallies_raw(kind), b.get_tallies_raw(kind)), (step, kind)
+    for x, y in zip(a.get_bank(), b.get_bank()):
+        assert np.array_equal(x, y), step
+    return sa, sb
+
+
+def run_pair(wl, steps):
+    a, b = pair(wl)
+    try:
+        out = [assert_same_step(a, b, n + 1) for n in range(steps)]
+    finally:
+        a.close()
+        b.close()
+    return out
+
+
+def thin_shield(n):
+    # the shield's regions squeezed onto [0, 0.4] (reflecting at 0, vacuum at
+    # 0.4), so that particles reflect and, from the fifth step on (v dt =
+    # 0.1), leak
+    wl = workloads.small_variant(workloads.shield(precision="fp32", n_cells=80), n)
+    wl["edges"] = wl["edges"] * 0.01
+    return wl
+
+
+@pytest.mark.parametrize("case", ["plain", "shield"])
+def test_event_kernel_equals_warp_kernel(case):
+    if case == "plain":
+        wl = workloads.small_variant(workloads.plain_slab(), 30000)
+        wl["precision"] = "fp32"
+    else:
+        wl = thin_shield(30000)
+    out = run_pair(wl, 12)
+    # the windows split (and, on the shield, particles leaked and reflected)
+    assert sum(s["split_events"] for s, _ in out) > 0
+    if case == "shield":
+        assert sum(s["leaked"] for s, _ in out) > 0 and sum(s["reflections"] for s, _ in out) > 0
+
+
+def test_event_kernel_multiplying_medium():
+    wl = workloads.azurv1(particles_per_step=20000, n_steps=8, precision="fp32")
+    out = run_pair(wl, 8)
+    assert sum(s["daughters"] for s, _ in out) > 0
+
+
+def test_event_kernel_split_storm_overflows_pools():
+    # centers far below the start weight: a particle splits into about forty
+    # daughters at its first window test (about one in ten reaches one in
+    # the step); with 650 start particles a block, a pass's splits make more
+    # daughters than a ring holds, so some leave through the record queue
+    wl = workloads.small_variant(workloads.plain_slab(), 200000)
+    wl["precision"] = "fp32"
+    a, b = pair(wl)
+    try:
+        s1, _ = assert_same_step(a, b, 1)
+        centers = np.full(len(wl["edges"]) - 1, s1["w_bar_next"] / 40.0)
+        for p in (a, b):
+            p.set_ww_centers(centers)
+        sa, sb = assert_same_step(a, b, 2)
+        assert sb["waves"] > 1  # the pools overflowed into the record queue
+        assert sa["daughters"] > sa["n_start"]
+        assert_same_step(a, b, 3)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_event_kernel_ragged_bank():
+    # 1000 particles: fewer than one pool per SM, most blocks get none
+    wl = workloads.small_variant(workloads.plain_slab(), 1000)
+    wl["precision"] = "fp32"
+    run_pair(wl, 6)
+
+
+def test_event_kernel_rejects_fp64_problem():
+    wl = workloads.small_variant(workloads.plain_slab(), 1000)
+    p = hww.Problem.from_workload(wl)
+    try:
+        with pytest.raises(hww.HWWError):
+            p.set_tracking(hww.TRACK_EVENT)
+        with pytest.raises(hww.HWWError):
+            p.set_tracking(7)
+        p.set_tracking(hww.TRACK_WARP)
+    finally:
+        p.close()
+
+
+def test_event_kernel_full_size():
+    wl = workloads.plain_at_scale(particles_per_step=10_000_000, precision="fp32")
+    out = run_pair(wl, 3)
+    assert out[-1][0]["segments"] > 2e7
