@@ -65,7 +65,7 @@ typedef enum {
 enum { HWW_BC_VACUUM = 0, HWW_BC_REFLECT = 1 };
 enum { HWW_FP64 = 0, HWW_FP32_TRACK = 1 };
 /* FP32 tracking kernels (hww_set_tracking) */
-enum { HWW_TRACK_WARP = 0, HWW_TRACK_EVENT = 1 };
+enum { HWW_TRACK_WARP = 0, HWW_TRACK_EVENT = 1, HWW_TRACK_AUTO = 2 };
 enum { HWW_FILTER_NONE = 0, HWW_FILTER_MA = 1, HWW_FILTER_FOURIER = 2 };
 /* window modes: HLOSM centers (the paper's method), analog (no windows),
  * lagged (centers from the previous step's track-length flux) */
@@ -315,33 +315,39 @@ hww_status batch_member_stats(hww_batch* b, int32_t i, hww_step_stats* stats);
 void destroy_batch(hww_batch* b);
 
 /* Launch accounting of a problem since creation or the last reset: kernels
- * the library launched, tracking-kernel launches, and (when timing is on)
- * the device time of the tracking launches measured with CUDA events on the
- * problem's stream. */
+ * the library launched, tracking-kernel launches (of which event_launches
+ * ran the event loop), and (when timing is on) the device time of the
+ * tracking launches measured with CUDA events on the problem's stream. */
 typedef struct {
     int64_t kernel_launches;
     int64_t track_launches;
     double track_ms;
     int64_t steps;
     int64_t census_capacity, queue_capacity;
+    int64_t event_launches;
 } hww_counters;
 
 /* The kernel that tracks an FP32 problem's start-bank particles (the events
  * of Sec. 2 and the tallies of Eq. phi-mc):
- *   HWW_TRACK_WARP  (default) a warp-synchronous history loop: each lane
- *                   follows one track event by event and takes new work
- *                   (daughters from its warp's stack, start particles) when
- *                   its track ends;
+ *   HWW_TRACK_WARP  a warp-synchronous history loop: each lane follows one
+ *                   track event by event and takes new work (daughters from
+ *                   its warp's stack, start particles) when its track ends;
  *   HWW_TRACK_EVENT an event-based loop: two 512-thread blocks per SM each
  *                   keep a ring of live particles in shared memory and
  *                   advance all of them by one event per pass, appending
- *                   survivors and daughters after a block-wide scan.
- * Both draw the same random numbers and do the same arithmetic, so a step
- * gives bit-identical tallies, census and next start bank with either; the
- * record waves (overflow, multiplying collisions' extra particles) always
- * run the warp loop.  HWW_ERR_ARG for an FP64 problem, an unknown kind, or
- * a mesh whose tallies (24 I bytes) leave a block less than 48 KB of ring.
- * Applies from the next step. */
+ *                   survivors and daughters after a block-wide scan;
+ *   HWW_TRACK_AUTO  the event loop until one of its steps overflows its rings
+ *                   into the record queue, then the warp loop for the rest
+ *                   of the run (the default for FP32 problems whose mesh
+ *                   leaves room for the rings; HWW_TRACK_WARP otherwise and
+ *                   for FP64).
+ * Both loops draw the same random numbers and do the same arithmetic, so a
+ * step gives bit-identical tallies, census and next start bank with either;
+ * the record waves (overflow, multiplying collisions' extra particles)
+ * always run the warp loop.  HWW_ERR_ARG for an unknown kind, for
+ * HWW_TRACK_EVENT or HWW_TRACK_AUTO on an FP64 problem or on a mesh whose
+ * tallies (24 I bytes) leave a block less than 48 KB of ring.  Applies from
+ * the next step (setting a kind restarts HWW_TRACK_AUTO's choice). */
 hww_status hww_set_tracking(hww_problem* p, int32_t kind);
 /* Turn CUDA-event timing of the tracking launches on (1) or off (0). */
 hww_status hww_set_timing(hww_problem* p, int32_t enable);

@@ -25,7 +25,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "call out of order", 3: "out of mem
           7: "CUDA runtime error", 8: "no CUDA device"}
 BC_VACUUM, BC_REFLECT = 0, 1
 FP64, FP32_TRACK = 0, 1
-TRACK_WARP, TRACK_EVENT = 0, 1
+TRACK_WARP, TRACK_EVENT, TRACK_AUTO = 0, 1, 2
 FILTER_NONE, FILTER_MA, FILTER_FOURIER = 0, 1, 2
 MODE_HWW, MODE_ANALOG, MODE_LWW = 0, 1, 2
 SCALE_MEAN_WEIGHT, SCALE_LITERAL = 0, 1
@@ -58,7 +58,8 @@ class StepStats(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("track_launches", C.c_int64), ("track_ms", C.c_double),
-                ("steps", C.c_int64), ("census_capacity", C.c_int64), ("queue_capacity", C.c_int64)]
+                ("steps", C.c_int64), ("census_capacity", C.c_int64), ("queue_capacity", C.c_int64),
+                ("event_launches", C.c_int64)]
 
 
 class BatchStats(C.Structure):
@@ -423,9 +424,10 @@ class Problem:
         _check(load().hww_set_timing(self._h, 1 if enable else 0), "hww_set_timing")
 
     def set_tracking(self, kind):
-        """FP32 problems: TRACK_WARP (warp-synchronous history loop, the
-        default) or TRACK_EVENT (event-based pool loop) for the start-bank
-        wave; both give bit-identical steps."""
+        """The start-bank wave's kernel: TRACK_WARP (warp-synchronous
+        history loop), TRACK_EVENT (event-based ring loop, FP32 only) or
+        TRACK_AUTO (the event loop until a step overflows its rings, then the
+        warp loop; the FP32 default); all give bit-identical steps."""
         _check(load().hww_set_tracking(self._h, int(kind)), "hww_set_tracking")
 
     def counters(self):

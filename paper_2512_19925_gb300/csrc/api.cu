@@ -115,8 +115,10 @@ struct hww_problem {
     int timing = 0;
     int track_kind = HWW_TRACK_WARP;  // FP32 wave-0 tracking kernel (hww_set_tracking)
     int ev_cap = 0;                   // the event kernel's ring capacity
+    int auto_warp = 0;                // HWW_TRACK_AUTO: an event-kernel step needed a record wave
+    int wave0_event = 0;              // the current step's wave 0 ran the event kernel
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
-    long long kernel_launches = 0, track_launches = 0;
+    long long kernel_launches = 0, track_launches = 0, event_launches = 0;
     double track_ms = 0.0;
 };
 
@@ -360,10 +362,15 @@ void launch_track(hww_problem* p, const TrackArgs<double>& a) {
 }
 void launch_track(hww_problem* p, const TrackArgs<float>& a) {
     if (p->timing) cudaEventRecord(p->ev_a, p->stream);
-    if (p->track_kind == HWW_TRACK_EVENT && a.from_bank)
+    const bool ev = a.from_bank && (p->track_kind == HWW_TRACK_EVENT ||
+                                    (p->track_kind == HWW_TRACK_AUTO && !p->auto_warp));
+    if (a.from_bank) p->wave0_event = ev ? 1 : 0;
+    if (ev) {
         launch_track_fp32_event(a, p->nsm, p->ev_cap, p->stream);
-    else
+        ++p->event_launches;
+    } else {
         launch_track_fp32(a, p->track_grid, TRACK_BLOCK, p->track_smem, p->stream);
+    }
     if (p->timing) cudaEventRecord(p->ev_b, p->stream);
     ++p->kernel_launches;
     ++p->track_launches;
@@ -412,6 +419,10 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b, long long lo = 0, long lo
         ++waves;
     }
     p->last_waves = waves;
+    // automatic choice: the event kernel until one of its steps overflows its
+    // rings into the record queue (late steps, many daughters per source
+    // particle, where the warp loop is as fast without a second wave)
+    if (p->track_kind == HWW_TRACK_AUTO && p->wave0_event && waves > 1) p->auto_warp = 1;
     return HWW_OK;
 }
 
@@ -1098,6 +1109,15 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
                          : track_blocks_per_sm_fp64(TRACK_BLOCK, p->track_smem, p->P2 > 0);
     if (per_sm < 1) per_sm = 1;
     p->track_grid = p->nsm * per_sm;
+    // FP32 problems choose their wave-0 kernel step by step where the
+    // event kernel's rings fit the mesh
+    if (p->fp32) {
+        const int cap = ev_ring_cap(I);
+        if (cap > 0 && track_event_smem_optin_fp32(I, cap) == 0) {
+            p->ev_cap = cap;
+            p->track_kind = HWW_TRACK_AUTO;
+        }
+    }
     *out = p;
     return HWW_OK;
 }
@@ -1411,8 +1431,8 @@ hww_status get_bank(const hww_problem* p, double* x, double* mu, int32_t* cell, 
 }
 
 hww_status hww_set_tracking(hww_problem* p, int32_t kind) {
-    if (!p || (kind != HWW_TRACK_WARP && kind != HWW_TRACK_EVENT)) return HWW_ERR_ARG;
-    if (kind == HWW_TRACK_EVENT) {
+    if (!p || (kind != HWW_TRACK_WARP && kind != HWW_TRACK_EVENT && kind != HWW_TRACK_AUTO)) return HWW_ERR_ARG;
+    if (kind != HWW_TRACK_WARP) {
         if (!p->fp32) return HWW_ERR_ARG;
         HWW_CK(cudaSetDevice(p->device));
         const int cap = ev_ring_cap(p->I);
@@ -1421,6 +1441,7 @@ hww_status hww_set_tracking(hww_problem* p, int32_t kind) {
         p->ev_cap = cap;
     }
     p->track_kind = kind;
+    p->auto_warp = 0;
     return HWW_OK;
 }
 
@@ -1439,6 +1460,7 @@ hww_status hww_get_counters(const hww_problem* p, hww_counters* out) {
     if (!p || !out) return HWW_ERR_ARG;
     out->kernel_launches = p->kernel_launches;
     out->track_launches = p->track_launches;
+    out->event_launches = p->event_launches;
     out->track_ms = p->track_ms;
     out->steps = p->steps;
     out->census_capacity = p->cen_cap;
@@ -1450,6 +1472,7 @@ hww_status hww_reset_counters(hww_problem* p) {
     if (!p) return HWW_ERR_ARG;
     p->kernel_launches = 0;
     p->track_launches = 0;
+    p->event_launches = 0;
     p->track_ms = 0.0;
     return HWW_OK;
 }

@@ -32,6 +32,7 @@ COUNTS = list(hww.STAT_FIELDS)
 def pair(wl):
     a = hww.Problem.from_workload(wl)
     b = hww.Problem.from_workload(wl)
+    a.set_tracking(hww.TRACK_WARP)
     b.set_tracking(hww.TRACK_EVENT)
     return a, b
 
@@ -122,6 +123,8 @@ def test_event_kernel_rejects_fp64_problem():
         with pytest.raises(hww.HWWError):
             p.set_tracking(hww.TRACK_EVENT)
         with pytest.raises(hww.HWWError):
+            p.set_tracking(hww.TRACK_AUTO)
+        with pytest.raises(hww.HWWError):
             p.set_tracking(7)
         p.set_tracking(hww.TRACK_WARP)
     finally:
@@ -132,3 +135,32 @@ def test_event_kernel_full_size():
     wl = workloads.plain_at_scale(particles_per_step=10_000_000, precision="fp32")
     out = run_pair(wl, 3)
     assert out[-1][0]["segments"] > 2e7
+
+
+def test_auto_choice_switches_to_warp_loop_after_an_overflow():
+    # the FP32 default: the event loop until one of its steps needs a
+    # record wave, then the warp loop; results equal the warp loop's all along
+    wl = workloads.small_variant(workloads.plain_slab(), 200000)
+    wl["precision"] = "fp32"
+    a = hww.Problem.from_workload(wl)
+    b = hww.Problem.from_workload(wl)
+    try:
+        a.set_tracking(hww.TRACK_WARP)
+        s1, _ = assert_same_step(a, b, 1)
+        assert b.counters()["event_launches"] == 1
+        centers = np.full(len(wl["edges"]) - 1, s1["w_bar_next"] / 40.0)
+        for p in (a, b):
+            p.set_ww_centers(centers)
+        # step 2's event loop overflows its rings (and the census bank: the
+        # step is replayed with more room, by then with the warp loop)
+        assert_same_step(a, b, 2)
+        assert b.counters()["event_launches"] == 2
+        for n in range(3, 6):
+            assert_same_step(a, b, n)
+        assert b.counters()["event_launches"] == 2  # the warp loop from step 3 on
+        b.set_tracking(hww.TRACK_AUTO)  # restarts the choice
+        assert_same_step(a, b, 6)
+        assert b.counters()["event_launches"] == 3
+    finally:
+        a.close()
+        b.close()
