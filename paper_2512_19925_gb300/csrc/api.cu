@@ -72,7 +72,7 @@ struct hww_problem {
     uint32_t *gcnt = nullptr, *gcur = nullptr;
     GroupRec* gro = nullptr;  // [N+1] census group records from the scan
     unsigned long long *tile_c = nullptr, *tile_w = nullptr;
-    uint32_t* member = nullptr;
+    MemberRec* member = nullptr;
     unsigned long long* cpre = nullptr;    // comb prefix C0 of every census particle (census-sized)
     uint32_t* glist = nullptr;             // ids of comb groups of 3+ members by size class (census-sized)
     // closures and LOSM

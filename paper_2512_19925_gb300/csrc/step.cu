@@ -130,19 +130,23 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
 // particle j owns the teeth in [C0_j, C0_j + w_j), C0_j = the group's weight
 // offset plus the weights of the group members before it.  Most groups have
 // one member: its C0 is set by the scatter pass, which lists only the members
-// of larger groups; their prefixes are found once per group: pairs by one
-// thread, groups of up to 32 by a warp segment of 4 to 32 lanes (a rank count
-// over shuffles), groups of 33 to 256 by a warp (bitonic sort in the warp's
-// shared memory, shuffle scan), larger ones by a block (bitonic sort and
-// scan in shared memory).  The copies are then written in census order,
-// reading the census bank and the stored prefixes coalesced.
+// of larger groups (each with its key and weight, so that the group passes
+// read their members contiguously); their prefixes are found once per group:
+// pairs by one thread, groups of up to 32 by a warp segment of 4 to 32 lanes
+// (a rank count over shuffles), larger groups by a warp (up to 256 members)
+// or a block with bucket lists: the lineage keys are uniform hashes, so
+// bucketing members by the top bits of the key into at least as many buckets
+// as members leaves about one member per bucket, the buckets are in key
+// order, and a member's prefix is the scan of the bucket weights before its
+// bucket plus the weights of the smaller keys in its own bucket's list.
+// The copies are then written in census order, reading the census bank and
+// the stored prefixes coalesced.
 // ---------------------------------------------------------------------------
-constexpr int NCLASS = 4;      // group size classes handled by warp segments of 4, 8, 16, 32 lanes
 constexpr int MID_CLASS = 4;   // 33..MID_MAX members: a warp per group
 constexpr int BIG_CLASS = 5;   // more: a block per group
 constexpr int MID_MAX = 256;
 constexpr int MID_WARPS = 4;   // warps (groups in flight) per block of the warp-per-group kernel
-constexpr int BIG_CAP = 2048;  // members a block sorts in shared memory
+constexpr int BIG_CAP = 4096;  // members a block keeps in shared memory
 constexpr int BIG_T = 256;
 static_assert(COMB_LISTS == BIG_CLASS + 1, "one list per size class");
 
@@ -159,7 +163,13 @@ __global__ void comb_scatter_kernel(CombArgs<Real> a) {
             continue;
         }
         const unsigned long long slot = (unsigned long long)g.off + atomicAdd(&a.gcur[id], 1u);
-        a.member[slot] = (uint32_t)j;
+        const LinW x = a.clw[j];
+        MemberRec r;
+        r.lin = x.lin;
+        r.wfx = x.wfx;
+        r.j = (uint32_t)j;
+        r.pad[0] = r.pad[1] = r.pad[2] = 0u;
+        a.member[slot] = r;
     }
 }
 
@@ -193,8 +203,8 @@ __global__ void comb_groups_kernel(CombArgs<Real> a) {
         if (g == 2) {
             const GroupRec G = a.gro[id];
             const unsigned long long base = G.off;
-            const uint32_t j0 = a.member[base], j1 = a.member[base + 1];
-            const LinW p0 = a.clw[j0], p1 = a.clw[j1];
+            const MemberRec p0 = a.member[base], p1 = a.member[base + 1];
+            const uint32_t j0 = p0.j, j1 = p1.j;
             const uint64_t l0 = p0.lin, l1 = p1.lin;
             const bool first0 = key_less(l0, j0, l1, j1);
             const unsigned long long C = G.offw;
@@ -262,8 +272,8 @@ __device__ __forceinline__ void seg_groups(const CombArgs<Real>& a, const uint32
     uint32_t jj = 0xFFFFFFFFu;
     unsigned long long w = 0;
     if ((uint32_t)li < g) {
-        jj = a.member[base + li];
-        const LinW x = a.clw[jj];
+        const MemberRec x = a.member[base + li];
+        jj = x.j;
         lin = x.lin;
         w = x.wfx;
     }
@@ -303,164 +313,124 @@ __global__ void comb_seg_kernel(CombArgs<Real> a) {
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
 
-// A warp's bitonic sort of 32 K keys (lineage, slot) with their weights, in
-// registers: element i = k 32 + lane sits in slot k of lane `lane`, so a
-// compare-exchange partner i ^ h is the same slot of lane ^ h (a shuffle) for
-// h < 32 and slot k ^ (h / 32) of the same lane for h >= 32.  Only the slot
-// loops are unrolled (the network's stages are loops), which keeps the code
-// small enough for the instruction cache.
-template <int K, int HS>
-__device__ __forceinline__ void slot_phase(uint64_t (&L)[K], uint32_t (&J)[K], unsigned long long (&Wt)[K],
-                                           int lane, int kk) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int k2 = k ^ HS;
-        if (k2 > k) {
-            const bool up = ((k * 32 + lane) & kk) == 0;
-            if (key_less(L[k2], J[k2], L[k], J[k]) == up) {
-                const uint64_t tl = L[k];
-                L[k] = L[k2];
-                L[k2] = tl;
-                const uint32_t tj = J[k];
-                J[k] = J[k2];
-                J[k2] = tj;
-                const unsigned long long tw = Wt[k];
-                Wt[k] = Wt[k2];
-                Wt[k2] = tw;
-            }
-        }
-    }
+// Bucket lists of one group held in shared memory: member i's key, weight
+// and census slot, the first member of each bucket's list (-1: empty) and
+// the next member of the same bucket.
+struct BucketView {
+    uint64_t* lin;
+    unsigned long long* w;
+    uint32_t* j;
+    int* next;
+    int* head;
+};
+
+// member i of a group into its bucket's list (bucket = the top bits of the
+// lineage key, `sh` = 64 - log2(buckets))
+__device__ __forceinline__ void bucket_insert(const BucketView& B, const MemberRec& m, int i, int sh) {
+    B.lin[i] = m.lin;
+    B.w[i] = m.wfx;
+    B.j[i] = m.j;
+    const int b = (int)(m.lin >> sh);
+    B.next[i] = atomicExch(&B.head[b], i);
 }
 
-template <int K>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&L)[K], uint32_t (&J)[K], unsigned long long (&Wt)[K],
-                                             int lane) {
-    for (int kk = 2; kk <= 32 * K; kk <<= 1) {
-        for (int h = kk >> 1; h >= 32; h >>= 1) {
-            const int hs = h >> 5;
-            if (hs == 1) slot_phase<K, 1>(L, J, Wt, lane, kk);
-            if (K >= 4 && hs == 2) slot_phase<K, 2>(L, J, Wt, lane, kk);
-            if (K >= 8 && hs == 4) slot_phase<K, 4>(L, J, Wt, lane, kk);
-        }
-        for (int h = min(kk >> 1, 16); h > 0; h >>= 1) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const uint64_t pl = __shfl_xor_sync(0xffffffffu, L[k], h);
-                const uint32_t pj = __shfl_xor_sync(0xffffffffu, J[k], h);
-                const unsigned long long pw = __shfl_xor_sync(0xffffffffu, Wt[k], h);
-                const int i = k * 32 + lane;
-                const bool up = (i & kk) == 0;
-                // the lower index of the pair keeps the smaller key when the
-                // run sorts up, the larger when it sorts down
-                const bool keep_min = (((i & h) == 0) == up);
-                const bool take = keep_min ? key_less(pl, pj, L[k], J[k]) : key_less(L[k], J[k], pl, pj);
-                if (take) {
-                    L[k] = pl;
-                    J[k] = pj;
-                    Wt[k] = pw;
+// total weight of buckets [b0, b1)
+__device__ __forceinline__ unsigned long long bucket_sum(const BucketView& B, int b0, int b1) {
+    unsigned long long t = 0;
+    for (int b = b0; b < b1; ++b)
+        for (int k = B.head[b]; k >= 0; k = B.next[k]) t += B.w[k];
+    return t;
+}
+
+// the prefixes of the members of buckets [b0, b1), `run` the weight before
+// bucket b0: the bucket's run plus the weights of the members of the same
+// bucket with a smaller (lineage, slot) key; counts members with an equal
+// lineage before each member (hash collisions) into coll
+template <class Real>
+__device__ __forceinline__ void bucket_prefixes(const CombArgs<Real>& a, const BucketView& B, int b0, int b1,
+                                                unsigned long long run, unsigned long long& coll) {
+    for (int b = b0; b < b1; ++b) {
+        unsigned long long bsum = 0;
+        for (int k = B.head[b]; k >= 0; k = B.next[k]) {
+            const uint64_t lk = B.lin[k];
+            const uint32_t jk = B.j[k];
+            unsigned long long pre = run;
+            for (int u = B.head[b]; u >= 0; u = B.next[u]) {
+                if (key_less(B.lin[u], B.j[u], lk, jk)) {
+                    pre += B.w[u];
+                    if (B.lin[u] == lk) ++coll;
                 }
             }
+            a.cpre[jk] = pre;
+            bsum += B.w[k];
         }
+        run += bsum;
     }
 }
 
-// one group of 33..32 K members by a warp: sort in registers, then the
-// exclusive scan of the sorted weights (slot by slot: the slots before, then
-// the lanes before in the same slot) gives each member's comb prefix
-template <class Real, int K>
-__device__ __forceinline__ void mid_group(const CombArgs<Real>& a, const GroupRec& G, int lane, uint64_t* spill,
-                                          unsigned long long& coll) {
-    const int g = (int)G.cnt;
-    uint64_t L[K];
-    uint32_t J[K];
-    unsigned long long Wt[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int i = k * 32 + lane;
-        if (i < g) {
-            const uint32_t jj = a.member[G.off + i];
-            const LinW x = a.clw[jj];
-            L[k] = x.lin;
-            J[k] = jj;
-            Wt[k] = x.wfx;
-        } else {  // padding sorts last and weighs nothing
-            L[k] = ~0ull;
-            J[k] = 0xFFFFFFFFu;
-            Wt[k] = 0;
-        }
-    }
-    warp_bitonic<K>(L, J, Wt, lane);
-    unsigned long long before = G.offw;  // weight of the slots before
-    bool eq = false;                     // an equal lineage right before some member
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        unsigned long long inc = Wt[k];
+// the number of buckets for g members: a power of two >= g, at least `lo`;
+// returns log2 of it
+__device__ __forceinline__ int bucket_bits(uint32_t g, int lo_bits) {
+    int bits = lo_bits;
+    while ((1u << bits) < g) ++bits;
+    return bits;
+}
+
+// one warp per group of 33..MID_MAX members: bucket lists in the warp's
+// share of shared memory (at least 32 buckets, a lane owns nb / 32
+// consecutive ones), a shuffle scan of the lanes' bucket weights
+template <class Real>
+__global__ void __launch_bounds__(32 * MID_WARPS) comb_mid_kernel(CombArgs<Real> a) {
+    __shared__ uint64_t s_lin[MID_WARPS][MID_MAX];
+    __shared__ unsigned long long s_w[MID_WARPS][MID_MAX];
+    __shared__ uint32_t s_j[MID_WARPS][MID_MAX];
+    __shared__ int s_next[MID_WARPS][MID_MAX];
+    __shared__ int s_head[MID_WARPS][MID_MAX];
+    const unsigned long long n = a.glist_n[MID_CLASS];
+    const uint32_t* list = a.glist + a.glist_off[MID_CLASS];
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const BucketView B{s_lin[wp], s_w[wp], s_j[wp], s_next[wp], s_head[wp]};
+    unsigned long long coll = 0;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * MID_WARPS + wp; e < n;
+         e += (unsigned long long)gridDim.x * MID_WARPS) {  // warp-uniform
+        const GroupRec G = a.gro[list[e]];
+        const int g = (int)G.cnt;
+        const int bits = bucket_bits(G.cnt, 5);
+        const int nb = 1 << bits, per = nb >> 5;
+        for (int b = lane; b < nb; b += 32) B.head[b] = -1;
+        __syncwarp();
+        for (int i = lane; i < g; i += 32) bucket_insert(B, a.member[G.off + i], i, 64 - bits);
+        __syncwarp();
+        const int b0 = lane * per;
+        const unsigned long long lsum = bucket_sum(B, b0, b0 + per);
+        unsigned long long inc = lsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
-        const int i = k * 32 + lane;
-        if (i < g) a.cpre[J[k]] = before + (inc - Wt[k]);
-        before += __shfl_sync(0xffffffffu, inc, 31);
-        // the sorted element before this one: lane - 1 of this slot, or lane
-        // 31 of the slot before
-        uint64_t prev = __shfl_up_sync(0xffffffffu, L[k], 1);
-        if (k > 0) {
-            const uint64_t last = __shfl_sync(0xffffffffu, L[k - 1], 31);
-            if (lane == 0) prev = last;
-        }
-        if (i > 0 && i < g && prev == L[k]) eq = true;
-    }
-    if (__any_sync(0xffffffffu, eq)) {
-        // equal lineages (a hash collision; essentially never): count the
-        // earlier members with the same lineage for every member, exactly
-#pragma unroll
-        for (int k = 0; k < K; ++k) spill[k * 32 + lane] = L[k];
+        bucket_prefixes(a, B, b0, b0 + per, G.offw + (inc - lsum), coll);
         __syncwarp();
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int i = k * 32 + lane;
-            if (i < g)
-                for (int b = i - 1; b >= 0 && spill[b] == L[k]; --b) ++coll;
-        }
-        __syncwarp();
-    }
-}
-
-// one warp per group of 33..MID_MAX members (the sort in registers: 2, 4 or
-// 8 members per lane)
-template <class Real>
-__global__ void __launch_bounds__(32 * MID_WARPS) comb_mid_kernel(CombArgs<Real> a) {
-    __shared__ uint64_t s_spill[MID_WARPS][MID_MAX];
-    const unsigned long long n = a.glist_n[MID_CLASS];
-    const uint32_t* list = a.glist + a.glist_off[MID_CLASS];
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned long long coll = 0;
-    for (unsigned long long e = (unsigned long long)blockIdx.x * MID_WARPS + wp; e < n;
-         e += (unsigned long long)gridDim.x * MID_WARPS) {  // warp-uniform
-        const GroupRec G = a.gro[list[e]];
-        if (G.cnt <= 64)
-            mid_group<Real, 2>(a, G, lane, s_spill[wp], coll);
-        else if (G.cnt <= 128)
-            mid_group<Real, 4>(a, G, lane, s_spill[wp], coll);
-        else
-            mid_group<Real, 8>(a, G, lane, s_spill[wp], coll);
     }
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
 
-// one block per group of more than MID_MAX members: bitonic sort by
-// (lineage, slot) in shared memory and a scan of the sorted weights (each
-// thread a contiguous run, joined by a shuffle scan per warp and one over
-// the warps' totals); groups beyond BIG_CAP members take the rank count
-// with the block's threads
+// dynamic shared memory of the block-per-group kernel: keys, weights, slots,
+// list links and bucket heads of BIG_CAP members
+constexpr size_t BIG_SMEM = (size_t)BIG_CAP * (8 + 8 + 4 + 4 + 4);
+
+// one block per group of more than MID_MAX members: bucket lists in shared
+// memory (a thread owns nb / BIG_T consecutive buckets, at least one), a
+// block scan of the threads' bucket weights; groups beyond BIG_CAP members
+// take the rank count with the block's threads
 template <class Real>
 __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
-    __shared__ uint64_t s_lin[BIG_CAP];
-    __shared__ unsigned long long s_w[BIG_CAP];
-    __shared__ uint32_t s_j[BIG_CAP];
+    extern __shared__ unsigned long long s_big[];
     __shared__ unsigned long long s_wsum[BIG_T / 32];
+    const BucketView B{reinterpret_cast<uint64_t*>(s_big), s_big + BIG_CAP,
+                       reinterpret_cast<uint32_t*>(s_big + 2 * BIG_CAP),
+                       reinterpret_cast<int*>(s_big + 2 * BIG_CAP) + BIG_CAP,
+                       reinterpret_cast<int*>(s_big + 2 * BIG_CAP) + 2 * BIG_CAP};
     const unsigned long long nbig = a.glist_n[BIG_CLASS];
     const uint32_t* list = a.glist + a.glist_off[BIG_CLASS];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -472,66 +442,28 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
         const unsigned long long C = G.offw;
         if (g > (uint32_t)BIG_CAP) {
             for (uint32_t t = threadIdx.x; t < g; t += blockDim.x) {
-                const uint32_t jt = a.member[base + t];
-                const uint64_t lt = a.clw[jt].lin;
+                const MemberRec mt = a.member[base + t];
                 unsigned long long C0 = C;
                 for (uint32_t u = 0; u < g; ++u) {
-                    const uint32_t ju = a.member[base + u];
-                    const LinW xu = a.clw[ju];
-                    const uint64_t lu = xu.lin;
-                    if (key_less(lu, ju, lt, jt)) {
-                        C0 += xu.wfx;
-                        if (lu == lt) ++coll;
+                    const MemberRec mu = a.member[base + u];
+                    if (key_less(mu.lin, mu.j, mt.lin, mt.j)) {
+                        C0 += mu.wfx;
+                        if (mu.lin == mt.lin) ++coll;
                     }
                 }
-                a.cpre[jt] = C0;
+                a.cpre[mt.j] = C0;
             }
             continue;
         }
-        int P = 1;
-        while (P < (int)g) P <<= 1;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            if (i < (int)g) {
-                const uint32_t jj = a.member[base + i];
-                const LinW x = a.clw[jj];
-                s_j[i] = jj;
-                s_lin[i] = x.lin;
-                s_w[i] = x.wfx;
-            } else {  // padding sorts last and weighs nothing
-                s_lin[i] = ~0ull;
-                s_j[i] = 0xFFFFFFFFu;
-                s_w[i] = 0;
-            }
-        }
+        const int bits = bucket_bits(g, 8);  // at least BIG_T buckets
+        const int nb = 1 << bits, per = nb / BIG_T;
+        for (int b = threadIdx.x; b < nb; b += BIG_T) B.head[b] = -1;
         __syncthreads();
-        for (int kk = 2; kk <= P; kk <<= 1) {
-            for (int h = kk >> 1; h > 0; h >>= 1) {
-                for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                    const int l = i ^ h;
-                    if (l > i) {
-                        const bool up = (i & kk) == 0;
-                        if (key_less(s_lin[l], s_j[l], s_lin[i], s_j[i]) == up) {
-                            const uint64_t tl = s_lin[i];
-                            s_lin[i] = s_lin[l];
-                            s_lin[l] = tl;
-                            const uint32_t tj = s_j[i];
-                            s_j[i] = s_j[l];
-                            s_j[l] = tj;
-                            const unsigned long long tw = s_w[i];
-                            s_w[i] = s_w[l];
-                            s_w[l] = tw;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        // exclusive scan of the sorted weights: each thread a contiguous run
-        const int per = (P + BIG_T - 1) / BIG_T;
-        const int i0 = threadIdx.x * per, i1 = min((int)g, i0 + per);
-        unsigned long long run = 0;
-        for (int i = i0; i < i1; ++i) run += s_w[i];
-        unsigned long long inc = run;
+        for (int i = threadIdx.x; i < (int)g; i += BIG_T) bucket_insert(B, a.member[base + i], i, 64 - bits);
+        __syncthreads();
+        const int b0 = threadIdx.x * per;
+        const unsigned long long tsum = bucket_sum(B, b0, b0 + per);
+        unsigned long long inc = tsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -541,13 +473,7 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
         __syncthreads();
         unsigned long long wbase = 0;
         for (int k = 0; k < wp; ++k) wbase += s_wsum[k];
-        unsigned long long C0 = C + wbase + (inc - run);
-        for (int i = i0; i < i1; ++i) {
-            // members with an equal lineage before this one (collisions)
-            for (int b = i - 1; b >= 0 && s_lin[b] == s_lin[i]; --b) ++coll;
-            a.cpre[s_j[i]] = C0;
-            C0 += s_w[i];
-        }
+        bucket_prefixes(a, B, b0, b0 + per, C + wbase + (inc - tsum), coll);
         __syncthreads();
     }
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
@@ -817,7 +743,7 @@ void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
     comb_groups_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_seg_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_mid_kernel<Real><<<grid, 32 * MID_WARPS, 0, s>>>(a);
-    comb_big_kernel<Real><<<grid, BIG_T, 0, s>>>(a);
+    comb_big_kernel<Real><<<grid, BIG_T, BIG_SMEM, s>>>(a);
     comb_write_kernel<Real><<<grid, 256, sizeof(long long) * 3 * (size_t)a.I, s>>>(a);
     if (a.P2 > 0) {  // about one block per SM (and score): few plane flushes
         const size_t all = sizeof(long long) * 3 * (size_t)a.P2 * (size_t)a.I;
@@ -846,8 +772,10 @@ void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s) {
 
 template <class Real>
 int comb_write_smem_optin(size_t smem) {
-    const int e = raise_smem_limit((const void*)comb_write_kernel<Real>, smem);
-    return e ? e : raise_smem_limit((const void*)deriv_census_kernel<Real>, smem);
+    int e = raise_smem_limit((const void*)comb_write_kernel<Real>, smem);
+    if (!e) e = raise_smem_limit((const void*)deriv_census_kernel<Real>, smem);
+    // the block-per-group pass's lists have a fixed size
+    return e ? e : raise_smem_limit((const void*)comb_big_kernel<Real>, BIG_SMEM);
 }
 
 // the all-scores census derivative pass: its planes, when they fit

@@ -14,6 +14,17 @@ struct __align__(16) GroupRec {
     uint32_t cnt;
 };
 
+// One census particle in its group's member list: its lineage key and comb
+// weight (copied from the census bank by the scatter pass, so that the
+// passes over groups read their members contiguously instead of gathering
+// them) and its census slot, in one 32-byte sector.
+struct __align__(32) MemberRec {
+    uint64_t lin;
+    unsigned long long wfx;
+    uint32_t j;
+    uint32_t pad[3];
+};
+
 struct ScanArgs {
     const uint32_t* cnt;
     const unsigned long long* w;
@@ -46,7 +57,7 @@ struct CombArgs {
     const uint32_t* gcnt;
     const GroupRec* gro;  // [N+1] group records (entry N: totals)
     uint32_t* gcur;
-    uint32_t* member;
+    MemberRec* member;
     BankRec<Real>* bank;  // next start bank
     unsigned long long* stats;
     unsigned* err;
@@ -72,6 +83,8 @@ template <class Real>
 void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s);
 template <class Real>
 void launch_comb_finalize(const CombArgs<Real>& a, cudaStream_t s);
+// raises the comb passes' dynamic shared memory limits (census tallies of
+// `smem` bytes, the large groups' bucket lists)
 template <class Real>
 int comb_write_smem_optin(size_t smem);
 template <class Real>
