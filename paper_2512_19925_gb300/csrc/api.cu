@@ -87,7 +87,9 @@ struct hww_problem {
     LosmWork work{};
     StepDev* sd = nullptr;
     unsigned* err = nullptr;
-    unsigned long long* h_count = nullptr;  // pinned
+    // pinned: after each tracking wave the record count, the census count and
+    // the error word (its low 32 bits), read with one synchronize
+    unsigned long long* h_count = nullptr;
     // host state
     int xs_set = 0, ww_set = 0;
     double rho = 1.0, eps = 1e-3;
@@ -400,6 +402,9 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b, long long lo = 0, long lo
     for (;;) {
         HWW_CK(cudaMemcpyAsync(p->h_count, b.q[cur].count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                p->stream));
+        HWW_CK(cudaMemcpyAsync(p->h_count + 1, p->counts, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               p->stream));
+        HWW_CK(cudaMemcpyAsync(p->h_count + 2, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
         HWW_CK(cudaStreamSynchronize(p->stream));
         account_track_time(p);
         p->q_peak = std::max(p->q_peak, (long long)*p->h_count);
@@ -873,13 +878,13 @@ hww_status track_with_regrow(hww_problem* p) {
         hww_status s = stage_pre(p);
         if (s) return s;
         p->q_peak = 0;
+        p->h_count[2] = 0;
         s = p->fp32 ? track_step(p, p->b32) : track_step(p, p->b64);
         if (s) return s;
-        unsigned e = 0;
-        unsigned long long ncen = 0;
-        HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
-        HWW_CK(cudaMemcpyAsync(&ncen, p->counts, sizeof(ncen), cudaMemcpyDeviceToHost, p->stream));
-        HWW_CK(cudaStreamSynchronize(p->stream));
+        // the step's tracking ends with a wave; its synchronize read the
+        // census count and the error word
+        const unsigned e = (unsigned)p->h_count[2];
+        const unsigned long long ncen = p->h_count[1];
         if (!(e & (ERR_CENSUS_OVERFLOW | ERR_QUEUE_OVERFLOW)) || attempt >= MAX_REGROW) return HWW_OK;
         s = regrow_banks(p, (long long)ncen, p->q_peak);
         if (s) return s;
@@ -1042,7 +1047,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         destroy_problem(p);
         return s;
     }
-    if (cudaMallocHost(&p->h_count, sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMallocHost(&p->h_count, 3 * sizeof(unsigned long long)) != cudaSuccess) {
         p->h_count = nullptr;
         destroy_problem(p);
         return HWW_ERR_OOM;

@@ -523,16 +523,17 @@ __device__ __forceinline__ long long first_tooth(unsigned long long C, unsigned 
 // fixed-point weight W = round(w 2^S) and, from the FP32 tally weight
 // a = fl32(w 2^S), round(a mu) and round(a (1/3 - mu^2)) (the event loop's
 // rule for its track-length contributions)
-__device__ __forceinline__ void census_terms(double w, double mu, double tscale, long long& c0, long long& c1,
+__device__ __forceinline__ void census_terms(double w, double mu, double tscale, int, long long& c0, long long& c1,
                                              long long& c2) {
     c0 = to_fixed(w, tscale);
     c1 = to_fixed(w * mu, tscale);
     c2 = to_fixed(w * (1.0 / 3.0 - mu * mu), tscale);
 }
-__device__ __forceinline__ void census_terms(double w, float mu, double tscale, long long& c0, long long& c1,
+__device__ __forceinline__ void census_terms(double w, float mu, double, int S, long long& c0, long long& c1,
                                              long long& c2) {
-    c0 = to_fixed(w, tscale);
-    const float a = tally_weight(w, tscale);
+    // the same roundings from the bits of w (no FP64 instruction)
+    c0 = fixed_bits(w, S);
+    const float a = tally_weight_bits(w, S);
     c1 = fx_mul24(a, mu);
     c2 = fx_mul24(a, 1.0f / 3.0f - mu * mu);
 }
@@ -548,11 +549,12 @@ __global__ void census_tally_kernel(CombArgs<Real> a) {
     const long long m = (long long)*a.ncensus_ptr;
     const long long mm = m < a.cen_cap ? m : a.cen_cap;
     const double tscale = a.sd->tscale;
+    const int S = a.sd->S;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
         const int k = a.ccell[j];
         long long c0, c1, c2;
-        census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
+        census_terms(a.cw[j], a.cmu[j], tscale, S, c0, c1, c2);
         sadd(&s_cen[k], c0);
         sadd(&s_cen[I + k], c1);
         sadd(&s_cen[2 * I + k], c2);
@@ -645,6 +647,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
     const unsigned long long W = a.gro[a.N].offw;
     const unsigned U = a.sd->U_comb;
     const double tscale = a.sd->tscale;
+    const int S = a.sd->S;
     const ToothScale ts = tooth_scale(W, a.N);
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < mm;
          j += (long long)gridDim.x * blockDim.x) {
@@ -653,7 +656,7 @@ __global__ void comb_write_kernel(CombArgs<Real> a) {
             // per lane and word (a warp aggregation would rarely merge lanes)
             const int k = a.ccell[j];
             long long c0, c1, c2;
-            census_terms(a.cw[j], a.cmu[j], tscale, c0, c1, c2);
+            census_terms(a.cw[j], a.cmu[j], tscale, S, c0, c1, c2);
             sadd(&s_cen[k], c0);
             sadd(&s_cen[I + k], c1);
             sadd(&s_cen[2 * I + k], c2);
