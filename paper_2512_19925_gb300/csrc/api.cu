@@ -486,12 +486,15 @@ hww_status comb_step(hww_problem* p, Banks<Real>& b) {
     s.tile_c = p->tile_c;
     s.tile_w = p->tile_w;
     s.out = p->gro;
+    s.glist = p->glist;
+    glist_offsets(p->cen_cap, s.glist_off);
+    s.glist_n = p->counts + 3;
     launch_group_scan(s, p->stream);
     HWW_CK(cudaGetLastError());
     p->kernel_launches += (group_scan_tiles(p->N) > 0) ? 3 : 1;
     launch_comb(comb_args(p, b), comb_grid(p), p->stream);
     HWW_CK(cudaGetLastError());
-    p->kernel_launches += 6 + (p->P2 > 0 ? 1 : 0);
+    p->kernel_launches += 5 + (p->P2 > 0 ? 1 : 0);
     return HWW_OK;
 }
 

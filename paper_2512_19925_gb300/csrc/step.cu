@@ -104,20 +104,98 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_tile_sums_kernel(ScanArgs a, 
     if (threadIdx.x == 0) a.out[a.n] = GroupRec{carry.w, (uint32_t)carry.c, 0u};
 }
 
+// size classes of the comb's group lists (step_kernels.cuh): pairs, groups
+// of 3-4, 5-8, 9-16, 17-32 members (warp segments), 33..MID_MAX (a warp per
+// group), more (a block per group)
+constexpr int MID_CLASS = 5;
+constexpr int BIG_CLASS = 6;
+constexpr int MID_MAX = 256;
+static_assert(COMB_LISTS == BIG_CLASS + 1, "one list per size class");
+
+__device__ __forceinline__ int size_class(uint32_t g) {
+    return g == 2 ? 0 : g <= 4 ? 1 : g <= 8 ? 2 : g <= 16 ? 3 : g <= 32 ? 4 : g <= (uint32_t)MID_MAX ? MID_CLASS
+                                                                                                   : BIG_CLASS;
+}
+
+// The scan's last pass: each tile's records (staged in shared memory, so
+// that they are written coalesced) and the ids of its groups of two or more
+// members appended to their size class's list.  A thread's per-class counts
+// are 16-bit fields of two words (classes 0-3, 4-6; a tile has at most 2048
+// groups), scanned over the block, so each class takes one global
+// reservation per tile.
 __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
+    __shared__ GroupRec s_out[SCAN_TILE];
+    __shared__ unsigned long long s_wa[SCAN_BLOCK / 32], s_wb[SCAN_BLOCK / 32];
+    __shared__ unsigned long long s_gbase[COMB_LISTS];
     const long long base = (long long)blockIdx.x * SCAN_TILE;
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
     Pair v[SCAN_ITEMS];
     Pair s{0ull, 0ull};
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = load_pair(a.cnt, a.w, base + (long long)threadIdx.x * SCAN_ITEMS + k, a.n);
+        v[k] = load_pair(a.cnt, a.w, base + (long long)t * SCAN_ITEMS + k, a.n);
         s = padd(s, v[k]);
     }
     block_exclusive_scan(s);
     Pair run{a.tile_c[blockIdx.x] + s.c, a.tile_w[blockIdx.x] + s.w};
+    int kc[SCAN_ITEMS];
+    unsigned long long A = 0, B = 0;  // this thread's groups per class, 16-bit fields
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        const long long i = base + (long long)threadIdx.x * SCAN_ITEMS + k;
-        if (i < a.n) a.out[i] = GroupRec{run.w, (uint32_t)run.c, (uint32_t)v[k].c};
+        s_out[t * SCAN_ITEMS + k] = GroupRec{run.w, (uint32_t)run.c, (uint32_t)v[k].c};
         run = padd(run, v[k]);
+        kc[k] = v[k].c >= 2 ? size_class((uint32_t)v[k].c) : -1;
+        if (kc[k] >= 4)
+            B += 1ull << (16 * (kc[k] - 4));
+        else if (kc[k] >= 0)
+            A += 1ull << (16 * kc[k]);
+    }
+    unsigned long long ia = A, ib = B;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long ya = __shfl_up_sync(0xffffffffu, ia, o);
+        const unsigned long long yb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += ya;
+            ib += yb;
+        }
+    }
+    if (lane == 31) {
+        s_wa[wp] = ia;
+        s_wb[wp] = ib;
+    }
+    __syncthreads();
+    if (wp == 0) {
+        constexpr int NW = SCAN_BLOCK / 32;
+        const unsigned long long xa = lane < NW ? s_wa[lane] : 0ull, xb = lane < NW ? s_wb[lane] : 0ull;
+        unsigned long long ja = xa, jb = xb;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long ya = __shfl_up_sync(0xffffffffu, ja, o);
+            const unsigned long long yb = __shfl_up_sync(0xffffffffu, jb, o);
+            if (lane >= o) {
+                ja += ya;
+                jb += yb;
+            }
+        }
+        if (lane < NW) {
+            s_wa[lane] = ja - xa;
+            s_wb[lane] = jb - xb;
+        }
+        if (lane == NW - 1) {
+            for (int c = 0; c < COMB_LISTS; ++c) {
+                const unsigned long long n = ((c < 4 ? ja : jb) >> (16 * (c & 3))) & 0xFFFFull;
+                s_gbase[c] = n ? atomicAdd(&a.glist_n[c], n) : 0ull;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < SCAN_TILE; i += SCAN_BLOCK)
+        if (base + i < a.n) a.out[base + i] = s_out[i];
+    unsigned long long ea = s_wa[wp] + ia - A, eb = s_wb[wp] + ib - B;  // groups before this thread's
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int c = kc[k];
+        if (c < 0) continue;
+        unsigned long long& e = c < 4 ? ea : eb;
+        const unsigned long long pos = s_gbase[c] + ((e >> (16 * (c & 3))) & 0xFFFFull);
+        a.glist[a.glist_off[c] + pos] = (uint32_t)(base + (long long)t * SCAN_ITEMS + k);
+        e += 1ull << (16 * (c & 3));
     }
 }
 
@@ -131,9 +209,10 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
 // offset plus the weights of the group members before it.  Most groups have
 // one member: its C0 is set by the scatter pass, which lists only the members
 // of larger groups (each with its key and weight, so that the group passes
-// read their members contiguously); their prefixes are found once per group:
-// pairs by one thread, groups of up to 32 by a warp segment of 4 to 32 lanes
-// (a rank count over shuffles), larger groups by a warp (up to 256 members)
+// read their members contiguously); the scan's last pass lists the groups by
+// size class, and their prefixes are found once per group: groups of up to
+// 32 by a warp segment of 2 to 32 lanes (a rank count over shuffles), larger
+// groups by a warp (up to 256 members)
 // or a block with bucket lists: the lineage keys are uniform hashes, so
 // bucketing members by the top bits of the key into at least as many buckets
 // as members leaves about one member per bucket, the buckets are in key
@@ -142,14 +221,9 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
 // The copies are then written in census order, reading the census bank and
 // the stored prefixes coalesced.
 // ---------------------------------------------------------------------------
-constexpr int MID_CLASS = 4;   // 33..MID_MAX members: a warp per group
-constexpr int BIG_CLASS = 5;   // more: a block per group
-constexpr int MID_MAX = 256;
 constexpr int MID_WARPS = 4;   // warps (groups in flight) per block of the warp-per-group kernel
 constexpr int BIG_CAP = 4096;  // members a block keeps in shared memory
 constexpr int BIG_T = 256;
-static_assert(COMB_LISTS == BIG_CLASS + 1, "one list per size class");
-
 template <class Real>
 __global__ void comb_scatter_kernel(CombArgs<Real> a) {
     const long long m = (long long)*a.ncensus_ptr;
@@ -175,79 +249,6 @@ __global__ void comb_scatter_kernel(CombArgs<Real> a) {
 
 __device__ __forceinline__ bool key_less(uint64_t la, uint32_t ja, uint64_t lb, uint32_t jb) {
     return la < lb || (la == lb && ja < jb);
-}
-
-// size class of a group: 3-4, 5-8, 9-16, 17-32 members -> 0..3, 33..MID_MAX
-// -> MID_CLASS, larger -> BIG_CLASS
-__device__ __forceinline__ int size_class(uint32_t g) {
-    return g <= 4 ? 0 : g <= 8 ? 1 : g <= 16 ? 2 : g <= 32 ? 3 : g <= (uint32_t)MID_MAX ? MID_CLASS : BIG_CLASS;
-}
-
-// one block per contiguous id range: a pair is ordered on the spot; groups
-// of three or more go to the list of their size class, in two passes over
-// the range (count, then write) so that each block reserves its list space
-// with one global atomic per class
-template <class Real>
-__global__ void comb_groups_kernel(CombArgs<Real> a) {
-    __shared__ unsigned long long s_cnt[COMB_LISTS], s_pos[COMB_LISTS];
-    const long long chunk = (a.N + gridDim.x - 1) / gridDim.x;
-    const long long lo = (long long)blockIdx.x * chunk;
-    const long long hi = min(a.N, lo + chunk);
-    if (threadIdx.x < COMB_LISTS) s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    unsigned long long coll = 0;
-    unsigned c[COMB_LISTS] = {};
-    for (long long id = lo + threadIdx.x; id < hi; id += blockDim.x) {
-        const uint32_t g = a.gcnt[id];
-        if (g < 2) continue;
-        if (g == 2) {
-            const GroupRec G = a.gro[id];
-            const unsigned long long base = G.off;
-            const MemberRec p0 = a.member[base], p1 = a.member[base + 1];
-            const uint32_t j0 = p0.j, j1 = p1.j;
-            const uint64_t l0 = p0.lin, l1 = p1.lin;
-            const bool first0 = key_less(l0, j0, l1, j1);
-            const unsigned long long C = G.offw;
-            a.cpre[first0 ? j0 : j1] = C;
-            a.cpre[first0 ? j1 : j0] = C + (first0 ? p0.wfx : p1.wfx);
-            if (l0 == l1) ++coll;
-            continue;
-        }
-        const int k = size_class(g);
-#pragma unroll
-        for (int kk = 0; kk < COMB_LISTS; ++kk) c[kk] += (kk == k) ? 1u : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < COMB_LISTS; ++k) {
-        unsigned v = c[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31u) == 0 && v) atomicAdd(&s_cnt[k], (unsigned long long)v);
-    }
-    __syncthreads();
-    if (threadIdx.x < COMB_LISTS) {
-        const unsigned long long n = s_cnt[threadIdx.x];
-        s_pos[threadIdx.x] = n ? atomicAdd(&a.glist_n[threadIdx.x], n) : 0ull;
-    }
-    __syncthreads();
-    // the whole block walks the range in step (the loop bound is uniform), so
-    // every warp is converged at the appends: one shared atomic per class
-    // and warp
-    const unsigned lane = threadIdx.x & 31u;
-    for (long long id0 = lo; id0 < hi; id0 += blockDim.x) {
-        const long long id = id0 + threadIdx.x;
-        const uint32_t g = (id < hi) ? a.gcnt[id] : 0u;
-        const int kc = (g >= 3) ? size_class(g) : -1;
-#pragma unroll
-        for (int k = 0; k < COMB_LISTS; ++k) {
-            const unsigned bal = __ballot_sync(0xffffffffu, kc == k);
-            if (!bal) continue;
-            unsigned long long base = 0;
-            if (lane == (unsigned)(__ffs(bal) - 1)) base = atomicAdd(&s_pos[k], (unsigned long long)__popc(bal));
-            base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-            if (kc == k) a.glist[a.glist_off[k] + base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)id;
-        }
-    }
-    if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
 
 // warp segments of S lanes, one group of at most S members per segment:
@@ -291,24 +292,28 @@ __device__ __forceinline__ void seg_groups(const CombArgs<Real>& a, const uint32
     if ((uint32_t)li < g) a.cpre[jj] = C + C0;
 }
 
-// the four warp-segment classes (3-4, 5-8, 9-16, 17-32 members) in one
-// launch: warp task t takes the next 32/S groups of its class's list
+// the five warp-segment classes (pairs, 3-4, 5-8, 9-16, 17-32 members) in
+// one launch: warp task t takes the next 32/S groups of its class's list
 template <class Real>
 __global__ void comb_seg_kernel(CombArgs<Real> a) {
-    const unsigned long long n0 = a.glist_n[0], n1 = a.glist_n[1], n2 = a.glist_n[2], n3 = a.glist_n[3];
-    const unsigned long long t1 = (n0 + 7) / 8, t2 = t1 + (n1 + 3) / 4, t3 = t2 + (n2 + 1) / 2, t4 = t3 + n3;
+    const unsigned long long n0 = a.glist_n[0], n1 = a.glist_n[1], n2 = a.glist_n[2], n3 = a.glist_n[3],
+                             n4 = a.glist_n[4];
+    const unsigned long long t1 = (n0 + 15) / 16, t2 = t1 + (n1 + 7) / 8, t3 = t2 + (n2 + 3) / 4,
+                             t4 = t3 + (n3 + 1) / 2, t5 = t4 + n4;
     const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarp = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     unsigned long long coll = 0;
-    for (unsigned long long t = warp; t < t4; t += nwarp) {  // warp-uniform branches
+    for (unsigned long long t = warp; t < t5; t += nwarp) {  // warp-uniform branches
         if (t < t1)
-            seg_groups<Real, 4>(a, a.glist + a.glist_off[0], n0, t * 8, coll);
+            seg_groups<Real, 2>(a, a.glist + a.glist_off[0], n0, t * 16, coll);
         else if (t < t2)
-            seg_groups<Real, 8>(a, a.glist + a.glist_off[1], n1, (t - t1) * 4, coll);
+            seg_groups<Real, 4>(a, a.glist + a.glist_off[1], n1, (t - t1) * 8, coll);
         else if (t < t3)
-            seg_groups<Real, 16>(a, a.glist + a.glist_off[2], n2, (t - t2) * 2, coll);
+            seg_groups<Real, 8>(a, a.glist + a.glist_off[2], n2, (t - t2) * 4, coll);
+        else if (t < t4)
+            seg_groups<Real, 16>(a, a.glist + a.glist_off[3], n3, (t - t3) * 2, coll);
         else
-            seg_groups<Real, 32>(a, a.glist + a.glist_off[3], n3, t - t3, coll);
+            seg_groups<Real, 32>(a, a.glist + a.glist_off[4], n4, t - t4, coll);
     }
     if (coll) atomicAdd(&a.stats[ST_LINEAGE], coll);
 }
@@ -743,7 +748,6 @@ long long group_scan_tiles(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE
 template <class Real>
 void launch_comb(const CombArgs<Real>& a, int grid, cudaStream_t s) {
     comb_scatter_kernel<Real><<<grid, 256, 0, s>>>(a);
-    comb_groups_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_seg_kernel<Real><<<grid, 256, 0, s>>>(a);
     comb_mid_kernel<Real><<<grid, 32 * MID_WARPS, 0, s>>>(a);
     comb_big_kernel<Real><<<grid, BIG_T, BIG_SMEM, s>>>(a);

@@ -25,6 +25,13 @@ struct __align__(32) MemberRec {
     uint32_t pad[3];
 };
 
+// lists of comb groups of 2+ members by size: 2, 3-4, 5-8, 9-16, 17-32 (warp
+// segments), 33-256 (a warp per group), more (a block per group); a list
+// whose groups have at least COMB_LIST_MIN[k] members holds at most
+// census / COMB_LIST_MIN[k] of them
+constexpr int COMB_LISTS = 7;
+constexpr long long COMB_LIST_MIN[COMB_LISTS] = {2, 3, 5, 9, 17, 33, 257};
+
 struct ScanArgs {
     const uint32_t* cnt;
     const unsigned long long* w;
@@ -32,14 +39,11 @@ struct ScanArgs {
     unsigned long long* tile_c;
     unsigned long long* tile_w;
     GroupRec* out;  // n+1 entries; entry n holds the totals
+    // the group lists by size class, filled by the scan's last pass
+    uint32_t* glist;
+    long long glist_off[COMB_LISTS];
+    unsigned long long* glist_n;  // [COMB_LISTS] list lengths (cleared with the step's accumulators)
 };
-
-// lists of comb groups of 3+ members by size: 3-4, 5-8, 9-16, 17-32 (warp
-// segments), 33-256 (a warp per group), more (a block per group); a list
-// whose groups have at least COMB_LIST_MIN[k] members holds at most
-// census / COMB_LIST_MIN[k] of them
-constexpr int COMB_LISTS = 6;
-constexpr long long COMB_LIST_MIN[COMB_LISTS] = {3, 5, 9, 17, 33, 257};
 
 template <class Real>
 struct CombArgs {
