@@ -58,11 +58,24 @@ WORKLOAD = ("plain_at_scale: slab [-50,50], Sigma_t=1, c=0.9, v=1, 1000 cells, d
 # derivative runs carry 48 B of scores more).
 STATE_BYTES = {"fp32": 40, "fp64": 52}
 SCORE_BYTES = 48
-# DRAM bytes (read + write) that one wave-0 launch of track32_kernel moves per
-# start particle, measured by ncu (profiles/track32_kernel_plain_at_scale_fp32.txt);
-# set to None whenever track32_kernel changes.
-TRACK32_DRAM_BYTES_PER_START = None
-TRACK32_DRAM_NOTE = None
+# DRAM bytes (read + write) that one wave-0 launch of the FP32 tracking
+# kernel of the timed steps (track32_event_kernel) moves per start particle,
+# measured by ncu (profiles/track32_event_kernel_plain_at_scale_fp32.txt);
+# set to None whenever that kernel changes.
+TRACK32_DRAM_BYTES_PER_START = 95.4
+TRACK32_DRAM_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of track32_event_kernel over steps 6..25 "
+                     "at 1e7 particles/step (one pass), mean per launch: 954.0 MB")
+
+
+def tracking_kernel_name(counters):
+    """The FP32 tracking kernel(s) behind a run's track_ms: the event loop
+    (wave 0 under the automatic choice) and/or the warp loop."""
+    ev, tot = counters.get("event_launches", 0), counters["track_launches"]
+    if tot and ev == tot:
+        return "track32_event_kernel"
+    if ev == 0:
+        return "track32_kernel"
+    return "track32_event_kernel (%d launches) + track32_kernel (%d launches)" % (ev, tot - ev)
 # the stored semi-analytic benchmark of the workload's census flux
 PULSE_REFERENCE = os.path.join(ROOT, "tests", "golden", "pulse_census_plain_at_scale.npz")
 
@@ -663,7 +676,7 @@ def main(args):
         if not args.no_shield:
             sh, shrun = run_shield(hww, torch, args.shield_particles, args.shield_steps)
             windows.append(sh.pop("window"))
-            sh["roofline"] = roofline_hbm("track32_kernel", STATE_BYTES["fp32"],
+            sh["roofline"] = roofline_hbm(tracking_kernel_name(shrun["counters"]), STATE_BYTES["fp32"],
                                           args.shield_particles * args.shield_steps,
                                           sum(s["census"] for s in shrun["stats"]), sum(shrun["track_ms"]),
                                           args.shield_steps, peak, peak_kind)
@@ -745,8 +758,8 @@ def main(args):
     # roofline of the dominant kernel (FP32 tracking), bank-streaming bytes
     cnt = fast["counters"]
     track_ms = cnt["track_ms"]
-    roof = roofline_hbm("track32_kernel", STATE_BYTES["fp32"], N * args.steps, fast["census"], track_ms, args.steps,
-                        peak, peak_kind)
+    roof = roofline_hbm(tracking_kernel_name(cnt), STATE_BYTES["fp32"], N * args.steps, fast["census"], track_ms,
+                        args.steps, peak, peak_kind)
     roof["launches"] = cnt["track_launches"]
     roof["traffic"] = TRACK32_DRAM_BYTES_PER_START * N if TRACK32_DRAM_BYTES_PER_START else None
     roof["traffic_note"] = TRACK32_DRAM_NOTE
