@@ -90,6 +90,9 @@ struct hww_problem {
     // pinned: after each tracking wave the record count, the census count and
     // the error word (its low 32 bits), read with one synchronize
     unsigned long long* h_count = nullptr;
+    unsigned long long* d_count = nullptr;  // the device's view of h_count (mapped)
+    StatsExport* h_stats = nullptr;          // pinned, mapped: a step's statistics read back
+    StatsExport* d_stats = nullptr;
     // host state
     int xs_set = 0, ww_set = 0;
     double rho = 1.0, eps = 1e-3;
@@ -385,6 +388,28 @@ void account_track_time(hww_problem* p) {
     if (cudaEventElapsedTime(&ms, p->ev_a, p->ev_b) == cudaSuccess) p->track_ms += ms;
 }
 
+// the host's view of a step's end: counters, step state and error word,
+// written by one small kernel into pinned mapped host memory (one launch and
+// one synchronize instead of small copies into pageable memory)
+__global__ void export_stats_kernel(const unsigned long long* stats, const StepDev* sd, const unsigned* err,
+                                    StatsExport* out) {
+    const int t = threadIdx.x;
+    if (t < ST_COUNT) out->stats[t] = stats[t];
+    if (t == 0) {
+        out->sd = *sd;
+        out->err = *err;
+    }
+}
+
+// after a tracking wave: the record count of its output queue, the census
+// count and the error word, into the mapped h_count
+__global__ void export_wave_kernel(const unsigned long long* qcount, const unsigned long long* ncen,
+                                   const unsigned* err, unsigned long long* out) {
+    out[0] = *qcount;
+    out[1] = *ncen;
+    out[2] = *err;
+}
+
 // the tracking waves of start-bank items [lo, hi): wave 0 from the bank,
 // then record waves until no record is left
 template <class Real>
@@ -400,11 +425,8 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b, long long lo = 0, long lo
     HWW_CK(cudaGetLastError());
     int cur = 0, waves = 1;
     for (;;) {
-        HWW_CK(cudaMemcpyAsync(p->h_count, b.q[cur].count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                               p->stream));
-        HWW_CK(cudaMemcpyAsync(p->h_count + 1, p->counts, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                               p->stream));
-        HWW_CK(cudaMemcpyAsync(p->h_count + 2, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+        export_wave_kernel<<<1, 1, 0, p->stream>>>(b.q[cur].count, p->counts, p->err, p->d_count);
+        HWW_CK(cudaGetLastError());
         HWW_CK(cudaStreamSynchronize(p->stream));
         account_track_time(p);
         p->q_peak = std::max(p->q_peak, (long long)*p->h_count);
@@ -881,7 +903,6 @@ hww_status track_with_regrow(hww_problem* p) {
         hww_status s = stage_pre(p);
         if (s) return s;
         p->q_peak = 0;
-        p->h_count[2] = 0;
         s = p->fp32 ? track_step(p, p->b32) : track_step(p, p->b64);
         if (s) return s;
         // the step's tracking ends with a wave; its synchronize read the
@@ -898,14 +919,12 @@ hww_status track_with_regrow(hww_problem* p) {
 }
 
 hww_status read_stats(hww_problem* p, hww_step_stats* st) {
-    unsigned long long h[ST_COUNT];
-    StepDev sdh;
-    unsigned e = 0;
-    HWW_CK(cudaMemcpyAsync(h, p->stats, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
-    HWW_CK(cudaMemcpyAsync(&sdh, p->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, p->stream));
-    HWW_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+    export_stats_kernel<<<1, 32, 0, p->stream>>>(p->stats, p->sd, p->err, p->d_stats);
+    HWW_CK(cudaGetLastError());
     HWW_CK(cudaStreamSynchronize(p->stream));
-    fill_stats(h, sdh.nbank, sdh.wbar, e, p->last_waves, st);
+    const StatsExport& x = *p->h_stats;
+    const unsigned e = x.err;
+    fill_stats(x.stats, x.sd.nbank, x.sd.wbar, e, p->last_waves, st);
     if (e) HWW_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
     return (hww_status)st->status;
 }
@@ -943,6 +962,7 @@ void destroy_problem(hww_problem* p) {
     free_banks(p);
     cudaStreamSynchronize(p->stream);
     if (p->h_count) cudaFreeHost(p->h_count);
+    if (p->h_stats) cudaFreeHost(p->h_stats);
     if (p->ev_a) cudaEventDestroy(p->ev_a);
     if (p->ev_b) cudaEventDestroy(p->ev_b);
     delete p;
@@ -1050,8 +1070,10 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         destroy_problem(p);
         return s;
     }
-    if (cudaMallocHost(&p->h_count, 3 * sizeof(unsigned long long)) != cudaSuccess) {
-        p->h_count = nullptr;
+    if (cudaHostAlloc(&p->h_count, 3 * sizeof(unsigned long long), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&p->d_count, p->h_count, 0) != cudaSuccess ||
+        cudaHostAlloc(&p->h_stats, sizeof(StatsExport), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&p->d_stats, p->h_stats, 0) != cudaSuccess) {
         destroy_problem(p);
         return HWW_ERR_OOM;
     }

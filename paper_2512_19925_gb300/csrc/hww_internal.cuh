@@ -71,6 +71,14 @@ struct StepDev {
     unsigned long long ncensus;    // census bank size of the step
 };
 
+// a step's statistics as the host reads them back: the counters, the step
+// state and the error word
+struct StatsExport {
+    unsigned long long stats[ST_COUNT];
+    StepDev sd;
+    unsigned err;
+};
+
 // one start-bank particle (position, direction, cell) in one aligned record,
 // so that a comb copy is one scattered store and a bank read one load:
 // 16 bytes for the FP32 path (cell-local offset), 32 for FP64
