@@ -761,8 +761,10 @@ def main(args):
     roof = roofline_hbm(tracking_kernel_name(cnt), STATE_BYTES["fp32"], N * args.steps, fast["census"], track_ms,
                         args.steps, peak, peak_kind)
     roof["launches"] = cnt["track_launches"]
-    roof["traffic"] = TRACK32_DRAM_BYTES_PER_START * N if TRACK32_DRAM_BYTES_PER_START else None
-    roof["traffic_note"] = TRACK32_DRAM_NOTE
+    # the measured traffic belongs to the event kernel at the default size
+    measured = TRACK32_DRAM_BYTES_PER_START and roof["kernel"] == "track32_event_kernel" and N == 10_000_000
+    roof["traffic"] = TRACK32_DRAM_BYTES_PER_START * N if measured else None
+    roof["traffic_note"] = TRACK32_DRAM_NOTE if measured else None
     roof["census_per_step"] = fast["census"] / args.steps
 
     if rank != 0:
