@@ -275,3 +275,29 @@ def test_large_comb_groups_parity():
     assert seen >= {1, 2, 3, 4}, seen  # 3..32, 33..256, 257..2048 and beyond 2048 all met
     g.close()
     o.close()
+
+
+def test_population_dies_out():
+    # a pure absorber a thousand mean free paths thick per cell: no particle
+    # survives a step's flight, so the census is empty, the comb gets no
+    # weight (W = 0), the next bank is empty with weight 0, and every later
+    # step runs its kernels over zero items
+    wl = workloads.plain_slab(particles_per_step=5003)
+    wl["edges"] = np.linspace(-1.0, 1.0, 41)
+    wl["sigma_t"] = np.full(40, 1000.0)
+    wl["c"] = np.full(40, 0.0)
+    stats = run_parity(wl, 4)
+    assert stats[0]["segments"] > 0 and stats[0]["census"] == 0 and stats[0]["n_next"] == 0
+    assert all(s["segments"] == 0 and s["census"] == 0 for s in stats[1:])
+    # the FP32 path, with either tracking loop, through the same empty steps
+    wl["precision"] = "fp32"
+    for kind in (hww.TRACK_EVENT, hww.TRACK_WARP):
+        p = hww.Problem.from_workload(wl)
+        try:
+            p.set_tracking(kind)
+            for n in range(4):
+                s = p.run_step()
+                assert s["census"] == 0 and s["n_next"] == 0, (kind, n)
+                assert (s["segments"] > 0) == (n == 0), (kind, n)
+        finally:
+            p.close()
