@@ -62,9 +62,8 @@ SCORE_BYTES = 48
 # kernel of the timed steps (track32_event_kernel) moves per start particle,
 # measured by ncu (profiles/track32_event_kernel_plain_at_scale_fp32.txt);
 # set to None whenever that kernel changes.
-TRACK32_DRAM_BYTES_PER_START = 95.4
-TRACK32_DRAM_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of track32_event_kernel over steps 6..25 "
-                     "at 1e7 particles/step (one pass), mean per launch: 954.0 MB")
+TRACK32_DRAM_BYTES_PER_START = None
+TRACK32_DRAM_NOTE = None
 
 
 def tracking_kernel_name(counters):
@@ -761,8 +760,10 @@ def main(args):
     roof = roofline_hbm(tracking_kernel_name(cnt), STATE_BYTES["fp32"], N * args.steps, fast["census"], track_ms,
                         args.steps, peak, peak_kind)
     roof["launches"] = cnt["track_launches"]
-    # the measured traffic belongs to the event kernel at the default size
-    measured = TRACK32_DRAM_BYTES_PER_START and roof["kernel"] == "track32_event_kernel" and N == 10_000_000
+    # the measured traffic is the event kernel's, one wave-0 launch per step,
+    # at the default size
+    measured = (TRACK32_DRAM_BYTES_PER_START and cnt.get("event_launches", 0) == args.steps and
+                N == 10_000_000)
     roof["traffic"] = TRACK32_DRAM_BYTES_PER_START * N if measured else None
     roof["traffic_note"] = TRACK32_DRAM_NOTE if measured else None
     roof["census_per_step"] = fast["census"] / args.steps

@@ -332,22 +332,20 @@ typedef struct {
  *   HWW_TRACK_WARP  a warp-synchronous history loop: each lane follows one
  *                   track event by event and takes new work (daughters from
  *                   its warp's stack, start particles) when its track ends;
- *   HWW_TRACK_EVENT an event-based loop: two 512-thread blocks per SM each
- *                   keep a ring of live particles in shared memory and
+ *   HWW_TRACK_EVENT an event-based loop: blocks of 256 threads (up to four per
+ *                   SM) each keep a ring of live particles in shared memory and
  *                   advance all of them by one event per pass, appending
  *                   survivors and daughters after a block-wide scan;
- *   HWW_TRACK_AUTO  the event loop until one of its steps overflows its rings
- *                   into the record queue, then the warp loop for the rest
- *                   of the run (the default for FP32 problems whose mesh
- *                   leaves room for the rings; HWW_TRACK_WARP otherwise and
- *                   for FP64).
+ *   HWW_TRACK_AUTO  the event loop where the mesh leaves room for its rings,
+ *                   the warp loop otherwise (the default; FP64 problems track
+ *                   with their own loop).
  * Both loops draw the same random numbers and do the same arithmetic, so a
  * step gives bit-identical tallies, census and next start bank with either;
  * the record waves (overflow, multiplying collisions' extra particles)
  * always run the warp loop.  HWW_ERR_ARG for an unknown kind, for
- * HWW_TRACK_EVENT or HWW_TRACK_AUTO on an FP64 problem or on a mesh whose
- * tallies (24 I bytes) leave a block less than 48 KB of ring.  Applies from
- * the next step (setting a kind restarts HWW_TRACK_AUTO's choice). */
+ * HWW_TRACK_EVENT or HWW_TRACK_AUTO on an FP64 problem, for HWW_TRACK_EVENT
+ * on a mesh whose tallies (24 I bytes) leave even one block per SM less than
+ * 24 KB of ring.  Applies from the next step. */
 hww_status hww_set_tracking(hww_problem* p, int32_t kind);
 /* Turn CUDA-event timing of the tracking launches on (1) or off (0). */
 hww_status hww_set_timing(hww_problem* p, int32_t enable);

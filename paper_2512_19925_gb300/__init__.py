@@ -426,8 +426,9 @@ class Problem:
     def set_tracking(self, kind):
         """The start-bank wave's kernel: TRACK_WARP (warp-synchronous
         history loop), TRACK_EVENT (event-based ring loop, FP32 only) or
-        TRACK_AUTO (the event loop until a step overflows its rings, then the
-        warp loop; the FP32 default); all give bit-identical steps."""
+        TRACK_AUTO (the event loop where the mesh leaves room for its rings,
+        else the warp loop; the FP32 default); all give bit-identical
+        steps."""
         _check(load().hww_set_tracking(self._h, int(kind)), "hww_set_tracking")
 
     def counters(self):

@@ -119,9 +119,7 @@ struct hww_problem {
     // launch accounting
     int timing = 0;
     int track_kind = HWW_TRACK_WARP;  // FP32 wave-0 tracking kernel (hww_set_tracking)
-    int ev_cap = 0;                   // the event kernel's ring capacity
-    int auto_warp = 0;                // HWW_TRACK_AUTO: an event-kernel step needed a record wave
-    int wave0_event = 0;              // the current step's wave 0 ran the event kernel
+    EvShape ev{0, 0};                 // the event kernel's blocks per SM and ring capacity
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     long long kernel_launches = 0, track_launches = 0, event_launches = 0;
     double track_ms = 0.0;
@@ -367,11 +365,10 @@ void launch_track(hww_problem* p, const TrackArgs<double>& a) {
 }
 void launch_track(hww_problem* p, const TrackArgs<float>& a) {
     if (p->timing) cudaEventRecord(p->ev_a, p->stream);
-    const bool ev = a.from_bank && (p->track_kind == HWW_TRACK_EVENT ||
-                                    (p->track_kind == HWW_TRACK_AUTO && !p->auto_warp));
-    if (a.from_bank) p->wave0_event = ev ? 1 : 0;
+    const bool ev = a.from_bank && p->ev.blocks_per_sm > 0 &&
+                    (p->track_kind == HWW_TRACK_EVENT || p->track_kind == HWW_TRACK_AUTO);
     if (ev) {
-        launch_track_fp32_event(a, p->nsm, p->ev_cap, p->stream);
+        launch_track_fp32_event(a, p->nsm, p->ev, p->stream);
         ++p->event_launches;
     } else {
         launch_track_fp32(a, p->track_grid, TRACK_BLOCK, p->track_smem, p->stream);
@@ -446,10 +443,6 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b, long long lo = 0, long lo
         ++waves;
     }
     p->last_waves = waves;
-    // automatic choice: the event kernel until one of its steps overflows its
-    // rings into the record queue (late steps, many daughters per source
-    // particle, where the warp loop is as fast without a second wave)
-    if (p->track_kind == HWW_TRACK_AUTO && p->wave0_event && waves > 1) p->auto_warp = 1;
     return HWW_OK;
 }
 
@@ -1139,12 +1132,13 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
                          : track_blocks_per_sm_fp64(TRACK_BLOCK, p->track_smem, p->P2 > 0);
     if (per_sm < 1) per_sm = 1;
     p->track_grid = p->nsm * per_sm;
-    // FP32 problems choose their wave-0 kernel step by step where the
-    // event kernel's rings fit the mesh
+    // FP32 problems track wave 0 with the event kernel where its rings fit
+    // the mesh (measured as fast as or faster than the warp loop on every
+    // step of the slab and shield workloads, its record waves included)
     if (p->fp32) {
-        const int cap = ev_ring_cap(I);
-        if (cap > 0 && track_event_smem_optin_fp32(I, cap) == 0) {
-            p->ev_cap = cap;
+        const EvShape sh = ev_shape(I);
+        if (sh.blocks_per_sm > 0 && track_event_smem_optin_fp32(I, sh.cap) == 0) {
+            p->ev = sh;
             p->track_kind = HWW_TRACK_AUTO;
         }
     }
@@ -1465,13 +1459,16 @@ hww_status hww_set_tracking(hww_problem* p, int32_t kind) {
     if (kind != HWW_TRACK_WARP) {
         if (!p->fp32) return HWW_ERR_ARG;
         HWW_CK(cudaSetDevice(p->device));
-        const int cap = ev_ring_cap(p->I);
-        if (cap == 0) return HWW_ERR_ARG;
-        if (track_event_smem_optin_fp32(p->I, cap) != 0) return HWW_ERR_CUDA;
-        p->ev_cap = cap;
+        const EvShape sh = ev_shape(p->I);
+        if (sh.blocks_per_sm == 0) {
+            if (kind == HWW_TRACK_EVENT) return HWW_ERR_ARG;
+            p->ev = sh;  // HWW_TRACK_AUTO: the warp loop
+        } else {
+            if (track_event_smem_optin_fp32(p->I, sh.cap) != 0) return HWW_ERR_CUDA;
+            p->ev = sh;
+        }
     }
     p->track_kind = kind;
-    p->auto_warp = 0;
     return HWW_OK;
 }
 

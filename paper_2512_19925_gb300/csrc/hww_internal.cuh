@@ -194,14 +194,19 @@ hww_status record_cuda_error(cudaError_t e);
 // kernels implemented in the tracking translation units
 void launch_track_fp64(const TrackArgs<double>& a, int grid, int block, size_t smem, cudaStream_t s);
 void launch_track_fp32(const TrackArgs<float>& a, int grid, int block, size_t smem, cudaStream_t s);
-// the event-based FP32 kernel of wave 0 (start-bank particles): two blocks of
-// 512 threads per SM, each with its tallies and a ring of `cap` particles in
-// dynamic shared memory; ev_ring_cap gives the ring for a mesh of I cells on
-// the current device (0: the mesh leaves no room)
-int ev_ring_cap(int I);
+// the event-based FP32 kernel of wave 0 (start-bank particles): blocks of
+// 256 threads, up to four per SM, each with its tallies and a ring of `cap`
+// particles in dynamic shared memory; ev_shape gives blocks per SM and the
+// ring for a mesh of I cells on the current device (blocks 0: the mesh leaves
+// no room)
+struct EvShape {
+    int blocks_per_sm;
+    int cap;
+};
+EvShape ev_shape(int I);
 size_t track_event_smem_fp32(int I, int cap);
 int track_event_smem_optin_fp32(int I, int cap);
-void launch_track_fp32_event(const TrackArgs<float>& a, int nsm, int cap, cudaStream_t s);
+void launch_track_fp32_event(const TrackArgs<float>& a, int nsm, const EvShape& shape, cudaStream_t s);
 void launch_track_batch_fp64(const TrackArgs<double>* args, const BatchPlan& plan, int grid, int block, size_t smem,
                              cudaStream_t s);
 void launch_track_batch_fp32(const TrackArgs<float>* args, const BatchPlan& plan, int grid, int block, size_t smem,

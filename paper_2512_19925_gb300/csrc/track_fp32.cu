@@ -1080,11 +1080,14 @@ __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const T
 // the next wave).  Every event of a pass is one SIMT lane's work, so lanes
 // idle only at divergent outcomes and in a block's last passes; the price is
 // the ring's shared-memory traffic (48 bytes read and written per event) and
-// three block barriers per pass, which the SM's second block hides.
+// three block barriers per pass, which the SM's other blocks hide (small
+// blocks, several per SM: a barrier waits for fewer warps).
 // ---------------------------------------------------------------------------
-constexpr int EV_THREADS = 512;
+constexpr int EV_THREADS = 256;
 constexpr int EV_WARPS = EV_THREADS / 32;
-constexpr int EV_BLOCKS_PER_SM = 2;
+// up to four blocks per SM (registers are budgeted for four); fewer where a
+// large mesh's tallies leave four blocks less than two passes of ring
+constexpr int EV_MAX_BLOCKS_PER_SM = 4;
 constexpr int EV_REC_BYTES = 48;  // ring bytes per particle
 
 // the ring's field arrays over a runtime capacity (the shared memory the
@@ -1164,7 +1167,7 @@ __device__ __forceinline__ void ev_start(const TrackArgs<float>& a, const BlockS
 
 __device__ __forceinline__ int ring_slot(int s, int cap) { return s >= cap ? s - cap : s; }
 
-__global__ void __launch_bounds__(EV_THREADS, EV_BLOCKS_PER_SM) track32_event_kernel(TrackArgs<float> a, int cap) {
+__global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_event_kernel(TrackArgs<float> a, int cap) {
     extern __shared__ long long sm[];
     __shared__ unsigned long long s_stats[ST_COUNT];
     __shared__ BlockScalars s_bs;
@@ -1393,29 +1396,34 @@ void launch_track_fp32(const TrackArgs<float>& a, int grid, int block, size_t sm
     track32_kernel<<<grid, block, smem, s>>>(a);
 }
 
-// the event kernel's ring capacity for a mesh of I cells: the shared memory a
-// block gets with two blocks per SM, less the tallies, in whole warps of
-// particles; 0 when that leaves less than two passes of room
-int ev_ring_cap(int I) {
+// the event kernel's launch shape for a mesh of I cells on the current
+// device: the most blocks per SM (4, 3, 2, 1) whose share of the SM's shared
+// memory, less the tallies, holds at least two passes of ring, and that ring
+// in whole warps of particles; blocks 0 when even one block per SM does not
+EvShape ev_shape(int I) {
     int dev = 0, per_sm = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const long long static_bytes = 1024 + 2048;  // the kernel's own variables and the per-block reserve, rounded up
-    const long long budget = std::min<long long>(optin, per_sm / EV_BLOCKS_PER_SM - static_bytes);
     const long long tallies = (long long)sizeof(long long) * ROWS32 * I;
-    long long cap = (budget - tallies) / EV_REC_BYTES;
-    cap = cap / 32 * 32;
-    // the pass's scan word holds EV_THREADS x cap outputs in 21 bits
-    return cap >= 2 * EV_THREADS ? (int)std::min<long long>(cap, (1 << 21) / EV_THREADS - 32) : 0;
+    for (int bps = EV_MAX_BLOCKS_PER_SM; bps >= 1; --bps) {
+        const long long budget = std::min<long long>(optin, per_sm / bps - static_bytes);
+        long long cap = (budget - tallies) / EV_REC_BYTES;
+        cap = cap / 32 * 32;
+        // the pass's scan word holds EV_THREADS x cap outputs in 21 bits
+        if (cap >= 2 * EV_THREADS) return EvShape{bps, (int)std::min<long long>(cap, (1 << 21) / EV_THREADS - 32)};
+    }
+    return EvShape{0, 0};
 }
 
 size_t track_event_smem_fp32(int I, int cap) {
     return sizeof(long long) * (size_t)ROWS32 * (size_t)I + (size_t)EV_REC_BYTES * (size_t)cap;
 }
 
-void launch_track_fp32_event(const TrackArgs<float>& a, int nsm, int cap, cudaStream_t s) {
-    track32_event_kernel<<<nsm * EV_BLOCKS_PER_SM, EV_THREADS, track_event_smem_fp32(a.I, cap), s>>>(a, cap);
+void launch_track_fp32_event(const TrackArgs<float>& a, int nsm, const EvShape& shape, cudaStream_t s) {
+    track32_event_kernel<<<nsm * shape.blocks_per_sm, EV_THREADS, track_event_smem_fp32(a.I, shape.cap), s>>>(
+        a, shape.cap);
 }
 
 int track_event_smem_optin_fp32(int I, int cap) {
