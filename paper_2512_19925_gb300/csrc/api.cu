@@ -74,7 +74,7 @@ struct hww_problem {
     unsigned long long *tile_c = nullptr, *tile_w = nullptr;
     MemberRec* member = nullptr;
     unsigned long long* cpre = nullptr;    // comb prefix C0 of every census particle (census-sized)
-    uint32_t* glist = nullptr;             // ids of comb groups of 3+ members by size class (census-sized)
+    GroupRec* glist = nullptr;             // records of the comb groups of 2+ members by size class (census-sized)
     // closures and LOSM
     // two closure sets (phi I+2, J I+1, F I+2, P 2): `cur` holds the
     // initial conditions of the next step, the other is built at t^n

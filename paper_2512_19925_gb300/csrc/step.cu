@@ -118,8 +118,9 @@ __device__ __forceinline__ int size_class(uint32_t g) {
 }
 
 // The scan's last pass: each tile's records (staged in shared memory, so
-// that they are written coalesced) and the ids of its groups of two or more
-// members appended to their size class's list.  A thread's per-class counts
+// that they are written coalesced), and the records of its groups of two or
+// more members appended to their size class's list (the group passes read
+// them there, without a gather by source id).  A thread's per-class counts
 // are 16-bit fields of two words (classes 0-3, 4-6; a tile has at most 2048
 // groups), scanned over the block, so each class takes one global
 // reservation per tile.
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) scan_apply_kernel(ScanArgs a) {
         if (c < 0) continue;
         unsigned long long& e = c < 4 ? ea : eb;
         const unsigned long long pos = s_gbase[c] + ((e >> (16 * (c & 3))) & 0xFFFFull);
-        a.glist[a.glist_off[c] + pos] = (uint32_t)(base + (long long)t * SCAN_ITEMS + k);
+        a.glist[a.glist_off[c] + pos] = s_out[t * SCAN_ITEMS + k];
         e += 1ull << (16 * (c & 3));
     }
 }
@@ -257,14 +258,14 @@ __device__ __forceinline__ bool key_less(uint64_t la, uint32_t ja, uint64_t lb, 
 // handles the 32/S groups [e0, e0 + 32/S) of a class list (the whole warp,
 // converged).
 template <class Real, int S>
-__device__ __forceinline__ void seg_groups(const CombArgs<Real>& a, const uint32_t* list, unsigned long long n,
+__device__ __forceinline__ void seg_groups(const CombArgs<Real>& a, const GroupRec* list, unsigned long long n,
                                            unsigned long long e0, unsigned long long& coll) {
     const int lane = threadIdx.x & 31, seg = lane / S, li = lane % S;
     const unsigned long long e = e0 + seg;
     uint32_t g = 0;
     unsigned long long base = 0, C = 0;
     if (e < n) {
-        const GroupRec G = a.gro[list[e]];
+        const GroupRec G = list[e];
         g = G.cnt;
         base = G.off;
         C = G.offw;
@@ -392,13 +393,13 @@ __global__ void __launch_bounds__(32 * MID_WARPS) comb_mid_kernel(CombArgs<Real>
     __shared__ int s_next[MID_WARPS][MID_MAX];
     __shared__ int s_head[MID_WARPS][MID_MAX];
     const unsigned long long n = a.glist_n[MID_CLASS];
-    const uint32_t* list = a.glist + a.glist_off[MID_CLASS];
+    const GroupRec* list = a.glist + a.glist_off[MID_CLASS];
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const BucketView B{s_lin[wp], s_w[wp], s_j[wp], s_next[wp], s_head[wp]};
     unsigned long long coll = 0;
     for (unsigned long long e = (unsigned long long)blockIdx.x * MID_WARPS + wp; e < n;
          e += (unsigned long long)gridDim.x * MID_WARPS) {  // warp-uniform
-        const GroupRec G = a.gro[list[e]];
+        const GroupRec G = list[e];
         const int g = (int)G.cnt;
         const int bits = bucket_bits(G.cnt, 5);
         const int nb = 1 << bits, per = nb >> 5;
@@ -437,11 +438,11 @@ __global__ void __launch_bounds__(BIG_T) comb_big_kernel(CombArgs<Real> a) {
                        reinterpret_cast<int*>(s_big + 2 * BIG_CAP) + BIG_CAP,
                        reinterpret_cast<int*>(s_big + 2 * BIG_CAP) + 2 * BIG_CAP};
     const unsigned long long nbig = a.glist_n[BIG_CLASS];
-    const uint32_t* list = a.glist + a.glist_off[BIG_CLASS];
+    const GroupRec* list = a.glist + a.glist_off[BIG_CLASS];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     unsigned long long coll = 0;
     for (unsigned long long e = blockIdx.x; e < nbig; e += gridDim.x) {
-        const GroupRec G = a.gro[list[e]];
+        const GroupRec G = list[e];
         const uint32_t g = G.cnt;
         const unsigned long long base = G.off;
         const unsigned long long C = G.offw;

@@ -39,8 +39,8 @@ struct ScanArgs {
     unsigned long long* tile_c;
     unsigned long long* tile_w;
     GroupRec* out;  // n+1 entries; entry n holds the totals
-    // the group lists by size class, filled by the scan's last pass
-    uint32_t* glist;
+    // the group lists by size class (group records), filled by the scan's last pass
+    GroupRec* glist;
     long long glist_off[COMB_LISTS];
     unsigned long long* glist_n;  // [COMB_LISTS] list lengths (cleared with the step's accumulators)
 };
@@ -66,7 +66,7 @@ struct CombArgs {
     unsigned long long* stats;
     unsigned* err;
     unsigned long long* cpre;        // [cen_cap] comb prefix C0 of every census particle
-    uint32_t* glist;                 // ids of groups of 3+ members, by size class (COMB_LISTS lists)
+    const GroupRec* glist;           // records of the groups of 2+ members, by size class (COMB_LISTS lists)
     long long glist_off[COMB_LISTS]; // start of each class's list in glist
     unsigned long long* glist_n;     // [COMB_LISTS] list lengths (cleared with the step's accumulators)
     int I;             // cells (census tallies)
