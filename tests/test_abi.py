@@ -48,3 +48,37 @@ def test_no_fallback_when_library_missing(tmp_path, monkeypatch):
     monkeypatch.setattr(hww, "_lib", None)
     with pytest.raises(RuntimeError):
         hww.load(build_if_missing=False)
+
+
+STRUCTS = [("hww_problem_desc", hww.ProblemDesc), ("hww_step_stats", hww.StepStats),
+           ("hww_counters", hww.Counters), ("hww_batch_stats", hww.BatchStats)]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # the binding's ctypes mirrors of the public structs against the header,
+    # compiled by the host C compiler: every field at the same offset, and
+    # the same size (a field the binding lacks shows as a size difference)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "hww.h"', "int main(void) {"]
+    for cname, py in STRUCTS:
+        lines.append('    printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('    printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for cname, py in STRUCTS:
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
