@@ -316,8 +316,12 @@ void destroy_batch(hww_batch* b);
 
 /* Launch accounting of a problem since creation or the last reset: kernels
  * the library launched, tracking-kernel launches (of which event_launches
- * ran the event loop), and (when timing is on) the device time of the
- * tracking launches measured with CUDA events on the problem's stream. */
+ * ran the event loop), the particles the event loop's blocks spilled (a
+ * pass's outputs beyond the block's ring wait in the block's slice of the
+ * record queue that wave 0 leaves idle, and the block tracks them itself;
+ * what the slice cannot hold goes to the record queue and a further wave),
+ * and (when timing is on) the device time of the tracking launches measured
+ * with CUDA events on the problem's stream. */
 typedef struct {
     int64_t kernel_launches;
     int64_t track_launches;
@@ -325,6 +329,7 @@ typedef struct {
     int64_t steps;
     int64_t census_capacity, queue_capacity;
     int64_t event_launches;
+    int64_t spilled;
 } hww_counters;
 
 /* The kernel that tracks an FP32 problem's start-bank particles (the events

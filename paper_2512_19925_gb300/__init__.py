@@ -59,7 +59,7 @@ class StepStats(C.Structure):
 class Counters(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("track_launches", C.c_int64), ("track_ms", C.c_double),
                 ("steps", C.c_int64), ("census_capacity", C.c_int64), ("queue_capacity", C.c_int64),
-                ("event_launches", C.c_int64)]
+                ("event_launches", C.c_int64), ("spilled", C.c_int64)]
 
 
 class BatchStats(C.Structure):

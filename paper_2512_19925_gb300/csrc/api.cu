@@ -87,10 +87,12 @@ struct hww_problem {
     LosmWork work{};
     StepDev* sd = nullptr;
     unsigned* err = nullptr;
-    // pinned: after each tracking wave the record count, the census count and
-    // the error word (its low 32 bits), read with one synchronize
+    // pinned: after each tracking wave the record count, the census count,
+    // the error word (its low 32 bits) and the spill count, read with one
+    // synchronize
     unsigned long long* h_count = nullptr;
     unsigned long long* d_count = nullptr;  // the device's view of h_count (mapped)
+    unsigned long long* spill_n = nullptr;  // device: particles the event loop spilled since the last reset
     StatsExport* h_stats = nullptr;          // pinned, mapped: a step's statistics read back
     StatsExport* d_stats = nullptr;
     // host state
@@ -122,6 +124,7 @@ struct hww_problem {
     EvShape ev{0, 0};                 // the event kernel's blocks per SM and ring capacity
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     long long kernel_launches = 0, track_launches = 0, event_launches = 0;
+    long long spilled = 0;  // spill_n as of the last tracking wave's synchronize
     double track_ms = 0.0;
 };
 
@@ -343,6 +346,7 @@ TrackArgs<Real> base_track_args(hww_problem* p, const Banks<Real>& b) {
     a.bnd = p->bnd;
     a.stats = p->stats;
     a.err = p->err;
+    a.spilled = p->spill_n;
     a.R = p->R;
     a.P2 = p->P2;
     a.region = p->d_region;
@@ -399,12 +403,14 @@ __global__ void export_stats_kernel(const unsigned long long* stats, const StepD
 }
 
 // after a tracking wave: the record count of its output queue, the census
-// count and the error word, into the mapped h_count
+// count, the error word and the spill count, into the mapped h_count
 __global__ void export_wave_kernel(const unsigned long long* qcount, const unsigned long long* ncen,
-                                   const unsigned* err, unsigned long long* out) {
+                                   const unsigned* err, const unsigned long long* spilled,
+                                   unsigned long long* out) {
     out[0] = *qcount;
     out[1] = *ncen;
     out[2] = *err;
+    out[3] = *spilled;
 }
 
 // the tracking waves of start-bank items [lo, hi): wave 0 from the bank,
@@ -422,10 +428,11 @@ hww_status track_waves(hww_problem* p, Banks<Real>& b, long long lo = 0, long lo
     HWW_CK(cudaGetLastError());
     int cur = 0, waves = 1;
     for (;;) {
-        export_wave_kernel<<<1, 1, 0, p->stream>>>(b.q[cur].count, p->counts, p->err, p->d_count);
+        export_wave_kernel<<<1, 1, 0, p->stream>>>(b.q[cur].count, p->counts, p->err, p->spill_n, p->d_count);
         HWW_CK(cudaGetLastError());
         HWW_CK(cudaStreamSynchronize(p->stream));
         account_track_time(p);
+        p->spilled = (long long)p->h_count[3];
         p->q_peak = std::max(p->q_peak, (long long)*p->h_count);
         if (*p->h_count == 0) break;
         if (waves >= MAX_WAVES) {
@@ -1037,7 +1044,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         (s = dalloc(p, &p->mat.inv_den, I + 2)) || (s = dalloc(p, &p->mat.vf, I + 2)) ||
         (s = dalloc(p, &p->mat.cp, I + 2)) || (s = dalloc(p, &p->mat.nA, I + 2)) ||
         (s = dalloc(p, &p->norm, (size_t)B * I + 6 * (size_t)I + 8)) || (s = dalloc(p, &p->sd, 1)) ||
-        (s = dalloc(p, &p->err, 1))) {
+        (s = dalloc(p, &p->err, 1)) || (s = dalloc(p, &p->spill_n, 1))) {
         destroy_problem(p);
         return s;
     }
@@ -1063,7 +1070,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
         destroy_problem(p);
         return s;
     }
-    if (cudaHostAlloc(&p->h_count, 3 * sizeof(unsigned long long), cudaHostAllocMapped) != cudaSuccess ||
+    if (cudaHostAlloc(&p->h_count, 4 * sizeof(unsigned long long), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void**)&p->d_count, p->h_count, 0) != cudaSuccess ||
         cudaHostAlloc(&p->h_stats, sizeof(StatsExport), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void**)&p->d_stats, p->h_stats, 0) != cudaSuccess) {
@@ -1104,6 +1111,7 @@ hww_status create_problem(const hww_problem_desc* d, hww_problem** out) {
     p->mat.bc_r = d->bc_right;
     up(p->sd, &sd, sizeof(StepDev));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->spill_n, 0, sizeof(unsigned long long), p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
         destroy_problem(p);
@@ -1488,6 +1496,7 @@ hww_status hww_get_counters(const hww_problem* p, hww_counters* out) {
     out->kernel_launches = p->kernel_launches;
     out->track_launches = p->track_launches;
     out->event_launches = p->event_launches;
+    out->spilled = p->spilled;
     out->track_ms = p->track_ms;
     out->steps = p->steps;
     out->census_capacity = p->cen_cap;
@@ -1500,7 +1509,10 @@ hww_status hww_reset_counters(hww_problem* p) {
     p->kernel_launches = 0;
     p->track_launches = 0;
     p->event_launches = 0;
+    p->spilled = 0;
     p->track_ms = 0.0;
+    HWW_CK(cudaSetDevice(p->device));
+    HWW_CK(cudaMemsetAsync(p->spill_n, 0, sizeof(unsigned long long), p->stream));
     return HWW_OK;
 }
 

@@ -166,6 +166,7 @@ struct TrackArgs {
     Acc128* bnd;    // 6
     unsigned long long* stats;
     unsigned* err;
+    unsigned long long* spilled;  // running count of the particles the event loop spilled (null: not kept)
     // likelihood-ratio derivatives (P2 = 2R > 0): score j < R is that of
     // Sigma_t of region j, R + r that of c of region r
     int R, P2;

@@ -1075,9 +1075,12 @@ __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const T
 // over the warp's prefix of daughter counts, its state taken by shuffles,
 // its lineage key drawn by the lane).  Fresh particles from the block's
 // contiguous range of the start bank keep at least one pass of work in the
-// ring.  Outputs beyond the ring's room, and the extra particles of a
-// multiplying collision, go to the record queue (the warp loop takes them in
-// the next wave).  Every event of a pass is one SIMT lane's work, so lanes
+// ring.  Outputs beyond the ring's room wait in the block's spill, a FIFO in
+// the block's own slice of the record queue that wave 0 leaves idle (it reads
+// no records); the refill drains the spill before it takes fresh particles,
+// so a block tracks its own overflow.  Only what the slice cannot hold, and
+// the extra particles of a multiplying collision, go to the record queue
+// (the warp loop takes them in the next wave).  Every event of a pass is one SIMT lane's work, so lanes
 // idle only at divergent outcomes and in a block's last passes; the price is
 // the ring's shared-memory traffic (48 bytes read and written per event) and
 // three block barriers per pass, which the SM's other blocks hide (small
@@ -1167,6 +1170,35 @@ __device__ __forceinline__ void ev_start(const TrackArgs<float>& a, const BlockS
 
 __device__ __forceinline__ int ring_slot(int s, int cap) { return s >= cap ? s - cap : s; }
 
+// a spilled particle in slot i of the idle record queue, every field of the
+// ring's copy kept (1/mu and the tally weight in the chunk words, which a
+// spilled particle does not use)
+__device__ __forceinline__ void spill_put(const RecQ<float>& s, long long i, const P32& q) {
+    s.x[i] = q.xo;
+    s.mu[i] = q.mu;
+    s.tau[i] = q.tau;
+    s.w[i] = q.w;
+    s.cell[i] = q.cell;
+    s.id[i] = q.id;
+    s.lin[i] = q.lin;
+    s.e[i] = q.e;
+    s.jstart[i] = __float_as_uint(q.inv_mu);
+    s.jcount[i] = __float_as_uint(q.tw);
+}
+
+__device__ __forceinline__ void spill_get(const RecQ<float>& s, long long i, P32& q) {
+    q.xo = s.x[i];
+    q.mu = s.mu[i];
+    q.tau = s.tau[i];
+    q.w = s.w[i];
+    q.cell = s.cell[i];
+    q.id = s.id[i];
+    q.lin = s.lin[i];
+    q.e = s.e[i];
+    q.inv_mu = __uint_as_float(s.jstart[i]);
+    q.tw = __uint_as_float(s.jcount[i]);
+}
+
 __global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_event_kernel(TrackArgs<float> a, int cap) {
     extern __shared__ long long sm[];
     __shared__ unsigned long long s_stats[ST_COUNT];
@@ -1209,17 +1241,38 @@ __global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_even
     // ring state, the same in every thread: particles [head, head + count)
     long long next = first;  // the next start particle of the range
     int head = 0, count = 0;
+    // spill state, the same in every thread: particles in slots [sp_h,
+    // sp_h + sp_n) (mod SC) of the block's slice; the first sp_rdy of them
+    // were written before the last pass's barriers, so any thread may read
+    // them (a pass's own spills become readable one pass later)
+    const int SC = (int)min(a.rin.cap / (long long)gridDim.x, (long long)(INT_MAX / 2));
+    const long long sbase = (long long)blockIdx.x * SC;
+    int sp_h = 0, sp_n = 0, sp_rdy = 0;
+    long long sp_total = 0;  // particles the block spilled
     unsigned long long mycnt = 0;  // lane k < EB_COUNT: counter kLaneStat[k]; then daughters, max events
     for (;;) {
-        // ---- keep a pass of work in the ring ----
-        const int add = (int)max(0LL, min((long long)min(EV_THREADS - count, cap - count), last - next));
-        if ((int)t < add) {
+        // ---- keep a pass of work in the ring: spilled particles first ----
+        const int want = max(0, min(EV_THREADS - count, cap - count));
+        const int fs = min(want, sp_rdy);
+        const int add = (int)max(0LL, min((long long)(want - fs), last - next));
+        if ((int)t < fs) {
             P32 q;
-            ev_start(a, bs, birth, k0, k1, next + t, q);
+            const int sl = sp_h + (int)t;
+            spill_get(a.rin, sbase + (sl >= SC ? sl - SC : sl), q);
+            R.put(ring_slot(head + count + (int)t, cap), q);
+        } else if ((int)t < fs + add) {
+            P32 q;
+            ev_start(a, bs, birth, k0, k1, next + ((int)t - fs), q);
             R.put(ring_slot(head + count + (int)t, cap), q);
         }
+        sp_h += fs;
+        if (sp_h >= SC) sp_h -= SC;
+        sp_n -= fs;
+        sp_rdy -= fs;
         next += add;
-        count += add;
+        count += fs + add;
+        // an empty ring after the refill means an empty spill too: a pass
+        // that spilled left the ring full
         if (count == 0) break;
         __syncthreads();
         // ---- the t-th particle from the head: one event ----
@@ -1256,8 +1309,9 @@ __global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_even
         // ---- outputs (a survivor, or a split's daughters) and census: slots ----
         const uint32_t nout = have ? 1u : nd;
         const unsigned cen = (eb >> EB_CENSUS) & 1u;
-        // outputs past the ring's room go to the record queue, so a count is
-        // capped at cap in the scan word (EV_THREADS x cap < 2^21 outputs)
+        // a lane reserves at most cap outputs in the scan word (EV_THREADS x
+        // cap < 2^21 outputs); a split into more daughters (up to
+        // MAX_DAUGHTERS) sends the rest to the record queue
         const unsigned v = (min(nout, (uint32_t)cap) << 11) | cen;
         unsigned incl = v;
         for (int o = 1; o < 32; o <<= 1) {
@@ -1284,9 +1338,21 @@ __global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_even
         const unsigned off = s_wsum[wid] + incl - v;
         const unsigned tot = s_total;
         // the pass's inputs are free now: outputs go at the ring's tail,
-        // into the room the particles not taken leave
+        // into the room the particles not taken leave, then to the spill's
+        // free slots, then to the record queue
         const int tail = ring_slot(head + count, cap);
         const int room = cap - (count - m);
+        const int sp_room = SC - sp_n;
+        const auto place = [&](const P32& x, unsigned long long o) {
+            if (o < (unsigned long long)room) {
+                R.put(ring_slot(tail + (int)o, cap), x);
+            } else if (o - (unsigned long long)room < (unsigned long long)sp_room) {
+                const int sl = sp_h + sp_n + (int)(o - (unsigned long long)room);
+                spill_put(a.rin, sbase + (sl >= SC ? sl - SC : sl), x);
+            } else {
+                push_record(a, x, x.w, x.e, 0u, 0u, warp_reserve(a.rout.count));
+            }
+        };
         if (cen) {
             const unsigned long long slot = s_cbase + (off & 0x7FFu);
             if ((long long)slot < a.cen.cap) {
@@ -1304,12 +1370,7 @@ __global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_even
             }
         }
         const unsigned o0 = off >> 11;
-        if (have) {
-            if ((int)o0 < room)
-                R.put(ring_slot(tail + (int)o0, cap), q);
-            else
-                push_record(a, q, q.w, q.e, 0u, 0u, warp_reserve(a.rout.count));
-        }
+        if (have) place(q, o0);
         // the warp's daughters, round by round over all its lanes
         uint32_t dincl = nd;  // daughters of lanes 0..lane
         for (int o = 1; o < 32; o <<= 1) {
@@ -1351,9 +1412,10 @@ __global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_even
                     const uint32_t j = g - pbase;
                     d.lin = lineage_hash(plin, pe, j);
                     d.e = 0;
-                    const unsigned long long sj = (unsigned long long)po + j;
-                    if (sj < (unsigned long long)room)
-                        R.put(ring_slot(tail + (int)sj, cap), d);
+                    // the parent's scan word reserved at most cap outputs;
+                    // its daughters past them have no slot of their own
+                    if (j < (uint32_t)cap)
+                        place(d, (unsigned long long)po + j);
                     else
                         push_record(a, d, d.w, 0u, 0u, 0u, warp_reserve(a.rout.count));
                 }
@@ -1372,9 +1434,15 @@ __global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_even
             mycnt += cadd;
             if (lane == (unsigned)LANE_MAXEV) mycnt = max(mycnt, (unsigned long long)smax);
         }
-        // the next pass's refill barrier orders these writes before its reads
+        // the next pass's refill barrier orders the ring's writes before its
+        // reads; the spill's writes wait one more pass (sp_rdy)
+        const int nput = (int)(tot >> 11);
         head = ring_slot(head + m, cap);
-        count = count - m + min((int)(tot >> 11), room);
+        count = count - m + min(nput, room);
+        const int nsp = min(max(0, nput - room), sp_room);
+        sp_rdy = sp_n;
+        sp_n += nsp;
+        sp_total += nsp;
     }
     // the warp's counts into the block's
     if (lane < (unsigned)EB_COUNT) {
@@ -1384,6 +1452,7 @@ __global__ void __launch_bounds__(EV_THREADS, EV_MAX_BLOCKS_PER_SM) track32_even
     } else if (lane == (unsigned)LANE_MAXEV) {
         if (mycnt) atomicMax(&s_stats[ST_MAX_EVENTS], mycnt);
     }
+    if (t == 0 && sp_total && a.spilled) atomicAdd(a.spilled, (unsigned long long)sp_total);
     __syncthreads();
     flush_jf(tl32, I, a.tl);
     if (b_blk >= 0) flush_batch_row(tl32, I, a.batch, b_blk, false);

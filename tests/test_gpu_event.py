@@ -7,9 +7,11 @@ words, counts and next start bank with either kernel, whatever order the
 kernels visit particles in.  Checked bit for bit, step after step, on the
 plain slab, the reflecting and leaking shield, the multiplying medium (whose
 extra particles go through the record queue), a split storm that overflows
-the particle pools into the record queue, a ragged bank that leaves most
-blocks' pools short, and the 1000-cell slab at its full 1e7 particles per
-step.
+the rings into the blocks' spills, splits into more daughters than a ring
+holds (the rest go to the record queue), a ragged bank that leaves most
+blocks' rings short, the 1000-cell slab at its full 1e7 particles per step,
+and 75 steps of the shield at 1e6 particles per step (spills every step from
+the 40th, giant splits in the thick region).
 """
 import numpy as np
 import pytest
@@ -89,9 +91,8 @@ def test_event_kernel_multiplying_medium():
 
 def test_event_kernel_split_storm_overflows_pools():
     # centers far below the start weight: a particle splits into about forty
-    # daughters at its first window test (about one in ten reaches one in
-    # the step); with 650 start particles a block, a pass's splits make more
-    # daughters than a ring holds, so some leave through the record queue
+    # daughters at its first window test; a pass's splits make more daughters
+    # than a ring holds, so some wait in the block's spill
     wl = workloads.small_variant(workloads.plain_slab(), 200000)
     wl["precision"] = "fp32"
     a, b = pair(wl)
@@ -100,9 +101,32 @@ def test_event_kernel_split_storm_overflows_pools():
         centers = np.full(len(wl["edges"]) - 1, s1["w_bar_next"] / 40.0)
         for p in (a, b):
             p.set_ww_centers(centers)
+        n0 = b.counters()["spilled"]
         sa, sb = assert_same_step(a, b, 2)
-        assert sb["waves"] > 1  # the pools overflowed into the record queue
+        assert b.counters()["spilled"] > n0  # the rings overflowed into the spills
         assert sa["daughters"] > sa["n_start"]
+        assert_same_step(a, b, 3)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_event_kernel_giant_splits_go_to_the_record_queue():
+    # centers 3000 times below the start weight: each split makes about 3000
+    # daughters, more than a ring holds and more than a lane reserves in a
+    # pass's scan (the ring's capacity), so the daughters past that go to the
+    # record queue and a second wave
+    wl = workloads.small_variant(workloads.plain_slab(), 20000)
+    wl["precision"] = "fp32"
+    a, b = pair(wl)
+    try:
+        s1, _ = assert_same_step(a, b, 1)
+        centers = np.full(len(wl["edges"]) - 1, s1["w_bar_next"] / 3000.0)
+        for p in (a, b):
+            p.set_ww_centers(centers)
+        _, sb = assert_same_step(a, b, 2)
+        assert sb["waves"] > 1
+        assert sb["daughters"] > 1000 * sb["split_events"] > 0
         assert_same_step(a, b, 3)
     finally:
         a.close()
@@ -139,8 +163,8 @@ def test_event_kernel_full_size():
 
 def test_auto_choice_keeps_the_event_loop_through_an_overflow():
     # the FP32 default runs the event loop on every step, also on a step
-    # whose rings overflow into the record queue (the warp loop takes the
-    # records); results equal the warp loop's all along
+    # whose rings overflow (into the spills); results equal the warp loop's
+    # all along
     wl = workloads.small_variant(workloads.plain_slab(), 200000)
     wl["precision"] = "fp32"
     a = hww.Problem.from_workload(wl)
@@ -155,12 +179,35 @@ def test_auto_choice_keeps_the_event_loop_through_an_overflow():
         # step 2 overflows the rings (and the census bank: the step is
         # replayed with more room, the event loop again)
         _, sb = assert_same_step(a, b, 2)
-        assert sb["waves"] > 1
+        assert b.counters()["spilled"] > 0
         n2 = b.counters()["event_launches"]
         assert n2 >= 2
         for n in range(3, 6):
             assert_same_step(a, b, n)
         assert b.counters()["event_launches"] == n2 + 3
+    finally:
+        a.close()
+        b.close()
+
+
+def test_event_kernel_shield_late_steps():
+    # the three-region shield at 1e6 particles per step: from about the 40th
+    # step the rings overflow every step, and particles deep in the thick
+    # region split into hundreds of daughters; 75 steps, counts compared every
+    # step and the raw tallies and the bank at the end
+    wl = workloads.shield(particles_per_step=1_000_000, precision="fp32")
+    a, b = pair(wl)
+    try:
+        for n in range(1, 76):
+            sa, sb = a.run_step(), b.run_step()
+            for k in COUNTS:
+                assert sa[k] == sb[k], (n, k, sa[k], sb[k])
+        for kind in RAW:
+            assert np.array_equal(a.get_tallies_raw(kind), b.get_tallies_raw(kind)), kind
+        for x, y in zip(a.get_bank(), b.get_bank()):
+            assert np.array_equal(x, y)
+        assert b.counters()["spilled"] > 0
+        assert sb["lineage_collisions"] == 0
     finally:
         a.close()
         b.close()
