@@ -61,12 +61,10 @@ SCORE_BYTES = 48
 # DRAM bytes (read + write) that one wave-0 launch of the FP32 tracking
 # kernel of the timed steps (track32_event_kernel) moves per start particle,
 # measured by ncu (profiles/track32_event_kernel_plain_at_scale_fp32.txt);
-# set to None whenever that kernel changes.  It was 95.4 B (954 MB per launch
-# at 1e7 particles per step) before the kernel gained its overflow spill, and
-# has not been measured since.
-TRACK32_DRAM_BYTES_PER_START = None
-TRACK32_DRAM_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of track32_event_kernel (wave 0) over steps "
-                     "6..25 at 1e7 particles/step (one pass), mean per launch: 954.0 MB; record waves not included")
+# set to None whenever that kernel changes.
+TRACK32_DRAM_BYTES_PER_START = 95.12
+TRACK32_DRAM_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of track32_event_kernel (wave 0, with its "
+                     "overflow spill) over steps 6..25 at 1e7 particles/step (one pass), mean per launch: 951.2 MB")
 
 
 def tracking_kernel_name(counters):
