@@ -340,13 +340,16 @@ typedef struct {
  *   HWW_TRACK_EVENT an event-based loop: blocks of 256 threads (up to four per
  *                   SM) each keep a ring of live particles in shared memory and
  *                   advance all of them by one event per pass, appending
- *                   survivors and daughters after a block-wide scan;
+ *                   survivors and daughters after a block-wide scan (what
+ *                   the ring cannot hold waits in the block's spill in
+ *                   global memory);
  *   HWW_TRACK_AUTO  the event loop where the mesh leaves room for its rings,
  *                   the warp loop otherwise (the default; FP64 problems track
  *                   with their own loop).
  * Both loops draw the same random numbers and do the same arithmetic, so a
  * step gives bit-identical tallies, census and next start bank with either;
- * the record waves (overflow, multiplying collisions' extra particles)
+ * the record waves (what the spills cannot hold, daughters of splits into
+ * more particles than a ring holds, multiplying collisions' extra particles)
  * always run the warp loop.  HWW_ERR_ARG for an unknown kind, for
  * HWW_TRACK_EVENT or HWW_TRACK_AUTO on an FP64 problem, for HWW_TRACK_EVENT
  * on a mesh whose tallies (24 I bytes) leave even one block per SM less than
