@@ -1078,13 +1078,15 @@ __global__ void __launch_bounds__(TRACK_THREADS, 2) track32_kernel_batch(const T
 // ring.  Outputs beyond the ring's room wait in the block's spill, a FIFO in
 // the block's own slice of the record queue that wave 0 leaves idle (it reads
 // no records); the refill drains the spill before it takes fresh particles,
-// so a block tracks its own overflow.  Only what the slice cannot hold, and
-// the extra particles of a multiplying collision, go to the record queue
-// (the warp loop takes them in the next wave).  Every event of a pass is one SIMT lane's work, so lanes
-// idle only at divergent outcomes and in a block's last passes; the price is
-// the ring's shared-memory traffic (48 bytes read and written per event) and
-// three block barriers per pass, which the SM's other blocks hide (small
-// blocks, several per SM: a barrier waits for fewer warps).
+// so a block tracks its own overflow.  Only what the slice cannot hold, the
+// daughters of a split into more particles than a ring holds, and the extra
+// particles of a multiplying collision go to the record queue (the warp loop
+// takes them in the next wave).  Every event of a pass is one SIMT lane's
+// work, so lanes idle only at divergent outcomes and in a block's last
+// passes; the price is the ring's shared-memory traffic (48 bytes read and
+// written per event) and three block barriers per pass, which the SM's other
+// blocks hide (small blocks, several per SM: a barrier waits for fewer
+// warps).
 // ---------------------------------------------------------------------------
 constexpr int EV_THREADS = 256;
 constexpr int EV_WARPS = EV_THREADS / 32;
